@@ -1,0 +1,179 @@
+/*
+ * puffinn_gb300.h -- C ABI of the GB300 (sm_103a) implementation of PUFFINN's
+ * LSH-forest index and adaptive k-NN query (Aumueller, Christiani, Pagh,
+ * Vesterli, ESA 2019).
+ *
+ * The user supplies only the points, a memory budget and the hash family at
+ * build time, and k plus the recall target 1 - delta at query time (Sec. 1.1,
+ * Sec. 5 "Parameter Choices"; Definition 1 of the (k, delta)-NN problem).
+ *
+ * General conventions
+ *   - Pointers are plain host or device addresses; the library detects which
+ *     with cudaPointerGetAttributes.  Device pointers must be on the device
+ *     that is current when the call is made.  Host inputs are copied to the
+ *     device inside the call; host outputs are written before the call returns.
+ *   - The caller owns every buffer it passes in; the library never frees or
+ *     retains caller memory.  Everything the index needs is copied into
+ *     library-owned device memory by pf_index_build.
+ *   - stream: a cudaStream_t (NULL = the legacy default stream).  Device work
+ *     is ordered on it.  Calls return after synchronising that stream, and the
+ *     returned status includes asynchronous device errors.
+ *   - No C++ exception, abort or exit crosses this boundary.  On error the
+ *     status is negative and pf_last_error_message() (thread-local) explains.
+ *   - Layouts are row-major.  n, Q <= 2^31 - 1; ids are uint32 row numbers of
+ *     the build input.
+ */
+#ifndef PUFFINN_GB300_H
+#define PUFFINN_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pf_index pf_index; /* opaque, owned by the library */
+
+typedef enum {
+  PF_OK = 0,
+  PF_ERR_INVALID_ARG = -1,      /* a size, pointer or option is out of range */
+  PF_ERR_BUDGET_TOO_SMALL = -2, /* the memory budget leaves room for no repetition */
+  PF_ERR_OOM = -3,              /* a device allocation failed */
+  PF_ERR_CUDA = -4,             /* a CUDA runtime / driver call or a kernel failed */
+  PF_ERR_DEVICE_TIMEOUT = -5,   /* a bounded device-side wait gave up */
+  PF_ERR_NOT_TRAINED = -6       /* learned start requested before pf_learned_train */
+} pf_status;
+
+typedef enum {
+  PF_SIMHASH = 0,       /* random hyperplane LSH, 1 bit per function (Sec. 2.2) */
+  PF_CROSSPOLYTOPE = 1  /* cross-polytope LSH, ceil(log2 2d) bits per function (Sec. 2.2, 4.3) */
+} pf_family;
+
+typedef enum { PF_F32 = 0 } pf_dtype;
+
+/* Build parameters (Sec. 4.2-4.3).  Zero-initialise and set what you need;
+ * zero means "default" for the optional fields. */
+typedef struct {
+  int64_t n;                    /* number of points, >= 1 */
+  int32_t d;                    /* dimension, 1..256 */
+  int32_t dtype;                /* pf_dtype of `points` */
+  int32_t family;               /* pf_family */
+  int32_t num_sketches;         /* M 64-bit sketches per point (Sec. 4.2); 0 -> 32 */
+  uint64_t memory_budget_bytes; /* index size budget (Sec. 5); sets the number of repetitions L */
+  uint64_t seed;                /* seed of every random draw of the index (hash functions, sketches, CP table) */
+  int32_t segment_B;            /* segment size B (Sec. 4.2, App. C); 0 -> 12 */
+  int32_t cp_draws;             /* Monte-Carlo draws per similarity for the CP table (Sec. 4.3); 0 -> 1000 */
+  int32_t num_tables;           /* if > 0, use exactly this L instead of the budget (tests, sweeps) */
+  int32_t reserved;
+} pf_build_params;
+
+/* Per-call search options.  NULL = defaults (FP32 scoring, filter on). */
+typedef struct {
+  int32_t scoring;             /* 0: float32 scoring; 1: bfloat16 scoring + exact float32 rerank */
+  int32_t filter;              /* 1: sketch filter on (Sec. 4.2); 0: off.  Set by pf_search_opts_default */
+  int32_t learned_start;       /* 1: start depth from the trained model (needs pf_learned_train) */
+  int32_t reserved0;
+  const int32_t* start_depth;  /* optional [Q] per-query start depth (host or device); NULL = none */
+} pf_search_opts;
+
+/* Per-query statistics (Sec. 5 reports recall and throughput; these counts
+ * explain both). */
+typedef struct {
+  int32_t start_depth;   /* first prefix length after the seed round */
+  int32_t stop_depth;    /* prefix length of the last round */
+  int32_t rounds;        /* rounds run */
+  int32_t reserved;
+  int64_t retrieved;     /* candidate positions read from the repetitions (with repeats) */
+  int64_t passed_filter; /* of those, how many passed the sketch filter */
+  int64_t scored;        /* similarities computed (float32, or bfloat16 estimates) */
+  int64_t reranked;      /* exact float32 similarities recomputed after a bfloat16 estimate */
+} pf_query_stats;
+
+typedef struct {
+  int64_t n;
+  int32_t d, d_pad;         /* d_pad = d rounded up to 16 */
+  int32_t family;
+  int32_t L;                /* repetitions */
+  int32_t Kb;               /* bits per code = maximum prefix length K */
+  int32_t ell;              /* bits per hash function */
+  int32_t fns;              /* hash functions per repetition */
+  int32_t M;                /* sketches per point */
+  int32_t B;                /* segment size */
+  int32_t trained;          /* a start-depth model is present */
+  uint64_t bytes_used;      /* device bytes the index keeps resident */
+  uint64_t budget_bytes;    /* budget it was built for */
+} pf_index_info_t;
+
+/* Internal arrays exposed read-only for verification (pf_index_array). */
+typedef enum {
+  PF_ARRAY_ROWS_F32 = 0,   /* float [n][d_pad]: normalised points (Sec. 4.2 "Vector storage") */
+  PF_ARRAY_ROWS_BF16 = 1,  /* bfloat16 [n][d_pad]: RNE copy used by bfloat16 scoring */
+  PF_ARRAY_CODES = 2,      /* uint32 [L][n]: sorted codes of each repetition (Sec. 4.2) */
+  PF_ARRAY_IDS = 3,        /* uint32 [L][n]: positions pos(p) in the same order */
+  PF_ARRAY_PREFIX = 4,     /* uint32 [L][8193]: lexicographic start of each 13-bit prefix */
+  PF_ARRAY_SKETCHES = 5,   /* uint64 [M][n]: 1-bit sketches (Sec. 3.3, 4.2) */
+  PF_ARRAY_HASH_ROWS = 6,  /* float [L*R + 64*M][d_pad]: Gaussian rows (R = fns*d_pad for CP, 32 for HP) */
+  PF_ARRAY_CP_TABLE = 7    /* double [41][ell+1]: CP collision table (Sec. 4.3); absent for HP */
+} pf_array;
+
+/* Build the index over `points` ([n][d] row-major, host or device).
+ * Sec. 4: normalise (Sec. 4.2), draw L*K hash functions and M*64 sketch
+ * hyperplanes from `seed`, hash every point, sort each repetition's
+ * (code, pos) array and tabulate its 13-bit prefixes, and estimate the CP
+ * collision table (Sec. 4.3).  L is the largest count whose resident bytes fit
+ * memory_budget_bytes (PF_ERR_BUDGET_TOO_SMALL if none).  On success *out
+ * receives a new index that the caller releases with pf_index_free. */
+pf_status pf_index_build(const pf_build_params* params, const void* points, pf_index** out, void* stream);
+
+/* Answer Q queries ([Q][d] float32, host or device) with Algorithm 1 as
+ * implemented in Sec. 4.1-4.2: rounds of decreasing prefix length, segment-
+ * wise range growth, sketch filter, exact similarity, top-k accumulator, and
+ * the stop test of Lemma 1 after each round.
+ *   k[Q]       (host or device) neighbours wanted per query, 1..k_max
+ *   recall[Q]  (host or device) target 1 - delta per query, in (0, 1)
+ *   k_max      row stride of the outputs, 1..128
+ *   out_ids    [Q][k_max] uint32, out_sims [Q][k_max] float32 (host or
+ *              device): sorted by similarity descending then id ascending;
+ *              slots >= min(k, n) hold id 0xFFFFFFFF and similarity -inf
+ *   stats      [Q] (host or device) or NULL
+ *   opts       NULL for defaults
+ * Each returned point is among the true k nearest with probability >= 1-delta
+ * when the filter is off (Lemma 1); with the filter on this holds empirically
+ * (Sec. 5.1). */
+pf_status pf_index_search(pf_index* index, const float* queries, int64_t Q, const int32_t* k,
+                          const double* recall, int32_t k_max, uint32_t* out_ids, float* out_sims,
+                          pf_query_stats* stats, const pf_search_opts* opts, void* stream);
+
+/* Hash Q queries only (the first step of every query, Sec. 4.1): normalise,
+ * then codes [Q][L] uint32 and sketches [Q][M] uint64 (host or device). */
+pf_status pf_hash_queries(pf_index* index, const float* queries, int64_t Q, uint32_t* qcodes,
+                          uint64_t* qsketches, void* stream);
+
+/* Sizes and resident bytes of an index. */
+pf_status pf_index_info(const pf_index* index, pf_index_info_t* info);
+
+/* Read-only device pointer and byte size of one internal array
+ * (PF_ERR_INVALID_ARG if the index has no such array). */
+pf_status pf_index_array(const pf_index* index, int32_t which, const void** device_ptr, uint64_t* bytes);
+
+/* Copy one internal array (pf_array) into dst (host or device), which must
+ * hold at least the array's byte size (see pf_index_array). */
+pf_status pf_index_read_array(const pf_index* index, int32_t which, void* dst, uint64_t dst_bytes, void* stream);
+
+/* Defaults: FP32 scoring, filter on, no learned start, no start depths. */
+void pf_search_opts_default(pf_search_opts* opts);
+
+/* Release an index (NULL is accepted). */
+void pf_index_free(pf_index* index);
+
+/* Static description of a status code. */
+const char* pf_status_string(pf_status status);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* pf_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PUFFINN_GB300_H */

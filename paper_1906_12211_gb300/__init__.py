@@ -1,0 +1,243 @@
+"""GB300 (sm_103a) implementation of PUFFINN's LSH-forest k-NN index.
+
+A thin ctypes binding over the C ABI in ``include/puffinn_gb300.h``: it only
+marshals arguments (torch CUDA tensors or numpy host arrays) into the library's
+``pf_*`` calls.  Every step of index build and search runs in the library's
+CUDA kernels; there is no CPU fallback -- if the compiled library is missing,
+every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpuffinn_gb300.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "puffinn_gb300.h")
+
+SIMHASH, CROSSPOLYTOPE = 0, 1
+FAMILIES = {"simhash": SIMHASH, "hp": SIMHASH, "crosspolytope": CROSSPOLYTOPE, "cp": CROSSPOLYTOPE}
+
+PF_OK = 0
+STATUS = {0: "PF_OK", -1: "PF_ERR_INVALID_ARG", -2: "PF_ERR_BUDGET_TOO_SMALL", -3: "PF_ERR_OOM",
+          -4: "PF_ERR_CUDA", -5: "PF_ERR_DEVICE_TIMEOUT", -6: "PF_ERR_NOT_TRAINED"}
+
+ARRAYS = {"rows_f32": 0, "rows_bf16": 1, "codes": 2, "ids": 3, "prefix": 4, "sketches": 5, "hash_rows": 6,
+          "cp_table": 7}
+
+
+class BuildParams(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("dtype", C.c_int32), ("family", C.c_int32),
+                ("num_sketches", C.c_int32), ("memory_budget_bytes", C.c_uint64), ("seed", C.c_uint64),
+                ("segment_B", C.c_int32), ("cp_draws", C.c_int32), ("num_tables", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class SearchOpts(C.Structure):
+    _fields_ = [("scoring", C.c_int32), ("filter", C.c_int32), ("learned_start", C.c_int32),
+                ("reserved0", C.c_int32), ("start_depth", C.c_void_p)]
+
+
+class QueryStats(C.Structure):
+    _fields_ = [("start_depth", C.c_int32), ("stop_depth", C.c_int32), ("rounds", C.c_int32),
+                ("reserved", C.c_int32), ("retrieved", C.c_int64), ("passed_filter", C.c_int64),
+                ("scored", C.c_int64), ("reranked", C.c_int64)]
+
+
+STATS_DTYPE = np.dtype([("start_depth", np.int32), ("stop_depth", np.int32), ("rounds", np.int32),
+                        ("reserved", np.int32), ("retrieved", np.int64), ("passed_filter", np.int64),
+                        ("scored", np.int64), ("reranked", np.int64)])
+
+
+class IndexInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("d_pad", C.c_int32), ("family", C.c_int32),
+                ("L", C.c_int32), ("Kb", C.c_int32), ("ell", C.c_int32), ("fns", C.c_int32), ("M", C.c_int32),
+                ("B", C.c_int32), ("trained", C.c_int32), ("bytes_used", C.c_uint64),
+                ("budget_bytes", C.c_uint64)]
+
+
+class PuffinnError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    from . import _build
+
+    return _build.build(force=force)
+
+
+def lib():
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library {LIB_PATH} is missing: run paper_1906_12211_gb300.build()")
+            L = C.CDLL(LIB_PATH)
+            vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+            sig = {
+                "pf_index_build": (i32, [vp, vp, vp, vp]),
+                "pf_index_search": (i32, [vp, vp, i64, vp, vp, i32, vp, vp, vp, vp, vp]),
+                "pf_hash_queries": (i32, [vp, vp, i64, vp, vp, vp]),
+                "pf_index_info": (i32, [vp, vp]),
+                "pf_index_array": (i32, [vp, i32, vp, vp]),
+                "pf_index_read_array": (i32, [vp, i32, vp, C.c_uint64, vp]),
+                "pf_search_opts_default": (None, [vp]),
+                "pf_index_free": (None, [vp]),
+                "pf_status_string": (C.c_char_p, [i32]),
+                "pf_last_error_message": (C.c_char_p, []),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions the public header declares."""
+    import re
+
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:[\w\*]+\s+)+\**(pf_\w+)\s*\(", txt, re.M)))
+
+
+def _check(status: int):
+    if status != PF_OK:
+        raise PuffinnError(status, lib().pf_last_error_message().decode())
+
+
+def _ptr(x):
+    """Address of a torch tensor or numpy array (contiguous)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    assert isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"]
+    return x.ctypes.data
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def _family(f) -> int:
+    return FAMILIES[f] if isinstance(f, str) else int(f)
+
+
+class Index:
+    """An LSH forest over n points (Sec. 4 of the paper), resident on the GPU."""
+
+    def __init__(self, points, family="crosspolytope", *, budget_bytes: int = 0, num_tables: int = 0,
+                 seed: int = 0, num_sketches: int = 32, segment_B: int = 12, cp_draws: int = 1000, stream=None):
+        n, d = int(points.shape[0]), int(points.shape[1])
+        p = BuildParams(n=n, d=d, dtype=0, family=_family(family), num_sketches=num_sketches,
+                        memory_budget_bytes=int(budget_bytes), seed=int(seed), segment_B=segment_B,
+                        cp_draws=cp_draws, num_tables=int(num_tables), reserved=0)
+        self._points_keepalive = points
+        h = C.c_void_p()
+        _check(lib().pf_index_build(C.byref(p), _ptr(points), C.byref(h), _stream_ptr(stream)))
+        self._h = h
+        self._points_keepalive = None
+        inf = IndexInfo()
+        _check(lib().pf_index_info(self._h, C.byref(inf)))
+        self.info = {f: getattr(inf, f) for f, _ in IndexInfo._fields_}
+        for key in ("n", "d", "d_pad", "L", "Kb", "ell", "fns", "M", "B"):
+            setattr(self, key, self.info[key])
+        self.family = self.info["family"]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pf_index_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def array(self, name: str, device: str = "cuda"):
+        """A copy of an internal array as a flat uint8 torch tensor (for verification)."""
+        import torch
+
+        ptr, nb = C.c_void_p(), C.c_uint64()
+        _check(lib().pf_index_array(self._h, ARRAYS[name], C.byref(ptr), C.byref(nb)))
+        out = torch.empty(int(nb.value), dtype=torch.uint8, device=device)
+        if device != "cpu":
+            torch.cuda.synchronize()
+        _check(lib().pf_index_read_array(self._h, ARRAYS[name], _ptr(out), int(nb.value), _stream_ptr(None)))
+        return out
+
+    def hash_queries(self, queries, qcodes=None, qsk=None, stream=None):
+        import torch
+
+        Q = int(queries.shape[0])
+        dev = queries.device if hasattr(queries, "device") else torch.device("cpu")
+        if qcodes is None:
+            qcodes = torch.empty((Q, self.L), dtype=torch.int32, device=dev)
+        if qsk is None:
+            qsk = torch.empty((Q, self.M), dtype=torch.int64, device=dev)
+        _check(lib().pf_hash_queries(self._h, _ptr(queries), Q, _ptr(qcodes), _ptr(qsk), _stream_ptr(stream)))
+        return qcodes, qsk
+
+    def search(self, queries, k, recall, *, k_max: int | None = None, scoring: str = "fp32", filter: bool = True,
+               start_depth=None, out_ids=None, out_sims=None, stats=None, stream=None):
+        """Answer a batch of queries; k and recall are per-query arrays (same
+        device as the queries) or scalars.  Returns (ids, sims, stats)."""
+        import torch
+
+        Q = int(queries.shape[0])
+        dev = queries.device if hasattr(queries, "device") else torch.device("cpu")
+        if not torch.is_tensor(k):
+            k = torch.full((Q,), int(k), dtype=torch.int32, device=dev)
+        if not torch.is_tensor(recall):
+            recall = torch.full((Q,), float(recall), dtype=torch.float64, device=dev)
+        if k_max is None:
+            k_max = int(k.max().item()) if Q else 1
+        if out_ids is None:
+            out_ids = torch.empty((Q, k_max), dtype=torch.int32, device=dev)
+        if out_sims is None:
+            out_sims = torch.empty((Q, k_max), dtype=torch.float32, device=dev)
+        if stats is True:
+            stats = torch.empty((Q, STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+        elif stats is False:
+            stats = None
+        o = SearchOpts()
+        lib().pf_search_opts_default(C.byref(o))
+        o.scoring = 1 if scoring == "bf16" else 0
+        o.filter = 1 if filter else 0
+        sd = None
+        if start_depth is not None:
+            sd = start_depth if torch.is_tensor(start_depth) else torch.full((Q,), int(start_depth),
+                                                                              dtype=torch.int32, device=dev)
+            o.start_depth = _ptr(sd)
+        _check(lib().pf_index_search(self._h, _ptr(queries), Q, _ptr(k), _ptr(recall), int(k_max), _ptr(out_ids),
+                                     _ptr(out_sims), _ptr(stats), C.byref(o), _stream_ptr(stream)))
+        return out_ids, out_sims, stats
+
+
+def stats_to_numpy(stats) -> np.ndarray:
+    """Per-query statistics as a numpy structured array."""
+    raw = stats.cpu().numpy() if hasattr(stats, "cpu") else np.asarray(stats)
+    return raw.reshape(-1).view(STATS_DTYPE)

@@ -1,0 +1,443 @@
+// C ABI of the library: argument checks, device memory ownership, host/device
+// staging, and the order of the build and search steps.  Every step of the
+// computation runs in this library's CUDA kernels.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pf_internal.h"
+
+namespace pf {
+
+namespace {
+thread_local std::string g_last_error;
+
+struct CudaFail {
+  cudaError_t err;
+  std::string where;
+};
+
+#define PF_CK(expr)                                                       \
+  do {                                                                    \
+    cudaError_t _e = (expr);                                              \
+    if (_e != cudaSuccess) throw CudaFail{_e, std::string(#expr)};        \
+  } while (0)
+
+template <class T>
+void dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * count);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error{PF_ERR_OOM, "cudaMalloc of " + std::to_string(sizeof(T) * count) + " bytes failed: " +
+                                cudaGetErrorString(e)};
+  }
+}
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+bool on_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+pf_status fail(pf_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+template <class F>
+pf_status guarded(F&& body) {
+  try {
+    g_last_error.clear();
+    return body();
+  } catch (const Error& e) {
+    return fail(e.status, e.msg);
+  } catch (const CudaFail& e) {
+    return fail(PF_ERR_CUDA, e.where + ": " + cudaGetErrorString(e.err));
+  } catch (const std::bad_alloc&) {
+    return fail(PF_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(PF_ERR_CUDA, "unexpected exception");
+  }
+}
+
+// bfloat16 hi/lo split of the float32 hash rows (for the tensor-core path)
+__global__ void split_bf16_kernel(const float* __restrict__ w, int64_t count, __nv_bfloat16* __restrict__ hi,
+                                  __nv_bfloat16* __restrict__ lo) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x) {
+    const float v = w[i];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+void free_ws(pf_workspace& ws) {
+  dfree(ws.qraw);
+  dfree(ws.qx);
+  dfree(ws.qx16);
+  dfree(ws.qcodes);
+  dfree(ws.qsk);
+  dfree(ws.k);
+  dfree(ws.recall);
+  dfree(ws.start);
+  dfree(ws.ids);
+  dfree(ws.sims);
+  dfree(ws.stats);
+  dfree(ws.counter);
+  ws.cap_q = 0;
+  ws.cap_kmax = 0;
+}
+
+void ensure_ws(pf_index* ix, int64_t Q, int k_max) {
+  pf_workspace& ws = ix->ws;
+  if (size_t(Q) <= ws.cap_q && size_t(k_max) <= ws.cap_kmax) return;
+  const size_t q = std::max<size_t>(size_t(Q), ws.cap_q);
+  const size_t km = std::max<size_t>(size_t(k_max), ws.cap_kmax);
+  free_ws(ws);
+  const int dp = ix->lay.d_pad;
+  dalloc(&ws.qraw, q * ix->d);
+  dalloc(&ws.qx, q * dp);
+  dalloc(&ws.qcodes, q * ix->L);
+  dalloc(&ws.qsk, q * ix->M);
+  dalloc(&ws.k, q);
+  dalloc(&ws.recall, q);
+  dalloc(&ws.start, q);
+  dalloc(&ws.ids, q * km);
+  dalloc(&ws.sims, q * km);
+  dalloc(&ws.stats, q);
+  dalloc(&ws.counter, 64);
+  ws.cap_q = q;
+  ws.cap_kmax = km;
+}
+
+void destroy(pf_index* ix) {
+  if (!ix) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ix->device);
+  dfree(ix->x32);
+  dfree(ix->x16);
+  dfree(ix->sk);
+  dfree(ix->W32);
+  dfree(ix->Whi);
+  dfree(ix->Wlo);
+  dfree(ix->Wthr);
+  dfree(ix->codes);
+  dfree(ix->ids);
+  dfree(ix->pfx);
+  dfree(ix->cpP);
+  dfree(ix->cos_tab);
+  free_ws(ix->ws);
+  cudaSetDevice(prev);
+  delete ix;
+}
+
+// Copy `bytes` from a host or device pointer into device buffer dst.
+void stage_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return;
+  PF_CK(cudaMemcpyAsync(dst, src, bytes, on_device(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+}
+
+// Hash and normalise Q queries (device pointer qsrc) into the workspace.
+void hash_queries_ws(pf_index* ix, const float* qdev, int64_t Q, cudaStream_t s) {
+  pf_workspace& ws = ix->ws;
+  PF_CK(launch_normalize(qdev, Q, ix->d, ix->lay.d_pad, ws.qx, nullptr, s));
+  PF_CK(launch_hash(ix, ws.qx, Q, ws.qcodes, 1, ix->L, ws.qsk, 1, ix->M, s));
+}
+
+const float* stage_queries(pf_index* ix, const float* queries, int64_t Q, cudaStream_t s) {
+  if (on_device(queries)) return queries;
+  stage_in(ix->ws.qraw, queries, sizeof(float) * size_t(Q) * ix->d, s);
+  return ix->ws.qraw;
+}
+
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+}  // namespace pf
+
+using namespace pf;
+
+extern "C" {
+
+void pf_search_opts_default(pf_search_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->filter = 1;
+}
+
+const char* pf_status_string(pf_status s) {
+  switch (s) {
+    case PF_OK: return "ok";
+    case PF_ERR_INVALID_ARG: return "invalid argument";
+    case PF_ERR_BUDGET_TOO_SMALL: return "memory budget too small for one repetition";
+    case PF_ERR_OOM: return "out of device memory";
+    case PF_ERR_CUDA: return "CUDA error";
+    case PF_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case PF_ERR_NOT_TRAINED: return "start-depth model not trained";
+  }
+  return "unknown status";
+}
+
+const char* pf_last_error_message(void) { return g_last_error.c_str(); }
+
+pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_index** out, void* stream) {
+  return guarded([&]() -> pf_status {
+    if (!prm || !points || !out) return fail(PF_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (prm->n < 1 || prm->n > 0x7fffffffLL) return fail(PF_ERR_INVALID_ARG, "n must be in [1, 2^31-1]");
+    if (prm->d < 1 || prm->d > kMaxD) return fail(PF_ERR_INVALID_ARG, "d must be in [1, 256]");
+    if (prm->dtype != PF_F32) return fail(PF_ERR_INVALID_ARG, "points must be float32");
+    if (prm->family != PF_SIMHASH && prm->family != PF_CROSSPOLYTOPE)
+      return fail(PF_ERR_INVALID_ARG, "unknown hash family");
+    const int M = prm->num_sketches ? prm->num_sketches : 32;
+    const int B = prm->segment_B ? prm->segment_B : 12;
+    const int draws = prm->cp_draws ? prm->cp_draws : 1000;
+    if (M < 1 || M > 256) return fail(PF_ERR_INVALID_ARG, "num_sketches must be in [1, 256]");
+    if (B < 1 || B > 4096) return fail(PF_ERR_INVALID_ARG, "segment_B must be in [1, 4096]");
+    if (draws < 1) return fail(PF_ERR_INVALID_ARG, "cp_draws must be >= 1");
+    int64_t L = prm->num_tables > 0 ? prm->num_tables
+                                    : budget_tables(prm->family, prm->n, prm->d, M, prm->memory_budget_bytes);
+    if (L < 1) return fail(PF_ERR_BUDGET_TOO_SMALL, "memory budget leaves room for no repetition");
+    if (L > kMaxL) L = kMaxL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    pf_index* ix = new pf_index();
+    try {
+      PF_CK(cudaGetDevice(&ix->device));
+      PF_CK(cudaDeviceGetAttribute(&ix->num_sms, cudaDevAttrMultiProcessorCount, ix->device));
+      ix->n = prm->n;
+      ix->d = prm->d;
+      ix->family = prm->family;
+      ix->L = int(L);
+      ix->M = M;
+      ix->B = B;
+      ix->lay = make_layout(prm->family, prm->d);
+      ix->budget = prm->memory_budget_bytes;
+      ix->bytes_used = resident_bytes(prm->family, prm->n, prm->d, M, ix->L);
+      const int dp = ix->lay.d_pad;
+      const int64_t n = ix->n;
+      ix->hash_rows = int64_t(ix->L) * ix->lay.rows_table + 64LL * M;
+      // bound on |bfloat16 estimate - canonical float32 similarity| for unit
+      // vectors: 2^-8 from rounding the row to bfloat16, plus the float32
+      // accumulation error of both sums (each <= d_pad * 2^-24 * |q||x|)
+      ix->bf16_err = float(std::ldexp(1.0, -8) * (1.0 + std::ldexp(1.0, -20)) + 2.2 * dp * std::ldexp(1.0, -24));
+
+      dalloc(&ix->x32, size_t(n) * dp);
+      dalloc(&ix->x16, size_t(n) * dp);
+      dalloc(&ix->sk, size_t(n) * M);
+      dalloc(&ix->W32, size_t(ix->hash_rows) * dp);
+      dalloc(&ix->Whi, size_t(ix->hash_rows) * dp);
+      dalloc(&ix->Wlo, size_t(ix->hash_rows) * dp);
+      dalloc(&ix->Wthr, size_t(ix->hash_rows));
+      dalloc(&ix->codes, size_t(n) * ix->L);
+      dalloc(&ix->ids, size_t(n) * ix->L);
+      dalloc(&ix->pfx, size_t(kPrefixSize) * ix->L);
+      dalloc(&ix->cos_tab, 65);
+      if (ix->family == PF_CROSSPOLYTOPE) dalloc(&ix->cpP, size_t(kAlphaSteps) * (ix->lay.ell + 1));
+
+      // random parameters on the host (bit-reproducible from the seed)
+      std::vector<float> W(size_t(ix->hash_rows) * dp), thr(size_t(ix->hash_rows));
+      gen_hash_rows(prm->seed, prm->family, ix->L, M, prm->d, ix->lay, W.data(), thr.data());
+      PF_CK(cudaMemcpyAsync(ix->W32, W.data(), sizeof(float) * W.size(), cudaMemcpyHostToDevice, s));
+      PF_CK(cudaMemcpyAsync(ix->Wthr, thr.data(), sizeof(float) * thr.size(), cudaMemcpyHostToDevice, s));
+      split_bf16_kernel<<<1024, 256, 0, s>>>(ix->W32, int64_t(W.size()), ix->Whi, ix->Wlo);
+      PF_CK(cudaGetLastError());
+      std::vector<double> cosv(65);
+      filter_cos_table(cosv.data());
+      PF_CK(cudaMemcpyAsync(ix->cos_tab, cosv.data(), sizeof(double) * 65, cudaMemcpyHostToDevice, s));
+      std::vector<double> P;
+      if (ix->family == PF_CROSSPOLYTOPE) {
+        P.resize(size_t(kAlphaSteps) * (ix->lay.ell + 1));
+        cp_collision_table(prm->seed, prm->d, ix->lay.ell, draws, P.data());
+        PF_CK(cudaMemcpyAsync(ix->cpP, P.data(), sizeof(double) * P.size(), cudaMemcpyHostToDevice, s));
+      }
+
+      // points -> device, normalise, hash, sort
+      const float* pin = static_cast<const float*>(points);
+      float* staged = nullptr;
+      if (!on_device(points)) {
+        dalloc(&staged, size_t(n) * prm->d);
+        PF_CK(cudaMemcpyAsync(staged, points, sizeof(float) * size_t(n) * prm->d, cudaMemcpyHostToDevice, s));
+        pin = staged;
+      }
+      uint32_t* raw_codes = nullptr;
+      try {
+        PF_CK(launch_normalize(pin, n, prm->d, dp, ix->x32, ix->x16, s));
+        dalloc(&raw_codes, size_t(n) * ix->L);
+        PF_CK(launch_hash(ix, ix->x32, n, raw_codes, n, 1, ix->sk, n, 1, s));
+        PF_CK(sort_tables(ix, raw_codes, s));
+        PF_CK(cudaStreamSynchronize(s));
+      } catch (...) {
+        cudaStreamSynchronize(s);
+        dfree(staged);
+        dfree(raw_codes);
+        throw;
+      }
+      dfree(staged);
+      dfree(raw_codes);
+      PF_CK(cudaGetLastError());
+    } catch (...) {
+      destroy(ix);
+      throw;
+    }
+    *out = ix;
+    return PF_OK;
+  });
+}
+
+pf_status pf_hash_queries(pf_index* ix, const float* queries, int64_t Q, uint32_t* qcodes, uint64_t* qsk,
+                          void* stream) {
+  return guarded([&]() -> pf_status {
+    if (!ix || !queries || !qcodes || !qsk) return fail(PF_ERR_INVALID_ARG, "null argument");
+    if (Q < 0 || Q > 0x7fffffffLL) return fail(PF_ERR_INVALID_ARG, "Q out of range");
+    if (Q == 0) return PF_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PF_CK(cudaSetDevice(ix->device));
+    ensure_ws(ix, Q, 1);
+    const float* qd = stage_queries(ix, queries, Q, s);
+    hash_queries_ws(ix, qd, Q, s);
+    PF_CK(cudaMemcpyAsync(qcodes, ix->ws.qcodes, sizeof(uint32_t) * size_t(Q) * ix->L, cudaMemcpyDefault, s));
+    PF_CK(cudaMemcpyAsync(qsk, ix->ws.qsk, sizeof(uint64_t) * size_t(Q) * ix->M, cudaMemcpyDefault, s));
+    PF_CK(cudaStreamSynchronize(s));
+    PF_CK(cudaGetLastError());
+    return PF_OK;
+  });
+}
+
+pf_status pf_index_search(pf_index* ix, const float* queries, int64_t Q, const int32_t* k, const double* recall,
+                          int32_t k_max, uint32_t* out_ids, float* out_sims, pf_query_stats* stats,
+                          const pf_search_opts* opts, void* stream) {
+  return guarded([&]() -> pf_status {
+    if (!ix || !queries || !k || !recall || !out_ids || !out_sims) return fail(PF_ERR_INVALID_ARG, "null argument");
+    if (Q < 0 || Q > 0x7fffffffLL) return fail(PF_ERR_INVALID_ARG, "Q out of range");
+    if (k_max < 1 || k_max > kMaxK) return fail(PF_ERR_INVALID_ARG, "k_max must be in [1, 128]");
+    pf_search_opts o;
+    pf_search_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.scoring != 0 && o.scoring != 1) return fail(PF_ERR_INVALID_ARG, "scoring must be 0 or 1");
+    if (o.learned_start) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
+    if (Q == 0) return PF_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PF_CK(cudaSetDevice(ix->device));
+    ensure_ws(ix, Q, k_max);
+    pf_workspace& ws = ix->ws;
+    // per-query k and recall are checked by the search kernel (error word 1)
+    const float* qd = stage_queries(ix, queries, Q, s);
+    const int32_t* kd = k;
+    const double* rd = recall;
+    const int32_t* sd = o.start_depth;
+    if (!on_device(k)) { stage_in(ws.k, k, sizeof(int32_t) * Q, s); kd = ws.k; }
+    if (!on_device(recall)) { stage_in(ws.recall, recall, sizeof(double) * Q, s); rd = ws.recall; }
+    if (sd && !on_device(sd)) { stage_in(ws.start, sd, sizeof(int32_t) * Q, s); sd = ws.start; }
+    hash_queries_ws(ix, qd, Q, s);
+
+    const bool ids_dev = on_device(out_ids), sims_dev = on_device(out_sims);
+    const bool st_dev = stats && on_device(stats);
+    SearchArgs a;
+    a.Q = int(Q);
+    a.qx = ws.qx;
+    a.qcodes = ws.qcodes;
+    a.qsk = ws.qsk;
+    a.k = kd;
+    a.recall = rd;
+    a.start = sd;
+    a.k_max = k_max;
+    a.filter = o.filter ? 1 : 0;
+    a.scoring = o.scoring;
+    a.out_ids = ids_dev ? out_ids : ws.ids;
+    a.out_sims = sims_dev ? out_sims : ws.sims;
+    a.stats = stats ? (st_dev ? stats : ws.stats) : nullptr;
+    a.counter = ws.counter;
+    PF_CK(cudaMemsetAsync(ws.counter, 0, sizeof(int32_t) * 64, s));
+    PF_CK(launch_search(ix, a, s));
+    if (!ids_dev)
+      PF_CK(cudaMemcpyAsync(out_ids, ws.ids, sizeof(uint32_t) * size_t(Q) * k_max, cudaMemcpyDeviceToHost, s));
+    if (!sims_dev)
+      PF_CK(cudaMemcpyAsync(out_sims, ws.sims, sizeof(float) * size_t(Q) * k_max, cudaMemcpyDeviceToHost, s));
+    if (stats && !st_dev)
+      PF_CK(cudaMemcpyAsync(stats, ws.stats, sizeof(pf_query_stats) * size_t(Q), cudaMemcpyDeviceToHost, s));
+    int32_t flags = 0;
+    PF_CK(cudaMemcpyAsync(&flags, ws.counter + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PF_CK(cudaStreamSynchronize(s));
+    PF_CK(cudaGetLastError());
+    if (flags & 1) return fail(PF_ERR_INVALID_ARG, "some k not in [1, k_max] or recall not in (0, 1)");
+    return PF_OK;
+  });
+}
+
+pf_status pf_index_info(const pf_index* ix, pf_index_info_t* info) {
+  if (!ix || !info) return fail(PF_ERR_INVALID_ARG, "null argument");
+  std::memset(info, 0, sizeof(*info));
+  info->n = ix->n;
+  info->d = ix->d;
+  info->d_pad = ix->lay.d_pad;
+  info->family = ix->family;
+  info->L = ix->L;
+  info->Kb = ix->lay.Kb;
+  info->ell = ix->lay.ell;
+  info->fns = ix->lay.fns;
+  info->M = ix->M;
+  info->B = ix->B;
+  info->trained = 0;
+  info->bytes_used = ix->bytes_used;
+  info->budget_bytes = ix->budget;
+  return PF_OK;
+}
+
+pf_status pf_index_array(const pf_index* ix, int32_t which, const void** ptr, uint64_t* bytes) {
+  if (!ix || !ptr || !bytes) return fail(PF_ERR_INVALID_ARG, "null argument");
+  const uint64_t n = uint64_t(ix->n), dp = uint64_t(ix->lay.d_pad), L = uint64_t(ix->L);
+  switch (which) {
+    case PF_ARRAY_ROWS_F32: *ptr = ix->x32; *bytes = n * dp * 4; break;
+    case PF_ARRAY_ROWS_BF16: *ptr = ix->x16; *bytes = n * dp * 2; break;
+    case PF_ARRAY_CODES: *ptr = ix->codes; *bytes = n * L * 4; break;
+    case PF_ARRAY_IDS: *ptr = ix->ids; *bytes = n * L * 4; break;
+    case PF_ARRAY_PREFIX: *ptr = ix->pfx; *bytes = uint64_t(kPrefixSize) * L * 4; break;
+    case PF_ARRAY_SKETCHES: *ptr = ix->sk; *bytes = n * uint64_t(ix->M) * 8; break;
+    case PF_ARRAY_HASH_ROWS: *ptr = ix->W32; *bytes = uint64_t(ix->hash_rows) * dp * 4; break;
+    case PF_ARRAY_CP_TABLE:
+      if (!ix->cpP) return fail(PF_ERR_INVALID_ARG, "index has no CP table");
+      *ptr = ix->cpP;
+      *bytes = uint64_t(kAlphaSteps) * (ix->lay.ell + 1) * 8;
+      break;
+    default: return fail(PF_ERR_INVALID_ARG, "unknown array");
+  }
+  return PF_OK;
+}
+
+pf_status pf_index_read_array(const pf_index* ix, int32_t which, void* dst, uint64_t dst_bytes, void* stream) {
+  return guarded([&]() -> pf_status {
+    const void* src = nullptr;
+    uint64_t nb = 0;
+    const pf_status st = pf_index_array(ix, which, &src, &nb);
+    if (st != PF_OK) return st;
+    if (!dst || dst_bytes < nb) return fail(PF_ERR_INVALID_ARG, "destination too small");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PF_CK(cudaMemcpyAsync(dst, src, nb, cudaMemcpyDefault, s));
+    PF_CK(cudaStreamSynchronize(s));
+    return PF_OK;
+  });
+}
+
+void pf_index_free(pf_index* ix) { destroy(ix); }
+
+}  // extern "C"

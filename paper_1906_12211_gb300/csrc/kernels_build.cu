@@ -1,0 +1,368 @@
+// Index-build kernels: normalisation, hashing (projection + sign/argmax with
+// float64 recheck), per-repetition LSD radix sort of (code, position) pairs,
+// and the 13-bit prefix tables.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "pf_internal.h"
+
+namespace pf {
+
+// ---------------------------------------------------------------------------
+// Normalisation (Sec. 4.2 "Vector storage"): squared norm summed in float64 in
+// index order (float*float products are exact in float64), correctly rounded
+// sqrt and division in float64, one rounding to float.  One thread per row;
+// padding columns are zero; a zero row stays zero.
+// ---------------------------------------------------------------------------
+__global__ void normalize_kernel(const float* __restrict__ in, int64_t rows, int d, int d_pad,
+                                 float* __restrict__ x32, __nv_bfloat16* __restrict__ x16) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const float* row = in + r * d;
+  double ss = 0.0;
+  for (int i = 0; i < d; ++i) {
+    const double v = double(row[i]);
+    ss = __dadd_rn(ss, __dmul_rn(v, v));
+  }
+  const double nrm = __dsqrt_rn(ss);
+  float* o = x32 + r * d_pad;
+  for (int i = 0; i < d_pad; ++i) {
+    const float y = (i < d && nrm > 0.0) ? __double2float_rn(__ddiv_rn(double(row[i]), nrm)) : 0.0f;
+    o[i] = y;
+    if (x16) x16[r * d_pad + i] = __float2bfloat16_rn(y);
+  }
+}
+
+cudaError_t launch_normalize(const float* in, int64_t rows, int d, int d_pad, float* x32, __nv_bfloat16* x16,
+                             cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  const int tb = 128;
+  normalize_kernel<<<unsigned((rows + tb - 1) / tb), tb, 0, s>>>(in, rows, d, d_pad, x32, x16);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Hashing.  Each CTA takes 128 points (one per thread) and one group of hash
+// rows: a whole repetition (CP: fns functions of d_pad rows; HP: 32 rows) or
+// one 64-row sketch.  Projections are float32 fused multiply-adds; their error
+// is below d*2^-24*|a|*|x| (<= 2^-16 |a| for d <= 256), far inside the recheck
+// band thr = 2^-12 |a|.  A decision closer to its boundary than the band is
+// recomputed in float64 in index order, which is the defining value:
+//   HP / sketch bit  = [<a, x> >= 0]
+//   CP value         = (sign << (l-1)) | argmax_c |<a_c, x>|, first c on ties
+// For CP the four largest |v| are kept; if the runner-up is within 2*band of
+// the best, the candidates within 2*band are recomputed in float64 (all d rows
+// when a fifth could be in the band).
+// ---------------------------------------------------------------------------
+constexpr int kHashPts = 128;
+constexpr int kHashChunk = 32;  // hash rows staged in shared memory at a time
+
+__device__ __forceinline__ double dot64(const float* __restrict__ a, const float* __restrict__ x, int d) {
+  double s = 0.0;
+  for (int i = 0; i < d; ++i) s = __dadd_rn(s, __dmul_rn(double(a[i]), double(x[i])));
+  return s;
+}
+
+struct Top4 {
+  float a[4];
+  int c[4];
+  __device__ void reset() {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      a[t] = -1.f;
+      c[t] = 0;
+    }
+  }
+  __device__ void push(float v, int cc) {
+    if (v <= a[3]) return;
+    int pos = 3;
+    while (pos > 0 && v > a[pos - 1]) {
+      a[pos] = a[pos - 1];
+      c[pos] = c[pos - 1];
+      --pos;
+    }
+    a[pos] = v;
+    c[pos] = cc;
+  }
+};
+
+__global__ void __launch_bounds__(kHashPts) hash_simt_kernel(
+    const float* __restrict__ x32, int64_t npts, int d, int d_pad, int family, int L, int fns, int ell,
+    int rows_table, const float* __restrict__ W, const float* __restrict__ thr, uint32_t* __restrict__ codes,
+    int64_t cj, int64_t cp, uint64_t* __restrict__ sk, int64_t sm, int64_t sp) {
+  extern __shared__ float smem[];
+  float* xT = smem;                         // [d_pad][kHashPts]
+  float* wS = smem + d_pad * kHashPts;      // [kHashChunk][d_pad]
+  const int tid = threadIdx.x;
+  const int64_t p0 = int64_t(blockIdx.x) * kHashPts;
+  const int64_t p = p0 + tid;
+  const int g = blockIdx.y;
+  const bool is_table = g < L;
+
+  for (int e = tid; e < d_pad * kHashPts; e += kHashPts) {
+    const int pt = e / d_pad, i = e % d_pad;
+    const int64_t pp = p0 + pt;
+    xT[i * kHashPts + pt] = pp < npts ? x32[pp * d_pad + i] : 0.f;
+  }
+
+  const int64_t row0 = is_table ? int64_t(g) * rows_table : int64_t(L) * rows_table + int64_t(g - L) * 64;
+  const int nrows = is_table ? rows_table : 64;
+  const float* xrow = x32 + (p < npts ? p : 0) * d_pad;
+
+  uint32_t code = 0;
+  uint64_t bits = 0;
+  Top4 top;
+  top.reset();
+  float best_v = 0.f;
+  int fn = 0;
+
+  for (int r0 = 0; r0 < nrows; r0 += kHashChunk) {
+    const int nr = min(kHashChunk, nrows - r0);
+    __syncthreads();
+    for (int e = tid; e < nr * d_pad; e += kHashPts) wS[e] = W[(row0 + r0) * d_pad + e];
+    __syncthreads();
+    for (int rr = 0; rr < nr; ++rr) {
+      const int r = r0 + rr;
+      const float* w = wS + rr * d_pad;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      for (int i = 0; i < d_pad; i += 4) {
+        a0 = __fmaf_rn(w[i + 0], xT[(i + 0) * kHashPts + tid], a0);
+        a1 = __fmaf_rn(w[i + 1], xT[(i + 1) * kHashPts + tid], a1);
+        a2 = __fmaf_rn(w[i + 2], xT[(i + 2) * kHashPts + tid], a2);
+        a3 = __fmaf_rn(w[i + 3], xT[(i + 3) * kHashPts + tid], a3);
+      }
+      const float v = (a0 + a1) + (a2 + a3);
+      const int64_t grow = row0 + r;
+      if (!is_table || family == PF_SIMHASH) {
+        bool bit = v >= 0.f;
+        if (fabsf(v) < thr[grow] && p < npts) bit = dot64(W + grow * d_pad, xrow, d) >= 0.0;
+        if (is_table) {
+          code |= (bit ? 1u : 0u) << (31 - r);
+        } else if (bit) {
+          bits |= uint64_t(1) << r;
+        }
+      } else {
+        const int c = r - fn * d_pad;
+        if (c < d) {
+          const float av = fabsf(v);
+          if (av > top.a[0]) best_v = v;
+          top.push(av, c);
+        }
+        if (c == d_pad - 1) {  // function complete
+          const float band = thr[grow];
+          int arg = top.c[0];
+          bool neg = best_v < 0.f;
+          if ((top.a[1] >= top.a[0] - 2.f * band || top.a[0] < band) && p < npts) {
+            const float* wf = W + (row0 + int64_t(fn) * d_pad) * d_pad;
+            double bestabs = -1.0, bestval = 0.0;
+            int besti = 0;
+            if (top.a[3] >= top.a[0] - 2.f * band) {
+              for (int cc = 0; cc < d; ++cc) {
+                const double v64 = dot64(wf + int64_t(cc) * d_pad, xrow, d);
+                if (fabs(v64) > bestabs) {
+                  bestabs = fabs(v64);
+                  bestval = v64;
+                  besti = cc;
+                }
+              }
+            } else {
+              for (int t = 0; t < 4; ++t) {
+                if (top.a[t] < top.a[0] - 2.f * band) continue;
+                const int cc = top.c[t];
+                const double v64 = dot64(wf + int64_t(cc) * d_pad, xrow, d);
+                const double av = fabs(v64);
+                if (av > bestabs || (av == bestabs && cc < besti)) {
+                  bestabs = av;
+                  bestval = v64;
+                  besti = cc;
+                }
+              }
+            }
+            arg = besti;
+            neg = bestval < 0.0;
+          }
+          const uint32_t value = ((neg ? 1u : 0u) << (ell - 1)) | uint32_t(arg);
+          code |= value << (32 - ell * (fn + 1));
+          ++fn;
+          top.reset();
+        }
+      }
+    }
+  }
+  if (p < npts) {
+    if (is_table)
+      codes[int64_t(g) * cj + p * cp] = code;
+    else
+      sk[int64_t(g - L) * sm + p * sp] = bits;
+  }
+}
+
+cudaError_t launch_hash(const pf_index* ix, const float* x32, int64_t npts, uint32_t* codes, int64_t cj,
+                        int64_t cp, uint64_t* sk, int64_t sm, int64_t sp, cudaStream_t s) {
+  if (npts <= 0) return cudaSuccess;
+  const Layout& lay = ix->lay;
+  const size_t smem = sizeof(float) * (size_t(lay.d_pad) * kHashPts + size_t(kHashChunk) * lay.d_pad);
+  cudaError_t e = cudaFuncSetAttribute(hash_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  dim3 grid(unsigned((npts + kHashPts - 1) / kHashPts), unsigned(ix->L + ix->M));
+  hash_simt_kernel<<<grid, kHashPts, smem, s>>>(x32, npts, ix->d, lay.d_pad, ix->family, ix->L, lay.fns, lay.ell,
+                                                lay.rows_table, ix->W32, ix->Wthr, codes, cj, cp, sk, sm, sp);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Per-repetition stable LSD radix sort of (code, position), 4 passes of 8 bits
+// (positions start as 0..n-1, so equal codes stay in position order, Sec. 4.2).
+// Each pass: per-tile digit histograms -> one exclusive scan per repetition in
+// (digit, tile) order -> stable scatter.  Within a tile, keys are ranked chunk
+// by chunk (256 keys, one per thread) with warp match masks, so equal digits
+// keep their input order.  No kernel waits on another CTA.
+// ---------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t* __restrict__ keys, int64_t n,
+                                                                 int shift, int ntiles,
+                                                                 uint32_t* __restrict__ counts) {
+  __shared__ uint32_t h[256];
+  const int tile = blockIdx.x, tab = blockIdx.y;
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t* k = keys + int64_t(tab) * n;
+  const int64_t base = int64_t(tile) * kSortTile;
+  for (int t = 0; t < kSortItems; ++t) {
+    const int64_t i = base + int64_t(t) * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[(k[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  counts[(int64_t(tab) * 256 + threadIdx.x) * ntiles + tile] = h[threadIdx.x];
+}
+
+// exclusive scan of counts[tab][256*ntiles] (digit-major), one CTA per table
+__global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* __restrict__ counts, int ntiles) {
+  __shared__ uint32_t part[1024];
+  const int64_t len = int64_t(256) * ntiles;
+  uint32_t* c = counts + int64_t(blockIdx.x) * len;
+  const int64_t per = (len + 1023) / 1024;
+  const int64_t b = threadIdx.x * per, e = min(len, b + per);
+  uint32_t sum = 0;
+  for (int64_t i = b; i < e; ++i) sum += c[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - sum;
+  for (int64_t i = b; i < e; ++i) {
+    const uint32_t v = c[i];
+    c[i] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, int64_t n, int shift, int ntiles, const uint32_t* __restrict__ offsets) {
+  __shared__ uint32_t base_off[256];
+  __shared__ uint32_t wcount[kSortThreads / 32][256];
+  const int tile = blockIdx.x, tab = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t* ki = kin + int64_t(tab) * n;
+  const uint32_t* vi = vin ? vin + int64_t(tab) * n : nullptr;
+  uint32_t* ko = kout + int64_t(tab) * n;
+  uint32_t* vo = vout + int64_t(tab) * n;
+  base_off[threadIdx.x] = offsets[(int64_t(tab) * 256 + threadIdx.x) * ntiles + tile];
+  for (int w = 0; w < kSortThreads / 32; ++w) wcount[w][threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = int64_t(tile) * kSortTile;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  for (int t = 0; t < kSortItems; ++t) {
+    const int64_t i = base + int64_t(t) * kSortThreads + threadIdx.x;
+    const bool valid = i < n;
+    const uint32_t key = valid ? ki[i] : 0u;
+    const uint32_t val = valid ? (vi ? vi[i] : uint32_t(i)) : 0u;
+    const uint32_t dig = valid ? ((key >> shift) & 255u) : 256u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, dig);
+    const uint32_t rank = __popc(peers & lt_mask);
+    if (valid && rank == 0) wcount[warp][dig] = __popc(peers);
+    __syncthreads();
+    {  // per digit: prefix over warps, advance the running tile offset
+      const int dg = threadIdx.x;
+      uint32_t run = base_off[dg];
+      for (int w = 0; w < kSortThreads / 32; ++w) {
+        const uint32_t c = wcount[w][dg];
+        wcount[w][dg] = run;
+        run += c;
+      }
+      base_off[dg] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = wcount[warp][dig] + rank;
+      ko[pos] = key;
+      vo[pos] = val;
+    }
+    __syncthreads();
+    for (int w = 0; w < kSortThreads / 32; ++w) wcount[w][threadIdx.x] = 0;
+    __syncthreads();
+  }
+}
+
+// pfx[t] = first position whose top 13 bits are >= t (t = 0..8192)
+__global__ void prefix_kernel(const uint32_t* __restrict__ codes, int64_t n, uint32_t* __restrict__ pfx) {
+  const int tab = blockIdx.y;
+  const uint32_t* c = codes + int64_t(tab) * n;
+  uint32_t* out = pfx + int64_t(tab) * kPrefixSize;
+  for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < n; p += int64_t(gridDim.x) * blockDim.x) {
+    const int top = int(c[p] >> (32 - kPrefixBits));
+    const int prev = p == 0 ? -1 : int(c[p - 1] >> (32 - kPrefixBits));
+    for (int t = prev + 1; t <= top; ++t) out[t] = uint32_t(p);
+    if (p == n - 1)
+      for (int t = top + 1; t < kPrefixSize; ++t) out[t] = uint32_t(n);
+  }
+}
+
+cudaError_t sort_tables(pf_index* ix, uint32_t* codes_unsorted, cudaStream_t s) {
+  const int64_t n = ix->n;
+  const int ntiles = int((n + kSortTile - 1) / kSortTile);
+  // tables per group: bound the temporary buffers to ~1 GiB
+  int G = int(std::max<int64_t>(1, std::min<int64_t>(ix->L, (int64_t(1) << 30) / std::max<int64_t>(1, n * 16))));
+  uint32_t *tk = nullptr, *tv = nullptr, *cnt = nullptr;
+  cudaError_t e;
+  if ((e = cudaMallocAsync(&tk, sizeof(uint32_t) * size_t(n) * G, s)) != cudaSuccess) return e;
+  if ((e = cudaMallocAsync(&tv, sizeof(uint32_t) * size_t(n) * G, s)) != cudaSuccess) return e;
+  if ((e = cudaMallocAsync(&cnt, sizeof(uint32_t) * size_t(256) * ntiles * G, s)) != cudaSuccess) return e;
+  for (int j0 = 0; j0 < ix->L && e == cudaSuccess; j0 += G) {
+    const int g = std::min(G, ix->L - j0);
+    uint32_t* keys0 = codes_unsorted + int64_t(j0) * n;
+    uint32_t* outk = ix->codes + int64_t(j0) * n;
+    uint32_t* outv = ix->ids + int64_t(j0) * n;
+    // pass buffers: in -> tmp -> out -> tmp -> out
+    const uint32_t* kin = keys0;
+    const uint32_t* vin = nullptr;
+    for (int pass = 0; pass < 4; ++pass) {
+      uint32_t* ko = (pass % 2 == 0) ? tk : outk;
+      uint32_t* vo = (pass % 2 == 0) ? tv : outv;
+      dim3 grid(ntiles, g);
+      radix_hist_kernel<<<grid, kSortThreads, 0, s>>>(kin, n, pass * 8, ntiles, cnt);
+      radix_scan_kernel<<<g, 1024, 0, s>>>(cnt, ntiles);
+      radix_scatter_kernel<<<grid, kSortThreads, 0, s>>>(kin, vin, ko, vo, n, pass * 8, ntiles, cnt);
+      kin = ko;
+      vin = vo;
+    }
+    prefix_kernel<<<dim3(unsigned(std::min<int64_t>(1024, (n + 255) / 256)), g), 256, 0, s>>>(
+        outk, n, ix->pfx + int64_t(j0) * kPrefixSize);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(tk, s);
+  cudaFreeAsync(tv, s);
+  cudaFreeAsync(cnt, s);
+  return e;
+}
+
+}  // namespace pf

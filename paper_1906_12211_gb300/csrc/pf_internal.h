@@ -1,0 +1,128 @@
+// Internal declarations of the GB300 PUFFINN library (not part of the ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "puffinn_gb300.h"
+
+namespace pf {
+
+constexpr int kPrefixBits = 13;                     // Sec. 4.2: 13-bit prefix table
+constexpr int kPrefixSize = (1 << kPrefixBits) + 1;
+constexpr int kAlphaSteps = 41;                     // Sec. 4.3: similarity grid step 0.05
+constexpr int kMaxK = 128;
+constexpr int kMaxD = 256;
+constexpr int kMaxL = 2048;
+
+enum Purpose : uint32_t { kPurposeHash = 1, kPurposeSketch = 2, kPurposeCpMc = 3 };
+
+// Shape of one repetition's code (Sec. 4.3): l bits per function, floor(32/l)
+// functions, K = fns * l bits.  Hash rows are padded so that every CP function
+// owns d_pad rows (rows c >= d are zero and never win the argmax).
+struct Layout {
+  int ell = 1, fns = 32, Kb = 32, d_pad = 16;
+  int rows_fn = 1;      // rows per hash function in the padded row matrix
+  int rows_table = 32;  // rows per repetition
+};
+Layout make_layout(int family, int d);
+
+// ---------------------------------------------------------------- host params
+float gaussian(uint64_t seed, uint32_t purpose, uint32_t a, uint32_t b, uint32_t c);
+// W[(L*rows_table + 64*M)][d_pad] float32 and per-row recheck band thr[]
+void gen_hash_rows(uint64_t seed, int family, int L, int M, int d, const Layout& lay, float* W, float* thr);
+void cp_collision_table(uint64_t seed, int d, int ell, int draws, double* P /*[41][ell+1]*/);
+void filter_cos_table(double* c /*[65]*/);
+int64_t budget_tables(int family, int64_t n, int d, int M, uint64_t budget);
+uint64_t resident_bytes(int family, int64_t n, int d, int M, int L);
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+struct Error {
+  pf_status status;
+  std::string msg;
+};
+
+}  // namespace pf
+
+// Workspace for one search call (grown on demand, owned by the index).
+struct pf_workspace {
+  size_t cap_q = 0;  // queries the buffers hold
+  float* qraw = nullptr;       // [Q][d] staged host queries
+  float* qx = nullptr;         // [Q][d_pad] normalised queries
+  __nv_bfloat16* qx16 = nullptr;
+  uint32_t* qcodes = nullptr;  // [Q][L]
+  uint64_t* qsk = nullptr;     // [Q][M]
+  int32_t* k = nullptr;
+  double* recall = nullptr;
+  int32_t* start = nullptr;
+  uint32_t* ids = nullptr;     // [Q][k_max] staged outputs
+  float* sims = nullptr;
+  pf_query_stats* stats = nullptr;
+  int32_t* counter = nullptr;  // work queue head + error word
+  size_t cap_kmax = 0;
+};
+
+struct pf_index {
+  int device = 0;
+  int64_t n = 0;
+  int d = 0, family = 0, L = 0, M = 32, B = 12;
+  pf::Layout lay;
+  uint64_t budget = 0, bytes_used = 0;
+  int64_t hash_rows = 0;  // L*rows_table + 64*M
+  // resident device arrays
+  float* x32 = nullptr;            // [n][d_pad]
+  __nv_bfloat16* x16 = nullptr;    // [n][d_pad]
+  uint64_t* sk = nullptr;          // [M][n]
+  float* W32 = nullptr;            // [hash_rows][d_pad]
+  __nv_bfloat16* Whi = nullptr;    // [hash_rows][d_pad]
+  __nv_bfloat16* Wlo = nullptr;    // [hash_rows][d_pad]
+  float* Wthr = nullptr;           // [hash_rows]
+  uint32_t* codes = nullptr;       // [L][n]
+  uint32_t* ids = nullptr;         // [L][n]
+  uint32_t* pfx = nullptr;         // [L][8193]
+  double* cpP = nullptr;           // [41][ell+1]
+  double* cos_tab = nullptr;       // [65]
+  float bf16_err = 0.f;            // bound on |bf16 estimate - float32 canonical similarity|
+  int num_sms = 0;
+  pf_workspace ws;
+};
+
+// ---------------------------------------------------------------- launchers
+namespace pf {
+
+// normalise rows (Sec. 4.2) -> x32 [rows][d_pad] (+ optional bf16 copy)
+cudaError_t launch_normalize(const float* in, int64_t rows, int d, int d_pad, float* x32, __nv_bfloat16* x16,
+                             cudaStream_t s);
+
+// Hash rows x32 [npts][d_pad] under all L repetitions and M sketches.
+// codes written at codes[j*cj + p*cp], sketches at sk[m*sm + p*sp].
+cudaError_t launch_hash(const pf_index* ix, const float* x32, int64_t npts, uint32_t* codes, int64_t cj,
+                        int64_t cp, uint64_t* sk, int64_t sm, int64_t sp, cudaStream_t s);
+
+// Sort every repetition's (code, position) pairs and build the prefix tables.
+cudaError_t sort_tables(pf_index* ix, uint32_t* codes_unsorted, cudaStream_t s);
+
+struct SearchArgs {
+  int Q = 0;
+  const float* qx = nullptr;
+  const uint32_t* qcodes = nullptr;
+  const uint64_t* qsk = nullptr;
+  const int32_t* k = nullptr;
+  const double* recall = nullptr;
+  const int32_t* start = nullptr;
+  int k_max = 0;
+  int filter = 1;
+  int scoring = 0;
+  uint32_t* out_ids = nullptr;
+  float* out_sims = nullptr;
+  pf_query_stats* stats = nullptr;
+  int32_t* counter = nullptr;
+};
+cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t s);
+
+}  // namespace pf
