@@ -307,9 +307,10 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
 pf_status pf_hash_queries(pf_index* ix, const float* queries, int64_t Q, uint32_t* qcodes, uint64_t* qsk,
                           void* stream) {
   return guarded([&]() -> pf_status {
-    if (!ix || !queries || !qcodes || !qsk) return fail(PF_ERR_INVALID_ARG, "null argument");
+    if (!ix) return fail(PF_ERR_INVALID_ARG, "null index");
     if (Q < 0 || Q > 0x7fffffffLL) return fail(PF_ERR_INVALID_ARG, "Q out of range");
-    if (Q == 0) return PF_OK;
+    if (Q == 0) return PF_OK;  // an empty batch may pass null buffers
+    if (!queries || !qcodes || !qsk) return fail(PF_ERR_INVALID_ARG, "null argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PF_CK(cudaSetDevice(ix->device));
     ensure_ws(ix, Q, 1);
@@ -327,9 +328,11 @@ pf_status pf_index_search(pf_index* ix, const float* queries, int64_t Q, const i
                           int32_t k_max, uint32_t* out_ids, float* out_sims, pf_query_stats* stats,
                           const pf_search_opts* opts, void* stream) {
   return guarded([&]() -> pf_status {
-    if (!ix || !queries || !k || !recall || !out_ids || !out_sims) return fail(PF_ERR_INVALID_ARG, "null argument");
+    if (!ix) return fail(PF_ERR_INVALID_ARG, "null index");
     if (Q < 0 || Q > 0x7fffffffLL) return fail(PF_ERR_INVALID_ARG, "Q out of range");
     if (k_max < 1 || k_max > kMaxK) return fail(PF_ERR_INVALID_ARG, "k_max must be in [1, 128]");
+    if (Q == 0) return PF_OK;  // an empty batch may pass null buffers
+    if (!queries || !k || !recall || !out_ids || !out_sims) return fail(PF_ERR_INVALID_ARG, "null argument");
     pf_search_opts o;
     pf_search_opts_default(&o);
     if (opts) o = *opts;
