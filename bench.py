@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Throughput of the batched adaptive k-NN query on one GB300.
+
+Workload: n = 1,000,000 unit vectors in d = 100 from an equal-weight mixture of
+1,000 von Mises-Fisher components (kappa = 50, centres uniform on the sphere);
+10,000 queries from the same mixture; cross-polytope LSH; 4 GiB index; k = 10.
+Metric: k-NN queries/s at measured recall >= 0.9 (recall against exact brute
+force).  One step = one batched search of all queries: query normalisation and
+hashing, the persistent search kernel, outputs.  The index build is timed
+separately (it is done once per index).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode bf16|fp32]
+  python bench.py --impl reference ...   (times the CPU oracle on a sample)
+
+Under torchrun every rank builds its own replica of the index and answers its
+own 10,000 queries (weak scaling, no collective on the data path); the timed
+region is bracketed by barriers and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import datagen  # noqa: E402
+
+WORKLOAD = "vmf1k-n1m-d100"
+METRIC = "k-NN queries/s at recall>=0.9 (n=1M, d=100, k=10)"
+UNIT = "queries/s"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB of L2
+CPU_SAMPLE_N = 20_000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--recall", type=float, default=0.95, help="recall target 1 - delta passed to the index")
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--Q", type=int, default=None)
+    ap.add_argument("--budget", type=int, default=None, help="index budget in bytes (default: the workload's)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def search_kernel_traffic():
+    """Per-launch DRAM bytes of the search kernel from the committed ncu summary,
+    valid only while the kernel source is the one that was profiled."""
+    path = os.path.join(ROOT, "profiles", "search_kernel_traffic.txt")
+    src = os.path.join(ROOT, "paper_1906_12211_gb300", "csrc", "kernels_search.cu")
+    if not os.path.exists(path):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernels_search.cu sha256[:16]") != digest:
+        return None
+    try:
+        return float(vals["dram bytes per launch (full workload)"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- workload
+def workload(rank: int, n_override=None, q_override=None, budget=None):
+    w = dict(datagen.WORKLOADS[WORKLOAD])
+    if budget is not None:
+        w["budget"] = int(budget)
+    n = w["n"] if n_override is None else n_override
+    Q = w["Q"] if q_override is None else q_override
+    X = datagen.vmf_mixture(n, w["d"], w["components"], w["kappa"], seed=0, purpose="points")
+    Qs = datagen.vmf_mixture(Q, w["d"], w["components"], w["kappa"], seed=rank, purpose="queries")
+    return w, X, Qs
+
+
+def brute_force_kth(torch, Xd, Qd, k):
+    """k-th largest exact similarity per query (float32 matmul on the GPU; used
+    only to measure recall)."""
+    Xn = torch.nn.functional.normalize(Xd, dim=1)
+    Qn = torch.nn.functional.normalize(Qd, dim=1)
+    out = []
+    for s in range(0, Qn.shape[0], 1024):
+        S = Qn[s:s + 1024] @ Xn.T
+        out.append(S.topk(k, dim=1).values[:, -1])
+        del S
+    return torch.cat(out)
+
+
+def algorithmic_bytes(st, L, n, d, k, mode):
+    """Bytes a query must touch (per query, averaged): prefix lookups and the
+    binary search for every repetition, id + code + sketch per retrieved
+    candidate, the row of every scored candidate (bf16 or fp32), the fp32 row of
+    every reranked one, the query and the output."""
+    import math
+
+    probes = max(1, math.ceil(math.log2(max(2, n / 8192))))
+    per_row = d * (2 if mode == "bf16" else 4)
+    b = (L * (8 + probes * 4) + st["retrieved"].astype(np.float64) * (4 + 4 + 8)
+         + st["scored"].astype(np.float64) * per_row + st["reranked"].astype(np.float64) * d * 4 + d * 4 + k * 8)
+    return float(b.mean())
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(X, Qs, L, k, recall, q_target_s=2.0):
+    """Oracle index over the first CPU_SAMPLE_N points of the same data with the
+    same number of repetitions; returns (index, queries, query count per step)."""
+    import oracle
+
+    oix = oracle.OracleIndex(X[:CPU_SAMPLE_N], oracle.CROSSPOLYTOPE, L=L, seed=0)
+    t = time.perf_counter()
+    oix.search(Qs[:64], k, recall)
+    per_q = (time.perf_counter() - t) / 64
+    nq = int(max(64, min(Qs.shape[0], q_target_s / max(per_q, 1e-6))))
+    return oix, nq
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w, X, Qs = workload(0, args.n, args.Q, args.budget)
+    import oracle
+
+    L = oracle.budget_L(oracle.CROSSPOLYTOPE, X.shape[0], X.shape[1], 32, w["budget"])
+    oix, nq = oracle_sample(X, Qs, L, w["k"], args.recall)
+    for _ in range(args.warmup):
+        oix.search(Qs[:nq], w["k"], args.recall)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oix.search(Qs[:nq], w["k"], args.recall)
+    el = time.perf_counter() - t
+    v = nq * args.steps / el
+    sample = (f"oracle index over the first {CPU_SAMPLE_N} of the {X.shape[0]} points (same data, L={L}, "
+              f"same seed), {nq} queries per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": int(X.shape[0]), "d": int(X.shape[1]), "k": w["k"],
+                   "recall_target": args.recall, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    import paper_1906_12211_gb300 as pf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pf.build()
+    dev = torch.device("cuda", local)
+    w, X, Qs = workload(rank, args.n, args.Q, args.budget)
+    Q, k = Qs.shape[0], w["k"]
+    Xd = torch.from_numpy(X).to(dev)
+    Qd = torch.from_numpy(Qs).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ix = pf.Index(Xd, "crosspolytope", budget_bytes=w["budget"], seed=0)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    kth = brute_force_kth(torch, Xd, Qd, k)
+    del Xd
+    kq = torch.full((Q,), k, dtype=torch.int32, device=dev)
+    rq = torch.full((Q,), args.recall, dtype=torch.float64, device=dev)
+    ids = torch.empty((Q, k), dtype=torch.int32, device=dev)
+    sims = torch.empty((Q, k), dtype=torch.float32, device=dev)
+    st = torch.empty((Q, pf.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(timing=False):
+        ix.search(Qd, kq, rq, k_max=k, scoring=args.mode, out_ids=ids, out_sims=sims, stats=st, timing=timing)
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms, kernel_ms, hash_ms = 0.0, 0.0, 0.0
+    for _ in range(args.steps):
+        flush.fill_(1)  # evict L2 between steps (outside the timed events)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(timing=True)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        h, kern, _ = ix.last_timing()
+        kernel_ms += kern
+        hash_ms += h
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_rank = total_ms / 1e3
+    if dist:
+        tt = torch.tensor([t_rank], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        dist.barrier()
+    else:
+        t_max = t_rank
+    value = Q * world * args.steps / t_max
+    stats = pf.stats_to_numpy(st)
+    recall = float((sims >= kth[:, None] - 1e-6).float().mean().item())
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        qh = torch.from_numpy(Qs).pin_memory()
+        kh = torch.full((Q,), k, dtype=torch.int32).pin_memory()
+        rh = torch.full((Q,), args.recall, dtype=torch.float64).pin_memory()
+        ih = torch.empty((Q, k), dtype=torch.int32).pin_memory()
+        sh = torch.empty((Q, k), dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            ix.search(qh, kh, rh, k_max=k, scoring=args.mode, out_ids=ih, out_sims=sh)
+        if dist:
+            dist.barrier()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            ix.search(qh, kh, rh, k_max=k, scoring=args.mode, out_ids=ih, out_sims=sh)
+        el = time.perf_counter() - t
+        if dist:
+            tt = torch.tensor([el], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = float(tt.item())
+        e2e = {"value": Q * world * args.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(Q * X.shape[1] * 4 + Q * 4 + Q * 8),
+               "d2h_bytes_per_step": int(Q * k * 8)}
+
+    peak, peak_kind = measured_peaks()
+    per_q = algorithmic_bytes(stats, ix.L, ix.n, ix.d, k, args.mode)
+    kern_s = kernel_ms / args.steps / 1e3
+    achieved = per_q * Q / kern_s / 1e9
+    traffic = search_kernel_traffic()
+    roofline = {"bound": "hbm", "kernel": "search_kernel", "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "algorithmic_bytes_per_launch": per_q * Q, "kernel_ms": kern_s * 1e3,
+                "query_hash_ms": hash_ms / args.steps}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        oix, nq = oracle_sample(X, Qs, ix.L, k, args.recall, q_target_s=15.0)
+        t = time.perf_counter()
+        oix.search(Qs[:nq], k, args.recall)
+        el = time.perf_counter() - t
+        cpu = {"value": nq / el, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"oracle index over the first {CPU_SAMPLE_N} of {ix.n} points (same data and seed, "
+                         f"L={ix.L}); {nq} queries; all host cores"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.mode == "fp32" else "bf16+f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": ix.n, "d": ix.d, "queries_per_gpu": Q, "k": k,
+                       "recall_target": args.recall, "family": "crosspolytope", "budget_bytes": w["budget"],
+                       "L": ix.L, "scoring": args.mode, "l2": "flushed between steps (512 MiB write)",
+                       "parallelism": f"replica x{world}"},
+            "recall": recall, "build_s": build_s,
+            "per_query": {f: float(stats[f].mean()) for f in ("stop_depth", "rounds", "retrieved",
+                                                             "passed_filter", "scored", "reranked")},
+            "gpu_launches": 3 * args.steps,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -73,7 +73,7 @@ typedef struct {
   int32_t scoring;             /* 0: float32 scoring; 1: bfloat16 scoring + exact float32 rerank */
   int32_t filter;              /* 1: sketch filter on (Sec. 4.2); 0: off.  Set by pf_search_opts_default */
   int32_t learned_start;       /* 1: start depth from the trained model (needs pf_learned_train) */
-  int32_t reserved0;
+  int32_t timing;              /* 1: record CUDA events around each phase (see pf_index_last_timing) */
   const int32_t* start_depth;  /* optional [Q] per-query start depth (host or device); NULL = none */
 } pf_search_opts;
 
@@ -149,6 +149,12 @@ pf_status pf_index_search(pf_index* index, const float* queries, int64_t Q, cons
  * then codes [Q][L] uint32 and sketches [Q][M] uint64 (host or device). */
 pf_status pf_hash_queries(pf_index* index, const float* queries, int64_t Q, uint32_t* qcodes,
                           uint64_t* qsketches, void* stream);
+
+/* Device time in milliseconds, measured with CUDA events on the call's stream,
+ * of the phases of the last pf_index_search on this index that ran with
+ * opts->timing = 1: t[0] query normalisation and hashing, t[1] the search
+ * kernel, t[2] all device work of the call.  count = entries to write (<= 3). */
+pf_status pf_index_last_timing(const pf_index* index, float* t, int32_t count);
 
 /* Sizes and resident bytes of an index. */
 pf_status pf_index_info(const pf_index* index, pf_index_info_t* info);

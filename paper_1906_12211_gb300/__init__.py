@@ -38,7 +38,7 @@ class BuildParams(C.Structure):
 
 class SearchOpts(C.Structure):
     _fields_ = [("scoring", C.c_int32), ("filter", C.c_int32), ("learned_start", C.c_int32),
-                ("reserved0", C.c_int32), ("start_depth", C.c_void_p)]
+                ("timing", C.c_int32), ("start_depth", C.c_void_p)]
 
 
 class QueryStats(C.Structure):
@@ -89,6 +89,7 @@ def lib():
                 "pf_index_search": (i32, [vp, vp, i64, vp, vp, i32, vp, vp, vp, vp, vp]),
                 "pf_hash_queries": (i32, [vp, vp, i64, vp, vp, vp]),
                 "pf_index_info": (i32, [vp, vp]),
+                "pf_index_last_timing": (i32, [vp, vp, i32]),
                 "pf_index_array": (i32, [vp, i32, vp, vp]),
                 "pf_index_read_array": (i32, [vp, i32, vp, C.c_uint64, vp]),
                 "pf_search_opts_default": (None, [vp]),
@@ -202,7 +203,7 @@ class Index:
         return qcodes, qsk
 
     def search(self, queries, k, recall, *, k_max: int | None = None, scoring: str = "fp32", filter: bool = True,
-               start_depth=None, out_ids=None, out_sims=None, stats=None, stream=None):
+               start_depth=None, out_ids=None, out_sims=None, stats=None, stream=None, timing: bool = False):
         """Answer a batch of queries; k and recall are per-query arrays (same
         device as the queries) or scalars.  Returns (ids, sims, stats)."""
         import torch
@@ -227,6 +228,7 @@ class Index:
         lib().pf_search_opts_default(C.byref(o))
         o.scoring = 1 if scoring == "bf16" else 0
         o.filter = 1 if filter else 0
+        o.timing = 1 if timing else 0
         sd = None
         if start_depth is not None:
             sd = start_depth if torch.is_tensor(start_depth) else torch.full((Q,), int(start_depth),
@@ -235,6 +237,13 @@ class Index:
         _check(lib().pf_index_search(self._h, _ptr(queries), Q, _ptr(k), _ptr(recall), int(k_max), _ptr(out_ids),
                                      _ptr(out_sims), _ptr(stats), C.byref(o), _stream_ptr(stream)))
         return out_ids, out_sims, stats
+
+
+    def last_timing(self):
+        """(hash_ms, search_kernel_ms, total_ms) of the last search run with timing=True."""
+        t = (C.c_float * 3)()
+        _check(lib().pf_index_last_timing(self._h, t, 3))
+        return tuple(float(v) for v in t)
 
 
 def stats_to_numpy(stats) -> np.ndarray:

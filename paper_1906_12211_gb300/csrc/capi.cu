@@ -145,6 +145,8 @@ void destroy(pf_index* ix) {
   dfree(ix->cpP);
   dfree(ix->cos_tab);
   free_ws(ix->ws);
+  for (auto& e : ix->ev)
+    if (e) cudaEventDestroy(e);
   cudaSetDevice(prev);
   delete ix;
 }
@@ -351,7 +353,14 @@ pf_status pf_index_search(pf_index* ix, const float* queries, int64_t Q, const i
     if (!on_device(k)) { stage_in(ws.k, k, sizeof(int32_t) * Q, s); kd = ws.k; }
     if (!on_device(recall)) { stage_in(ws.recall, recall, sizeof(double) * Q, s); rd = ws.recall; }
     if (sd && !on_device(sd)) { stage_in(ws.start, sd, sizeof(int32_t) * Q, s); sd = ws.start; }
+    const bool timing = o.timing != 0;
+    if (timing) {
+      for (auto& e : ix->ev)
+        if (!e) PF_CK(cudaEventCreate(&e));
+      PF_CK(cudaEventRecord(ix->ev[0], s));
+    }
     hash_queries_ws(ix, qd, Q, s);
+    if (timing) PF_CK(cudaEventRecord(ix->ev[1], s));
 
     const bool ids_dev = on_device(out_ids), sims_dev = on_device(out_sims);
     const bool st_dev = stats && on_device(stats);
@@ -372,6 +381,7 @@ pf_status pf_index_search(pf_index* ix, const float* queries, int64_t Q, const i
     a.counter = ws.counter;
     PF_CK(cudaMemsetAsync(ws.counter, 0, sizeof(int32_t) * 64, s));
     PF_CK(launch_search(ix, a, s));
+    if (timing) PF_CK(cudaEventRecord(ix->ev[2], s));
     if (!ids_dev)
       PF_CK(cudaMemcpyAsync(out_ids, ws.ids, sizeof(uint32_t) * size_t(Q) * k_max, cudaMemcpyDeviceToHost, s));
     if (!sims_dev)
@@ -383,8 +393,19 @@ pf_status pf_index_search(pf_index* ix, const float* queries, int64_t Q, const i
     PF_CK(cudaStreamSynchronize(s));
     PF_CK(cudaGetLastError());
     if (flags & 1) return fail(PF_ERR_INVALID_ARG, "some k not in [1, k_max] or recall not in (0, 1)");
+    if (timing) {
+      PF_CK(cudaEventElapsedTime(&ix->last_ms[0], ix->ev[0], ix->ev[1]));
+      PF_CK(cudaEventElapsedTime(&ix->last_ms[1], ix->ev[1], ix->ev[2]));
+      PF_CK(cudaEventElapsedTime(&ix->last_ms[2], ix->ev[0], ix->ev[2]));
+    }
     return PF_OK;
   });
+}
+
+pf_status pf_index_last_timing(const pf_index* ix, float* t, int32_t count) {
+  if (!ix || !t || count < 0 || count > 3) return fail(PF_ERR_INVALID_ARG, "bad argument");
+  for (int i = 0; i < count; ++i) t[i] = ix->last_ms[i];
+  return PF_OK;
 }
 
 pf_status pf_index_info(const pf_index* ix, pf_index_info_t* info) {

@@ -90,6 +90,8 @@ struct pf_index {
   float bf16_err = 0.f;            // bound on |bf16 estimate - float32 canonical similarity|
   int num_sms = 0;
   pf_workspace ws;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // phase timing events
+  float last_ms[3] = {0.f, 0.f, 0.f};
 };
 
 // ---------------------------------------------------------------- launchers
