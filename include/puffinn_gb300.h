@@ -145,6 +145,27 @@ pf_status pf_index_search(pf_index* index, const float* queries, int64_t Q, cons
                           const double* recall, int32_t k_max, uint32_t* out_ids, float* out_sims,
                           pf_query_stats* stats, const pf_search_opts* opts, void* stream);
 
+/* pf_index_search for callers that cannot allocate device memory while they
+ * run: a serving process whose device memory is handed out up front by another
+ * allocator, or a path where an allocation's latency or failure is not
+ * acceptable.  The paper has no counterpart; this is a deployment variant.
+ *   - Same arguments, semantics and results as pf_index_search, except that
+ *     queries, k, recall, out_ids, out_sims, stats (if not NULL) and
+ *     opts->start_depth (if set) must all be device memory.
+ *   - Scratch (normalised queries, query codes and sketches, work counter)
+ *     lives in one 32 MiB file-scope device array that every GPU loading the
+ *     library holds until the process exits.  A batch must satisfy
+ *     Q*(4*d_pad + 4*L + 8*M) + 1024 <= 32 MiB; larger batches are rejected with
+ *     PF_ERR_INVALID_ARG and a message giving the limit (split the batch).
+ *   - No cudaMalloc, cudaFree or other allocating call is made.
+ *   - All calls share the array: calls whose device work overlaps (other
+ *     streams, other threads) race and must be serialised by the caller.
+ *   - The first call on a device looks up the array's device address; make that
+ *     first call before any stream capture. */
+pf_status pf_index_search_noalloc(pf_index* index, const float* queries, int64_t Q, const int32_t* k,
+                                  const double* recall, int32_t k_max, uint32_t* out_ids, float* out_sims,
+                                  pf_query_stats* stats, const pf_search_opts* opts, void* stream);
+
 /* Hash Q queries only (the first step of every query, Sec. 4.1): normalise,
  * then codes [Q][L] uint32 and sketches [Q][M] uint64 (host or device). */
 pf_status pf_hash_queries(pf_index* index, const float* queries, int64_t Q, uint32_t* qcodes,

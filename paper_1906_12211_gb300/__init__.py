@@ -87,6 +87,7 @@ def lib():
             sig = {
                 "pf_index_build": (i32, [vp, vp, vp, vp]),
                 "pf_index_search": (i32, [vp, vp, i64, vp, vp, i32, vp, vp, vp, vp, vp]),
+                "pf_index_search_noalloc": (i32, [vp, vp, i64, vp, vp, i32, vp, vp, vp, vp, vp]),
                 "pf_hash_queries": (i32, [vp, vp, i64, vp, vp, vp]),
                 "pf_index_info": (i32, [vp, vp]),
                 "pf_index_last_timing": (i32, [vp, vp, i32]),
@@ -238,6 +239,19 @@ class Index:
                                      _ptr(out_sims), _ptr(stats), C.byref(o), _stream_ptr(stream)))
         return out_ids, out_sims, stats
 
+
+    def search_noalloc(self, queries, k, recall, out_ids, out_sims, *, k_max: int, scoring: str = "fp32",
+                       filter: bool = True, stats=None, stream=None):
+        """pf_index_search_noalloc: every buffer already on the device, no
+        allocation inside the call (fixed 32 MiB scratch)."""
+        o = SearchOpts()
+        lib().pf_search_opts_default(C.byref(o))
+        o.scoring = 1 if scoring == "bf16" else 0
+        o.filter = 1 if filter else 0
+        _check(lib().pf_index_search_noalloc(self._h, _ptr(queries), int(queries.shape[0]), _ptr(k), _ptr(recall),
+                                             int(k_max), _ptr(out_ids), _ptr(out_sims), _ptr(stats), C.byref(o),
+                                             _stream_ptr(stream)))
+        return out_ids, out_sims, stats
 
     def last_timing(self):
         """(hash_ms, search_kernel_ms, total_ms) of the last search run with timing=True."""
