@@ -5,18 +5,23 @@
 // Per round at prefix length i, for every repetition j the warp extends the
 // range [l, r) of positions around the query's code so that it covers the
 // block of codes sharing the first i bits, growing each side in whole
-// segments of B entries (Sec. 4.2, App. C).  The new positions are streamed
-// lane-parallel: position -> id -> sketch Hamming filter (Sec. 4.2) -> exact
-// similarity -> top-k accumulator (unique ids, ordered by similarity then id).
-// After the round the stop test of Lemma 1 runs in float64.
+// segments of B entries (Sec. 4.2, App. C).  The new positions of 32
+// repetitions are flattened and streamed lane-parallel, four per lane per step
+// so that many independent loads are in flight: position -> id -> sketch
+// Hamming filter (Sec. 4.2) -> compacted candidate buffer.  Buffered
+// candidates are scored (float32 canonical, or a bfloat16 estimate followed by
+// an exact float32 rerank of those whose estimate plus its error bound can
+// still reach the running k-th similarity) and offered to the top-k
+// accumulator (unique ids, ordered by similarity then id).  After the round
+// the stop test of Lemma 1 runs in float64.
 //
 // Readings shared with the oracle: the sketch threshold and s_k are taken at
 // the start of each round; the stop test runs once per round (Sec. 4.1); the
 // canonical similarity is float32 with 32 partial sums (partial c takes the
 // coordinates = c mod 32 in index order by fused multiply-add) combined as
-// s[c] += s[c + w] for w = 16, 8, 4, 2, 1.  Because only the filter depends on
-// the order of insertion and it uses the round's snapshot, the result does not
-// depend on the order in which lanes visit candidates.
+// s[c] += s[c + w] for w = 16, 8, 4, 2, 1.  Only the filter depends on s_k and
+// it uses the round's snapshot, so the result does not depend on the order in
+// which lanes visit candidates.
 #include <cuda_bf16.h>
 
 #include "pf_internal.h"
@@ -26,11 +31,13 @@ namespace pf {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kWarps = 4;          // warps (queries in flight) per CTA
-constexpr int kCandBuf = 64;       // compacted candidate ids per warp
+constexpr int kWarps = 4;      // warps (queries in flight) per CTA
+constexpr int kUnroll = 4;     // candidate positions per lane per step
+constexpr int kCandBuf = 256;  // compacted candidate ids per warp
+constexpr int kFlushAt = kCandBuf - 32 * kUnroll;
 
 struct Dev {
-  int64_t n;
+  int n;
   int d, d_pad, L, Kb, M, B, family, ell;
   const float* x32;
   const __nv_bfloat16* x16;
@@ -60,7 +67,7 @@ __device__ __forceinline__ bool better(float s1, uint32_t i1, float s2, uint32_t
   return s1 > s2 || (s1 == s2 && i1 < i2);
 }
 
-__device__ __forceinline__ double ipow(double x, int64_t e) {
+__device__ __forceinline__ double ipow(double x, int e) {
   double r = 1.0, b = x;
   while (e > 0) {
     if (e & 1) r = __dmul_rn(r, b);
@@ -72,7 +79,7 @@ __device__ __forceinline__ double ipow(double x, int64_t e) {
 
 // probability that a point at similarity s collides with the query on the
 // first `depth` bits of one repetition (Sec. 4.3)
-__device__ double collision_prob(const Dev& P, double s, int depth) {
+__device__ __noinline__ double collision_prob(const Dev& P, double s, int depth) {
   if (P.family == PF_SIMHASH) {
     const double sc = s > 1.0 ? 1.0 : (s < -1.0 ? -1.0 : s);
     const double p = 1.0 - acos(sc) / M_PI;
@@ -96,82 +103,39 @@ __device__ __forceinline__ int filter_tau(const Dev& P, float s_k) {
 __device__ __forceinline__ bool prefix_match(uint32_t a, uint32_t b, uint32_t mask) { return ((a ^ b) & mask) == 0; }
 
 // first position in [lo, hi) of codes with code >= key
-__device__ __forceinline__ int64_t lower_bound(const uint32_t* c, int64_t lo, int64_t hi, uint32_t key) {
+__device__ __forceinline__ uint32_t lower_bound(const uint32_t* c, uint32_t lo, uint32_t hi, uint32_t key) {
   while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (c[mid] < key) lo = mid + 1; else hi = mid;
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(c + mid) < key) lo = mid + 1; else hi = mid;
   }
   return lo;
 }
 
-// Canonical float32 similarity of the query (shared memory, d_pad floats) and
-// row `id`, computed by the 8 lanes of a group (lane g8 owns partials
-// 4*g8 .. 4*g8+3, i.e. float4 chunks g8, g8+8, ...).  Valid in all 8 lanes.
-__device__ __forceinline__ float sim_canonical(const float* __restrict__ q, const float* __restrict__ row,
-                                               int d_pad, int g8, unsigned gmask) {
-  const float4* q4 = reinterpret_cast<const float4*>(q);
-  const float4* r4 = reinterpret_cast<const float4*>(row);
-  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int ch = g8; ch * 4 < d_pad; ch += 8) {
-    const float4 a = q4[ch];
-    const float4 b = __ldg(r4 + ch);
-    s.x = __fmaf_rn(a.x, b.x, s.x);
-    s.y = __fmaf_rn(a.y, b.y, s.y);
-    s.z = __fmaf_rn(a.z, b.z, s.z);
-    s.w = __fmaf_rn(a.w, b.w, s.w);
-  }
-  // s[c] += s[c+16], s[c] += s[c+8], s[c] += s[c+4]: partner lanes 4, 2, 1 away
-#pragma unroll
-  for (int off = 4; off >= 1; off >>= 1) {
-    s.x = __fadd_rn(s.x, __shfl_xor_sync(gmask, s.x, off, 8));
-    s.y = __fadd_rn(s.y, __shfl_xor_sync(gmask, s.y, off, 8));
-    s.z = __fadd_rn(s.z, __shfl_xor_sync(gmask, s.z, off, 8));
-    s.w = __fadd_rn(s.w, __shfl_xor_sync(gmask, s.w, off, 8));
-  }
-  return __fadd_rn(__fadd_rn(s.x, s.z), __fadd_rn(s.y, s.w));
-}
-
-// bfloat16 estimate: float32 query against the bfloat16 row; any order.
-__device__ __forceinline__ float sim_bf16(const float* __restrict__ q, const __nv_bfloat16* __restrict__ row,
-                                          int d_pad, int g8, unsigned gmask) {
-  const uint4* r8 = reinterpret_cast<const uint4*>(row);
-  float acc = 0.f;
-  for (int ch = g8; ch * 8 < d_pad; ch += 8) {
-    const uint4 u = __ldg(r8 + ch);
-    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const float lo = __uint_as_float(w[t] << 16);
-      const float hi = __uint_as_float(w[t] & 0xffff0000u);
-      acc = fmaf(q[ch * 8 + 2 * t], lo, acc);
-      acc = fmaf(q[ch * 8 + 2 * t + 1], hi, acc);
-    }
-  }
-#pragma unroll
-  for (int off = 4; off >= 1; off >>= 1) acc += __shfl_xor_sync(gmask, acc, off, 8);
-  return acc;
-}
-
 struct WarpState {
-  float* q;        // [d_pad]
-  uint32_t* l;     // [L]
-  uint32_t* r;     // [L]
-  float* pq_s;     // [k_max]
-  uint32_t* pq_id; // [k_max]
-  uint32_t* cbuf;  // [kCandBuf]
+  float* q;         // [d_pad]
+  uint32_t* l;      // [L]
+  uint32_t* r;      // [L]
+  float* pq_s;      // [k_max]
+  uint32_t* pq_id;  // [k_max]
+  uint32_t* cbuf;   // [kCandBuf]
+};
+
+struct Counters {
+  uint32_t retrieved = 0, passed = 0, scored = 0, reranked = 0;
 };
 
 // Offer (s, id) to the sorted top-k of the warp (all lanes call with the same
 // arguments).  Returns the new size.
-__device__ int pq_offer(WarpState& w, int size, int k, float s, uint32_t id, int lane) {
+__device__ __forceinline__ int pq_offer(WarpState& w, int size, int k, float s, uint32_t id, int lane) {
+  if (size == k && !better(s, id, w.pq_s[k - 1], w.pq_id[k - 1])) return size;
   bool dup = false;
   int cnt = 0;
   for (int t = lane; t < size; t += 32) {
-    dup |= w.pq_id[t] == id;
-    cnt += better(w.pq_s[t], w.pq_id[t], s, id) ? 1 : 0;
+    const uint32_t it = w.pq_id[t];
+    dup |= it == id;
+    cnt += better(w.pq_s[t], it, s, id) ? 1 : 0;
   }
   if (__any_sync(kFull, dup)) return size;
-  if (size == k && !better(s, id, w.pq_s[k - 1], w.pq_id[k - 1])) return size;
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(kFull, cnt, off);
   const int pos = cnt;
@@ -204,44 +168,151 @@ __device__ int pq_offer(WarpState& w, int size, int k, float s, uint32_t id, int
   return nsize;
 }
 
-struct Counters {
-  int64_t retrieved = 0, passed = 0, scored = 0, reranked = 0;
-};
-
-// Score the buffered candidate ids and offer them to the top-k.
-__device__ int flush_candidates(const Dev& P, WarpState& w, int cnt, int size, int k, int lane, Counters& ct) {
-  const int g = lane >> 3, g8 = lane & 7;
-  const unsigned gmask = 0xffu << (lane & ~7);  // the 8 lanes scoring one candidate
-  for (int c0 = 0; c0 < cnt; c0 += 4) {
-    const int c = c0 + g;
-    const bool valid = c < cnt;
-    const uint32_t id = valid ? w.cbuf[c] : 0u;
-    float s;
-    bool need = valid;
-    if (P.scoring == 1) {
-      const float est = sim_bf16(w.q, P.x16 + int64_t(id) * P.d_pad, P.d_pad, g8, gmask);
-      // the running k-th similarity only rises, so a candidate whose
-      // estimate plus the error bound is below it cannot enter the top-k
-      if (size == k && est + P.bf16_err < w.pq_s[k - 1]) need = false;
-      const unsigned rr = __ballot_sync(kFull, need && g8 == 0);
-      if (lane == 0) ct.reranked += __popc(rr);
-    }
-    s = need ? sim_canonical(w.q, P.x32 + int64_t(id) * P.d_pad, P.d_pad, g8, gmask) : 0.f;
-    const unsigned vb = __ballot_sync(kFull, valid && g8 == 0);
-    if (lane == 0) ct.scored += __popc(vb);
-    // offer in candidate order (the result is order independent)
+// Canonical float32 similarities of the query with two rows, computed by the
+// 8 lanes of a group (lane g8 owns partials 4*g8 .. 4*g8+3, i.e. float4
+// chunks g8, g8+8, ...).  Both rows' loads are issued before the arithmetic.
+template <int NT>
+__device__ __forceinline__ void sim_canonical2(const float* __restrict__ q, const float* __restrict__ ra,
+                                               const float* __restrict__ rb, int d_pad, int g8, unsigned gmask,
+                                               float& out_a, float& out_b) {
+  const float4* q4 = reinterpret_cast<const float4*>(q);
+  const float4* a4 = reinterpret_cast<const float4*>(ra);
+  const float4* b4 = reinterpret_cast<const float4*>(rb);
+  float4 va[NT], vb[NT];
 #pragma unroll
-    for (int gg = 0; gg < 4; ++gg) {
-      const float ss = __shfl_sync(kFull, s, gg * 8);
-      const uint32_t ii = __shfl_sync(kFull, id, gg * 8);
-      const bool nn = __shfl_sync(kFull, need ? 1 : 0, gg * 8) != 0;
-      if (nn) size = pq_offer(w, size, k, ss, ii, lane);
+  for (int t = 0; t < NT; ++t) {
+    const int ch = g8 + 8 * t;
+    va[t] = ch * 4 < d_pad ? __ldg(a4 + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+    vb[t] = ch * 4 < d_pad ? __ldg(b4 + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  float4 sa = make_float4(0.f, 0.f, 0.f, 0.f), sb = sa;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const int ch = g8 + 8 * t;
+    if (ch * 4 < d_pad) {
+      const float4 x = q4[ch];
+      sa.x = __fmaf_rn(x.x, va[t].x, sa.x);
+      sa.y = __fmaf_rn(x.y, va[t].y, sa.y);
+      sa.z = __fmaf_rn(x.z, va[t].z, sa.z);
+      sa.w = __fmaf_rn(x.w, va[t].w, sa.w);
+      sb.x = __fmaf_rn(x.x, vb[t].x, sb.x);
+      sb.y = __fmaf_rn(x.y, vb[t].y, sb.y);
+      sb.z = __fmaf_rn(x.z, vb[t].z, sb.z);
+      sb.w = __fmaf_rn(x.w, vb[t].w, sb.w);
+    }
+  }
+  // s[c] += s[c+16], s[c] += s[c+8], s[c] += s[c+4]: partner lanes 4, 2, 1 away
+#pragma unroll
+  for (int off = 4; off >= 1; off >>= 1) {
+    sa.x = __fadd_rn(sa.x, __shfl_xor_sync(gmask, sa.x, off, 8));
+    sa.y = __fadd_rn(sa.y, __shfl_xor_sync(gmask, sa.y, off, 8));
+    sa.z = __fadd_rn(sa.z, __shfl_xor_sync(gmask, sa.z, off, 8));
+    sa.w = __fadd_rn(sa.w, __shfl_xor_sync(gmask, sa.w, off, 8));
+    sb.x = __fadd_rn(sb.x, __shfl_xor_sync(gmask, sb.x, off, 8));
+    sb.y = __fadd_rn(sb.y, __shfl_xor_sync(gmask, sb.y, off, 8));
+    sb.z = __fadd_rn(sb.z, __shfl_xor_sync(gmask, sb.z, off, 8));
+    sb.w = __fadd_rn(sb.w, __shfl_xor_sync(gmask, sb.w, off, 8));
+  }
+  // s[c] += s[c+2], then s[0] += s[1]
+  out_a = __fadd_rn(__fadd_rn(sa.x, sa.z), __fadd_rn(sa.y, sa.w));
+  out_b = __fadd_rn(__fadd_rn(sb.x, sb.z), __fadd_rn(sb.y, sb.w));
+}
+
+// bfloat16 estimate of <q, x> by the 4 lanes of a group: float32 query against
+// the bfloat16 row (chunks of 8 elements g4, g4+4, ...), any summation order.
+template <int NT>
+__device__ __forceinline__ float sim_bf16(const float* __restrict__ q, const __nv_bfloat16* __restrict__ row,
+                                          int d_pad, int g4, unsigned gmask) {
+  const uint4* r8 = reinterpret_cast<const uint4*>(row);
+  uint4 v[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const int ch = g4 + 4 * t;
+    v[t] = ch * 8 < d_pad ? __ldg(r8 + ch) : make_uint4(0u, 0u, 0u, 0u);
+  }
+  float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const int ch = g4 + 4 * t;
+    if (ch * 8 < d_pad) {
+      const float4 qa = reinterpret_cast<const float4*>(q)[2 * ch];
+      const float4 qb = reinterpret_cast<const float4*>(q)[2 * ch + 1];
+      acc0 = fmaf(qa.x, __uint_as_float(v[t].x << 16), acc0);
+      acc1 = fmaf(qa.y, __uint_as_float(v[t].x & 0xffff0000u), acc1);
+      acc0 = fmaf(qa.z, __uint_as_float(v[t].y << 16), acc0);
+      acc1 = fmaf(qa.w, __uint_as_float(v[t].y & 0xffff0000u), acc1);
+      acc0 = fmaf(qb.x, __uint_as_float(v[t].z << 16), acc0);
+      acc1 = fmaf(qb.y, __uint_as_float(v[t].z & 0xffff0000u), acc1);
+      acc0 = fmaf(qb.z, __uint_as_float(v[t].w << 16), acc0);
+      acc1 = fmaf(qb.w, __uint_as_float(v[t].w & 0xffff0000u), acc1);
+    }
+  }
+  float acc = acc0 + acc1;
+  acc += __shfl_xor_sync(gmask, acc, 2, 4);
+  acc += __shfl_xor_sync(gmask, acc, 1, 4);
+  return acc;
+}
+
+// Exact float32 similarities of the `cnt` ids at the front of cbuf, each
+// offered to the top-k (8 candidates per step: 4 groups of 8 lanes, 2 rows
+// each).
+template <int NT>
+__device__ __forceinline__ int canonical_and_offer(const Dev& P, WarpState& w, int cnt, int size, int k, int lane) {
+  const int g = lane >> 3, g8 = lane & 7;
+  const unsigned gmask = 0xffu << (lane & ~7);
+  for (int c0 = 0; c0 < cnt; c0 += 8) {
+    const int ca = c0 + g, cb = c0 + 4 + g;
+    const uint32_t ida = ca < cnt ? w.cbuf[ca] : w.cbuf[c0];
+    const uint32_t idb = cb < cnt ? w.cbuf[cb] : w.cbuf[c0];
+    float sa, sb;
+    sim_canonical2<NT>(w.q, P.x32 + size_t(ida) * P.d_pad, P.x32 + size_t(idb) * P.d_pad, P.d_pad, g8, gmask, sa, sb);
+    const int m = min(8, cnt - c0);
+    for (int t = 0; t < m; ++t) {
+      const int src = (t & 3) * 8;
+      const float s = __shfl_sync(kFull, t < 4 ? sa : sb, src);
+      const uint32_t id = __shfl_sync(kFull, t < 4 ? ida : idb, src);
+      size = pq_offer(w, size, k, s, id, lane);
     }
   }
   return size;
 }
 
-__global__ void __launch_bounds__(kWarps * 32) search_kernel(Dev P) {
+// Score the cnt buffered candidate ids and offer them to the top-k.
+template <int NT>
+__device__ __forceinline__ int flush_candidates(const Dev& P, WarpState& w, int cnt, int size, int k, int lane,
+                                                Counters& ct) {
+  if (lane == 0) ct.scored += cnt;
+  if (P.scoring != 1) return canonical_and_offer<NT>(P, w, cnt, size, k, lane);
+  // bfloat16 estimates, 8 rows per step (4 lanes each).  A candidate can enter
+  // the top-k only if its exact similarity reaches the running k-th, which
+  // never decreases; the estimate is within bf16_err of the exact value, so
+  // candidates with estimate + bf16_err below the current k-th are dropped and
+  // the others are compacted in place at the front of cbuf.
+  const int g = lane >> 2, g4 = lane & 3;
+  const unsigned gmask = 0xfu << (lane & ~3);
+  const bool full = size == k;
+  const float kth = full ? w.pq_s[k - 1] : -INFINITY;
+  int nr = 0;
+  for (int c0 = 0; c0 < cnt; c0 += 8) {
+    const int c = c0 + g;
+    const bool valid = c < cnt;
+    const uint32_t id = valid ? w.cbuf[c] : w.cbuf[c0];
+    const float est = sim_bf16<NT>(w.q, P.x16 + size_t(id) * P.d_pad, P.d_pad, g4, gmask);
+    const bool need = valid && (!full || est + P.bf16_err >= kth);
+    const unsigned b = __ballot_sync(kFull, need && g4 == 0);
+    __syncwarp();
+    if (need && g4 == 0) w.cbuf[nr + __popc(b & ((1u << lane) - 1u))] = id;
+    nr += __popc(b);
+    __syncwarp();
+  }
+  if (lane == 0) ct.reranked += nr;
+  return canonical_and_offer<NT>(P, w, nr, size, k, lane);
+}
+
+// NT = d_pad / 32 rounded up: float4 chunks of a float32 row per lane of an
+// 8-lane group (and 16-byte chunks of a bfloat16 row per lane of a 4-lane group)
+template <int NT>
+__global__ void __launch_bounds__(kWarps * 32, 5) search_kernel(Dev P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int d_pad = P.d_pad, L = P.L, kmax = P.k_max;
@@ -256,7 +327,8 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(Dev P) {
   w.pq_s = reinterpret_cast<float*>(w.r + L);
   w.pq_id = reinterpret_cast<uint32_t*>(w.pq_s + kmax);
   w.cbuf = w.pq_id + kmax;
-  const int64_t n = P.n;
+  const uint32_t n = uint32_t(P.n);
+  const uint32_t lt_mask = (1u << lane) - 1u;
 
   for (;;) {
     int qi = 0;
@@ -264,21 +336,21 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(Dev P) {
     qi = __shfl_sync(kFull, qi, 0);
     if (qi >= P.Q) break;
 
-    const float* qg = P.qx + int64_t(qi) * d_pad;
-    for (int i = lane; i < d_pad; i += 32) w.q[i] = qg[i];
-    const uint32_t* qc = P.qcodes + int64_t(qi) * L;
-    const uint64_t* qs = P.qsk + int64_t(qi) * P.M;
     const int k = P.k[qi];
     const double rec = P.recall[qi];
     if (k < 1 || k > kmax || !(rec > 0.0 && rec < 1.0)) {
       if (lane == 0) atomicOr(P.counter + 1, 1);
       for (int t = lane; t < kmax; t += 32) {
-        P.out_ids[int64_t(qi) * kmax + t] = 0xffffffffu;
-        P.out_sims[int64_t(qi) * kmax + t] = -INFINITY;
+        P.out_ids[size_t(qi) * kmax + t] = 0xffffffffu;
+        P.out_sims[size_t(qi) * kmax + t] = -INFINITY;
       }
       continue;
     }
     const double delta = 1.0 - rec;
+    const float* qg = P.qx + size_t(qi) * d_pad;
+    for (int i = lane; i < d_pad; i += 32) w.q[i] = qg[i];
+    const uint32_t* qc = P.qcodes + size_t(qi) * L;
+    const uint64_t* qs = P.qsk + size_t(qi) * P.M;
     int i0 = P.Kb;
     if (P.start) {
       const int sd = P.start[qi];
@@ -287,11 +359,11 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(Dev P) {
     // initial empty range at the first code >= the query's code
     for (int j = lane; j < L; j += 32) {
       const uint32_t c = qc[j];
-      const uint32_t* pj = P.pfx + int64_t(j) * kPrefixSize;
+      const uint32_t* pj = P.pfx + size_t(j) * kPrefixSize;
       const uint32_t t = c >> (32 - kPrefixBits);
-      const int64_t lb = lower_bound(P.codes + int64_t(j) * n, pj[t], pj[t + 1], c);
-      w.l[j] = uint32_t(lb);
-      w.r[j] = uint32_t(lb);
+      const uint32_t lb = lower_bound(P.codes + size_t(j) * n, __ldg(pj + t), __ldg(pj + t + 1), c);
+      w.l[j] = lb;
+      w.r[j] = lb;
     }
     __syncwarp();
 
@@ -305,73 +377,77 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(Dev P) {
         // prefix length 0: every point collides in every repetition, so the
         // round is a linear scan of all points (Lemma 1, i = 0), unfiltered.
         int nb = 0;
-        for (int64_t b0 = 0; b0 < n; b0 += 32) {
-          const int64_t id = b0 + lane;
+        for (uint32_t b0 = 0; b0 < n; b0 += 32) {
+          const uint32_t id = b0 + lane;
           const unsigned m = __ballot_sync(kFull, id < n);
-          if (id < n) w.cbuf[nb + __popc(m & ((1u << lane) - 1u))] = uint32_t(id);
+          if (id < n) w.cbuf[nb + __popc(m & lt_mask)] = id;
           nb += __popc(m);
-          if (lane == 0) { ct.retrieved += __popc(m); ct.passed += __popc(m); }
+          if (lane == 0) {
+            ct.retrieved += __popc(m);
+            ct.passed += __popc(m);
+          }
           __syncwarp();
-          if (nb >= kCandBuf - 32) {
-            size = flush_candidates(P, w, nb, size, k, lane, ct);
+          if (nb > kFlushAt) {
+            size = flush_candidates<NT>(P, w, nb, size, k, lane, ct);
             nb = 0;
           }
         }
-        if (nb) size = flush_candidates(P, w, nb, size, k, lane, ct);
+        if (nb) size = flush_candidates<NT>(P, w, nb, size, k, lane, ct);
         ++rounds;
         stop_depth = 0;
         break;
       }
       const uint32_t mask = 0xffffffffu << (32 - depth);
       const bool single = prev == depth + 1;
-      // side that can grow when only bit `depth` (0-based from the top) is dropped
       int nb = 0;
       for (int jb = 0; jb < L; jb += 32) {
         const int j = jb + lane;
         uint32_t l = 0, r = 0, nl = 0, nr = 0;
         if (j < L) {
           const uint32_t qcj = qc[j];
-          const uint32_t* cj = P.codes + int64_t(j) * n;
+          const uint32_t* cj = P.codes + size_t(j) * n;
           l = w.l[j];
           r = w.r[j];
           nl = l;
           nr = r;
+          // in a one-bit step only the side of the dropped bit can grow
+          // (bit `depth`, counted from the top, of the query's code)
           const bool dropped_one = (qcj >> (31 - depth)) & 1u;
           const bool try_left = !single || dropped_one;
           const bool try_right = !single || !dropped_one;
           const uint32_t B = uint32_t(P.B);
-          if (try_left && l > 0 && prefix_match(cj[l - 1], qcj, mask)) {
+          if (try_left && l > 0 && prefix_match(__ldg(cj + l - 1), qcj, mask)) {
             // smallest m >= 1 with l - B*m <= 0 or codes[l - B*m - 1] outside the block
-            uint32_t lo = 0, hi = 1;  // f(lo) false, search f(hi)
+            uint32_t lo = 0, hi = 1;
             for (;;) {
               const int64_t pos = int64_t(l) - int64_t(B) * hi;
-              if (pos <= 0 || !prefix_match(cj[pos - 1], qcj, mask)) break;
+              if (pos <= 0 || !prefix_match(__ldg(cj + pos - 1), qcj, mask)) break;
               lo = hi;
               hi *= 2;
             }
             while (hi - lo > 1) {
               const uint32_t mid = (lo + hi) >> 1;
               const int64_t pos = int64_t(l) - int64_t(B) * mid;
-              if (pos <= 0 || !prefix_match(cj[pos - 1], qcj, mask)) hi = mid; else lo = mid;
+              if (pos <= 0 || !prefix_match(__ldg(cj + pos - 1), qcj, mask)) hi = mid; else lo = mid;
             }
             const int64_t pos = int64_t(l) - int64_t(B) * hi;
             nl = pos < 0 ? 0u : uint32_t(pos);
           }
-          if (try_right && r < n && prefix_match(cj[r], qcj, mask)) {
+          if (try_right && r < n && prefix_match(__ldg(cj + r), qcj, mask)) {
             uint32_t lo = 0, hi = 1;
             for (;;) {
               const int64_t pos = int64_t(r) + int64_t(B) * hi;
-              if (pos >= n || !prefix_match(cj[pos], qcj, mask)) break;
+              if (pos >= int64_t(n) || !prefix_match(__ldg(cj + pos), qcj, mask)) break;
               lo = hi;
               hi *= 2;
             }
             while (hi - lo > 1) {
               const uint32_t mid = (lo + hi) >> 1;
               const int64_t pos = int64_t(r) + int64_t(B) * mid;
-              if (pos >= n || !prefix_match(cj[pos], qcj, mask)) hi = mid; else lo = mid;
+              if (pos >= int64_t(n) || !prefix_match(__ldg(cj + pos), qcj, mask)) hi = mid; else lo = mid;
             }
             const int64_t pos = int64_t(r) + int64_t(B) * hi;
-            nr = pos > n ? uint32_t(n) : uint32_t(pos);
+            nr = pos > int64_t(n) ? n : uint32_t(pos);
           }
           w.l[j] = nl;
           w.r[j] = nr;
@@ -388,45 +464,61 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(Dev P) {
         const uint32_t ex = inc - cnt;
         const uint32_t total = __shfl_sync(kFull, inc, 31);
         if (lane == 0) ct.retrieved += total;
-        for (uint32_t e0 = 0; e0 < total; e0 += 32) {
-          const uint32_t idx = e0 + lane;
-          // owner lane: largest o with ex_o <= idx
-          int o = 0;
+        for (uint32_t e0 = 0; e0 < total; e0 += 32 * kUnroll) {
+          uint32_t id[kUnroll], pos[kUnroll];
+          int jo[kUnroll];
+          bool valid[kUnroll];
 #pragma unroll
-          for (int step = 16; step >= 1; step >>= 1) {
-            const uint32_t v = __shfl_sync(kFull, ex, o + step);
-            if (v <= idx) o += step;
-          }
-          const uint32_t ex_o = __shfl_sync(kFull, ex, o);
-          const uint32_t cl_o = __shfl_sync(kFull, cl, o);
-          const uint32_t nl_o = __shfl_sync(kFull, nl, o);
-          const uint32_t r_o = __shfl_sync(kFull, r, o);
-          bool pass = false;
-          uint32_t id = 0;
-          if (idx < total) {
-            const uint32_t off = idx - ex_o;
-            const int jo = jb + o;
-            const uint32_t pos = off < cl_o ? nl_o + off : r_o + (off - cl_o);
-            id = __ldg(P.ids + int64_t(jo) * n + pos);
-            pass = true;
-            if (P.filter) {
-              const int m = jo % P.M;
-              const uint64_t h = __ldg(P.sk + int64_t(m) * n + id) ^ qs[m];
-              pass = __popcll(h) <= tau;
+          for (int u = 0; u < kUnroll; ++u) {
+            const uint32_t idx = e0 + 32 * u + lane;
+            // owner lane: largest o with ex_o <= idx
+            int o = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+              const uint32_t v = __shfl_sync(kFull, ex, o + step);
+              if (v <= idx) o += step;
             }
+            const uint32_t ex_o = __shfl_sync(kFull, ex, o);
+            const uint32_t cl_o = __shfl_sync(kFull, cl, o);
+            const uint32_t nl_o = __shfl_sync(kFull, nl, o);
+            const uint32_t r_o = __shfl_sync(kFull, r, o);
+            valid[u] = idx < total;
+            const uint32_t off = idx - ex_o;
+            jo[u] = jb + o;
+            pos[u] = off < cl_o ? nl_o + off : r_o + (off - cl_o);
           }
-          const unsigned pm = __ballot_sync(kFull, pass);
-          if (pass) w.cbuf[nb + __popc(pm & ((1u << lane) - 1u))] = id;
-          nb += __popc(pm);
-          if (lane == 0) ct.passed += __popc(pm);
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u)
+            id[u] = valid[u] ? __ldg(P.ids + size_t(jo[u]) * n + pos[u]) : 0u;
+          bool pass[kUnroll];
+          if (P.filter) {
+            uint64_t h[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+              const int m = jo[u] % P.M;
+              h[u] = valid[u] ? __ldg(P.sk + size_t(m) * n + id[u]) ^ qs[m] : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) pass[u] = valid[u] && __popcll(h[u]) <= tau;
+          } else {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) pass[u] = valid[u];
+          }
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            const unsigned pm = __ballot_sync(kFull, pass[u]);
+            if (pass[u]) w.cbuf[nb + __popc(pm & lt_mask)] = id[u];
+            nb += __popc(pm);
+            if (lane == 0) ct.passed += __popc(pm);
+          }
           __syncwarp();
-          if (nb > kCandBuf - 32) {
-            size = flush_candidates(P, w, nb, size, k, lane, ct);
+          if (nb > kFlushAt) {
+            size = flush_candidates<NT>(P, w, nb, size, k, lane, ct);
             nb = 0;
           }
         }
       }
-      if (nb) size = flush_candidates(P, w, nb, size, k, lane, ct);
+      if (nb) size = flush_candidates<NT>(P, w, nb, size, k, lane, ct);
       ++rounds;
       stop_depth = depth;
       int stop = 0;
@@ -442,8 +534,8 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(Dev P) {
     }
 
     for (int t = lane; t < kmax; t += 32) {
-      P.out_ids[int64_t(qi) * kmax + t] = t < size ? w.pq_id[t] : 0xffffffffu;
-      P.out_sims[int64_t(qi) * kmax + t] = t < size ? w.pq_s[t] : -INFINITY;
+      P.out_ids[size_t(qi) * kmax + t] = t < size ? w.pq_id[t] : 0xffffffffu;
+      P.out_sims[size_t(qi) * kmax + t] = t < size ? w.pq_s[t] : -INFINITY;
     }
     if (P.stats && lane == 0) {
       pf_query_stats st;
@@ -466,7 +558,7 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(Dev P) {
 cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t s) {
   if (a.Q <= 0) return cudaSuccess;
   Dev P;
-  P.n = ix->n;
+  P.n = int(ix->n);
   P.d = ix->d;
   P.d_pad = ix->lay.d_pad;
   P.L = ix->L;
@@ -500,16 +592,18 @@ cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t 
   P.counter = a.counter;
   const size_t per_warp = size_t(P.d_pad) * 4 + size_t(P.L) * 8 + size_t(P.k_max) * 8 + kCandBuf * 4;
   const size_t smem = ((per_warp + 15) & ~size_t(15)) * kWarps;
-  cudaError_t e = cudaFuncSetAttribute(search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  const int nt = (P.d_pad + 31) / 32;
+  auto kern = nt <= 1 ? search_kernel<1> : nt <= 2 ? search_kernel<2> : nt <= 4 ? search_kernel<4> : search_kernel<8>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel, kWarps * 32, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int blocks = ix->num_sms * per_sm;
   const int need = (a.Q + kWarps - 1) / kWarps;
   if (blocks > need) blocks = need;
-  search_kernel<<<blocks, kWarps * 32, smem, s>>>(P);
+  kern<<<blocks, kWarps * 32, smem, s>>>(P);
   return cudaGetLastError();
 }
 
