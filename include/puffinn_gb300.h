@@ -155,7 +155,7 @@ pf_status pf_index_search(pf_index* index, const float* queries, int64_t Q, cons
  *   - Scratch (normalised queries, query codes and sketches, work counter)
  *     lives in one 32 MiB file-scope device array that every GPU loading the
  *     library holds until the process exits.  A batch must satisfy
- *     Q*(4*d_pad + 4*L + 8*M) + 1024 <= 32 MiB; larger batches are rejected with
+ *     Q*(8*d_pad + 4*L + 8*M) + 1536 <= 32 MiB; larger batches are rejected with
  *     PF_ERR_INVALID_ARG and a message giving the limit (split the batch).
  *   - No cudaMalloc, cudaFree or other allocating call is made.
  *   - All calls share the array: calls whose device work overlaps (other

@@ -91,7 +91,8 @@ __global__ void split_bf16_kernel(const float* __restrict__ w, int64_t count, __
 void free_ws(pf_workspace& ws) {
   dfree(ws.qraw);
   dfree(ws.qx);
-  dfree(ws.qx16);
+  dfree(ws.qxh);
+  dfree(ws.qxl);
   dfree(ws.qcodes);
   dfree(ws.qsk);
   dfree(ws.k);
@@ -114,6 +115,8 @@ void ensure_ws(pf_index* ix, int64_t Q, int k_max) {
   const int dp = ix->lay.d_pad;
   dalloc(&ws.qraw, q * ix->d);
   dalloc(&ws.qx, q * dp);
+  dalloc(&ws.qxh, q * dp);
+  dalloc(&ws.qxl, q * dp);
   dalloc(&ws.qcodes, q * ix->L);
   dalloc(&ws.qsk, q * ix->M);
   dalloc(&ws.k, q);
@@ -144,6 +147,7 @@ void destroy(pf_index* ix) {
   dfree(ix->pfx);
   dfree(ix->cpP);
   dfree(ix->cos_tab);
+  dfree(ix->dev_error);
   free_ws(ix->ws);
   for (auto& e : ix->ev)
     if (e) cudaEventDestroy(e);
@@ -160,8 +164,8 @@ void stage_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
 // Hash and normalise Q queries (device pointer qsrc) into the workspace.
 void hash_queries_ws(pf_index* ix, const float* qdev, int64_t Q, cudaStream_t s) {
   pf_workspace& ws = ix->ws;
-  PF_CK(launch_normalize(qdev, Q, ix->d, ix->lay.d_pad, ws.qx, nullptr, s));
-  PF_CK(launch_hash(ix, ws.qx, Q, ws.qcodes, 1, ix->L, ws.qsk, 1, ix->M, s));
+  PF_CK(launch_normalize(qdev, Q, ix->d, ix->lay.d_pad, ws.qx, ws.qxh, ws.qxl, s));
+  PF_CK(launch_hash(ix, ws.qx, ws.qxh, ws.qxl, Q, ws.qcodes, 1, ix->L, ws.qsk, 1, ix->M, s));
 }
 
 const float* stage_queries(pf_index* ix, const float* queries, int64_t Q, cudaStream_t s) {
@@ -254,6 +258,8 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       dalloc(&ix->ids, size_t(n) * ix->L);
       dalloc(&ix->pfx, size_t(kPrefixSize) * ix->L);
       dalloc(&ix->cos_tab, 65);
+      dalloc(&ix->dev_error, 16);
+      PF_CK(cudaMemsetAsync(ix->dev_error, 0, 16 * sizeof(int32_t), s));
       if (ix->family == PF_CROSSPOLYTOPE) dalloc(&ix->cpP, size_t(kAlphaSteps) * (ix->lay.ell + 1));
 
       // random parameters on the host (bit-reproducible from the seed)
@@ -282,21 +288,28 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
         pin = staged;
       }
       uint32_t* raw_codes = nullptr;
+      __nv_bfloat16* xlo = nullptr;  // low bfloat16 half of the rows, only while hashing
+      int32_t herr = 0;
       try {
-        PF_CK(launch_normalize(pin, n, prm->d, dp, ix->x32, ix->x16, s));
+        dalloc(&xlo, size_t(n) * dp);
+        PF_CK(launch_normalize(pin, n, prm->d, dp, ix->x32, ix->x16, xlo, s));
         dalloc(&raw_codes, size_t(n) * ix->L);
-        PF_CK(launch_hash(ix, ix->x32, n, raw_codes, n, 1, ix->sk, n, 1, s));
+        PF_CK(launch_hash(ix, ix->x32, ix->x16, xlo, n, raw_codes, n, 1, ix->sk, n, 1, s));
         PF_CK(sort_tables(ix, raw_codes, s));
+        PF_CK(cudaMemcpyAsync(&herr, ix->dev_error, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PF_CK(cudaStreamSynchronize(s));
       } catch (...) {
         cudaStreamSynchronize(s);
         dfree(staged);
         dfree(raw_codes);
+        dfree(xlo);
         throw;
       }
       dfree(staged);
       dfree(raw_codes);
+      dfree(xlo);
       PF_CK(cudaGetLastError());
+      if (herr) throw Error{PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait of the hashing kernel timed out"};
     } catch (...) {
       destroy(ix);
       throw;
@@ -392,6 +405,9 @@ pf_status pf_index_search(pf_index* ix, const float* queries, int64_t Q, const i
     PF_CK(cudaMemcpyAsync(&flags, ws.counter + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     PF_CK(cudaStreamSynchronize(s));
     PF_CK(cudaGetLastError());
+    int32_t herr = 0;
+    PF_CK(cudaMemcpy(&herr, ix->dev_error, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (herr) return fail(PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out");
     if (flags & 1) return fail(PF_ERR_INVALID_ARG, "some k not in [1, k_max] or recall not in (0, 1)");
     if (timing) {
       PF_CK(cudaEventElapsedTime(&ix->last_ms[0], ix->ev[0], ix->ev[1]));

@@ -12,6 +12,7 @@
 // the parts that must start at zero are cleared by each call.  Two calls whose
 // device work overlaps (different streams, or different host threads) race on
 // the array: serialise them.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -33,8 +34,8 @@ unsigned char* g_scratch_addr[kMaxDevices] = {};
 size_t round_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 size_t scratch_bytes(const pf_index* ix, int64_t Q) {
-  return round_up(size_t(Q) * ix->lay.d_pad * sizeof(float)) + round_up(size_t(Q) * ix->L * sizeof(uint32_t)) +
-         round_up(size_t(Q) * ix->M * sizeof(uint64_t)) + kAlign;
+  return round_up(size_t(Q) * ix->lay.d_pad * sizeof(float)) + 2 * round_up(size_t(Q) * ix->lay.d_pad * 2) +
+         round_up(size_t(Q) * ix->L * sizeof(uint32_t)) + round_up(size_t(Q) * ix->M * sizeof(uint64_t)) + kAlign;
 }
 
 bool device_pointer(const void* p) {
@@ -88,10 +89,10 @@ extern "C" pf_status pf_index_search_noalloc(pf_index* ix, const float* queries,
     if (o.learned_start) return reject(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
     const size_t need = scratch_bytes(ix, Q);
     if (need > kScratchBytes) {
-      const size_t per_q = size_t(ix->lay.d_pad) * 4 + size_t(ix->L) * 4 + size_t(ix->M) * 8;
+      const size_t per_q = size_t(ix->lay.d_pad) * 8 + size_t(ix->L) * 4 + size_t(ix->M) * 8;
       return reject(PF_ERR_INVALID_ARG,
                     "batch too large for the fixed 32 MiB search scratch: this index allows about " +
-                        std::to_string((kScratchBytes - 4 * kAlign) / per_q) + " queries per call, got " +
+                        std::to_string((kScratchBytes - 6 * kAlign) / per_q) + " queries per call, got " +
                         std::to_string(Q));
     }
     cudaError_t e = cudaSetDevice(ix->device);
@@ -108,6 +109,10 @@ extern "C" pf_status pf_index_search_noalloc(pf_index* ix, const float* queries,
     if ((e = scratch_address(ix->device, &base)) != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
     float* qx = reinterpret_cast<float*>(base);
     base += round_up(size_t(Q) * ix->lay.d_pad * sizeof(float));
+    __nv_bfloat16* qxh = reinterpret_cast<__nv_bfloat16*>(base);
+    base += round_up(size_t(Q) * ix->lay.d_pad * 2);
+    __nv_bfloat16* qxl = reinterpret_cast<__nv_bfloat16*>(base);
+    base += round_up(size_t(Q) * ix->lay.d_pad * 2);
     uint32_t* qcodes = reinterpret_cast<uint32_t*>(base);
     base += round_up(size_t(Q) * ix->L * sizeof(uint32_t));
     uint64_t* qsk = reinterpret_cast<uint64_t*>(base);
@@ -116,9 +121,9 @@ extern "C" pf_status pf_index_search_noalloc(pf_index* ix, const float* queries,
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if ((e = cudaMemsetAsync(counter, 0, kAlign, s)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    if ((e = pf::launch_normalize(queries, Q, ix->d, ix->lay.d_pad, qx, nullptr, s)) != cudaSuccess)
+    if ((e = pf::launch_normalize(queries, Q, ix->d, ix->lay.d_pad, qx, qxh, qxl, s)) != cudaSuccess)
       return cuda_fail(e, "normalize");
-    if ((e = pf::launch_hash(ix, qx, Q, qcodes, 1, ix->L, qsk, 1, ix->M, s)) != cudaSuccess)
+    if ((e = pf::launch_hash(ix, qx, qxh, qxl, Q, qcodes, 1, ix->L, qsk, 1, ix->M, s)) != cudaSuccess)
       return cuda_fail(e, "hash");
     pf::SearchArgs a;
     a.Q = int(Q);
@@ -140,6 +145,10 @@ extern "C" pf_status pf_index_search_noalloc(pf_index* ix, const float* queries,
     if ((e = cudaMemcpyAsync(&flags, counter + 1, sizeof(flags), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpyAsync");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int32_t herr = 0;
+    if ((e = cudaMemcpy(&herr, ix->dev_error, sizeof(herr), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpy");
+    if (herr) return reject(PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out");
     if (flags & 1) return reject(PF_ERR_INVALID_ARG, "some k not in [1, k_max] or recall not in (0, 1)");
     return PF_OK;
   } catch (...) {

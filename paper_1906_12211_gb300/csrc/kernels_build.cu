@@ -16,7 +16,8 @@ namespace pf {
 // padding columns are zero; a zero row stays zero.
 // ---------------------------------------------------------------------------
 __global__ void normalize_kernel(const float* __restrict__ in, int64_t rows, int d, int d_pad,
-                                 float* __restrict__ x32, __nv_bfloat16* __restrict__ x16) {
+                                 float* __restrict__ x32, __nv_bfloat16* __restrict__ xh,
+                                 __nv_bfloat16* __restrict__ xl) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   const float* row = in + r * d;
@@ -30,15 +31,19 @@ __global__ void normalize_kernel(const float* __restrict__ in, int64_t rows, int
   for (int i = 0; i < d_pad; ++i) {
     const float y = (i < d && nrm > 0.0) ? __double2float_rn(__ddiv_rn(double(row[i]), nrm)) : 0.0f;
     o[i] = y;
-    if (x16) x16[r * d_pad + i] = __float2bfloat16_rn(y);
+    if (xh) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(y);
+      xh[r * d_pad + i] = h;
+      if (xl) xl[r * d_pad + i] = __float2bfloat16_rn(y - __bfloat162float(h));
+    }
   }
 }
 
-cudaError_t launch_normalize(const float* in, int64_t rows, int d, int d_pad, float* x32, __nv_bfloat16* x16,
-                             cudaStream_t s) {
+cudaError_t launch_normalize(const float* in, int64_t rows, int d, int d_pad, float* x32, __nv_bfloat16* xh,
+                             __nv_bfloat16* xl, cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
   const int tb = 128;
-  normalize_kernel<<<unsigned((rows + tb - 1) / tb), tb, 0, s>>>(in, rows, d, d_pad, x32, x16);
+  normalize_kernel<<<unsigned((rows + tb - 1) / tb), tb, 0, s>>>(in, rows, d, d_pad, x32, xh, xl);
   return cudaGetLastError();
 }
 
@@ -198,9 +203,12 @@ __global__ void __launch_bounds__(kHashPts) hash_simt_kernel(
   }
 }
 
-cudaError_t launch_hash(const pf_index* ix, const float* x32, int64_t npts, uint32_t* codes, int64_t cj,
-                        int64_t cp, uint64_t* sk, int64_t sm, int64_t sp, cudaStream_t s) {
+cudaError_t launch_hash(const pf_index* ix, const float* x32, const __nv_bfloat16* xh, const __nv_bfloat16* xl,
+                        int64_t npts, uint32_t* codes, int64_t cj, int64_t cp, uint64_t* sk, int64_t sm,
+                        int64_t sp, cudaStream_t s) {
   if (npts <= 0) return cudaSuccess;
+  if (hash_tc_supported(ix) && xh && xl)
+    return launch_hash_tc(ix, xh, xl, x32, npts, codes, cj, cp, sk, sm, sp, ix->dev_error, s);
   const Layout& lay = ix->lay;
   const size_t smem = sizeof(float) * (size_t(lay.d_pad) * kHashPts + size_t(kHashChunk) * lay.d_pad);
   cudaError_t e = cudaFuncSetAttribute(hash_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));

@@ -1,0 +1,508 @@
+// Hashing on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// The projections of a block of 128 points onto all hash rows are the dense
+// contraction V = X W^T (K = d_pad).  Each product is evaluated as three
+// bfloat16 products with float32 accumulation in tensor memory,
+//   X W^T ~= Xh Wh^T + Xh Wl^T + Xl Wh^T,   X = Xh + Xl, W = Wh + Wl,
+// whose error is below 3*2^-16*|x||w| for the split plus the accumulation
+// error (< K' * 2^-23 * |x||w|, K' = 3*d_pad <= 384), i.e. < 1.0e-4 |w| for
+// unit x.  The epilogue decides every hash bit with the rule of the SIMT
+// kernel using a band of 2^-11 |w| (= 2 * the stored 2^-12 |w|): a decision
+// closer to its boundary than the band is recomputed in float64 in index order,
+// which is the defining value (Sec. 2.2: HP bit = [<a,x> >= 0]; CP value =
+// sign and index of the largest |<a_c,x>|), so codes are bit-identical to the
+// float64 definition.
+//
+// Kernel structure (one CTA of 128 threads per SM, persistent):
+//   - work item = (128-point tile, range of hash-row segments); a segment is
+//     one repetition (CP: fns tiles of d_pad rows; HP: a group of 4
+//     repetitions = 128 rows) or a group of 2 sketches (128 rows);
+//   - the A tile (Xh, Xl of the 128 points) stays in shared memory for the
+//     item; B tiles (Wh, Wl of one N tile) are double-buffered with cp.async;
+//     both use the 128-byte-swizzled K-major layout (8-row groups 1024 B apart,
+//     16-byte chunk c of row r stored at chunk c ^ (r mod 8));
+//   - thread 0 issues 3 * KB * 4 MMAs (M = 128, N = tile rows, K = 16) into
+//     one of two 128-column accumulators in tensor memory and commits them to
+//     an mbarrier; meanwhile all 4 warps load the next B tile and run the
+//     epilogue of the previous tile (tcgen05.ld, one thread per point);
+//   - every mbarrier wait is bounded: on time-out the kernel records an error
+//     word, drains its own copies, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "pf_internal.h"
+
+namespace pf {
+
+namespace {
+
+constexpr int kBM = 128;          // points per tile (MMA M)
+constexpr int kThreads = 128;
+constexpr int kTileBytes = kBM * 128;  // one 64-element K block of 128 rows
+constexpr int kTmemCols = 256;    // two accumulators of 128 columns
+constexpr uint32_t kWaitLimit = 1u << 26;
+
+struct HashArgs {
+  const __nv_bfloat16* xh;
+  const __nv_bfloat16* xl;
+  const float* x32;
+  int64_t npts;
+  const __nv_bfloat16* wh;
+  const __nv_bfloat16* wl;
+  const float* w32;
+  const float* thr;
+  int64_t hash_rows;
+  int d, d_pad, KB, family, L, M, fns, ell, rows_table;
+  int seg_tables;  // segments that are repetitions (CP) or groups of 4 repetitions (HP)
+  int segs;        // + sketch groups of 2
+  int split;       // segment ranges per point tile
+  int items;       // point tiles * split
+  uint32_t* codes;
+  int64_t cj, cp;
+  uint64_t* sk;
+  int64_t sm, sp;
+  int32_t* error;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait for the phase with the given parity; false on time-out
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, bf16 inputs, f32 accumulate
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+               : "memory");
+}
+
+// 16 consecutive 32-bit columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// shared-memory descriptor of a K-major, 128-byte-swizzled tile
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= uint64_t(1) << 16;                  // leading byte offset (unused for swizzled K-major)
+  d |= uint64_t(1024 >> 4) << 32;          // stride byte offset: 8-row groups are 1024 B apart
+  d |= uint64_t(1) << 46;                  // descriptor version of tcgen05
+  d |= uint64_t(2) << 61;                  // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: bf16 x bf16 -> f32, both operands K-major
+__device__ __forceinline__ uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(m >> 4) << 24);
+}
+
+__device__ __forceinline__ double dot64(const float* __restrict__ a, const float* __restrict__ x, int d) {
+  double s = 0.0;
+  for (int i = 0; i < d; ++i) s = __dadd_rn(s, __dmul_rn(double(a[i]), double(x[i])));
+  return s;
+}
+
+// Issue cp.async copies of `rows` rows (bf16, row length d_pad) starting at row
+// `row0` of src into a swizzled tile; rows >= limit and columns >= d_pad read 0.
+__device__ __forceinline__ void load_tile(uint32_t dst, const __nv_bfloat16* __restrict__ src, int64_t row0,
+                                          int rows, int64_t limit, int d_pad, int KB) {
+  const int chunks = KB * 8;  // 16-byte chunks per row
+  for (int e = threadIdx.x; e < rows * chunks; e += kThreads) {
+    const int r = e / chunks, c = e % chunks;
+    const int kb = c >> 3, cc = c & 7;
+    const int64_t row = row0 + r;
+    const int col = c * 8;
+    const bool ok = row < limit && col < d_pad;
+    const void* g = ok ? static_cast<const void*>(src + row * d_pad + col) : static_cast<const void*>(src);
+    const uint32_t off = uint32_t(kb * kTileBytes + r * 128 + ((cc ^ (r & 7)) << 4));
+    cp_async16(dst + off, g, ok ? 16u : 0u);
+  }
+}
+
+struct Tile {
+  int seg;      // segment index
+  int first;    // first tile of its segment
+  int last;     // last tile of its segment
+  int fn;       // CP function index within the repetition
+  int64_t row0; // first hash row
+  int rows;     // N
+};
+
+__device__ __forceinline__ Tile tile_of(const HashArgs& A, int seg, int f) {
+  Tile t;
+  t.seg = seg;
+  t.fn = f;
+  if (seg < A.seg_tables) {
+    if (A.family == PF_CROSSPOLYTOPE) {
+      t.row0 = (int64_t(seg) * A.fns + f) * A.d_pad;
+      t.rows = A.d_pad;
+      t.first = f == 0;
+      t.last = f == A.fns - 1;
+    } else {
+      t.row0 = int64_t(seg) * 128;
+      t.rows = 128;
+      t.first = t.last = 1;
+    }
+  } else {
+    t.row0 = int64_t(A.L) * A.rows_table + int64_t(seg - A.seg_tables) * 128;
+    t.rows = 128;
+    t.first = t.last = 1;
+  }
+  return t;
+}
+
+__device__ __forceinline__ int tiles_in_seg(const HashArgs& A, int seg) {
+  return (seg < A.seg_tables && A.family == PF_CROSSPOLYTOPE) ? A.fns : 1;
+}
+
+struct EpiState {
+  uint32_t code;
+};
+
+// Epilogue of one N tile for the thread's point p (accumulator columns at taddr).
+__device__ void epilogue(const HashArgs& A, const Tile& t, uint32_t taddr, int64_t p, EpiState& st) {
+  const bool live = p < A.npts;
+  const float* xrow = A.x32 + (live ? p : 0) * A.d_pad;
+  if (t.seg < A.seg_tables && A.family == PF_CROSSPOLYTOPE) {
+    if (t.first) st.code = 0;
+    float a[4] = {-1.f, -1.f, -1.f, -1.f};
+    int c4[4] = {0, 0, 0, 0};
+    float best_v = 0.f;
+    for (int c0 = 0; c0 < t.rows; c0 += 16) {
+      float v[16];
+      tmem_ld16(taddr + uint32_t(c0), v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int c = c0 + i;
+        if (c < A.d) {
+          const float av = fabsf(v[i]);
+          if (av > a[3]) {
+            if (av > a[0]) best_v = v[i];
+            int pos = 3;
+            while (pos > 0 && av > a[pos - 1]) {
+              a[pos] = a[pos - 1];
+              c4[pos] = c4[pos - 1];
+              --pos;
+            }
+            a[pos] = av;
+            c4[pos] = c;
+          }
+        }
+      }
+    }
+    const float band = 2.f * A.thr[t.row0];
+    int arg = c4[0];
+    bool neg = best_v < 0.f;
+    if (live && (a[1] >= a[0] - 2.f * band || a[0] < band)) {
+      const float* wf = A.w32 + t.row0 * A.d_pad;
+      double bestabs = -1.0, bestval = 0.0;
+      int besti = 0;
+      if (a[3] >= a[0] - 2.f * band) {
+        for (int cc = 0; cc < A.d; ++cc) {
+          const double v64 = dot64(wf + int64_t(cc) * A.d_pad, xrow, A.d);
+          if (fabs(v64) > bestabs) {
+            bestabs = fabs(v64);
+            bestval = v64;
+            besti = cc;
+          }
+        }
+      } else {
+        for (int q = 0; q < 4; ++q) {
+          if (a[q] < a[0] - 2.f * band) continue;
+          const int cc = c4[q];
+          const double v64 = dot64(wf + int64_t(cc) * A.d_pad, xrow, A.d);
+          const double av = fabs(v64);
+          if (av > bestabs || (av == bestabs && cc < besti)) {
+            bestabs = av;
+            bestval = v64;
+            besti = cc;
+          }
+        }
+      }
+      arg = besti;
+      neg = bestval < 0.0;
+    }
+    const uint32_t value = ((neg ? 1u : 0u) << (A.ell - 1)) | uint32_t(arg);
+    st.code |= value << (32 - A.ell * (t.fn + 1));
+    if (t.last && live) A.codes[int64_t(t.seg) * A.cj + p * A.cp] = st.code;
+    return;
+  }
+  // 128 one-bit rows: 4 HP repetitions (32 bits each) or 2 sketches (64 bits each)
+  const bool is_sketch = t.seg >= A.seg_tables;
+  uint64_t bits[2] = {0ull, 0ull};
+  for (int c0 = 0; c0 < 128; c0 += 16) {
+    float v[16];
+    tmem_ld16(taddr + uint32_t(c0), v);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int c = c0 + i;
+      const int64_t row = t.row0 + c;
+      bool bit = v[i] >= 0.f;
+      if (row < A.hash_rows && live && fabsf(v[i]) < 2.f * A.thr[row])
+        bit = dot64(A.w32 + row * A.d_pad, xrow, A.d) >= 0.0;
+      if (bit) bits[c >> 6] |= uint64_t(1) << (c & 63);
+    }
+  }
+  if (!live) return;
+  if (is_sketch) {
+    for (int s = 0; s < 2; ++s) {
+      const int m = (t.seg - A.seg_tables) * 2 + s;
+      if (m < A.M) A.sk[int64_t(m) * A.sm + p * A.sp] = bits[s];
+    }
+  } else {
+    for (int s = 0; s < 4; ++s) {
+      const int j = t.seg * 4 + s;
+      if (j >= A.L) break;
+      const uint32_t w = uint32_t(bits[s >> 1] >> ((s & 1) * 32));
+      // column c of repetition j is function c: the first function is the top bit
+      A.codes[int64_t(j) * A.cj + p * A.cp] = __brev(w);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned base for the swizzled tiles
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int KB = A.KB;
+  const uint32_t sA = smem_u32(base);                       // [2 splits][KB] tiles
+  const uint32_t sB = sA + uint32_t(2 * KB * kTileBytes);   // [2 stages][2 splits][KB] tiles
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t tmem_base_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  if (warp == 0) {
+    tmem_alloc(smem_u32(&tmem_base_slot), kTmemCols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(smem_u32(&bars[0]), 1);
+    mbar_init(smem_u32(&bars[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_slot;
+  uint32_t phase[2] = {0u, 0u};
+  bool failed = false;
+
+  const int seg_per = (A.segs + A.split - 1) / A.split;
+  for (int item = blockIdx.x; item < A.items && !failed; item += gridDim.x) {
+    const int mt = item / A.split, part = item % A.split;
+    const int seg0 = part * seg_per, seg1 = min(A.segs, seg0 + seg_per);
+    if (seg0 >= seg1) continue;
+    const int64_t p0 = int64_t(mt) * kBM;
+    const int64_t p = p0 + tid;
+
+    // A tile (both splits) and the first B tile
+    load_tile(sA, A.xh, p0, kBM, A.npts, A.d_pad, KB);
+    load_tile(sA + uint32_t(KB * kTileBytes), A.xl, p0, kBM, A.npts, A.d_pad, KB);
+    Tile cur = tile_of(A, seg0, 0);
+    load_tile(sB, A.wh, cur.row0, cur.rows, A.hash_rows, A.d_pad, KB);
+    load_tile(sB + uint32_t(KB * kTileBytes), A.wl, cur.row0, cur.rows, A.hash_rows, A.d_pad, KB);
+    cp_async_commit();
+
+    EpiState st;
+    st.code = 0;
+    Tile prev = cur;
+    int seg = seg0, f = 0;
+    int t = 0;
+    for (;; ++t) {
+      const int buf = t & 1;
+      // tile t resident in stage buf: make it visible to the tensor cores
+      cp_async_wait_all();
+      fence_proxy_async();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t idesc = idesc_bf16(kBM, cur.rows);
+        const uint32_t d_tmem = tmem + uint32_t(buf * 128);
+        const uint32_t bstage = sB + uint32_t(buf * 2 * KB * kTileBytes);
+        int acc = 0;
+        // (Xh, Wh), (Xh, Wl), (Xl, Wh)
+        for (int split = 0; split < 3; ++split) {
+          const uint32_t a_t = sA + uint32_t((split == 2 ? KB : 0) * kTileBytes);
+          const uint32_t b_t = bstage + uint32_t((split == 1 ? KB : 0) * kTileBytes);
+          for (int kb = 0; kb < KB; ++kb)
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t off = uint32_t(kb * kTileBytes + kk * 32);
+              mma_bf16(d_tmem, sw128_desc(a_t + off), sw128_desc(b_t + off), idesc, acc);
+              acc = 1;
+            }
+        }
+        mma_commit(smem_u32(&bars[buf]));
+      }
+      // next tile of this item, if any
+      int nseg = seg, nf = f + 1;
+      if (nf >= tiles_in_seg(A, nseg)) {
+        nseg += 1;
+        nf = 0;
+      }
+      const bool has_next = nseg < seg1;
+      if (t >= 1) {
+        // the previous tile's MMAs are done: its stage and accumulator are free
+        if (!mbar_wait(smem_u32(&bars[buf ^ 1]), phase[buf ^ 1])) failed = true;
+        phase[buf ^ 1] ^= 1u;
+        tc_fence_after();
+      }
+      Tile nxt = cur;
+      if (has_next && !failed) {
+        nxt = tile_of(A, nseg, nf);
+        const uint32_t bstage = sB + uint32_t((buf ^ 1) * 2 * KB * kTileBytes);
+        load_tile(bstage, A.wh, nxt.row0, nxt.rows, A.hash_rows, A.d_pad, KB);
+        load_tile(bstage + uint32_t(KB * kTileBytes), A.wl, nxt.row0, nxt.rows, A.hash_rows, A.d_pad, KB);
+      }
+      cp_async_commit();
+      if (t >= 1 && !failed)
+        epilogue(A, prev, tmem + (uint32_t(warp * 32) << 16) + uint32_t((buf ^ 1) * 128), p, st);
+      tc_fence_before();
+      __syncthreads();
+      if (failed) break;
+      prev = cur;
+      if (!has_next) break;
+      cur = nxt;
+      seg = nseg;
+      f = nf;
+    }
+    if (failed) break;
+    // epilogue of the item's last tile
+    const int lb = t & 1;
+    if (!mbar_wait(smem_u32(&bars[lb]), phase[lb])) {
+      failed = true;
+      break;
+    }
+    phase[lb] ^= 1u;
+    tc_fence_after();
+    epilogue(A, prev, tmem + (uint32_t(warp * 32) << 16) + uint32_t(lb * 128), p, st);
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (failed && tid == 0) atomicOr(A.error, 2);
+  cp_async_wait_all();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+}  // namespace
+
+bool hash_tc_supported(const pf_index* ix) { return ix->lay.d_pad <= 128; }
+
+size_t hash_tc_smem(int d_pad) {
+  const int KB = (d_pad + 63) / 64;
+  return size_t(2 * KB + 4 * KB) * kTileBytes + 1024;
+}
+
+cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __nv_bfloat16* xl, const float* x32,
+                           int64_t npts, uint32_t* codes, int64_t cj, int64_t cp, uint64_t* sk, int64_t sm,
+                           int64_t sp, int32_t* error, cudaStream_t s) {
+  if (npts <= 0) return cudaSuccess;
+  HashArgs A;
+  A.xh = xh;
+  A.xl = xl;
+  A.x32 = x32;
+  A.npts = npts;
+  A.wh = ix->Whi;
+  A.wl = ix->Wlo;
+  A.w32 = ix->W32;
+  A.thr = ix->Wthr;
+  A.hash_rows = ix->hash_rows;
+  A.d = ix->d;
+  A.d_pad = ix->lay.d_pad;
+  A.KB = (A.d_pad + 63) / 64;
+  A.family = ix->family;
+  A.L = ix->L;
+  A.M = ix->M;
+  A.fns = ix->lay.fns;
+  A.ell = ix->lay.ell;
+  A.rows_table = ix->lay.rows_table;
+  A.seg_tables = ix->family == PF_CROSSPOLYTOPE ? ix->L : (ix->L + 3) / 4;
+  A.segs = A.seg_tables + (ix->M + 1) / 2;
+  const int mtiles = int((npts + kBM - 1) / kBM);
+  A.split = std::max(1, std::min(A.segs, (2 * ix->num_sms + mtiles - 1) / mtiles));
+  A.items = mtiles * A.split;
+  A.codes = codes;
+  A.cj = cj;
+  A.cp = cp;
+  A.sk = sk;
+  A.sm = sm;
+  A.sp = sp;
+  A.error = error;
+  const size_t smem = hash_tc_smem(A.d_pad);
+  cudaError_t e = cudaFuncSetAttribute(hash_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(A.items, ix->num_sms);
+  hash_tc_kernel<<<grid, kThreads, smem, s>>>(A);
+  return cudaGetLastError();
+}
+
+}  // namespace pf

@@ -54,7 +54,8 @@ struct pf_workspace {
   size_t cap_q = 0;  // queries the buffers hold
   float* qraw = nullptr;       // [Q][d] staged host queries
   float* qx = nullptr;         // [Q][d_pad] normalised queries
-  __nv_bfloat16* qx16 = nullptr;
+  __nv_bfloat16* qxh = nullptr;  // [Q][d_pad] bfloat16 high half of qx
+  __nv_bfloat16* qxl = nullptr;  // [Q][d_pad] bfloat16 low half (qx - qxh)
   uint32_t* qcodes = nullptr;  // [Q][L]
   uint64_t* qsk = nullptr;     // [Q][M]
   int32_t* k = nullptr;
@@ -88,6 +89,7 @@ struct pf_index {
   double* cpP = nullptr;           // [41][ell+1]
   double* cos_tab = nullptr;       // [65]
   float bf16_err = 0.f;            // bound on |bf16 estimate - float32 canonical similarity|
+  int32_t* dev_error = nullptr;    // device error word (bit 1: a bounded wait timed out)
   int num_sms = 0;
   pf_workspace ws;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // phase timing events
@@ -97,14 +99,21 @@ struct pf_index {
 // ---------------------------------------------------------------- launchers
 namespace pf {
 
-// normalise rows (Sec. 4.2) -> x32 [rows][d_pad] (+ optional bf16 copy)
-cudaError_t launch_normalize(const float* in, int64_t rows, int d, int d_pad, float* x32, __nv_bfloat16* x16,
-                             cudaStream_t s);
+// normalise rows (Sec. 4.2) -> x32 [rows][d_pad], and optionally its bfloat16
+// split x32 = xh + xl (xh is the round-to-nearest bfloat16 copy)
+cudaError_t launch_normalize(const float* in, int64_t rows, int d, int d_pad, float* x32, __nv_bfloat16* xh,
+                             __nv_bfloat16* xl, cudaStream_t s);
 
-// Hash rows x32 [npts][d_pad] under all L repetitions and M sketches.
-// codes written at codes[j*cj + p*cp], sketches at sk[m*sm + p*sp].
-cudaError_t launch_hash(const pf_index* ix, const float* x32, int64_t npts, uint32_t* codes, int64_t cj,
-                        int64_t cp, uint64_t* sk, int64_t sm, int64_t sp, cudaStream_t s);
+// Hash rows x32 [npts][d_pad] (with its bfloat16 split xh + xl) under all L
+// repetitions and M sketches.  Codes written at codes[j*cj + p*cp], sketches
+// at sk[m*sm + p*sp].  Uses the tensor-core kernel when d_pad <= 128.
+cudaError_t launch_hash(const pf_index* ix, const float* x32, const __nv_bfloat16* xh, const __nv_bfloat16* xl,
+                        int64_t npts, uint32_t* codes, int64_t cj, int64_t cp, uint64_t* sk, int64_t sm,
+                        int64_t sp, cudaStream_t s);
+bool hash_tc_supported(const pf_index* ix);
+cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __nv_bfloat16* xl, const float* x32,
+                           int64_t npts, uint32_t* codes, int64_t cj, int64_t cp, uint64_t* sk, int64_t sm,
+                           int64_t sp, int32_t* error, cudaStream_t s);
 
 // Sort every repetition's (code, position) pairs and build the prefix tables.
 cudaError_t sort_tables(pf_index* ix, uint32_t* codes_unsorted, cudaStream_t s);

@@ -83,7 +83,23 @@ def cpodd(orc):
     return Case(orc, "gauss-n1500-d37", X, Q, "crosspolytope", L=16, seed=9)
 
 
-CASES = ["cfg1", "cpmid", "cpodd"]
+@pytest.fixture(scope="module")
+def cpwide(orc):
+    # d = 150 (d_pad 160 > 128: the float32 SIMT hashing kernel), CP with l = 9
+    X = datagen.vmf_mixture(3000, 150, 20, 40.0, seed=5)
+    Q = datagen.vmf_mixture(40, 150, 20, 40.0, seed=5, purpose="queries")
+    return Case(orc, "vmf-n3000-d150", X, Q, "crosspolytope", L=12, seed=4)
+
+
+@pytest.fixture(scope="module")
+def hpodd(orc):
+    # SimHash with L = 7 (not a multiple of the 4-repetition hashing groups), d = 20
+    X = datagen.gaussian(2500, 20, seed=6)
+    Q = datagen.gaussian(50, 20, seed=6, purpose="queries")
+    return Case(orc, "gauss-n2500-d20", X, Q, "simhash", L=7, seed=2)
+
+
+CASES = ["cfg1", "cpmid", "cpodd", "cpwide", "hpodd"]
 
 
 @pytest.fixture
