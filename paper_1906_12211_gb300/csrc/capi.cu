@@ -102,6 +102,8 @@ void free_ws(pf_workspace& ws) {
   dfree(ws.sims);
   dfree(ws.stats);
   dfree(ws.counter);
+  dfree(ws.rq);
+  dfree(ws.rq_count);
   ws.cap_q = 0;
   ws.cap_kmax = 0;
 }
@@ -126,6 +128,8 @@ void ensure_ws(pf_index* ix, int64_t Q, int k_max) {
   dalloc(&ws.sims, q * km);
   dalloc(&ws.stats, q);
   dalloc(&ws.counter, 64);
+  dalloc(&ws.rq, recheck_capacity(int64_t(q)));
+  dalloc(&ws.rq_count, 1);
   ws.cap_q = q;
   ws.cap_kmax = km;
 }
@@ -165,7 +169,8 @@ void stage_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
 void hash_queries_ws(pf_index* ix, const float* qdev, int64_t Q, cudaStream_t s) {
   pf_workspace& ws = ix->ws;
   PF_CK(launch_normalize(qdev, Q, ix->d, ix->lay.d_pad, ws.qx, ws.qxh, ws.qxl, s));
-  PF_CK(launch_hash(ix, ws.qx, ws.qxh, ws.qxl, Q, ws.qcodes, 1, ix->L, ws.qsk, 1, ix->M, s));
+  PF_CK(launch_hash(ix, ws.qx, ws.qxh, ws.qxl, Q, ws.qcodes, 1, ix->L, ws.qsk, 1, ix->M, ws.rq, ws.rq_count,
+                    recheck_capacity(Q), s));
 }
 
 const float* stage_queries(pf_index* ix, const float* queries, int64_t Q, cudaStream_t s) {
@@ -289,12 +294,17 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       }
       uint32_t* raw_codes = nullptr;
       __nv_bfloat16* xlo = nullptr;  // low bfloat16 half of the rows, only while hashing
+      RecheckReq* rq = nullptr;      // deferred float64 rechecks, only while hashing
+      uint32_t* rq_count = nullptr;
       int32_t herr = 0;
       try {
         dalloc(&xlo, size_t(n) * dp);
         PF_CK(launch_normalize(pin, n, prm->d, dp, ix->x32, ix->x16, xlo, s));
         dalloc(&raw_codes, size_t(n) * ix->L);
-        PF_CK(launch_hash(ix, ix->x32, ix->x16, xlo, n, raw_codes, n, 1, ix->sk, n, 1, s));
+        dalloc(&rq, recheck_capacity(n));
+        dalloc(&rq_count, 1);
+        PF_CK(launch_hash(ix, ix->x32, ix->x16, xlo, n, raw_codes, n, 1, ix->sk, n, 1, rq, rq_count,
+                          recheck_capacity(n), s));
         PF_CK(sort_tables(ix, raw_codes, s));
         PF_CK(cudaMemcpyAsync(&herr, ix->dev_error, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PF_CK(cudaStreamSynchronize(s));
@@ -303,11 +313,15 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
         dfree(staged);
         dfree(raw_codes);
         dfree(xlo);
+        dfree(rq);
+        dfree(rq_count);
         throw;
       }
       dfree(staged);
       dfree(raw_codes);
       dfree(xlo);
+      dfree(rq);
+      dfree(rq_count);
       PF_CK(cudaGetLastError());
       if (herr) throw Error{PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait of the hashing kernel timed out"};
     } catch (...) {

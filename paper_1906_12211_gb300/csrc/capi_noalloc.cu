@@ -123,7 +123,9 @@ extern "C" pf_status pf_index_search_noalloc(pf_index* ix, const float* queries,
     if ((e = cudaMemsetAsync(counter, 0, kAlign, s)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     if ((e = pf::launch_normalize(queries, Q, ix->d, ix->lay.d_pad, qx, qxh, qxl, s)) != cudaSuccess)
       return cuda_fail(e, "normalize");
-    if ((e = pf::launch_hash(ix, qx, qxh, qxl, Q, qcodes, 1, ix->L, qsk, 1, ix->M, s)) != cudaSuccess)
+    // no deferred-recheck queue here: near-boundary hash decisions are rechecked inline
+    if ((e = pf::launch_hash(ix, qx, qxh, qxl, Q, qcodes, 1, ix->L, qsk, 1, ix->M, nullptr, nullptr, 0, s)) !=
+        cudaSuccess)
       return cuda_fail(e, "hash");
     pf::SearchArgs a;
     a.Q = int(Q);

@@ -69,26 +69,42 @@ __device__ __forceinline__ double dot64(const float* __restrict__ a, const float
   return s;
 }
 
+// the four largest |v| (a[0] >= ... >= a[3]) and their rows, in registers
 struct Top4 {
   float a[4];
   int c[4];
-  __device__ void reset() {
+  __device__ __forceinline__ void reset() {
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       a[t] = -1.f;
       c[t] = 0;
     }
   }
-  __device__ void push(float v, int cc) {
-    if (v <= a[3]) return;
-    int pos = 3;
-    while (pos > 0 && v > a[pos - 1]) {
-      a[pos] = a[pos - 1];
-      c[pos] = c[pos - 1];
-      --pos;
+  __device__ __forceinline__ void push(float v, int cc) {
+    if (!(v > a[3])) return;
+    if (v > a[2]) {
+      a[3] = a[2];
+      c[3] = c[2];
+      if (v > a[1]) {
+        a[2] = a[1];
+        c[2] = c[1];
+        if (v > a[0]) {
+          a[1] = a[0];
+          c[1] = c[0];
+          a[0] = v;
+          c[0] = cc;
+        } else {
+          a[1] = v;
+          c[1] = cc;
+        }
+      } else {
+        a[2] = v;
+        c[2] = cc;
+      }
+    } else {
+      a[3] = v;
+      c[3] = cc;
     }
-    a[pos] = v;
-    c[pos] = cc;
   }
 };
 
@@ -205,10 +221,10 @@ __global__ void __launch_bounds__(kHashPts) hash_simt_kernel(
 
 cudaError_t launch_hash(const pf_index* ix, const float* x32, const __nv_bfloat16* xh, const __nv_bfloat16* xl,
                         int64_t npts, uint32_t* codes, int64_t cj, int64_t cp, uint64_t* sk, int64_t sm,
-                        int64_t sp, cudaStream_t s) {
+                        int64_t sp, RecheckReq* rq, uint32_t* rq_count, uint32_t rq_cap, cudaStream_t s) {
   if (npts <= 0) return cudaSuccess;
   if (hash_tc_supported(ix) && xh && xl)
-    return launch_hash_tc(ix, xh, xl, x32, npts, codes, cj, cp, sk, sm, sp, ix->dev_error, s);
+    return launch_hash_tc(ix, xh, xl, x32, npts, codes, cj, cp, sk, sm, sp, ix->dev_error, rq, rq_count, rq_cap, s);
   const Layout& lay = ix->lay;
   const size_t smem = sizeof(float) * (size_t(lay.d_pad) * kHashPts + size_t(kHashChunk) * lay.d_pad);
   cudaError_t e = cudaFuncSetAttribute(hash_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));

@@ -5,10 +5,12 @@
 // bfloat16 products with float32 accumulation in tensor memory,
 //   X W^T ~= Xh Wh^T + Xh Wl^T + Xl Wh^T,   X = Xh + Xl, W = Wh + Wl,
 // whose error is below 3*2^-16*|x||w| for the split plus the accumulation
-// error (< K' * 2^-23 * |x||w|, K' = 3*d_pad <= 384), i.e. < 1.0e-4 |w| for
-// unit x.  The epilogue decides every hash bit with the rule of the SIMT
-// kernel using a band of 2^-11 |w| (= 2 * the stored 2^-12 |w|): a decision
-// closer to its boundary than the band is recomputed in float64 in index order,
+// error of the float32 accumulation in tensor memory (<= 24 MMA steps of 16
+// exact products, each step rounding with relative error <= 2^-20 even for a
+// truncating adder: < 2.3e-5 |x||w|), i.e. < 7e-5 |w| for unit x.  The
+// epilogue decides every hash bit with the rule of the SIMT kernel and the
+// same band 2^-12 |w| = 2.44e-4 |w|: a decision closer to its boundary than
+// the band is recomputed in float64 in index order,
 // which is the defining value (Sec. 2.2: HP bit = [<a,x> >= 0]; CP value =
 // sign and index of the largest |<a_c,x>|), so codes are bit-identical to the
 // float64 definition.
@@ -63,6 +65,9 @@ struct HashArgs {
   uint64_t* sk;
   int64_t sm, sp;
   int32_t* error;
+  RecheckReq* rq;       // deferred float64 rechecks (may be null)
+  uint32_t* rq_count;   // requests written (may exceed rq_cap: the excess was done inline)
+  uint32_t rq_cap;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -226,63 +231,143 @@ struct EpiState {
   uint32_t code;
 };
 
+// float64 projections of up to 4 CP hyperplanes (rows c[q] of function wf,
+// those with use[q]) onto x, in index order; chains interleaved for ILP
+__device__ __forceinline__ void dot64x4(const float* __restrict__ wf, const int (&c)[4], const bool (&use)[4],
+                                        const float* __restrict__ x, int d, int d_pad, double (&out)[4]) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  const float* w0 = wf + int64_t(c[0]) * d_pad;
+  const float* w1 = wf + int64_t(c[1]) * d_pad;
+  const float* w2 = wf + int64_t(c[2]) * d_pad;
+  const float* w3 = wf + int64_t(c[3]) * d_pad;
+  for (int i = 0; i < d; ++i) {
+    const double xi = double(x[i]);
+    if (use[0]) s0 = __dadd_rn(s0, __dmul_rn(double(w0[i]), xi));
+    if (use[1]) s1 = __dadd_rn(s1, __dmul_rn(double(w1[i]), xi));
+    if (use[2]) s2 = __dadd_rn(s2, __dmul_rn(double(w2[i]), xi));
+    if (use[3]) s3 = __dadd_rn(s3, __dmul_rn(double(w3[i]), xi));
+  }
+  out[0] = s0;
+  out[1] = s1;
+  out[2] = s2;
+  out[3] = s3;
+}
+
+// keep the four largest |v| (a0 >= a1 >= a2 >= a3) in registers
+__device__ __forceinline__ void top4_push(float av, float v, int c, float& a0, float& a1, float& a2, float& a3,
+                                          int& c0, int& c1, int& c2, int& c3, float& best_v) {
+  if (!(av > a3)) return;
+  if (av > a2) {
+    a3 = a2;
+    c3 = c2;
+    if (av > a1) {
+      a2 = a1;
+      c2 = c1;
+      if (av > a0) {
+        a1 = a0;
+        c1 = c0;
+        a0 = av;
+        c0 = c;
+        best_v = v;
+      } else {
+        a1 = av;
+        c1 = c;
+      }
+    } else {
+      a2 = av;
+      c2 = c;
+    }
+  } else {
+    a3 = av;
+    c3 = c;
+  }
+}
+
+// Reserve `cnt` consecutive request slots for this lane (warp-aggregated: one
+// atomic per warp) and return the first.  All lanes of the warp must call it.
+// Slots at or beyond rq_cap do not exist: the caller rechecks those inline, so
+// every slot below min(count, rq_cap) is written by exactly one lane.
+__device__ __forceinline__ uint32_t reserve_requests(const HashArgs& A, uint32_t cnt) {
+  const int lane = threadIdx.x & 31;
+  uint32_t inc = cnt;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, inc, off);
+    if (lane >= off) inc += v;
+  }
+  const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+  if (total == 0 || !A.rq) return 0xffffffffu;
+  uint32_t base = 0;
+  if (lane == 0) base = atomicAdd(A.rq_count, total);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  return base + inc - cnt;
+}
+
 // Epilogue of one N tile for the thread's point p (accumulator columns at taddr).
-__device__ void epilogue(const HashArgs& A, const Tile& t, uint32_t taddr, int64_t p, EpiState& st) {
+__device__ __forceinline__ void epilogue(const HashArgs& A, const Tile& t, uint32_t taddr, int64_t p,
+                                         EpiState& st) {
   const bool live = p < A.npts;
   const float* xrow = A.x32 + (live ? p : 0) * A.d_pad;
   if (t.seg < A.seg_tables && A.family == PF_CROSSPOLYTOPE) {
     if (t.first) st.code = 0;
-    float a[4] = {-1.f, -1.f, -1.f, -1.f};
-    int c4[4] = {0, 0, 0, 0};
+    float a0 = -1.f, a1 = -1.f, a2 = -1.f, a3 = -1.f;
+    int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
     float best_v = 0.f;
-    for (int c0 = 0; c0 < t.rows; c0 += 16) {
+    for (int cb = 0; cb < t.rows; cb += 16) {
       float v[16];
-      tmem_ld16(taddr + uint32_t(c0), v);
+      tmem_ld16(taddr + uint32_t(cb), v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int c = c0 + i;
-        if (c < A.d) {
-          const float av = fabsf(v[i]);
-          if (av > a[3]) {
-            if (av > a[0]) best_v = v[i];
-            int pos = 3;
-            while (pos > 0 && av > a[pos - 1]) {
-              a[pos] = a[pos - 1];
-              c4[pos] = c4[pos - 1];
-              --pos;
-            }
-            a[pos] = av;
-            c4[pos] = c;
-          }
-        }
-      }
+      for (int i = 0; i < 16; ++i)
+        if (cb + i < A.d) top4_push(fabsf(v[i]), v[i], cb + i, a0, a1, a2, a3, c0, c1, c2, c3, best_v);
     }
-    const float band = 2.f * A.thr[t.row0];
-    int arg = c4[0];
+    const float band = A.thr[t.row0];
+    int arg = c0;
     bool neg = best_v < 0.f;
-    if (live && (a[1] >= a[0] - 2.f * band || a[0] < band)) {
+    const bool need = live && (a1 >= a0 - 2.f * band || a0 < band);
+    const uint32_t slot = reserve_requests(A, need ? 1u : 0u);
+    if (need && slot < A.rq_cap) {
+      // keep the tensor-core decision now; the fix-up kernel rewrites the field
+      RecheckReq q;
+      q.p = uint32_t(p);
+      q.row0 = uint32_t(t.row0);
+      const bool all = a3 >= a0 - 2.f * band;
+      const uint32_t use = 1u | (a1 >= a0 - 2.f * band ? 2u : 0u) | (a2 >= a0 - 2.f * band ? 4u : 0u);
+      q.info = uint32_t(t.seg) | (uint32_t(t.fn) << 20) | (use << 26) | ((all ? 3u : 0u) << 30);
+      q.c[0] = uint8_t(c0);
+      q.c[1] = uint8_t(c1);
+      q.c[2] = uint8_t(c2);
+      q.c[3] = uint8_t(c3);
+      A.rq[slot] = q;
+    } else if (need) {
       const float* wf = A.w32 + t.row0 * A.d_pad;
       double bestabs = -1.0, bestval = 0.0;
       int besti = 0;
-      if (a[3] >= a[0] - 2.f * band) {
-        for (int cc = 0; cc < A.d; ++cc) {
-          const double v64 = dot64(wf + int64_t(cc) * A.d_pad, xrow, A.d);
-          if (fabs(v64) > bestabs) {
-            bestabs = fabs(v64);
-            bestval = v64;
-            besti = cc;
-          }
+      if (a3 >= a0 - 2.f * band) {
+        // a fifth row could be in the band: all rows, 4 at a time
+        for (int cc = 0; cc < A.d; cc += 4) {
+          const int cs[4] = {cc, min(cc + 1, A.d - 1), min(cc + 2, A.d - 1), min(cc + 3, A.d - 1)};
+          const bool us[4] = {true, cc + 1 < A.d, cc + 2 < A.d, cc + 3 < A.d};
+          double v64[4];
+          dot64x4(wf, cs, us, xrow, A.d, A.d_pad, v64);
+          for (int q = 0; q < 4; ++q)
+            if (us[q] && fabs(v64[q]) > bestabs) {
+              bestabs = fabs(v64[q]);
+              bestval = v64[q];
+              besti = cs[q];
+            }
         }
       } else {
-        for (int q = 0; q < 4; ++q) {
-          if (a[q] < a[0] - 2.f * band) continue;
-          const int cc = c4[q];
-          const double v64 = dot64(wf + int64_t(cc) * A.d_pad, xrow, A.d);
-          const double av = fabs(v64);
-          if (av > bestabs || (av == bestabs && cc < besti)) {
+        const int cs[4] = {c0, c1, c2, c3};
+        const bool us[4] = {true, a1 >= a0 - 2.f * band, a2 >= a0 - 2.f * band, false};
+        double v64[4];
+        dot64x4(wf, cs, us, xrow, A.d, A.d_pad, v64);
+        for (int q = 0; q < 3; ++q) {
+          if (!us[q]) continue;
+          const double av = fabs(v64[q]);
+          if (av > bestabs || (av == bestabs && cs[q] < besti)) {
             bestabs = av;
-            bestval = v64;
-            besti = cc;
+            bestval = v64[q];
+            besti = cs[q];
           }
         }
       }
@@ -296,33 +381,67 @@ __device__ void epilogue(const HashArgs& A, const Tile& t, uint32_t taddr, int64
   }
   // 128 one-bit rows: 4 HP repetitions (32 bits each) or 2 sketches (64 bits each)
   const bool is_sketch = t.seg >= A.seg_tables;
-  uint64_t bits[2] = {0ull, 0ull};
-  for (int c0 = 0; c0 < 128; c0 += 16) {
+  const int64_t row_end = is_sketch ? A.hash_rows : int64_t(A.L) * A.rows_table;
+  uint64_t bits0 = 0ull, bits1 = 0ull;
+  for (int cb = 0; cb < 128; cb += 16) {
     float v[16];
-    tmem_ld16(taddr + uint32_t(c0), v);
+    tmem_ld16(taddr + uint32_t(cb), v);
+    uint32_t needm = 0;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-      const int c = c0 + i;
+      const int c = cb + i;
       const int64_t row = t.row0 + c;
-      bool bit = v[i] >= 0.f;
-      if (row < A.hash_rows && live && fabsf(v[i]) < 2.f * A.thr[row])
-        bit = dot64(A.w32 + row * A.d_pad, xrow, A.d) >= 0.0;
-      if (bit) bits[c >> 6] |= uint64_t(1) << (c & 63);
+      if (row < row_end && live && fabsf(v[i]) < A.thr[row]) needm |= 1u << i;
+      if (v[i] >= 0.f) {
+        if (c < 64)
+          bits0 |= uint64_t(1) << c;
+        else
+          bits1 |= uint64_t(1) << (c - 64);
+      }
+    }
+    if (__any_sync(0xffffffffu, needm != 0)) {
+      uint32_t slot = reserve_requests(A, __popc(needm));
+      while (needm) {
+        const int i = __ffs(needm) - 1;
+        needm &= needm - 1;
+        const int c = cb + i;
+        const int64_t row = t.row0 + c;
+        if (slot < A.rq_cap) {
+          RecheckReq q;
+          q.p = uint32_t(p);
+          q.row0 = uint32_t(row);
+          if (is_sketch) {
+            const int64_t r = row - int64_t(A.L) * A.rows_table;
+            q.info = uint32_t(r >> 6) | (uint32_t(r & 63) << 20) | (2u << 30);
+          } else {
+            q.info = uint32_t(row >> 5) | (uint32_t(row & 31) << 20) | (1u << 30);
+          }
+          q.c[0] = q.c[1] = q.c[2] = q.c[3] = 0;
+          A.rq[slot] = q;
+          ++slot;  // stays >= rq_cap (including the "no queue" value) once it gets there
+        } else {
+          const bool bit = dot64(A.w32 + row * A.d_pad, xrow, A.d) >= 0.0;
+          const uint64_t m = uint64_t(1) << (c & 63);
+          if (c < 64)
+            bits0 = bit ? (bits0 | m) : (bits0 & ~m);
+          else
+            bits1 = bit ? (bits1 | m) : (bits1 & ~m);
+        }
+      }
     }
   }
   if (!live) return;
   if (is_sketch) {
-    for (int s = 0; s < 2; ++s) {
-      const int m = (t.seg - A.seg_tables) * 2 + s;
-      if (m < A.M) A.sk[int64_t(m) * A.sm + p * A.sp] = bits[s];
-    }
+    const int m0 = (t.seg - A.seg_tables) * 2;
+    if (m0 < A.M) A.sk[int64_t(m0) * A.sm + p * A.sp] = bits0;
+    if (m0 + 1 < A.M) A.sk[int64_t(m0 + 1) * A.sm + p * A.sp] = bits1;
   } else {
+    const uint32_t w[4] = {uint32_t(bits0), uint32_t(bits0 >> 32), uint32_t(bits1), uint32_t(bits1 >> 32)};
+#pragma unroll
     for (int s = 0; s < 4; ++s) {
       const int j = t.seg * 4 + s;
-      if (j >= A.L) break;
-      const uint32_t w = uint32_t(bits[s >> 1] >> ((s & 1) * 32));
       // column c of repetition j is function c: the first function is the top bit
-      A.codes[int64_t(j) * A.cj + p * A.cp] = __brev(w);
+      if (j < A.L) A.codes[int64_t(j) * A.cj + p * A.cp] = __brev(w[s]);
     }
   }
 }
@@ -453,6 +572,73 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A) {
   if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
+// Deferred float64 rechecks: one thread per request rewrites the decided field
+// of a code (CP function value or HP bit) or sketch bit with the float64
+// decision.  Fields of different requests are disjoint, so the two atomic
+// updates (clear, then set) of concurrent requests on one word commute.
+__global__ void recheck_kernel(HashArgs A) {
+  const uint32_t total = min(*A.rq_count, A.rq_cap);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const RecheckReq q = A.rq[i];
+    const int64_t p = q.p;
+    const float* xrow = A.x32 + p * A.d_pad;
+    const uint32_t kind = q.info >> 30;
+    if (kind == 0 || kind == 3) {
+      const int j = int(q.info & 0xFFFFFu), fn = int((q.info >> 20) & 63u);
+      const float* wf = A.w32 + int64_t(q.row0) * A.d_pad;
+      double bestabs = -1.0, bestval = 0.0;
+      int besti = 0;
+      if (kind == 3) {
+        for (int cc = 0; cc < A.d; cc += 4) {
+          const int cs[4] = {cc, min(cc + 1, A.d - 1), min(cc + 2, A.d - 1), min(cc + 3, A.d - 1)};
+          const bool us[4] = {true, cc + 1 < A.d, cc + 2 < A.d, cc + 3 < A.d};
+          double v64[4];
+          dot64x4(wf, cs, us, xrow, A.d, A.d_pad, v64);
+          for (int u = 0; u < 4; ++u)
+            if (us[u] && fabs(v64[u]) > bestabs) {
+              bestabs = fabs(v64[u]);
+              bestval = v64[u];
+              besti = cs[u];
+            }
+        }
+      } else {
+        const uint32_t use = (q.info >> 26) & 15u;
+        const int cs[4] = {q.c[0], q.c[1], q.c[2], q.c[3]};
+        const bool us[4] = {(use & 1u) != 0, (use & 2u) != 0, (use & 4u) != 0, false};
+        double v64[4];
+        dot64x4(wf, cs, us, xrow, A.d, A.d_pad, v64);
+        for (int u = 0; u < 3; ++u) {
+          if (!us[u]) continue;
+          const double av = fabs(v64[u]);
+          if (av > bestabs || (av == bestabs && cs[u] < besti)) {
+            bestabs = av;
+            bestval = v64[u];
+            besti = cs[u];
+          }
+        }
+      }
+      const uint32_t value = ((bestval < 0.0 ? 1u : 0u) << (A.ell - 1)) | uint32_t(besti);
+      const int shift = 32 - A.ell * (fn + 1);
+      const uint32_t field = ((1u << A.ell) - 1u) << shift;
+      uint32_t* w = A.codes + int64_t(j) * A.cj + p * A.cp;
+      atomicAnd(w, ~field);
+      atomicOr(w, value << shift);
+    } else {
+      const bool bit = dot64(A.w32 + int64_t(q.row0) * A.d_pad, xrow, A.d) >= 0.0;
+      const int idx = int(q.info & 0xFFFFFu), b = int((q.info >> 20) & 63u);
+      if (kind == 1) {
+        uint32_t* w = A.codes + int64_t(idx) * A.cj + p * A.cp;
+        const uint32_t m = 1u << (31 - b);
+        if (bit) atomicOr(w, m); else atomicAnd(w, ~m);
+      } else {
+        unsigned long long* w = reinterpret_cast<unsigned long long*>(A.sk + int64_t(idx) * A.sm + p * A.sp);
+        const unsigned long long m = 1ull << b;
+        if (bit) atomicOr(w, m); else atomicAnd(w, ~m);
+      }
+    }
+  }
+}
+
 }  // namespace
 
 bool hash_tc_supported(const pf_index* ix) { return ix->lay.d_pad <= 128; }
@@ -464,7 +650,8 @@ size_t hash_tc_smem(int d_pad) {
 
 cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __nv_bfloat16* xl, const float* x32,
                            int64_t npts, uint32_t* codes, int64_t cj, int64_t cp, uint64_t* sk, int64_t sm,
-                           int64_t sp, int32_t* error, cudaStream_t s) {
+                           int64_t sp, int32_t* error, RecheckReq* rq, uint32_t* rq_count, uint32_t rq_cap,
+                           cudaStream_t s) {
   if (npts <= 0) return cudaSuccess;
   HashArgs A;
   A.xh = xh;
@@ -497,11 +684,22 @@ cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __
   A.sm = sm;
   A.sp = sp;
   A.error = error;
+  A.rq = rq_cap ? rq : nullptr;
+  if (!A.rq) rq_cap = 0;
+  A.rq_count = rq_count;
+  A.rq_cap = A.rq ? rq_cap : 0u;
+  if (A.rq) {
+    cudaError_t e0 = cudaMemsetAsync(rq_count, 0, sizeof(uint32_t), s);
+    if (e0 != cudaSuccess) return e0;
+  }
   const size_t smem = hash_tc_smem(A.d_pad);
   cudaError_t e = cudaFuncSetAttribute(hash_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   const int grid = std::min(A.items, ix->num_sms);
   hash_tc_kernel<<<grid, kThreads, smem, s>>>(A);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !A.rq) return e;
+  recheck_kernel<<<4 * ix->num_sms, 256, 0, s>>>(A);
   return cudaGetLastError();
 }
 

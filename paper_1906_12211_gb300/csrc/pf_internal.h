@@ -40,6 +40,14 @@ void filter_cos_table(double* c /*[65]*/);
 int64_t budget_tables(int family, int64_t n, int d, int M, uint64_t budget);
 uint64_t resident_bytes(int family, int64_t n, int d, int M, int L);
 
+// A hash decision the tensor-core kernel leaves to the float64 fix-up pass.
+struct RecheckReq {
+  uint32_t p;     // point (row of the normalised matrix)
+  uint32_t row0;  // CP: first hash row of the function; one-bit decisions: the hash row
+  uint32_t info;  // bits 0-19 repetition / sketch, 20-25 function / bit, 26-29 CP candidate mask, 30-31 kind
+  uint8_t c[4];   // CP candidate hyperplanes
+};
+
 // ---------------------------------------------------------------- errors
 void set_error(const std::string& msg);
 struct Error {
@@ -65,6 +73,8 @@ struct pf_workspace {
   float* sims = nullptr;
   pf_query_stats* stats = nullptr;
   int32_t* counter = nullptr;  // work queue head + error word
+  pf::RecheckReq* rq = nullptr;  // deferred hash rechecks
+  uint32_t* rq_count = nullptr;
   size_t cap_kmax = 0;
 };
 
@@ -107,13 +117,18 @@ cudaError_t launch_normalize(const float* in, int64_t rows, int d, int d_pad, fl
 // Hash rows x32 [npts][d_pad] (with its bfloat16 split xh + xl) under all L
 // repetitions and M sketches.  Codes written at codes[j*cj + p*cp], sketches
 // at sk[m*sm + p*sp].  Uses the tensor-core kernel when d_pad <= 128.
+// rq: optional queue of deferred float64 rechecks (capacity rq_cap, counter
+// rq_count); without one, or when it is full, rechecks run inline.
 cudaError_t launch_hash(const pf_index* ix, const float* x32, const __nv_bfloat16* xh, const __nv_bfloat16* xl,
                         int64_t npts, uint32_t* codes, int64_t cj, int64_t cp, uint64_t* sk, int64_t sm,
-                        int64_t sp, cudaStream_t s);
+                        int64_t sp, RecheckReq* rq, uint32_t* rq_count, uint32_t rq_cap, cudaStream_t s);
+// recheck-queue entries to provision for npts points
+inline uint32_t recheck_capacity(int64_t npts) { return uint32_t(npts * 48 + 65536); }
 bool hash_tc_supported(const pf_index* ix);
 cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __nv_bfloat16* xl, const float* x32,
                            int64_t npts, uint32_t* codes, int64_t cj, int64_t cp, uint64_t* sk, int64_t sm,
-                           int64_t sp, int32_t* error, cudaStream_t s);
+                           int64_t sp, int32_t* error, RecheckReq* rq, uint32_t* rq_count, uint32_t rq_cap,
+                           cudaStream_t s);
 
 // Sort every repetition's (code, position) pairs and build the prefix tables.
 cudaError_t sort_tables(pf_index* ix, uint32_t* codes_unsorted, cudaStream_t s);
