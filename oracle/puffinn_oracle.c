@@ -323,20 +323,21 @@ int orc_filter_tau(double s_k) {
  * the hash functions and the tables.  Reading: bytes of the layout the GPU
  * library keeps resident, with d' = d rounded up to a multiple of 16:
  *   fixed     = n d' (4 + 2)   rows as float32 and bfloat16
- *             + n M 8          sketches
  *             + 64 M d' 8      sketch planes (float32 + two bfloat16 halves)
+ *             + n M 8          the M sketches of every point (layout 1 only)
  *   per table = n (4 + 4)      sorted codes and positions
+ *             + n 8            the sketch of each entry (layout 0 only)
  *             + 8193 * 4       prefix table
  *             + R d' 8         hash rows (float32 + two bfloat16 halves),
  *               R = F * d' for CP (rows of a function padded to d'), 32 for HP
  *   L = floor((budget - fixed) / per_table). */
-int64_t orc_budget_L(int family, int64_t n, int d, int M, uint64_t budget_bytes) {
+int64_t orc_budget_L(int family, int64_t n, int d, int M, uint64_t budget_bytes, int sketch_layout) {
   int64_t dp = ((int64_t)d + 15) / 16 * 16;
   int F;
   orc_layout(family, d, NULL, &F, NULL, NULL);
   int64_t R = (family == ORC_CROSSPOLYTOPE) ? (int64_t)F * dp : 32;
-  int64_t fixed = n * dp * 6 + n * (int64_t)M * 8 + 64 * (int64_t)M * dp * 8;
-  int64_t per_table = n * 8 + (int64_t)((1 << ORC_PREFIX_BITS) + 1) * 4 + R * dp * 8;
+  int64_t fixed = n * dp * 6 + 64 * (int64_t)M * dp * 8 + (sketch_layout == 1 ? n * (int64_t)M * 8 : 0);
+  int64_t per_table = n * (sketch_layout == 1 ? 8 : 16) + (int64_t)((1 << ORC_PREFIX_BITS) + 1) * 4 + R * dp * 8;
   if ((int64_t)budget_bytes <= fixed) return 0;
   return ((int64_t)budget_bytes - fixed) / per_table;
 }

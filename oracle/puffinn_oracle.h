@@ -74,8 +74,9 @@ double orc_ipow(double x, int64_t e);
 /* ---- sketch filter threshold (Sec. 4.2 "Filtering", Fig. 2 footnote) ---- */
 int orc_filter_tau(double s_k);
 
-/* ---- memory budget -> number of repetitions (Sec. 5, index size) ---- */
-int64_t orc_budget_L(int family, int64_t n, int d, int M, uint64_t budget_bytes);
+/* ---- memory budget -> number of repetitions (Sec. 5, index size) ----
+ * sketch_layout 0: one sketch copy per repetition entry; 1: M per point */
+int64_t orc_budget_L(int family, int64_t n, int d, int M, uint64_t budget_bytes, int sketch_layout);
 
 /* ---- canonical float32 inner product ---- */
 float orc_sim(const float* q, const float* x, int d);

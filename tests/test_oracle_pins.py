@@ -250,14 +250,17 @@ def test_cp_full_code_collision_matches_table(orc):
 
 # ------------------------------------------------------------ budget
 def test_budget_formula_values(orc):
-    # hand-evaluated with the layout stated in orc_budget_L
+    # hand-evaluated with the layouts stated in orc_budget_L
     n, d, M = 1_000_000, 100, 32
     dp, R = 112, 4 * 112
-    fixed = n * dp * 6 + n * M * 8 + 64 * M * dp * 8
-    per = n * 8 + 8193 * 4 + R * dp * 8
-    assert orc.budget_L(orc.CROSSPOLYTOPE, n, d, M, 4 << 30) == ((4 << 30) - fixed) // per == 398
-    assert orc.budget_L(orc.SIMHASH, 10_000, 64, 32, 32 << 20) == 202
-    assert orc.budget_L(orc.SIMHASH, 10_000, 64, 32, 1 << 20) == 0
+    fixed_point = n * dp * 6 + n * M * 8 + 64 * M * dp * 8
+    per_point = n * 8 + 8193 * 4 + R * dp * 8
+    assert orc.budget_L(orc.CROSSPOLYTOPE, n, d, M, 4 << 30, 1) == ((4 << 30) - fixed_point) // per_point == 398
+    fixed_table = n * dp * 6 + 64 * M * dp * 8
+    per_table = n * 16 + 8193 * 4 + R * dp * 8
+    assert orc.budget_L(orc.CROSSPOLYTOPE, n, d, M, 4 << 30, 0) == ((4 << 30) - fixed_table) // per_table == 220
+    assert orc.budget_L(orc.SIMHASH, 10_000, 64, 32, 32 << 20, 1) == 202
+    assert orc.budget_L(orc.SIMHASH, 10_000, 64, 32, 1 << 20, 0) == 0
 
 
 # ------------------------------------------------------------ similarity
