@@ -52,6 +52,15 @@ typedef enum {
 
 typedef enum { PF_F32 = 0 } pf_dtype;
 
+/* Where the 1-bit sketches live (Sec. 4.2 stores M sketches per point and lets
+ * repetition j use sketch j mod M).  Both layouts hold the same values and give
+ * the same results for the same L; they differ in memory and access pattern. */
+typedef enum {
+  PF_SKETCH_PER_TABLE = 0, /* default: repetition j keeps, next to its sorted ids, the sketch j mod M of the
+                              point at each position (8 more bytes per entry, read contiguously) */
+  PF_SKETCH_PER_POINT = 1  /* M sketches per point, gathered by id during the search */
+} pf_sketch_layout;
+
 /* Build parameters (Sec. 4.2-4.3).  Zero-initialise and set what you need;
  * zero means "default" for the optional fields. */
 typedef struct {
@@ -65,7 +74,7 @@ typedef struct {
   int32_t segment_B;            /* segment size B (Sec. 4.2, App. C); 0 -> 12 */
   int32_t cp_draws;             /* Monte-Carlo draws per similarity for the CP table (Sec. 4.3); 0 -> 1000 */
   int32_t num_tables;           /* if > 0, use exactly this L instead of the budget (tests, sweeps) */
-  int32_t reserved;
+  int32_t sketch_layout;        /* pf_sketch_layout; 0 -> PF_SKETCH_PER_TABLE */
 } pf_build_params;
 
 /* Per-call search options.  NULL = defaults (FP32 scoring, filter on). */
@@ -101,6 +110,7 @@ typedef struct {
   int32_t M;                /* sketches per point */
   int32_t B;                /* segment size */
   int32_t trained;          /* a start-depth model is present */
+  int32_t sketch_layout;    /* pf_sketch_layout */
   uint64_t bytes_used;      /* device bytes the index keeps resident */
   uint64_t budget_bytes;    /* budget it was built for */
 } pf_index_info_t;
@@ -112,9 +122,11 @@ typedef enum {
   PF_ARRAY_CODES = 2,      /* uint32 [L][n]: sorted codes of each repetition (Sec. 4.2) */
   PF_ARRAY_IDS = 3,        /* uint32 [L][n]: positions pos(p) in the same order */
   PF_ARRAY_PREFIX = 4,     /* uint32 [L][8193]: lexicographic start of each 13-bit prefix */
-  PF_ARRAY_SKETCHES = 5,   /* uint64 [M][n]: 1-bit sketches (Sec. 3.3, 4.2) */
+  PF_ARRAY_SKETCHES = 5,   /* uint64 [M][n]: 1-bit sketches (Sec. 3.3, 4.2); PF_SKETCH_PER_POINT only */
   PF_ARRAY_HASH_ROWS = 6,  /* float [L*R + 64*M][d_pad]: Gaussian rows (R = fns*d_pad for CP, 32 for HP) */
-  PF_ARRAY_CP_TABLE = 7    /* double [41][ell+1]: CP collision table (Sec. 4.3); absent for HP */
+  PF_ARRAY_CP_TABLE = 7,   /* double [41][ell+1]: CP collision table (Sec. 4.3); absent for HP */
+  PF_ARRAY_TABLE_SKETCHES = 8 /* uint64 [L][n]: sketch (j mod M) of the point at each position of repetition j;
+                                 PF_SKETCH_PER_TABLE only */
 } pf_array;
 
 /* Build the index over `points` ([n][d] row-major, host or device).
@@ -122,7 +134,8 @@ typedef enum {
  * hyperplanes from `seed`, hash every point, sort each repetition's
  * (code, pos) array and tabulate its 13-bit prefixes, and estimate the CP
  * collision table (Sec. 4.3).  L is the largest count whose resident bytes fit
- * memory_budget_bytes (PF_ERR_BUDGET_TOO_SMALL if none).  On success *out
+ * memory_budget_bytes (PF_ERR_BUDGET_TOO_SMALL if none); the bytes counted are
+ * those of the chosen sketch layout.  On success *out
  * receives a new index that the caller releases with pf_index_free. */
 pf_status pf_index_build(const pf_build_params* params, const void* points, pf_index** out, void* stream);
 

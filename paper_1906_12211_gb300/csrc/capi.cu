@@ -142,6 +142,7 @@ void destroy(pf_index* ix) {
   dfree(ix->x32);
   dfree(ix->x16);
   dfree(ix->sk);
+  dfree(ix->skc);
   dfree(ix->W32);
   dfree(ix->Whi);
   dfree(ix->Wlo);
@@ -225,8 +226,11 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
     if (M < 1 || M > 256) return fail(PF_ERR_INVALID_ARG, "num_sketches must be in [1, 256]");
     if (B < 1 || B > 4096) return fail(PF_ERR_INVALID_ARG, "segment_B must be in [1, 4096]");
     if (draws < 1) return fail(PF_ERR_INVALID_ARG, "cp_draws must be >= 1");
+    if (prm->sketch_layout != PF_SKETCH_PER_TABLE && prm->sketch_layout != PF_SKETCH_PER_POINT)
+      return fail(PF_ERR_INVALID_ARG, "unknown sketch layout");
     int64_t L = prm->num_tables > 0 ? prm->num_tables
-                                    : budget_tables(prm->family, prm->n, prm->d, M, prm->memory_budget_bytes);
+                                    : budget_tables(prm->family, prm->n, prm->d, M, prm->memory_budget_bytes,
+                                                    prm->sketch_layout);
     if (L < 1) return fail(PF_ERR_BUDGET_TOO_SMALL, "memory budget leaves room for no repetition");
     if (L > kMaxL) L = kMaxL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -243,7 +247,8 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       ix->B = B;
       ix->lay = make_layout(prm->family, prm->d);
       ix->budget = prm->memory_budget_bytes;
-      ix->bytes_used = resident_bytes(prm->family, prm->n, prm->d, M, ix->L);
+      ix->sketch_layout = prm->sketch_layout;
+      ix->bytes_used = resident_bytes(prm->family, prm->n, prm->d, M, ix->L, prm->sketch_layout);
       const int dp = ix->lay.d_pad;
       const int64_t n = ix->n;
       ix->hash_rows = int64_t(ix->L) * ix->lay.rows_table + 64LL * M;
@@ -254,7 +259,10 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
 
       dalloc(&ix->x32, size_t(n) * dp);
       dalloc(&ix->x16, size_t(n) * dp);
-      dalloc(&ix->sk, size_t(n) * M);
+      if (ix->sketch_layout == PF_SKETCH_PER_POINT)
+        dalloc(&ix->sk, size_t(n) * M);
+      else
+        dalloc(&ix->skc, size_t(n) * ix->L);
       dalloc(&ix->W32, size_t(ix->hash_rows) * dp);
       dalloc(&ix->Whi, size_t(ix->hash_rows) * dp);
       dalloc(&ix->Wlo, size_t(ix->hash_rows) * dp);
@@ -296,16 +304,23 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       __nv_bfloat16* xlo = nullptr;  // low bfloat16 half of the rows, only while hashing
       RecheckReq* rq = nullptr;      // deferred float64 rechecks, only while hashing
       uint32_t* rq_count = nullptr;
+      uint64_t* sk_tmp = nullptr;    // per-point sketches, only while building a per-table layout
       int32_t herr = 0;
       try {
+        uint64_t* sk_out = ix->sk;
+        if (!sk_out) {
+          dalloc(&sk_tmp, size_t(n) * M);
+          sk_out = sk_tmp;
+        }
         dalloc(&xlo, size_t(n) * dp);
         PF_CK(launch_normalize(pin, n, prm->d, dp, ix->x32, ix->x16, xlo, s));
         dalloc(&raw_codes, size_t(n) * ix->L);
         dalloc(&rq, recheck_capacity(n));
         dalloc(&rq_count, 1);
-        PF_CK(launch_hash(ix, ix->x32, ix->x16, xlo, n, raw_codes, n, 1, ix->sk, n, 1, rq, rq_count,
+        PF_CK(launch_hash(ix, ix->x32, ix->x16, xlo, n, raw_codes, n, 1, sk_out, n, 1, rq, rq_count,
                           recheck_capacity(n), s));
         PF_CK(sort_tables(ix, raw_codes, s));
+        if (ix->skc) PF_CK(gather_table_sketches(ix, sk_out, ix->skc, s));
         PF_CK(cudaMemcpyAsync(&herr, ix->dev_error, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PF_CK(cudaStreamSynchronize(s));
       } catch (...) {
@@ -315,6 +330,7 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
         dfree(xlo);
         dfree(rq);
         dfree(rq_count);
+        dfree(sk_tmp);
         throw;
       }
       dfree(staged);
@@ -322,6 +338,7 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       dfree(xlo);
       dfree(rq);
       dfree(rq_count);
+      dfree(sk_tmp);
       PF_CK(cudaGetLastError());
       if (herr) throw Error{PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait of the hashing kernel timed out"};
     } catch (...) {
@@ -452,6 +469,7 @@ pf_status pf_index_info(const pf_index* ix, pf_index_info_t* info) {
   info->M = ix->M;
   info->B = ix->B;
   info->trained = 0;
+  info->sketch_layout = ix->sketch_layout;
   info->bytes_used = ix->bytes_used;
   info->budget_bytes = ix->budget;
   return PF_OK;
@@ -466,7 +484,16 @@ pf_status pf_index_array(const pf_index* ix, int32_t which, const void** ptr, ui
     case PF_ARRAY_CODES: *ptr = ix->codes; *bytes = n * L * 4; break;
     case PF_ARRAY_IDS: *ptr = ix->ids; *bytes = n * L * 4; break;
     case PF_ARRAY_PREFIX: *ptr = ix->pfx; *bytes = uint64_t(kPrefixSize) * L * 4; break;
-    case PF_ARRAY_SKETCHES: *ptr = ix->sk; *bytes = n * uint64_t(ix->M) * 8; break;
+    case PF_ARRAY_SKETCHES:
+      if (!ix->sk) return fail(PF_ERR_INVALID_ARG, "index keeps its sketches per repetition");
+      *ptr = ix->sk;
+      *bytes = n * uint64_t(ix->M) * 8;
+      break;
+    case PF_ARRAY_TABLE_SKETCHES:
+      if (!ix->skc) return fail(PF_ERR_INVALID_ARG, "index keeps its sketches per point");
+      *ptr = ix->skc;
+      *bytes = n * L * 8;
+      break;
     case PF_ARRAY_HASH_ROWS: *ptr = ix->W32; *bytes = uint64_t(ix->hash_rows) * dp * 4; break;
     case PF_ARRAY_CP_TABLE:
       if (!ix->cpP) return fail(PF_ERR_INVALID_ARG, "index has no CP table");

@@ -351,6 +351,24 @@ __global__ void prefix_kernel(const uint32_t* __restrict__ codes, int64_t n, uin
   }
 }
 
+// Per-repetition copy of the sketches in the repetition's sorted order, so the
+// search reads a candidate's id and sketch from the same position.
+__global__ void table_sketch_kernel(const uint32_t* __restrict__ ids, const uint64_t* __restrict__ sk, int64_t n,
+                                    int L, int M, uint64_t* __restrict__ skc) {
+  const int64_t total = n * L;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t j = e / n;
+    skc[e] = sk[(j % M) * n + ids[e]];
+  }
+}
+
+cudaError_t gather_table_sketches(const pf_index* ix, const uint64_t* sk, uint64_t* skc, cudaStream_t s) {
+  const int64_t total = ix->n * ix->L;
+  const int blocks = int(std::min<int64_t>(int64_t(ix->num_sms) * 16, (total + 255) / 256));
+  table_sketch_kernel<<<blocks, 256, 0, s>>>(ix->ids, sk, ix->n, ix->L, ix->M, skc);
+  return cudaGetLastError();
+}
+
 cudaError_t sort_tables(pf_index* ix, uint32_t* codes_unsorted, cudaStream_t s) {
   const int64_t n = ix->n;
   const int ntiles = int((n + kSortTile - 1) / kSortTile);

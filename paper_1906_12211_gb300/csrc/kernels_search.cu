@@ -44,7 +44,8 @@ struct Dev {
   const uint32_t* codes;
   const uint32_t* ids;
   const uint32_t* pfx;
-  const uint64_t* sk;
+  const uint64_t* sk;   // [M][n] per-point sketches, or null
+  const uint64_t* skc;  // [L][n] per-repetition sketches, or null
   const double* cpP;
   const double* cos_tab;
   float bf16_err;
@@ -493,10 +494,16 @@ __global__ void __launch_bounds__(kWarps * 32, 5) search_kernel(Dev P) {
           bool pass[kUnroll];
           if (P.filter) {
             uint64_t h[kUnroll];
+            if (P.skc) {  // the sketch sits at the same position as the id
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-              const int m = jo[u] % P.M;
-              h[u] = valid[u] ? __ldg(P.sk + size_t(m) * n + id[u]) ^ qs[m] : 0ull;
+              for (int u = 0; u < kUnroll; ++u)
+                h[u] = valid[u] ? __ldg(P.skc + size_t(jo[u]) * n + pos[u]) ^ qs[jo[u] % P.M] : 0ull;
+            } else {
+#pragma unroll
+              for (int u = 0; u < kUnroll; ++u) {
+                const int m = jo[u] % P.M;
+                h[u] = valid[u] ? __ldg(P.sk + size_t(m) * n + id[u]) ^ qs[m] : 0ull;
+              }
             }
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) pass[u] = valid[u] && __popcll(h[u]) <= tau;
@@ -573,6 +580,7 @@ cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t 
   P.ids = ix->ids;
   P.pfx = ix->pfx;
   P.sk = ix->sk;
+  P.skc = ix->skc;
   P.cpP = ix->cpP;
   P.cos_tab = ix->cos_tab;
   P.bf16_err = ix->bf16_err;

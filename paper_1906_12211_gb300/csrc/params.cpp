@@ -195,19 +195,24 @@ void filter_cos_table(double* c) {
 
 // Device bytes the index keeps resident for L repetitions; the budget rule
 // picks the largest L whose total fits (Sec. 5: the index size covers the
-// data, the hash functions and the tables).
-uint64_t resident_bytes(int family, int64_t n, int d, int M, int L) {
+// data, the hash functions and the tables).  Per repetition: sorted codes and
+// ids, the prefix table, the hash rows (float32 + two bfloat16 halves) and,
+// with per-repetition sketches, one uint64 per entry.  Fixed: the rows
+// (float32 + bfloat16), the sketch planes and, with per-point sketches, the M
+// sketches of every point.
+uint64_t resident_bytes(int family, int64_t n, int d, int M, int L, int sketch_layout) {
   const Layout lay = make_layout(family, d);
   const int64_t dp = lay.d_pad;
-  const int64_t fixed = n * dp * 6 + n * int64_t(M) * 8 + 64LL * M * dp * 8;
-  const int64_t per_table = n * 8 + int64_t(kPrefixSize) * 4 + int64_t(lay.rows_table) * dp * 8;
+  const bool per_point = sketch_layout == PF_SKETCH_PER_POINT;
+  const int64_t fixed = n * dp * 6 + 64LL * M * dp * 8 + (per_point ? n * int64_t(M) * 8 : 0);
+  const int64_t per_table = n * (per_point ? 8 : 16) + int64_t(kPrefixSize) * 4 + int64_t(lay.rows_table) * dp * 8;
   return uint64_t(fixed + per_table * L);
 }
 
-int64_t budget_tables(int family, int64_t n, int d, int M, uint64_t budget) {
-  const uint64_t fixed = resident_bytes(family, n, d, M, 0);
+int64_t budget_tables(int family, int64_t n, int d, int M, uint64_t budget, int sketch_layout) {
+  const uint64_t fixed = resident_bytes(family, n, d, M, 0, sketch_layout);
   if (budget <= fixed) return 0;
-  const uint64_t per_table = resident_bytes(family, n, d, M, 1) - fixed;
+  const uint64_t per_table = resident_bytes(family, n, d, M, 1, sketch_layout) - fixed;
   return int64_t((budget - fixed) / per_table);
 }
 

@@ -37,8 +37,8 @@ float gaussian(uint64_t seed, uint32_t purpose, uint32_t a, uint32_t b, uint32_t
 void gen_hash_rows(uint64_t seed, int family, int L, int M, int d, const Layout& lay, float* W, float* thr);
 void cp_collision_table(uint64_t seed, int d, int ell, int draws, double* P /*[41][ell+1]*/);
 void filter_cos_table(double* c /*[65]*/);
-int64_t budget_tables(int family, int64_t n, int d, int M, uint64_t budget);
-uint64_t resident_bytes(int family, int64_t n, int d, int M, int L);
+int64_t budget_tables(int family, int64_t n, int d, int M, uint64_t budget, int sketch_layout);
+uint64_t resident_bytes(int family, int64_t n, int d, int M, int L, int sketch_layout);
 
 // A hash decision the tensor-core kernel leaves to the float64 fix-up pass.
 struct RecheckReq {
@@ -82,13 +82,15 @@ struct pf_index {
   int device = 0;
   int64_t n = 0;
   int d = 0, family = 0, L = 0, M = 32, B = 12;
+  int sketch_layout = PF_SKETCH_PER_TABLE;
   pf::Layout lay;
   uint64_t budget = 0, bytes_used = 0;
   int64_t hash_rows = 0;  // L*rows_table + 64*M
   // resident device arrays
   float* x32 = nullptr;            // [n][d_pad]
   __nv_bfloat16* x16 = nullptr;    // [n][d_pad]
-  uint64_t* sk = nullptr;          // [M][n]
+  uint64_t* sk = nullptr;          // [M][n] (per-point layout)
+  uint64_t* skc = nullptr;         // [L][n] sketch j mod M of the point at each position (per-table layout)
   float* W32 = nullptr;            // [hash_rows][d_pad]
   __nv_bfloat16* Whi = nullptr;    // [hash_rows][d_pad]
   __nv_bfloat16* Wlo = nullptr;    // [hash_rows][d_pad]
@@ -132,6 +134,8 @@ cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __
 
 // Sort every repetition's (code, position) pairs and build the prefix tables.
 cudaError_t sort_tables(pf_index* ix, uint32_t* codes_unsorted, cudaStream_t s);
+// skc[j][pos] = sk[j mod M][ids[j][pos]] for every repetition
+cudaError_t gather_table_sketches(const pf_index* ix, const uint64_t* sk, uint64_t* skc, cudaStream_t s);
 
 struct SearchArgs {
   int Q = 0;

@@ -45,9 +45,9 @@ def oracle_rows_from_lib(ix, W):
 
 
 class Case:
-    def __init__(self, orc, name, X, Q, family, L=None, budget=None, seed=0, B=12):
-        self.name, self.X, self.Q = name, X, Q
-        kw = dict(seed=seed, segment_B=B)
+    def __init__(self, orc, name, X, Q, family, L=None, budget=None, seed=0, B=12, layout="table"):
+        self.name, self.X, self.Q, self.layout = name, X, Q, layout
+        kw = dict(seed=seed, segment_B=B, sketch_layout=layout)
         if budget is not None:
             kw["budget_bytes"] = budget
         else:
@@ -63,8 +63,24 @@ def cfg1(orc):
     # points and queries i.i.d. N(0,1), n = 10,000, d = 64, SimHash, 32 MiB
     X, Q = datagen.make("gauss-n10k-d64", seed=0)
     c = Case(orc, "gauss-n10k-d64", X, Q, "simhash", budget=32 << 20)
-    assert c.gpu.L == orc.budget_L(orc.SIMHASH, 10_000, 64, 32, 32 << 20)
+    assert c.gpu.L == orc.budget_L(orc.SIMHASH, 10_000, 64, 32, 32 << 20, 0)
     return c
+
+
+@pytest.fixture(scope="module")
+def cfg1pp(orc):
+    # the same workload with M sketches per point (the paper's layout), 32 MiB
+    X, Q = datagen.make("gauss-n10k-d64", seed=0)
+    c = Case(orc, "gauss-n10k-d64-pp", X, Q, "simhash", budget=32 << 20, layout="point")
+    assert c.gpu.L == orc.budget_L(orc.SIMHASH, 10_000, 64, 32, 32 << 20, 1)
+    return c
+
+
+@pytest.fixture(scope="module")
+def cpmidpp(orc):
+    X = datagen.vmf_mixture(20_000, 100, 50, 50.0, seed=3)
+    Q = datagen.vmf_mixture(150, 100, 50, 50.0, seed=3, purpose="queries")
+    return Case(orc, "vmf-n20k-d100-pp", X, Q, "crosspolytope", L=40, seed=7, layout="point")
 
 
 @pytest.fixture(scope="module")
@@ -99,7 +115,7 @@ def hpodd(orc):
     return Case(orc, "gauss-n2500-d20", X, Q, "simhash", L=7, seed=2)
 
 
-CASES = ["cfg1", "cpmid", "cpodd", "cpwide", "hpodd"]
+CASES = ["cfg1", "cpmid", "cpodd", "cpwide", "hpodd", "cfg1pp", "cpmidpp"]
 
 
 @pytest.fixture
@@ -141,8 +157,13 @@ def test_tables_sketches_prefix_bit_exact(case):
     assert np.array_equal(ids, case.orc.ids)
     pfx = u32(ix.array("prefix"), (ix.L, 8193))
     assert np.array_equal(pfx, case.orc.pfx)
-    sk = ix.array("sketches").cpu().numpy().view(np.uint64).reshape(ix.M, ix.n)
-    assert np.array_equal(sk, case.orc.sk)
+    if case.layout == "point":
+        sk = ix.array("sketches").cpu().numpy().view(np.uint64).reshape(ix.M, ix.n)
+        assert np.array_equal(sk, case.orc.sk)
+    else:
+        skc = ix.array("table_sketches").cpu().numpy().view(np.uint64).reshape(ix.L, ix.n)
+        ref = np.stack([case.orc.sk[j % ix.M][case.orc.ids[j]] for j in range(ix.L)])
+        assert np.array_equal(skc, ref)
 
 
 @pytest.mark.parametrize("case", CASES, indirect=True)
