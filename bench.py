@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="bf16", choices=["bf16", "fp32"])
-    ap.add_argument("--recall", type=float, default=0.95, help="recall target 1 - delta passed to the index")
+    ap.add_argument("--recall", type=float, default=0.9, help="recall target 1 - delta passed to the index")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--Q", type=int, default=None)
     ap.add_argument("--budget", type=int, default=None, help="index budget in bytes (default: the workload's)")
