@@ -179,6 +179,45 @@ pf_status pf_index_search_noalloc(pf_index* index, const float* queries, int64_t
                                   const double* recall, int32_t k_max, uint32_t* out_ids, float* out_sims,
                                   pf_query_stats* stats, const pf_search_opts* opts, void* stream);
 
+/* ---- learned start depth (the paper has no counterpart: an optional
+ *      predictor layered on Algorithm 1's depth schedule) ----
+ * A 2-layer perceptron (hidden 256, ReLU) maps a query's features -- its
+ * normalised vector and its first 64-bit sketch as +-1 -- to a distribution
+ * over the prefix length at which the plain schedule K, K-1, ... stops.  With
+ * opts->learned_start the search runs one round at K and then starts at the
+ * smallest depth d with P(stop depth > d) <= 0.05; the stop test of Lemma 1
+ * still ends every query, so the recall guarantee is that of the plain method. */
+typedef struct {
+  float final_loss;      /* mean cross-entropy of the last epoch */
+  float train_accuracy;  /* fraction of training queries whose predicted start depth >= their stop depth */
+  float mean_stop;       /* mean stop depth of the training traces */
+  float mean_start;      /* mean predicted start depth on the training queries */
+  int32_t samples;       /* training queries */
+  int32_t epochs;
+} pf_learned_report;
+
+/* Train the start-depth model of `index` on Qt training queries ([Qt][d],
+ * host or device): trace the plain search of each (k, recall) to get its stop
+ * depth, then `epochs` passes of mini-batch Adam (batch 1024, learning rate
+ * 1e-3, weights drawn from `seed`) with this library's kernels.  Replaces any
+ * previous model.  report may be NULL. */
+pf_status pf_learned_train(pf_index* index, const float* train_queries, int64_t Qt, int32_t k, double recall,
+                           int32_t epochs, uint64_t seed, pf_learned_report* report, void* stream);
+
+/* Start depths the trained model picks for Q queries (int32 [Q], host or
+ * device).  PF_ERR_NOT_TRAINED without a model. */
+pf_status pf_learned_predict(pf_index* index, const float* queries, int64_t Q, int32_t* start_depth, void* stream);
+
+/* One forward + backward pass of the start-depth perceptron on caller data
+ * (all device pointers, float32, row-major): X [B][F], y [B] class labels in
+ * [0, C), W1 [H][F], b1 [H], W2 [C][H], b2 [C].  Writes the mean
+ * cross-entropy to *loss (device) and its gradients dW1, db1, dW2, db2.
+ * Exposed so that the gradients can be checked against an independent CPU
+ * implementation. */
+pf_status pf_mlp_forward_backward(const float* X, const int32_t* y, int32_t B, int32_t F, int32_t H, int32_t C,
+                                  const float* W1, const float* b1, const float* W2, const float* b2, float* loss,
+                                  float* dW1, float* db1, float* dW2, float* db2, void* stream);
+
 /* Hash Q queries only (the first step of every query, Sec. 4.1): normalise,
  * then codes [Q][L] uint32 and sketches [Q][M] uint64 (host or device). */
 pf_status pf_hash_queries(pf_index* index, const float* queries, int64_t Q, uint32_t* qcodes,

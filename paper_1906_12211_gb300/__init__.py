@@ -60,6 +60,11 @@ class IndexInfo(C.Structure):
                 ("budget_bytes", C.c_uint64)]
 
 
+class LearnedReport(C.Structure):
+    _fields_ = [("final_loss", C.c_float), ("train_accuracy", C.c_float), ("mean_stop", C.c_float),
+                ("mean_start", C.c_float), ("samples", C.c_int32), ("epochs", C.c_int32)]
+
+
 class PuffinnError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -92,6 +97,10 @@ def lib():
                 "pf_hash_queries": (i32, [vp, vp, i64, vp, vp, vp]),
                 "pf_index_info": (i32, [vp, vp]),
                 "pf_index_last_timing": (i32, [vp, vp, i32]),
+                "pf_learned_train": (i32, [vp, vp, i64, i32, C.c_double, i32, C.c_uint64, vp, vp]),
+                "pf_learned_predict": (i32, [vp, vp, i64, vp, vp]),
+                "pf_mlp_forward_backward": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                                  vp]),
                 "pf_index_array": (i32, [vp, i32, vp, vp]),
                 "pf_index_read_array": (i32, [vp, i32, vp, C.c_uint64, vp]),
                 "pf_search_opts_default": (None, [vp]),
@@ -206,8 +215,26 @@ class Index:
         _check(lib().pf_hash_queries(self._h, _ptr(queries), Q, _ptr(qcodes), _ptr(qsk), _stream_ptr(stream)))
         return qcodes, qsk
 
+    def learned_train(self, train_queries, k: int, recall: float, *, epochs: int = 20, seed: int = 0, stream=None):
+        """Train the start-depth model on traces of the plain search; returns the report."""
+        rep = LearnedReport()
+        _check(lib().pf_learned_train(self._h, _ptr(train_queries), int(train_queries.shape[0]), int(k),
+                                      float(recall), int(epochs), int(seed), C.byref(rep), _stream_ptr(stream)))
+        return {f: getattr(rep, f) for f, _ in LearnedReport._fields_}
+
+    def learned_predict(self, queries, out=None, stream=None):
+        import torch
+
+        Q = int(queries.shape[0])
+        dev = queries.device if hasattr(queries, "device") else torch.device("cpu")
+        if out is None:
+            out = torch.empty(Q, dtype=torch.int32, device=dev)
+        _check(lib().pf_learned_predict(self._h, _ptr(queries), Q, _ptr(out), _stream_ptr(stream)))
+        return out
+
     def search(self, queries, k, recall, *, k_max: int | None = None, scoring: str = "fp32", filter: bool = True,
-               start_depth=None, out_ids=None, out_sims=None, stats=None, stream=None, timing: bool = False):
+               start_depth=None, out_ids=None, out_sims=None, stats=None, stream=None, timing: bool = False,
+               learned: bool = False):
         """Answer a batch of queries; k and recall are per-query arrays (same
         device as the queries) or scalars.  Returns (ids, sims, stats)."""
         import torch
@@ -233,6 +260,7 @@ class Index:
         o.scoring = 1 if scoring == "bf16" else 0
         o.filter = 1 if filter else 0
         o.timing = 1 if timing else 0
+        o.learned_start = 1 if learned else 0
         sd = None
         if start_depth is not None:
             sd = start_depth if torch.is_tensor(start_depth) else torch.full((Q,), int(start_depth),
@@ -261,6 +289,19 @@ class Index:
         t = (C.c_float * 3)()
         _check(lib().pf_index_last_timing(self._h, t, 3))
         return tuple(float(v) for v in t)
+
+
+def mlp_forward_backward(X, y, W1, b1, W2, b2, stream=None):
+    """pf_mlp_forward_backward on torch CUDA tensors; returns (loss, dW1, db1, dW2, db2)."""
+    import torch
+
+    B, F = X.shape
+    H, C = W1.shape[0], W2.shape[0]
+    loss = torch.zeros(1, dtype=torch.float32, device=X.device)
+    g = [torch.empty_like(t) for t in (W1, b1, W2, b2)]
+    _check(lib().pf_mlp_forward_backward(_ptr(X), _ptr(y), B, F, H, C, _ptr(W1), _ptr(b1), _ptr(W2), _ptr(b2),
+                                         _ptr(loss), *[_ptr(t) for t in g], _stream_ptr(stream)))
+    return (loss, *g)
 
 
 def stats_to_numpy(stats) -> np.ndarray:

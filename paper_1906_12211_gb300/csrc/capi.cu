@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <numeric>
+#include <random>
 #include <cstring>
 #include <new>
 #include <string>
@@ -153,6 +155,9 @@ void destroy(pf_index* ix) {
   dfree(ix->cpP);
   dfree(ix->cos_tab);
   dfree(ix->dev_error);
+  dfree(ix->mlp_w);
+  dfree(ix->mlp_w1h);
+  dfree(ix->mlp_w2h);
   free_ws(ix->ws);
   for (auto& e : ix->ev)
     if (e) cudaEventDestroy(e);
@@ -172,6 +177,15 @@ void hash_queries_ws(pf_index* ix, const float* qdev, int64_t Q, cudaStream_t s)
   PF_CK(launch_normalize(qdev, Q, ix->d, ix->lay.d_pad, ws.qx, ws.qxh, ws.qxl, s));
   PF_CK(launch_hash(ix, ws.qx, ws.qxh, ws.qxl, Q, ws.qcodes, 1, ix->L, ws.qsk, 1, ix->M, ws.rq, ws.rq_count,
                     recheck_capacity(Q), s));
+}
+
+// start depths of the model for the Q hashed queries of the workspace -> ws.start
+void predict_ws(pf_index* ix, int64_t Q, cudaStream_t s) {
+  const int F = ix->mlp_F, H = kMlpHidden, C = ix->mlp_C;
+  const float* b1 = ix->mlp_w + size_t(H) * F;
+  const float* b2 = b1 + H + size_t(C) * H;
+  PF_CK(mlp_predict(ix->ws.qx, ix->ws.qsk, int(Q), ix->lay.d_pad, ix->M, ix->mlp_w1h, b1, ix->mlp_w2h, b2, C,
+                    kMlpTail, ix->ws.start, s));
 }
 
 const float* stage_queries(pf_index* ix, const float* queries, int64_t Q, cudaStream_t s) {
@@ -383,7 +397,7 @@ pf_status pf_index_search(pf_index* ix, const float* queries, int64_t Q, const i
     pf_search_opts_default(&o);
     if (opts) o = *opts;
     if (o.scoring != 0 && o.scoring != 1) return fail(PF_ERR_INVALID_ARG, "scoring must be 0 or 1");
-    if (o.learned_start) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
+    if (o.learned_start && !ix->mlp_trained) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
     if (Q == 0) return PF_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PF_CK(cudaSetDevice(ix->device));
@@ -404,6 +418,10 @@ pf_status pf_index_search(pf_index* ix, const float* queries, int64_t Q, const i
       PF_CK(cudaEventRecord(ix->ev[0], s));
     }
     hash_queries_ws(ix, qd, Q, s);
+    if (o.learned_start) {
+      predict_ws(ix, Q, s);
+      sd = ws.start;
+    }
     if (timing) PF_CK(cudaEventRecord(ix->ev[1], s));
 
     const bool ids_dev = on_device(out_ids), sims_dev = on_device(out_sims);
@@ -468,7 +486,7 @@ pf_status pf_index_info(const pf_index* ix, pf_index_info_t* info) {
   info->fns = ix->lay.fns;
   info->M = ix->M;
   info->B = ix->B;
-  info->trained = 0;
+  info->trained = ix->mlp_trained;
   info->sketch_layout = ix->sketch_layout;
   info->bytes_used = ix->bytes_used;
   info->budget_bytes = ix->budget;
@@ -514,6 +532,224 @@ pf_status pf_index_read_array(const pf_index* ix, int32_t which, void* dst, uint
     if (!dst || dst_bytes < nb) return fail(PF_ERR_INVALID_ARG, "destination too small");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PF_CK(cudaMemcpyAsync(dst, src, nb, cudaMemcpyDefault, s));
+    PF_CK(cudaStreamSynchronize(s));
+    return PF_OK;
+  });
+}
+
+pf_status pf_mlp_forward_backward(const float* X, const int32_t* y, int32_t B, int32_t F, int32_t H, int32_t C,
+                                  const float* W1, const float* b1, const float* W2, const float* b2, float* loss,
+                                  float* dW1, float* db1, float* dW2, float* db2, void* stream) {
+  return guarded([&]() -> pf_status {
+    if (!X || !y || !W1 || !b1 || !W2 || !b2 || !loss || !dW1 || !db1 || !dW2 || !db2)
+      return fail(PF_ERR_INVALID_ARG, "null argument");
+    if (B < 1 || F < 1 || H < 1 || C < 1) return fail(PF_ERR_INVALID_ARG, "sizes must be >= 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float *h = nullptr, *z = nullptr, *dz = nullptr, *dh = nullptr;
+    try {
+      dalloc(&h, size_t(B) * H);
+      dalloc(&z, size_t(B) * C);
+      dalloc(&dz, size_t(B) * C);
+      dalloc(&dh, size_t(B) * H);
+      PF_CK(mlp_forward_backward(X, y, B, F, H, C, W1, b1, W2, b2, loss, dW1, db1, dW2, db2, h, z, dz, dh, s));
+      PF_CK(cudaStreamSynchronize(s));
+    } catch (...) {
+      cudaStreamSynchronize(s);
+      dfree(h); dfree(z); dfree(dz); dfree(dh);
+      throw;
+    }
+    dfree(h); dfree(z); dfree(dz); dfree(dh);
+    return PF_OK;
+  });
+}
+
+pf_status pf_learned_train(pf_index* ix, const float* train_queries, int64_t Qt, int32_t k, double recall,
+                           int32_t epochs, uint64_t seed, pf_learned_report* report, void* stream) {
+  return guarded([&]() -> pf_status {
+    if (!ix || !train_queries) return fail(PF_ERR_INVALID_ARG, "null argument");
+    if (Qt < 1 || Qt > 0x7fffffffLL) return fail(PF_ERR_INVALID_ARG, "Qt out of range");
+    if (k < 1 || k > kMaxK) return fail(PF_ERR_INVALID_ARG, "k must be in [1, 128]");
+    if (!(recall > 0.0 && recall < 1.0)) return fail(PF_ERR_INVALID_ARG, "recall not in (0, 1)");
+    if (epochs < 1 || epochs > 100000) return fail(PF_ERR_INVALID_ARG, "epochs must be in [1, 100000]");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PF_CK(cudaSetDevice(ix->device));
+    const int F = ix->lay.d_pad + 64, H = kMlpHidden, C = ix->lay.Kb + 1;
+    const int64_t nW1 = int64_t(H) * F, nW2 = int64_t(C) * H, nparam = nW1 + H + nW2 + C;
+    const int Bt = 1024;
+    // traces of the plain schedule: the stop depth of every training query
+    const int64_t chunk = std::min<int64_t>(Qt, 32768);
+    float *X = nullptr, *Xp = nullptr, *P = nullptr, *G = nullptr, *Mo = nullptr, *Vo = nullptr;
+    float *h = nullptr, *z = nullptr, *dz = nullptr, *dh = nullptr, *losses = nullptr;
+    int32_t *y = nullptr, *yp = nullptr, *perm = nullptr, *kk = nullptr;
+    double* rr = nullptr;
+    __nv_bfloat16 *w1h = nullptr, *w2h = nullptr;
+    auto cleanup = [&]() {
+      dfree(X); dfree(Xp); dfree(P); dfree(G); dfree(Mo); dfree(Vo); dfree(h); dfree(z); dfree(dz); dfree(dh);
+      dfree(losses); dfree(y); dfree(yp); dfree(perm); dfree(kk); dfree(rr); dfree(w1h); dfree(w2h);
+    };
+    std::vector<int32_t> hy(Qt);
+    try {
+      dalloc(&X, size_t(Qt) * F);
+      dalloc(&Xp, size_t(Qt) * F);
+      dalloc(&y, size_t(Qt));
+      dalloc(&yp, size_t(Qt));
+      dalloc(&perm, size_t(Qt));
+      dalloc(&kk, size_t(chunk));
+      dalloc(&rr, size_t(chunk));
+      ensure_ws(ix, chunk, k);
+      pf_workspace& ws = ix->ws;
+      {
+        std::vector<int32_t> kv(chunk, k);
+        std::vector<double> rv(chunk, recall);
+        PF_CK(cudaMemcpyAsync(kk, kv.data(), sizeof(int32_t) * chunk, cudaMemcpyHostToDevice, s));
+        PF_CK(cudaMemcpyAsync(rr, rv.data(), sizeof(double) * chunk, cudaMemcpyHostToDevice, s));
+        PF_CK(cudaStreamSynchronize(s));
+      }
+      std::vector<pf_query_stats> st(chunk);
+      for (int64_t q0 = 0; q0 < Qt; q0 += chunk) {
+        const int64_t nq = std::min(chunk, Qt - q0);
+        const float* src = train_queries + size_t(q0) * ix->d;
+        const float* qd = stage_queries(ix, src, nq, s);
+        hash_queries_ws(ix, qd, nq, s);
+        SearchArgs a;
+        a.Q = int(nq);
+        a.qx = ws.qx;
+        a.qcodes = ws.qcodes;
+        a.qsk = ws.qsk;
+        a.k = kk;
+        a.recall = rr;
+        a.k_max = k;
+        a.filter = 1;
+        a.scoring = 1;
+        a.out_ids = ws.ids;
+        a.out_sims = ws.sims;
+        a.stats = ws.stats;
+        a.counter = ws.counter;
+        PF_CK(cudaMemsetAsync(ws.counter, 0, sizeof(int32_t) * 64, s));
+        PF_CK(launch_search(ix, a, s));
+        PF_CK(mlp_features(ws.qx, ws.qsk, int(nq), ix->lay.d_pad, ix->M, X + size_t(q0) * F, s));
+        PF_CK(cudaMemcpyAsync(st.data(), ws.stats, sizeof(pf_query_stats) * nq, cudaMemcpyDeviceToHost, s));
+        PF_CK(cudaStreamSynchronize(s));
+        for (int64_t i = 0; i < nq; ++i) hy[q0 + i] = st[i].stop_depth;
+      }
+      PF_CK(cudaMemcpyAsync(y, hy.data(), sizeof(int32_t) * Qt, cudaMemcpyHostToDevice, s));
+      // weights: W1 ~ N(0, 2/F), W2 ~ N(0, 1/H), zero biases (host, from the seed)
+      std::vector<float> hp(nparam, 0.f);
+      const float s1 = std::sqrt(2.f / float(F)), s2 = std::sqrt(1.f / float(H));
+      for (int64_t i = 0; i < nW1; ++i) hp[i] = s1 * gaussian(seed, 4u, 0u, uint32_t(i / F), uint32_t(i % F));
+      for (int64_t i = 0; i < nW2; ++i)
+        hp[nW1 + H + i] = s2 * gaussian(seed, 4u, 1u, uint32_t(i / H), uint32_t(i % H));
+      dalloc(&P, size_t(nparam));
+      dalloc(&G, size_t(nparam));
+      dalloc(&Mo, size_t(nparam));
+      dalloc(&Vo, size_t(nparam));
+      PF_CK(cudaMemcpyAsync(P, hp.data(), sizeof(float) * nparam, cudaMemcpyHostToDevice, s));
+      PF_CK(cudaMemsetAsync(Mo, 0, sizeof(float) * nparam, s));
+      PF_CK(cudaMemsetAsync(Vo, 0, sizeof(float) * nparam, s));
+      dalloc(&h, size_t(Bt) * H);
+      dalloc(&z, size_t(Bt) * C);
+      dalloc(&dz, size_t(Bt) * C);
+      dalloc(&dh, size_t(Bt) * H);
+      const int nb = int((Qt + Bt - 1) / Bt);
+      dalloc(&losses, size_t(nb));
+      float *W1 = P, *b1 = P + nW1, *W2 = b1 + H, *b2 = W2 + nW2;
+      float *gW1 = G, *gb1 = G + nW1, *gW2 = gb1 + H, *gb2 = gW2 + nW2;
+      std::mt19937_64 rng(seed ^ 0x5DEECE66DULL);
+      std::vector<int32_t> order(Qt);
+      std::iota(order.begin(), order.end(), 0);
+      int t = 0;
+      float last_loss = 0.f;
+      for (int ep = 0; ep < epochs; ++ep) {
+        std::shuffle(order.begin(), order.end(), rng);
+        PF_CK(cudaMemcpyAsync(perm, order.data(), sizeof(int32_t) * Qt, cudaMemcpyHostToDevice, s));
+        PF_CK(gather_rows(X, perm, int(Qt), F, Xp, s));
+        PF_CK(gather_rows(reinterpret_cast<const float*>(y), perm, int(Qt), 1, reinterpret_cast<float*>(yp), s));
+        for (int b = 0; b < nb; ++b) {
+          const int B = int(std::min<int64_t>(Bt, Qt - int64_t(b) * Bt));
+          PF_CK(mlp_forward_backward(Xp + size_t(b) * Bt * F, yp + size_t(b) * Bt, B, F, H, C, W1, b1, W2, b2,
+                                     losses + b, gW1, gb1, gW2, gb2, h, z, dz, dh, s));
+          PF_CK(adam_step(P, G, Mo, Vo, nparam, 1e-3f, ++t, s));
+        }
+        if (ep == epochs - 1) {
+          std::vector<float> hl(nb);
+          PF_CK(cudaMemcpyAsync(hl.data(), losses, sizeof(float) * nb, cudaMemcpyDeviceToHost, s));
+          PF_CK(cudaStreamSynchronize(s));
+          double sum = 0.0, wsum = 0.0;
+          for (int b = 0; b < nb; ++b) {
+            const double wgt = double(std::min<int64_t>(Bt, Qt - int64_t(b) * Bt));
+            sum += hl[b] * wgt;
+            wsum += wgt;
+          }
+          last_loss = float(sum / wsum);
+        }
+      }
+      dalloc(&w1h, size_t(nW1));
+      dalloc(&w2h, size_t(nW2));
+      PF_CK(to_bf16(W1, w1h, nW1, s));
+      PF_CK(to_bf16(W2, w2h, nW2, s));
+      PF_CK(cudaStreamSynchronize(s));
+      // install the model
+      dfree(ix->mlp_w);
+      dfree(ix->mlp_w1h);
+      dfree(ix->mlp_w2h);
+      ix->mlp_w = P;
+      P = nullptr;
+      ix->mlp_w1h = w1h;
+      w1h = nullptr;
+      ix->mlp_w2h = w2h;
+      w2h = nullptr;
+      ix->mlp_F = F;
+      ix->mlp_C = C;
+      ix->mlp_trained = 1;
+      if (report) {
+        // predicted start depths on the training queries
+        int64_t covered = 0;
+        double sum_start = 0.0, sum_stop = 0.0;
+        std::vector<int32_t> sd(chunk);
+        for (int64_t q0 = 0; q0 < Qt; q0 += chunk) {
+          const int64_t nq = std::min(chunk, Qt - q0);
+          const float* qd = stage_queries(ix, train_queries + size_t(q0) * ix->d, nq, s);
+          hash_queries_ws(ix, qd, nq, s);
+          predict_ws(ix, nq, s);
+          PF_CK(cudaMemcpyAsync(sd.data(), ws.start, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, s));
+          PF_CK(cudaStreamSynchronize(s));
+          for (int64_t i = 0; i < nq; ++i) {
+            covered += sd[i] >= hy[q0 + i] ? 1 : 0;
+            sum_start += sd[i];
+            sum_stop += hy[q0 + i];
+          }
+        }
+        report->final_loss = last_loss;
+        report->train_accuracy = float(double(covered) / double(Qt));
+        report->mean_stop = float(sum_stop / double(Qt));
+        report->mean_start = float(sum_start / double(Qt));
+        report->samples = int32_t(Qt);
+        report->epochs = epochs;
+      }
+    } catch (...) {
+      cudaStreamSynchronize(s);
+      cleanup();
+      throw;
+    }
+    cleanup();
+    return PF_OK;
+  });
+}
+
+pf_status pf_learned_predict(pf_index* ix, const float* queries, int64_t Q, int32_t* start_depth, void* stream) {
+  return guarded([&]() -> pf_status {
+    if (!ix) return fail(PF_ERR_INVALID_ARG, "null index");
+    if (!ix->mlp_trained) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
+    if (Q < 0 || Q > 0x7fffffffLL) return fail(PF_ERR_INVALID_ARG, "Q out of range");
+    if (Q == 0) return PF_OK;
+    if (!queries || !start_depth) return fail(PF_ERR_INVALID_ARG, "null argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PF_CK(cudaSetDevice(ix->device));
+    ensure_ws(ix, Q, 1);
+    const float* qd = stage_queries(ix, queries, Q, s);
+    hash_queries_ws(ix, qd, Q, s);
+    predict_ws(ix, Q, s);
+    PF_CK(cudaMemcpyAsync(start_depth, ix->ws.start, sizeof(int32_t) * size_t(Q), cudaMemcpyDefault, s));
     PF_CK(cudaStreamSynchronize(s));
     return PF_OK;
   });

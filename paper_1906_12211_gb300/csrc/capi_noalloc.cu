@@ -86,7 +86,8 @@ extern "C" pf_status pf_index_search_noalloc(pf_index* ix, const float* queries,
     pf_search_opts_default(&o);
     if (opts) o = *opts;
     if (o.scoring != 0 && o.scoring != 1) return reject(PF_ERR_INVALID_ARG, "scoring must be 0 or 1");
-    if (o.learned_start) return reject(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
+    if (o.learned_start)
+      return reject(PF_ERR_INVALID_ARG, "the learned start depth needs pf_index_search (it uses the index workspace)");
     const size_t need = scratch_bytes(ix, Q);
     if (need > kScratchBytes) {
       const size_t per_q = size_t(ix->lay.d_pad) * 8 + size_t(ix->L) * 4 + size_t(ix->M) * 8;

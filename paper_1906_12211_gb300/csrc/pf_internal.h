@@ -18,6 +18,8 @@ constexpr int kAlphaSteps = 41;                     // Sec. 4.3: similarity grid
 constexpr int kMaxK = 128;
 constexpr int kMaxD = 256;
 constexpr int kMaxL = 2048;
+constexpr int kMlpHidden = 256;                     // start-depth model hidden units
+constexpr float kMlpTail = 0.05f;                   // start where P(stop depth > start) <= this
 
 enum Purpose : uint32_t { kPurposeHash = 1, kPurposeSketch = 2, kPurposeCpMc = 3 };
 
@@ -104,6 +106,12 @@ struct pf_index {
   int32_t* dev_error = nullptr;    // device error word (bit 1: a bounded wait timed out)
   int num_sms = 0;
   pf_workspace ws;
+  // start-depth model: params = [W1 (H x F) | b1 (H) | W2 (C x H) | b2 (C)], float32
+  int mlp_trained = 0, mlp_F = 0, mlp_C = 0;
+  float* mlp_w = nullptr;
+  __nv_bfloat16* mlp_w1h = nullptr;  // bfloat16 W1 for inference
+  __nv_bfloat16* mlp_w2h = nullptr;  // bfloat16 W2 for inference
+  float* mlp_x = nullptr;            // [cap_q][F] feature scratch of the search path
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // phase timing events
   float last_ms[3] = {0.f, 0.f, 0.f};
 };
@@ -154,5 +162,18 @@ struct SearchArgs {
   int32_t* counter = nullptr;
 };
 cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t s);
+
+// start-depth perceptron (kernels_mlp.cu)
+cudaError_t mlp_features(const float* qx, const uint64_t* qsk, int Q, int d_pad, int M, float* x, cudaStream_t s);
+cudaError_t mlp_forward_backward(const float* X, const int32_t* y, int B, int F, int H, int C, const float* W1,
+                                 const float* b1, const float* W2, const float* b2, float* loss, float* dW1,
+                                 float* db1, float* dW2, float* db2, float* h, float* z, float* dz, float* dh,
+                                 cudaStream_t s);
+cudaError_t adam_step(float* w, const float* g, float* m, float* v, int64_t count, float lr, int t, cudaStream_t s);
+cudaError_t to_bf16(const float* a, __nv_bfloat16* b, int64_t count, cudaStream_t s);
+cudaError_t mlp_predict(const float* qx, const uint64_t* qsk, int Q, int d_pad, int M, const __nv_bfloat16* W1,
+                        const float* b1, const __nv_bfloat16* W2, const float* b2, int C, float tail, int32_t* start,
+                        cudaStream_t s);
+cudaError_t gather_rows(const float* src, const int32_t* idx, int rows, int cols, float* dst, cudaStream_t s);
 
 }  // namespace pf
