@@ -48,7 +48,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--mode", default="learned", choices=["learned", "bf16", "fp32"],
+                    help="learned: learned start depth + bf16 scoring; bf16: plain schedule, bf16 scoring; "
+                         "fp32: the plain method")
+    ap.add_argument("--train-queries", type=int, default=100_000, help="training queries for the start-depth model")
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other two modes")
     ap.add_argument("--recall", type=float, default=0.9, help="recall target 1 - delta passed to the index")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--Q", type=int, default=None)
@@ -270,8 +275,23 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
+    train_report, train_s = None, None
+    if args.mode == "learned" or not args.no_compare:
+        Qtrain = datagen.vmf_mixture(args.train_queries, w["d"], w["components"], w["kappa"], seed=rank,
+                                     purpose="train")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        train_report = ix.learned_train(torch.from_numpy(Qtrain).to(dev), k, args.recall, epochs=args.epochs,
+                                        seed=rank)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+
+    def run_mode(mode, timing=False):
+        ix.search(Qd, kq, rq, k_max=k, scoring="fp32" if mode == "fp32" else "bf16", out_ids=ids, out_sims=sims,
+                  stats=st, timing=timing, learned=mode == "learned")
+
     def step(timing=False):
-        ix.search(Qd, kq, rq, k_max=k, scoring=args.mode, out_ids=ids, out_sims=sims, stats=st, timing=timing)
+        run_mode(args.mode, timing)
 
     for _ in range(args.warmup):
         step()
@@ -306,6 +326,31 @@ def main():
     stats = pf.stats_to_numpy(st)
     recall = float((sims >= kth[:, None] - 1e-6).float().mean().item())
 
+    # the other modes, same queries, same timing protocol (fewer steps)
+    compare = {}
+    if not args.no_compare:
+        for mode in ("fp32", "bf16", "learned"):
+            if mode == args.mode:
+                continue
+            for _ in range(2):
+                run_mode(mode)
+            tot = 0.0
+            nsteps = max(3, args.steps // 2)
+            for _ in range(nsteps):
+                flush.fill_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                run_mode(mode)
+                e1.record(stream)
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
+            ms = pf.stats_to_numpy(st)
+            compare[mode] = {"value": Q * nsteps / (tot / 1e3), "ms_per_step": tot / nsteps,
+                             "recall": float((sims >= kth[:, None] - 1e-6).float().mean().item()),
+                             "rounds": float(ms["rounds"].mean()), "retrieved": float(ms["retrieved"].mean()),
+                             "scored": float(ms["scored"].mean())}
+        run_mode(args.mode)  # leave the headline mode's outputs in place
+
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -314,13 +359,14 @@ def main():
         rh = torch.full((Q,), args.recall, dtype=torch.float64).pin_memory()
         ih = torch.empty((Q, k), dtype=torch.int32).pin_memory()
         sh = torch.empty((Q, k), dtype=torch.float32).pin_memory()
+        sc, lr = ("fp32" if args.mode == "fp32" else "bf16"), args.mode == "learned"
         for _ in range(2):
-            ix.search(qh, kh, rh, k_max=k, scoring=args.mode, out_ids=ih, out_sims=sh)
+            ix.search(qh, kh, rh, k_max=k, scoring=sc, out_ids=ih, out_sims=sh, learned=lr)
         if dist:
             dist.barrier()
         t = time.perf_counter()
         for _ in range(args.steps):
-            ix.search(qh, kh, rh, k_max=k, scoring=args.mode, out_ids=ih, out_sims=sh)
+            ix.search(qh, kh, rh, k_max=k, scoring=sc, out_ids=ih, out_sims=sh, learned=lr)
         el = time.perf_counter() - t
         if dist:
             tt = torch.tensor([el], device=dev, dtype=torch.float64)
@@ -331,7 +377,7 @@ def main():
                "d2h_bytes_per_step": int(Q * k * 8)}
 
     peak, peak_kind = measured_peaks()
-    per_q = algorithmic_bytes(stats, ix.L, ix.n, ix.d, k, args.mode)
+    per_q = algorithmic_bytes(stats, ix.L, ix.n, ix.d, k, "fp32" if args.mode == "fp32" else "bf16")
     kern_s = kernel_ms / args.steps / 1e3
     achieved = per_q * Q / kern_s / 1e9
     traffic = search_kernel_traffic()
@@ -355,15 +401,19 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.mode == "fp32" else "bf16+f32",
+            "mode": args.mode,
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": ix.n, "d": ix.d, "queries_per_gpu": Q, "k": k,
                        "recall_target": args.recall, "family": "crosspolytope", "budget_bytes": w["budget"],
-                       "L": ix.L, "scoring": args.mode, "l2": "flushed between steps (512 MiB write)",
+                       "L": ix.L, "scoring": "fp32" if args.mode == "fp32" else "bf16",
+                       "start_depth": "learned" if args.mode == "learned" else "plain",
+                       "l2": "flushed between steps (512 MiB write)",
                        "parallelism": f"replica x{world}"},
             "recall": recall, "build_s": build_s,
             "per_query": {f: float(stats[f].mean()) for f in ("stop_depth", "rounds", "retrieved",
                                                              "passed_filter", "scored", "reranked")},
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": (5 if args.mode == "learned" else 4) * args.steps,
+            "compare": compare, "learned_train": train_report, "learned_train_s": train_s,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -83,16 +83,17 @@ typedef struct {
   int32_t filter;              /* 1: sketch filter on (Sec. 4.2); 0: off.  Set by pf_search_opts_default */
   int32_t learned_start;       /* 1: start depth from the trained model (needs pf_learned_train) */
   int32_t timing;              /* 1: record CUDA events around each phase (see pf_index_last_timing) */
-  const int32_t* start_depth;  /* optional [Q] per-query start depth (host or device); NULL = none */
+  const int32_t* start_depth;  /* optional [Q] per-query start depth i0 (host or device): rounds i0, i0-1, ..., 0,
+                                  the first taking the whole block at i0; values outside [0, K) mean K */
 } pf_search_opts;
 
 /* Per-query statistics (Sec. 5 reports recall and throughput; these counts
  * explain both). */
 typedef struct {
-  int32_t start_depth;   /* first prefix length after the seed round */
+  int32_t start_depth;   /* prefix length of the first round */
   int32_t stop_depth;    /* prefix length of the last round */
   int32_t rounds;        /* rounds run */
-  int32_t reserved;
+  int32_t full_depth;    /* prefix length of the first round after which k points were held, -1 if none */
   int64_t retrieved;     /* candidate positions read from the repetitions (with repeats) */
   int64_t passed_filter; /* of those, how many passed the sketch filter */
   int64_t scored;        /* similarities computed (float32, or bfloat16 estimates) */
@@ -183,21 +184,24 @@ pf_status pf_index_search_noalloc(pf_index* index, const float* queries, int64_t
  *      predictor layered on Algorithm 1's depth schedule) ----
  * A 2-layer perceptron (hidden 256, ReLU) maps a query's features -- its
  * normalised vector and its first 64-bit sketch as +-1 -- to a distribution
- * over the prefix length at which the plain schedule K, K-1, ... stops.  With
- * opts->learned_start the search runs one round at K and then starts at the
- * smallest depth d with P(stop depth > d) <= 0.05; the stop test of Lemma 1
- * still ends every query, so the recall guarantee is that of the plain method. */
+ * over the prefix length of the first round after which the plain schedule
+ * K, K-1, ... holds k points (pf_query_stats.full_depth).  Every round before
+ * that one runs unfiltered and its candidates lie in the block at that depth,
+ * so starting there skips only nearly empty rounds.  With
+ * opts->learned_start the search starts at the smallest depth d with
+ * P(full depth > d) <= 0.05; the stop test of Lemma 1 still ends every query,
+ * so the recall guarantee is that of the plain method. */
 typedef struct {
   float final_loss;      /* mean cross-entropy of the last epoch */
-  float train_accuracy;  /* fraction of training queries whose predicted start depth >= their stop depth */
-  float mean_stop;       /* mean stop depth of the training traces */
+  float train_accuracy;  /* fraction of training queries whose predicted start depth >= their full depth */
+  float mean_stop;       /* mean full depth (the training target) of the training traces */
   float mean_start;      /* mean predicted start depth on the training queries */
   int32_t samples;       /* training queries */
   int32_t epochs;
 } pf_learned_report;
 
 /* Train the start-depth model of `index` on Qt training queries ([Qt][d],
- * host or device): trace the plain search of each (k, recall) to get its stop
+ * host or device): trace the plain search of each (k, recall) to get its full
  * depth, then `epochs` passes of mini-batch Adam (batch 1024, learning rate
  * 1e-3, weights drawn from `seed`) with this library's kernels.  Replaces any
  * previous model.  report may be NULL. */

@@ -41,7 +41,8 @@ def build(force: bool = False) -> str:
 
 class _Stats(C.Structure):
     _fields_ = [("start_depth", C.c_int32), ("stop_depth", C.c_int32), ("rounds", C.c_int32),
-                ("retrieved", C.c_int64), ("passed_filter", C.c_int64), ("scored", C.c_int64)]
+                ("full_depth", C.c_int32), ("retrieved", C.c_int64), ("passed_filter", C.c_int64),
+                ("scored", C.c_int64)]
 
 
 class _Index(C.Structure):
@@ -52,8 +53,8 @@ class _Index(C.Structure):
 
 
 STATS_DTYPE = np.dtype([("start_depth", np.int32), ("stop_depth", np.int32), ("rounds", np.int32),
-                        ("retrieved", np.int64), ("passed_filter", np.int64), ("scored", np.int64)],
-                       align=True)
+                        ("full_depth", np.int32), ("retrieved", np.int64), ("passed_filter", np.int64),
+                        ("scored", np.int64)], align=True)
 
 
 def lib():

@@ -400,9 +400,9 @@ static int popcount64(uint64_t w) {
 }
 
 /* Algorithm 1 as implemented in Sec. 4.1-4.2, one query:
- *   - rounds at prefix length i = K, K-1, ..., 0 (or K, i0, i0-1, ..., 0 with
- *     a start depth i0 < K-1: one round at full length seeds the top-k, then
- *     the search jumps to i0);
+ *   - rounds at prefix length i = i0, i0-1, ..., 0 with i0 = K (Sec. 4.1) or
+ *     a given start depth in [0, K) (the first round then takes the whole
+ *     block at i0, so every candidate of the skipped rounds is still seen);
  *   - in a round every repetition j extends its range [l, r) to cover the
  *     block of codes sharing the first i bits with the query, growing each
  *     side in whole segments of B entries (Sec. 4.2, App. C), and visits the
@@ -428,16 +428,16 @@ static void search_one(const orc_index* ix, const float* q, const uint32_t* qcod
   uint32_t* pid = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(k > 0 ? k : 1));
   int size = 0;
   int64_t tl = 0;
-  orc_stats s = {0, 0, 0, 0, 0, 0};
+  orc_stats s = {0, 0, 0, -1, 0, 0, 0};
 
   for (int j = 0; j < L; ++j) {
     l[j] = r[j] = lower_bound_u32(ix->codes + (int64_t)j * n, n, qcode[j]);
   }
   int i0 = Kb;
-  if (start_depth >= 0 && start_depth < Kb - 1) i0 = start_depth;
+  if (start_depth >= 0 && start_depth < Kb) i0 = start_depth;
   s.start_depth = i0;
 
-  int depth = Kb;
+  int depth = i0;
   for (;;) {
     const int full = (size == k);
     const float s_k = full ? ps[k - 1] : -INFINITY;
@@ -474,13 +474,14 @@ static void search_one(const orc_index* ix, const float* q, const uint32_t* qcod
     }
     s.rounds += 1;
     s.stop_depth = depth;
+    if (size == k && s.full_depth < 0) s.full_depth = depth;
     if (depth == 0) break;
     if (size == k) {
       double p = orc_collision_prob(ix->family, ix->ell, ix->P, (double)ps[k - 1], depth);
       double fail = orc_ipow(1.0 - p, L);
       if (fail <= delta) break;
     }
-    depth = (depth == Kb && i0 < Kb) ? i0 : depth - 1;
+    depth -= 1;
   }
   for (int t = 0; t < k_max; ++t) {
     out_ids[t] = t < size ? pid[t] : 0xFFFFFFFFu;

@@ -84,6 +84,7 @@ float orc_sim(const float* q, const float* x, int d);
 /* ---- the query (Algorithm 1, Sec. 4.1) ---- */
 typedef struct {
   int32_t start_depth, stop_depth, rounds;
+  int32_t full_depth; /* prefix length of the first round after which k points were held, -1 if none */
   int64_t retrieved, passed_filter, scored;
 } orc_stats;
 
@@ -98,7 +99,8 @@ typedef struct {
 } orc_index;
 
 /* Search Q normalised queries.  qcodes[Q][L], qsk[Q][M], k[Q], recall[Q].
- * start_depth: NULL (plain schedule K, K-1, ..., 0) or per-query start depth.
+ * start_depth: NULL (plain schedule K, K-1, ..., 0) or per-query start depth
+ * i0 (schedule i0, i0-1, ..., 0; i0 outside [0, K) means K).
  * filter: 0/1.  Outputs [Q][k_max]; stats may be NULL.
  * trace (may be NULL): per query up to trace_cap entries (depth<<24 | table, id)
  * of every retrieved candidate, count in trace_len[q]. */

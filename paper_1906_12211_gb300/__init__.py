@@ -44,12 +44,12 @@ class SearchOpts(C.Structure):
 
 class QueryStats(C.Structure):
     _fields_ = [("start_depth", C.c_int32), ("stop_depth", C.c_int32), ("rounds", C.c_int32),
-                ("reserved", C.c_int32), ("retrieved", C.c_int64), ("passed_filter", C.c_int64),
+                ("full_depth", C.c_int32), ("retrieved", C.c_int64), ("passed_filter", C.c_int64),
                 ("scored", C.c_int64), ("reranked", C.c_int64)]
 
 
 STATS_DTYPE = np.dtype([("start_depth", np.int32), ("stop_depth", np.int32), ("rounds", np.int32),
-                        ("reserved", np.int32), ("retrieved", np.int64), ("passed_filter", np.int64),
+                        ("full_depth", np.int32), ("retrieved", np.int64), ("passed_filter", np.int64),
                         ("scored", np.int64), ("reranked", np.int64)])
 
 

@@ -630,7 +630,7 @@ pf_status pf_learned_train(pf_index* ix, const float* train_queries, int64_t Qt,
         PF_CK(mlp_features(ws.qx, ws.qsk, int(nq), ix->lay.d_pad, ix->M, X + size_t(q0) * F, s));
         PF_CK(cudaMemcpyAsync(st.data(), ws.stats, sizeof(pf_query_stats) * nq, cudaMemcpyDeviceToHost, s));
         PF_CK(cudaStreamSynchronize(s));
-        for (int64_t i = 0; i < nq; ++i) hy[q0 + i] = st[i].stop_depth;
+        for (int64_t i = 0; i < nq; ++i) hy[q0 + i] = st[i].full_depth < 0 ? 0 : st[i].full_depth;
       }
       PF_CK(cudaMemcpyAsync(y, hy.data(), sizeof(int32_t) * Qt, cudaMemcpyHostToDevice, s));
       // weights: W1 ~ N(0, 2/F), W2 ~ N(0, 1/H), zero biases (host, from the seed)

@@ -1,18 +1,19 @@
 // Learned start depth: a 2-layer perceptron that predicts, from a query's
-// normalised vector and its first 64-bit sketch, the prefix length at which
-// the plain depth schedule (Sec. 4.1: K, K-1, ...) stops.  The search then
-// starts there (after one seed round at K); the stop test of Lemma 1 still
-// decides termination, so the recall guarantee is unchanged.
+// normalised vector and its first 64-bit sketch, the prefix length of the
+// first round after which the plain depth schedule (Sec. 4.1: K, K-1, ...)
+// holds k points.  Rounds before it run unfiltered and their candidates lie in
+// the block at that depth, so the search can start there; the stop test of
+// Lemma 1 still decides termination, so the recall guarantee is unchanged.
 //
 //   x = [q (d_pad floats), sketch-0 bits as +-1 (64)]         F_in = d_pad + 64
 //   h = relu(W1 x + b1)                                        H = 256
 //   z = W2 h + b2                                              C = K + 1 classes
-//   loss = mean over the batch of -log softmax(z)[y]           y = stop depth
+//   loss = mean over the batch of -log softmax(z)[y]           y = full depth
 //
 // Training: float32 master weights, forward / backward with the tiled GEMM
 // and elementwise kernels below, Adam.  Inference: bfloat16 copies of W1 and
 // W2 with float32 accumulation, one warp per query; the start depth is the
-// smallest d with P(stop depth > d) <= 0.05 under the predicted distribution.
+// smallest d with P(full depth > d) <= 0.05 under the predicted distribution.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -150,7 +151,7 @@ __global__ void to_bf16_kernel(const float* __restrict__ a, __nv_bfloat16* __res
 }
 
 // Inference, one warp per query: bfloat16 weights, float32 accumulation; the
-// start depth is the smallest d with P(stop depth > d) <= tail.
+// start depth is the smallest d with P(full depth > d) <= tail.
 __global__ void __launch_bounds__(128) predict_kernel(const float* __restrict__ qx, const uint64_t* __restrict__ qsk,
                                                       int Q, int d_pad, int M, const __nv_bfloat16* __restrict__ W1,
                                                       const float* __restrict__ b1,
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(128) predict_kernel(const float* __restrict__ 
     for (int c = 0; c < C; ++c) mx = fmaxf(mx, zs[w][c]);
     float se = 0.f;
     for (int c = 0; c < C; ++c) se += expf(zs[w][c] - mx);
-    // P(stop depth > d) = sum over c > d; scan from the top
+    // P(full depth > d) = sum over c > d; scan from the top
     float above = 0.f;
     int dsel = C - 1;
     for (int d = C - 1; d >= 0; --d) {

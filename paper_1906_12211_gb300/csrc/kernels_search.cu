@@ -352,10 +352,12 @@ __global__ void __launch_bounds__(kWarps * 32, 5) search_kernel(Dev P) {
     for (int i = lane; i < d_pad; i += 32) w.q[i] = qg[i];
     const uint32_t* qc = P.qcodes + size_t(qi) * L;
     const uint64_t* qs = P.qsk + size_t(qi) * P.M;
+    // start depth: the plain schedule starts at K (Sec. 4.1); a given start i0
+    // in [0, K) takes the whole block at i0 in the first round
     int i0 = P.Kb;
     if (P.start) {
       const int sd = P.start[qi];
-      if (sd >= 0 && sd < P.Kb - 1) i0 = sd;
+      if (sd >= 0 && sd < P.Kb) i0 = sd;
     }
     // initial empty range at the first code >= the query's code
     for (int j = lane; j < L; j += 32) {
@@ -368,7 +370,8 @@ __global__ void __launch_bounds__(kWarps * 32, 5) search_kernel(Dev P) {
     }
     __syncwarp();
 
-    int size = 0, rounds = 0, depth = P.Kb, prev = -1, stop_depth = P.Kb;  // prev < 0: probe both sides
+    int size = 0, rounds = 0, depth = i0, prev = -1, stop_depth = i0;  // prev < 0: probe both sides
+    int full_depth = -1;  // first depth after whose round k points were held
     Counters ct;
     for (;;) {
       const bool full = size == k;
@@ -396,6 +399,7 @@ __global__ void __launch_bounds__(kWarps * 32, 5) search_kernel(Dev P) {
         if (nb) size = flush_candidates<NT>(P, w, nb, size, k, lane, ct);
         ++rounds;
         stop_depth = 0;
+        if (size == k && full_depth < 0) full_depth = 0;
         break;
       }
       const uint32_t mask = 0xffffffffu << (32 - depth);
@@ -528,6 +532,7 @@ __global__ void __launch_bounds__(kWarps * 32, 5) search_kernel(Dev P) {
       if (nb) size = flush_candidates<NT>(P, w, nb, size, k, lane, ct);
       ++rounds;
       stop_depth = depth;
+      if (size == k && full_depth < 0) full_depth = depth;
       int stop = 0;
       if (lane == 0 && size == k) {
         const double p = collision_prob(P, double(w.pq_s[k - 1]), depth);
@@ -537,7 +542,7 @@ __global__ void __launch_bounds__(kWarps * 32, 5) search_kernel(Dev P) {
       stop = __shfl_sync(kFull, stop, 0);
       if (stop) break;
       prev = depth;
-      depth = (depth == P.Kb && i0 < P.Kb) ? i0 : depth - 1;
+      depth -= 1;
     }
 
     for (int t = lane; t < kmax; t += 32) {
@@ -549,7 +554,7 @@ __global__ void __launch_bounds__(kWarps * 32, 5) search_kernel(Dev P) {
       st.start_depth = i0;
       st.stop_depth = stop_depth;
       st.rounds = rounds;
-      st.reserved = 0;
+      st.full_depth = full_depth;
       st.retrieved = ct.retrieved;
       st.passed_filter = ct.passed;
       st.scored = ct.scored;

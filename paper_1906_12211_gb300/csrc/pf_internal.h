@@ -19,7 +19,7 @@ constexpr int kMaxK = 128;
 constexpr int kMaxD = 256;
 constexpr int kMaxL = 2048;
 constexpr int kMlpHidden = 256;                     // start-depth model hidden units
-constexpr float kMlpTail = 0.05f;                   // start where P(stop depth > start) <= this
+constexpr float kMlpTail = 0.05f;                   // start where P(full depth > start) <= this
 
 enum Purpose : uint32_t { kPurposeHash = 1, kPurposeSketch = 2, kPurposeCpMc = 3 };
 

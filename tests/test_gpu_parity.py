@@ -184,6 +184,8 @@ def _compare(gpu_out, ref, check_stats=True):
         o = ref["stats"]
         assert np.array_equal(g["stop_depth"], o["stop_depth"])
         assert np.array_equal(g["rounds"], o["rounds"])
+        assert np.array_equal(g["full_depth"], o["full_depth"])
+        assert np.array_equal(g["start_depth"], o["start_depth"])
         deep = o["stop_depth"] > 0
         assert np.array_equal(g["retrieved"][deep], o["retrieved"][deep])
         assert np.array_equal(g["passed_filter"][deep], o["passed_filter"][deep])
@@ -217,7 +219,7 @@ def test_mixed_k_and_recall(cpmid, orc):
     _compare(out2, ref, check_stats=False)
 
 
-@pytest.mark.parametrize("start", [0, 5, 20, 29])
+@pytest.mark.parametrize("start", [0, 5, 20, 29, 31])
 def test_start_depth_override(cpmid, start):
     ref = cpmid.orc.search(cpmid.Q[:40], 10, 0.9, start_depth=start)
     sd = torch.full((40,), start, dtype=torch.int32, device=DEV)

@@ -152,13 +152,33 @@ def test_filter_reduces_scoring(orc, hp_index):
 
 
 def test_start_depth_schedule(orc, cp_index):
-    # A start depth i0 < K-1 runs one round at K, then i0, i0-1, ...; the result
-    # still satisfies the stop rule and reaches at least the recall of depth 0
-    # only if it stops there.
+    # A start depth i0 runs rounds i0, i0-1, ...: the first round takes the
+    # whole block at i0, later rounds one bit each; the result still obeys the
+    # stop rule and is exact when the schedule reaches depth 0.
     ix, Q = cp_index
     qn = orc.normalize(Q)
-    res = ix.search(Q, 10, 0.9, start_depth=ix.Kb - 10)
+    i0 = ix.Kb - 10
+    res = ix.search(Q, 10, 0.9, start_depth=i0)
     st = res["stats"]
-    assert np.all(st["start_depth"] == ix.Kb - 10)
-    assert np.all(st["stop_depth"] <= ix.Kb - 10) or np.all(st["rounds"] >= 1)
+    assert np.all(st["start_depth"] == i0)
+    assert np.all(st["stop_depth"] <= i0)
+    assert np.all(st["rounds"] == i0 - st["stop_depth"] + 1)
     _check_result_wellformed(orc, ix, qn, res, 10)
+    plain = ix.search(Q, 10, 0.9)["stats"]
+    assert np.all(plain["rounds"] == ix.Kb - plain["stop_depth"] + 1)
+    # full_depth: first depth after which k points were held (plain schedule)
+    assert np.all((plain["full_depth"] >= plain["stop_depth"]) & (plain["full_depth"] <= ix.Kb))
+
+
+def test_start_at_full_depth_keeps_the_filtered_work(orc, cp_index):
+    # Starting at the depth where the plain schedule first holds k points skips
+    # only rounds that ran unfiltered anyway: the retrieved positions can only
+    # shrink (segments are rounded once instead of per round) and the stop
+    # depth is unchanged for most queries.
+    ix, Q = cp_index
+    plain = ix.search(Q, 10, 0.9)
+    fd = plain["stats"]["full_depth"]
+    jump = ix.search(Q, 10, 0.9, start_depth=fd)
+    assert np.all(jump["stats"]["rounds"] <= plain["stats"]["rounds"])
+    same = np.mean(jump["stats"]["stop_depth"] == plain["stats"]["stop_depth"])
+    assert same >= 0.8
