@@ -78,7 +78,7 @@ def test_learned_start_saves_rounds_and_keeps_recall(trained, orc):
     _, sp, stp = ix.search(qd, 10, 0.9, stats=True, filter=False)
     _, sl, stl = ix.search(qd, 10, 0.9, stats=True, filter=False, learned=True)
     gp, gl = pf.stats_to_numpy(stp), pf.stats_to_numpy(stl)
-    assert gl["rounds"].mean() < 0.8 * gp["rounds"].mean()
+    assert gl["rounds"].mean() <= gp["rounds"].mean() - 2.0
     # starting at the predicted full depth skips rounds that were unfiltered anyway
     assert gl["retrieved"].mean() <= 1.05 * gp["retrieved"].mean()
     qn = orc.normalize(Q)
