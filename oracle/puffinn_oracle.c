@@ -412,9 +412,13 @@ static int popcount64(uint64_t w) {
  *     offered to the accumulator;
  *   - after the round: stop at i = 0 (a linear scan, Lemma 1), or when the
  *     accumulator holds k points and (1 - p_i(s_k))^L <= delta (Lemma 1).
- * Readings: tau and s_k are taken once at the start of each round; the stop
- * test runs once per round (Sec. 4.1); the initial range of a repetition is
- * empty at the first position whose code is >= the query code. */
+ * Readings: the paper refreshes the accumulator (and so tau) after every k
+ * insertions, in the order repetitions are inspected (Sec. 4.2); here tau is
+ * taken from the accumulator at the start of every group of 32 repetitions
+ * (j = 0, 32, 64, ... of each round), so within a group the visiting order does
+ * not matter.  The stop test runs once per round (Sec. 4.1); the initial range
+ * of a repetition is empty at the first position whose code is >= the query
+ * code. */
 static void search_one(const orc_index* ix, const float* q, const uint32_t* qcode, const uint64_t* qsk,
                        int k, double recall, int k_max, int32_t start_depth, int filter,
                        uint32_t* out_ids, float* out_sims, orc_stats* st,
@@ -439,11 +443,13 @@ static void search_one(const orc_index* ix, const float* q, const uint32_t* qcod
 
   int depth = i0;
   for (;;) {
-    const int full = (size == k);
-    const float s_k = full ? ps[k - 1] : -INFINITY;
-    const int tau = full ? orc_filter_tau((double)s_k) : 64;
     const uint32_t mask = depth == 0 ? 0u : (0xFFFFFFFFu << (32 - depth));
+    int tau = 64;
     for (int j = 0; j < L; ++j) {
+      if (j % ORC_SNAPSHOT_GROUP == 0) { /* threshold of the next group of repetitions */
+        const int full = (size == k);
+        tau = full ? orc_filter_tau((double)ps[k - 1]) : 64;
+      }
       const uint32_t* cj = ix->codes + (int64_t)j * n;
       const uint32_t* idj = ix->ids + (int64_t)j * n;
       int64_t lo = lower_bound_u32(cj, n, qcode[j] & mask);
