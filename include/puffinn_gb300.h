@@ -184,24 +184,23 @@ pf_status pf_index_search_noalloc(pf_index* index, const float* queries, int64_t
  *      predictor layered on Algorithm 1's depth schedule) ----
  * A 2-layer perceptron (hidden 256, ReLU) maps a query's features -- its
  * normalised vector and its first 64-bit sketch as +-1 -- to a distribution
- * over the prefix length of the first round after which the plain schedule
- * K, K-1, ... holds k points (pf_query_stats.full_depth).  Every round before
- * that one runs unfiltered and its candidates lie in the block at that depth,
- * so starting there skips only nearly empty rounds.  With
- * opts->learned_start the search starts at the smallest depth d with
- * P(full depth > d) <= 0.05; the stop test of Lemma 1 still ends every query,
- * so the recall guarantee is that of the plain method. */
+ * over the prefix length at which the plain schedule K, K-1, ... stops.  With
+ * opts->learned_start the search starts at min(K, q + 6), q the smallest depth
+ * with P(stop depth > q) <= 0.05: the first round takes the block at that depth
+ * at once (its sketch threshold refreshed every 32 repetitions), later rounds
+ * drop one bit each.  The stop test of Lemma 1 still ends every query, so the
+ * recall guarantee is that of the plain method. */
 typedef struct {
   float final_loss;      /* mean cross-entropy of the last epoch */
-  float train_accuracy;  /* fraction of training queries whose predicted start depth >= their full depth */
-  float mean_stop;       /* mean full depth (the training target) of the training traces */
+  float train_accuracy;  /* fraction of training queries whose predicted quantile >= their stop depth */
+  float mean_stop;       /* mean stop depth of the training traces */
   float mean_start;      /* mean predicted start depth on the training queries */
   int32_t samples;       /* training queries */
   int32_t epochs;
 } pf_learned_report;
 
 /* Train the start-depth model of `index` on Qt training queries ([Qt][d],
- * host or device): trace the plain search of each (k, recall) to get its full
+ * host or device): trace the plain search of each (k, recall) to get its stop
  * depth, then `epochs` passes of mini-batch Adam (batch 1024, learning rate
  * 1e-3, weights drawn from `seed`) with this library's kernels.  Replaces any
  * previous model.  report may be NULL. */

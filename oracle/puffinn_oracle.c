@@ -414,11 +414,12 @@ static int popcount64(uint64_t w) {
  *     accumulator holds k points and (1 - p_i(s_k))^L <= delta (Lemma 1).
  * Readings: the paper refreshes the accumulator (and so tau) after every k
  * insertions, in the order repetitions are inspected (Sec. 4.2); here tau is
- * taken from the accumulator at the start of every group of 32 repetitions
- * (j = 0, 32, 64, ... of each round), so within a group the visiting order does
- * not matter.  The stop test runs once per round (Sec. 4.1); the initial range
- * of a repetition is empty at the first position whose code is >= the query
- * code. */
+ * taken from the accumulator at the start of each round and, in a query's first
+ * round (which starts with an empty accumulator), also at the start of every
+ * group of 32 repetitions (j = 32, 64, ...), so within a group the visiting
+ * order does not matter.  The stop test runs once per round (Sec. 4.1); the
+ * initial range of a repetition is empty at the first position whose code is
+ * >= the query code. */
 static void search_one(const orc_index* ix, const float* q, const uint32_t* qcode, const uint64_t* qsk,
                        int k, double recall, int k_max, int32_t start_depth, int filter,
                        uint32_t* out_ids, float* out_sims, orc_stats* st,
@@ -446,7 +447,7 @@ static void search_one(const orc_index* ix, const float* q, const uint32_t* qcod
     const uint32_t mask = depth == 0 ? 0u : (0xFFFFFFFFu << (32 - depth));
     int tau = 64;
     for (int j = 0; j < L; ++j) {
-      if (j % ORC_SNAPSHOT_GROUP == 0) { /* threshold of the next group of repetitions */
+      if (j == 0 || (s.rounds == 0 && j % ORC_SNAPSHOT_GROUP == 0)) { /* threshold snapshot */
         const int full = (size == k);
         tau = full ? orc_filter_tau((double)ps[k - 1]) : 64;
       }

@@ -185,7 +185,7 @@ void predict_ws(pf_index* ix, int64_t Q, cudaStream_t s) {
   const float* b1 = ix->mlp_w + size_t(H) * F;
   const float* b2 = b1 + H + size_t(C) * H;
   PF_CK(mlp_predict(ix->ws.qx, ix->ws.qsk, int(Q), ix->lay.d_pad, ix->M, ix->mlp_w1h, b1, ix->mlp_w2h, b2, C,
-                    kMlpTail, ix->ws.start, s));
+                    kMlpTail, kMlpMargin, ix->ws.start, s));
 }
 
 const float* stage_queries(pf_index* ix, const float* queries, int64_t Q, cudaStream_t s) {
@@ -630,7 +630,7 @@ pf_status pf_learned_train(pf_index* ix, const float* train_queries, int64_t Qt,
         PF_CK(mlp_features(ws.qx, ws.qsk, int(nq), ix->lay.d_pad, ix->M, X + size_t(q0) * F, s));
         PF_CK(cudaMemcpyAsync(st.data(), ws.stats, sizeof(pf_query_stats) * nq, cudaMemcpyDeviceToHost, s));
         PF_CK(cudaStreamSynchronize(s));
-        for (int64_t i = 0; i < nq; ++i) hy[q0 + i] = st[i].full_depth < 0 ? 0 : st[i].full_depth;
+        for (int64_t i = 0; i < nq; ++i) hy[q0 + i] = st[i].stop_depth;
       }
       PF_CK(cudaMemcpyAsync(y, hy.data(), sizeof(int32_t) * Qt, cudaMemcpyHostToDevice, s));
       // weights: W1 ~ N(0, 2/F), W2 ~ N(0, 1/H), zero biases (host, from the seed)
@@ -714,7 +714,7 @@ pf_status pf_learned_train(pf_index* ix, const float* train_queries, int64_t Qt,
           PF_CK(cudaMemcpyAsync(sd.data(), ws.start, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, s));
           PF_CK(cudaStreamSynchronize(s));
           for (int64_t i = 0; i < nq; ++i) {
-            covered += sd[i] >= hy[q0 + i] ? 1 : 0;
+            covered += sd[i] - kMlpMargin >= hy[q0 + i] || sd[i] == ix->lay.Kb ? 1 : 0;
             sum_start += sd[i];
             sum_stop += hy[q0 + i];
           }

@@ -1,19 +1,21 @@
 // Learned start depth: a 2-layer perceptron that predicts, from a query's
-// normalised vector and its first 64-bit sketch, the prefix length of the
-// first round after which the plain depth schedule (Sec. 4.1: K, K-1, ...)
-// holds k points.  Rounds before it run unfiltered and their candidates lie in
-// the block at that depth, so the search can start there; the stop test of
-// Lemma 1 still decides termination, so the recall guarantee is unchanged.
+// normalised vector and its first 64-bit sketch, the prefix length at which
+// the plain depth schedule (Sec. 4.1: K, K-1, ...) stops.  The search starts a
+// few bits above a high quantile of that prediction: the first round takes the
+// block at the start depth at once (its sketch threshold refreshed every 32
+// repetitions), later rounds drop one bit each.  The stop test of Lemma 1 still
+// decides termination, so the recall guarantee is unchanged.
 //
 //   x = [q (d_pad floats), sketch-0 bits as +-1 (64)]         F_in = d_pad + 64
 //   h = relu(W1 x + b1)                                        H = 256
 //   z = W2 h + b2                                              C = K + 1 classes
-//   loss = mean over the batch of -log softmax(z)[y]           y = full depth
+//   loss = mean over the batch of -log softmax(z)[y]           y = stop depth
 //
 // Training: float32 master weights, forward / backward with the tiled GEMM
 // and elementwise kernels below, Adam.  Inference: bfloat16 copies of W1 and
-// W2 with float32 accumulation, one warp per query; the start depth is the
-// smallest d with P(full depth > d) <= 0.05 under the predicted distribution.
+// W2 with float32 accumulation, one warp per query; the start depth is
+// min(K, q + 6) with q the smallest d with P(stop depth > d) <= 0.05 under the
+// predicted distribution.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -151,13 +153,14 @@ __global__ void to_bf16_kernel(const float* __restrict__ a, __nv_bfloat16* __res
 }
 
 // Inference, one warp per query: bfloat16 weights, float32 accumulation; the
-// start depth is the smallest d with P(full depth > d) <= tail.
+// start depth is min(C - 1, q + margin), q the smallest d with
+// P(stop depth > d) <= tail.
 __global__ void __launch_bounds__(128) predict_kernel(const float* __restrict__ qx, const uint64_t* __restrict__ qsk,
                                                       int Q, int d_pad, int M, const __nv_bfloat16* __restrict__ W1,
                                                       const float* __restrict__ b1,
                                                       const __nv_bfloat16* __restrict__ W2,
                                                       const float* __restrict__ b2, int C, float tail,
-                                                      int32_t* __restrict__ start) {
+                                                      int margin, int32_t* __restrict__ start) {
   __shared__ float xs[4][kMaxD + 64];
   __shared__ float hs[4][kMlpHidden];
   __shared__ float zs[4][64];
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(128) predict_kernel(const float* __restrict__ 
     for (int c = 0; c < C; ++c) mx = fmaxf(mx, zs[w][c]);
     float se = 0.f;
     for (int c = 0; c < C; ++c) se += expf(zs[w][c] - mx);
-    // P(full depth > d) = sum over c > d; scan from the top
+    // P(stop depth > d) = sum over c > d; scan from the top
     float above = 0.f;
     int dsel = C - 1;
     for (int d = C - 1; d >= 0; --d) {
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(128) predict_kernel(const float* __restrict__ 
       dsel = d;
       above += expf(zs[w][d] - mx);
     }
-    start[q] = dsel;
+    start[q] = min(C - 1, dsel + margin);
   }
 }
 
@@ -254,10 +257,10 @@ cudaError_t to_bf16(const float* a, __nv_bfloat16* b, int64_t count, cudaStream_
 }
 
 cudaError_t mlp_predict(const float* qx, const uint64_t* qsk, int Q, int d_pad, int M, const __nv_bfloat16* W1,
-                        const float* b1, const __nv_bfloat16* W2, const float* b2, int C, float tail, int32_t* start,
-                        cudaStream_t s) {
+                        const float* b1, const __nv_bfloat16* W2, const float* b2, int C, float tail, int margin,
+                        int32_t* start, cudaStream_t s) {
   if (Q <= 0) return cudaSuccess;
-  predict_kernel<<<(Q + 3) / 4, 128, 0, s>>>(qx, qsk, Q, d_pad, M, W1, b1, W2, b2, C, tail, start);
+  predict_kernel<<<(Q + 3) / 4, 128, 0, s>>>(qx, qsk, Q, d_pad, M, W1, b1, W2, b2, C, tail, margin, start);
   return cudaGetLastError();
 }
 

@@ -16,10 +16,11 @@
 // the stop test of Lemma 1 runs in float64.
 //
 // Readings shared with the oracle: the sketch threshold is taken from the
-// top-k at the start of every group of 32 repetitions of a round (the paper
-// refreshes it every k insertions, Sec. 4.2; a group is one warp step, and all
-// candidates of the previous group have been offered by then); the stop test
-// runs once per round (Sec. 4.1); the
+// top-k at the start of each round and, in a query's first round (which starts
+// with an empty top-k), also at the start of every group of 32 repetitions (the
+// paper refreshes it every k insertions, Sec. 4.2; a group is one warp step,
+// and all candidates of the previous group have been offered by then); the
+// stop test runs once per round (Sec. 4.1); the
 // canonical similarity is float32 with 32 partial sums (partial c takes the
 // coordinates = c mod 32 in index order by fused multiply-add) combined as
 // s[c] += s[c + w] for w = 16, 8, 4, 2, 1.  Only the filter depends on s_k and
@@ -405,13 +406,16 @@ __global__ void __launch_bounds__(kWarps * 32, 5) search_kernel(Dev P) {
       const uint32_t mask = 0xffffffffu << (32 - depth);
       const bool single = prev == depth + 1;
       int nb = 0;
+      int tau = 64;
       for (int jb = 0; jb < L; jb += 32) {
-        // the previous group's candidates are in the top-k: snapshot its threshold
-        if (nb) {
-          size = flush_candidates<NT>(P, w, nb, size, k, lane, ct);
-          nb = 0;
+        if (jb == 0 || rounds == 0) {
+          // threshold snapshot; the previous group's candidates go into the top-k first
+          if (nb) {
+            size = flush_candidates<NT>(P, w, nb, size, k, lane, ct);
+            nb = 0;
+          }
+          tau = size == k ? filter_tau(P, w.pq_s[k - 1]) : 64;
         }
-        const int tau = size == k ? filter_tau(P, w.pq_s[k - 1]) : 64;
         const int j = jb + lane;
         uint32_t l = 0, r = 0, nl = 0, nr = 0;
         if (j < L) {

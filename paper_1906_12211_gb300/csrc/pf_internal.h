@@ -19,7 +19,8 @@ constexpr int kMaxK = 128;
 constexpr int kMaxD = 256;
 constexpr int kMaxL = 2048;
 constexpr int kMlpHidden = 256;                     // start-depth model hidden units
-constexpr float kMlpTail = 0.05f;                   // start where P(full depth > start) <= this
+constexpr float kMlpTail = 0.05f;                   // quantile: P(stop depth > q) <= this
+constexpr int kMlpMargin = 6;                       // start depth = quantile + this many bits (capped at K)
 
 enum Purpose : uint32_t { kPurposeHash = 1, kPurposeSketch = 2, kPurposeCpMc = 3 };
 
@@ -172,8 +173,8 @@ cudaError_t mlp_forward_backward(const float* X, const int32_t* y, int B, int F,
 cudaError_t adam_step(float* w, const float* g, float* m, float* v, int64_t count, float lr, int t, cudaStream_t s);
 cudaError_t to_bf16(const float* a, __nv_bfloat16* b, int64_t count, cudaStream_t s);
 cudaError_t mlp_predict(const float* qx, const uint64_t* qsk, int Q, int d_pad, int M, const __nv_bfloat16* W1,
-                        const float* b1, const __nv_bfloat16* W2, const float* b2, int C, float tail, int32_t* start,
-                        cudaStream_t s);
+                        const float* b1, const __nv_bfloat16* W2, const float* b2, int C, float tail, int margin,
+                        int32_t* start, cudaStream_t s);
 cudaError_t gather_rows(const float* src, const int32_t* idx, int rows, int cols, float* dst, cudaStream_t s);
 
 }  // namespace pf

@@ -55,8 +55,8 @@ def test_training_report(trained):
     ix, _, rep, _, _ = trained
     assert rep["samples"] == 4000 and rep["epochs"] == 30
     assert np.isfinite(rep["final_loss"]) and rep["final_loss"] < np.log(ix.Kb + 1)
-    assert rep["train_accuracy"] >= 0.8  # predicted start at or deeper than the full depth
-    assert rep["mean_start"] >= rep["mean_stop"] - 0.5  # mean_stop: mean training target (full depth)
+    assert rep["train_accuracy"] >= 0.8  # predicted quantile at or deeper than the stop depth
+    assert rep["mean_start"] >= rep["mean_stop"]
 
 
 def test_learned_search_equals_oracle_at_predicted_depths(trained):
@@ -79,8 +79,6 @@ def test_learned_start_saves_rounds_and_keeps_recall(trained, orc):
     _, sl, stl = ix.search(qd, 10, 0.9, stats=True, filter=False, learned=True)
     gp, gl = pf.stats_to_numpy(stp), pf.stats_to_numpy(stl)
     assert gl["rounds"].mean() <= gp["rounds"].mean() - 2.0
-    # starting at the predicted full depth skips rounds that were unfiltered anyway
-    assert gl["retrieved"].mean() <= 1.05 * gp["retrieved"].mean()
     qn = orc.normalize(Q)
     _, bs = orc.brute_force(o.x, qn, 10)
     rec_plain = float(np.mean(sp.cpu().numpy() >= bs[:, -1:]))
