@@ -317,7 +317,7 @@ __device__ __forceinline__ int flush_candidates(const Dev& P, WarpState& w, int 
 // NT = d_pad / 32 rounded up: float4 chunks of a float32 row per lane of an
 // 8-lane group (and 16-byte chunks of a bfloat16 row per lane of a 4-lane group)
 template <int NT>
-__global__ void __launch_bounds__(kWarps * 32, 5) search_kernel(Dev P) {
+__global__ void __launch_bounds__(kWarps * 32, 8) search_kernel(Dev P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int d_pad = P.d_pad, L = P.L, kmax = P.k_max;
