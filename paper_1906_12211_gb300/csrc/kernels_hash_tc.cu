@@ -15,20 +15,23 @@
 // sign and index of the largest |<a_c,x>|), so codes are bit-identical to the
 // float64 definition.
 //
-// Kernel structure (one CTA of 128 threads per SM, persistent):
+// Kernel structure (one CTA of 6 warps per SM, persistent, warp-specialised):
 //   - work item = (128-point tile, range of hash-row segments); a segment is
 //     one repetition (CP: fns tiles of d_pad rows; HP: a group of 4
 //     repetitions = 128 rows) or a group of 2 sketches (128 rows);
-//   - the A tile (Xh, Xl of the 128 points) stays in shared memory for the
-//     item; B tiles (Wh, Wl of one N tile) are double-buffered with cp.async;
-//     both use the 128-byte-swizzled K-major layout (8-row groups 1024 B apart,
-//     16-byte chunk c of row r stored at chunk c ^ (r mod 8));
-//   - thread 0 issues 3 * KB * 4 MMAs (M = 128, N = tile rows, K = 16) into
-//     one of two 128-column accumulators in tensor memory and commits them to
-//     an mbarrier; meanwhile all 4 warps load the next B tile and run the
-//     epilogue of the previous tile (tcgen05.ld, one thread per point);
+//   - warp 0 (one thread) is the TMA producer: the item's A tile (Xh, Xl of the
+//     128 points) once, then for every N tile its B operand as 2*KB boxes of 64
+//     columns (Wh and Wl per K block) into a ring of 8 shared-memory stages;
+//     all tiles are K-major with the 128-byte swizzle;
+//   - warp 1 owns the tensor memory and (one thread) issues the MMAs: per K
+//     block, Xh*Wh and Xl*Wh from the Wh stage and Xh*Wl from the Wl stage, into
+//     one of two 128-column accumulators; tcgen05.commit frees each stage and
+//     publishes each finished accumulator;
+//   - warps 2-5 are the epilogue (one thread per point, tcgen05.ld of its lane)
+//     and hand each accumulator back through an mbarrier;
 //   - every mbarrier wait is bounded: on time-out the kernel records an error
-//     word, drains its own copies, frees its tensor memory and returns.
+//     word and every role leaves its loop.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -40,10 +43,11 @@ namespace pf {
 namespace {
 
 constexpr int kBM = 128;          // points per tile (MMA M)
-constexpr int kThreads = 128;
+constexpr int kThreads = 192;     // producer warp, MMA warp, 4 epilogue warps
 constexpr int kTileBytes = kBM * 128;  // one 64-element K block of 128 rows
+constexpr int kStages = 8;        // B ring
 constexpr int kTmemCols = 256;    // two accumulators of 128 columns
-constexpr uint32_t kWaitLimit = 1u << 26;
+constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait polls per bounded wait
 
 struct HashArgs {
   const __nv_bfloat16* xh;
@@ -74,12 +78,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
 }
@@ -105,7 +103,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
@@ -136,6 +133,21 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+// 2-D tiled TMA load of box {64 columns, rows} at (x = column, y = row)
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
 }
 
 // 16 consecutive 32-bit columns of this thread's tensor-memory lane
@@ -172,23 +184,6 @@ __device__ __forceinline__ double dot64(const float* __restrict__ a, const float
   double s = 0.0;
   for (int i = 0; i < d; ++i) s = __dadd_rn(s, __dmul_rn(double(a[i]), double(x[i])));
   return s;
-}
-
-// Issue cp.async copies of `rows` rows (bf16, row length d_pad) starting at row
-// `row0` of src into a swizzled tile; rows >= limit and columns >= d_pad read 0.
-__device__ __forceinline__ void load_tile(uint32_t dst, const __nv_bfloat16* __restrict__ src, int64_t row0,
-                                          int rows, int64_t limit, int d_pad, int KB) {
-  const int chunks = KB * 8;  // 16-byte chunks per row
-  for (int e = threadIdx.x; e < rows * chunks; e += kThreads) {
-    const int r = e / chunks, c = e % chunks;
-    const int kb = c >> 3, cc = c & 7;
-    const int64_t row = row0 + r;
-    const int col = c * 8;
-    const bool ok = row < limit && col < d_pad;
-    const void* g = ok ? static_cast<const void*>(src + row * d_pad + col) : static_cast<const void*>(src);
-    const uint32_t off = uint32_t(kb * kTileBytes + r * 128 + ((cc ^ (r & 7)) << 4));
-    cp_async16(dst + off, g, ok ? 16u : 0u);
-  }
 }
 
 struct Tile {
@@ -446,130 +441,147 @@ __device__ __forceinline__ void epilogue(const HashArgs& A, const Tile& t, uint3
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A) {
+struct TensorMaps {
+  CUtensorMap xh, xl;        // A: [npts][d_pad], box {64, 128}
+  CUtensorMap wh_f, wl_f;    // B, CP function tiles: box {64, d_pad}
+  CUtensorMap wh_g, wl_g;    // B, 128-row groups: box {64, 128}
+};
+
+__global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const __grid_constant__ TensorMaps T) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte aligned base for the swizzled tiles
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int KB = A.KB;
   const uint32_t sA = smem_u32(base);                       // [2 splits][KB] tiles
-  const uint32_t sB = sA + uint32_t(2 * KB * kTileBytes);   // [2 stages][2 splits][KB] tiles
-  __shared__ __align__(8) uint64_t bars[2];
+  const uint32_t sB = sA + uint32_t(2 * KB * kTileBytes);   // [kStages] tiles
+  __shared__ __align__(8) uint64_t bfull[kStages], bempty[kStages], accfull[2], accempty[2], afull, aempty;
   __shared__ uint32_t tmem_base_slot;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  __shared__ volatile int failed;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  if (warp == 0) {
+  if (tid == 0) {
+    for (int u = 0; u < kStages; ++u) {
+      mbar_init(smem_u32(&bfull[u]), 1);
+      mbar_init(smem_u32(&bempty[u]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&accfull[b]), 1);
+      mbar_init(smem_u32(&accempty[b]), 128);
+    }
+    mbar_init(smem_u32(&afull), 1);
+    mbar_init(smem_u32(&aempty), 1);
+    failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
     tmem_alloc(smem_u32(&tmem_base_slot), kTmemCols);
     tmem_relinquish();
-  }
-  if (tid == 0) {
-    mbar_init(smem_u32(&bars[0]), 1);
-    mbar_init(smem_u32(&bars[1]), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_slot;
-  uint32_t phase[2] = {0u, 0u};
-  bool failed = false;
-
   const int seg_per = (A.segs + A.split - 1) / A.split;
-  for (int item = blockIdx.x; item < A.items && !failed; item += gridDim.x) {
-    const int mt = item / A.split, part = item % A.split;
-    const int seg0 = part * seg_per, seg1 = min(A.segs, seg0 + seg_per);
-    if (seg0 >= seg1) continue;
-    const int64_t p0 = int64_t(mt) * kBM;
-    const int64_t p = p0 + tid;
 
-    // A tile (both splits) and the first B tile
-    load_tile(sA, A.xh, p0, kBM, A.npts, A.d_pad, KB);
-    load_tile(sA + uint32_t(KB * kTileBytes), A.xl, p0, kBM, A.npts, A.d_pad, KB);
-    Tile cur = tile_of(A, seg0, 0);
-    load_tile(sB, A.wh, cur.row0, cur.rows, A.hash_rows, A.d_pad, KB);
-    load_tile(sB + uint32_t(KB * kTileBytes), A.wl, cur.row0, cur.rows, A.hash_rows, A.d_pad, KB);
-    cp_async_commit();
-
-    EpiState st;
-    st.code = 0;
-    Tile prev = cur;
-    int seg = seg0, f = 0;
-    int t = 0;
-    for (;; ++t) {
-      const int buf = t & 1;
-      // tile t resident in stage buf: make it visible to the tensor cores
-      cp_async_wait_all();
-      fence_proxy_async();
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t idesc = idesc_bf16(kBM, cur.rows);
-        const uint32_t d_tmem = tmem + uint32_t(buf * 128);
-        const uint32_t bstage = sB + uint32_t(buf * 2 * KB * kTileBytes);
-        int acc = 0;
-        // (Xh, Wh), (Xh, Wl), (Xl, Wh)
-        for (int split = 0; split < 3; ++split) {
-          const uint32_t a_t = sA + uint32_t((split == 2 ? KB : 0) * kTileBytes);
-          const uint32_t b_t = bstage + uint32_t((split == 1 ? KB : 0) * kTileBytes);
-          for (int kb = 0; kb < KB; ++kb)
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint32_t off = uint32_t(kb * kTileBytes + kk * 32);
-              mma_bf16(d_tmem, sw128_desc(a_t + off), sw128_desc(b_t + off), idesc, acc);
-              acc = 1;
-            }
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    uint32_t stage = 0, items_done = 0;
+    for (int item = blockIdx.x; item < A.items; item += gridDim.x) {
+      const int mt = item / A.split, part = item % A.split;
+      const int seg0 = part * seg_per, seg1 = min(A.segs, seg0 + seg_per);
+      if (seg0 >= seg1) continue;
+      if (items_done > 0 && !mbar_wait(smem_u32(&aempty), (items_done - 1) & 1)) { failed = 1; break; }
+      mbar_expect_tx(smem_u32(&afull), uint32_t(2 * KB * kTileBytes));
+      for (int kb = 0; kb < KB; ++kb) {
+        tma_load_2d(sA + uint32_t(kb * kTileBytes), &T.xh, kb * 64, mt * kBM, smem_u32(&afull));
+        tma_load_2d(sA + uint32_t((KB + kb) * kTileBytes), &T.xl, kb * 64, mt * kBM, smem_u32(&afull));
+      }
+      ++items_done;
+      bool bad = false;
+      for (int seg = seg0; seg < seg1 && !bad; ++seg)
+        for (int f = 0; f < tiles_in_seg(A, seg) && !bad; ++f) {
+          const Tile t = tile_of(A, seg, f);
+          const bool fn_tile = t.rows == A.d_pad && seg < A.seg_tables && A.family == PF_CROSSPOLYTOPE;
+          const CUtensorMap* mh = fn_tile ? &T.wh_f : &T.wh_g;
+          const CUtensorMap* ml = fn_tile ? &T.wl_f : &T.wl_g;
+          for (int u = 0; u < 2 * KB; ++u, ++stage) {
+            const uint32_t slot = stage % kStages, round = stage / kStages;
+            if (!mbar_wait(smem_u32(&bempty[slot]), (round & 1) ^ 1)) { bad = true; break; }
+            mbar_expect_tx(smem_u32(&bfull[slot]), uint32_t(t.rows * 128));
+            tma_load_2d(sB + slot * kTileBytes, (u & 1) ? ml : mh, (u >> 1) * 64, int(t.row0), smem_u32(&bfull[slot]));
+          }
         }
-        mma_commit(smem_u32(&bars[buf]));
-      }
-      // next tile of this item, if any
-      int nseg = seg, nf = f + 1;
-      if (nf >= tiles_in_seg(A, nseg)) {
-        nseg += 1;
-        nf = 0;
-      }
-      const bool has_next = nseg < seg1;
-      if (t >= 1) {
-        // the previous tile's MMAs are done: its stage and accumulator are free
-        if (!mbar_wait(smem_u32(&bars[buf ^ 1]), phase[buf ^ 1])) failed = true;
-        phase[buf ^ 1] ^= 1u;
-        tc_fence_after();
-      }
-      Tile nxt = cur;
-      if (has_next && !failed) {
-        nxt = tile_of(A, nseg, nf);
-        const uint32_t bstage = sB + uint32_t((buf ^ 1) * 2 * KB * kTileBytes);
-        load_tile(bstage, A.wh, nxt.row0, nxt.rows, A.hash_rows, A.d_pad, KB);
-        load_tile(bstage + uint32_t(KB * kTileBytes), A.wl, nxt.row0, nxt.rows, A.hash_rows, A.d_pad, KB);
-      }
-      cp_async_commit();
-      if (t >= 1 && !failed)
-        epilogue(A, prev, tmem + (uint32_t(warp * 32) << 16) + uint32_t((buf ^ 1) * 128), p, st);
-      tc_fence_before();
-      __syncthreads();
-      if (failed) break;
-      prev = cur;
-      if (!has_next) break;
-      cur = nxt;
-      seg = nseg;
-      f = nf;
+      if (bad) { failed = 1; break; }
     }
-    if (failed) break;
-    // epilogue of the item's last tile
-    const int lb = t & 1;
-    if (!mbar_wait(smem_u32(&bars[lb]), phase[lb])) {
-      failed = true;
-      break;
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    uint32_t stage = 0, items_done = 0, g = 0;
+    for (int item = blockIdx.x; item < A.items && !failed; item += gridDim.x) {
+      const int part = item % A.split;
+      const int seg0 = part * seg_per, seg1 = min(A.segs, seg0 + seg_per);
+      if (seg0 >= seg1) continue;
+      if (!mbar_wait(smem_u32(&afull), items_done & 1)) { failed = 1; break; }
+      ++items_done;
+      tc_fence_after();
+      bool bad = false;
+      for (int seg = seg0; seg < seg1 && !bad; ++seg)
+        for (int f = 0; f < tiles_in_seg(A, seg) && !bad; ++f, ++g) {
+          const Tile t = tile_of(A, seg, f);
+          const uint32_t b = g & 1;
+          if (!mbar_wait(smem_u32(&accempty[b]), ((g >> 1) & 1) ^ 1)) { bad = true; break; }
+          tc_fence_after();
+          const uint32_t idesc = idesc_bf16(kBM, t.rows);
+          const uint32_t d_tmem = tmem + b * 128;
+          uint32_t acc = 0;
+          for (int u = 0; u < 2 * KB; ++u, ++stage) {
+            const uint32_t slot = stage % kStages, round = stage / kStages;
+            if (!mbar_wait(smem_u32(&bfull[slot]), round & 1)) { bad = true; break; }
+            tc_fence_after();
+            const int kb = u >> 1;
+            const uint32_t bt = sB + slot * kTileBytes;
+            // Wh stage: Xh*Wh and Xl*Wh; Wl stage: Xh*Wl
+            for (int half = 0; half < ((u & 1) ? 1 : 2); ++half) {
+              const uint32_t at = sA + uint32_t(((half ? KB : 0) + kb) * kTileBytes);
+              for (int kk = 0; kk < 4; ++kk) {
+                mma_bf16(d_tmem, sw128_desc(at + kk * 32), sw128_desc(bt + kk * 32), idesc, acc);
+                acc = 1;
+              }
+            }
+            mma_commit(smem_u32(&bempty[slot]));
+          }
+          mma_commit(smem_u32(&accfull[b]));
+        }
+      mma_commit(smem_u32(&aempty));
+      if (bad) { failed = 1; break; }
     }
-    phase[lb] ^= 1u;
-    tc_fence_after();
-    epilogue(A, prev, tmem + (uint32_t(warp * 32) << 16) + uint32_t(lb * 128), p, st);
-    tc_fence_before();
-    __syncthreads();
+  } else if (warp >= 2) {
+    // ---------------- epilogue: thread = point, TMEM lane quarter = warp % 4
+    const int quarter = warp & 3;
+    uint32_t g = 0;
+    for (int item = blockIdx.x; item < A.items && !failed; item += gridDim.x) {
+      const int mt = item / A.split, part = item % A.split;
+      const int seg0 = part * seg_per, seg1 = min(A.segs, seg0 + seg_per);
+      if (seg0 >= seg1) continue;
+      const int64_t p = int64_t(mt) * kBM + quarter * 32 + lane;
+      EpiState st;
+      st.code = 0;
+      bool bad = false;
+      for (int seg = seg0; seg < seg1 && !bad; ++seg)
+        for (int f = 0; f < tiles_in_seg(A, seg) && !bad; ++f, ++g) {
+          const Tile t = tile_of(A, seg, f);
+          const uint32_t b = g & 1;
+          if (!mbar_wait(smem_u32(&accfull[b]), (g >> 1) & 1)) { bad = true; break; }
+          tc_fence_after();
+          epilogue(A, t, tmem + (uint32_t(quarter * 32) << 16) + b * 128, p, st);
+          tc_fence_before();
+          mbar_arrive(smem_u32(&accempty[b]));
+        }
+      if (bad) { failed = 1; break; }
+    }
   }
-  if (failed && tid == 0) atomicOr(A.error, 2);
-  cp_async_wait_all();
-  tc_fence_before();
   __syncthreads();
+  if (failed && tid == 0) atomicOr(A.error, 2);
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+  if (warp == 1) tmem_dealloc(tmem, kTmemCols);
 }
 
 // Deferred float64 rechecks: one thread per request rewrites the decided field
@@ -645,8 +657,42 @@ bool hash_tc_supported(const pf_index* ix) { return ix->lay.d_pad <= 128; }
 
 size_t hash_tc_smem(int d_pad) {
   const int KB = (d_pad + 63) / 64;
-  return size_t(2 * KB + 4 * KB) * kTileBytes + 1024;
+  return size_t(2 * KB + kStages) * kTileBytes + 1024;
 }
+
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  }
+  return fn;
+}
+
+// 2-D bf16 tensor [rows][d_pad] (row-major), box {64, box_rows}, 128-byte swizzle;
+// rows and columns outside the tensor read as zero
+bool make_map(CUtensorMap* m, const void* base, int64_t rows, int d_pad, int box_rows) {
+  EncodeTiled enc = encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {cuuint64_t(d_pad), cuuint64_t(rows)};
+  const cuuint64_t strides[1] = {cuuint64_t(d_pad) * 2};
+  const cuuint32_t box[2] = {64u, cuuint32_t(box_rows)};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
 
 cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __nv_bfloat16* xl, const float* x32,
                            int64_t npts, uint32_t* codes, int64_t cj, int64_t cp, uint64_t* sk, int64_t sm,
@@ -685,9 +731,16 @@ cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __
   A.sp = sp;
   A.error = error;
   A.rq = rq_cap ? rq : nullptr;
-  if (!A.rq) rq_cap = 0;
   A.rq_count = rq_count;
   A.rq_cap = A.rq ? rq_cap : 0u;
+  TensorMaps T;
+  const int fn_rows = ix->family == PF_CROSSPOLYTOPE ? A.d_pad : 128;
+  if (!make_map(&T.xh, xh, npts, A.d_pad, kBM) || !make_map(&T.xl, xl, npts, A.d_pad, kBM) ||
+      !make_map(&T.wh_f, ix->Whi, ix->hash_rows, A.d_pad, fn_rows) ||
+      !make_map(&T.wl_f, ix->Wlo, ix->hash_rows, A.d_pad, fn_rows) ||
+      !make_map(&T.wh_g, ix->Whi, ix->hash_rows, A.d_pad, 128) ||
+      !make_map(&T.wl_g, ix->Wlo, ix->hash_rows, A.d_pad, 128))
+    return cudaErrorInvalidValue;
   if (A.rq) {
     cudaError_t e0 = cudaMemsetAsync(rq_count, 0, sizeof(uint32_t), s);
     if (e0 != cudaSuccess) return e0;
@@ -696,7 +749,7 @@ cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __
   cudaError_t e = cudaFuncSetAttribute(hash_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   const int grid = std::min(A.items, ix->num_sms);
-  hash_tc_kernel<<<grid, kThreads, smem, s>>>(A);
+  hash_tc_kernel<<<grid, kThreads, smem, s>>>(A, T);
   e = cudaGetLastError();
   if (e != cudaSuccess || !A.rq) return e;
   recheck_kernel<<<4 * ix->num_sms, 256, 0, s>>>(A);
