@@ -131,7 +131,7 @@ void ensure_ws(pf_index* ix, int64_t Q, int k_max) {
   dalloc(&ws.stats, q);
   dalloc(&ws.counter, 64);
   dalloc(&ws.rq, recheck_capacity(int64_t(q)));
-  dalloc(&ws.rq_count, 1);
+  dalloc(&ws.rq_count, size_t(ix->num_sms));
   ws.cap_q = q;
   ws.cap_kmax = km;
 }
@@ -330,7 +330,7 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
         PF_CK(launch_normalize(pin, n, prm->d, dp, ix->x32, ix->x16, xlo, s));
         dalloc(&raw_codes, size_t(n) * ix->L);
         dalloc(&rq, recheck_capacity(n));
-        dalloc(&rq_count, 1);
+        dalloc(&rq_count, size_t(ix->num_sms));
         PF_CK(launch_hash(ix, ix->x32, ix->x16, xlo, n, raw_codes, n, 1, sk_out, n, 1, rq, rq_count,
                           recheck_capacity(n), s));
         PF_CK(sort_tables(ix, raw_codes, s));

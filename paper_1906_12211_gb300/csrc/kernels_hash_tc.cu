@@ -16,19 +16,28 @@
 // float64 definition.
 //
 // Kernel structure (one CTA of 6 warps per SM, persistent, warp-specialised):
-//   - work item = (128-point tile, range of hash-row segments); a segment is
-//     one repetition (CP: fns tiles of d_pad rows; HP: a group of 4
-//     repetitions = 128 rows) or a group of 2 sketches (128 rows);
-//   - warp 0 (one thread) is the TMA producer: the item's A tile (Xh, Xl of the
-//     128 points) once, then for every N tile its B operand as 2*KB boxes of 64
-//     columns (Wh and Wl per K block) into a ring of 8 shared-memory stages;
-//     all tiles are K-major with the 128-byte swizzle;
+//   - a unit of work is (128-point tile, segment); a segment is one
+//     repetition (CP: fns tiles of d_pad rows; HP: a group of 4 repetitions =
+//     128 rows) or a group of 2 sketches (128 rows); CTA b takes the
+//     contiguous units [b*U/G, (b+1)*U/G) of the U = tiles*segments, so the
+//     CTAs' shares differ by at most one segment and each CTA loads the A
+//     tiles of only the one or two point tiles its range touches;
+//   - warp 0 (one thread) is the TMA producer: the A tile (Xh, Xl of the 128
+//     points) once per run of segments, then for every N tile its B operand as
+//     2*KB boxes of 64 columns (Wh and Wl per K block) into a ring of 8
+//     shared-memory stages; all tiles are K-major with the 128-byte swizzle;
 //   - warp 1 owns the tensor memory and (one thread) issues the MMAs: per K
 //     block, Xh*Wh and Xl*Wh from the Wh stage and Xh*Wl from the Wl stage, into
-//     one of two 128-column accumulators; tcgen05.commit frees each stage and
-//     publishes each finished accumulator;
+//     one of four 128-column accumulators (all 512 columns, so the epilogue
+//     warps can drift up to three tiles apart); tcgen05.commit frees each
+//     stage and publishes each finished accumulator;
 //   - warps 2-5 are the epilogue (one thread per point, tcgen05.ld of its lane)
-//     and hand each accumulator back through an mbarrier;
+//     and hand each accumulator back through an mbarrier; for a CP function
+//     the thread keeps the three largest |v| as integer sort keys in four
+//     independent chains (no branches); a decision closer to its boundary than
+//     the band is queued, with the top two rows as the candidates (or "all
+//     rows" when a third row is also close), in the CTA's own region of the
+//     request queue (a shared-memory counter, no global atomics);
 //   - every mbarrier wait is bounded: on time-out the kernel records an error
 //     word and every role leaves its loop.
 #include <cuda.h>
@@ -46,7 +55,8 @@ constexpr int kBM = 128;          // points per tile (MMA M)
 constexpr int kThreads = 192;     // producer warp, MMA warp, 4 epilogue warps
 constexpr int kTileBytes = kBM * 128;  // one 64-element K block of 128 rows
 constexpr int kStages = 8;        // B ring
-constexpr int kTmemCols = 256;    // two accumulators of 128 columns
+constexpr int kAcc = 4;           // accumulators of 128 columns (the whole tensor memory)
+constexpr int kTmemCols = 128 * kAcc;
 constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait polls per bounded wait
 
 struct HashArgs {
@@ -62,16 +72,15 @@ struct HashArgs {
   int d, d_pad, KB, family, L, M, fns, ell, rows_table;
   int seg_tables;  // segments that are repetitions (CP) or groups of 4 repetitions (HP)
   int segs;        // + sketch groups of 2
-  int split;       // segment ranges per point tile
-  int items;       // point tiles * split
+  int64_t units;   // point tiles * segs; CTA b takes units [b*units/grid, (b+1)*units/grid)
   uint32_t* codes;
   int64_t cj, cp;
   uint64_t* sk;
   int64_t sm, sp;
   int32_t* error;
-  RecheckReq* rq;       // deferred float64 rechecks (may be null)
-  uint32_t* rq_count;   // requests written (may exceed rq_cap: the excess was done inline)
-  uint32_t rq_cap;
+  RecheckReq* rq;       // deferred float64 rechecks (may be null): region b = [b*rq_per, (b+1)*rq_per)
+  uint32_t* rq_count;   // per region: requests written there (the ones that did not fit ran inline)
+  uint32_t rq_per;      // entries per region (0 without a queue)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -164,6 +173,83 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// columns [0, 64) of this thread's lane, waited for
+__device__ __forceinline__ void tmem_ld64_x64(uint32_t taddr, uint32_t (&r)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr), "r"(taddr + 32u)
+      : "memory");
+}
+
+// columns [0, 48); the rest of r reads as zero
+__device__ __forceinline__ void tmem_ld64_x48(uint32_t taddr, uint32_t (&r)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%48];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47}, [%49];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
+      : "r"(taddr), "r"(taddr + 32u)
+      : "memory");
+#pragma unroll
+  for (int i = 48; i < 64; ++i) r[i] = 0u;
+}
+
+// columns [0, 32); the rest of r reads as zero
+__device__ __forceinline__ void tmem_ld64_x32(uint32_t taddr, uint32_t (&r)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 32; i < 64; ++i) r[i] = 0u;
+}
+
+// columns [0, 16); the rest of r reads as zero
+__device__ __forceinline__ void tmem_ld64_x16(uint32_t taddr, uint32_t (&r)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 16; i < 64; ++i) r[i] = 0u;
+}
+
+// columns [0, min(n, 64)) of this thread's lane, n a positive multiple of 16
+// and the same in the whole warp; columns from n on read as zero
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, int n, uint32_t (&r)[64]) {
+  if (n >= 64)
+    tmem_ld64_x64(taddr, r);
+  else if (n == 48)
+    tmem_ld64_x48(taddr, r);
+  else if (n == 32)
+    tmem_ld64_x32(taddr, r);
+  else
+    tmem_ld64_x16(taddr, r);
+}
+
 // shared-memory descriptor of a K-major, 128-byte-swizzled tile
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   uint64_t d = 0;
@@ -218,6 +304,20 @@ __device__ __forceinline__ Tile tile_of(const HashArgs& A, int seg, int f) {
   return t;
 }
 
+// A run of consecutive segments of one point tile within the CTA's units.
+struct Chunk {
+  int mt, seg0, seg1;
+};
+
+__device__ __forceinline__ bool next_chunk(const HashArgs& A, int64_t& u, int64_t hi, Chunk& c) {
+  if (u >= hi) return false;
+  c.mt = int(u / A.segs);
+  c.seg0 = int(u - int64_t(c.mt) * A.segs);
+  c.seg1 = int(min(hi - int64_t(c.mt) * A.segs, int64_t(A.segs)));
+  u = int64_t(c.mt) * A.segs + c.seg1;
+  return true;
+}
+
 __device__ __forceinline__ int tiles_in_seg(const HashArgs& A, int seg) {
   return (seg < A.seg_tables && A.family == PF_CROSSPOLYTOPE) ? A.fns : 1;
 }
@@ -248,41 +348,31 @@ __device__ __forceinline__ void dot64x4(const float* __restrict__ wf, const int 
   out[3] = s3;
 }
 
-// keep the four largest |v| (a0 >= a1 >= a2 >= a3) in registers
-__device__ __forceinline__ void top4_push(float av, float v, int c, float& a0, float& a1, float& a2, float& a3,
-                                          int& c0, int& c1, int& c2, int& c3, float& best_v) {
-  if (!(av > a3)) return;
-  if (av > a2) {
-    a3 = a2;
-    c3 = c2;
-    if (av > a1) {
-      a2 = a1;
-      c2 = c1;
-      if (av > a0) {
-        a1 = a0;
-        c1 = c0;
-        a0 = av;
-        c0 = c;
-        best_v = v;
-      } else {
-        a1 = av;
-        c1 = c;
-      }
-    } else {
-      a2 = av;
-      c2 = c;
-    }
-  } else {
-    a3 = av;
-    c3 = c;
-  }
+// Sort key of the projection v on hyperplane c (c < 128) of a CP function:
+// bits 31..8 are |v| cut to its 8 exponent and 16 high mantissa bits, bits
+// 7..1 hold 127 - c and bit 0 the sign of v.  Unsigned order of keys is the
+// order of |v| up to the cut (less than 2^-16 |v|), ties to the smaller c.
+__device__ __forceinline__ uint32_t cp_key(uint32_t vbits, int c) {
+  const uint32_t r = __funnelshift_l(vbits, vbits, 1);  // |v| << 1 | sign
+  return (r | 0xFEu) - 2u * uint32_t(c);
+}
+__device__ __forceinline__ float cp_key_abs(uint32_t k) { return __uint_as_float((k >> 1) & 0x7FFFFF80u); }
+__device__ __forceinline__ int cp_key_col(uint32_t k) { return 127 - int((k >> 1) & 0x7Fu); }
+
+// the three largest keys seen (m0 > m1 > m2; keys of distinct columns differ)
+__device__ __forceinline__ void top3_push(uint32_t k, uint32_t& m0, uint32_t& m1, uint32_t& m2) {
+  m2 = max(m2, min(m1, k));
+  m1 = max(m1, min(m0, k));
+  m0 = max(m0, k);
 }
 
-// Reserve `cnt` consecutive request slots for this lane (warp-aggregated: one
-// atomic per warp) and return the first.  All lanes of the warp must call it.
-// Slots at or beyond rq_cap do not exist: the caller rechecks those inline, so
-// every slot below min(count, rq_cap) is written by exactly one lane.
-__device__ __forceinline__ uint32_t reserve_requests(const HashArgs& A, uint32_t cnt) {
+// Reserve `cnt` consecutive entries of this CTA's region of the request queue
+// for this lane (warp-aggregated: one shared-memory atomic per warp) and
+// return the first, counted from the region's start.  Entries at or beyond
+// rq_per do not exist: the caller rechecks those inline, so every entry below
+// min(count, rq_per) is written by exactly one lane.  All lanes of the warp
+// must call it.
+__device__ __forceinline__ uint32_t reserve_requests(const HashArgs& A, uint32_t* s_count, uint32_t cnt) {
   const int lane = threadIdx.x & 31;
   uint32_t inc = cnt;
 #pragma unroll
@@ -293,81 +383,99 @@ __device__ __forceinline__ uint32_t reserve_requests(const HashArgs& A, uint32_t
   const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
   if (total == 0 || !A.rq) return 0xffffffffu;
   uint32_t base = 0;
-  if (lane == 0) base = atomicAdd(A.rq_count, total);
+  if (lane == 0) base = atomicAdd(s_count, total);
   base = __shfl_sync(0xffffffffu, base, 0);
   return base + inc - cnt;
 }
 
+__device__ __forceinline__ RecheckReq* request_at(const HashArgs& A, uint32_t local) {
+  return A.rq + size_t(blockIdx.x) * A.rq_per + local;
+}
+
 // Epilogue of one N tile for the thread's point p (accumulator columns at taddr).
 __device__ __forceinline__ void epilogue(const HashArgs& A, const Tile& t, uint32_t taddr, int64_t p,
-                                         EpiState& st) {
+                                         EpiState& st, uint32_t* s_count) {
   const bool live = p < A.npts;
   const float* xrow = A.x32 + (live ? p : 0) * A.d_pad;
   if (t.seg < A.seg_tables && A.family == PF_CROSSPOLYTOPE) {
     if (t.first) st.code = 0;
-    float a0 = -1.f, a1 = -1.f, a2 = -1.f, a3 = -1.f;
-    int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-    float best_v = 0.f;
-    for (int cb = 0; cb < t.rows; cb += 16) {
-      float v[16];
-      tmem_ld16(taddr + uint32_t(cb), v);
-#pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (cb + i < A.d) top4_push(fabsf(v[i]), v[i], cb + i, a0, a1, a2, a3, c0, c1, c2, c3, best_v);
-    }
     const float band = A.thr[t.row0];
-    int arg = c0;
-    bool neg = best_v < 0.f;
-    const bool need = live && (a1 >= a0 - 2.f * band || a0 < band);
-    const uint32_t slot = reserve_requests(A, need ? 1u : 0u);
-    if (need && slot < A.rq_cap) {
-      // keep the tensor-core decision now; the fix-up kernel rewrites the field
-      RecheckReq q;
-      q.p = uint32_t(p);
-      q.row0 = uint32_t(t.row0);
-      const bool all = a3 >= a0 - 2.f * band;
-      const uint32_t use = 1u | (a1 >= a0 - 2.f * band ? 2u : 0u) | (a2 >= a0 - 2.f * band ? 4u : 0u);
-      q.info = uint32_t(t.seg) | (uint32_t(t.fn) << 20) | (use << 26) | ((all ? 3u : 0u) << 30);
-      q.c[0] = uint8_t(c0);
-      q.c[1] = uint8_t(c1);
-      q.c[2] = uint8_t(c2);
-      q.c[3] = uint8_t(c3);
-      A.rq[slot] = q;
-    } else if (need) {
-      const float* wf = A.w32 + t.row0 * A.d_pad;
-      double bestabs = -1.0, bestval = 0.0;
-      int besti = 0;
-      if (a3 >= a0 - 2.f * band) {
-        // a fifth row could be in the band: all rows, 4 at a time
-        for (int cc = 0; cc < A.d; cc += 4) {
-          const int cs[4] = {cc, min(cc + 1, A.d - 1), min(cc + 2, A.d - 1), min(cc + 3, A.d - 1)};
-          const bool us[4] = {true, cc + 1 < A.d, cc + 2 < A.d, cc + 3 < A.d};
+    // the three largest |v| over the function's rows, four independent
+    // chains; rows c >= d of a function are zero and reach the top three
+    // only when fewer than three rows are nonzero (then every row is rechecked)
+    uint32_t m0[4] = {0u, 0u, 0u, 0u}, m1[4] = {0u, 0u, 0u, 0u}, m2[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (64 * h < t.rows) {
+        uint32_t r[64];
+        tmem_ld64(taddr + uint32_t(64 * h), t.rows - 64 * h, r);
+#pragma unroll
+        for (int i = 0; i < 64; ++i) top3_push(cp_key(r[i], 64 * h + i), m0[i & 3], m1[i & 3], m2[i & 3]);
+      }
+    }
+    uint32_t k0 = m0[0], k1 = m1[0], k2 = m2[0];
+#pragma unroll
+    for (int q = 1; q < 4; ++q) {
+      top3_push(m0[q], k0, k1, k2);
+      top3_push(m1[q], k0, k1, k2);
+      top3_push(m2[q], k0, k1, k2);
+    }
+    const float a0 = cp_key_abs(k0), a1 = cp_key_abs(k1), a2 = cp_key_abs(k2);
+    // every row whose |v| can be within 2*band of the maximum reaches lim:
+    // a0 * 2^-15 covers the cut of the keys
+    const float lim = a0 - 2.f * band - a0 * 3.0517578125e-05f;
+    int arg = cp_key_col(k0);
+    bool neg = (k0 & 1u) != 0u;
+    const bool need = live && (a1 >= lim || a0 < band);
+    if (__any_sync(0xffffffffu, need)) {
+      // rare: candidates are the top two, or every row once a third reaches lim
+      const bool all = a0 < band || a2 >= lim;
+      const int cs0 = arg, cs1 = cp_key_col(k1);
+      const uint32_t local = reserve_requests(A, s_count, need ? 1u : 0u);
+      if (need && local < A.rq_per) {
+        // keep the tensor-core decision now; the fix-up kernel rewrites the field
+        RecheckReq q;
+        q.p = uint32_t(p);
+        q.row0 = uint32_t(t.row0);
+        q.info = uint32_t(t.seg) | (uint32_t(t.fn) << 20) | (3u << 26) | ((all ? 3u : 0u) << 30);
+        q.c[0] = uint8_t(cs0);
+        q.c[1] = uint8_t(cs1);
+        q.c[2] = q.c[3] = 0;
+        *request_at(A, local) = q;
+      } else if (need) {
+        const float* wf = A.w32 + t.row0 * A.d_pad;
+        double bestabs = -1.0, bestval = 0.0;
+        int besti = 0;
+        if (all) {
+          for (int cc = 0; cc < A.d; cc += 4) {
+            const int cs[4] = {cc, min(cc + 1, A.d - 1), min(cc + 2, A.d - 1), min(cc + 3, A.d - 1)};
+            const bool us[4] = {true, cc + 1 < A.d, cc + 2 < A.d, cc + 3 < A.d};
+            double v64[4];
+            dot64x4(wf, cs, us, xrow, A.d, A.d_pad, v64);
+            for (int u = 0; u < 4; ++u)
+              if (us[u] && fabs(v64[u]) > bestabs) {
+                bestabs = fabs(v64[u]);
+                bestval = v64[u];
+                besti = cs[u];
+              }
+          }
+        } else {
+          const int cs[4] = {cs0, cs1, cs1, cs1};
+          const bool us[4] = {true, true, false, false};
           double v64[4];
           dot64x4(wf, cs, us, xrow, A.d, A.d_pad, v64);
-          for (int q = 0; q < 4; ++q)
-            if (us[q] && fabs(v64[q]) > bestabs) {
-              bestabs = fabs(v64[q]);
-              bestval = v64[q];
-              besti = cs[q];
+          for (int u = 0; u < 2; ++u) {
+            const double av = fabs(v64[u]);
+            if (av > bestabs || (av == bestabs && cs[u] < besti)) {
+              bestabs = av;
+              bestval = v64[u];
+              besti = cs[u];
             }
-        }
-      } else {
-        const int cs[4] = {c0, c1, c2, c3};
-        const bool us[4] = {true, a1 >= a0 - 2.f * band, a2 >= a0 - 2.f * band, false};
-        double v64[4];
-        dot64x4(wf, cs, us, xrow, A.d, A.d_pad, v64);
-        for (int q = 0; q < 3; ++q) {
-          if (!us[q]) continue;
-          const double av = fabs(v64[q]);
-          if (av > bestabs || (av == bestabs && cs[q] < besti)) {
-            bestabs = av;
-            bestval = v64[q];
-            besti = cs[q];
           }
         }
+        arg = besti;
+        neg = bestval < 0.0;
       }
-      arg = besti;
-      neg = bestval < 0.0;
     }
     const uint32_t value = ((neg ? 1u : 0u) << (A.ell - 1)) | uint32_t(arg);
     st.code |= value << (32 - A.ell * (t.fn + 1));
@@ -395,13 +503,13 @@ __device__ __forceinline__ void epilogue(const HashArgs& A, const Tile& t, uint3
       }
     }
     if (__any_sync(0xffffffffu, needm != 0)) {
-      uint32_t slot = reserve_requests(A, __popc(needm));
+      uint32_t local = reserve_requests(A, s_count, __popc(needm));
       while (needm) {
         const int i = __ffs(needm) - 1;
         needm &= needm - 1;
         const int c = cb + i;
         const int64_t row = t.row0 + c;
-        if (slot < A.rq_cap) {
+        if (local < A.rq_per) {
           RecheckReq q;
           q.p = uint32_t(p);
           q.row0 = uint32_t(row);
@@ -412,8 +520,8 @@ __device__ __forceinline__ void epilogue(const HashArgs& A, const Tile& t, uint3
             q.info = uint32_t(row >> 5) | (uint32_t(row & 31) << 20) | (1u << 30);
           }
           q.c[0] = q.c[1] = q.c[2] = q.c[3] = 0;
-          A.rq[slot] = q;
-          ++slot;  // stays >= rq_cap (including the "no queue" value) once it gets there
+          *request_at(A, local) = q;
+          ++local;  // stays >= rq_per (including the "no queue" value) once it gets there
         } else {
           const bool bit = dot64(A.w32 + row * A.d_pad, xrow, A.d) >= 0.0;
           const uint64_t m = uint64_t(1) << (c & 63);
@@ -453,7 +561,8 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
   const int KB = A.KB;
   const uint32_t sA = smem_u32(base);                       // [2 splits][KB] tiles
   const uint32_t sB = sA + uint32_t(2 * KB * kTileBytes);   // [kStages] tiles
-  __shared__ __align__(8) uint64_t bfull[kStages], bempty[kStages], accfull[2], accempty[2], afull, aempty;
+  __shared__ __align__(8) uint64_t bfull[kStages], bempty[kStages], accfull[kAcc], accempty[kAcc], afull, aempty;
+  __shared__ uint32_t s_count;  // entries reserved in this CTA's region of the request queue
   __shared__ uint32_t tmem_base_slot;
   __shared__ volatile int failed;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -463,13 +572,14 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
       mbar_init(smem_u32(&bfull[u]), 1);
       mbar_init(smem_u32(&bempty[u]), 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kAcc; ++b) {
       mbar_init(smem_u32(&accfull[b]), 1);
       mbar_init(smem_u32(&accempty[b]), 128);
     }
     mbar_init(smem_u32(&afull), 1);
     mbar_init(smem_u32(&aempty), 1);
     failed = 0;
+    s_count = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 1) {
@@ -480,15 +590,16 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_slot;
-  const int seg_per = (A.segs + A.split - 1) / A.split;
+  const int64_t u_lo = int64_t(blockIdx.x) * A.units / gridDim.x;
+  const int64_t u_hi = int64_t(blockIdx.x + 1) * A.units / gridDim.x;
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
     uint32_t stage = 0, items_done = 0;
-    for (int item = blockIdx.x; item < A.items; item += gridDim.x) {
-      const int mt = item / A.split, part = item % A.split;
-      const int seg0 = part * seg_per, seg1 = min(A.segs, seg0 + seg_per);
-      if (seg0 >= seg1) continue;
+    int64_t u = u_lo;
+    Chunk ch;
+    while (next_chunk(A, u, u_hi, ch)) {
+      const int mt = ch.mt, seg0 = ch.seg0, seg1 = ch.seg1;
       if (items_done > 0 && !mbar_wait(smem_u32(&aempty), (items_done - 1) & 1)) { failed = 1; break; }
       mbar_expect_tx(smem_u32(&afull), uint32_t(2 * KB * kTileBytes));
       for (int kb = 0; kb < KB; ++kb) {
@@ -515,10 +626,10 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     uint32_t stage = 0, items_done = 0, g = 0;
-    for (int item = blockIdx.x; item < A.items && !failed; item += gridDim.x) {
-      const int part = item % A.split;
-      const int seg0 = part * seg_per, seg1 = min(A.segs, seg0 + seg_per);
-      if (seg0 >= seg1) continue;
+    int64_t u = u_lo;
+    Chunk ch;
+    while (!failed && next_chunk(A, u, u_hi, ch)) {
+      const int seg0 = ch.seg0, seg1 = ch.seg1;
       if (!mbar_wait(smem_u32(&afull), items_done & 1)) { failed = 1; break; }
       ++items_done;
       tc_fence_after();
@@ -526,8 +637,8 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
       for (int seg = seg0; seg < seg1 && !bad; ++seg)
         for (int f = 0; f < tiles_in_seg(A, seg) && !bad; ++f, ++g) {
           const Tile t = tile_of(A, seg, f);
-          const uint32_t b = g & 1;
-          if (!mbar_wait(smem_u32(&accempty[b]), ((g >> 1) & 1) ^ 1)) { bad = true; break; }
+          const uint32_t b = g % kAcc;
+          if (!mbar_wait(smem_u32(&accempty[b]), ((g / kAcc) & 1) ^ 1)) { bad = true; break; }
           tc_fence_after();
           const uint32_t idesc = idesc_bf16(kBM, t.rows);
           const uint32_t d_tmem = tmem + b * 128;
@@ -557,10 +668,10 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
     // ---------------- epilogue: thread = point, TMEM lane quarter = warp % 4
     const int quarter = warp & 3;
     uint32_t g = 0;
-    for (int item = blockIdx.x; item < A.items && !failed; item += gridDim.x) {
-      const int mt = item / A.split, part = item % A.split;
-      const int seg0 = part * seg_per, seg1 = min(A.segs, seg0 + seg_per);
-      if (seg0 >= seg1) continue;
+    int64_t u = u_lo;
+    Chunk ch;
+    while (!failed && next_chunk(A, u, u_hi, ch)) {
+      const int mt = ch.mt, seg0 = ch.seg0, seg1 = ch.seg1;
       const int64_t p = int64_t(mt) * kBM + quarter * 32 + lane;
       EpiState st;
       st.code = 0;
@@ -568,10 +679,10 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
       for (int seg = seg0; seg < seg1 && !bad; ++seg)
         for (int f = 0; f < tiles_in_seg(A, seg) && !bad; ++f, ++g) {
           const Tile t = tile_of(A, seg, f);
-          const uint32_t b = g & 1;
-          if (!mbar_wait(smem_u32(&accfull[b]), (g >> 1) & 1)) { bad = true; break; }
+          const uint32_t b = g % kAcc;
+          if (!mbar_wait(smem_u32(&accfull[b]), (g / kAcc) & 1)) { bad = true; break; }
           tc_fence_after();
-          epilogue(A, t, tmem + (uint32_t(quarter * 32) << 16) + b * 128, p, st);
+          epilogue(A, t, tmem + (uint32_t(quarter * 32) << 16) + b * 128, p, st, &s_count);
           tc_fence_before();
           mbar_arrive(smem_u32(&accempty[b]));
         }
@@ -579,74 +690,181 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
     }
   }
   __syncthreads();
+  if (tid == 0 && A.rq) A.rq_count[blockIdx.x] = min(s_count, A.rq_per);
   if (failed && tid == 0) atomicOr(A.error, 2);
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem, kTmemCols);
 }
 
-// Deferred float64 rechecks: one thread per request rewrites the decided field
-// of a code (CP function value or HP bit) or sketch bit with the float64
+// float64 projections, in index order, of the rows w[u] with bit u of `use`
+// onto x (d elements): four elements per load, the loads of the next group
+// issued before the arithmetic of this one (rows start 16-byte aligned)
+__device__ __forceinline__ void dot64_rows(const float* const (&w)[4], uint32_t use, const float* __restrict__ x,
+                                           int d, double (&out)[4]) {
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  const int d4 = d & ~3;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 xv = z, wv[4] = {z, z, z, z};
+  if (d4 > 0) {
+    xv = __ldg(reinterpret_cast<const float4*>(x));
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (use & (1u << u)) wv[u] = __ldg(reinterpret_cast<const float4*>(w[u]));
+  }
+  for (int i = 0; i < d4; i += 4) {
+    float4 xn = z, wn[4] = {z, z, z, z};
+    if (i + 4 < d4) {
+      xn = __ldg(reinterpret_cast<const float4*>(x + i + 4));
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (use & (1u << u)) wn[u] = __ldg(reinterpret_cast<const float4*>(w[u] + i + 4));
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!(use & (1u << u))) continue;
+      s[u] = __dadd_rn(s[u], __dmul_rn(double(wv[u].x), double(xv.x)));
+      s[u] = __dadd_rn(s[u], __dmul_rn(double(wv[u].y), double(xv.y)));
+      s[u] = __dadd_rn(s[u], __dmul_rn(double(wv[u].z), double(xv.z)));
+      s[u] = __dadd_rn(s[u], __dmul_rn(double(wv[u].w), double(xv.w)));
+    }
+    xv = xn;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) wv[u] = wn[u];
+  }
+  for (int i = d4; i < d; ++i)
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (use & (1u << u)) s[u] = __dadd_rn(s[u], __dmul_rn(double(w[u][i]), double(x[i])));
+#pragma unroll
+  for (int u = 0; u < 4; ++u) out[u] = s[u];
+}
+
+// rewrite the CP field of function fn of repetition j for point p with the
+// float64 decision (row besti, sign of bestval)
+__device__ __forceinline__ void store_cp_field(const HashArgs& A, uint32_t info, int64_t p, int besti,
+                                               double bestval) {
+  const int j = int(info & 0xFFFFFu), fn = int((info >> 20) & 63u);
+  const uint32_t value = ((bestval < 0.0 ? 1u : 0u) << (A.ell - 1)) | uint32_t(besti);
+  const int shift = 32 - A.ell * (fn + 1);
+  const uint32_t field = ((1u << A.ell) - 1u) << shift;
+  uint32_t* w = A.codes + int64_t(j) * A.cj + p * A.cp;
+  atomicAnd(w, ~field);
+  atomicOr(w, value << shift);
+}
+
+// One request of kind 0 (CP, listed candidate rows), 1 (HP bit) or 2 (sketch bit).
+__device__ __forceinline__ void recheck_one(const HashArgs& A, const RecheckReq& q) {
+  const int64_t p = q.p;
+  const float* xrow = A.x32 + p * A.d_pad;
+  const uint32_t kind = q.info >> 30;
+  if (kind == 0) {
+    const uint32_t use = (q.info >> 26) & 15u;
+    const float* wf = A.w32 + int64_t(q.row0) * A.d_pad;
+    const int cs[4] = {q.c[0], q.c[1], q.c[2], q.c[3]};
+    const float* w[4] = {wf + int64_t(cs[0]) * A.d_pad, wf + int64_t(cs[1]) * A.d_pad, wf + int64_t(cs[2]) * A.d_pad,
+                         wf + int64_t(cs[3]) * A.d_pad};
+    double v64[4];
+    dot64_rows(w, use, xrow, A.d, v64);
+    double bestabs = -1.0, bestval = 0.0;
+    int besti = 0;
+    for (int u = 0; u < 4; ++u) {
+      if (!(use & (1u << u))) continue;
+      const double av = fabs(v64[u]);
+      if (av > bestabs || (av == bestabs && cs[u] < besti)) {
+        bestabs = av;
+        bestval = v64[u];
+        besti = cs[u];
+      }
+    }
+    store_cp_field(A, q.info, p, besti, bestval);
+    return;
+  }
+  const float* w[4] = {A.w32 + int64_t(q.row0) * A.d_pad, xrow, xrow, xrow};
+  double v64[4];
+  dot64_rows(w, 1u, xrow, A.d, v64);
+  const bool bit = v64[0] >= 0.0;
+  const int idx = int(q.info & 0xFFFFFu), b = int((q.info >> 20) & 63u);
+  if (kind == 1) {
+    uint32_t* cw = A.codes + int64_t(idx) * A.cj + p * A.cp;
+    const uint32_t m = 1u << (31 - b);
+    if (bit) atomicOr(cw, m); else atomicAnd(cw, ~m);
+  } else {
+    unsigned long long* sw = reinterpret_cast<unsigned long long*>(A.sk + int64_t(idx) * A.sm + p * A.sp);
+    const unsigned long long m = 1ull << b;
+    if (bit) atomicOr(sw, m); else atomicAnd(sw, ~m);
+  }
+}
+
+// One CP request of kind 3 (every row a candidate), by a whole warp: lane l
+// takes rows l, l+32, ... (d <= 128), each in float64 in index order, then the
+// warp keeps the largest |value|, ties to the smaller row.
+__device__ __forceinline__ void recheck_all_rows(const HashArgs& A, uint32_t p32, uint32_t row0, uint32_t info) {
+  const int lane = threadIdx.x & 31;
+  const int64_t p = p32;
+  const float* xrow = A.x32 + p * A.d_pad;
+  const float* wf = A.w32 + int64_t(row0) * A.d_pad;
+  const float* w[4];
+  uint32_t use = 0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int c = lane + 32 * u;
+    w[u] = wf + int64_t(min(c, A.d - 1)) * A.d_pad;
+    if (c < A.d) use |= 1u << u;
+  }
+  double v64[4];
+  dot64_rows(w, use, xrow, A.d, v64);
+  double bestabs = -1.0, bestval = 0.0;
+  int besti = 0x7FFFFFFF;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if ((use & (1u << u)) && fabs(v64[u]) > bestabs) {
+      bestabs = fabs(v64[u]);
+      bestval = v64[u];
+      besti = lane + 32 * u;
+    }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const double oa = __shfl_xor_sync(0xffffffffu, bestabs, off);
+    const double ov = __shfl_xor_sync(0xffffffffu, bestval, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, besti, off);
+    if (oa > bestabs || (oa == bestabs && oi < besti)) {
+      bestabs = oa;
+      bestval = ov;
+      besti = oi;
+    }
+  }
+  if (lane == 0) store_cp_field(A, info, p, besti, bestval);
+}
+
+// Deferred float64 rechecks: `blocks_per_region` CTAs per region of the queue;
+// a warp takes 32 consecutive requests, one per lane, and then does the
+// "all rows" requests among them together.  Each request rewrites the decided
+// field of a code (CP function value or HP bit) or sketch bit with the float64
 // decision.  Fields of different requests are disjoint, so the two atomic
 // updates (clear, then set) of concurrent requests on one word commute.
-__global__ void recheck_kernel(HashArgs A) {
-  const uint32_t total = min(*A.rq_count, A.rq_cap);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    const RecheckReq q = A.rq[i];
-    const int64_t p = q.p;
-    const float* xrow = A.x32 + p * A.d_pad;
-    const uint32_t kind = q.info >> 30;
-    if (kind == 0 || kind == 3) {
-      const int j = int(q.info & 0xFFFFFu), fn = int((q.info >> 20) & 63u);
-      const float* wf = A.w32 + int64_t(q.row0) * A.d_pad;
-      double bestabs = -1.0, bestval = 0.0;
-      int besti = 0;
-      if (kind == 3) {
-        for (int cc = 0; cc < A.d; cc += 4) {
-          const int cs[4] = {cc, min(cc + 1, A.d - 1), min(cc + 2, A.d - 1), min(cc + 3, A.d - 1)};
-          const bool us[4] = {true, cc + 1 < A.d, cc + 2 < A.d, cc + 3 < A.d};
-          double v64[4];
-          dot64x4(wf, cs, us, xrow, A.d, A.d_pad, v64);
-          for (int u = 0; u < 4; ++u)
-            if (us[u] && fabs(v64[u]) > bestabs) {
-              bestabs = fabs(v64[u]);
-              bestval = v64[u];
-              besti = cs[u];
-            }
-        }
-      } else {
-        const uint32_t use = (q.info >> 26) & 15u;
-        const int cs[4] = {q.c[0], q.c[1], q.c[2], q.c[3]};
-        const bool us[4] = {(use & 1u) != 0, (use & 2u) != 0, (use & 4u) != 0, false};
-        double v64[4];
-        dot64x4(wf, cs, us, xrow, A.d, A.d_pad, v64);
-        for (int u = 0; u < 3; ++u) {
-          if (!us[u]) continue;
-          const double av = fabs(v64[u]);
-          if (av > bestabs || (av == bestabs && cs[u] < besti)) {
-            bestabs = av;
-            bestval = v64[u];
-            besti = cs[u];
-          }
-        }
-      }
-      const uint32_t value = ((bestval < 0.0 ? 1u : 0u) << (A.ell - 1)) | uint32_t(besti);
-      const int shift = 32 - A.ell * (fn + 1);
-      const uint32_t field = ((1u << A.ell) - 1u) << shift;
-      uint32_t* w = A.codes + int64_t(j) * A.cj + p * A.cp;
-      atomicAnd(w, ~field);
-      atomicOr(w, value << shift);
-    } else {
-      const bool bit = dot64(A.w32 + int64_t(q.row0) * A.d_pad, xrow, A.d) >= 0.0;
-      const int idx = int(q.info & 0xFFFFFu), b = int((q.info >> 20) & 63u);
-      if (kind == 1) {
-        uint32_t* w = A.codes + int64_t(idx) * A.cj + p * A.cp;
-        const uint32_t m = 1u << (31 - b);
-        if (bit) atomicOr(w, m); else atomicAnd(w, ~m);
-      } else {
-        unsigned long long* w = reinterpret_cast<unsigned long long*>(A.sk + int64_t(idx) * A.sm + p * A.sp);
-        const unsigned long long m = 1ull << b;
-        if (bit) atomicOr(w, m); else atomicAnd(w, ~m);
-      }
+__global__ void recheck_kernel(HashArgs A, int blocks_per_region) {
+  const int region = blockIdx.x / blocks_per_region, sub = blockIdx.x % blocks_per_region;
+  const uint32_t count = min(A.rq_count[region], A.rq_per);
+  const RecheckReq* rq = A.rq + size_t(region) * A.rq_per;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t stride = uint32_t(blocks_per_region) * blockDim.x;
+  for (uint32_t base = uint32_t(sub) * blockDim.x + uint32_t(warp) * 32u; base < count; base += stride) {
+    const uint32_t i = base + uint32_t(lane);
+    const bool has = i < count;
+    RecheckReq q;
+    q.p = q.row0 = q.info = 0u;
+    q.c[0] = q.c[1] = q.c[2] = q.c[3] = 0;
+    if (has) q = rq[i];
+    const bool full = has && (q.info >> 30) == 3u;
+    if (has && !full) recheck_one(A, q);
+    uint32_t fm = __ballot_sync(0xffffffffu, full);
+    while (fm) {
+      const int src = __ffs(fm) - 1;
+      fm &= fm - 1;
+      const uint32_t p = __shfl_sync(0xffffffffu, q.p, src);
+      const uint32_t row0 = __shfl_sync(0xffffffffu, q.row0, src);
+      const uint32_t info = __shfl_sync(0xffffffffu, q.info, src);
+      recheck_all_rows(A, p, row0, info);
     }
   }
 }
@@ -720,9 +938,8 @@ cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __
   A.rows_table = ix->lay.rows_table;
   A.seg_tables = ix->family == PF_CROSSPOLYTOPE ? ix->L : (ix->L + 3) / 4;
   A.segs = A.seg_tables + (ix->M + 1) / 2;
-  const int mtiles = int((npts + kBM - 1) / kBM);
-  A.split = std::max(1, std::min(A.segs, (2 * ix->num_sms + mtiles - 1) / mtiles));
-  A.items = mtiles * A.split;
+  const int64_t mtiles = (npts + kBM - 1) / kBM;
+  A.units = mtiles * A.segs;
   A.codes = codes;
   A.cj = cj;
   A.cp = cp;
@@ -730,9 +947,10 @@ cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __
   A.sm = sm;
   A.sp = sp;
   A.error = error;
-  A.rq = rq_cap ? rq : nullptr;
+  const int grid = int(std::min<int64_t>(A.units, ix->num_sms));
+  A.rq = rq_cap && rq_count ? rq : nullptr;
   A.rq_count = rq_count;
-  A.rq_cap = A.rq ? rq_cap : 0u;
+  A.rq_per = A.rq ? rq_cap / uint32_t(grid) : 0u;
   TensorMaps T;
   const int fn_rows = ix->family == PF_CROSSPOLYTOPE ? A.d_pad : 128;
   if (!make_map(&T.xh, xh, npts, A.d_pad, kBM) || !make_map(&T.xl, xl, npts, A.d_pad, kBM) ||
@@ -741,18 +959,13 @@ cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __
       !make_map(&T.wh_g, ix->Whi, ix->hash_rows, A.d_pad, 128) ||
       !make_map(&T.wl_g, ix->Wlo, ix->hash_rows, A.d_pad, 128))
     return cudaErrorInvalidValue;
-  if (A.rq) {
-    cudaError_t e0 = cudaMemsetAsync(rq_count, 0, sizeof(uint32_t), s);
-    if (e0 != cudaSuccess) return e0;
-  }
   const size_t smem = hash_tc_smem(A.d_pad);
   cudaError_t e = cudaFuncSetAttribute(hash_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  const int grid = std::min(A.items, ix->num_sms);
   hash_tc_kernel<<<grid, kThreads, smem, s>>>(A, T);
   e = cudaGetLastError();
   if (e != cudaSuccess || !A.rq) return e;
-  recheck_kernel<<<4 * ix->num_sms, 256, 0, s>>>(A);
+  recheck_kernel<<<4 * grid, 256, 0, s>>>(A, 4);
   return cudaGetLastError();
 }
 

@@ -128,8 +128,10 @@ cudaError_t launch_normalize(const float* in, int64_t rows, int d, int d_pad, fl
 // Hash rows x32 [npts][d_pad] (with its bfloat16 split xh + xl) under all L
 // repetitions and M sketches.  Codes written at codes[j*cj + p*cp], sketches
 // at sk[m*sm + p*sp].  Uses the tensor-core kernel when d_pad <= 128.
-// rq: optional queue of deferred float64 rechecks (capacity rq_cap, counter
-// rq_count); without one, or when it is full, rechecks run inline.
+// rq: optional queue of deferred float64 rechecks (capacity rq_cap, split
+// into one region per CTA of the hashing kernel; rq_count holds one counter per
+// region, at least ix->num_sms of them); without a queue, or where a region is
+// full, rechecks run inline.
 cudaError_t launch_hash(const pf_index* ix, const float* x32, const __nv_bfloat16* xh, const __nv_bfloat16* xl,
                         int64_t npts, uint32_t* codes, int64_t cj, int64_t cp, uint64_t* sk, int64_t sm,
                         int64_t sp, RecheckReq* rq, uint32_t* rq_count, uint32_t rq_cap, cudaStream_t s);
