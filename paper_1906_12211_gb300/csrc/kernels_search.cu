@@ -1,31 +1,33 @@
 // The adaptive k-NN query (Algorithm 1 as implemented in Sec. 4.1-4.2), one
-// warp per query, persistent CTAs pulling queries from an atomic counter so
-// queries of very different cost share one launch.
+// CTA of four warps per query, persistent CTAs pulling queries from an atomic
+// counter so queries of very different cost share one launch.
 //
-// Per round at prefix length i, for every repetition j the warp extends the
+// Per round at prefix length i, for every repetition j the CTA extends the
 // range [l, r) of positions around the query's code so that it covers the
 // block of codes sharing the first i bits, growing each side in whole
-// segments of B entries (Sec. 4.2, App. C).  The new positions of 32
-// repetitions are flattened and streamed lane-parallel, four per lane per step
-// so that many independent loads are in flight: position -> id -> sketch
-// Hamming filter (Sec. 4.2) -> compacted candidate buffer.  Buffered
-// candidates are scored (float32 canonical, or a bfloat16 estimate followed by
-// an exact float32 rerank of those whose estimate plus its error bound can
-// still reach the running k-th similarity) and offered to the top-k
-// accumulator (unique ids, ordered by similarity then id).  After the round
-// the stop test of Lemma 1 runs in float64.
+// segments of B entries (Sec. 4.2, App. C).  The round's new positions form at
+// most two runs per repetition; the runs are cut into chunks of 32 positions
+// (one per lane) and the four warps take the chunks in turn, four chunks per
+// step so that many coalesced loads are in flight: position -> id and sketch
+// -> Hamming filter (Sec. 4.2) -> the warp's compacted candidate buffer.
+// Buffered candidates are scored (float32 canonical, or a bfloat16 estimate
+// followed by an exact float32 rerank of those whose estimate plus its error
+// bound can still reach the k-th similarity known so far) and offered to the
+// warp's own top-k list (unique ids, ordered by similarity then id).  At every
+// threshold snapshot the warp lists are merged into the query's top-k, which
+// is the top-k of all candidates offered so far; after the round the stop test
+// of Lemma 1 runs in float64.
 //
 // Readings shared with the oracle: the sketch threshold is taken from the
 // top-k at the start of each round and, in a query's first round (which starts
 // with an empty top-k), also at the start of every group of 32 repetitions (the
-// paper refreshes it every k insertions, Sec. 4.2; a group is one warp step,
-// and all candidates of the previous group have been offered by then); the
-// stop test runs once per round (Sec. 4.1); the
-// canonical similarity is float32 with 32 partial sums (partial c takes the
-// coordinates = c mod 32 in index order by fused multiply-add) combined as
-// s[c] += s[c + w] for w = 16, 8, 4, 2, 1.  Only the filter depends on s_k and
-// it uses the round's snapshot, so the result does not depend on the order in
-// which lanes visit candidates.
+// paper refreshes it every k insertions, Sec. 4.2; all candidates of the
+// previous group have been offered by then); the stop test runs once per round
+// (Sec. 4.1); the canonical similarity is float32 with 32 partial sums
+// (partial c takes the coordinates = c mod 32 in index order by fused
+// multiply-add) combined as s[c] += s[c + w] for w = 16, 8, 4, 2, 1.  Only the
+// filter depends on s_k and it uses the snapshot, so the result does not
+// depend on which warp or lane visits a candidate, nor in which order.
 #include <cuda_bf16.h>
 
 #include "pf_internal.h"
@@ -35,10 +37,12 @@ namespace pf {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kWarps = 4;      // warps (queries in flight) per CTA
-constexpr int kUnroll = 4;     // candidate positions per lane per step
-constexpr int kCandBuf = 256;  // compacted candidate ids per warp
+constexpr int kQW = 4;          // warps per query (one CTA)
+constexpr int kThreads = 32 * kQW;
+constexpr int kUnroll = 4;      // 32-position chunks per warp step
+constexpr int kCandBuf = 384;   // compacted candidate ids per warp
 constexpr int kFlushAt = kCandBuf - 32 * kUnroll;
+constexpr int kGroup = 32;      // repetitions per threshold snapshot in a first round
 
 struct Dev {
   int n;
@@ -116,29 +120,16 @@ __device__ __forceinline__ uint32_t lower_bound(const uint32_t* c, uint32_t lo, 
   return lo;
 }
 
-struct WarpState {
-  float* q;         // [d_pad]
-  uint32_t* l;      // [L]
-  uint32_t* r;      // [L]
-  float* pq_s;      // [k_max]
-  uint32_t* pq_id;  // [k_max]
-  uint32_t* cbuf;   // [kCandBuf]
-};
-
-struct Counters {
-  uint32_t retrieved = 0, passed = 0, scored = 0, reranked = 0;
-};
-
-// Offer (s, id) to the sorted top-k of the warp (all lanes call with the same
-// arguments).  Returns the new size.
-__device__ __forceinline__ int pq_offer(WarpState& w, int size, int k, float s, uint32_t id, int lane) {
-  if (size == k && !better(s, id, w.pq_s[k - 1], w.pq_id[k - 1])) return size;
+// Offer (s, id) to the sorted top-k list (ps, pid) of `size` entries (all
+// lanes of the warp call with the same arguments).  Returns the new size.
+__device__ __forceinline__ int pq_offer(float* ps, uint32_t* pid, int size, int k, float s, uint32_t id, int lane) {
+  if (size == k && !better(s, id, ps[k - 1], pid[k - 1])) return size;
   bool dup = false;
   int cnt = 0;
   for (int t = lane; t < size; t += 32) {
-    const uint32_t it = w.pq_id[t];
+    const uint32_t it = pid[t];
     dup |= it == id;
-    cnt += better(w.pq_s[t], it, s, id) ? 1 : 0;
+    cnt += better(ps[t], it, s, id) ? 1 : 0;
   }
   if (__any_sync(kFull, dup)) return size;
 #pragma unroll
@@ -152,8 +143,8 @@ __device__ __forceinline__ int pq_offer(WarpState& w, int size, int k, float s, 
   for (int u = 0; u < kMaxK / 32; ++u) {
     const int t = lane + 32 * u;
     if (t > pos && t < nsize) {
-      vs[u] = w.pq_s[t - 1];
-      vi[u] = w.pq_id[t - 1];
+      vs[u] = ps[t - 1];
+      vi[u] = pid[t - 1];
     }
   }
   __syncwarp();
@@ -161,13 +152,13 @@ __device__ __forceinline__ int pq_offer(WarpState& w, int size, int k, float s, 
   for (int u = 0; u < kMaxK / 32; ++u) {
     const int t = lane + 32 * u;
     if (t > pos && t < nsize) {
-      w.pq_s[t] = vs[u];
-      w.pq_id[t] = vi[u];
+      ps[t] = vs[u];
+      pid[t] = vi[u];
     }
   }
   if (lane == 0) {
-    w.pq_s[pos] = s;
-    w.pq_id[pos] = id;
+    ps[pos] = s;
+    pid[pos] = id;
   }
   __syncwarp();
   return nsize;
@@ -223,22 +214,23 @@ __device__ __forceinline__ void sim_canonical2(const float* __restrict__ q, cons
   out_b = __fadd_rn(__fadd_rn(sb.x, sb.z), __fadd_rn(sb.y, sb.w));
 }
 
-// bfloat16 estimate of <q, x> by the 4 lanes of a group: float32 query against
-// the bfloat16 row (chunks of 8 elements g4, g4+4, ...), any summation order.
-template <int NT>
-__device__ __forceinline__ float sim_bf16(const float* __restrict__ q, const __nv_bfloat16* __restrict__ row,
-                                          int d_pad, int g4, unsigned gmask) {
+// bfloat16 estimate of <q, x> by a pair of lanes: float32 query against the
+// bfloat16 row, lane h of the pair takes the 8-element chunks h, h+2, ...; any
+// summation order (the error bound covers every order).
+template <int NT2>
+__device__ __forceinline__ float sim_bf16_pair(const float* __restrict__ q, const __nv_bfloat16* __restrict__ row,
+                                               int d_pad, int h) {
   const uint4* r8 = reinterpret_cast<const uint4*>(row);
-  uint4 v[NT];
+  uint4 v[NT2];
 #pragma unroll
-  for (int t = 0; t < NT; ++t) {
-    const int ch = g4 + 4 * t;
+  for (int t = 0; t < NT2; ++t) {
+    const int ch = h + 2 * t;
     v[t] = ch * 8 < d_pad ? __ldg(r8 + ch) : make_uint4(0u, 0u, 0u, 0u);
   }
   float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
-  for (int t = 0; t < NT; ++t) {
-    const int ch = g4 + 4 * t;
+  for (int t = 0; t < NT2; ++t) {
+    const int ch = h + 2 * t;
     if (ch * 8 < d_pad) {
       const float4 qa = reinterpret_cast<const float4*>(q)[2 * ch];
       const float4 qb = reinterpret_cast<const float4*>(q)[2 * ch + 1];
@@ -252,110 +244,139 @@ __device__ __forceinline__ float sim_bf16(const float* __restrict__ q, const __n
       acc1 = fmaf(qb.w, __uint_as_float(v[t].w & 0xffff0000u), acc1);
     }
   }
-  float acc = acc0 + acc1;
-  acc += __shfl_xor_sync(gmask, acc, 2, 4);
-  acc += __shfl_xor_sync(gmask, acc, 1, 4);
-  return acc;
+  const float acc = acc0 + acc1;
+  return acc + __shfl_xor_sync(kFull, acc, 1);
+}
+
+struct Counters {
+  uint32_t retrieved = 0, passed = 0, scored = 0, reranked = 0;
+};
+
+// Order-preserving map of a float to an unsigned key (for atomicMax).
+__device__ __forceinline__ uint32_t order_key(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float order_value(uint32_t key) {
+  return __uint_as_float((key & 0x80000000u) ? (key & 0x7FFFFFFFu) : ~key);
 }
 
 // Exact float32 similarities of the `cnt` ids at the front of cbuf, each
-// offered to the top-k (8 candidates per step: 4 groups of 8 lanes, 2 rows
-// each).
+// offered to the list (ps, pid) (8 candidates per step: 4 groups of 8 lanes,
+// 2 rows each).
 template <int NT>
-__device__ __forceinline__ int canonical_and_offer(const Dev& P, WarpState& w, int cnt, int size, int k, int lane) {
+__device__ __forceinline__ int canonical_and_offer(const Dev& P, const float* q, const uint32_t* cbuf, int cnt,
+                                                   float* ps, uint32_t* pid, int size, int k, int lane) {
   const int g = lane >> 3, g8 = lane & 7;
   const unsigned gmask = 0xffu << (lane & ~7);
   for (int c0 = 0; c0 < cnt; c0 += 8) {
     const int ca = c0 + g, cb = c0 + 4 + g;
-    const uint32_t ida = ca < cnt ? w.cbuf[ca] : w.cbuf[c0];
-    const uint32_t idb = cb < cnt ? w.cbuf[cb] : w.cbuf[c0];
+    const uint32_t ida = ca < cnt ? cbuf[ca] : cbuf[c0];
+    const uint32_t idb = cb < cnt ? cbuf[cb] : cbuf[c0];
     float sa, sb;
-    sim_canonical2<NT>(w.q, P.x32 + size_t(ida) * P.d_pad, P.x32 + size_t(idb) * P.d_pad, P.d_pad, g8, gmask, sa, sb);
+    sim_canonical2<NT>(q, P.x32 + size_t(ida) * P.d_pad, P.x32 + size_t(idb) * P.d_pad, P.d_pad, g8, gmask, sa, sb);
     const int m = min(8, cnt - c0);
     for (int t = 0; t < m; ++t) {
       const int src = (t & 3) * 8;
       const float s = __shfl_sync(kFull, t < 4 ? sa : sb, src);
       const uint32_t id = __shfl_sync(kFull, t < 4 ? ida : idb, src);
-      size = pq_offer(w, size, k, s, id, lane);
+      size = pq_offer(ps, pid, size, k, s, id, lane);
     }
   }
   return size;
 }
 
-// Score the cnt buffered candidate ids and offer them to the top-k.
-template <int NT>
-__device__ __forceinline__ int flush_candidates(const Dev& P, WarpState& w, int cnt, int size, int k, int lane,
+// Score the cnt buffered candidate ids of a warp and offer them to its list.
+// kth_known: a k-th similarity already reached by the query (or -inf).
+template <int NT, int NT2>
+__device__ __forceinline__ int flush_candidates(const Dev& P, const float* q, uint32_t* cbuf, int cnt, float* ps,
+                                                uint32_t* pid, int size, int k, uint32_t* kth_shared, int lane,
                                                 Counters& ct) {
   if (lane == 0) ct.scored += cnt;
-  if (P.scoring != 1) return canonical_and_offer<NT>(P, w, cnt, size, k, lane);
-  // bfloat16 estimates, 8 rows per step (4 lanes each).  A candidate can enter
-  // the top-k only if its exact similarity reaches the running k-th, which
-  // never decreases; the estimate is within bf16_err of the exact value, so
-  // candidates with estimate + bf16_err below the current k-th are dropped and
-  // the others are compacted in place at the front of cbuf.
-  const int g = lane >> 2, g4 = lane & 3;
-  const unsigned gmask = 0xfu << (lane & ~3);
-  const bool full = size == k;
-  const float kth = full ? w.pq_s[k - 1] : -INFINITY;
+  if (P.scoring != 1) return canonical_and_offer<NT>(P, q, cbuf, cnt, ps, pid, size, k, lane);
+  // bfloat16 estimates, 16 rows per step (a pair of lanes each).  A candidate
+  // can enter the final top-k only if its exact similarity reaches every k-th
+  // similarity the query has already reached (that of the merged top-k, of
+  // this warp's list, or of another warp's list, shared as the maximum: each
+  // is a k-th of a subset of the candidates); the estimate is within bf16_err
+  // of the exact value, so candidates whose estimate + bf16_err is below it
+  // are dropped and the others are compacted in place at the front of cbuf.
+  const int g = lane >> 1, h = lane & 1;
+  const float kth = fmaxf(order_value(*kth_shared), size == k ? ps[k - 1] : -INFINITY);
   int nr = 0;
-  for (int c0 = 0; c0 < cnt; c0 += 8) {
+  for (int c0 = 0; c0 < cnt; c0 += 16) {
     const int c = c0 + g;
     const bool valid = c < cnt;
-    const uint32_t id = valid ? w.cbuf[c] : w.cbuf[c0];
-    const float est = sim_bf16<NT>(w.q, P.x16 + size_t(id) * P.d_pad, P.d_pad, g4, gmask);
-    const bool need = valid && (!full || est + P.bf16_err >= kth);
-    const unsigned b = __ballot_sync(kFull, need && g4 == 0);
+    const uint32_t id = valid ? cbuf[c] : cbuf[c0];
+    const float est = sim_bf16_pair<NT2>(q, P.x16 + size_t(id) * P.d_pad, P.d_pad, h);
+    const bool need = valid && est + P.bf16_err >= kth;
+    const unsigned b = __ballot_sync(kFull, need && h == 0);
     __syncwarp();
-    if (need && g4 == 0) w.cbuf[nr + __popc(b & ((1u << lane) - 1u))] = id;
+    if (need && h == 0) cbuf[nr + __popc(b & ((1u << lane) - 1u))] = id;
     nr += __popc(b);
     __syncwarp();
   }
   if (lane == 0) ct.reranked += nr;
-  return canonical_and_offer<NT>(P, w, nr, size, k, lane);
+  size = canonical_and_offer<NT>(P, q, cbuf, nr, ps, pid, size, k, lane);
+  if (lane == 0 && size == k) atomicMax(kth_shared, order_key(ps[k - 1]));
+  return size;
 }
 
 // NT = d_pad / 32 rounded up: float4 chunks of a float32 row per lane of an
-// 8-lane group (and 16-byte chunks of a bfloat16 row per lane of a 4-lane group)
-template <int NT>
-__global__ void __launch_bounds__(kWarps * 32, 8) search_kernel(Dev P) {
+// 8-lane group; NT2 = d_pad / 16 rounded up: 16-byte chunks of a bfloat16 row
+// per lane of a pair
+template <int NT, int NT2>
+__global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int d_pad = P.d_pad, L = P.L, kmax = P.k_max;
-  // per-warp shared memory: q | l | r | pq_s | pq_id | cbuf
-  const size_t per_warp = size_t(d_pad) * 4 + size_t(L) * 8 + size_t(kmax) * 8 + kCandBuf * 4;
-  const size_t per_warp_al = (per_warp + 15) & ~size_t(15);
-  unsigned char* base = smem_raw + per_warp_al * warp;
-  WarpState w;
-  w.q = reinterpret_cast<float*>(base);
-  w.l = reinterpret_cast<uint32_t*>(base + size_t(d_pad) * 4);
-  w.r = w.l + L;
-  w.pq_s = reinterpret_cast<float*>(w.r + L);
-  w.pq_id = reinterpret_cast<uint32_t*>(w.pq_s + kmax);
-  w.cbuf = w.pq_id + kmax;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int d_pad = P.d_pad, L = P.L, kmax = P.k_max, M = P.M;
+  // shared memory: q | qsk | l | r | la | lc | ra | rc | cpre | gs | gid | ws | wid | cbuf
+  float* q = reinterpret_cast<float*>(smem_raw);
+  uint64_t* qsk = reinterpret_cast<uint64_t*>(q + d_pad);
+  uint32_t* sl = reinterpret_cast<uint32_t*>(qsk + M);
+  uint32_t* sr = sl + L;
+  uint32_t* la = sr + L;
+  uint32_t* lc = la + L;
+  uint32_t* ra = lc + L;
+  uint32_t* rc = ra + L;
+  uint32_t* cpre = rc + L;  // [L + 1]
+  float* gs = reinterpret_cast<float*>(cpre + L + 1);
+  uint32_t* gid = reinterpret_cast<uint32_t*>(gs + kmax);
+  float* ws = reinterpret_cast<float*>(gid + kmax);              // [kQW][kmax]
+  uint32_t* wid = reinterpret_cast<uint32_t*>(ws + kQW * kmax);  // [kQW][kmax]
+  uint32_t* cbuf = wid + kQW * kmax + warp * kCandBuf;           // this warp's buffer
+  float* my_s = ws + warp * kmax;
+  uint32_t* my_id = wid + warp * kmax;
+  __shared__ int s_qi, s_size, s_stop, s_wsize[kQW];
+  __shared__ uint32_t s_kth;  // order key of the largest k-th similarity reached by a list of the query
+  __shared__ uint32_t s_scan[kQW];
+  __shared__ uint32_t s_ct[kQW][4];
   const uint32_t n = uint32_t(P.n);
   const uint32_t lt_mask = (1u << lane) - 1u;
+  const int per = (L + kThreads - 1) / kThreads;  // repetitions per thread in the range pass
 
   for (;;) {
-    int qi = 0;
-    if (lane == 0) qi = atomicAdd(P.counter, 1);
-    qi = __shfl_sync(kFull, qi, 0);
+    if (tid == 0) s_qi = atomicAdd(P.counter, 1);
+    __syncthreads();
+    const int qi = s_qi;
     if (qi >= P.Q) break;
 
     const int k = P.k[qi];
     const double rec = P.recall[qi];
     if (k < 1 || k > kmax || !(rec > 0.0 && rec < 1.0)) {
-      if (lane == 0) atomicOr(P.counter + 1, 1);
-      for (int t = lane; t < kmax; t += 32) {
+      if (tid == 0) atomicOr(P.counter + 1, 1);
+      for (int t = tid; t < kmax; t += kThreads) {
         P.out_ids[size_t(qi) * kmax + t] = 0xffffffffu;
         P.out_sims[size_t(qi) * kmax + t] = -INFINITY;
       }
+      __syncthreads();  // s_qi is rewritten by the next fetch
       continue;
     }
     const double delta = 1.0 - rec;
     const float* qg = P.qx + size_t(qi) * d_pad;
-    for (int i = lane; i < d_pad; i += 32) w.q[i] = qg[i];
+    for (int i = tid; i < d_pad; i += kThreads) q[i] = qg[i];
+    for (int m = tid; m < M; m += kThreads) qsk[m] = P.qsk[size_t(qi) * M + m];
     const uint32_t* qc = P.qcodes + size_t(qi) * L;
-    const uint64_t* qs = P.qsk + size_t(qi) * P.M;
     // start depth: the plain schedule starts at K (Sec. 4.1); a given start i0
     // in [0, K) takes the whole block at i0 in the first round
     int i0 = P.Kb;
@@ -364,28 +385,34 @@ __global__ void __launch_bounds__(kWarps * 32, 8) search_kernel(Dev P) {
       if (sd >= 0 && sd < P.Kb) i0 = sd;
     }
     // initial empty range at the first code >= the query's code
-    for (int j = lane; j < L; j += 32) {
+    for (int j = tid; j < L; j += kThreads) {
       const uint32_t c = qc[j];
       const uint32_t* pj = P.pfx + size_t(j) * kPrefixSize;
       const uint32_t t = c >> (32 - kPrefixBits);
       const uint32_t lb = lower_bound(P.codes + size_t(j) * n, __ldg(pj + t), __ldg(pj + t + 1), c);
-      w.l[j] = lb;
-      w.r[j] = lb;
+      sl[j] = lb;
+      sr[j] = lb;
     }
-    __syncwarp();
+    if (tid == 0) {
+      s_size = 0;
+      s_kth = order_key(-INFINITY);
+    }
+    if (lane == 0) s_wsize[warp] = 0;
+    __syncthreads();
 
-    int size = 0, rounds = 0, depth = i0, prev = -1, stop_depth = i0;  // prev < 0: probe both sides
+    int rounds = 0, depth = i0, prev = -1, stop_depth = i0;  // prev < 0: probe both sides
     int full_depth = -1;  // first depth after whose round k points were held
     Counters ct;
+    int wsize = 0;  // entries of this warp's list
     for (;;) {
       if (depth == 0) {
         // prefix length 0: every point collides in every repetition, so the
         // round is a linear scan of all points (Lemma 1, i = 0), unfiltered.
         int nb = 0;
-        for (uint32_t b0 = 0; b0 < n; b0 += 32) {
+        for (uint32_t b0 = uint32_t(warp) * 32u; b0 < n; b0 += kThreads) {
           const uint32_t id = b0 + lane;
           const unsigned m = __ballot_sync(kFull, id < n);
-          if (id < n) w.cbuf[nb + __popc(m & lt_mask)] = id;
+          if (id < n) cbuf[nb + __popc(m & lt_mask)] = id;
           nb += __popc(m);
           if (lane == 0) {
             ct.retrieved += __popc(m);
@@ -393,185 +420,247 @@ __global__ void __launch_bounds__(kWarps * 32, 8) search_kernel(Dev P) {
           }
           __syncwarp();
           if (nb > kFlushAt) {
-            size = flush_candidates<NT>(P, w, nb, size, k, lane, ct);
+            wsize = flush_candidates<NT, NT2>(P, q, cbuf, nb, my_s, my_id, wsize, k, &s_kth, lane, ct);
             nb = 0;
           }
         }
-        if (nb) size = flush_candidates<NT>(P, w, nb, size, k, lane, ct);
+        if (nb) wsize = flush_candidates<NT, NT2>(P, q, cbuf, nb, my_s, my_id, wsize, k, &s_kth, lane, ct);
+        if (lane == 0) s_wsize[warp] = wsize;
+        __syncthreads();
+        if (warp == 0) {
+          int size = s_size;
+          for (int w = 0; w < kQW; ++w)
+            for (int t = 0; t < s_wsize[w]; ++t) size = pq_offer(gs, gid, size, k, ws[w * kmax + t], wid[w * kmax + t], lane);
+          if (lane == 0) {
+            s_size = size;
+            if (size == k) atomicMax(&s_kth, order_key(gs[k - 1]));
+          }
+        }
+        __syncthreads();
         ++rounds;
         stop_depth = 0;
-        if (size == k && full_depth < 0) full_depth = 0;
+        if (s_size == k && full_depth < 0) full_depth = 0;
         break;
       }
+      // ---- range pass: thread t extends repetitions [t*per, (t+1)*per)
       const uint32_t mask = 0xffffffffu << (32 - depth);
       const bool single = prev == depth + 1;
-      int nb = 0;
-      int tau = 64;
-      for (int jb = 0; jb < L; jb += 32) {
-        if (jb == 0 || rounds == 0) {
-          // threshold snapshot; the previous group's candidates go into the top-k first
-          if (nb) {
-            size = flush_candidates<NT>(P, w, nb, size, k, lane, ct);
-            nb = 0;
-          }
-          tau = size == k ? filter_tau(P, w.pq_s[k - 1]) : 64;
-        }
-        const int j = jb + lane;
-        uint32_t l = 0, r = 0, nl = 0, nr = 0;
-        if (j < L) {
-          const uint32_t qcj = qc[j];
-          const uint32_t* cj = P.codes + size_t(j) * n;
-          l = w.l[j];
-          r = w.r[j];
-          nl = l;
-          nr = r;
-          // in a one-bit step only the side of the dropped bit can grow
-          // (bit `depth`, counted from the top, of the query's code)
-          const bool dropped_one = (qcj >> (31 - depth)) & 1u;
-          const bool try_left = !single || dropped_one;
-          const bool try_right = !single || !dropped_one;
-          const uint32_t B = uint32_t(P.B);
-          if (try_left && l > 0 && prefix_match(__ldg(cj + l - 1), qcj, mask)) {
-            // smallest m >= 1 with l - B*m <= 0 or codes[l - B*m - 1] outside the block
-            uint32_t lo = 0, hi = 1;
-            for (;;) {
-              const int64_t pos = int64_t(l) - int64_t(B) * hi;
-              if (pos <= 0 || !prefix_match(__ldg(cj + pos - 1), qcj, mask)) break;
-              lo = hi;
-              hi *= 2;
-            }
-            while (hi - lo > 1) {
-              const uint32_t mid = (lo + hi) >> 1;
-              const int64_t pos = int64_t(l) - int64_t(B) * mid;
-              if (pos <= 0 || !prefix_match(__ldg(cj + pos - 1), qcj, mask)) hi = mid; else lo = mid;
-            }
+      uint32_t my_chunks = 0;
+      const int jlo = min(L, tid * per), jhi = min(L, jlo + per);
+      for (int j = jlo; j < jhi; ++j) {
+        const uint32_t qcj = qc[j];
+        const uint32_t* cj = P.codes + size_t(j) * n;
+        const uint32_t l = sl[j], r = sr[j];
+        uint32_t nl = l, nr = r;
+        // in a one-bit step only the side of the dropped bit can grow
+        // (bit `depth`, counted from the top, of the query's code)
+        const bool dropped_one = (qcj >> (31 - depth)) & 1u;
+        const bool try_left = !single || dropped_one;
+        const bool try_right = !single || !dropped_one;
+        const uint32_t B = uint32_t(P.B);
+        if (try_left && l > 0 && prefix_match(__ldg(cj + l - 1), qcj, mask)) {
+          // smallest m >= 1 with l - B*m <= 0 or codes[l - B*m - 1] outside the block
+          uint32_t lo = 0, hi = 1;
+          for (;;) {
             const int64_t pos = int64_t(l) - int64_t(B) * hi;
-            nl = pos < 0 ? 0u : uint32_t(pos);
+            if (pos <= 0 || !prefix_match(__ldg(cj + pos - 1), qcj, mask)) break;
+            lo = hi;
+            hi *= 2;
           }
-          if (try_right && r < n && prefix_match(__ldg(cj + r), qcj, mask)) {
-            uint32_t lo = 0, hi = 1;
-            for (;;) {
-              const int64_t pos = int64_t(r) + int64_t(B) * hi;
-              if (pos >= int64_t(n) || !prefix_match(__ldg(cj + pos), qcj, mask)) break;
-              lo = hi;
-              hi *= 2;
-            }
-            while (hi - lo > 1) {
-              const uint32_t mid = (lo + hi) >> 1;
-              const int64_t pos = int64_t(r) + int64_t(B) * mid;
-              if (pos >= int64_t(n) || !prefix_match(__ldg(cj + pos), qcj, mask)) hi = mid; else lo = mid;
-            }
+          while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            const int64_t pos = int64_t(l) - int64_t(B) * mid;
+            if (pos <= 0 || !prefix_match(__ldg(cj + pos - 1), qcj, mask)) hi = mid; else lo = mid;
+          }
+          const int64_t pos = int64_t(l) - int64_t(B) * hi;
+          nl = pos < 0 ? 0u : uint32_t(pos);
+        }
+        if (try_right && r < n && prefix_match(__ldg(cj + r), qcj, mask)) {
+          uint32_t lo = 0, hi = 1;
+          for (;;) {
             const int64_t pos = int64_t(r) + int64_t(B) * hi;
-            nr = pos > int64_t(n) ? n : uint32_t(pos);
+            if (pos >= int64_t(n) || !prefix_match(__ldg(cj + pos), qcj, mask)) break;
+            lo = hi;
+            hi *= 2;
           }
-          w.l[j] = nl;
-          w.r[j] = nr;
+          while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            const int64_t pos = int64_t(r) + int64_t(B) * mid;
+            if (pos >= int64_t(n) || !prefix_match(__ldg(cj + pos), qcj, mask)) hi = mid; else lo = mid;
+          }
+          const int64_t pos = int64_t(r) + int64_t(B) * hi;
+          nr = pos > int64_t(n) ? n : uint32_t(pos);
         }
-        const uint32_t cl = l - nl;
-        const uint32_t cnt = cl + (nr - r);
-        // inclusive warp scan of cnt
-        uint32_t inc = cnt;
+        sl[j] = nl;
+        sr[j] = nr;
+        la[j] = nl;
+        lc[j] = l - nl;
+        ra[j] = r;
+        rc[j] = nr - r;
+        my_chunks += ((l - nl + 31) >> 5) + ((nr - r + 31) >> 5);
+      }
+      // exclusive scan of the chunk counts over the repetitions -> cpre
+      uint32_t inc = my_chunks;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const uint32_t v = __shfl_up_sync(kFull, inc, off);
-          if (lane >= off) inc += v;
-        }
-        const uint32_t ex = inc - cnt;
-        const uint32_t total = __shfl_sync(kFull, inc, 31);
-        if (lane == 0) ct.retrieved += total;
-        for (uint32_t e0 = 0; e0 < total; e0 += 32 * kUnroll) {
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, inc, off);
+        if (lane >= off) inc += v;
+      }
+      if (lane == 31) s_scan[warp] = inc;
+      __syncthreads();
+      uint32_t run = inc - my_chunks;
+      for (int w = 0; w < warp; ++w) run += s_scan[w];
+      for (int j = jlo; j < jhi; ++j) {
+        cpre[j] = run;
+        run += ((lc[j] + 31) >> 5) + ((rc[j] + 31) >> 5);
+      }
+      if (tid == kThreads - 1) cpre[L] = run;
+      __syncthreads();
+
+      // ---- stream the chunks, group by group
+      const int ngroups = rounds == 0 ? (L + kGroup - 1) / kGroup : 1;
+      for (int grp = 0; grp < ngroups; ++grp) {
+        const int j0 = rounds == 0 ? grp * kGroup : 0;
+        const int j1 = rounds == 0 ? min(L, j0 + kGroup) : L;
+        // threshold snapshot: every earlier candidate is in the merged top-k
+        const int gsize = s_size;
+        const float gkth = gsize == k ? gs[k - 1] : -INFINITY;
+        const int tau = gsize == k ? filter_tau(P, gkth) : 64;
+        const uint32_t c_end = cpre[j1];
+        int jc = j0;
+        int nb = 0;
+        for (uint32_t c0 = cpre[j0] + uint32_t(warp) * kUnroll; c0 < c_end; c0 += kQW * kUnroll) {
           uint32_t id[kUnroll], pos[kUnroll];
           int jo[kUnroll];
           bool valid[kUnroll];
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) {
-            const uint32_t idx = e0 + 32 * u + lane;
-            // owner lane: largest o with ex_o <= idx
-            int o = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-              const uint32_t v = __shfl_sync(kFull, ex, o + step);
-              if (v <= idx) o += step;
+            const uint32_t c = c0 + u;
+            valid[u] = false;
+            pos[u] = 0;
+            jo[u] = jc;
+            if (c < c_end) {
+              while (cpre[jc + 1] <= c) ++jc;  // chunk -> repetition (c only grows)
+              const uint32_t lk = c - cpre[jc];
+              const uint32_t nlc = (lc[jc] + 31) >> 5;
+              uint32_t off, len, start;
+              if (lk < nlc) {
+                off = lk * 32 + lane;
+                len = lc[jc];
+                start = la[jc];
+              } else {
+                off = (lk - nlc) * 32 + lane;
+                len = rc[jc];
+                start = ra[jc];
+              }
+              valid[u] = off < len;
+              pos[u] = start + off;
+              jo[u] = jc;
             }
-            const uint32_t ex_o = __shfl_sync(kFull, ex, o);
-            const uint32_t cl_o = __shfl_sync(kFull, cl, o);
-            const uint32_t nl_o = __shfl_sync(kFull, nl, o);
-            const uint32_t r_o = __shfl_sync(kFull, r, o);
-            valid[u] = idx < total;
-            const uint32_t off = idx - ex_o;
-            jo[u] = jb + o;
-            pos[u] = off < cl_o ? nl_o + off : r_o + (off - cl_o);
           }
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u)
             id[u] = valid[u] ? __ldg(P.ids + size_t(jo[u]) * n + pos[u]) : 0u;
           bool pass[kUnroll];
           if (P.filter) {
-            uint64_t h[kUnroll];
+            uint64_t hd[kUnroll];
             if (P.skc) {  // the sketch sits at the same position as the id
 #pragma unroll
               for (int u = 0; u < kUnroll; ++u)
-                h[u] = valid[u] ? __ldg(P.skc + size_t(jo[u]) * n + pos[u]) ^ qs[jo[u] % P.M] : 0ull;
+                hd[u] = valid[u] ? __ldg(P.skc + size_t(jo[u]) * n + pos[u]) ^ qsk[jo[u] % M] : 0ull;
             } else {
 #pragma unroll
               for (int u = 0; u < kUnroll; ++u) {
-                const int m = jo[u] % P.M;
-                h[u] = valid[u] ? __ldg(P.sk + size_t(m) * n + id[u]) ^ qs[m] : 0ull;
+                const int m = jo[u] % M;
+                hd[u] = valid[u] ? __ldg(P.sk + size_t(m) * n + id[u]) ^ qsk[m] : 0ull;
               }
             }
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) pass[u] = valid[u] && __popcll(h[u]) <= tau;
+            for (int u = 0; u < kUnroll; ++u) pass[u] = valid[u] && __popcll(hd[u]) <= tau;
           } else {
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) pass[u] = valid[u];
           }
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) {
+            const unsigned vm = __ballot_sync(kFull, valid[u]);
             const unsigned pm = __ballot_sync(kFull, pass[u]);
-            if (pass[u]) w.cbuf[nb + __popc(pm & lt_mask)] = id[u];
+            if (pass[u]) cbuf[nb + __popc(pm & lt_mask)] = id[u];
             nb += __popc(pm);
-            if (lane == 0) ct.passed += __popc(pm);
+            if (lane == 0) {
+              ct.retrieved += __popc(vm);
+              ct.passed += __popc(pm);
+            }
           }
           __syncwarp();
           if (nb > kFlushAt) {
-            size = flush_candidates<NT>(P, w, nb, size, k, lane, ct);
+            wsize = flush_candidates<NT, NT2>(P, q, cbuf, nb, my_s, my_id, wsize, k, &s_kth, lane, ct);
             nb = 0;
           }
         }
+        if (nb) wsize = flush_candidates<NT, NT2>(P, q, cbuf, nb, my_s, my_id, wsize, k, &s_kth, lane, ct);
+        // merge the warp lists into the query's top-k
+        if (lane == 0) s_wsize[warp] = wsize;
+        __syncthreads();
+        if (warp == 0) {
+          int size = s_size;
+          for (int w = 0; w < kQW; ++w)
+            for (int t = 0; t < s_wsize[w]; ++t) size = pq_offer(gs, gid, size, k, ws[w * kmax + t], wid[w * kmax + t], lane);
+          if (lane == 0) {
+            s_size = size;
+            if (size == k) atomicMax(&s_kth, order_key(gs[k - 1]));
+          }
+        }
+        wsize = 0;
+        __syncthreads();
       }
-      if (nb) size = flush_candidates<NT>(P, w, nb, size, k, lane, ct);
       ++rounds;
       stop_depth = depth;
+      const int size = s_size;
       if (size == k && full_depth < 0) full_depth = depth;
-      int stop = 0;
-      if (lane == 0 && size == k) {
-        const double p = collision_prob(P, double(w.pq_s[k - 1]), depth);
-        const double fail = ipow(__dsub_rn(1.0, p), L);
-        stop = fail <= delta ? 1 : 0;
+      if (tid == 0) {
+        int stop = 0;
+        if (size == k) {
+          const double p = collision_prob(P, double(gs[k - 1]), depth);
+          const double fail = ipow(__dsub_rn(1.0, p), L);
+          stop = fail <= delta ? 1 : 0;
+        }
+        s_stop = stop;
       }
-      stop = __shfl_sync(kFull, stop, 0);
+      __syncthreads();
+      const int stop = s_stop;
       if (stop) break;
       prev = depth;
       depth -= 1;
     }
 
-    for (int t = lane; t < kmax; t += 32) {
-      P.out_ids[size_t(qi) * kmax + t] = t < size ? w.pq_id[t] : 0xffffffffu;
-      P.out_sims[size_t(qi) * kmax + t] = t < size ? w.pq_s[t] : -INFINITY;
+    const int size = s_size;
+    for (int t = tid; t < kmax; t += kThreads) {
+      P.out_ids[size_t(qi) * kmax + t] = t < size ? gid[t] : 0xffffffffu;
+      P.out_sims[size_t(qi) * kmax + t] = t < size ? gs[t] : -INFINITY;
     }
-    if (P.stats && lane == 0) {
+    if (lane == 0) {
+      s_ct[warp][0] = ct.retrieved;
+      s_ct[warp][1] = ct.passed;
+      s_ct[warp][2] = ct.scored;
+      s_ct[warp][3] = ct.reranked;
+    }
+    __syncthreads();
+    if (P.stats && tid == 0) {
       pf_query_stats st;
       st.start_depth = i0;
       st.stop_depth = stop_depth;
       st.rounds = rounds;
       st.full_depth = full_depth;
-      st.retrieved = ct.retrieved;
-      st.passed_filter = ct.passed;
-      st.scored = ct.scored;
-      st.reranked = P.scoring == 1 ? ct.reranked : 0;
+      int64_t sum[4] = {0, 0, 0, 0};
+      for (int w = 0; w < kQW; ++w)
+        for (int c = 0; c < 4; ++c) sum[c] += s_ct[w][c];
+      st.retrieved = sum[0];
+      st.passed_filter = sum[1];
+      st.scored = sum[2];
+      st.reranked = P.scoring == 1 ? sum[3] : 0;
       P.stats[qi] = st;
     }
-    __syncwarp();
   }
 }
 
@@ -613,20 +702,23 @@ cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t 
   P.out_sims = a.out_sims;
   P.stats = a.stats;
   P.counter = a.counter;
-  const size_t per_warp = size_t(P.d_pad) * 4 + size_t(P.L) * 8 + size_t(P.k_max) * 8 + kCandBuf * 4;
-  const size_t smem = ((per_warp + 15) & ~size_t(15)) * kWarps;
+  // q | qsk | l, r, la, lc, ra, rc | cpre | top-k | warp lists | warp candidate buffers
+  const size_t smem = size_t(P.d_pad) * 4 + size_t(P.M) * 8 + size_t(P.L) * 24 + size_t(P.L + 1) * 4 +
+                      size_t(P.k_max) * 8 * (1 + kQW) + size_t(kCandBuf) * 4 * kQW;
   const int nt = (P.d_pad + 31) / 32;
-  auto kern = nt <= 1 ? search_kernel<1> : nt <= 2 ? search_kernel<2> : nt <= 4 ? search_kernel<4> : search_kernel<8>;
+  auto kern = nt <= 1   ? search_kernel<1, 2>
+              : nt <= 2 ? search_kernel<2, 4>
+              : nt <= 4 ? search_kernel<4, 8>
+                        : search_kernel<8, 16>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int blocks = ix->num_sms * per_sm;
-  const int need = (a.Q + kWarps - 1) / kWarps;
-  if (blocks > need) blocks = need;
-  kern<<<blocks, kWarps * 32, smem, s>>>(P);
+  if (blocks > a.Q) blocks = a.Q;
+  kern<<<blocks, kThreads, smem, s>>>(P);
   return cudaGetLastError();
 }
 
