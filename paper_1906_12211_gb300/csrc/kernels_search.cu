@@ -132,29 +132,25 @@ __device__ __forceinline__ int pq_offer(float* ps, uint32_t* pid, int size, int 
     cnt += better(ps[t], it, s, id) ? 1 : 0;
   }
   if (__any_sync(kFull, dup)) return size;
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(kFull, cnt, off);
-  const int pos = cnt;
+  const int pos = __reduce_add_sync(kFull, cnt);
   const int nsize = size < k ? size + 1 : k;
-  // shift [pos, nsize-1) one slot right
-  float vs[kMaxK / 32];
-  uint32_t vi[kMaxK / 32];
-#pragma unroll
-  for (int u = 0; u < kMaxK / 32; ++u) {
-    const int t = lane + 32 * u;
-    if (t > pos && t < nsize) {
-      vs[u] = ps[t - 1];
-      vi[u] = pid[t - 1];
+  // shift [pos, nsize - 1) one slot right, the highest block of 32 slots
+  // first (a block reads only slots of its own or of the next lower block)
+  for (int base = ((nsize - 1) >> 5) << 5; base >= 0; base -= 32) {
+    const int t = base + lane;
+    const bool mv = t > pos && t < nsize;
+    float vs = 0.f;
+    uint32_t vi = 0u;
+    if (mv) {
+      vs = ps[t - 1];
+      vi = pid[t - 1];
     }
-  }
-  __syncwarp();
-#pragma unroll
-  for (int u = 0; u < kMaxK / 32; ++u) {
-    const int t = lane + 32 * u;
-    if (t > pos && t < nsize) {
-      ps[t] = vs[u];
-      pid[t] = vi[u];
+    __syncwarp();
+    if (mv) {
+      ps[t] = vs;
+      pid[t] = vi;
     }
+    __syncwarp();
   }
   if (lane == 0) {
     ps[pos] = s;
@@ -166,7 +162,8 @@ __device__ __forceinline__ int pq_offer(float* ps, uint32_t* pid, int size, int 
 
 // Canonical float32 similarities of the query with two rows, computed by the
 // 8 lanes of a group (lane g8 owns partials 4*g8 .. 4*g8+3, i.e. float4
-// chunks g8, g8+8, ...).  Both rows' loads are issued before the arithmetic.
+// chunks g8, g8+8, ...); the loads of up to 4 chunks of both rows are issued
+// before their arithmetic.
 template <int NT>
 __device__ __forceinline__ void sim_canonical2(const float* __restrict__ q, const float* __restrict__ ra,
                                                const float* __restrict__ rb, int d_pad, int g8, unsigned gmask,
@@ -174,27 +171,31 @@ __device__ __forceinline__ void sim_canonical2(const float* __restrict__ q, cons
   const float4* q4 = reinterpret_cast<const float4*>(q);
   const float4* a4 = reinterpret_cast<const float4*>(ra);
   const float4* b4 = reinterpret_cast<const float4*>(rb);
-  float4 va[NT], vb[NT];
-#pragma unroll
-  for (int t = 0; t < NT; ++t) {
-    const int ch = g8 + 8 * t;
-    va[t] = ch * 4 < d_pad ? __ldg(a4 + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
-    vb[t] = ch * 4 < d_pad ? __ldg(b4 + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
+  constexpr int kBatch = NT < 4 ? NT : 4;  // chunks of both rows loaded before their arithmetic
   float4 sa = make_float4(0.f, 0.f, 0.f, 0.f), sb = sa;
 #pragma unroll
-  for (int t = 0; t < NT; ++t) {
-    const int ch = g8 + 8 * t;
-    if (ch * 4 < d_pad) {
-      const float4 x = q4[ch];
-      sa.x = __fmaf_rn(x.x, va[t].x, sa.x);
-      sa.y = __fmaf_rn(x.y, va[t].y, sa.y);
-      sa.z = __fmaf_rn(x.z, va[t].z, sa.z);
-      sa.w = __fmaf_rn(x.w, va[t].w, sa.w);
-      sb.x = __fmaf_rn(x.x, vb[t].x, sb.x);
-      sb.y = __fmaf_rn(x.y, vb[t].y, sb.y);
-      sb.z = __fmaf_rn(x.z, vb[t].z, sb.z);
-      sb.w = __fmaf_rn(x.w, vb[t].w, sb.w);
+  for (int t0 = 0; t0 < NT; t0 += kBatch) {
+    float4 va[kBatch], vb[kBatch];
+#pragma unroll
+    for (int t = 0; t < kBatch; ++t) {
+      const int ch = g8 + 8 * (t0 + t);
+      va[t] = ch * 4 < d_pad ? __ldg(a4 + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+      vb[t] = ch * 4 < d_pad ? __ldg(b4 + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int t = 0; t < kBatch; ++t) {
+      const int ch = g8 + 8 * (t0 + t);
+      if (ch * 4 < d_pad) {
+        const float4 x = q4[ch];
+        sa.x = __fmaf_rn(x.x, va[t].x, sa.x);
+        sa.y = __fmaf_rn(x.y, va[t].y, sa.y);
+        sa.z = __fmaf_rn(x.z, va[t].z, sa.z);
+        sa.w = __fmaf_rn(x.w, va[t].w, sa.w);
+        sb.x = __fmaf_rn(x.x, vb[t].x, sb.x);
+        sb.y = __fmaf_rn(x.y, vb[t].y, sb.y);
+        sb.z = __fmaf_rn(x.z, vb[t].z, sb.z);
+        sb.w = __fmaf_rn(x.w, vb[t].w, sb.w);
+      }
     }
   }
   // s[c] += s[c+16], s[c] += s[c+8], s[c] += s[c+4]: partner lanes 4, 2, 1 away
@@ -221,27 +222,31 @@ template <int NT2>
 __device__ __forceinline__ float sim_bf16_pair(const float* __restrict__ q, const __nv_bfloat16* __restrict__ row,
                                                int d_pad, int h) {
   const uint4* r8 = reinterpret_cast<const uint4*>(row);
-  uint4 v[NT2];
-#pragma unroll
-  for (int t = 0; t < NT2; ++t) {
-    const int ch = h + 2 * t;
-    v[t] = ch * 8 < d_pad ? __ldg(r8 + ch) : make_uint4(0u, 0u, 0u, 0u);
-  }
+  constexpr int kBatch = NT2 < 8 ? NT2 : 8;  // chunks loaded before their arithmetic
   float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
-  for (int t = 0; t < NT2; ++t) {
-    const int ch = h + 2 * t;
-    if (ch * 8 < d_pad) {
-      const float4 qa = reinterpret_cast<const float4*>(q)[2 * ch];
-      const float4 qb = reinterpret_cast<const float4*>(q)[2 * ch + 1];
-      acc0 = fmaf(qa.x, __uint_as_float(v[t].x << 16), acc0);
-      acc1 = fmaf(qa.y, __uint_as_float(v[t].x & 0xffff0000u), acc1);
-      acc0 = fmaf(qa.z, __uint_as_float(v[t].y << 16), acc0);
-      acc1 = fmaf(qa.w, __uint_as_float(v[t].y & 0xffff0000u), acc1);
-      acc0 = fmaf(qb.x, __uint_as_float(v[t].z << 16), acc0);
-      acc1 = fmaf(qb.y, __uint_as_float(v[t].z & 0xffff0000u), acc1);
-      acc0 = fmaf(qb.z, __uint_as_float(v[t].w << 16), acc0);
-      acc1 = fmaf(qb.w, __uint_as_float(v[t].w & 0xffff0000u), acc1);
+  for (int t0 = 0; t0 < NT2; t0 += kBatch) {
+    uint4 v[kBatch];
+#pragma unroll
+    for (int t = 0; t < kBatch; ++t) {
+      const int ch = h + 2 * (t0 + t);
+      v[t] = ch * 8 < d_pad ? __ldg(r8 + ch) : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int t = 0; t < kBatch; ++t) {
+      const int ch = h + 2 * (t0 + t);
+      if (ch * 8 < d_pad) {
+        const float4 qa = reinterpret_cast<const float4*>(q)[2 * ch];
+        const float4 qb = reinterpret_cast<const float4*>(q)[2 * ch + 1];
+        acc0 = fmaf(qa.x, __uint_as_float(v[t].x << 16), acc0);
+        acc1 = fmaf(qa.y, __uint_as_float(v[t].x & 0xffff0000u), acc1);
+        acc0 = fmaf(qa.z, __uint_as_float(v[t].y << 16), acc0);
+        acc1 = fmaf(qa.w, __uint_as_float(v[t].y & 0xffff0000u), acc1);
+        acc0 = fmaf(qb.x, __uint_as_float(v[t].z << 16), acc0);
+        acc1 = fmaf(qb.y, __uint_as_float(v[t].z & 0xffff0000u), acc1);
+        acc0 = fmaf(qb.z, __uint_as_float(v[t].w << 16), acc0);
+        acc1 = fmaf(qb.w, __uint_as_float(v[t].w & 0xffff0000u), acc1);
+      }
     }
   }
   const float acc = acc0 + acc1;
@@ -251,15 +256,6 @@ __device__ __forceinline__ float sim_bf16_pair(const float* __restrict__ q, cons
 struct Counters {
   uint32_t retrieved = 0, passed = 0, scored = 0, reranked = 0;
 };
-
-// Order-preserving map of a float to an unsigned key (for atomicMax).
-__device__ __forceinline__ uint32_t order_key(float f) {
-  const uint32_t u = __float_as_uint(f);
-  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float order_value(uint32_t key) {
-  return __uint_as_float((key & 0x80000000u) ? (key & 0x7FFFFFFFu) : ~key);
-}
 
 // Exact float32 similarities of the `cnt` ids at the front of cbuf, each
 // offered to the list (ps, pid) (8 candidates per step: 4 groups of 8 lanes,
@@ -290,19 +286,21 @@ __device__ __forceinline__ int canonical_and_offer(const Dev& P, const float* q,
 // kth_known: a k-th similarity already reached by the query (or -inf).
 template <int NT, int NT2>
 __device__ __forceinline__ int flush_candidates(const Dev& P, const float* q, uint32_t* cbuf, int cnt, float* ps,
-                                                uint32_t* pid, int size, int k, uint32_t* kth_shared, int lane,
+                                                uint32_t* pid, int size, int k, float kth_known, int lane,
                                                 Counters& ct) {
   if (lane == 0) ct.scored += cnt;
   if (P.scoring != 1) return canonical_and_offer<NT>(P, q, cbuf, cnt, ps, pid, size, k, lane);
   // bfloat16 estimates, 16 rows per step (a pair of lanes each).  A candidate
   // can enter the final top-k only if its exact similarity reaches every k-th
-  // similarity the query has already reached (that of the merged top-k, of
-  // this warp's list, or of another warp's list, shared as the maximum: each
-  // is a k-th of a subset of the candidates); the estimate is within bf16_err
-  // of the exact value, so candidates whose estimate + bf16_err is below it
-  // are dropped and the others are compacted in place at the front of cbuf.
+  // similarity the query has already reached (that of the merged top-k at the
+  // last snapshot, or of this warp's list: each is a k-th of a subset of the
+  // candidates); the estimate is within bf16_err of the exact value, so
+  // candidates whose estimate + bf16_err is below it are dropped and the
+  // others are compacted in place at the front of cbuf.  Each warp takes a
+  // fixed share of the chunks, so the work done (and its count) does not
+  // depend on timing.
   const int g = lane >> 1, h = lane & 1;
-  const float kth = fmaxf(order_value(*kth_shared), size == k ? ps[k - 1] : -INFINITY);
+  const float kth = fmaxf(kth_known, size == k ? ps[k - 1] : -INFINITY);
   int nr = 0;
   for (int c0 = 0; c0 < cnt; c0 += 16) {
     const int c = c0 + g;
@@ -317,9 +315,7 @@ __device__ __forceinline__ int flush_candidates(const Dev& P, const float* q, ui
     __syncwarp();
   }
   if (lane == 0) ct.reranked += nr;
-  size = canonical_and_offer<NT>(P, q, cbuf, nr, ps, pid, size, k, lane);
-  if (lane == 0 && size == k) atomicMax(kth_shared, order_key(ps[k - 1]));
-  return size;
+  return canonical_and_offer<NT>(P, q, cbuf, nr, ps, pid, size, k, lane);
 }
 
 // NT = d_pad / 32 rounded up: float4 chunks of a float32 row per lane of an
@@ -330,16 +326,14 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int d_pad = P.d_pad, L = P.L, kmax = P.k_max, M = P.M;
-  // shared memory: q | qsk | l | r | la | lc | ra | rc | cpre | gs | gid | ws | wid | cbuf
+  // shared memory: q | runs | range | qsk | cpre | gs | gid | ws | wid | cbuf
+  // (q is read as float4 and runs as uint4: both 16-byte aligned, d_pad is a
+  // multiple of 16)
   float* q = reinterpret_cast<float*>(smem_raw);
-  uint64_t* qsk = reinterpret_cast<uint64_t*>(q + d_pad);
-  uint32_t* sl = reinterpret_cast<uint32_t*>(qsk + M);
-  uint32_t* sr = sl + L;
-  uint32_t* la = sr + L;
-  uint32_t* lc = la + L;
-  uint32_t* ra = lc + L;
-  uint32_t* rc = ra + L;
-  uint32_t* cpre = rc + L;  // [L + 1]
+  uint4* runs = reinterpret_cast<uint4*>(q + d_pad);  // [L] this round's (left start, left count, right start, right count)
+  uint2* range = reinterpret_cast<uint2*>(runs + L);  // [L] current [l, r)
+  uint64_t* qsk = reinterpret_cast<uint64_t*>(range + L);
+  uint32_t* cpre = reinterpret_cast<uint32_t*>(qsk + M);  // [L + 1] chunk prefix
   float* gs = reinterpret_cast<float*>(cpre + L + 1);
   uint32_t* gid = reinterpret_cast<uint32_t*>(gs + kmax);
   float* ws = reinterpret_cast<float*>(gid + kmax);              // [kQW][kmax]
@@ -348,7 +342,6 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
   float* my_s = ws + warp * kmax;
   uint32_t* my_id = wid + warp * kmax;
   __shared__ int s_qi, s_size, s_stop, s_wsize[kQW];
-  __shared__ uint32_t s_kth;  // order key of the largest k-th similarity reached by a list of the query
   __shared__ uint32_t s_scan[kQW];
   __shared__ uint32_t s_ct[kQW][4];
   const uint32_t n = uint32_t(P.n);
@@ -390,13 +383,9 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
       const uint32_t* pj = P.pfx + size_t(j) * kPrefixSize;
       const uint32_t t = c >> (32 - kPrefixBits);
       const uint32_t lb = lower_bound(P.codes + size_t(j) * n, __ldg(pj + t), __ldg(pj + t + 1), c);
-      sl[j] = lb;
-      sr[j] = lb;
+      range[j] = make_uint2(lb, lb);
     }
-    if (tid == 0) {
-      s_size = 0;
-      s_kth = order_key(-INFINITY);
-    }
+    if (tid == 0) s_size = 0;
     if (lane == 0) s_wsize[warp] = 0;
     __syncthreads();
 
@@ -408,6 +397,7 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
       if (depth == 0) {
         // prefix length 0: every point collides in every repetition, so the
         // round is a linear scan of all points (Lemma 1, i = 0), unfiltered.
+        const float kth0 = s_size == k ? gs[k - 1] : -INFINITY;
         int nb = 0;
         for (uint32_t b0 = uint32_t(warp) * 32u; b0 < n; b0 += kThreads) {
           const uint32_t id = b0 + lane;
@@ -420,21 +410,18 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
           }
           __syncwarp();
           if (nb > kFlushAt) {
-            wsize = flush_candidates<NT, NT2>(P, q, cbuf, nb, my_s, my_id, wsize, k, &s_kth, lane, ct);
+            wsize = flush_candidates<NT, NT2>(P, q, cbuf, nb, my_s, my_id, wsize, k, kth0, lane, ct);
             nb = 0;
           }
         }
-        if (nb) wsize = flush_candidates<NT, NT2>(P, q, cbuf, nb, my_s, my_id, wsize, k, &s_kth, lane, ct);
+        if (nb) wsize = flush_candidates<NT, NT2>(P, q, cbuf, nb, my_s, my_id, wsize, k, kth0, lane, ct);
         if (lane == 0) s_wsize[warp] = wsize;
         __syncthreads();
         if (warp == 0) {
           int size = s_size;
           for (int w = 0; w < kQW; ++w)
             for (int t = 0; t < s_wsize[w]; ++t) size = pq_offer(gs, gid, size, k, ws[w * kmax + t], wid[w * kmax + t], lane);
-          if (lane == 0) {
-            s_size = size;
-            if (size == k) atomicMax(&s_kth, order_key(gs[k - 1]));
-          }
+          if (lane == 0) s_size = size;
         }
         __syncthreads();
         ++rounds;
@@ -450,7 +437,8 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
       for (int j = jlo; j < jhi; ++j) {
         const uint32_t qcj = qc[j];
         const uint32_t* cj = P.codes + size_t(j) * n;
-        const uint32_t l = sl[j], r = sr[j];
+        const uint2 lr = range[j];
+        const uint32_t l = lr.x, r = lr.y;
         uint32_t nl = l, nr = r;
         // in a one-bit step only the side of the dropped bit can grow
         // (bit `depth`, counted from the top, of the query's code)
@@ -491,12 +479,8 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
           const int64_t pos = int64_t(r) + int64_t(B) * hi;
           nr = pos > int64_t(n) ? n : uint32_t(pos);
         }
-        sl[j] = nl;
-        sr[j] = nr;
-        la[j] = nl;
-        lc[j] = l - nl;
-        ra[j] = r;
-        rc[j] = nr - r;
+        range[j] = make_uint2(nl, nr);
+        runs[j] = make_uint4(nl, l - nl, r, nr - r);
         my_chunks += ((l - nl + 31) >> 5) + ((nr - r + 31) >> 5);
       }
       // exclusive scan of the chunk counts over the repetitions -> cpre
@@ -512,7 +496,8 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
       for (int w = 0; w < warp; ++w) run += s_scan[w];
       for (int j = jlo; j < jhi; ++j) {
         cpre[j] = run;
-        run += ((lc[j] + 31) >> 5) + ((rc[j] + 31) >> 5);
+        const uint4 ru = runs[j];
+        run += ((ru.y + 31) >> 5) + ((ru.w + 31) >> 5);
       }
       if (tid == kThreads - 1) cpre[L] = run;
       __syncthreads();
@@ -542,16 +527,17 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
             if (c < c_end) {
               while (cpre[jc + 1] <= c) ++jc;  // chunk -> repetition (c only grows)
               const uint32_t lk = c - cpre[jc];
-              const uint32_t nlc = (lc[jc] + 31) >> 5;
+              const uint4 ru = runs[jc];
+              const uint32_t nlc = (ru.y + 31) >> 5;
               uint32_t off, len, start;
               if (lk < nlc) {
                 off = lk * 32 + lane;
-                len = lc[jc];
-                start = la[jc];
+                len = ru.y;
+                start = ru.x;
               } else {
                 off = (lk - nlc) * 32 + lane;
-                len = rc[jc];
-                start = ra[jc];
+                len = ru.w;
+                start = ru.z;
               }
               valid[u] = off < len;
               pos[u] = start + off;
@@ -594,11 +580,11 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
           }
           __syncwarp();
           if (nb > kFlushAt) {
-            wsize = flush_candidates<NT, NT2>(P, q, cbuf, nb, my_s, my_id, wsize, k, &s_kth, lane, ct);
+            wsize = flush_candidates<NT, NT2>(P, q, cbuf, nb, my_s, my_id, wsize, k, gkth, lane, ct);
             nb = 0;
           }
         }
-        if (nb) wsize = flush_candidates<NT, NT2>(P, q, cbuf, nb, my_s, my_id, wsize, k, &s_kth, lane, ct);
+        if (nb) wsize = flush_candidates<NT, NT2>(P, q, cbuf, nb, my_s, my_id, wsize, k, gkth, lane, ct);
         // merge the warp lists into the query's top-k
         if (lane == 0) s_wsize[warp] = wsize;
         __syncthreads();
@@ -606,10 +592,7 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
           int size = s_size;
           for (int w = 0; w < kQW; ++w)
             for (int t = 0; t < s_wsize[w]; ++t) size = pq_offer(gs, gid, size, k, ws[w * kmax + t], wid[w * kmax + t], lane);
-          if (lane == 0) {
-            s_size = size;
-            if (size == k) atomicMax(&s_kth, order_key(gs[k - 1]));
-          }
+          if (lane == 0) s_size = size;
         }
         wsize = 0;
         __syncthreads();
@@ -702,8 +685,8 @@ cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t 
   P.out_sims = a.out_sims;
   P.stats = a.stats;
   P.counter = a.counter;
-  // q | qsk | l, r, la, lc, ra, rc | cpre | top-k | warp lists | warp candidate buffers
-  const size_t smem = size_t(P.d_pad) * 4 + size_t(P.M) * 8 + size_t(P.L) * 24 + size_t(P.L + 1) * 4 +
+  // q | runs | ranges | qsk | cpre | top-k | warp lists | warp candidate buffers
+  const size_t smem = size_t(P.d_pad) * 4 + size_t(P.L) * 24 + size_t(P.M) * 8 + size_t(P.L + 1) * 4 +
                       size_t(P.k_max) * 8 * (1 + kQW) + size_t(kCandBuf) * 4 * kQW;
   const int nt = (P.d_pad + 31) / 32;
   auto kern = nt <= 1   ? search_kernel<1, 2>
