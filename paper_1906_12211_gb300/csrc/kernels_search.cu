@@ -6,10 +6,11 @@
 // range [l, r) of positions around the query's code so that it covers the
 // block of codes sharing the first i bits, growing each side in whole
 // segments of B entries (Sec. 4.2, App. C).  The round's new positions form at
-// most two runs per repetition; the runs are cut into chunks of 32 positions
-// (one per lane) and the four warps take the chunks in turn, four chunks per
-// step so that many coalesced loads are in flight: position -> id and sketch
-// -> Hamming filter (Sec. 4.2) -> the warp's compacted candidate buffer.
+// most two runs per repetition; the runs are cut into chunks of up to 128
+// positions and the four warps take the chunks in turn, one chunk per warp
+// step (four lane-strided, coalesced loads of ids and of sketches per lane):
+// position -> id and sketch -> Hamming filter (Sec. 4.2) -> the warp's
+// compacted candidate buffer.
 // Buffered candidates are scored (float32 canonical, or a bfloat16 estimate
 // followed by an exact float32 rerank of those whose estimate plus its error
 // bound can still reach the k-th similarity known so far) and offered to the
@@ -39,7 +40,8 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kQW = 4;          // warps per query (one CTA)
 constexpr int kThreads = 32 * kQW;
-constexpr int kUnroll = 4;      // 32-position chunks per warp step
+constexpr int kUnroll = 4;      // positions per lane per warp step
+constexpr uint32_t kSpan = 32 * kUnroll;  // positions of one run per chunk (one warp step)
 constexpr int kCandBuf = 384;   // compacted candidate ids per warp
 constexpr int kFlushAt = kCandBuf - 32 * kUnroll;
 constexpr int kGroup = 32;      // repetitions per threshold snapshot in a first round
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
         }
         range[j] = make_uint2(nl, nr);
         runs[j] = make_uint4(nl, l - nl, r, nr - r);
-        my_chunks += ((l - nl + 31) >> 5) + ((nr - r + 31) >> 5);
+        my_chunks += (l - nl + kSpan - 1) / kSpan + (nr - r + kSpan - 1) / kSpan;
       }
       // exclusive scan of the chunk counts over the repetitions -> cpre
       uint32_t inc = my_chunks;
@@ -497,7 +499,7 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
       for (int j = jlo; j < jhi; ++j) {
         cpre[j] = run;
         const uint4 ru = runs[j];
-        run += ((ru.y + 31) >> 5) + ((ru.w + 31) >> 5);
+        run += (ru.y + kSpan - 1) / kSpan + (ru.w + kSpan - 1) / kSpan;
       }
       if (tid == kThreads - 1) cpre[L] = run;
       __syncthreads();
@@ -513,77 +515,67 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
         const int tau = gsize == k ? filter_tau(P, gkth) : 64;
         const uint32_t c_end = cpre[j1];
         int jc = j0;
+        uint64_t qh = qsk[j0 % M];  // the query's sketch for repetition jc
         int nb = 0;
-        for (uint32_t c0 = cpre[j0] + uint32_t(warp) * kUnroll; c0 < c_end; c0 += kQW * kUnroll) {
-          uint32_t id[kUnroll], pos[kUnroll];
-          int jo[kUnroll];
-          bool valid[kUnroll];
+        // warp w takes chunks w, w + 4, ...: up to kSpan positions of one run,
+        // lane-strided so that every load instruction is coalesced
+        for (uint32_t c = cpre[j0] + uint32_t(warp); c < c_end; c += kQW) {
+          if (cpre[jc + 1] <= c) {  // chunk -> repetition (c only grows)
+            do ++jc; while (cpre[jc + 1] <= c);
+            qh = qsk[jc % M];
+          }
+          const uint32_t lk = c - cpre[jc];
+          const uint4 ru = runs[jc];
+          const uint32_t nlc = (ru.y + kSpan - 1) / kSpan;
+          const bool left = lk < nlc;
+          const uint32_t off = (left ? lk : lk - nlc) * kSpan;
+          const uint32_t start = (left ? ru.x : ru.z) + off;
+          const uint32_t cnt = min((left ? ru.y : ru.w) - off, kSpan);
+          const size_t rowbase = size_t(jc) * n + start;
+          uint32_t id[kUnroll];
+          bool pass[kUnroll];
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) {
-            const uint32_t c = c0 + u;
-            valid[u] = false;
-            pos[u] = 0;
-            jo[u] = jc;
-            if (c < c_end) {
-              while (cpre[jc + 1] <= c) ++jc;  // chunk -> repetition (c only grows)
-              const uint32_t lk = c - cpre[jc];
-              const uint4 ru = runs[jc];
-              const uint32_t nlc = (ru.y + 31) >> 5;
-              uint32_t off, len, start;
-              if (lk < nlc) {
-                off = lk * 32 + lane;
-                len = ru.y;
-                start = ru.x;
-              } else {
-                off = (lk - nlc) * 32 + lane;
-                len = ru.w;
-                start = ru.z;
-              }
-              valid[u] = off < len;
-              pos[u] = start + off;
-              jo[u] = jc;
-            }
+            const uint32_t o = 32u * u + uint32_t(lane);
+            id[u] = o < cnt ? __ldg(P.ids + rowbase + o) : 0u;
           }
-#pragma unroll
-          for (int u = 0; u < kUnroll; ++u)
-            id[u] = valid[u] ? __ldg(P.ids + size_t(jo[u]) * n + pos[u]) : 0u;
-          bool pass[kUnroll];
           if (P.filter) {
             uint64_t hd[kUnroll];
             if (P.skc) {  // the sketch sits at the same position as the id
 #pragma unroll
-              for (int u = 0; u < kUnroll; ++u)
-                hd[u] = valid[u] ? __ldg(P.skc + size_t(jo[u]) * n + pos[u]) ^ qsk[jo[u] % M] : 0ull;
+              for (int u = 0; u < kUnroll; ++u) {
+                const uint32_t o = 32u * u + uint32_t(lane);
+                hd[u] = o < cnt ? __ldg(P.skc + rowbase + o) ^ qh : 0ull;
+              }
             } else {
+              const uint64_t* skm = P.sk + size_t(jc % M) * n;
 #pragma unroll
               for (int u = 0; u < kUnroll; ++u) {
-                const int m = jo[u] % M;
-                hd[u] = valid[u] ? __ldg(P.sk + size_t(m) * n + id[u]) ^ qsk[m] : 0ull;
+                const uint32_t o = 32u * u + uint32_t(lane);
+                hd[u] = o < cnt ? __ldg(skm + id[u]) ^ qh : 0ull;
               }
             }
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) pass[u] = valid[u] && __popcll(hd[u]) <= tau;
+            for (int u = 0; u < kUnroll; ++u) pass[u] = 32u * u + uint32_t(lane) < cnt && __popcll(hd[u]) <= tau;
           } else {
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) pass[u] = valid[u];
+            for (int u = 0; u < kUnroll; ++u) pass[u] = 32u * u + uint32_t(lane) < cnt;
           }
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) {
-            const unsigned vm = __ballot_sync(kFull, valid[u]);
             const unsigned pm = __ballot_sync(kFull, pass[u]);
             if (pass[u]) cbuf[nb + __popc(pm & lt_mask)] = id[u];
             nb += __popc(pm);
-            if (lane == 0) {
-              ct.retrieved += __popc(vm);
-              ct.passed += __popc(pm);
-            }
           }
+          if (lane == 0) ct.retrieved += cnt;
           __syncwarp();
           if (nb > kFlushAt) {
+            if (lane == 0) ct.passed += uint32_t(nb);  // every buffered candidate passed the filter
             wsize = flush_candidates<NT, NT2>(P, q, cbuf, nb, my_s, my_id, wsize, k, gkth, lane, ct);
             nb = 0;
           }
         }
+        if (lane == 0) ct.passed += uint32_t(nb);
         if (nb) wsize = flush_candidates<NT, NT2>(P, q, cbuf, nb, my_s, my_id, wsize, k, gkth, lane, ct);
         // merge the warp lists into the query's top-k
         if (lane == 0) s_wsize[warp] = wsize;
