@@ -6,9 +6,9 @@
 // range [l, r) of positions around the query's code so that it covers the
 // block of codes sharing the first i bits, growing each side in whole
 // segments of B entries (Sec. 4.2, App. C).  The round's new positions form at
-// most two runs per repetition; the runs are cut into chunks of up to 128
+// most two runs per repetition; the runs are cut into chunks of up to 256
 // positions and the four warps take the chunks in turn, one chunk per warp
-// step (four lane-strided, coalesced loads of ids and of sketches per lane):
+// step (eight lane-strided, coalesced loads of ids and of sketches per lane):
 // position -> id and sketch -> Hamming filter (Sec. 4.2) -> the warp's
 // compacted candidate buffer.
 // Buffered candidates are scored (float32 canonical, or a bfloat16 estimate
@@ -40,11 +40,12 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kQW = 4;          // warps per query (one CTA)
 constexpr int kThreads = 32 * kQW;
-constexpr int kUnroll = 4;      // positions per lane per warp step
+constexpr int kUnroll = 8;      // positions per lane per warp step
 constexpr uint32_t kSpan = 32 * kUnroll;  // positions of one run per chunk (one warp step)
-constexpr int kCandBuf = 384;   // compacted candidate ids per warp
+constexpr int kCandBuf = 512;   // compacted candidate ids per warp
 constexpr int kFlushAt = kCandBuf - 32 * kUnroll;
 constexpr int kGroup = 32;      // repetitions per threshold snapshot in a first round
+constexpr int kSub = 64;        // candidates per bfloat16 sub-batch (the pruning bound is refreshed between)
 
 struct Dev {
   int n;
@@ -301,23 +302,29 @@ __device__ __forceinline__ int flush_candidates(const Dev& P, const float* q, ui
   // others are compacted in place at the front of cbuf.  Each warp takes a
   // fixed share of the chunks, so the work done (and its count) does not
   // depend on timing.
+  // The buffer is taken in sub-batches of kSub so that the bound rises as soon
+  // as the reranked candidates of one sub-batch are in the list.
   const int g = lane >> 1, h = lane & 1;
-  const float kth = fmaxf(kth_known, size == k ? ps[k - 1] : -INFINITY);
-  int nr = 0;
-  for (int c0 = 0; c0 < cnt; c0 += 16) {
-    const int c = c0 + g;
-    const bool valid = c < cnt;
-    const uint32_t id = valid ? cbuf[c] : cbuf[c0];
-    const float est = sim_bf16_pair<NT2>(q, P.x16 + size_t(id) * P.d_pad, P.d_pad, h);
-    const bool need = valid && est + P.bf16_err >= kth;
-    const unsigned b = __ballot_sync(kFull, need && h == 0);
-    __syncwarp();
-    if (need && h == 0) cbuf[nr + __popc(b & ((1u << lane) - 1u))] = id;
-    nr += __popc(b);
-    __syncwarp();
+  for (int b0 = 0; b0 < cnt; b0 += kSub) {
+    const int b1 = min(cnt, b0 + kSub);
+    const float kth = fmaxf(kth_known, size == k ? ps[k - 1] : -INFINITY);
+    int nr = 0;
+    for (int c0 = b0; c0 < b1; c0 += 16) {
+      const int c = c0 + g;
+      const bool valid = c < b1;
+      const uint32_t id = valid ? cbuf[c] : cbuf[c0];
+      const float est = sim_bf16_pair<NT2>(q, P.x16 + size_t(id) * P.d_pad, P.d_pad, h);
+      const bool need = valid && est + P.bf16_err >= kth;
+      const unsigned b = __ballot_sync(kFull, need && h == 0);
+      __syncwarp();
+      if (need && h == 0) cbuf[b0 + nr + __popc(b & ((1u << lane) - 1u))] = id;
+      nr += __popc(b);
+      __syncwarp();
+    }
+    if (lane == 0) ct.reranked += nr;
+    size = canonical_and_offer<NT>(P, q, cbuf + b0, nr, ps, pid, size, k, lane);
   }
-  if (lane == 0) ct.reranked += nr;
-  return canonical_and_offer<NT>(P, q, cbuf, nr, ps, pid, size, k, lane);
+  return size;
 }
 
 // NT = d_pad / 32 rounded up: float4 chunks of a float32 row per lane of an
