@@ -455,38 +455,58 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
         const bool try_left = !single || dropped_one;
         const bool try_right = !single || !dropped_one;
         const uint32_t B = uint32_t(P.B);
-        if (try_left && l > 0 && prefix_match(__ldg(cj + l - 1), qcj, mask)) {
-          // smallest m >= 1 with l - B*m <= 0 or codes[l - B*m - 1] outside the block
-          uint32_t lo = 0, hi = 1;
-          for (;;) {
+        if (depth <= kPrefixBits) {
+          // the block [blo, bhi) of codes sharing the first `depth` bits is a
+          // run of 13-bit prefix buckets: two table reads.  A side grows by the
+          // smallest whole number of segments that reaches the block's end
+          // (or the array's end): the same positions as probing segment by
+          // segment until the entry beyond the range is outside the block.
+          const uint32_t* pj = P.pfx + size_t(j) * kPrefixSize;
+          const uint32_t span = 1u << (kPrefixBits - depth);
+          const uint32_t t0 = (qcj >> (32 - kPrefixBits)) & ~(span - 1u);
+          const uint32_t blo = __ldg(pj + t0), bhi = __ldg(pj + t0 + span);
+          if (try_left && l > blo) {
+            const uint32_t m = (l - blo + B - 1) / B;
+            nl = l >= B * m ? l - B * m : 0u;
+          }
+          if (try_right && r < bhi) {
+            const uint32_t m = (bhi - r + B - 1) / B;
+            nr = min(n, r + B * m);
+          }
+        } else {
+          if (try_left && l > 0 && prefix_match(__ldg(cj + l - 1), qcj, mask)) {
+            // smallest m >= 1 with l - B*m <= 0 or codes[l - B*m - 1] outside the block
+            uint32_t lo = 0, hi = 1;
+            for (;;) {
+              const int64_t pos = int64_t(l) - int64_t(B) * hi;
+              if (pos <= 0 || !prefix_match(__ldg(cj + pos - 1), qcj, mask)) break;
+              lo = hi;
+              hi *= 2;
+            }
+            while (hi - lo > 1) {
+              const uint32_t mid = (lo + hi) >> 1;
+              const int64_t pos = int64_t(l) - int64_t(B) * mid;
+              if (pos <= 0 || !prefix_match(__ldg(cj + pos - 1), qcj, mask)) hi = mid; else lo = mid;
+            }
             const int64_t pos = int64_t(l) - int64_t(B) * hi;
-            if (pos <= 0 || !prefix_match(__ldg(cj + pos - 1), qcj, mask)) break;
-            lo = hi;
-            hi *= 2;
+            nl = pos < 0 ? 0u : uint32_t(pos);
           }
-          while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            const int64_t pos = int64_t(l) - int64_t(B) * mid;
-            if (pos <= 0 || !prefix_match(__ldg(cj + pos - 1), qcj, mask)) hi = mid; else lo = mid;
-          }
-          const int64_t pos = int64_t(l) - int64_t(B) * hi;
-          nl = pos < 0 ? 0u : uint32_t(pos);
-        }
-        if (try_right && r < n && prefix_match(__ldg(cj + r), qcj, mask)) {
-          uint32_t lo = 0, hi = 1;
-          for (;;) {
+          if (try_right && r < n && prefix_match(__ldg(cj + r), qcj, mask)) {
+            uint32_t lo = 0, hi = 1;
+            for (;;) {
+              const int64_t pos = int64_t(r) + int64_t(B) * hi;
+              if (pos >= int64_t(n) || !prefix_match(__ldg(cj + pos), qcj, mask)) break;
+              lo = hi;
+              hi *= 2;
+            }
+            while (hi - lo > 1) {
+              const uint32_t mid = (lo + hi) >> 1;
+              const int64_t pos = int64_t(r) + int64_t(B) * mid;
+              if (pos >= int64_t(n) || !prefix_match(__ldg(cj + pos), qcj, mask)) hi = mid; else lo = mid;
+            }
             const int64_t pos = int64_t(r) + int64_t(B) * hi;
-            if (pos >= int64_t(n) || !prefix_match(__ldg(cj + pos), qcj, mask)) break;
-            lo = hi;
-            hi *= 2;
+            nr = pos > int64_t(n) ? n : uint32_t(pos);
           }
-          while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            const int64_t pos = int64_t(r) + int64_t(B) * mid;
-            if (pos >= int64_t(n) || !prefix_match(__ldg(cj + pos), qcj, mask)) hi = mid; else lo = mid;
-          }
-          const int64_t pos = int64_t(r) + int64_t(B) * hi;
-          nr = pos > int64_t(n) ? n : uint32_t(pos);
         }
         range[j] = make_uint2(nl, nr);
         runs[j] = make_uint4(nl, l - nl, r, nr - r);
