@@ -173,14 +173,15 @@ def brute_force_kth(torch, Xd, Qd, k):
 
 def algorithmic_bytes(st, L, n, d, k, mode):
     """Bytes a query must touch (per query, averaged): prefix lookups and the
-    binary search for every repetition, id + code + sketch per retrieved
-    candidate, the row of every scored candidate (bf16 or fp32), the fp32 row of
-    every reranked one, the query and the output."""
+    binary search for every repetition, id + sketch per retrieved candidate
+    (the per-repetition sketch layout), the row of every scored candidate
+    (bf16 or fp32), the fp32 row of every reranked one, the query and the
+    output."""
     import math
 
     probes = max(1, math.ceil(math.log2(max(2, n / 8192))))
     per_row = d * (2 if mode == "bf16" else 4)
-    b = (L * (8 + probes * 4) + st["retrieved"].astype(np.float64) * (4 + 4 + 8)
+    b = (L * (8 + probes * 4) + st["retrieved"].astype(np.float64) * (4 + 8)
          + st["scored"].astype(np.float64) * per_row + st["reranked"].astype(np.float64) * d * 4 + d * 4 + k * 8)
     return float(b.mean())
 
