@@ -685,7 +685,7 @@ pf_status pf_learned_train(pf_index* ix, const float* train_queries, int64_t Qt,
       }
       dalloc(&w1h, size_t(nW1));
       dalloc(&w2h, size_t(nW2));
-      PF_CK(to_bf16(W1, w1h, nW1, s));
+      PF_CK(to_bf16_transposed(W1, w1h, H, F, s));  // [H][F] -> [F][H]
       PF_CK(to_bf16(W2, w2h, nW2, s));
       PF_CK(cudaStreamSynchronize(s));
       // install the model

@@ -152,53 +152,67 @@ __global__ void to_bf16_kernel(const float* __restrict__ a, __nv_bfloat16* __res
     b[i] = __float2bfloat16_rn(a[i]);
 }
 
-// Inference, one warp per query: bfloat16 weights, float32 accumulation; the
-// start depth is min(C - 1, q + margin), q the smallest d with
-// P(stop depth > d) <= tail.
-__global__ void __launch_bounds__(128) predict_kernel(const float* __restrict__ qx, const uint64_t* __restrict__ qsk,
-                                                      int Q, int d_pad, int M, const __nv_bfloat16* __restrict__ W1,
-                                                      const float* __restrict__ b1,
-                                                      const __nv_bfloat16* __restrict__ W2,
-                                                      const float* __restrict__ b2, int C, float tail,
-                                                      int margin, int32_t* __restrict__ start) {
-  __shared__ float xs[4][kMaxD + 64];
-  __shared__ float hs[4][kMlpHidden];
-  __shared__ float zs[4][64];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int q = blockIdx.x * 4 + w;
-  if (q >= Q) return;
+// Inference for a tile of kPredQ queries per CTA of 256 threads (= hidden
+// units): thread u accumulates its hidden unit for all queries of the tile
+// (the bfloat16 first layer is stored transposed, [F][H], so one feature step
+// is one coalesced row shared by the tile); float32 accumulation.  The start
+// depth is min(C - 1, q + margin), q the smallest d with P(stop depth > d) <= tail.
+constexpr int kPredQ = 16;
+__global__ void __launch_bounds__(kMlpHidden) predict_kernel(const float* __restrict__ qx,
+                                                             const uint64_t* __restrict__ qsk, int Q, int d_pad,
+                                                             int M, const __nv_bfloat16* __restrict__ W1t,
+                                                             const float* __restrict__ b1,
+                                                             const __nv_bfloat16* __restrict__ W2,
+                                                             const float* __restrict__ b2, int C, float tail,
+                                                             int margin, int32_t* __restrict__ start) {
+  __shared__ float xs[kPredQ][kMaxD + 64];
+  __shared__ float hs[kPredQ][kMlpHidden];
+  __shared__ float zs[kPredQ][64];
+  const int tid = threadIdx.x;
+  const int q0 = blockIdx.x * kPredQ;
+  const int nq = min(kPredQ, Q - q0);
   const int F = d_pad + 64;
-  for (int i = lane; i < F; i += 32)
-    xs[w][i] = i < d_pad ? qx[size_t(q) * d_pad + i] : (((qsk[size_t(q) * M] >> (i - d_pad)) & 1ull) ? 1.f : -1.f);
-  __syncwarp();
-  for (int u = lane; u < kMlpHidden; u += 32) {
-    const __nv_bfloat16* row = W1 + size_t(u) * F;
-    float a = b1[u];
-    for (int i = 0; i < F; ++i) a = fmaf(__bfloat162float(row[i]), xs[w][i], a);
-    hs[w][u] = fmaxf(a, 0.f);
+  for (int e = tid; e < nq * F; e += kMlpHidden) {
+    const int t = e / F, i = e % F;
+    const int64_t q = q0 + t;
+    xs[t][i] = i < d_pad ? qx[q * d_pad + i] : (((qsk[q * M] >> (i - d_pad)) & 1ull) ? 1.f : -1.f);
   }
-  __syncwarp();
-  for (int c = lane; c < C; c += 32) {
+  __syncthreads();
+  const int u = tid;
+  float acc[kPredQ];
+#pragma unroll
+  for (int t = 0; t < kPredQ; ++t) acc[t] = b1[u];
+  for (int i = 0; i < F; ++i) {
+    const float w = __bfloat162float(W1t[size_t(i) * kMlpHidden + u]);
+#pragma unroll
+    for (int t = 0; t < kPredQ; ++t) acc[t] = fmaf(w, xs[t][i], acc[t]);
+  }
+#pragma unroll
+  for (int t = 0; t < kPredQ; ++t) hs[t][u] = fmaxf(acc[t], 0.f);
+  __syncthreads();
+  for (int e = tid; e < nq * C; e += kMlpHidden) {
+    const int t = e / C, c = e % C;
     const __nv_bfloat16* row = W2 + size_t(c) * kMlpHidden;
     float a = b2[c];
-    for (int u = 0; u < kMlpHidden; ++u) a = fmaf(__bfloat162float(row[u]), hs[w][u], a);
-    zs[w][c] = a;
+    for (int h = 0; h < kMlpHidden; ++h) a = fmaf(__bfloat162float(row[h]), hs[t][h], a);
+    zs[t][c] = a;
   }
-  __syncwarp();
-  if (lane == 0) {
+  __syncthreads();
+  if (tid < nq) {
+    const float* z = zs[tid];
     float mx = -INFINITY;
-    for (int c = 0; c < C; ++c) mx = fmaxf(mx, zs[w][c]);
+    for (int c = 0; c < C; ++c) mx = fmaxf(mx, z[c]);
     float se = 0.f;
-    for (int c = 0; c < C; ++c) se += expf(zs[w][c] - mx);
+    for (int c = 0; c < C; ++c) se += expf(z[c] - mx);
     // P(stop depth > d) = sum over c > d; scan from the top
     float above = 0.f;
     int dsel = C - 1;
     for (int d = C - 1; d >= 0; --d) {
       if (above > tail * se) break;
       dsel = d;
-      above += expf(zs[w][d] - mx);
+      above += expf(z[d] - mx);
     }
-    start[q] = min(C - 1, dsel + margin);
+    start[q0 + tid] = min(C - 1, dsel + margin);
   }
 }
 
@@ -251,16 +265,32 @@ cudaError_t adam_step(float* w, const float* g, float* m, float* v, int64_t coun
   return cudaGetLastError();
 }
 
+__global__ void to_bf16_transposed_kernel(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, int rows,
+                                          int cols) {
+  const int64_t count = int64_t(rows) * cols;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < count; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = e / cols, c = e % cols;
+    b[c * rows + r] = __float2bfloat16_rn(a[e]);
+  }
+}
+
+// b[c][r] = bfloat16(a[r][c]) for a [rows][cols]
+cudaError_t to_bf16_transposed(const float* a, __nv_bfloat16* b, int rows, int cols, cudaStream_t s) {
+  to_bf16_transposed_kernel<<<256, 256, 0, s>>>(a, b, rows, cols);
+  return cudaGetLastError();
+}
+
 cudaError_t to_bf16(const float* a, __nv_bfloat16* b, int64_t count, cudaStream_t s) {
   to_bf16_kernel<<<256, 256, 0, s>>>(a, b, count);
   return cudaGetLastError();
 }
 
-cudaError_t mlp_predict(const float* qx, const uint64_t* qsk, int Q, int d_pad, int M, const __nv_bfloat16* W1,
+cudaError_t mlp_predict(const float* qx, const uint64_t* qsk, int Q, int d_pad, int M, const __nv_bfloat16* W1t,
                         const float* b1, const __nv_bfloat16* W2, const float* b2, int C, float tail, int margin,
                         int32_t* start, cudaStream_t s) {
   if (Q <= 0) return cudaSuccess;
-  predict_kernel<<<(Q + 3) / 4, 128, 0, s>>>(qx, qsk, Q, d_pad, M, W1, b1, W2, b2, C, tail, margin, start);
+  predict_kernel<<<(Q + kPredQ - 1) / kPredQ, kMlpHidden, 0, s>>>(qx, qsk, Q, d_pad, M, W1t, b1, W2, b2, C, tail,
+                                                                  margin, start);
   return cudaGetLastError();
 }
 

@@ -110,7 +110,7 @@ struct pf_index {
   // start-depth model: params = [W1 (H x F) | b1 (H) | W2 (C x H) | b2 (C)], float32
   int mlp_trained = 0, mlp_F = 0, mlp_C = 0;
   float* mlp_w = nullptr;
-  __nv_bfloat16* mlp_w1h = nullptr;  // bfloat16 W1 for inference
+  __nv_bfloat16* mlp_w1h = nullptr;  // bfloat16 W1 for inference, transposed: [F][H]
   __nv_bfloat16* mlp_w2h = nullptr;  // bfloat16 W2 for inference
   float* mlp_x = nullptr;            // [cap_q][F] feature scratch of the search path
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // phase timing events
@@ -174,7 +174,8 @@ cudaError_t mlp_forward_backward(const float* X, const int32_t* y, int B, int F,
                                  cudaStream_t s);
 cudaError_t adam_step(float* w, const float* g, float* m, float* v, int64_t count, float lr, int t, cudaStream_t s);
 cudaError_t to_bf16(const float* a, __nv_bfloat16* b, int64_t count, cudaStream_t s);
-cudaError_t mlp_predict(const float* qx, const uint64_t* qsk, int Q, int d_pad, int M, const __nv_bfloat16* W1,
+cudaError_t to_bf16_transposed(const float* a, __nv_bfloat16* b, int rows, int cols, cudaStream_t s);
+cudaError_t mlp_predict(const float* qx, const uint64_t* qsk, int Q, int d_pad, int M, const __nv_bfloat16* W1t,
                         const float* b1, const __nv_bfloat16* W2, const float* b2, int C, float tail, int margin,
                         int32_t* start, cudaStream_t s);
 cudaError_t gather_rows(const float* src, const int32_t* idx, int rows, int cols, float* dst, cudaStream_t s);
