@@ -739,6 +739,49 @@ __device__ __forceinline__ void dot64_rows(const float* const (&w)[4], uint32_t 
   for (int u = 0; u < 4; ++u) out[u] = s[u];
 }
 
+// float32 projections, in index order by fused multiply-add, of the rows w[u]
+// with bit u of `use` onto x, each with a bound on its distance to the float64
+// projection in index order: both are within (d+1)*2^-24 * sum|w_i x_i| of the
+// exact sum (plus the underflow of d products), so they are within
+// err = (d+2)*2^-23 * sum|w_i x_i| + d*2^-126 of each other (the float32 sum of
+// |w_i x_i| is itself within a factor 1 + (d+1)*2^-24 of the exact one).
+// A decision whose float32 margin exceeds the bound is the float64 decision.
+__device__ __forceinline__ void dot32_rows(const float* const (&w)[4], uint32_t use, const float* __restrict__ x,
+                                           int d, float (&out)[4], float (&err)[4]) {
+  float s[4] = {0.f, 0.f, 0.f, 0.f}, a[4] = {0.f, 0.f, 0.f, 0.f};
+  const int d4 = d & ~3;
+  for (int i = 0; i < d4; i += 4) {
+    const float4 xv = __ldg(reinterpret_cast<const float4*>(x + i));
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!(use & (1u << u))) continue;
+      const float4 wv = __ldg(reinterpret_cast<const float4*>(w[u] + i));
+      s[u] = __fmaf_rn(wv.x, xv.x, s[u]);
+      s[u] = __fmaf_rn(wv.y, xv.y, s[u]);
+      s[u] = __fmaf_rn(wv.z, xv.z, s[u]);
+      s[u] = __fmaf_rn(wv.w, xv.w, s[u]);
+      a[u] = __fmaf_rn(fabsf(wv.x), fabsf(xv.x), a[u]);
+      a[u] = __fmaf_rn(fabsf(wv.y), fabsf(xv.y), a[u]);
+      a[u] = __fmaf_rn(fabsf(wv.z), fabsf(xv.z), a[u]);
+      a[u] = __fmaf_rn(fabsf(wv.w), fabsf(xv.w), a[u]);
+    }
+  }
+  for (int i = d4; i < d; ++i)
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (use & (1u << u)) {
+        s[u] = __fmaf_rn(w[u][i], x[i], s[u]);
+        a[u] = __fmaf_rn(fabsf(w[u][i]), fabsf(x[i]), a[u]);
+      }
+  const float f = float(d + 2) * 1.1920928955078125e-07f;  // (d+2) * 2^-23
+  const float tiny = float(d) * 1.1754943508222875e-38f;   // d * 2^-126
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    out[u] = s[u];
+    err[u] = __fmaf_ru(f, a[u], tiny);
+  }
+}
+
 // rewrite the CP field of function fn of repetition j for point p with the
 // float64 decision (row besti, sign of bestval)
 __device__ __forceinline__ void store_cp_field(const HashArgs& A, uint32_t info, int64_t p, int besti,
@@ -763,6 +806,23 @@ __device__ __forceinline__ void recheck_one(const HashArgs& A, const RecheckReq&
     const int cs[4] = {q.c[0], q.c[1], q.c[2], q.c[3]};
     const float* w[4] = {wf + int64_t(cs[0]) * A.d_pad, wf + int64_t(cs[1]) * A.d_pad, wf + int64_t(cs[2]) * A.d_pad,
                          wf + int64_t(cs[3]) * A.d_pad};
+    // float32 first: the row whose |value| exceeds every other listed row's
+    // by more than both bounds, with a sign outside its bound, is the
+    // float64 decision
+    float v32[4], e32[4];
+    dot32_rows(w, use, xrow, A.d, v32, e32);
+    int top = -1;
+    for (int u = 0; u < 4 && top < 0; ++u) {
+      if (!(use & (1u << u)) || !(fabsf(v32[u]) > e32[u])) continue;
+      bool clear = true;
+      for (int o = 0; o < 4; ++o)
+        if (o != u && (use & (1u << o)) && !(fabsf(v32[u]) - fabsf(v32[o]) > e32[u] + e32[o])) clear = false;
+      if (clear) top = u;
+    }
+    if (top >= 0) {
+      store_cp_field(A, q.info, p, cs[top], double(v32[top]));
+      return;
+    }
     double v64[4];
     dot64_rows(w, use, xrow, A.d, v64);
     double bestabs = -1.0, bestval = 0.0;
@@ -780,9 +840,16 @@ __device__ __forceinline__ void recheck_one(const HashArgs& A, const RecheckReq&
     return;
   }
   const float* w[4] = {A.w32 + int64_t(q.row0) * A.d_pad, xrow, xrow, xrow};
-  double v64[4];
-  dot64_rows(w, 1u, xrow, A.d, v64);
-  const bool bit = v64[0] >= 0.0;
+  float v32[4], e32[4];
+  dot32_rows(w, 1u, xrow, A.d, v32, e32);
+  bool bit;
+  if (fabsf(v32[0]) > e32[0]) {
+    bit = v32[0] > 0.f;  // the float64 value has the same sign (and is not zero)
+  } else {
+    double v64[4];
+    dot64_rows(w, 1u, xrow, A.d, v64);
+    bit = v64[0] >= 0.0;
+  }
   const int idx = int(q.info & 0xFFFFFu), b = int((q.info >> 20) & 63u);
   if (kind == 1) {
     uint32_t* cw = A.codes + int64_t(idx) * A.cj + p * A.cp;
@@ -810,6 +877,47 @@ __device__ __forceinline__ void recheck_all_rows(const HashArgs& A, uint32_t p32
     const int c = lane + 32 * u;
     w[u] = wf + int64_t(min(c, A.d - 1)) * A.d_pad;
     if (c < A.d) use |= 1u << u;
+  }
+  // float32 first: decided if the largest |value| exceeds every other row's by
+  // more than the largest bound twice over and its sign is outside the bound
+  {
+    float v32[4], e32[4];
+    dot32_rows(w, use, xrow, A.d, v32, e32);
+    float m1 = -1.f, m2 = -1.f, emax = 0.f, val = 0.f;
+    int i1 = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!(use & (1u << u))) continue;
+      const float av = fabsf(v32[u]);
+      emax = fmaxf(emax, e32[u]);
+      if (av > m1) {
+        m2 = m1;
+        m1 = av;
+        i1 = lane + 32 * u;
+        val = v32[u];
+      } else {
+        m2 = fmaxf(m2, av);
+      }
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      const float o1 = __shfl_xor_sync(0xffffffffu, m1, off), o2 = __shfl_xor_sync(0xffffffffu, m2, off);
+      const float oe = __shfl_xor_sync(0xffffffffu, emax, off), ov = __shfl_xor_sync(0xffffffffu, val, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, i1, off);
+      emax = fmaxf(emax, oe);
+      if (o1 > m1 || (o1 == m1 && oi < i1)) {
+        m2 = fmaxf(m1, o2);
+        m1 = o1;
+        i1 = oi;
+        val = ov;
+      } else {
+        m2 = fmaxf(m2, o1);
+      }
+    }
+    if (m1 > emax && m1 - m2 > 2.f * emax) {
+      if (lane == 0) store_cp_field(A, info, p, i1, double(val));
+      return;
+    }
   }
   double v64[4];
   dot64_rows(w, use, xrow, A.d, v64);

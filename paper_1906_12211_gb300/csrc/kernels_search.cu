@@ -166,10 +166,11 @@ __device__ __forceinline__ int pq_offer(float* ps, uint32_t* pid, int size, int 
 // Canonical float32 similarities of the query with two rows, computed by the
 // 8 lanes of a group (lane g8 owns partials 4*g8 .. 4*g8+3, i.e. float4
 // chunks g8, g8+8, ...); the loads of up to 4 chunks of both rows are issued
-// before their arithmetic.
+// before their arithmetic.  Chunks wholly beyond the d coordinates (the zero
+// padding up to d') are neither read nor added.
 template <int NT>
 __device__ __forceinline__ void sim_canonical2(const float* __restrict__ q, const float* __restrict__ ra,
-                                               const float* __restrict__ rb, int d_pad, int g8, unsigned gmask,
+                                               const float* __restrict__ rb, int d, int g8, unsigned gmask,
                                                float& out_a, float& out_b) {
   const float4* q4 = reinterpret_cast<const float4*>(q);
   const float4* a4 = reinterpret_cast<const float4*>(ra);
@@ -182,13 +183,13 @@ __device__ __forceinline__ void sim_canonical2(const float* __restrict__ q, cons
 #pragma unroll
     for (int t = 0; t < kBatch; ++t) {
       const int ch = g8 + 8 * (t0 + t);
-      va[t] = ch * 4 < d_pad ? __ldg(a4 + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
-      vb[t] = ch * 4 < d_pad ? __ldg(b4 + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+      va[t] = ch * 4 < d ? __ldg(a4 + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+      vb[t] = ch * 4 < d ? __ldg(b4 + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
     for (int t = 0; t < kBatch; ++t) {
       const int ch = g8 + 8 * (t0 + t);
-      if (ch * 4 < d_pad) {
+      if (ch * 4 < d) {
         const float4 x = q4[ch];
         sa.x = __fmaf_rn(x.x, va[t].x, sa.x);
         sa.y = __fmaf_rn(x.y, va[t].y, sa.y);
@@ -219,11 +220,12 @@ __device__ __forceinline__ void sim_canonical2(const float* __restrict__ q, cons
 }
 
 // bfloat16 estimate of <q, x> by a pair of lanes: float32 query against the
-// bfloat16 row, lane h of the pair takes the 8-element chunks h, h+2, ...; any
-// summation order (the error bound covers every order).
+// bfloat16 row, lane h of the pair takes the 8-element chunks h, h+2, ... below
+// d (the rest is zero padding); any summation order (the error bound covers
+// every order).
 template <int NT2>
 __device__ __forceinline__ float sim_bf16_pair(const float* __restrict__ q, const __nv_bfloat16* __restrict__ row,
-                                               int d_pad, int h) {
+                                               int d, int h) {
   const uint4* r8 = reinterpret_cast<const uint4*>(row);
   constexpr int kBatch = NT2 < 8 ? NT2 : 8;  // chunks loaded before their arithmetic
   float acc0 = 0.f, acc1 = 0.f;
@@ -233,12 +235,12 @@ __device__ __forceinline__ float sim_bf16_pair(const float* __restrict__ q, cons
 #pragma unroll
     for (int t = 0; t < kBatch; ++t) {
       const int ch = h + 2 * (t0 + t);
-      v[t] = ch * 8 < d_pad ? __ldg(r8 + ch) : make_uint4(0u, 0u, 0u, 0u);
+      v[t] = ch * 8 < d ? __ldg(r8 + ch) : make_uint4(0u, 0u, 0u, 0u);
     }
 #pragma unroll
     for (int t = 0; t < kBatch; ++t) {
       const int ch = h + 2 * (t0 + t);
-      if (ch * 8 < d_pad) {
+      if (ch * 8 < d) {
         const float4 qa = reinterpret_cast<const float4*>(q)[2 * ch];
         const float4 qb = reinterpret_cast<const float4*>(q)[2 * ch + 1];
         acc0 = fmaf(qa.x, __uint_as_float(v[t].x << 16), acc0);
@@ -273,7 +275,7 @@ __device__ __forceinline__ int canonical_and_offer(const Dev& P, const float* q,
     const uint32_t ida = ca < cnt ? cbuf[ca] : cbuf[c0];
     const uint32_t idb = cb < cnt ? cbuf[cb] : cbuf[c0];
     float sa, sb;
-    sim_canonical2<NT>(q, P.x32 + size_t(ida) * P.d_pad, P.x32 + size_t(idb) * P.d_pad, P.d_pad, g8, gmask, sa, sb);
+    sim_canonical2<NT>(q, P.x32 + size_t(ida) * P.d_pad, P.x32 + size_t(idb) * P.d_pad, P.d, g8, gmask, sa, sb);
     const int m = min(8, cnt - c0);
     for (int t = 0; t < m; ++t) {
       const int src = (t & 3) * 8;
@@ -313,7 +315,7 @@ __device__ __forceinline__ int flush_candidates(const Dev& P, const float* q, ui
       const int c = c0 + g;
       const bool valid = c < b1;
       const uint32_t id = valid ? cbuf[c] : cbuf[c0];
-      const float est = sim_bf16_pair<NT2>(q, P.x16 + size_t(id) * P.d_pad, P.d_pad, h);
+      const float est = sim_bf16_pair<NT2>(q, P.x16 + size_t(id) * P.d_pad, P.d, h);
       const bool need = valid && est + P.bf16_err >= kth;
       const unsigned b = __ballot_sync(kFull, need && h == 0);
       __syncwarp();
