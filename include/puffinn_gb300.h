@@ -246,7 +246,63 @@ pf_status pf_index_read_array(const pf_index* index, int32_t which, void* dst, u
 /* Defaults: FP32 scoring, filter on, no learned start, no start depths. */
 void pf_search_opts_default(pf_search_opts* opts);
 
-/* Release an index (NULL is accepted). */
+/* ---- Launch-shape tuning (the shape is not part of the method of Sec. 4:
+ * results, statistics and their order are the same for every shape) ----
+ * Times the search kernel of a batch (Q queries of one k and recall, opts as
+ * in pf_index_search: scoring, filter, learned start) for each candidate shape
+ * -- 4 or 8 positions per lane per streaming step, times the largest resident
+ * CTAs per SM and one or two fewer -- and keeps the fastest for the index's
+ * later searches and plans.  queries: host or device, [Q][d] float32.
+ * report (may be NULL) receives the choice.  Errors: PF_ERR_INVALID_ARG (bad
+ * sizes, or search plans bound to the index exist), PF_ERR_NOT_TRAINED, CUDA. */
+typedef struct {
+  int32_t unroll;       /* chosen positions per lane per streaming step */
+  int32_t ctas_per_sm;  /* chosen CTAs per SM */
+  int32_t candidates;   /* shapes timed */
+  float best_ms;        /* search-kernel time of the chosen shape on the batch */
+  float default_ms;     /* ... of the default shape (8 positions, full occupancy) */
+} pf_tune_report;
+pf_status pf_index_tune(pf_index* index, const float* queries, int64_t Q, int32_t k, double recall,
+                        const pf_search_opts* opts, pf_tune_report* report, void* stream);
+
+/* ---- Captured search (a CUDA graph of one batch shape) ----
+ * pf_index_search for a fixed Q, k_max and options, bound to caller-owned
+ * DEVICE buffers: normalisation, hashing (with its float64 fix-up), the
+ * learned start (if opts->learned_start) and the search kernel are captured
+ * once into a CUDA graph; pf_search_plan_run launches it (one graph launch,
+ * asynchronous on `stream`), reading whatever the buffers hold at that time.
+ * The plan owns its own workspace, so plans and plain searches of one index
+ * do not share scratch; runs of one plan must not overlap.  A plan is bound to
+ * the index's state at creation: while plans exist, pf_learned_train and
+ * pf_index_tune fail with PF_ERR_INVALID_ARG and pf_index_free does nothing
+ * (it sets the error message), so free plans first. */
+typedef struct pf_search_plan pf_search_plan;
+typedef struct {
+  const float* queries;        /* [Q][d] float32 */
+  const int32_t* k;            /* [Q] in [1, k_max] */
+  const double* recall;        /* [Q] in (0, 1) */
+  const int32_t* start_depth;  /* [Q] per-query start depths, or NULL (see pf_search_opts) */
+  uint32_t* out_ids;           /* [Q][k_max] */
+  float* out_sims;             /* [Q][k_max] */
+  pf_query_stats* stats;       /* [Q], or NULL */
+} pf_plan_io;
+/* opts: scoring, filter, learned_start (timing and opts->start_depth are
+ * ignored: the start depths, if any, are io->start_depth).  Errors:
+ * PF_ERR_INVALID_ARG (Q < 1, k_max outside [1, 128], a null or host pointer),
+ * PF_ERR_NOT_TRAINED, PF_ERR_OOM, CUDA. */
+pf_status pf_search_plan_create(pf_index* index, int64_t Q, int32_t k_max, const pf_plan_io* io,
+                                const pf_search_opts* opts, pf_search_plan** out);
+/* Launch the captured graph on `stream`; returns without waiting. */
+pf_status pf_search_plan_run(pf_search_plan* plan, void* stream);
+/* Wait for `stream` and report what the last run found: PF_ERR_INVALID_ARG if
+ * some k or recall was out of range (those queries return empty rows),
+ * PF_ERR_DEVICE_TIMEOUT if a bounded device-side wait expired. */
+pf_status pf_search_plan_check(pf_search_plan* plan, void* stream);
+/* Release a plan (NULL is accepted). */
+void pf_search_plan_free(pf_search_plan* plan);
+
+/* Release an index (NULL is accepted).  Does nothing while search plans bound
+ * to it exist (pf_last_error_message says so). */
 void pf_index_free(pf_index* index);
 
 /* Static description of a status code. */

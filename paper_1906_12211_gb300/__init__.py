@@ -65,6 +65,16 @@ class LearnedReport(C.Structure):
                 ("mean_start", C.c_float), ("samples", C.c_int32), ("epochs", C.c_int32)]
 
 
+class TuneReport(C.Structure):
+    _fields_ = [("unroll", C.c_int32), ("ctas_per_sm", C.c_int32), ("candidates", C.c_int32),
+                ("best_ms", C.c_float), ("default_ms", C.c_float)]
+
+
+class PlanIO(C.Structure):
+    _fields_ = [("queries", C.c_void_p), ("k", C.c_void_p), ("recall", C.c_void_p), ("start_depth", C.c_void_p),
+                ("out_ids", C.c_void_p), ("out_sims", C.c_void_p), ("stats", C.c_void_p)]
+
+
 class PuffinnError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -105,6 +115,11 @@ def lib():
                 "pf_index_read_array": (i32, [vp, i32, vp, C.c_uint64, vp]),
                 "pf_search_opts_default": (None, [vp]),
                 "pf_index_free": (None, [vp]),
+                "pf_index_tune": (i32, [vp, vp, i64, i32, C.c_double, vp, vp, vp]),
+                "pf_search_plan_create": (i32, [vp, i64, i32, vp, vp, vp]),
+                "pf_search_plan_run": (i32, [vp, vp]),
+                "pf_search_plan_check": (i32, [vp, vp]),
+                "pf_search_plan_free": (None, [vp]),
                 "pf_status_string": (C.c_char_p, [i32]),
                 "pf_last_error_message": (C.c_char_p, []),
             }
@@ -284,11 +299,65 @@ class Index:
                                              _stream_ptr(stream)))
         return out_ids, out_sims, stats
 
+    def _opts(self, scoring, filter, learned):
+        o = SearchOpts()
+        lib().pf_search_opts_default(C.byref(o))
+        o.scoring = 1 if scoring == "bf16" else 0
+        o.filter = 1 if filter else 0
+        o.learned_start = 1 if learned else 0
+        return o
+
+    def tune(self, queries, k: int, recall: float, *, scoring: str = "fp32", filter: bool = True,
+             learned: bool = False, stream=None):
+        """pf_index_tune: time the search launch shapes on this batch and keep the fastest."""
+        rep = TuneReport()
+        o = self._opts(scoring, filter, learned)
+        _check(lib().pf_index_tune(self._h, _ptr(queries), int(queries.shape[0]), int(k), float(recall),
+                                   C.byref(o), C.byref(rep), _stream_ptr(stream)))
+        return {f: getattr(rep, f) for f, _ in TuneReport._fields_}
+
+    def plan(self, queries, k, recall, out_ids, out_sims, *, k_max: int, stats=None, start_depth=None,
+             scoring: str = "fp32", filter: bool = True, learned: bool = False):
+        """pf_search_plan_create: a CUDA graph of this search bound to these device tensors."""
+        return SearchPlan(self, queries, k, recall, out_ids, out_sims, k_max=k_max, stats=stats,
+                          start_depth=start_depth, opts=self._opts(scoring, filter, learned))
+
     def last_timing(self):
         """(hash_ms, search_kernel_ms, total_ms) of the last search run with timing=True."""
         t = (C.c_float * 3)()
         _check(lib().pf_index_last_timing(self._h, t, 3))
         return tuple(float(v) for v in t)
+
+
+class SearchPlan:
+    """A captured search (CUDA graph) bound to device tensors; run() launches it."""
+
+    def __init__(self, index, queries, k, recall, out_ids, out_sims, *, k_max, stats, start_depth, opts):
+        self._index = index
+        self._keep = (queries, k, recall, out_ids, out_sims, stats, start_depth)
+        io = PlanIO(_ptr(queries), _ptr(k), _ptr(recall), _ptr(start_depth), _ptr(out_ids), _ptr(out_sims),
+                    _ptr(stats))
+        h = C.c_void_p()
+        _check(lib().pf_search_plan_create(index._h, int(queries.shape[0]), int(k_max), C.byref(io), C.byref(opts),
+                                           C.byref(h)))
+        self._h = h
+
+    def run(self, stream=None):
+        _check(lib().pf_search_plan_run(self._h, _stream_ptr(stream)))
+
+    def check(self, stream=None):
+        _check(lib().pf_search_plan_check(self._h, _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pf_search_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mlp_forward_backward(X, y, W1, b1, W2, b2, stream=None):

@@ -110,11 +110,8 @@ void free_ws(pf_workspace& ws) {
   ws.cap_kmax = 0;
 }
 
-void ensure_ws(pf_index* ix, int64_t Q, int k_max) {
-  pf_workspace& ws = ix->ws;
-  if (size_t(Q) <= ws.cap_q && size_t(k_max) <= ws.cap_kmax) return;
-  const size_t q = std::max<size_t>(size_t(Q), ws.cap_q);
-  const size_t km = std::max<size_t>(size_t(k_max), ws.cap_kmax);
+// (re)allocate a workspace for q queries of up to km results
+void alloc_ws(pf_index* ix, pf_workspace& ws, size_t q, size_t km) {
   free_ws(ws);
   const int dp = ix->lay.d_pad;
   dalloc(&ws.qraw, q * ix->d);
@@ -134,6 +131,12 @@ void ensure_ws(pf_index* ix, int64_t Q, int k_max) {
   dalloc(&ws.rq_count, size_t(ix->num_sms));
   ws.cap_q = q;
   ws.cap_kmax = km;
+}
+
+void ensure_ws(pf_index* ix, int64_t Q, int k_max) {
+  pf_workspace& ws = ix->ws;
+  if (size_t(Q) <= ws.cap_q && size_t(k_max) <= ws.cap_kmax) return;
+  alloc_ws(ix, ws, std::max<size_t>(size_t(Q), ws.cap_q), std::max<size_t>(size_t(k_max), ws.cap_kmax));
 }
 
 void destroy(pf_index* ix) {
@@ -172,20 +175,19 @@ void stage_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
 }
 
 // Hash and normalise Q queries (device pointer qsrc) into the workspace.
-void hash_queries_ws(pf_index* ix, const float* qdev, int64_t Q, cudaStream_t s) {
-  pf_workspace& ws = ix->ws;
+void hash_queries_ws(pf_index* ix, pf_workspace& ws, const float* qdev, int64_t Q, cudaStream_t s) {
   PF_CK(launch_normalize(qdev, Q, ix->d, ix->lay.d_pad, ws.qx, ws.qxh, ws.qxl, s));
   PF_CK(launch_hash(ix, ws.qx, ws.qxh, ws.qxl, Q, ws.qcodes, 1, ix->L, ws.qsk, 1, ix->M, ws.rq, ws.rq_count,
                     recheck_capacity(Q), s));
 }
 
 // start depths of the model for the Q hashed queries of the workspace -> ws.start
-void predict_ws(pf_index* ix, int64_t Q, cudaStream_t s) {
+void predict_ws(pf_index* ix, pf_workspace& ws, int64_t Q, cudaStream_t s) {
   const int F = ix->mlp_F, H = kMlpHidden, C = ix->mlp_C;
   const float* b1 = ix->mlp_w + size_t(H) * F;
   const float* b2 = b1 + H + size_t(C) * H;
-  PF_CK(mlp_predict(ix->ws.qx, ix->ws.qsk, int(Q), ix->lay.d_pad, ix->M, ix->mlp_w1h, b1, ix->mlp_w2h, b2, C,
-                    kMlpTail, kMlpMargin, ix->ws.start, s));
+  PF_CK(mlp_predict(ws.qx, ws.qsk, int(Q), ix->lay.d_pad, ix->M, ix->mlp_w1h, b1, ix->mlp_w2h, b2, C, kMlpTail,
+                    kMlpMargin, ws.start, s));
 }
 
 const float* stage_queries(pf_index* ix, const float* queries, int64_t Q, cudaStream_t s) {
@@ -375,7 +377,7 @@ pf_status pf_hash_queries(pf_index* ix, const float* queries, int64_t Q, uint32_
     PF_CK(cudaSetDevice(ix->device));
     ensure_ws(ix, Q, 1);
     const float* qd = stage_queries(ix, queries, Q, s);
-    hash_queries_ws(ix, qd, Q, s);
+    hash_queries_ws(ix, ix->ws, qd, Q, s);
     PF_CK(cudaMemcpyAsync(qcodes, ix->ws.qcodes, sizeof(uint32_t) * size_t(Q) * ix->L, cudaMemcpyDefault, s));
     PF_CK(cudaMemcpyAsync(qsk, ix->ws.qsk, sizeof(uint64_t) * size_t(Q) * ix->M, cudaMemcpyDefault, s));
     PF_CK(cudaStreamSynchronize(s));
@@ -417,9 +419,9 @@ pf_status pf_index_search(pf_index* ix, const float* queries, int64_t Q, const i
         if (!e) PF_CK(cudaEventCreate(&e));
       PF_CK(cudaEventRecord(ix->ev[0], s));
     }
-    hash_queries_ws(ix, qd, Q, s);
+    hash_queries_ws(ix, ix->ws, qd, Q, s);
     if (o.learned_start) {
-      predict_ws(ix, Q, s);
+      predict_ws(ix, ix->ws, Q, s);
       sd = ws.start;
     }
     if (timing) PF_CK(cudaEventRecord(ix->ev[1], s));
@@ -571,6 +573,7 @@ pf_status pf_learned_train(pf_index* ix, const float* train_queries, int64_t Qt,
     if (k < 1 || k > kMaxK) return fail(PF_ERR_INVALID_ARG, "k must be in [1, 128]");
     if (!(recall > 0.0 && recall < 1.0)) return fail(PF_ERR_INVALID_ARG, "recall not in (0, 1)");
     if (epochs < 1 || epochs > 100000) return fail(PF_ERR_INVALID_ARG, "epochs must be in [1, 100000]");
+    if (ix->live_plans > 0) return fail(PF_ERR_INVALID_ARG, "search plans bound to the index exist");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PF_CK(cudaSetDevice(ix->device));
     const int F = ix->lay.d_pad + 64, H = kMlpHidden, C = ix->lay.Kb + 1;
@@ -610,7 +613,7 @@ pf_status pf_learned_train(pf_index* ix, const float* train_queries, int64_t Qt,
         const int64_t nq = std::min(chunk, Qt - q0);
         const float* src = train_queries + size_t(q0) * ix->d;
         const float* qd = stage_queries(ix, src, nq, s);
-        hash_queries_ws(ix, qd, nq, s);
+        hash_queries_ws(ix, ix->ws, qd, nq, s);
         SearchArgs a;
         a.Q = int(nq);
         a.qx = ws.qx;
@@ -709,8 +712,8 @@ pf_status pf_learned_train(pf_index* ix, const float* train_queries, int64_t Qt,
         for (int64_t q0 = 0; q0 < Qt; q0 += chunk) {
           const int64_t nq = std::min(chunk, Qt - q0);
           const float* qd = stage_queries(ix, train_queries + size_t(q0) * ix->d, nq, s);
-          hash_queries_ws(ix, qd, nq, s);
-          predict_ws(ix, nq, s);
+          hash_queries_ws(ix, ix->ws, qd, nq, s);
+          predict_ws(ix, ix->ws, nq, s);
           PF_CK(cudaMemcpyAsync(sd.data(), ws.start, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, s));
           PF_CK(cudaStreamSynchronize(s));
           for (int64_t i = 0; i < nq; ++i) {
@@ -747,14 +750,265 @@ pf_status pf_learned_predict(pf_index* ix, const float* queries, int64_t Q, int3
     PF_CK(cudaSetDevice(ix->device));
     ensure_ws(ix, Q, 1);
     const float* qd = stage_queries(ix, queries, Q, s);
-    hash_queries_ws(ix, qd, Q, s);
-    predict_ws(ix, Q, s);
+    hash_queries_ws(ix, ix->ws, qd, Q, s);
+    predict_ws(ix, ix->ws, Q, s);
     PF_CK(cudaMemcpyAsync(start_depth, ix->ws.start, sizeof(int32_t) * size_t(Q), cudaMemcpyDefault, s));
     PF_CK(cudaStreamSynchronize(s));
     return PF_OK;
   });
 }
 
-void pf_index_free(pf_index* ix) { destroy(ix); }
+void pf_index_free(pf_index* ix) {
+  if (ix && ix->live_plans > 0) {
+    set_error("pf_index_free: search plans bound to the index still exist; free them first");
+    return;
+  }
+  destroy(ix);
+}
+
+// ---------------------------------------------------------------- tuning
+pf_status pf_index_tune(pf_index* ix, const float* queries, int64_t Q, int32_t k, double recall,
+                        const pf_search_opts* opts, pf_tune_report* report, void* stream) {
+  return guarded([&]() -> pf_status {
+    if (!ix || !queries) return fail(PF_ERR_INVALID_ARG, "null argument");
+    if (Q < 1 || Q > 0x7fffffffLL) return fail(PF_ERR_INVALID_ARG, "Q must be in [1, 2^31-1]");
+    if (k < 1 || k > kMaxK) return fail(PF_ERR_INVALID_ARG, "k must be in [1, 128]");
+    if (!(recall > 0.0 && recall < 1.0)) return fail(PF_ERR_INVALID_ARG, "recall must be in (0, 1)");
+    if (ix->live_plans > 0) return fail(PF_ERR_INVALID_ARG, "search plans bound to the index exist");
+    pf_search_opts o;
+    pf_search_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.scoring != 0 && o.scoring != 1) return fail(PF_ERR_INVALID_ARG, "scoring must be 0 or 1");
+    if (o.learned_start && !ix->mlp_trained) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PF_CK(cudaSetDevice(ix->device));
+    ensure_ws(ix, Q, k);
+    pf_workspace& ws = ix->ws;
+    const float* qd = stage_queries(ix, queries, Q, s);
+    {
+      std::vector<int32_t> kv(size_t(Q), k);
+      std::vector<double> rv(size_t(Q), recall);
+      PF_CK(cudaMemcpyAsync(ws.k, kv.data(), sizeof(int32_t) * size_t(Q), cudaMemcpyHostToDevice, s));
+      PF_CK(cudaMemcpyAsync(ws.recall, rv.data(), sizeof(double) * size_t(Q), cudaMemcpyHostToDevice, s));
+      PF_CK(cudaStreamSynchronize(s));
+    }
+    const int32_t* sd = o.start_depth;
+    if (sd && !on_device(sd)) {
+      stage_in(ws.start, sd, sizeof(int32_t) * size_t(Q), s);
+      sd = ws.start;
+    }
+    hash_queries_ws(ix, ws, qd, Q, s);
+    if (o.learned_start) {
+      predict_ws(ix, ws, Q, s);
+      sd = ws.start;
+    }
+    SearchArgs a;
+    a.Q = int(Q);
+    a.qx = ws.qx;
+    a.qcodes = ws.qcodes;
+    a.qsk = ws.qsk;
+    a.k = ws.k;
+    a.recall = ws.recall;
+    a.start = sd;
+    a.k_max = k;
+    a.filter = o.filter ? 1 : 0;
+    a.scoring = o.scoring;
+    a.out_ids = ws.ids;
+    a.out_sims = ws.sims;
+    a.stats = nullptr;
+    a.counter = ws.counter;
+    std::vector<SearchShape> cand;
+    for (int U : {8, 4}) {
+      const int mx = search_max_ctas_per_sm(ix, k, U);
+      for (int c = mx; c >= 1 && c >= mx - 2; --c) cand.push_back(SearchShape{U, c});
+    }
+    if (cand.empty()) return fail(PF_ERR_CUDA, "no launchable search shape");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PF_CK(cudaEventCreate(&e0));
+    PF_CK(cudaEventCreate(&e1));
+    float best = 0.f, dflt = 0.f;
+    SearchShape pick = cand[0];
+    try {
+      for (size_t i = 0; i < cand.size(); ++i) {
+        a.shape = cand[i];
+        float t = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {  // the first run warms up; the best of two timed runs
+          PF_CK(cudaMemsetAsync(ws.counter, 0, sizeof(int32_t) * 64, s));
+          PF_CK(cudaEventRecord(e0, s));
+          PF_CK(launch_search(ix, a, s));
+          PF_CK(cudaEventRecord(e1, s));
+          PF_CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          PF_CK(cudaEventElapsedTime(&ms, e0, e1));
+          if (rep == 1 || (rep == 2 && ms < t)) t = ms;
+        }
+        if (i == 0) dflt = t;
+        if (i == 0 || t < best) {
+          best = t;
+          pick = cand[i];
+        }
+      }
+    } catch (...) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ix->search_shape = pick;
+    if (report) {
+      report->unroll = pick.unroll;
+      report->ctas_per_sm = pick.ctas_per_sm;
+      report->candidates = int32_t(cand.size());
+      report->best_ms = best;
+      report->default_ms = dflt;
+    }
+    return PF_OK;
+  });
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- plans
+struct pf_search_plan {
+  pf_index* ix = nullptr;
+  int64_t Q = 0;
+  int k_max = 0;
+  pf_search_opts opts{};
+  pf_plan_io io{};
+  pf_workspace ws;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+// The captured sequence: the same steps as pf_index_search on device buffers.
+void plan_sequence(pf_search_plan* pl, cudaStream_t s) {
+  pf_index* ix = pl->ix;
+  pf_workspace& ws = pl->ws;
+  hash_queries_ws(ix, ws, pl->io.queries, pl->Q, s);
+  const int32_t* sd = pl->io.start_depth;
+  if (pl->opts.learned_start) {
+    predict_ws(ix, ws, pl->Q, s);
+    sd = ws.start;
+  }
+  SearchArgs a;
+  a.Q = int(pl->Q);
+  a.qx = ws.qx;
+  a.qcodes = ws.qcodes;
+  a.qsk = ws.qsk;
+  a.k = pl->io.k;
+  a.recall = pl->io.recall;
+  a.start = sd;
+  a.k_max = pl->k_max;
+  a.filter = pl->opts.filter ? 1 : 0;
+  a.scoring = pl->opts.scoring;
+  a.out_ids = pl->io.out_ids;
+  a.out_sims = pl->io.out_sims;
+  a.stats = pl->io.stats;
+  a.counter = ws.counter;
+  PF_CK(cudaMemsetAsync(ws.counter, 0, sizeof(int32_t) * 64, s));
+  PF_CK(launch_search(ix, a, s));
+}
+
+void plan_release(pf_search_plan* pl) {
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  free_ws(pl->ws);
+  delete pl;
+}
+
+}  // namespace
+
+extern "C" {
+
+pf_status pf_search_plan_create(pf_index* ix, int64_t Q, int32_t k_max, const pf_plan_io* io,
+                                const pf_search_opts* opts, pf_search_plan** out) {
+  return guarded([&]() -> pf_status {
+    if (!ix || !io || !out) return fail(PF_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (Q < 1 || Q > 0x7fffffffLL) return fail(PF_ERR_INVALID_ARG, "Q must be in [1, 2^31-1]");
+    if (k_max < 1 || k_max > kMaxK) return fail(PF_ERR_INVALID_ARG, "k_max must be in [1, 128]");
+    PF_CK(cudaSetDevice(ix->device));
+    const void* need[] = {io->queries, io->k, io->recall, io->out_ids, io->out_sims};
+    for (const void* p : need)
+      if (!p || !on_device(p)) return fail(PF_ERR_INVALID_ARG, "plan buffers must be device pointers");
+    if ((io->start_depth && !on_device(io->start_depth)) || (io->stats && !on_device(io->stats)))
+      return fail(PF_ERR_INVALID_ARG, "plan buffers must be device pointers");
+    pf_search_opts o;
+    pf_search_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.scoring != 0 && o.scoring != 1) return fail(PF_ERR_INVALID_ARG, "scoring must be 0 or 1");
+    if (o.learned_start && !ix->mlp_trained) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
+    o.start_depth = nullptr;
+    o.timing = 0;
+    pf_search_plan* pl = new pf_search_plan;
+    pl->ix = ix;
+    pl->Q = Q;
+    pl->k_max = k_max;
+    pl->opts = o;
+    pl->io = *io;
+    cudaStream_t cs = nullptr;
+    try {
+      alloc_ws(ix, pl->ws, size_t(Q), size_t(k_max));
+      PF_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      PF_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+      try {
+        plan_sequence(pl, cs);
+      } catch (...) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(cs, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+      }
+      PF_CK(cudaStreamEndCapture(cs, &pl->graph));
+      PF_CK(cudaGraphInstantiate(&pl->exec, pl->graph, 0));
+      PF_CK(cudaStreamDestroy(cs));
+      cs = nullptr;
+    } catch (...) {
+      if (cs) cudaStreamDestroy(cs);
+      plan_release(pl);
+      throw;
+    }
+    ix->live_plans += 1;
+    *out = pl;
+    return PF_OK;
+  });
+}
+
+pf_status pf_search_plan_run(pf_search_plan* pl, void* stream) {
+  return guarded([&]() -> pf_status {
+    if (!pl) return fail(PF_ERR_INVALID_ARG, "null plan");
+    PF_CK(cudaSetDevice(pl->ix->device));
+    PF_CK(cudaGraphLaunch(pl->exec, static_cast<cudaStream_t>(stream)));
+    return PF_OK;
+  });
+}
+
+pf_status pf_search_plan_check(pf_search_plan* pl, void* stream) {
+  return guarded([&]() -> pf_status {
+    if (!pl) return fail(PF_ERR_INVALID_ARG, "null plan");
+    PF_CK(cudaSetDevice(pl->ix->device));
+    PF_CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int32_t flags = 0, herr = 0;
+    PF_CK(cudaMemcpy(&flags, pl->ws.counter + 1, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    PF_CK(cudaMemcpy(&herr, pl->ix->dev_error, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (herr) return fail(PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out");
+    if (flags & 1) return fail(PF_ERR_INVALID_ARG, "some k not in [1, k_max] or recall not in (0, 1)");
+    return PF_OK;
+  });
+}
+
+void pf_search_plan_free(pf_search_plan* pl) {
+  if (!pl) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(pl->ix->device);
+  cudaDeviceSynchronize();  // a launched graph may still be running
+  pl->ix->live_plans -= 1;
+  plan_release(pl);
+  cudaSetDevice(prev);
+}
 
 }  // extern "C"

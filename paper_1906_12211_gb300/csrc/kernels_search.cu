@@ -40,10 +40,10 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kQW = 4;          // warps per query (one CTA)
 constexpr int kThreads = 32 * kQW;
-constexpr int kUnroll = 8;      // positions per lane per warp step
-constexpr uint32_t kSpan = 32 * kUnroll;  // positions of one run per chunk (one warp step)
-constexpr int kCandBuf = 512;   // compacted candidate ids per warp
-constexpr int kFlushAt = kCandBuf - 32 * kUnroll;
+// U = positions per lane per streaming step (a template parameter: 4 or 8,
+// chosen by the tuner); a chunk is 32*U positions of one run
+constexpr int kFlushAt = 256;   // a warp scores its buffer once it holds more than this
+__host__ __device__ constexpr int cand_buf(int U) { return kFlushAt + 32 * U; }  // compacted ids per warp
 constexpr int kGroup = 32;      // repetitions per threshold snapshot in a first round
 constexpr int kSub = 64;        // candidates per bfloat16 sub-batch (the pruning bound is refreshed between)
 
@@ -332,8 +332,11 @@ __device__ __forceinline__ int flush_candidates(const Dev& P, const float* q, ui
 // NT = d_pad / 32 rounded up: float4 chunks of a float32 row per lane of an
 // 8-lane group; NT2 = d_pad / 16 rounded up: 16-byte chunks of a bfloat16 row
 // per lane of a pair
-template <int NT, int NT2>
+template <int NT, int NT2, int U>
 __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
+  constexpr int kUnroll = U;
+  constexpr uint32_t kSpan = 32u * U;
+  constexpr int kCandBuf = cand_buf(U);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int d_pad = P.d_pad, L = P.L, kmax = P.k_max, M = P.M;
@@ -706,24 +709,49 @@ cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t 
   P.out_sims = a.out_sims;
   P.stats = a.stats;
   P.counter = a.counter;
+  const SearchShape sh = a.shape.unroll ? a.shape : ix->search_shape;
+  const int U = sh.unroll == 4 ? 4 : 8;
   // q | runs | ranges | qsk | cpre | top-k | warp lists | warp candidate buffers
   const size_t smem = size_t(P.d_pad) * 4 + size_t(P.L) * 24 + size_t(P.M) * 8 + size_t(P.L + 1) * 4 +
-                      size_t(P.k_max) * 8 * (1 + kQW) + size_t(kCandBuf) * 4 * kQW;
+                      size_t(P.k_max) * 8 * (1 + kQW) + size_t(cand_buf(U)) * 4 * kQW;
   const int nt = (P.d_pad + 31) / 32;
-  auto kern = nt <= 1   ? search_kernel<1, 2>
-              : nt <= 2 ? search_kernel<2, 4>
-              : nt <= 4 ? search_kernel<4, 8>
-                        : search_kernel<8, 16>;
+  void (*kern)(Dev);
+  if (U == 4)
+    kern = nt <= 1 ? search_kernel<1, 2, 4> : nt <= 2 ? search_kernel<2, 4, 4> : nt <= 4 ? search_kernel<4, 8, 4>
+                                                                                      : search_kernel<8, 16, 4>;
+  else
+    kern = nt <= 1 ? search_kernel<1, 2, 8> : nt <= 2 ? search_kernel<2, 4, 8> : nt <= 4 ? search_kernel<4, 8, 8>
+                                                                                      : search_kernel<8, 16, 8>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  if (sh.ctas_per_sm > 0 && sh.ctas_per_sm < per_sm) per_sm = sh.ctas_per_sm;
   int blocks = ix->num_sms * per_sm;
   if (blocks > a.Q) blocks = a.Q;
   kern<<<blocks, kThreads, smem, s>>>(P);
   return cudaGetLastError();
+}
+
+int search_max_ctas_per_sm(const pf_index* ix, int k_max, int unroll) {
+  const int U = unroll == 4 ? 4 : 8;
+  const int d_pad = ix->lay.d_pad, L = ix->L, M = ix->M;
+  const size_t smem = size_t(d_pad) * 4 + size_t(L) * 24 + size_t(M) * 8 + size_t(L + 1) * 4 +
+                      size_t(k_max) * 8 * (1 + kQW) + size_t(cand_buf(U)) * 4 * kQW;
+  const int nt = (d_pad + 31) / 32;
+  void (*kern)(Dev);
+  if (U == 4)
+    kern = nt <= 1 ? search_kernel<1, 2, 4> : nt <= 2 ? search_kernel<2, 4, 4> : nt <= 4 ? search_kernel<4, 8, 4>
+                                                                                      : search_kernel<8, 16, 4>;
+  else
+    kern = nt <= 1 ? search_kernel<1, 2, 8> : nt <= 2 ? search_kernel<2, 4, 8> : nt <= 4 ? search_kernel<4, 8, 8>
+                                                                                      : search_kernel<8, 16, 8>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) != cudaSuccess) return 0;
+  return per_sm;
 }
 
 }  // namespace pf

@@ -34,6 +34,13 @@ struct Layout {
 };
 Layout make_layout(int family, int d);
 
+// Launch shape of the search kernel (not part of the method): positions per
+// lane per streaming step (4 or 8) and a cap on CTAs per SM (0: occupancy).
+struct SearchShape {
+  int unroll = 0;       // 0 in SearchArgs: the index's tuned shape
+  int ctas_per_sm = 0;
+};
+
 // ---------------------------------------------------------------- host params
 float gaussian(uint64_t seed, uint32_t purpose, uint32_t a, uint32_t b, uint32_t c);
 // W[(L*rows_table + 64*M)][d_pad] float32 and per-row recheck band thr[]
@@ -106,6 +113,8 @@ struct pf_index {
   float bf16_err = 0.f;            // bound on |bf16 estimate - float32 canonical similarity|
   int32_t* dev_error = nullptr;    // device error word (bit 1: a bounded wait timed out)
   int num_sms = 0;
+  pf::SearchShape search_shape{8, 0};  // chosen by pf_index_tune (default: 8 positions per lane, full occupancy)
+  int live_plans = 0;                   // captured search plans bound to this index
   pf_workspace ws;
   // start-depth model: params = [W1 (H x F) | b1 (H) | W2 (C x H) | b2 (C)], float32
   int mlp_trained = 0, mlp_F = 0, mlp_C = 0;
@@ -150,6 +159,7 @@ cudaError_t gather_table_sketches(const pf_index* ix, const uint64_t* sk, uint64
 
 struct SearchArgs {
   int Q = 0;
+  SearchShape shape;   // launch shape override (unroll 0: the index's)
   const float* qx = nullptr;
   const uint32_t* qcodes = nullptr;
   const uint64_t* qsk = nullptr;
@@ -165,6 +175,8 @@ struct SearchArgs {
   int32_t* counter = nullptr;
 };
 cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t s);
+// CTAs per SM the search kernel can keep resident for this index (0 on error)
+int search_max_ctas_per_sm(const pf_index* ix, int k_max, int unroll);
 
 // start-depth perceptron (kernels_mlp.cu)
 cudaError_t mlp_features(const float* qx, const uint64_t* qsk, int Q, int d_pad, int M, float* x, cudaStream_t s);
