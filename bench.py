@@ -7,7 +7,10 @@ Workload: n = 1,000,000 unit vectors in d = 100 from an equal-weight mixture of
 Metric: k-NN queries/s at measured recall >= 0.9 (recall against exact brute
 force).  One step = one batched search of all queries: query normalisation and
 hashing, the persistent search kernel, outputs.  The index build is timed
-separately (it is done once per index).
+separately (it is done once per index).  Before timing, the search kernel's
+launch shape is tuned on a separate query set of the same distribution
+(pf_index_tune); the same step is also timed as one CUDA-graph launch
+(pf_search_plan_run), reported under "graph".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--mode bf16|fp32]
   python bench.py --impl reference ...   (times the CPU oracle on a sample)
@@ -60,6 +63,8 @@ def parse():
     ap.add_argument("--budget", type=int, default=None, help="index budget in bytes (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape of the search kernel")
+    ap.add_argument("--no-graph", action="store_true", help="skip timing the captured (CUDA graph) search")
     return ap.parse_args()
 
 
@@ -287,6 +292,14 @@ def main():
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
 
+    # launch shape of the search kernel: timed on a separate query set of the
+    # same distribution (the tuner's choice changes no result)
+    tune_report = None
+    if not args.no_tune:
+        Qtune = datagen.vmf_mixture(Q, w["d"], w["components"], w["kappa"], seed=rank, purpose="tune")
+        tune_report = ix.tune(torch.from_numpy(Qtune).to(dev), k, args.recall,
+                              scoring="fp32" if args.mode == "fp32" else "bf16", learned=args.mode == "learned")
+
     def run_mode(mode, timing=False):
         ix.search(Qd, kq, rq, k_max=k, scoring="fp32" if mode == "fp32" else "bf16", out_ids=ids, out_sims=sims,
                   stats=st, timing=timing, learned=mode == "learned")
@@ -352,6 +365,27 @@ def main():
                              "scored": float(ms["scored"].mean())}
         run_mode(args.mode)  # leave the headline mode's outputs in place
 
+    # the same step as one CUDA-graph launch (pf_search_plan_run) on the same buffers
+    graph = None
+    if not args.no_graph:
+        plan = ix.plan(Qd, kq, rq, ids, sims, k_max=k, stats=st, scoring="fp32" if args.mode == "fp32" else "bf16",
+                       learned=args.mode == "learned")
+        for _ in range(2):
+            plan.run()
+        plan.check()
+        tot = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.run()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        plan.check()
+        plan.close()
+        graph = {"value": Q * args.steps / (tot / 1e3), "ms_per_step": tot / args.steps}
+
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -415,6 +449,7 @@ def main():
                                                              "passed_filter", "scored", "reranked")},
             "gpu_launches": (5 if args.mode == "learned" else 4) * args.steps,
             "compare": compare, "learned_train": train_report, "learned_train_s": train_s,
+            "search_shape": tune_report, "graph": graph,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
         }
         print(json.dumps(line), flush=True)
