@@ -58,8 +58,8 @@ def parse():
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other two modes")
     ap.add_argument("--recall", type=float, default=0.9, help="recall target 1 - delta passed to the index")
-    ap.add_argument("--n", type=int, default=None)
-    ap.add_argument("--Q", type=int, default=None)
+    ap.add_argument("--points", type=int, default=None, help="override the workload's number of points")
+    ap.add_argument("--queries", type=int, default=None, help="override the number of queries per rank")
     ap.add_argument("--budget", type=int, default=None, help="index budget in bytes (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -163,6 +163,24 @@ def workload(rank: int, n_override=None, q_override=None, budget=None):
     return w, X, Qs
 
 
+def max_over_ranks(seconds: float, dist=None, device=None) -> float:
+    """The slowest rank's time (the job ends when its last rank does); the
+    local value without a process group."""
+    if dist is None:
+        return seconds
+    import torch
+
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(queries_per_rank: int, world: int, steps: int, seconds: float) -> float:
+    """Queries per second of the whole job: every rank answers its own batch
+    each step (weak scaling), timed by the slowest rank."""
+    return queries_per_rank * world * steps / seconds
+
+
 def brute_force_kth(torch, Xd, Qd, k):
     """k-th largest exact similarity per query (float32 matmul on the GPU; used
     only to measure recall)."""
@@ -216,7 +234,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w, X, Qs = workload(0, args.n, args.Q, args.budget)
+    w, X, Qs = workload(0, args.points, args.queries, args.budget)
     import oracle
 
     L = oracle.budget_L(oracle.CROSSPOLYTOPE, X.shape[0], X.shape[1], 32, w["budget"])
@@ -262,7 +280,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     pf.build()
     dev = torch.device("cuda", local)
-    w, X, Qs = workload(rank, args.n, args.Q, args.budget)
+    w, X, Qs = workload(rank, args.points, args.queries, args.budget)
     Q, k = Qs.shape[0], w["k"]
     Xd = torch.from_numpy(X).to(dev)
     Qd = torch.from_numpy(Qs).to(dev)
@@ -328,15 +346,10 @@ def main():
         hash_ms += h
     torch.cuda.synchronize()
     clk = clocks.stop()
-    t_rank = total_ms / 1e3
+    t_max = max_over_ranks(total_ms / 1e3, dist, dev)
     if dist:
-        tt = torch.tensor([t_rank], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
         dist.barrier()
-    else:
-        t_max = t_rank
-    value = Q * world * args.steps / t_max
+    value = whole_job_rate(Q, world, args.steps, t_max)
     stats = pf.stats_to_numpy(st)
     recall = float((sims >= kth[:, None] - 1e-6).float().mean().item())
 
@@ -402,12 +415,8 @@ def main():
         t = time.perf_counter()
         for _ in range(args.steps):
             ix.search(qh, kh, rh, k_max=k, scoring=sc, out_ids=ih, out_sims=sh, learned=lr)
-        el = time.perf_counter() - t
-        if dist:
-            tt = torch.tensor([el], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            el = float(tt.item())
-        e2e = {"value": Q * world * args.steps / el, "unit": UNIT,
+        el = max_over_ranks(time.perf_counter() - t, dist, dev)
+        e2e = {"value": whole_job_rate(Q, world, args.steps, el), "unit": UNIT,
                "h2d_bytes_per_step": int(Q * X.shape[1] * 4 + Q * 4 + Q * 8),
                "d2h_bytes_per_step": int(Q * k * 8)}
 
