@@ -140,8 +140,8 @@ def search_kernel_traffic():
     digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     vals = {}
     for line in open(path):
-        if ":" in line and not line.startswith("#"):
-            k, v = line.split(":", 1)
+        if ": " in line and not line.startswith("#"):
+            k, v = line.rsplit(": ", 1)
             vals[k.strip()] = v.strip()
     if vals.get("kernels_search.cu sha256[:16]") != digest:
         return None

@@ -165,9 +165,12 @@ __global__ void __launch_bounds__(kMlpHidden) predict_kernel(const float* __rest
                                                              const __nv_bfloat16* __restrict__ W2,
                                                              const float* __restrict__ b2, int C, float tail,
                                                              int margin, int32_t* __restrict__ start) {
-  __shared__ float xs[kPredQ][kMaxD + 64];
+  // xs holds the features, then (once the hidden layer is done) the output
+  // layer's C <= 33 rows of bfloat16 weights
+  __shared__ __align__(16) float xs[kPredQ][kMaxD + 64];
   __shared__ float hs[kPredQ][kMlpHidden];
   __shared__ float zs[kPredQ][64];
+  __nv_bfloat16* w2s = reinterpret_cast<__nv_bfloat16*>(&xs[0][0]);
   const int tid = threadIdx.x;
   const int q0 = blockIdx.x * kPredQ;
   const int nq = min(kPredQ, Q - q0);
@@ -182,17 +185,24 @@ __global__ void __launch_bounds__(kMlpHidden) predict_kernel(const float* __rest
   float acc[kPredQ];
 #pragma unroll
   for (int t = 0; t < kPredQ; ++t) acc[t] = b1[u];
-  for (int i = 0; i < F; ++i) {
-    const float w = __bfloat162float(W1t[size_t(i) * kMlpHidden + u]);
+  // F is a multiple of 16 (d_pad + 64): eight weight loads in flight per step
+  for (int i0 = 0; i0 < F; i0 += 8) {
+    float w[8];
 #pragma unroll
-    for (int t = 0; t < kPredQ; ++t) acc[t] = fmaf(w, xs[t][i], acc[t]);
+    for (int j = 0; j < 8; ++j) w[j] = __bfloat162float(W1t[size_t(i0 + j) * kMlpHidden + u]);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int t = 0; t < kPredQ; ++t) acc[t] = fmaf(w[j], xs[t][i0 + j], acc[t]);
   }
 #pragma unroll
   for (int t = 0; t < kPredQ; ++t) hs[t][u] = fmaxf(acc[t], 0.f);
   __syncthreads();
+  for (int e = tid; e < C * kMlpHidden; e += kMlpHidden) w2s[e] = W2[e];
+  __syncthreads();
   for (int e = tid; e < nq * C; e += kMlpHidden) {
     const int t = e / C, c = e % C;
-    const __nv_bfloat16* row = W2 + size_t(c) * kMlpHidden;
+    const __nv_bfloat16* row = w2s + c * kMlpHidden;
     float a = b2[c];
     for (int h = 0; h < kMlpHidden; ++h) a = fmaf(__bfloat162float(row[h]), hs[t][h], a);
     zs[t][c] = a;
