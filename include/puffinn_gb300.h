@@ -61,6 +61,15 @@ typedef enum {
   PF_SKETCH_PER_POINT = 1  /* M sketches per point, gathered by id during the search */
 } pf_sketch_layout;
 
+/* Precision in which the normalised rows are kept (Sec. 4.2 keeps 16-bit
+ * vectors).  With binary16 the stored point is the round-to-nearest-even
+ * binary16 copy of the float64-normalised row: it is what is hashed, and the
+ * canonical float32 similarity is taken of it (read back exactly as float32). */
+typedef enum {
+  PF_ROWS_F32 = 0,  /* default: float32 rows */
+  PF_ROWS_F16 = 1   /* binary16 rows: half the row bytes */
+} pf_row_storage;
+
 /* Build parameters (Sec. 4.2-4.3).  Zero-initialise and set what you need;
  * zero means "default" for the optional fields. */
 typedef struct {
@@ -75,6 +84,7 @@ typedef struct {
   int32_t cp_draws;             /* Monte-Carlo draws per similarity for the CP table (Sec. 4.3); 0 -> 1000 */
   int32_t num_tables;           /* if > 0, use exactly this L instead of the budget (tests, sweeps) */
   int32_t sketch_layout;        /* pf_sketch_layout; 0 -> PF_SKETCH_PER_TABLE */
+  int32_t row_storage;          /* pf_row_storage; 0 -> PF_ROWS_F32 */
 } pf_build_params;
 
 /* Per-call search options.  NULL = defaults (FP32 scoring, filter on). */
@@ -112,6 +122,7 @@ typedef struct {
   int32_t B;                /* segment size */
   int32_t trained;          /* a start-depth model is present */
   int32_t sketch_layout;    /* pf_sketch_layout */
+  int32_t row_storage;      /* pf_row_storage */
   uint64_t bytes_used;      /* device bytes the index keeps resident */
   uint64_t budget_bytes;    /* budget it was built for */
 } pf_index_info_t;
@@ -126,8 +137,10 @@ typedef enum {
   PF_ARRAY_SKETCHES = 5,   /* uint64 [M][n]: 1-bit sketches (Sec. 3.3, 4.2); PF_SKETCH_PER_POINT only */
   PF_ARRAY_HASH_ROWS = 6,  /* float [L*R + 64*M][d_pad]: Gaussian rows (R = fns*d_pad for CP, 32 for HP) */
   PF_ARRAY_CP_TABLE = 7,   /* double [41][ell+1]: CP collision table (Sec. 4.3); absent for HP */
-  PF_ARRAY_TABLE_SKETCHES = 8 /* uint64 [L][n]: sketch (j mod M) of the point at each position of repetition j;
-                                 PF_SKETCH_PER_TABLE only */
+  PF_ARRAY_TABLE_SKETCHES = 8, /* uint64 [L][n]: sketch (j mod M) of the point at each position of repetition j;
+                                  PF_SKETCH_PER_TABLE only */
+  PF_ARRAY_ROWS_F16 = 9        /* binary16 [n][d_pad]: normalised points; PF_ROWS_F16 only (PF_ARRAY_ROWS_F32 is
+                                  then absent) */
 } pf_array;
 
 /* Build the index over `points` ([n][d] row-major, host or device).
@@ -136,7 +149,7 @@ typedef enum {
  * (code, pos) array and tabulate its 13-bit prefixes, and estimate the CP
  * collision table (Sec. 4.3).  L is the largest count whose resident bytes fit
  * memory_budget_bytes (PF_ERR_BUDGET_TOO_SMALL if none); the bytes counted are
- * those of the chosen sketch layout.  On success *out
+ * those of the chosen sketch layout and row storage.  On success *out
  * receives a new index that the caller releases with pf_index_free. */
 pf_status pf_index_build(const pf_build_params* params, const void* points, pf_index** out, void* stream);
 

@@ -82,7 +82,7 @@ def lib():
                 "orc_collision_prob": (f64, [C.c_int, C.c_int, vp, f64, C.c_int]),
                 "orc_ipow": (f64, [f64, i64]),
                 "orc_filter_tau": (C.c_int, [f64]),
-                "orc_budget_L": (i64, [C.c_int, i64, C.c_int, C.c_int, u64, C.c_int]),
+                "orc_budget_L": (i64, [C.c_int, i64, C.c_int, C.c_int, u64, C.c_int, C.c_int]),
                 "orc_sim": (C.c_float, [vp, vp, C.c_int]),
                 "orc_search": (None, [vp, vp, vp, vp, i64, vp, vp, i32, vp, C.c_int, vp, vp, vp, vp, i64, vp]),
                 "orc_brute_force": (None, [vp, i64, C.c_int, vp, i64, C.c_int, vp, vp]),
@@ -207,9 +207,17 @@ def filter_tau(s_k: float) -> int:
     return int(lib().orc_filter_tau(s_k))
 
 
-def budget_L(family: int, n: int, d: int, M: int, budget_bytes: int, sketch_layout: int = 0) -> int:
-    """sketch_layout 0: a sketch per repetition entry; 1: M sketches per point."""
-    return int(lib().orc_budget_L(family, n, d, M, budget_bytes, sketch_layout))
+def budget_L(family: int, n: int, d: int, M: int, budget_bytes: int, sketch_layout: int = 0,
+             row_storage: int = 0) -> int:
+    """sketch_layout 0: a sketch per repetition entry; 1: M sketches per point.
+    row_storage 0: float32 rows; 1: binary16 rows."""
+    return int(lib().orc_budget_L(family, n, d, M, budget_bytes, sketch_layout, row_storage))
+
+
+def round_rows_f16(x: np.ndarray) -> np.ndarray:
+    """Normalised rows as stored in binary16 (round to nearest, ties to even),
+    read back exactly as float32."""
+    return np.ascontiguousarray(x, np.float32).astype(np.float16).astype(np.float32)
 
 
 def sim(q, x) -> np.float32:
@@ -233,18 +241,21 @@ class OracleIndex:
     """The whole index of Sec. 4, built step by step on the CPU."""
 
     def __init__(self, points, family: int, *, L: int | None = None, budget_bytes: int | None = None,
-                 seed: int = 0, M: int = 32, B: int = 12, cp_draws: int = 1000, sketch_layout: int = 0):
+                 seed: int = 0, M: int = 32, B: int = 12, cp_draws: int = 1000, sketch_layout: int = 0,
+                 row_storage: int = 0):
         points = _c(points, np.float32)
         self.n, self.d = points.shape
         self.family, self.seed, self.M, self.B = family, seed, M, B
         lay = layout(family, self.d)
         self.ell, self.F, self.Kb = lay["ell"], lay["F"], lay["Kb"]
         if L is None:
-            L = budget_L(family, self.n, self.d, M, int(budget_bytes), sketch_layout)
+            L = budget_L(family, self.n, self.d, M, int(budget_bytes), sketch_layout, row_storage)
         self.L = int(L)
         if self.L < 1:
             raise ValueError("memory budget too small for one repetition")
         self.x = normalize(points)
+        if row_storage == 1:  # the stored point is the binary16 rounding of the normalised row
+            self.x = round_rows_f16(self.x)
         self.A = gen_hash_params(seed, family, self.L, self.d)
         self.S = gen_sketch_params(seed, M, self.d)
         codes = hash_codes(family, self.A, self.x)

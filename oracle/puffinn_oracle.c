@@ -331,12 +331,15 @@ int orc_filter_tau(double s_k) {
  *             + R d' 8         hash rows (float32 + two bfloat16 halves),
  *               R = F * d' for CP (rows of a function padded to d'), 32 for HP
  *   L = floor((budget - fixed) / per_table). */
-int64_t orc_budget_L(int family, int64_t n, int d, int M, uint64_t budget_bytes, int sketch_layout) {
+int64_t orc_budget_L(int family, int64_t n, int d, int M, uint64_t budget_bytes, int sketch_layout,
+                     int row_storage) {
   int64_t dp = ((int64_t)d + 15) / 16 * 16;
   int F;
   orc_layout(family, d, NULL, &F, NULL, NULL);
   int64_t R = (family == ORC_CROSSPOLYTOPE) ? (int64_t)F * dp : 32;
-  int64_t fixed = n * dp * 6 + 64 * (int64_t)M * dp * 8 + (sketch_layout == 1 ? n * (int64_t)M * 8 : 0);
+  /* rows: float32 (4 B) or binary16 (2 B) per element, plus the bfloat16 copy (2 B) */
+  int64_t row_bytes = row_storage == 1 ? 4 : 6;
+  int64_t fixed = n * dp * row_bytes + 64 * (int64_t)M * dp * 8 + (sketch_layout == 1 ? n * (int64_t)M * 8 : 0);
   int64_t per_table = n * (sketch_layout == 1 ? 8 : 16) + (int64_t)((1 << ORC_PREFIX_BITS) + 1) * 4 + R * dp * 8;
   if ((int64_t)budget_bytes <= fixed) return 0;
   return ((int64_t)budget_bytes - fixed) / per_table;

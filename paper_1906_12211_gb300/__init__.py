@@ -26,7 +26,8 @@ STATUS = {0: "PF_OK", -1: "PF_ERR_INVALID_ARG", -2: "PF_ERR_BUDGET_TOO_SMALL", -
           -4: "PF_ERR_CUDA", -5: "PF_ERR_DEVICE_TIMEOUT", -6: "PF_ERR_NOT_TRAINED"}
 
 ARRAYS = {"rows_f32": 0, "rows_bf16": 1, "codes": 2, "ids": 3, "prefix": 4, "sketches": 5, "hash_rows": 6,
-          "cp_table": 7, "table_sketches": 8}
+          "cp_table": 7, "table_sketches": 8, "rows_f16": 9}
+ROW_STORAGE = {"f32": 0, "f16": 1}
 SKETCH_LAYOUTS = {"table": 0, "point": 1}
 
 
@@ -34,7 +35,7 @@ class BuildParams(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("dtype", C.c_int32), ("family", C.c_int32),
                 ("num_sketches", C.c_int32), ("memory_budget_bytes", C.c_uint64), ("seed", C.c_uint64),
                 ("segment_B", C.c_int32), ("cp_draws", C.c_int32), ("num_tables", C.c_int32),
-                ("sketch_layout", C.c_int32)]
+                ("sketch_layout", C.c_int32), ("row_storage", C.c_int32)]
 
 
 class SearchOpts(C.Structure):
@@ -56,8 +57,8 @@ STATS_DTYPE = np.dtype([("start_depth", np.int32), ("stop_depth", np.int32), ("r
 class IndexInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("d_pad", C.c_int32), ("family", C.c_int32),
                 ("L", C.c_int32), ("Kb", C.c_int32), ("ell", C.c_int32), ("fns", C.c_int32), ("M", C.c_int32),
-                ("B", C.c_int32), ("trained", C.c_int32), ("sketch_layout", C.c_int32), ("bytes_used", C.c_uint64),
-                ("budget_bytes", C.c_uint64)]
+                ("B", C.c_int32), ("trained", C.c_int32), ("sketch_layout", C.c_int32), ("row_storage", C.c_int32),
+                ("bytes_used", C.c_uint64), ("budget_bytes", C.c_uint64)]
 
 
 class LearnedReport(C.Structure):
@@ -177,12 +178,12 @@ class Index:
 
     def __init__(self, points, family="crosspolytope", *, budget_bytes: int = 0, num_tables: int = 0,
                  seed: int = 0, num_sketches: int = 32, segment_B: int = 12, cp_draws: int = 1000,
-                 sketch_layout: str = "table", stream=None):
+                 sketch_layout: str = "table", rows: str = "f32", stream=None):
         n, d = int(points.shape[0]), int(points.shape[1])
         p = BuildParams(n=n, d=d, dtype=0, family=_family(family), num_sketches=num_sketches,
                         memory_budget_bytes=int(budget_bytes), seed=int(seed), segment_B=segment_B,
                         cp_draws=cp_draws, num_tables=int(num_tables),
-                        sketch_layout=SKETCH_LAYOUTS[sketch_layout])
+                        sketch_layout=SKETCH_LAYOUTS[sketch_layout], row_storage=ROW_STORAGE[rows])
         self._points_keepalive = points
         h = C.c_void_p()
         _check(lib().pf_index_build(C.byref(p), _ptr(points), C.byref(h), _stream_ptr(stream)))
@@ -191,7 +192,7 @@ class Index:
         inf = IndexInfo()
         _check(lib().pf_index_info(self._h, C.byref(inf)))
         self.info = {f: getattr(inf, f) for f, _ in IndexInfo._fields_}
-        for key in ("n", "d", "d_pad", "L", "Kb", "ell", "fns", "M", "B", "sketch_layout"):
+        for key in ("n", "d", "d_pad", "L", "Kb", "ell", "fns", "M", "B", "sketch_layout", "row_storage"):
             setattr(self, key, self.info[key])
         self.family = self.info["family"]
 

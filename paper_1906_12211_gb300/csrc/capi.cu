@@ -145,6 +145,7 @@ void destroy(pf_index* ix) {
   cudaGetDevice(&prev);
   cudaSetDevice(ix->device);
   dfree(ix->x32);
+  dfree(ix->xf16);
   dfree(ix->x16);
   dfree(ix->sk);
   dfree(ix->skc);
@@ -244,9 +245,11 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
     if (draws < 1) return fail(PF_ERR_INVALID_ARG, "cp_draws must be >= 1");
     if (prm->sketch_layout != PF_SKETCH_PER_TABLE && prm->sketch_layout != PF_SKETCH_PER_POINT)
       return fail(PF_ERR_INVALID_ARG, "unknown sketch layout");
+    if (prm->row_storage != PF_ROWS_F32 && prm->row_storage != PF_ROWS_F16)
+      return fail(PF_ERR_INVALID_ARG, "unknown row storage");
     int64_t L = prm->num_tables > 0 ? prm->num_tables
                                     : budget_tables(prm->family, prm->n, prm->d, M, prm->memory_budget_bytes,
-                                                    prm->sketch_layout);
+                                                    prm->sketch_layout, prm->row_storage);
     if (L < 1) return fail(PF_ERR_BUDGET_TOO_SMALL, "memory budget leaves room for no repetition");
     if (L > kMaxL) L = kMaxL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -264,7 +267,8 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       ix->lay = make_layout(prm->family, prm->d);
       ix->budget = prm->memory_budget_bytes;
       ix->sketch_layout = prm->sketch_layout;
-      ix->bytes_used = resident_bytes(prm->family, prm->n, prm->d, M, ix->L, prm->sketch_layout);
+      ix->row_storage = prm->row_storage;
+      ix->bytes_used = resident_bytes(prm->family, prm->n, prm->d, M, ix->L, prm->sketch_layout, prm->row_storage);
       const int dp = ix->lay.d_pad;
       const int64_t n = ix->n;
       ix->hash_rows = int64_t(ix->L) * ix->lay.rows_table + 64LL * M;
@@ -273,7 +277,10 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       // accumulation error of both sums (each <= d_pad * 2^-24 * |q||x|)
       ix->bf16_err = float(std::ldexp(1.0, -8) * (1.0 + std::ldexp(1.0, -20)) + 2.2 * dp * std::ldexp(1.0, -24));
 
-      dalloc(&ix->x32, size_t(n) * dp);
+      if (ix->row_storage == PF_ROWS_F16)
+        dalloc(&ix->xf16, size_t(n) * dp);
+      else
+        dalloc(&ix->x32, size_t(n) * dp);
       dalloc(&ix->x16, size_t(n) * dp);
       if (ix->sketch_layout == PF_SKETCH_PER_POINT)
         dalloc(&ix->sk, size_t(n) * M);
@@ -321,6 +328,7 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       RecheckReq* rq = nullptr;      // deferred float64 rechecks, only while hashing
       uint32_t* rq_count = nullptr;
       uint64_t* sk_tmp = nullptr;    // per-point sketches, only while building a per-table layout
+      float* x32_tmp = nullptr;      // float32 rows, only while hashing binary16 rows
       int32_t herr = 0;
       try {
         uint64_t* sk_out = ix->sk;
@@ -329,11 +337,18 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
           sk_out = sk_tmp;
         }
         dalloc(&xlo, size_t(n) * dp);
-        PF_CK(launch_normalize(pin, n, prm->d, dp, ix->x32, ix->x16, xlo, s));
+        float* x32 = ix->x32;
+        if (ix->row_storage == PF_ROWS_F16) {
+          dalloc(&x32_tmp, size_t(n) * dp);
+          x32 = x32_tmp;
+        }
+        PF_CK(launch_normalize(pin, n, prm->d, dp, x32, ix->x16, xlo, s));
+        if (ix->row_storage == PF_ROWS_F16)  // the stored point is the binary16 row: hash that
+          PF_CK(launch_round_rows_f16(x32, n, dp, ix->xf16, ix->x16, xlo, s));
         dalloc(&raw_codes, size_t(n) * ix->L);
         dalloc(&rq, recheck_capacity(n));
         dalloc(&rq_count, size_t(ix->num_sms));
-        PF_CK(launch_hash(ix, ix->x32, ix->x16, xlo, n, raw_codes, n, 1, sk_out, n, 1, rq, rq_count,
+        PF_CK(launch_hash(ix, x32, ix->x16, xlo, n, raw_codes, n, 1, sk_out, n, 1, rq, rq_count,
                           recheck_capacity(n), s));
         PF_CK(sort_tables(ix, raw_codes, s));
         if (ix->skc) PF_CK(gather_table_sketches(ix, sk_out, ix->skc, s));
@@ -347,6 +362,7 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
         dfree(rq);
         dfree(rq_count);
         dfree(sk_tmp);
+        dfree(x32_tmp);
         throw;
       }
       dfree(staged);
@@ -355,6 +371,7 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       dfree(rq);
       dfree(rq_count);
       dfree(sk_tmp);
+      dfree(x32_tmp);
       PF_CK(cudaGetLastError());
       if (herr) throw Error{PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait of the hashing kernel timed out"};
     } catch (...) {
@@ -490,6 +507,7 @@ pf_status pf_index_info(const pf_index* ix, pf_index_info_t* info) {
   info->B = ix->B;
   info->trained = ix->mlp_trained;
   info->sketch_layout = ix->sketch_layout;
+  info->row_storage = ix->row_storage;
   info->bytes_used = ix->bytes_used;
   info->budget_bytes = ix->budget;
   return PF_OK;
@@ -499,7 +517,16 @@ pf_status pf_index_array(const pf_index* ix, int32_t which, const void** ptr, ui
   if (!ix || !ptr || !bytes) return fail(PF_ERR_INVALID_ARG, "null argument");
   const uint64_t n = uint64_t(ix->n), dp = uint64_t(ix->lay.d_pad), L = uint64_t(ix->L);
   switch (which) {
-    case PF_ARRAY_ROWS_F32: *ptr = ix->x32; *bytes = n * dp * 4; break;
+    case PF_ARRAY_ROWS_F32:
+      if (!ix->x32) return fail(PF_ERR_INVALID_ARG, "index keeps its rows in binary16");
+      *ptr = ix->x32;
+      *bytes = n * dp * 4;
+      break;
+    case PF_ARRAY_ROWS_F16:
+      if (!ix->xf16) return fail(PF_ERR_INVALID_ARG, "index keeps its rows in float32");
+      *ptr = ix->xf16;
+      *bytes = n * dp * 2;
+      break;
     case PF_ARRAY_ROWS_BF16: *ptr = ix->x16; *bytes = n * dp * 2; break;
     case PF_ARRAY_CODES: *ptr = ix->codes; *bytes = n * L * 4; break;
     case PF_ARRAY_IDS: *ptr = ix->ids; *bytes = n * L * 4; break;

@@ -39,6 +39,26 @@ __global__ void normalize_kernel(const float* __restrict__ in, int64_t rows, int
   }
 }
 
+__global__ void round_rows_f16_kernel(float* __restrict__ x32, int64_t count, __half* __restrict__ xf16,
+                                      __nv_bfloat16* __restrict__ xh, __nv_bfloat16* __restrict__ xl) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x) {
+    const __half h = __float2half_rn(x32[i]);
+    const float y = __half2float(h);  // exact
+    x32[i] = y;
+    xf16[i] = h;
+    const __nv_bfloat16 b = __float2bfloat16_rn(y);
+    xh[i] = b;
+    if (xl) xl[i] = __float2bfloat16_rn(y - __bfloat162float(b));
+  }
+}
+
+cudaError_t launch_round_rows_f16(float* x32, int64_t rows, int d_pad, __half* xf16, __nv_bfloat16* xh,
+                                  __nv_bfloat16* xl, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  round_rows_f16_kernel<<<1024, 256, 0, s>>>(x32, rows * d_pad, xf16, xh, xl);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_normalize(const float* in, int64_t rows, int d, int d_pad, float* x32, __nv_bfloat16* xh,
                              __nv_bfloat16* xl, cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;

@@ -50,7 +50,8 @@ constexpr int kSub = 64;        // candidates per bfloat16 sub-batch (the prunin
 struct Dev {
   int n;
   int d, d_pad, L, Kb, M, B, family, ell;
-  const float* x32;
+  const float* x32;     // float32 rows, or null
+  const __half* xf16;   // binary16 rows (read back exactly as float32), or null
   const __nv_bfloat16* x16;
   const uint32_t* codes;
   const uint32_t* ids;
@@ -168,13 +169,21 @@ __device__ __forceinline__ int pq_offer(float* ps, uint32_t* pid, int size, int 
 // chunks g8, g8+8, ...); the loads of up to 4 chunks of both rows are issued
 // before their arithmetic.  Chunks wholly beyond the d coordinates (the zero
 // padding up to d') are neither read nor added.
+// four consecutive coordinates (chunk ch) of a float32 or a binary16 row
+__device__ __forceinline__ float4 row_chunk(const float* __restrict__ r32, const __half* __restrict__ r16, int ch) {
+  if (r32) return __ldg(reinterpret_cast<const float4*>(r32) + ch);
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(r16) + ch);
+  const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+  const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
 template <int NT>
 __device__ __forceinline__ void sim_canonical2(const float* __restrict__ q, const float* __restrict__ ra,
-                                               const float* __restrict__ rb, int d, int g8, unsigned gmask,
+                                               const float* __restrict__ rb, const __half* __restrict__ ha,
+                                               const __half* __restrict__ hb, int d, int g8, unsigned gmask,
                                                float& out_a, float& out_b) {
   const float4* q4 = reinterpret_cast<const float4*>(q);
-  const float4* a4 = reinterpret_cast<const float4*>(ra);
-  const float4* b4 = reinterpret_cast<const float4*>(rb);
   constexpr int kBatch = NT < 4 ? NT : 4;  // chunks of both rows loaded before their arithmetic
   float4 sa = make_float4(0.f, 0.f, 0.f, 0.f), sb = sa;
 #pragma unroll
@@ -183,8 +192,8 @@ __device__ __forceinline__ void sim_canonical2(const float* __restrict__ q, cons
 #pragma unroll
     for (int t = 0; t < kBatch; ++t) {
       const int ch = g8 + 8 * (t0 + t);
-      va[t] = ch * 4 < d ? __ldg(a4 + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
-      vb[t] = ch * 4 < d ? __ldg(b4 + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+      va[t] = ch * 4 < d ? row_chunk(ra, ha, ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+      vb[t] = ch * 4 < d ? row_chunk(rb, hb, ch) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
     for (int t = 0; t < kBatch; ++t) {
@@ -275,7 +284,11 @@ __device__ __forceinline__ int canonical_and_offer(const Dev& P, const float* q,
     const uint32_t ida = ca < cnt ? cbuf[ca] : cbuf[c0];
     const uint32_t idb = cb < cnt ? cbuf[cb] : cbuf[c0];
     float sa, sb;
-    sim_canonical2<NT>(q, P.x32 + size_t(ida) * P.d_pad, P.x32 + size_t(idb) * P.d_pad, P.d, g8, gmask, sa, sb);
+    const size_t oa = size_t(ida) * P.d_pad, ob = size_t(idb) * P.d_pad;
+    if (P.x32)
+      sim_canonical2<NT>(q, P.x32 + oa, P.x32 + ob, nullptr, nullptr, P.d, g8, gmask, sa, sb);
+    else
+      sim_canonical2<NT>(q, nullptr, nullptr, P.xf16 + oa, P.xf16 + ob, P.d, g8, gmask, sa, sb);
     const int m = min(8, cnt - c0);
     for (int t = 0; t < m; ++t) {
       const int src = (t & 3) * 8;
@@ -686,6 +699,7 @@ cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t 
   P.family = ix->family;
   P.ell = ix->lay.ell;
   P.x32 = ix->x32;
+  P.xf16 = ix->xf16;
   P.x16 = ix->x16;
   P.codes = ix->codes;
   P.ids = ix->ids;

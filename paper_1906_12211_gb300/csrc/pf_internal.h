@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -47,8 +48,8 @@ float gaussian(uint64_t seed, uint32_t purpose, uint32_t a, uint32_t b, uint32_t
 void gen_hash_rows(uint64_t seed, int family, int L, int M, int d, const Layout& lay, float* W, float* thr);
 void cp_collision_table(uint64_t seed, int d, int ell, int draws, double* P /*[41][ell+1]*/);
 void filter_cos_table(double* c /*[65]*/);
-int64_t budget_tables(int family, int64_t n, int d, int M, uint64_t budget, int sketch_layout);
-uint64_t resident_bytes(int family, int64_t n, int d, int M, int L, int sketch_layout);
+int64_t budget_tables(int family, int64_t n, int d, int M, uint64_t budget, int sketch_layout, int row_storage);
+uint64_t resident_bytes(int family, int64_t n, int d, int M, int L, int sketch_layout, int row_storage);
 
 // A hash decision the tensor-core kernel leaves to the float64 fix-up pass.
 struct RecheckReq {
@@ -97,7 +98,9 @@ struct pf_index {
   uint64_t budget = 0, bytes_used = 0;
   int64_t hash_rows = 0;  // L*rows_table + 64*M
   // resident device arrays
-  float* x32 = nullptr;            // [n][d_pad]
+  float* x32 = nullptr;            // [n][d_pad] (float32 rows; null with binary16 rows)
+  __half* xf16 = nullptr;          // [n][d_pad] (binary16 rows; null with float32 rows)
+  int row_storage = PF_ROWS_F32;
   __nv_bfloat16* x16 = nullptr;    // [n][d_pad]
   uint64_t* sk = nullptr;          // [M][n] (per-point layout)
   uint64_t* skc = nullptr;         // [L][n] sketch j mod M of the point at each position (per-table layout)
@@ -129,6 +132,11 @@ struct pf_index {
 // ---------------------------------------------------------------- launchers
 namespace pf {
 
+// round normalised rows x32 [rows][d_pad] in place to binary16 (nearest, ties to
+// even), keep the binary16 copy, and redo the bfloat16 split xh + xl (xl may be
+// null) of the rounded rows
+cudaError_t launch_round_rows_f16(float* x32, int64_t rows, int d_pad, __half* xf16, __nv_bfloat16* xh,
+                                  __nv_bfloat16* xl, cudaStream_t s);
 // normalise rows (Sec. 4.2) -> x32 [rows][d_pad], and optionally its bfloat16
 // split x32 = xh + xl (xh is the round-to-nearest bfloat16 copy)
 cudaError_t launch_normalize(const float* in, int64_t rows, int d, int d_pad, float* x32, __nv_bfloat16* xh,

@@ -45,16 +45,16 @@ def oracle_rows_from_lib(ix, W):
 
 
 class Case:
-    def __init__(self, orc, name, X, Q, family, L=None, budget=None, seed=0, B=12, layout="table"):
-        self.name, self.X, self.Q, self.layout = name, X, Q, layout
-        kw = dict(seed=seed, segment_B=B, sketch_layout=layout)
+    def __init__(self, orc, name, X, Q, family, L=None, budget=None, seed=0, B=12, layout="table", rows="f32"):
+        self.name, self.X, self.Q, self.layout, self.rows = name, X, Q, layout, rows
+        kw = dict(seed=seed, segment_B=B, sketch_layout=layout, rows=rows)
         if budget is not None:
             kw["budget_bytes"] = budget
         else:
             kw["num_tables"] = L
         self.gpu = gpu_index(X, family, **kw)
         fam = orc.SIMHASH if family == "simhash" else orc.CROSSPOLYTOPE
-        self.orc = orc.OracleIndex(X, fam, L=self.gpu.L, seed=seed, B=B)
+        self.orc = orc.OracleIndex(X, fam, L=self.gpu.L, seed=seed, B=B, row_storage=1 if rows == "f16" else 0)
         self.qd = torch.from_numpy(Q).to(DEV)
 
 
@@ -115,7 +115,33 @@ def hpodd(orc):
     return Case(orc, "gauss-n2500-d20", X, Q, "simhash", L=7, seed=2)
 
 
-CASES = ["cfg1", "cpmid", "cpodd", "cpwide", "hpodd", "cfg1pp", "cpmidpp"]
+@pytest.fixture(scope="module")
+def cfg1h(orc):
+    # config 1 with binary16 rows (the stored points are the rounded rows), 32 MiB
+    X, Q = datagen.make("gauss-n10k-d64", seed=0)
+    c = Case(orc, "gauss-n10k-d64-f16", X, Q, "simhash", budget=32 << 20, rows="f16")
+    assert c.gpu.L == orc.budget_L(orc.SIMHASH, 10_000, 64, 32, 32 << 20, 0, 1)
+    assert c.gpu.L > orc.budget_L(orc.SIMHASH, 10_000, 64, 32, 32 << 20, 0, 0)  # rows take less of the budget
+    return c
+
+
+@pytest.fixture(scope="module")
+def cpmidh(orc):
+    # the vMF case (d = 96 as in the 10M-point workload) with binary16 rows
+    X = datagen.vmf_mixture(20_000, 96, 50, 100.0, seed=8)
+    Q = datagen.vmf_mixture(150, 96, 50, 100.0, seed=8, purpose="queries")
+    return Case(orc, "vmf-n20k-d96-f16", X, Q, "crosspolytope", L=40, seed=5, rows="f16")
+
+
+@pytest.fixture(scope="module")
+def cpwideh(orc):
+    # d = 150 (float32 SIMT hashing of the rounded rows) with binary16 rows
+    X = datagen.vmf_mixture(3000, 150, 20, 40.0, seed=5)
+    Q = datagen.vmf_mixture(40, 150, 20, 40.0, seed=5, purpose="queries")
+    return Case(orc, "vmf-n3000-d150-f16", X, Q, "crosspolytope", L=12, seed=4, rows="f16")
+
+
+CASES = ["cfg1", "cpmid", "cpodd", "cpwide", "hpodd", "cfg1pp", "cpmidpp", "cfg1h", "cpmidh", "cpwideh"]
 
 
 @pytest.fixture
@@ -140,7 +166,14 @@ def test_parameters_bit_equal(case):
 @pytest.mark.parametrize("case", CASES, indirect=True)
 def test_normalised_rows_bit_exact(case):
     ix = case.gpu
-    x = ix.array("rows_f32").cpu().numpy().view(np.float32).reshape(ix.n, ix.d_pad)
+    if case.rows == "f16":
+        h = ix.array("rows_f16").cpu().numpy().view(np.float16).reshape(ix.n, ix.d_pad)
+        assert np.array_equal(h[:, : ix.d].view(np.uint16), case.orc.x.astype(np.float16).view(np.uint16))
+        x = h.astype(np.float32)
+        with pytest.raises(pf.PuffinnError):
+            ix.array("rows_f32")
+    else:
+        x = ix.array("rows_f32").cpu().numpy().view(np.float32).reshape(ix.n, ix.d_pad)
     assert np.array_equal(x[:, : ix.d], case.orc.x)
     assert np.all(x[:, ix.d:] == 0)
     xb = ix.array("rows_bf16").view(torch.bfloat16).reshape(ix.n, ix.d_pad)

@@ -263,6 +263,29 @@ def test_budget_formula_values(orc):
     assert orc.budget_L(orc.SIMHASH, 10_000, 64, 32, 1 << 20, 0) == 0
 
 
+def test_budget_with_binary16_rows(orc):
+    # the 10M x 96 workload with binary16 rows (2 B) + the bfloat16 copy (2 B), 40 GiB, a sketch per entry
+    n, d, M = 10_000_000, 96, 32
+    dp, R = 96, 4 * 96  # CP with l = ceil(log2 192) = 8: 4 functions of 96 rows
+    fixed = n * dp * 4 + 64 * M * dp * 8
+    per_table = n * 16 + 8193 * 4 + R * dp * 8
+    want = ((40 << 30) - fixed) // per_table
+    assert want == 243
+    assert orc.budget_L(orc.CROSSPOLYTOPE, n, d, M, 40 << 30, 0, 1) == want
+    # float32 rows leave room for fewer repetitions
+    assert orc.budget_L(orc.CROSSPOLYTOPE, n, d, M, 40 << 30, 0, 0) == ((40 << 30) - fixed - n * dp * 2) // per_table
+
+
+def test_binary16_rows_round_to_nearest_even(orc):
+    # binary16 has 10 fraction bits: at 1 the spacing is 2^-10, so 1 + 2^-11 and
+    # 1 + 3*2^-11 are ties that go to the even neighbours 1 and 1 + 2^-9
+    x = np.array([[1 + 2.0 ** -11, 1 + 3 * 2.0 ** -11, 1 + 2.0 ** -12, -0.1, 6.1e-5]], np.float32)
+    got = orc.round_rows_f16(x)[0]
+    assert got[0] == 1.0 and got[1] == np.float32(1 + 2.0 ** -9) and got[2] == 1.0
+    assert got[3] == np.float32(np.float16(-0.1)) and abs(got[3] + 0.1) <= 2.0 ** -14
+    assert got[4] == np.float32(np.float16(6.1e-5))  # the subnormal range is kept (no flush to zero)
+
+
 # ------------------------------------------------------------ similarity
 def test_canonical_sim(orc):
     e = np.zeros(100, np.float32)
