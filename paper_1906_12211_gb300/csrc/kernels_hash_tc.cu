@@ -15,24 +15,29 @@
 // sign and index of the largest |<a_c,x>|), so codes are bit-identical to the
 // float64 definition.
 //
-// Kernel structure (one CTA of 6 warps per SM, persistent, warp-specialised):
-//   - a unit of work is (128-point tile, segment); a segment is one
+// Kernel structure (one CTA of 10 warps per SM, persistent, warp-specialised):
+//   - a unit of work is (pair of 128-point tiles, segment); a segment is one
 //     repetition (CP: fns tiles of d_pad rows; HP: a group of 4 repetitions =
 //     128 rows) or a group of 2 sketches (128 rows); CTA b takes the
-//     contiguous units [b*U/G, (b+1)*U/G) of the U = tiles*segments, so the
+//     contiguous units [b*U/G, (b+1)*U/G) of the U = pairs*segments, so the
 //     CTAs' shares differ by at most one segment and each CTA loads the A
-//     tiles of only the one or two point tiles its range touches;
-//   - warp 0 (one thread) is the TMA producer: the A tile (Xh, Xl of the 128
-//     points) once per run of segments, then for every N tile its B operand as
-//     2*KB boxes of 64 columns (Wh and Wl per K block) into a ring of 8
-//     shared-memory stages; all tiles are K-major with the 128-byte swizzle;
+//     tiles of only the one or two pairs its range touches.  Both point tiles
+//     of a pair are multiplied by every B tile the CTA loads, which halves
+//     the B stream from L2 (the operand that bounds the kernel);
+//   - warp 0 (one thread) is the TMA producer: the A tiles (Xh, Xl of the 256
+//     points, 128 KB for d_pad <= 128) once per run of segments, then for
+//     every N tile its B operand as 2*KB boxes of 64 columns (Wh and Wl per K
+//     block) into a ring of shared-memory stages (as many as fit beside the A
+//     tiles, at most 8); all tiles are K-major with the 128-byte swizzle;
 //   - warp 1 owns the tensor memory and (one thread) issues the MMAs: per K
-//     block, Xh*Wh and Xl*Wh from the Wh stage and Xh*Wl from the Wl stage, into
-//     one of four 128-column accumulators (all 512 columns, so the epilogue
-//     warps can drift up to three tiles apart); tcgen05.commit frees each
+//     block and point tile, Xh*Wh and Xl*Wh from the Wh stage and Xh*Wl from
+//     the Wl stage, into the point tile's 128-column accumulator of one of two
+//     buffers (2 buffers x 2 point tiles = all 512 columns, so the epilogue
+//     of one N tile overlaps the MMAs of the next); tcgen05.commit frees each
 //     stage and publishes each finished accumulator;
-//   - warps 2-5 are the epilogue (one thread per point, tcgen05.ld of its lane)
-//     and hand each accumulator back through an mbarrier; for a CP function
+//   - warps 2-5 (point tile 0) and 6-9 (point tile 1) are the epilogue (one
+//     thread per point, tcgen05.ld of its lane quarter = warp % 4) and hand
+//     each accumulator back through an mbarrier; for a CP function
 //     the thread keeps the three largest |v| as integer sort keys in four
 //     independent chains (no branches); a decision closer to its boundary than
 //     the band is queued, with the top two rows as the candidates (or "all
@@ -52,11 +57,12 @@ namespace pf {
 namespace {
 
 constexpr int kBM = 128;          // points per tile (MMA M)
-constexpr int kThreads = 192;     // producer warp, MMA warp, 4 epilogue warps
+constexpr int kPair = 2;          // point tiles per work unit: they share every B tile
+constexpr int kThreads = 32 * (2 + 4 * kPair);  // producer warp, MMA warp, 4 epilogue warps per point tile
 constexpr int kTileBytes = kBM * 128;  // one 64-element K block of 128 rows
-constexpr int kStages = 8;        // B ring
-constexpr int kAcc = 4;           // accumulators of 128 columns (the whole tensor memory)
-constexpr int kTmemCols = 128 * kAcc;
+constexpr int kMaxStages = 8;     // B ring (fewer when the A tiles leave less shared memory)
+constexpr int kSmemLimit = 232448;     // shared memory a CTA may use
+constexpr int kTmemCols = 512;    // [2 buffers][kPair point tiles] accumulators of 128 columns
 constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait polls per bounded wait
 
 struct HashArgs {
@@ -72,7 +78,8 @@ struct HashArgs {
   int d, d_pad, KB, family, L, M, fns, ell, rows_table;
   int seg_tables;  // segments that are repetitions (CP) or groups of 4 repetitions (HP)
   int segs;        // + sketch groups of 2
-  int64_t units;   // point tiles * segs; CTA b takes units [b*units/grid, (b+1)*units/grid)
+  int64_t units;   // point-tile pairs * segs; CTA b takes units [b*units/grid, (b+1)*units/grid)
+  int stages;      // B ring stages
   uint32_t* codes;
   int64_t cj, cp;
   uint64_t* sk;
@@ -304,17 +311,18 @@ __device__ __forceinline__ Tile tile_of(const HashArgs& A, int seg, int f) {
   return t;
 }
 
-// A run of consecutive segments of one point tile within the CTA's units.
+// A run of consecutive segments of one pair of point tiles (2*pair, 2*pair+1)
+// within the CTA's units.
 struct Chunk {
-  int mt, seg0, seg1;
+  int pair, seg0, seg1;
 };
 
 __device__ __forceinline__ bool next_chunk(const HashArgs& A, int64_t& u, int64_t hi, Chunk& c) {
   if (u >= hi) return false;
-  c.mt = int(u / A.segs);
-  c.seg0 = int(u - int64_t(c.mt) * A.segs);
-  c.seg1 = int(min(hi - int64_t(c.mt) * A.segs, int64_t(A.segs)));
-  u = int64_t(c.mt) * A.segs + c.seg1;
+  c.pair = int(u / A.segs);
+  c.seg0 = int(u - int64_t(c.pair) * A.segs);
+  c.seg1 = int(min(hi - int64_t(c.pair) * A.segs, int64_t(A.segs)));
+  u = int64_t(c.pair) * A.segs + c.seg1;
   return true;
 }
 
@@ -558,24 +566,27 @@ struct TensorMaps {
 __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const __grid_constant__ TensorMaps T) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int KB = A.KB;
-  const uint32_t sA = smem_u32(base);                       // [2 splits][KB] tiles
-  const uint32_t sB = sA + uint32_t(2 * KB * kTileBytes);   // [kStages] tiles
-  __shared__ __align__(8) uint64_t bfull[kStages], bempty[kStages], accfull[kAcc], accempty[kAcc], afull, aempty;
+  const int KB = A.KB, S = A.stages;
+  const uint32_t a_bytes = uint32_t(2 * KB * kTileBytes);      // Xh, Xl of one point tile
+  const uint32_t sA = smem_u32(base);                          // [kPair][2 splits][KB] tiles
+  const uint32_t sB = sA + uint32_t(kPair) * a_bytes;          // [S] tiles
+  __shared__ __align__(8) uint64_t bfull[kMaxStages], bempty[kMaxStages], accfull[2][kPair], accempty[2][kPair],
+      afull, aempty;
   __shared__ uint32_t s_count;  // entries reserved in this CTA's region of the request queue
   __shared__ uint32_t tmem_base_slot;
   __shared__ volatile int failed;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
-    for (int u = 0; u < kStages; ++u) {
+    for (int u = 0; u < S; ++u) {
       mbar_init(smem_u32(&bfull[u]), 1);
       mbar_init(smem_u32(&bempty[u]), 1);
     }
-    for (int b = 0; b < kAcc; ++b) {
-      mbar_init(smem_u32(&accfull[b]), 1);
-      mbar_init(smem_u32(&accempty[b]), 128);
-    }
+    for (int b = 0; b < 2; ++b)
+      for (int pt = 0; pt < kPair; ++pt) {
+        mbar_init(smem_u32(&accfull[b][pt]), 1);
+        mbar_init(smem_u32(&accempty[b][pt]), 128);
+      }
     mbar_init(smem_u32(&afull), 1);
     mbar_init(smem_u32(&aempty), 1);
     failed = 0;
@@ -599,12 +610,15 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
     int64_t u = u_lo;
     Chunk ch;
     while (next_chunk(A, u, u_hi, ch)) {
-      const int mt = ch.mt, seg0 = ch.seg0, seg1 = ch.seg1;
+      const int seg0 = ch.seg0, seg1 = ch.seg1;
       if (items_done > 0 && !mbar_wait(smem_u32(&aempty), (items_done - 1) & 1)) { failed = 1; break; }
-      mbar_expect_tx(smem_u32(&afull), uint32_t(2 * KB * kTileBytes));
-      for (int kb = 0; kb < KB; ++kb) {
-        tma_load_2d(sA + uint32_t(kb * kTileBytes), &T.xh, kb * 64, mt * kBM, smem_u32(&afull));
-        tma_load_2d(sA + uint32_t((KB + kb) * kTileBytes), &T.xl, kb * 64, mt * kBM, smem_u32(&afull));
+      mbar_expect_tx(smem_u32(&afull), uint32_t(kPair) * a_bytes);
+      for (int pt = 0; pt < kPair; ++pt) {
+        const int row = (ch.pair * kPair + pt) * kBM;  // rows beyond the points read as zero
+        for (int kb = 0; kb < KB; ++kb) {
+          tma_load_2d(sA + pt * a_bytes + uint32_t(kb * kTileBytes), &T.xh, kb * 64, row, smem_u32(&afull));
+          tma_load_2d(sA + pt * a_bytes + uint32_t((KB + kb) * kTileBytes), &T.xl, kb * 64, row, smem_u32(&afull));
+        }
       }
       ++items_done;
       bool bad = false;
@@ -615,7 +629,7 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
           const CUtensorMap* mh = fn_tile ? &T.wh_f : &T.wh_g;
           const CUtensorMap* ml = fn_tile ? &T.wl_f : &T.wl_g;
           for (int u = 0; u < 2 * KB; ++u, ++stage) {
-            const uint32_t slot = stage % kStages, round = stage / kStages;
+            const uint32_t slot = stage % S, round = stage / S;
             if (!mbar_wait(smem_u32(&bempty[slot]), (round & 1) ^ 1)) { bad = true; break; }
             mbar_expect_tx(smem_u32(&bfull[slot]), uint32_t(t.rows * 128));
             tma_load_2d(sB + slot * kTileBytes, (u & 1) ? ml : mh, (u >> 1) * 64, int(t.row0), smem_u32(&bfull[slot]));
@@ -624,7 +638,7 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
       if (bad) { failed = 1; break; }
     }
   } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
+    // ---------------- MMA issuer: both point tiles of the pair from every B stage
     uint32_t stage = 0, items_done = 0, g = 0;
     int64_t u = u_lo;
     Chunk ch;
@@ -637,54 +651,57 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
       for (int seg = seg0; seg < seg1 && !bad; ++seg)
         for (int f = 0; f < tiles_in_seg(A, seg) && !bad; ++f, ++g) {
           const Tile t = tile_of(A, seg, f);
-          const uint32_t b = g % kAcc;
-          if (!mbar_wait(smem_u32(&accempty[b]), ((g / kAcc) & 1) ^ 1)) { bad = true; break; }
+          const uint32_t b = g & 1;
+          for (int pt = 0; pt < kPair && !bad; ++pt)
+            if (!mbar_wait(smem_u32(&accempty[b][pt]), ((g >> 1) & 1) ^ 1)) bad = true;
+          if (bad) break;
           tc_fence_after();
           const uint32_t idesc = idesc_bf16(kBM, t.rows);
-          const uint32_t d_tmem = tmem + b * 128;
-          uint32_t acc = 0;
           for (int u = 0; u < 2 * KB; ++u, ++stage) {
-            const uint32_t slot = stage % kStages, round = stage / kStages;
+            const uint32_t slot = stage % S, round = stage / S;
             if (!mbar_wait(smem_u32(&bfull[slot]), round & 1)) { bad = true; break; }
             tc_fence_after();
             const int kb = u >> 1;
             const uint32_t bt = sB + slot * kTileBytes;
-            // Wh stage: Xh*Wh and Xl*Wh; Wl stage: Xh*Wl
-            for (int half = 0; half < ((u & 1) ? 1 : 2); ++half) {
-              const uint32_t at = sA + uint32_t(((half ? KB : 0) + kb) * kTileBytes);
-              for (int kk = 0; kk < 4; ++kk) {
-                mma_bf16(d_tmem, sw128_desc(at + kk * 32), sw128_desc(bt + kk * 32), idesc, acc);
-                acc = 1;
+            for (int pt = 0; pt < kPair; ++pt) {
+              const uint32_t d_tmem = tmem + (b * kPair + pt) * 128;
+              // Wh stage: Xh*Wh and Xl*Wh; Wl stage: Xh*Wl
+              for (int half = 0; half < ((u & 1) ? 1 : 2); ++half) {
+                const uint32_t at = sA + pt * a_bytes + uint32_t(((half ? KB : 0) + kb) * kTileBytes);
+                for (int kk = 0; kk < 4; ++kk)
+                  mma_bf16(d_tmem, sw128_desc(at + kk * 32), sw128_desc(bt + kk * 32), idesc,
+                           (u | half | kk) ? 1u : 0u);
               }
             }
             mma_commit(smem_u32(&bempty[slot]));
           }
-          mma_commit(smem_u32(&accfull[b]));
+          for (int pt = 0; pt < kPair; ++pt) mma_commit(smem_u32(&accfull[b][pt]));
         }
       mma_commit(smem_u32(&aempty));
       if (bad) { failed = 1; break; }
     }
   } else if (warp >= 2) {
-    // ---------------- epilogue: thread = point, TMEM lane quarter = warp % 4
-    const int quarter = warp & 3;
+    // ---------------- epilogue: group pt (warps 2-5: point tile 0, 6-9: point tile 1),
+    // thread = point, TMEM lane quarter = warp % 4
+    const int pt = (warp - 2) >> 2, quarter = warp & 3;
     uint32_t g = 0;
     int64_t u = u_lo;
     Chunk ch;
     while (!failed && next_chunk(A, u, u_hi, ch)) {
-      const int mt = ch.mt, seg0 = ch.seg0, seg1 = ch.seg1;
-      const int64_t p = int64_t(mt) * kBM + quarter * 32 + lane;
+      const int seg0 = ch.seg0, seg1 = ch.seg1;
+      const int64_t p = int64_t(ch.pair * kPair + pt) * kBM + quarter * 32 + lane;
       EpiState st;
       st.code = 0;
       bool bad = false;
       for (int seg = seg0; seg < seg1 && !bad; ++seg)
         for (int f = 0; f < tiles_in_seg(A, seg) && !bad; ++f, ++g) {
           const Tile t = tile_of(A, seg, f);
-          const uint32_t b = g % kAcc;
-          if (!mbar_wait(smem_u32(&accfull[b]), (g / kAcc) & 1)) { bad = true; break; }
+          const uint32_t b = g & 1;
+          if (!mbar_wait(smem_u32(&accfull[b][pt]), (g >> 1) & 1)) { bad = true; break; }
           tc_fence_after();
-          epilogue(A, t, tmem + (uint32_t(quarter * 32) << 16) + b * 128, p, st, &s_count);
+          epilogue(A, t, tmem + (uint32_t(quarter * 32) << 16) + (b * kPair + pt) * 128, p, st, &s_count);
           tc_fence_before();
-          mbar_arrive(smem_u32(&accempty[b]));
+          mbar_arrive(smem_u32(&accempty[b][pt]));
         }
       if (bad) { failed = 1; break; }
     }
@@ -981,9 +998,16 @@ __global__ void recheck_kernel(HashArgs A, int blocks_per_region) {
 
 bool hash_tc_supported(const pf_index* ix) { return ix->lay.d_pad <= 128; }
 
+int hash_tc_stages(int d_pad) {
+  const int KB = (d_pad + 63) / 64;
+  // the static barriers (padded to 1 KB) and the 1 KB alignment slack
+  const int left = kSmemLimit - 2048 - kPair * 2 * KB * kTileBytes;
+  return std::min(kMaxStages, left / kTileBytes);
+}
+
 size_t hash_tc_smem(int d_pad) {
   const int KB = (d_pad + 63) / 64;
-  return size_t(2 * KB + kStages) * kTileBytes + 1024;
+  return size_t(kPair * 2 * KB + hash_tc_stages(d_pad)) * kTileBytes + 1024;
 }
 
 namespace {
@@ -1047,7 +1071,8 @@ cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __
   A.seg_tables = ix->family == PF_CROSSPOLYTOPE ? ix->L : (ix->L + 3) / 4;
   A.segs = A.seg_tables + (ix->M + 1) / 2;
   const int64_t mtiles = (npts + kBM - 1) / kBM;
-  A.units = mtiles * A.segs;
+  A.units = (mtiles + kPair - 1) / kPair * A.segs;
+  A.stages = hash_tc_stages(A.d_pad);
   A.codes = codes;
   A.cj = cj;
   A.cp = cp;
