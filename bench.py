@@ -130,9 +130,14 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def search_kernel_traffic():
+def search_kernel_traffic(args=None):
     """Per-launch DRAM bytes of the search kernel from the committed ncu summary,
-    valid only while the kernel source is the one that was profiled."""
+    valid only while the kernel source is the one that was profiled and for the
+    workload it was taken on (the default one: learned start, bf16 scoring)."""
+    if args is not None and (args.points is not None or args.queries is not None or args.budget is not None
+                             or args.mode != "learned" or args.train_queries != 100_000 or args.epochs != 20
+                             or args.recall != 0.9):
+        return None
     path = os.path.join(ROOT, "profiles", "search_kernel_traffic.txt")
     src = os.path.join(ROOT, "paper_1906_12211_gb300", "csrc", "kernels_search.cu")
     if not os.path.exists(path):
@@ -424,7 +429,7 @@ def main():
     per_q = algorithmic_bytes(stats, ix.L, ix.n, ix.d, k, "fp32" if args.mode == "fp32" else "bf16")
     kern_s = kernel_ms / args.steps / 1e3
     achieved = per_q * Q / kern_s / 1e9
-    traffic = search_kernel_traffic()
+    traffic = search_kernel_traffic(args)
     roofline = {"bound": "hbm", "kernel": "search_kernel", "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "algorithmic_bytes_per_launch": per_q * Q, "kernel_ms": kern_s * 1e3,

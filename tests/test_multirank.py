@@ -78,3 +78,20 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["value"] == d["value"]
+
+
+def test_traffic_summary_only_for_the_profiled_workload():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    base = dict(points=None, queries=None, budget=None, mode="learned", train_queries=100_000, epochs=20, recall=0.9)
+    import argparse
+
+    for key, other in (("points", 5000), ("queries", 100), ("budget", 1 << 30), ("mode", "bf16"),
+                       ("train_queries", 20_000), ("epochs", 5), ("recall", 0.95)):
+        a = argparse.Namespace(**dict(base, **{key: other}))
+        assert bench.search_kernel_traffic(a) is None, key
+    # the default workload gets the committed figure while the source is unchanged
+    # (or None once the kernel differs from the profiled one)
+    v = bench.search_kernel_traffic(argparse.Namespace(**base))
+    assert v is None or v > 1e10
