@@ -92,25 +92,37 @@ __device__ __forceinline__ double ipow(double x, int e) {
 
 // probability that a point at similarity s collides with the query on the
 // first `depth` bits of one repetition (Sec. 4.3)
-__device__ __noinline__ double collision_prob(const Dev& P, double s, int depth) {
+// s_k: a k-th similarity (float32).  alpha_up[u]: the grid value (5u - 100)/100
+// (a float64 division) rounded up to float32, so that alpha <= s_k exactly when
+// alpha_up <= s_k; the grid point is the largest u with alpha <= s_k (or 0).
+// The grid search runs in float32: the float64 pipe of sm_103 is narrow.
+__device__ __noinline__ double collision_prob(const Dev& P, const float* alpha_up, float s_k, int depth) {
   if (P.family == PF_SIMHASH) {
+    const double s = double(s_k);
     const double sc = s > 1.0 ? 1.0 : (s < -1.0 ? -1.0 : s);
     const double p = 1.0 - acos(sc) / M_PI;
     return ipow(p, depth);
   }
   int t = 0;
   for (int u = 0; u < kAlphaSteps; ++u)
-    if (double(5 * u - 100) / 100.0 <= s) t = u;
+    if (alpha_up[u] <= s_k) t = u;
   const double* row = P.cpP + t * (P.ell + 1);
   return __dmul_rn(ipow(row[P.ell], depth / P.ell), row[depth % P.ell]);
 }
 
-__device__ __forceinline__ int filter_tau(const Dev& P, float s_k) {
-  int tau = 0;
-  const double s = double(s_k);
-  for (int t = 0; t <= 64; ++t)
-    if (P.cos_tab[t] >= s) tau = t;
-  return tau;
+// The largest t in [0, 64] with cos(t pi / 64) >= s_k (0 if none), from the
+// table cosf[t] = the float64 cos(t pi / 64) rounded down to float32: for a
+// float32 s_k, c >= s_k holds exactly when round_down(c) >= s_k, and the table
+// does not increase, so a binary search for the first t with cosf[t] < s_k
+// gives the same t as a scan of the float64 table (every thread computes it at
+// every snapshot, and float64 compares are slow on sm_103).
+__device__ __forceinline__ int filter_tau(const float* cosf, float s_k) {
+  int lo = 0, hi = 65;  // first t with !(cosf[t] >= s_k) lies in [lo, hi]
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (cosf[mid] >= s_k) lo = mid + 1; else hi = mid;
+  }
+  return lo > 0 ? lo - 1 : 0;
 }
 
 __device__ __forceinline__ bool prefix_match(uint32_t a, uint32_t b, uint32_t mask) { return ((a ^ b) & mask) == 0; }
@@ -370,10 +382,15 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
   uint32_t* my_id = wid + warp * kmax;
   __shared__ int s_qi, s_size, s_stop, s_wsize[kQW];
   __shared__ uint32_t s_scan[kQW];
+  __shared__ float s_cosf[65];
+  __shared__ float s_alpha[kAlphaSteps];
   __shared__ uint32_t s_ct[kQW][4];
   const uint32_t n = uint32_t(P.n);
   const uint32_t lt_mask = (1u << lane) - 1u;
   const int per = (L + kThreads - 1) / kThreads;  // repetitions per thread in the range pass
+  for (int t = tid; t < 65; t += kThreads) s_cosf[t] = __double2float_rd(P.cos_tab[t]);
+  for (int u = tid; u < kAlphaSteps; u += kThreads) s_alpha[u] = __double2float_ru(double(5 * u - 100) / 100.0);
+  __syncthreads();
 
   for (;;) {
     if (tid == 0) s_qi = atomicAdd(P.counter, 1);
@@ -557,7 +574,7 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
         // threshold snapshot: every earlier candidate is in the merged top-k
         const int gsize = s_size;
         const float gkth = gsize == k ? gs[k - 1] : -INFINITY;
-        const int tau = gsize == k ? filter_tau(P, gkth) : 64;
+        const int tau = gsize == k ? filter_tau(s_cosf, gkth) : 64;
         const uint32_t c_end = cpre[j1];
         int jc = j0;
         uint64_t qh = qsk[j0 % M];  // the query's sketch for repetition jc
@@ -641,7 +658,7 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(Dev P) {
       if (tid == 0) {
         int stop = 0;
         if (size == k) {
-          const double p = collision_prob(P, double(gs[k - 1]), depth);
+          const double p = collision_prob(P, s_alpha, gs[k - 1], depth);
           const double fail = ipow(__dsub_rn(1.0, p), L);
           stop = fail <= delta ? 1 : 0;
         }
