@@ -314,6 +314,19 @@ pf_status pf_search_plan_check(pf_search_plan* plan, void* stream);
 /* Release a plan (NULL is accepted). */
 void pf_search_plan_free(pf_search_plan* plan);
 
+/* ---- Diagnostics of the bounded device-side waits ----
+ * Every wait of the tensor-core hashing kernel (Sec. 2.2 hashing of the
+ * queries) on one of its pipeline barriers gives up after 1 s, records an
+ * error word and leaves the kernel; the call that launched it then returns
+ * PF_ERR_DEVICE_TIMEOUT and clears the word, and the index stays usable.
+ * This call hashes the Q queries (host or device, [Q][d] float32) with the
+ * kernel's weight-tile loads withheld, so that the waits on them expire (about
+ * 1 s), and returns what the library reports for it: PF_ERR_DEVICE_TIMEOUT
+ * when the time-out path works.  No output is written.  Errors:
+ * PF_ERR_INVALID_ARG (null argument, Q < 1, an index hashed without the
+ * tensor-core kernel (d' > 128), or search plans bound to the index), CUDA. */
+pf_status pf_index_selftest_timeout(pf_index* index, const float* queries, int64_t Q, void* stream);
+
 /* Release an index (NULL is accepted).  Does nothing while search plans bound
  * to it exist (pf_last_error_message says so). */
 void pf_index_free(pf_index* index);

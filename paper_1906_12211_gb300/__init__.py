@@ -117,6 +117,7 @@ def lib():
                 "pf_search_opts_default": (None, [vp]),
                 "pf_index_free": (None, [vp]),
                 "pf_index_tune": (i32, [vp, vp, i64, i32, C.c_double, vp, vp, vp]),
+                "pf_index_selftest_timeout": (i32, [vp, vp, i64, vp]),
                 "pf_search_plan_create": (i32, [vp, i64, i32, vp, vp, vp]),
                 "pf_search_plan_run": (i32, [vp, vp]),
                 "pf_search_plan_check": (i32, [vp, vp]),
@@ -316,6 +317,11 @@ class Index:
         _check(lib().pf_index_tune(self._h, _ptr(queries), int(queries.shape[0]), int(k), float(recall),
                                    C.byref(o), C.byref(rep), _stream_ptr(stream)))
         return {f: getattr(rep, f) for f, _ in TuneReport._fields_}
+
+    def selftest_timeout(self, queries, stream=None):
+        """pf_index_selftest_timeout: hash with the weight loads withheld; raises
+        PuffinnError(PF_ERR_DEVICE_TIMEOUT) when the bounded waits work."""
+        _check(lib().pf_index_selftest_timeout(self._h, _ptr(queries), int(queries.shape[0]), _stream_ptr(stream)))
 
     def plan(self, queries, k, recall, out_ids, out_sims, *, k_max: int, stats=None, start_depth=None,
              scoring: str = "fp32", filter: bool = True, learned: bool = False):

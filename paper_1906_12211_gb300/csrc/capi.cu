@@ -197,6 +197,16 @@ const float* stage_queries(pf_index* ix, const float* queries, int64_t Q, cudaSt
   return ix->ws.qraw;
 }
 
+// After the stream has been synchronised: did a bounded device-side wait give
+// up since the last check?  The error word is cleared, so the index stays
+// usable (a call's outputs are its own; the index itself is not written).
+bool device_timed_out(pf_index* ix) {
+  int32_t herr = 0;
+  PF_CK(cudaMemcpy(&herr, ix->dev_error, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (herr) PF_CK(cudaMemset(ix->dev_error, 0, sizeof(int32_t)));
+  return herr != 0;
+}
+
 }  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
@@ -399,6 +409,7 @@ pf_status pf_hash_queries(pf_index* ix, const float* queries, int64_t Q, uint32_
     PF_CK(cudaMemcpyAsync(qsk, ix->ws.qsk, sizeof(uint64_t) * size_t(Q) * ix->M, cudaMemcpyDefault, s));
     PF_CK(cudaStreamSynchronize(s));
     PF_CK(cudaGetLastError());
+    if (device_timed_out(ix)) return fail(PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out");
     return PF_OK;
   });
 }
@@ -473,9 +484,7 @@ pf_status pf_index_search(pf_index* ix, const float* queries, int64_t Q, const i
     PF_CK(cudaMemcpyAsync(&flags, ws.counter + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     PF_CK(cudaStreamSynchronize(s));
     PF_CK(cudaGetLastError());
-    int32_t herr = 0;
-    PF_CK(cudaMemcpy(&herr, ix->dev_error, sizeof(int32_t), cudaMemcpyDeviceToHost));
-    if (herr) return fail(PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out");
+    if (device_timed_out(ix)) return fail(PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out");
     if (flags & 1) return fail(PF_ERR_INVALID_ARG, "some k not in [1, k_max] or recall not in (0, 1)");
     if (timing) {
       PF_CK(cudaEventElapsedTime(&ix->last_ms[0], ix->ev[0], ix->ev[1]));
@@ -662,6 +671,7 @@ pf_status pf_learned_train(pf_index* ix, const float* train_queries, int64_t Qt,
         PF_CK(cudaStreamSynchronize(s));
         for (int64_t i = 0; i < nq; ++i) hy[q0 + i] = st[i].stop_depth;
       }
+      if (device_timed_out(ix)) throw Error{PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out"};
       PF_CK(cudaMemcpyAsync(y, hy.data(), sizeof(int32_t) * Qt, cudaMemcpyHostToDevice, s));
       // weights: W1 ~ N(0, 2/F), W2 ~ N(0, 1/H), zero biases (host, from the seed)
       std::vector<float> hp(nparam, 0.f);
@@ -749,6 +759,7 @@ pf_status pf_learned_train(pf_index* ix, const float* train_queries, int64_t Qt,
             sum_stop += hy[q0 + i];
           }
         }
+        if (device_timed_out(ix)) throw Error{PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out"};
         report->final_loss = last_loss;
         report->train_accuracy = float(double(covered) / double(Qt));
         report->mean_stop = float(sum_stop / double(Qt));
@@ -781,6 +792,31 @@ pf_status pf_learned_predict(pf_index* ix, const float* queries, int64_t Q, int3
     predict_ws(ix, ix->ws, Q, s);
     PF_CK(cudaMemcpyAsync(start_depth, ix->ws.start, sizeof(int32_t) * size_t(Q), cudaMemcpyDefault, s));
     PF_CK(cudaStreamSynchronize(s));
+    if (device_timed_out(ix)) return fail(PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out");
+    return PF_OK;
+  });
+}
+
+pf_status pf_index_selftest_timeout(pf_index* ix, const float* queries, int64_t Q, void* stream) {
+  return guarded([&]() -> pf_status {
+    if (!ix || !queries) return fail(PF_ERR_INVALID_ARG, "null argument");
+    if (Q < 1 || Q > 0x7fffffffLL) return fail(PF_ERR_INVALID_ARG, "Q out of range");
+    if (!hash_tc_supported(ix)) return fail(PF_ERR_INVALID_ARG, "this index hashes without the tensor-core kernel");
+    if (ix->live_plans > 0) return fail(PF_ERR_INVALID_ARG, "search plans bound to the index exist");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PF_CK(cudaSetDevice(ix->device));
+    ensure_ws(ix, Q, 1);
+    const float* qd = stage_queries(ix, queries, Q, s);
+    struct Hold {
+      pf_index* ix;
+      ~Hold() { ix->hold_weight_loads = 0; }
+    } hold{ix};
+    ix->hold_weight_loads = 1;
+    hash_queries_ws(ix, ix->ws, qd, Q, s);
+    PF_CK(cudaStreamSynchronize(s));
+    ix->hold_weight_loads = 0;
+    PF_CK(cudaGetLastError());
+    if (device_timed_out(ix)) return fail(PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out");
     return PF_OK;
   });
 }
@@ -882,6 +918,7 @@ pf_status pf_index_tune(pf_index* ix, const float* queries, int64_t Q, int32_t k
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (device_timed_out(ix)) return fail(PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out");
     ix->search_shape = pick;
     if (report) {
       report->unroll = pick.unroll;
@@ -1018,10 +1055,9 @@ pf_status pf_search_plan_check(pf_search_plan* pl, void* stream) {
     if (!pl) return fail(PF_ERR_INVALID_ARG, "null plan");
     PF_CK(cudaSetDevice(pl->ix->device));
     PF_CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
-    int32_t flags = 0, herr = 0;
+    int32_t flags = 0;
     PF_CK(cudaMemcpy(&flags, pl->ws.counter + 1, sizeof(int32_t), cudaMemcpyDeviceToHost));
-    PF_CK(cudaMemcpy(&herr, pl->ix->dev_error, sizeof(int32_t), cudaMemcpyDeviceToHost));
-    if (herr) return fail(PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out");
+    if (device_timed_out(pl->ix)) return fail(PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out");
     if (flags & 1) return fail(PF_ERR_INVALID_ARG, "some k not in [1, k_max] or recall not in (0, 1)");
     return PF_OK;
   });

@@ -63,7 +63,9 @@ constexpr int kTileBytes = kBM * 128;  // one 64-element K block of 128 rows
 constexpr int kMaxStages = 8;     // B ring (fewer when the A tiles leave less shared memory)
 constexpr int kSmemLimit = 232448;     // shared memory a CTA may use
 constexpr int kTmemCols = 512;    // [2 buffers][kPair point tiles] accumulators of 128 columns
-constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait polls per bounded wait
+constexpr uint32_t kSuspendNs = 5000;        // longest sleep of one try_wait
+constexpr uint64_t kWaitNs = 1000000000ull;  // a bounded wait gives up after 1 s
+constexpr uint32_t kWaitPolls = 1u << 26;    // ... or after this many polls
 
 struct HashArgs {
   const __nv_bfloat16* xh;
@@ -80,6 +82,7 @@ struct HashArgs {
   int segs;        // + sketch groups of 2
   int64_t units;   // point-tile pairs * segs; CTA b takes units [b*units/grid, (b+1)*units/grid)
   int stages;      // B ring stages
+  int hold_b;      // diagnostics: issue no B loads, so that the waits on them expire
   uint32_t* codes;
   int64_t cj, cp;
   uint64_t* sk;
@@ -98,24 +101,38 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
 }
 
+// one poll; a thread whose phase is not complete may sleep up to kSuspendNs
+// (woken early when the phase completes), so idle roles do not spin on the
+// issue slots the epilogue needs
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n"
       " .reg .pred p;\n"
-      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n"
       "}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
 
-// bounded wait for the phase with the given parity; false on time-out
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bounded wait for the phase with the given parity: false once kWaitNs have
+// passed (or after kWaitPolls polls, whichever comes first)
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it)
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < kWaitPolls; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
   return false;
 }
 
@@ -621,6 +638,7 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
         }
       }
       ++items_done;
+      if (A.hold_b) break;  // the MMA and epilogue roles time out (the A loads above complete)
       bool bad = false;
       for (int seg = seg0; seg < seg1 && !bad; ++seg)
         for (int f = 0; f < tiles_in_seg(A, seg) && !bad; ++f) {
@@ -1073,6 +1091,7 @@ cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __
   const int64_t mtiles = (npts + kBM - 1) / kBM;
   A.units = (mtiles + kPair - 1) / kPair * A.segs;
   A.stages = hash_tc_stages(A.d_pad);
+  A.hold_b = ix->hold_weight_loads;
   A.codes = codes;
   A.cj = cj;
   A.cp = cp;
