@@ -13,7 +13,7 @@ from __future__ import annotations
 import numpy as np
 
 _PURPOSE = {"points": 11, "queries": 12, "centres": 13, "kappa": 14, "mix": 15,
-            "planted": 16, "train": 17, "params": 18, "tune": 19}
+            "planted": 16, "train": 17, "params": 18, "tune": 19, "queries2": 20}
 
 
 def _rng(seed: int, purpose: str) -> np.random.Generator:
