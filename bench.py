@@ -44,7 +44,14 @@ sys.path.insert(0, ROOT)
 import datagen  # noqa: E402
 
 WORKLOAD = "vmf1k-n1m-d100"
-METRIC = "k-NN queries/s at recall>=0.9 (n=1M, d=100, k=10)"
+METRICS = {
+    "vmf1k-n1m-d100": "k-NN queries/s at recall>=0.9 (n=1M, d=100, k=10)",
+    # Sec. 5 SYNTHETIC (n = 10^6, 300 dimensions, 1,000 queries, k = 10)
+    "paper-synthetic-n1m-d300": "k-NN queries/s, recall target 0.99 (paper SYNTHETIC: n=1M, 300 dims, k=10)",
+}
+METRIC = METRICS[WORKLOAD]
+# the paper's single-thread CPU figure on SYNTHETIC: 360.3 queries/s at recall 0.971 (Sec. 5, Fig. 7)
+PAPER_SYNTHETIC_QPS, PAPER_SYNTHETIC_RECALL = 360.3, 0.971
 UNIT = "queries/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB of L2
 CPU_SAMPLE_N = 20_000
@@ -62,7 +69,10 @@ def parse():
     ap.add_argument("--train-queries", type=int, default=100_000, help="training queries for the start-depth model")
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other two modes")
-    ap.add_argument("--recall", type=float, default=0.9, help="recall target 1 - delta passed to the index")
+    ap.add_argument("--recall", type=float, default=None,
+                    help="recall target 1 - delta passed to the index (default: the workload's)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(METRICS),
+                    help="vmf1k-n1m-d100 (default) or the paper's SYNTHETIC construction (Sec. 5)")
     ap.add_argument("--points", type=int, default=None, help="override the workload's number of points")
     ap.add_argument("--queries", type=int, default=None, help="override the number of queries per rank")
     ap.add_argument("--budget", type=int, default=None, help="index budget in bytes (default: the workload's)")
@@ -71,7 +81,10 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape of the search kernel")
     ap.add_argument("--no-graph", action="store_true",
                     help="skip the captured (CUDA graph) searches: the headline is then the sequential step")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.recall is None:
+        args.recall = datagen.WORKLOADS[args.workload]["recall"]
+    return args
 
 
 # ---------------------------------------------------------------- clocks
@@ -142,7 +155,7 @@ def search_kernel_traffic(args=None):
     workload it was taken on (the default one: learned start, bf16 scoring)."""
     if args is not None and (args.points is not None or args.queries is not None or args.budget is not None
                              or args.mode != "learned" or args.train_queries != 100_000 or args.epochs != 20
-                             or args.recall != 0.9):
+                             or args.recall != 0.9 or getattr(args, "workload", WORKLOAD) != WORKLOAD):
         return None
     path = os.path.join(ROOT, "profiles", "search_kernel_traffic.txt")
     src = os.path.join(ROOT, "paper_1906_12211_gb300", "csrc", "kernels_search.cu")
@@ -163,15 +176,35 @@ def search_kernel_traffic(args=None):
 
 
 # ---------------------------------------------------------------- workload
-def workload(rank: int, n_override=None, q_override=None, budget=None):
-    w = dict(datagen.WORKLOADS[WORKLOAD])
+def workload(rank: int, n_override=None, q_override=None, budget=None, name=WORKLOAD):
+    """(workload dict, points, this rank's queries).  The points are the same on
+    every rank; each rank draws its own query batch from the same distribution."""
+    w = dict(datagen.WORKLOADS[name])
+    w["name"] = name
     if budget is not None:
         w["budget"] = int(budget)
     n = w["n"] if n_override is None else n_override
     Q = w["Q"] if q_override is None else q_override
-    X = datagen.vmf_mixture(n, w["d"], w["components"], w["kappa"], seed=0, purpose="points")
-    Qs = datagen.vmf_mixture(Q, w["d"], w["components"], w["kappa"], seed=rank, purpose="queries")
-    return w, X, Qs
+    if name == "paper-synthetic-n1m-d300":
+        X = datagen.paper_synthetic_points(n, w["block"], seed=0)
+    else:
+        X = datagen.vmf_mixture(n, w["d"], w["components"], w["kappa"], seed=0, purpose="points")
+    return w, X, queries(w, Q, "queries", rank)
+
+
+def queries(w, m: int, purpose: str, rank: int):
+    """m queries of the workload w for one purpose (queries, queries2, train, tune)."""
+    if w["name"] == "paper-synthetic-n1m-d300":
+        return datagen.paper_synthetic_queries(m, w["block"], seed=0, purpose=purpose, stream=rank)
+    return datagen.vmf_mixture(m, w["d"], w["components"], w["kappa"], seed=0, purpose=purpose, stream=rank)
+
+
+def cpu_sample_points(w, X):
+    """The points the CPU oracle indexes: the first CPU_SAMPLE_N (SYNTHETIC: the
+    first CPU_SAMPLE_N - 1 and its last point, every query's neighbour)."""
+    if w["name"] == "paper-synthetic-n1m-d300":
+        return np.concatenate([X[:CPU_SAMPLE_N - 1], X[-1:]])
+    return X[:CPU_SAMPLE_N]
 
 
 def max_over_ranks(seconds: float, dist=None, device=None) -> float:
@@ -221,12 +254,12 @@ def algorithmic_bytes(st, L, n, d, k, mode):
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_sample(X, Qs, L, k, recall, q_target_s=2.0):
-    """Oracle index over the first CPU_SAMPLE_N points of the same data with the
+def oracle_sample(w, X, Qs, L, k, recall, q_target_s=2.0):
+    """Oracle index over a CPU_SAMPLE_N-point sample of the same data with the
     same number of repetitions; returns (index, queries, query count per step)."""
     import oracle
 
-    oix = oracle.OracleIndex(X[:CPU_SAMPLE_N], oracle.CROSSPOLYTOPE, L=L, seed=0)
+    oix = oracle.OracleIndex(cpu_sample_points(w, X), oracle.CROSSPOLYTOPE, L=L, seed=0)
     t = time.perf_counter()
     oix.search(Qs[:64], k, recall)
     per_q = (time.perf_counter() - t) / 64
@@ -245,11 +278,11 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w, X, Qs = workload(0, args.points, args.queries, args.budget)
+    w, X, Qs = workload(0, args.points, args.queries, args.budget, args.workload)
     import oracle
 
     L = oracle.budget_L(oracle.CROSSPOLYTOPE, X.shape[0], X.shape[1], 32, w["budget"])
-    oix, nq = oracle_sample(X, Qs, L, w["k"], args.recall)
+    oix, nq = oracle_sample(w, X, Qs, L, w["k"], args.recall)
     for _ in range(args.warmup):
         oix.search(Qs[:nq], w["k"], args.recall)
     t = time.perf_counter()
@@ -257,13 +290,13 @@ def run_reference(args):
         oix.search(Qs[:nq], w["k"], args.recall)
     el = time.perf_counter() - t
     v = nq * args.steps / el
-    sample = (f"oracle index over the first {CPU_SAMPLE_N} of the {X.shape[0]} points (same data, L={L}, "
+    sample = (f"oracle index over a {CPU_SAMPLE_N}-point sample of the {X.shape[0]} points (same data, L={L}, "
               f"same seed), {nq} queries per step")
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "impl": "reference", "metric": METRICS[args.workload], "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": int(X.shape[0]), "d": int(X.shape[1]), "k": w["k"],
+        "config": {"workload": args.workload, "n": int(X.shape[0]), "d": int(X.shape[1]), "k": w["k"],
                    "recall_target": args.recall, "sample": sample},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -291,7 +324,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     pf.build()
     dev = torch.device("cuda", local)
-    w, X, Qs = workload(rank, args.points, args.queries, args.budget)
+    w, X, Qs = workload(rank, args.points, args.queries, args.budget, args.workload)
     Q, k = Qs.shape[0], w["k"]
     Xd = torch.from_numpy(X).to(dev)
     Qd = torch.from_numpy(Qs).to(dev)
@@ -312,8 +345,7 @@ def main():
 
     train_report, train_s = None, None
     if args.mode == "learned" or not args.no_compare:
-        Qtrain = datagen.vmf_mixture(args.train_queries, w["d"], w["components"], w["kappa"], seed=rank,
-                                     purpose="train")
+        Qtrain = queries(w, args.train_queries, "train", rank)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         train_report = ix.learned_train(torch.from_numpy(Qtrain).to(dev), k, args.recall, epochs=args.epochs,
@@ -325,7 +357,7 @@ def main():
     # same distribution (the tuner's choice changes no result)
     tune_report = None
     if not args.no_tune:
-        Qtune = datagen.vmf_mixture(Q, w["d"], w["components"], w["kappa"], seed=rank, purpose="tune")
+        Qtune = queries(w, Q, "tune", rank)
         tune_report = ix.tune(torch.from_numpy(Qtune).to(dev), k, args.recall,
                               scoring="fp32" if args.mode == "fp32" else "bf16", learned=args.mode == "learned")
 
@@ -393,7 +425,7 @@ def main():
     pipe, clk_pipe, plans = None, None, None
     sc, lr = ("fp32" if args.mode == "fp32" else "bf16"), args.mode == "learned"
     if not args.no_graph:
-        Qs2 = datagen.vmf_mixture(Q, w["d"], w["components"], w["kappa"], seed=rank, purpose="queries2")
+        Qs2 = queries(w, Q, "queries2", rank)
         qdev = [Qd, torch.from_numpy(Qs2).to(dev)]
         kdev = [kq, kq.clone()]
         rdev = [rq, rq.clone()]
@@ -494,33 +526,38 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        oix, nq = oracle_sample(X, Qs, ix.L, k, args.recall, q_target_s=15.0)
+        oix, nq = oracle_sample(w, X, Qs, ix.L, k, args.recall, q_target_s=15.0)
         t = time.perf_counter()
         oix.search(Qs[:nq], k, args.recall)
         el = time.perf_counter() - t
         cpu = {"value": nq / el, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"oracle index over the first {CPU_SAMPLE_N} of {ix.n} points (same data and seed, "
+               "sample": f"oracle index over a {CPU_SAMPLE_N}-point sample of the {ix.n} points (same data and seed, "
                          f"L={ix.L}); {nq} queries; all host cores"}
 
     sequential = {"value": value, "ms_per_step": t_max / args.steps * 1e3,
                   "l2": "flushed between steps (512 MiB write)", "clocks": clk}
     if pipe:
         value, ms_step, clk = pipe["value"], pipe["ms_per_step"], clk_pipe
-        l2 = ("inputs larger than L2 (4 GiB index streamed every step; two different 10,000-query batches "
-              "alternate)")
+        l2 = (f"inputs larger than L2 ({w['budget'] / 2**30:.0f} GiB index streamed every step; two different "
+              f"{Q:,}-query batches alternate)")
         pipelining = "two batches in flight: two captured plans (CUDA graphs) alternating on two streams"
     else:
         ms_step = t_max / args.steps * 1e3
         l2 = "flushed between steps (512 MiB write)"
         pipelining = "none: one batch at a time"
+    # the paper's figure exists for SYNTHETIC only (a single-thread CPU at recall
+    # 0.971): the ratio is given when the measured recall reaches it
+    vs_baseline = None
+    if args.workload == "paper-synthetic-n1m-d300" and recall >= PAPER_SYNTHETIC_RECALL:
+        vs_baseline = value / PAPER_SYNTHETIC_QPS
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": METRICS[args.workload], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.mode == "fp32" else "bf16+f32",
+            "scaling": "weak", "vs_baseline": vs_baseline, "dtype": "f32" if args.mode == "fp32" else "bf16+f32",
             "mode": args.mode,
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": ix.n, "d": ix.d, "queries_per_gpu": Q, "k": k,
+            "config": {"workload": args.workload, "n": ix.n, "d": ix.d, "queries_per_gpu": Q, "k": k,
                        "recall_target": args.recall, "family": "crosspolytope", "budget_bytes": w["budget"],
                        "L": ix.L, "scoring": "fp32" if args.mode == "fp32" else "bf16",
                        "start_depth": "learned" if args.mode == "learned" else "plain",

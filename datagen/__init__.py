@@ -16,8 +16,11 @@ _PURPOSE = {"points": 11, "queries": 12, "centres": 13, "kappa": 14, "mix": 15,
             "planted": 16, "train": 17, "params": 18, "tune": 19, "queries2": 20}
 
 
-def _rng(seed: int, purpose: str) -> np.random.Generator:
-    return np.random.Generator(np.random.Philox(np.random.SeedSequence([int(seed), _PURPOSE[purpose]])))
+def _rng(seed: int, purpose: str, stream: int = 0) -> np.random.Generator:
+    """Stream 0 is the default stream of (seed, purpose); other streams give
+    independent draws of the same distribution (e.g. one query batch per rank)."""
+    words = [int(seed), _PURPOSE[purpose]] + ([int(stream)] if stream else [])
+    return np.random.Generator(np.random.Philox(np.random.SeedSequence(words)))
 
 
 def gaussian(n: int, d: int, seed: int = 0, purpose: str = "points") -> np.ndarray:
@@ -52,11 +55,11 @@ def _vmf_w(rng: np.random.Generator, kappa: np.ndarray, d: int) -> np.ndarray:
 
 
 def vmf_mixture(n: int, d: int, components: int, kappa, seed: int = 0, purpose: str = "points",
-                chunk: int = 1 << 18) -> np.ndarray:
+                chunk: int = 1 << 18, stream: int = 0) -> np.ndarray:
     """Unit vectors from an equal-weight mixture of von Mises-Fisher
     distributions; centres are normalised N(0, I) draws (shared by all
-    purposes of one seed).  kappa: a scalar, or a (lo, hi) pair for a per-
-    component concentration drawn uniformly from [lo, hi]."""
+    purposes and streams of one seed).  kappa: a scalar, or a (lo, hi) pair for
+    a per-component concentration drawn uniformly from [lo, hi]."""
     crng = _rng(seed, "centres")
     centres = crng.standard_normal((components, d))
     centres /= np.linalg.norm(centres, axis=1, keepdims=True)
@@ -65,7 +68,7 @@ def vmf_mixture(n: int, d: int, components: int, kappa, seed: int = 0, purpose: 
     else:
         lo, hi = kappa
         kap = _rng(seed, "kappa").uniform(lo, hi, size=components)
-    rng = _rng(seed, purpose)
+    rng = _rng(seed, purpose, stream)
     out = np.empty((n, d), np.float32)
     for s in range(0, n, chunk):
         e = min(n, s + chunk)
@@ -106,27 +109,39 @@ def planted(n_background: int, d: int, n_queries: int, c_nn: float = 0.8, n_deco
     return pts, q.astype(np.float32), nn
 
 
-def paper_synthetic(n: int, d: int, m: int, seed: int = 0):
-    """The SYNTHETIC construction of Sec. 5 (dimension 3d): points
-    (0, y_i, z_i) with N(0, 1/(2d)) coordinates, one point (v, w, 0), queries
-    (v, 0, r_i) with |r_i| = sqrt(1/2).  Returns (points, queries); the last
-    point is every query's nearest neighbour in expectation."""
+def _synthetic_vw(d: int, seed: int):
+    s = np.sqrt(1.0 / (2 * d))
+    rng = _rng(seed, "centres")
+    return rng.normal(0, s, d), rng.normal(0, s, d)
+
+
+def paper_synthetic_points(n: int, d: int, seed: int = 0, chunk: int = 1 << 18) -> np.ndarray:
+    """Points of the SYNTHETIC construction of Sec. 5 (dimension 3d): n - 1
+    points (0, y_i, z_i) whose coordinates are N(0, 1/(2d)) draws, and as the
+    last point (v, w, 0) with v, w of the same law (expected squared length 1/2
+    each): the nearest neighbour, in expectation, of every query."""
     rng = _rng(seed, "points")
     s = np.sqrt(1.0 / (2 * d))
     pts = np.zeros((n, 3 * d), np.float32)
-    pts[: n - 1, d:2 * d] = rng.normal(0, s, (n - 1, d))
-    pts[: n - 1, 2 * d:] = rng.normal(0, s, (n - 1, d))
-    v = rng.normal(0, s, d)
-    w = rng.normal(0, s, d)
+    for a in range(0, n - 1, chunk):
+        e = min(n - 1, a + chunk)
+        pts[a:e, d:] = rng.normal(0, s, (e - a, 2 * d))
+    v, w = _synthetic_vw(d, seed)
     pts[n - 1, :d] = v
     pts[n - 1, d:2 * d] = w
-    qr = _rng(seed, "queries")
-    r = qr.standard_normal((m, d))
+    return pts
+
+
+def paper_synthetic_queries(m: int, d: int, seed: int = 0, purpose: str = "queries", stream: int = 0) -> np.ndarray:
+    """Queries of the SYNTHETIC construction of Sec. 5: (v, 0, r_i) with the v of
+    the last point and r_i uniform of length sqrt(1/2)."""
+    v, _ = _synthetic_vw(d, seed)
+    r = _rng(seed, purpose, stream).standard_normal((m, d))
     r *= np.sqrt(0.5) / np.linalg.norm(r, axis=1, keepdims=True)
     qs = np.zeros((m, 3 * d), np.float32)
     qs[:, :d] = v
     qs[:, 2 * d:] = r
-    return pts, qs
+    return qs
 
 
 def mixed_k_recall(Q: int, ks=(1, 10, 100), deltas=(0.5, 0.1, 0.01), seed: int = 0):
@@ -146,6 +161,9 @@ WORKLOADS = {
                              recall=0.95),
     "vmf4k-n2m-d128-mixed": dict(n=2_000_000, d=128, Q=100_000, family="crosspolytope", budget=8 << 30,
                                  components=4000, kappa=(20.0, 200.0)),
+    # Sec. 5 SYNTHETIC: n = 10^6, 3 x 100 dimensions, 1,000 queries
+    "paper-synthetic-n1m-d300": dict(n=1_000_000, d=300, Q=1000, family="crosspolytope", budget=8 << 30, k=10,
+                                     recall=0.99, block=100),
 }
 
 
@@ -159,6 +177,9 @@ def make(name: str, seed: int = 0, n: int | None = None, Q: int | None = None):
     if name.startswith("vmf"):
         return (vmf_mixture(n, w["d"], w["components"], w["kappa"], seed, "points"),
                 vmf_mixture(Q, w["d"], w["components"], w["kappa"], seed, "queries"))
+    if name == "paper-synthetic-n1m-d300":
+        return (paper_synthetic_points(n, w["block"], seed),
+                paper_synthetic_queries(Q, w["block"], seed))
     if name == "planted-n3m-d256":
         nb = max(0, n - Q * 2001)
         pts, qs, _ = planted(nb, w["d"], Q, seed=seed)

@@ -74,7 +74,7 @@ typedef enum {
  * zero means "default" for the optional fields. */
 typedef struct {
   int64_t n;                    /* number of points, >= 1 */
-  int32_t d;                    /* dimension, 1..256 */
+  int32_t d;                    /* dimension, 1..320 */
   int32_t dtype;                /* pf_dtype of `points` */
   int32_t family;               /* pf_family */
   int32_t num_sketches;         /* M 64-bit sketches per point (Sec. 4.2); 0 -> 32 */

@@ -243,7 +243,7 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
     if (!prm || !points || !out) return fail(PF_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
     if (prm->n < 1 || prm->n > 0x7fffffffLL) return fail(PF_ERR_INVALID_ARG, "n must be in [1, 2^31-1]");
-    if (prm->d < 1 || prm->d > kMaxD) return fail(PF_ERR_INVALID_ARG, "d must be in [1, 256]");
+    if (prm->d < 1 || prm->d > kMaxD) return fail(PF_ERR_INVALID_ARG, "d must be in [1, 320]");
     if (prm->dtype != PF_F32) return fail(PF_ERR_INVALID_ARG, "points must be float32");
     if (prm->family != PF_SIMHASH && prm->family != PF_CROSSPOLYTOPE)
       return fail(PF_ERR_INVALID_ARG, "unknown hash family");

@@ -71,7 +71,7 @@ cudaError_t launch_normalize(const float* in, int64_t rows, int d, int d_pad, fl
 // Hashing.  Each CTA takes 128 points (one per thread) and one group of hash
 // rows: a whole repetition (CP: fns functions of d_pad rows; HP: 32 rows) or
 // one 64-row sketch.  Projections are float32 fused multiply-adds; their error
-// is below d*2^-24*|a|*|x| (<= 2^-16 |a| for d <= 256), far inside the recheck
+// is below d*2^-24*|a|*|x| (<= 2^-15 |a| for d <= 320), far inside the recheck
 // band thr = 2^-12 |a|.  A decision closer to its boundary than the band is
 // recomputed in float64 in index order, which is the defining value:
 //   HP / sketch bit  = [<a, x> >= 0]
@@ -82,6 +82,7 @@ cudaError_t launch_normalize(const float* in, int64_t rows, int d, int d_pad, fl
 // ---------------------------------------------------------------------------
 constexpr int kHashPts = 128;
 constexpr int kHashChunk = 32;  // hash rows staged in shared memory at a time
+constexpr int kRowBlock = 8;    // rows whose projections a thread accumulates together
 
 __device__ __forceinline__ double dot64(const float* __restrict__ a, const float* __restrict__ x, int d) {
   double s = 0.0;
@@ -133,23 +134,27 @@ __global__ void __launch_bounds__(kHashPts) hash_simt_kernel(
     int rows_table, const float* __restrict__ W, const float* __restrict__ thr, uint32_t* __restrict__ codes,
     int64_t cj, int64_t cp, uint64_t* __restrict__ sk, int64_t sm, int64_t sp) {
   extern __shared__ float smem[];
-  float* xT = smem;                         // [d_pad][kHashPts]
-  float* wS = smem + d_pad * kHashPts;      // [kHashChunk][d_pad]
+  const int xs = d_pad + 4;                 // row stride: float4 reads of 8 lanes hit 32 distinct banks
+  float* xS = smem;                         // [kHashPts][d_pad + 4] this CTA's points
+  float* wS = smem + kHashPts * xs;         // [kHashChunk][d_pad] staged hash rows
   const int tid = threadIdx.x;
   const int64_t p0 = int64_t(blockIdx.x) * kHashPts;
   const int64_t p = p0 + tid;
   const int g = blockIdx.y;
   const bool is_table = g < L;
+  const int q4 = d_pad / 4;
 
-  for (int e = tid; e < d_pad * kHashPts; e += kHashPts) {
-    const int pt = e / d_pad, i = e % d_pad;
+  for (int e = tid; e < kHashPts * q4; e += kHashPts) {
+    const int pt = e / q4, i4 = e % q4;
     const int64_t pp = p0 + pt;
-    xT[i * kHashPts + pt] = pp < npts ? x32[pp * d_pad + i] : 0.f;
+    reinterpret_cast<float4*>(xS + pt * xs)[i4] =
+        pp < npts ? __ldg(reinterpret_cast<const float4*>(x32 + pp * d_pad) + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 
   const int64_t row0 = is_table ? int64_t(g) * rows_table : int64_t(L) * rows_table + int64_t(g - L) * 64;
   const int nrows = is_table ? rows_table : 64;
   const float* xrow = x32 + (p < npts ? p : 0) * d_pad;
+  const float4* xv4 = reinterpret_cast<const float4*>(xS + tid * xs);
 
   uint32_t code = 0;
   uint64_t bits = 0;
@@ -158,77 +163,92 @@ __global__ void __launch_bounds__(kHashPts) hash_simt_kernel(
   float best_v = 0.f;
   int fn = 0;
 
+  // the decision for row r of the group from its float32 projection v (rows in order)
+  auto row_done = [&](int r, float v) {
+    const int64_t grow = row0 + r;
+    if (!is_table || family == PF_SIMHASH) {
+      bool bit = v >= 0.f;
+      if (fabsf(v) < thr[grow] && p < npts) bit = dot64(W + grow * d_pad, xrow, d) >= 0.0;
+      if (is_table) {
+        code |= (bit ? 1u : 0u) << (31 - r);
+      } else if (bit) {
+        bits |= uint64_t(1) << r;
+      }
+      return;
+    }
+    const int c = r - fn * d_pad;
+    if (c < d) {
+      const float av = fabsf(v);
+      if (av > top.a[0]) best_v = v;
+      top.push(av, c);
+    }
+    if (c == d_pad - 1) {  // function complete
+      const float band = thr[grow];
+      int arg = top.c[0];
+      bool neg = best_v < 0.f;
+      if ((top.a[1] >= top.a[0] - 2.f * band || top.a[0] < band) && p < npts) {
+        const float* wf = W + (row0 + int64_t(fn) * d_pad) * d_pad;
+        double bestabs = -1.0, bestval = 0.0;
+        int besti = 0;
+        if (top.a[3] >= top.a[0] - 2.f * band) {
+          for (int cc = 0; cc < d; ++cc) {
+            const double v64 = dot64(wf + int64_t(cc) * d_pad, xrow, d);
+            if (fabs(v64) > bestabs) {
+              bestabs = fabs(v64);
+              bestval = v64;
+              besti = cc;
+            }
+          }
+        } else {
+          for (int t = 0; t < 4; ++t) {
+            if (top.a[t] < top.a[0] - 2.f * band) continue;
+            const int cc = top.c[t];
+            const double v64 = dot64(wf + int64_t(cc) * d_pad, xrow, d);
+            const double av = fabs(v64);
+            if (av > bestabs || (av == bestabs && cc < besti)) {
+              bestabs = av;
+              bestval = v64;
+              besti = cc;
+            }
+          }
+        }
+        arg = besti;
+        neg = bestval < 0.0;
+      }
+      const uint32_t value = ((neg ? 1u : 0u) << (ell - 1)) | uint32_t(arg);
+      code |= value << (32 - ell * (fn + 1));
+      ++fn;
+      top.reset();
+    }
+  };
+
+  // kRowBlock rows at a time: one float4 of the point and one (broadcast) of
+  // each row per step, 4 * kRowBlock fused multiply-adds.  Every chunk holds a
+  // multiple of kRowBlock rows (rows_table = fns * d_pad or 32, sketches 64).
   for (int r0 = 0; r0 < nrows; r0 += kHashChunk) {
     const int nr = min(kHashChunk, nrows - r0);
     __syncthreads();
-    for (int e = tid; e < nr * d_pad; e += kHashPts) wS[e] = W[(row0 + r0) * d_pad + e];
+    for (int e = tid; e < nr * q4; e += kHashPts)
+      reinterpret_cast<float4*>(wS)[e] = __ldg(reinterpret_cast<const float4*>(W + (row0 + r0) * d_pad) + e);
     __syncthreads();
-    for (int rr = 0; rr < nr; ++rr) {
-      const int r = r0 + rr;
-      const float* w = wS + rr * d_pad;
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      for (int i = 0; i < d_pad; i += 4) {
-        a0 = __fmaf_rn(w[i + 0], xT[(i + 0) * kHashPts + tid], a0);
-        a1 = __fmaf_rn(w[i + 1], xT[(i + 1) * kHashPts + tid], a1);
-        a2 = __fmaf_rn(w[i + 2], xT[(i + 2) * kHashPts + tid], a2);
-        a3 = __fmaf_rn(w[i + 3], xT[(i + 3) * kHashPts + tid], a3);
-      }
-      const float v = (a0 + a1) + (a2 + a3);
-      const int64_t grow = row0 + r;
-      if (!is_table || family == PF_SIMHASH) {
-        bool bit = v >= 0.f;
-        if (fabsf(v) < thr[grow] && p < npts) bit = dot64(W + grow * d_pad, xrow, d) >= 0.0;
-        if (is_table) {
-          code |= (bit ? 1u : 0u) << (31 - r);
-        } else if (bit) {
-          bits |= uint64_t(1) << r;
-        }
-      } else {
-        const int c = r - fn * d_pad;
-        if (c < d) {
-          const float av = fabsf(v);
-          if (av > top.a[0]) best_v = v;
-          top.push(av, c);
-        }
-        if (c == d_pad - 1) {  // function complete
-          const float band = thr[grow];
-          int arg = top.c[0];
-          bool neg = best_v < 0.f;
-          if ((top.a[1] >= top.a[0] - 2.f * band || top.a[0] < band) && p < npts) {
-            const float* wf = W + (row0 + int64_t(fn) * d_pad) * d_pad;
-            double bestabs = -1.0, bestval = 0.0;
-            int besti = 0;
-            if (top.a[3] >= top.a[0] - 2.f * band) {
-              for (int cc = 0; cc < d; ++cc) {
-                const double v64 = dot64(wf + int64_t(cc) * d_pad, xrow, d);
-                if (fabs(v64) > bestabs) {
-                  bestabs = fabs(v64);
-                  bestval = v64;
-                  besti = cc;
-                }
-              }
-            } else {
-              for (int t = 0; t < 4; ++t) {
-                if (top.a[t] < top.a[0] - 2.f * band) continue;
-                const int cc = top.c[t];
-                const double v64 = dot64(wf + int64_t(cc) * d_pad, xrow, d);
-                const double av = fabs(v64);
-                if (av > bestabs || (av == bestabs && cc < besti)) {
-                  bestabs = av;
-                  bestval = v64;
-                  besti = cc;
-                }
-              }
-            }
-            arg = besti;
-            neg = bestval < 0.0;
-          }
-          const uint32_t value = ((neg ? 1u : 0u) << (ell - 1)) | uint32_t(arg);
-          code |= value << (32 - ell * (fn + 1));
-          ++fn;
-          top.reset();
+    for (int rr = 0; rr < nr; rr += kRowBlock) {
+      float acc[kRowBlock];
+#pragma unroll
+      for (int q = 0; q < kRowBlock; ++q) acc[q] = 0.f;
+      const float4* w4 = reinterpret_cast<const float4*>(wS + rr * d_pad);
+      for (int i4 = 0; i4 < q4; ++i4) {
+        const float4 xv = xv4[i4];
+#pragma unroll
+        for (int q = 0; q < kRowBlock; ++q) {
+          const float4 wv = w4[q * q4 + i4];
+          acc[q] = __fmaf_rn(wv.x, xv.x, acc[q]);
+          acc[q] = __fmaf_rn(wv.y, xv.y, acc[q]);
+          acc[q] = __fmaf_rn(wv.z, xv.z, acc[q]);
+          acc[q] = __fmaf_rn(wv.w, xv.w, acc[q]);
         }
       }
+#pragma unroll
+      for (int q = 0; q < kRowBlock; ++q) row_done(r0 + rr + q, acc[q]);
     }
   }
   if (p < npts) {
@@ -246,7 +266,7 @@ cudaError_t launch_hash(const pf_index* ix, const float* x32, const __nv_bfloat1
   if (hash_tc_supported(ix) && xh && xl)
     return launch_hash_tc(ix, xh, xl, x32, npts, codes, cj, cp, sk, sm, sp, ix->dev_error, rq, rq_count, rq_cap, s);
   const Layout& lay = ix->lay;
-  const size_t smem = sizeof(float) * (size_t(lay.d_pad) * kHashPts + size_t(kHashChunk) * lay.d_pad);
+  const size_t smem = sizeof(float) * (size_t(lay.d_pad + 4) * kHashPts + size_t(kHashChunk) * lay.d_pad);
   cudaError_t e = cudaFuncSetAttribute(hash_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   dim3 grid(unsigned((npts + kHashPts - 1) / kHashPts), unsigned(ix->L + ix->M));

@@ -748,11 +748,17 @@ cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t 
   const int nt = (P.d_pad + 31) / 32;
   void (*kern)(Dev);
   if (U == 4)
-    kern = nt <= 1 ? search_kernel<1, 2, 4> : nt <= 2 ? search_kernel<2, 4, 4> : nt <= 4 ? search_kernel<4, 8, 4>
-                                                                                      : search_kernel<8, 16, 4>;
+    kern = nt <= 1   ? search_kernel<1, 2, 4>
+           : nt <= 2 ? search_kernel<2, 4, 4>
+           : nt <= 4 ? search_kernel<4, 8, 4>
+           : nt <= 8 ? search_kernel<8, 16, 4>
+                     : search_kernel<16, 32, 4>;
   else
-    kern = nt <= 1 ? search_kernel<1, 2, 8> : nt <= 2 ? search_kernel<2, 4, 8> : nt <= 4 ? search_kernel<4, 8, 8>
-                                                                                      : search_kernel<8, 16, 8>;
+    kern = nt <= 1   ? search_kernel<1, 2, 8>
+           : nt <= 2 ? search_kernel<2, 4, 8>
+           : nt <= 4 ? search_kernel<4, 8, 8>
+           : nt <= 8 ? search_kernel<8, 16, 8>
+                     : search_kernel<16, 32, 8>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -774,11 +780,17 @@ int search_max_ctas_per_sm(const pf_index* ix, int k_max, int unroll) {
   const int nt = (d_pad + 31) / 32;
   void (*kern)(Dev);
   if (U == 4)
-    kern = nt <= 1 ? search_kernel<1, 2, 4> : nt <= 2 ? search_kernel<2, 4, 4> : nt <= 4 ? search_kernel<4, 8, 4>
-                                                                                      : search_kernel<8, 16, 4>;
+    kern = nt <= 1   ? search_kernel<1, 2, 4>
+           : nt <= 2 ? search_kernel<2, 4, 4>
+           : nt <= 4 ? search_kernel<4, 8, 4>
+           : nt <= 8 ? search_kernel<8, 16, 4>
+                     : search_kernel<16, 32, 4>;
   else
-    kern = nt <= 1 ? search_kernel<1, 2, 8> : nt <= 2 ? search_kernel<2, 4, 8> : nt <= 4 ? search_kernel<4, 8, 8>
-                                                                                      : search_kernel<8, 16, 8>;
+    kern = nt <= 1   ? search_kernel<1, 2, 8>
+           : nt <= 2 ? search_kernel<2, 4, 8>
+           : nt <= 4 ? search_kernel<4, 8, 8>
+           : nt <= 8 ? search_kernel<8, 16, 8>
+                     : search_kernel<16, 32, 8>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) != cudaSuccess) return 0;

@@ -17,7 +17,7 @@ constexpr int kPrefixBits = 13;                     // Sec. 4.2: 13-bit prefix t
 constexpr int kPrefixSize = (1 << kPrefixBits) + 1;
 constexpr int kAlphaSteps = 41;                     // Sec. 4.3: similarity grid step 0.05
 constexpr int kMaxK = 128;
-constexpr int kMaxD = 256;
+constexpr int kMaxD = 320;
 constexpr int kMaxL = 2048;
 constexpr int kMlpHidden = 256;                     // start-depth model hidden units
 constexpr float kMlpTail = 0.05f;                   // quantile: P(stop depth > q) <= this

@@ -141,7 +141,25 @@ def cpwideh(orc):
     return Case(orc, "vmf-n3000-d150-f16", X, Q, "crosspolytope", L=12, seed=4, rows="f16")
 
 
-CASES = ["cfg1", "cpmid", "cpodd", "cpwide", "hpodd", "cfg1pp", "cpmidpp", "cfg1h", "cpmidh", "cpwideh"]
+@pytest.fixture(scope="module")
+def cpsyn(orc):
+    # the paper's SYNTHETIC construction (Sec. 5) at n = 3,000: 3 x 100 = 300
+    # dimensions (d_pad 304: SIMT hashing, CP with l = 10, three functions of 30 bits)
+    X = datagen.paper_synthetic_points(3000, 100, seed=2)
+    Q = datagen.paper_synthetic_queries(40, 100, seed=2)
+    return Case(orc, "paper-synthetic-n3000-d300", X, Q, "crosspolytope", L=8, seed=6)
+
+
+@pytest.fixture(scope="module")
+def cpmaxd(orc):
+    # the largest dimension the library takes (d = 320), HP to keep the oracle fast
+    X = datagen.gaussian(1200, 320, seed=12)
+    Q = datagen.gaussian(30, 320, seed=12, purpose="queries")
+    return Case(orc, "gauss-n1200-d320", X, Q, "simhash", L=10, seed=3)
+
+
+CASES = ["cfg1", "cpmid", "cpodd", "cpwide", "hpodd", "cfg1pp", "cpmidpp", "cfg1h", "cpmidh", "cpwideh", "cpsyn",
+         "cpmaxd"]
 
 
 @pytest.fixture

@@ -109,3 +109,32 @@ def test_planted_neighbour_is_found(planted):
     a = ix.search(planted["Qd"], 1, 0.95, scoring="bf16")
     b = ix.search(planted["Qd"], 1, 0.95, scoring="fp32")
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+@pytest.fixture(scope="module")
+def synthetic():
+    pf.build()
+    w = datagen.WORKLOADS["paper-synthetic-n1m-d300"]
+    X = datagen.paper_synthetic_points(w["n"], w["block"], seed=0)
+    Qs = datagen.paper_synthetic_queries(w["Q"], w["block"], seed=0)
+    Xd = torch.from_numpy(X).to(DEV)
+    ix = pf.Index(Xd, "crosspolytope", budget_bytes=w["budget"], seed=0)
+    return {"ix": ix, "Xd": Xd, "Qd": torch.from_numpy(Qs).to(DEV), "n": w["n"], "recall": w["recall"]}
+
+
+def test_paper_synthetic_recall_and_neighbour(synthetic, orc):
+    """Sec. 5 SYNTHETIC at full size (n = 10^6, 300 dimensions, 1,000 queries,
+    k = 10, 8 GiB): L from the budget rule; with the filter off recall >= 1 - delta
+    (Lemma 1) and the planted last point first for every query; bf16 scoring
+    returns the float32 results with the filter on."""
+    ix, Qd, n, rec = synthetic["ix"], synthetic["Qd"], synthetic["n"], synthetic["recall"]
+    assert ix.d == 300 and ix.d_pad == 304 and ix.L == orc.budget_L(orc.CROSSPOLYTOPE, n, 300, 32, 8 << 30, 0)
+    ids, sims, st = ix.search(Qd, 10, rec, scoring="bf16", filter=False, stats=True)
+    top = _kth_table(synthetic["Xd"], Qd, 10)
+    hit = (sims >= top[:, 9:10] - 1e-6).float().mean().item()
+    trials = Qd.shape[0] * 10
+    assert hit >= rec - 3 * np.sqrt(rec * (1 - rec) / trials), hit
+    assert bool((ids[:, 0] == n - 1).all())
+    a = ix.search(Qd, 10, rec, scoring="bf16")
+    b = ix.search(Qd, 10, rec, scoring="fp32")
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
