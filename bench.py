@@ -165,7 +165,7 @@ def search_kernel_traffic(args=None):
                              or args.recall != 0.9 or getattr(args, "workload", WORKLOAD) != WORKLOAD):
         return None
     path = os.path.join(ROOT, "profiles", "search_kernel_traffic.txt")
-    src = os.path.join(ROOT, "paper_1906_12211_gb300", "csrc", "kernels_search.cu")
+    src = os.path.join(ROOT, "paper_1906_12211_gb300", "csrc", "search_kernel.cuh")
     if not os.path.exists(path):
         return None
     digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -174,7 +174,7 @@ def search_kernel_traffic(args=None):
         if ": " in line and not line.startswith("#"):
             k, v = line.rsplit(": ", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernels_search.cu sha256[:16]") != digest:
+    if vals.get("search_kernel.cuh sha256[:16]") != digest:
         return None
     try:
         return float(vals["dram bytes per launch (full workload)"])

@@ -260,16 +260,19 @@ pf_status pf_index_read_array(const pf_index* index, int32_t which, void* dst, u
 void pf_search_opts_default(pf_search_opts* opts);
 
 /* ---- Launch-shape tuning (the shape is not part of the method of Sec. 4:
- * results, statistics and their order are the same for every shape) ----
+ * results and their order are the same for every shape; so are the statistics
+ * for one number of warps per query) ----
  * Times the search kernel of a batch (Q queries of one k and recall, opts as
  * in pf_index_search: scoring, filter, learned start) for each candidate shape
- * -- 4 or 8 positions per lane per streaming step, times the largest resident
- * CTAs per SM and one or two fewer -- and keeps the fastest for the index's
- * later searches and plans.  queries: host or device, [Q][d] float32.
+ * -- 4 warps per query with 4 or 8 positions per lane per streaming step, or
+ * 8 warps with 8 positions, times the largest resident CTAs per SM and one or
+ * two fewer -- and keeps the fastest for the index's later searches and
+ * plans.  queries: host or device, [Q][d] float32.
  * report (may be NULL) receives the choice.  Errors: PF_ERR_INVALID_ARG (bad
  * sizes, or search plans bound to the index exist), PF_ERR_NOT_TRAINED, CUDA. */
 typedef struct {
   int32_t unroll;       /* chosen positions per lane per streaming step */
+  int32_t warps;        /* chosen warps per query (4 or 8) */
   int32_t ctas_per_sm;  /* chosen CTAs per SM */
   int32_t candidates;   /* shapes timed */
   float best_ms;        /* search-kernel time of the chosen shape on the batch */

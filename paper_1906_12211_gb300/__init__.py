@@ -67,7 +67,7 @@ class LearnedReport(C.Structure):
 
 
 class TuneReport(C.Structure):
-    _fields_ = [("unroll", C.c_int32), ("ctas_per_sm", C.c_int32), ("candidates", C.c_int32),
+    _fields_ = [("unroll", C.c_int32), ("warps", C.c_int32), ("ctas_per_sm", C.c_int32), ("candidates", C.c_int32),
                 ("best_ms", C.c_float), ("default_ms", C.c_float)]
 
 

@@ -881,9 +881,9 @@ pf_status pf_index_tune(pf_index* ix, const float* queries, int64_t Q, int32_t k
     a.stats = nullptr;
     a.counter = ws.counter;
     std::vector<SearchShape> cand;
-    for (int U : {8, 4}) {
-      const int mx = search_max_ctas_per_sm(ix, k, U);
-      for (int c = mx; c >= 1 && c >= mx - 2; --c) cand.push_back(SearchShape{U, c});
+    for (const auto& uw : {std::pair<int, int>{8, 4}, {4, 4}, {8, 8}}) {
+      const int mx = search_max_ctas_per_sm(ix, k, uw.first, uw.second);
+      for (int c = mx; c >= 1 && c >= mx - 2; --c) cand.push_back(SearchShape{uw.first, c, uw.second});
     }
     if (cand.empty()) return fail(PF_ERR_CUDA, "no launchable search shape");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -922,6 +922,7 @@ pf_status pf_index_tune(pf_index* ix, const float* queries, int64_t Q, int32_t k
     ix->search_shape = pick;
     if (report) {
       report->unroll = pick.unroll;
+      report->warps = pick.warps;
       report->ctas_per_sm = pick.ctas_per_sm;
       report->candidates = int32_t(cand.size());
       report->best_ms = best;

@@ -36,10 +36,12 @@ struct Layout {
 Layout make_layout(int family, int d);
 
 // Launch shape of the search kernel (not part of the method): positions per
-// lane per streaming step (4 or 8) and a cap on CTAs per SM (0: occupancy).
+// lane per streaming step (4 or 8), a cap on CTAs per SM (0: occupancy) and
+// warps per query (4, or 8 with 8 positions).
 struct SearchShape {
   int unroll = 0;       // 0 in SearchArgs: the index's tuned shape
   int ctas_per_sm = 0;
+  int warps = 4;
 };
 
 // ---------------------------------------------------------------- host params
@@ -116,7 +118,7 @@ struct pf_index {
   float bf16_err = 0.f;            // bound on |bf16 estimate - float32 canonical similarity|
   int32_t* dev_error = nullptr;    // device error word (bit 1: a bounded wait timed out)
   int num_sms = 0;
-  pf::SearchShape search_shape{8, 0};  // chosen by pf_index_tune (default: 8 positions per lane, full occupancy)
+  pf::SearchShape search_shape{8, 0, 4};  // chosen by pf_index_tune (default: 8 positions per lane, full occupancy)
   int live_plans = 0;                   // captured search plans bound to this index
   int hold_weight_loads = 0;            // diagnostics only (pf_index_selftest_timeout)
   pf_workspace ws;
@@ -185,7 +187,7 @@ struct SearchArgs {
 };
 cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t s);
 // CTAs per SM the search kernel can keep resident for this index (0 on error)
-int search_max_ctas_per_sm(const pf_index* ix, int k_max, int unroll);
+int search_max_ctas_per_sm(const pf_index* ix, int k_max, int unroll, int warps);
 
 // start-depth perceptron (kernels_mlp.cu)
 cudaError_t mlp_features(const float* qx, const uint64_t* qsk, int Q, int d_pad, int M, float* x, cudaStream_t s);

@@ -115,8 +115,14 @@ def test_tuning_changes_no_result(idx, scoring, learned):
     kk = torch.full((600,), 10, dtype=torch.int32, device=DEV)
     before = ix.search(q, kk, 0.9, k_max=KMAX, scoring=scoring, learned=learned, stats=True)
     rep = ix.tune(q, 10, 0.9, scoring=scoring, learned=learned)
-    assert rep["unroll"] in (4, 8) and rep["ctas_per_sm"] >= 1 and rep["candidates"] >= 2
+    assert rep["unroll"] in (4, 8) and rep["warps"] in (4, 8) and rep["ctas_per_sm"] >= 1
+    assert rep["candidates"] >= 3 and (rep["warps"] == 4 or rep["unroll"] == 8)
     assert 0.0 < rep["best_ms"] <= rep["default_ms"]
     after = ix.search(q, kk, 0.9, k_max=KMAX, scoring=scoring, learned=learned, stats=True)
-    for a, b in zip(before, after):
-        assert torch.equal(a, b)
+    assert torch.equal(before[0], after[0]) and torch.equal(before[1], after[1])
+    # the method's counts are the same for every shape; how many bf16 estimates
+    # needed an exact rerank depends on how the candidates meet the warp lists
+    sb, sa = pf.stats_to_numpy(before[2]), pf.stats_to_numpy(after[2])
+    for f in sb.dtype.names:
+        if f != "reranked":
+            assert np.array_equal(sb[f], sa[f]), f
