@@ -81,7 +81,8 @@ cudaError_t launch_normalize(const float* in, int64_t rows, int d, int d_pad, fl
 // when a fifth could be in the band).
 // ---------------------------------------------------------------------------
 constexpr int kHashPts = 128;
-constexpr int kHashChunk = 32;  // hash rows staged in shared memory at a time
+constexpr int kHashGroups = 2;  // groups of hash rows per CTA, one per set of kHashPts threads
+constexpr int kHashChunk = 16;  // hash rows of a group staged in shared memory at a time
 constexpr int kRowBlock = 8;    // rows whose projections a thread accumulates together
 
 __device__ __forceinline__ double dot64(const float* __restrict__ a, const float* __restrict__ x, int d) {
@@ -129,22 +130,24 @@ struct Top4 {
   }
 };
 
-__global__ void __launch_bounds__(kHashPts) hash_simt_kernel(
-    const float* __restrict__ x32, int64_t npts, int d, int d_pad, int family, int L, int fns, int ell,
+__global__ void __launch_bounds__(kHashPts * kHashGroups) hash_simt_kernel(
+    const float* __restrict__ x32, int64_t npts, int d, int d_pad, int family, int L, int M, int fns, int ell,
     int rows_table, const float* __restrict__ W, const float* __restrict__ thr, uint32_t* __restrict__ codes,
     int64_t cj, int64_t cp, uint64_t* __restrict__ sk, int64_t sm, int64_t sp) {
   extern __shared__ float smem[];
   const int xs = d_pad + 4;                 // row stride: float4 reads of 8 lanes hit 32 distinct banks
-  float* xS = smem;                         // [kHashPts][d_pad + 4] this CTA's points
-  float* wS = smem + kHashPts * xs;         // [kHashChunk][d_pad] staged hash rows
-  const int tid = threadIdx.x;
+  // the CTA's kHashPts points are shared by its kHashGroups sets of threads;
+  // set h hashes them with group blockIdx.y * kHashGroups + h
+  const int h = threadIdx.x / kHashPts, tid = threadIdx.x % kHashPts;
+  float* xS = smem;                                   // [kHashPts][d_pad + 4] this CTA's points
+  float* wS = smem + kHashPts * xs + h * kHashChunk * d_pad;  // [kHashChunk][d_pad] this set's rows
   const int64_t p0 = int64_t(blockIdx.x) * kHashPts;
   const int64_t p = p0 + tid;
-  const int g = blockIdx.y;
-  const bool is_table = g < L;
+  const int g = blockIdx.y * kHashGroups + h;
+  const bool is_table = g < L, live_g = g < L + M;
   const int q4 = d_pad / 4;
 
-  for (int e = tid; e < kHashPts * q4; e += kHashPts) {
+  for (int e = threadIdx.x; e < kHashPts * q4; e += kHashPts * kHashGroups) {
     const int pt = e / q4, i4 = e % q4;
     const int64_t pp = p0 + pt;
     reinterpret_cast<float4*>(xS + pt * xs)[i4] =
@@ -152,7 +155,13 @@ __global__ void __launch_bounds__(kHashPts) hash_simt_kernel(
   }
 
   const int64_t row0 = is_table ? int64_t(g) * rows_table : int64_t(L) * rows_table + int64_t(g - L) * 64;
-  const int nrows = is_table ? rows_table : 64;
+  const int nrows = !live_g ? 0 : is_table ? rows_table : 64;
+  // every set runs as many chunks as the longest group of the CTA (barriers)
+  int max_rows = 0;
+  for (int u = 0; u < kHashGroups; ++u) {
+    const int gu = blockIdx.y * kHashGroups + u;
+    max_rows = max(max_rows, gu < L ? rows_table : gu < L + M ? 64 : 0);
+  }
   const float* xrow = x32 + (p < npts ? p : 0) * d_pad;
   const float4* xv4 = reinterpret_cast<const float4*>(xS + tid * xs);
 
@@ -225,8 +234,8 @@ __global__ void __launch_bounds__(kHashPts) hash_simt_kernel(
   // kRowBlock rows at a time: one float4 of the point and one (broadcast) of
   // each row per step, 4 * kRowBlock fused multiply-adds.  Every chunk holds a
   // multiple of kRowBlock rows (rows_table = fns * d_pad or 32, sketches 64).
-  for (int r0 = 0; r0 < nrows; r0 += kHashChunk) {
-    const int nr = min(kHashChunk, nrows - r0);
+  for (int r0 = 0; r0 < max_rows; r0 += kHashChunk) {
+    const int nr = max(0, min(kHashChunk, nrows - r0));
     __syncthreads();
     for (int e = tid; e < nr * q4; e += kHashPts)
       reinterpret_cast<float4*>(wS)[e] = __ldg(reinterpret_cast<const float4*>(W + (row0 + r0) * d_pad) + e);
@@ -251,7 +260,7 @@ __global__ void __launch_bounds__(kHashPts) hash_simt_kernel(
       for (int q = 0; q < kRowBlock; ++q) row_done(r0 + rr + q, acc[q]);
     }
   }
-  if (p < npts) {
+  if (p < npts && live_g) {
     if (is_table)
       codes[int64_t(g) * cj + p * cp] = code;
     else
@@ -266,11 +275,12 @@ cudaError_t launch_hash(const pf_index* ix, const float* x32, const __nv_bfloat1
   if (hash_tc_supported(ix) && xh && xl)
     return launch_hash_tc(ix, xh, xl, x32, npts, codes, cj, cp, sk, sm, sp, ix->dev_error, rq, rq_count, rq_cap, s);
   const Layout& lay = ix->lay;
-  const size_t smem = sizeof(float) * (size_t(lay.d_pad + 4) * kHashPts + size_t(kHashChunk) * lay.d_pad);
+  const size_t smem = sizeof(float) * (size_t(lay.d_pad + 4) * kHashPts + size_t(kHashGroups * kHashChunk) * lay.d_pad);
   cudaError_t e = cudaFuncSetAttribute(hash_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  dim3 grid(unsigned((npts + kHashPts - 1) / kHashPts), unsigned(ix->L + ix->M));
-  hash_simt_kernel<<<grid, kHashPts, smem, s>>>(x32, npts, ix->d, lay.d_pad, ix->family, ix->L, lay.fns, lay.ell,
+  dim3 grid(unsigned((npts + kHashPts - 1) / kHashPts), unsigned((ix->L + ix->M + kHashGroups - 1) / kHashGroups));
+  hash_simt_kernel<<<grid, kHashPts * kHashGroups, smem, s>>>(x32, npts, ix->d, lay.d_pad, ix->family, ix->L, ix->M,
+                                                              lay.fns, lay.ell,
                                                 lay.rows_table, ix->W32, ix->Wthr, codes, cj, cp, sk, sm, sp);
   return cudaGetLastError();
 }
