@@ -517,35 +517,63 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
             nr = min(n, r + B * m);
           }
         } else {
-          if (try_left && l > 0 && prefix_match(__ldg(cj + l - 1), qcj, mask)) {
-            // smallest m >= 1 with l - B*m <= 0 or codes[l - B*m - 1] outside the block
-            uint32_t lo = 0, hi = 1;
-            for (;;) {
-              const int64_t pos = int64_t(l) - int64_t(B) * hi;
-              if (pos <= 0 || !prefix_match(__ldg(cj + pos - 1), qcj, mask)) break;
-              lo = hi;
-              hi *= 2;
-            }
-            while (hi - lo > 1) {
-              const uint32_t mid = (lo + hi) >> 1;
-              const int64_t pos = int64_t(l) - int64_t(B) * mid;
-              if (pos <= 0 || !prefix_match(__ldg(cj + pos - 1), qcj, mask)) hi = mid; else lo = mid;
+          // above 13 bits: a side grows by m* segments, m* the smallest m >= 1
+          // whose position is outside the array or whose code is outside the
+          // block.  The entry next to the range and the first kProbe segment
+          // boundaries of both sides are read together (one round trip in the
+          // common case); past them the search gallops on.  A position outside
+          // the array reads as a code outside the block (~qcj).
+          constexpr int kProbe = 4;
+          const bool lv = try_left && l > 0, rv = try_right && r < n;
+          uint32_t cl[kProbe + 1], cr[kProbe + 1];
+#pragma unroll
+          for (int m = 0; m <= kProbe; ++m) {
+            const int64_t pl = int64_t(l) - int64_t(B) * m - 1, pr = int64_t(r) + int64_t(B) * m;
+            cl[m] = lv && pl >= 0 ? __ldg(cj + pl) : ~qcj;
+            cr[m] = rv && pr < int64_t(n) ? __ldg(cj + pr) : ~qcj;
+          }
+          if (lv && prefix_match(cl[0], qcj, mask)) {
+            uint32_t lo = 0, hi = 0;
+#pragma unroll
+            for (int m = kProbe; m >= 1; --m)
+              if (!prefix_match(cl[m], qcj, mask)) hi = m;
+            if (hi == 0) {  // the first kProbe boundaries are all inside the block
+              lo = kProbe;
+              hi = 2 * kProbe;
+              for (;;) {
+                const int64_t pos = int64_t(l) - int64_t(B) * hi;
+                if (pos <= 0 || !prefix_match(__ldg(cj + pos - 1), qcj, mask)) break;
+                lo = hi;
+                hi *= 2;
+              }
+              while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                const int64_t pos = int64_t(l) - int64_t(B) * mid;
+                if (pos <= 0 || !prefix_match(__ldg(cj + pos - 1), qcj, mask)) hi = mid; else lo = mid;
+              }
             }
             const int64_t pos = int64_t(l) - int64_t(B) * hi;
             nl = pos < 0 ? 0u : uint32_t(pos);
           }
-          if (try_right && r < n && prefix_match(__ldg(cj + r), qcj, mask)) {
-            uint32_t lo = 0, hi = 1;
-            for (;;) {
-              const int64_t pos = int64_t(r) + int64_t(B) * hi;
-              if (pos >= int64_t(n) || !prefix_match(__ldg(cj + pos), qcj, mask)) break;
-              lo = hi;
-              hi *= 2;
-            }
-            while (hi - lo > 1) {
-              const uint32_t mid = (lo + hi) >> 1;
-              const int64_t pos = int64_t(r) + int64_t(B) * mid;
-              if (pos >= int64_t(n) || !prefix_match(__ldg(cj + pos), qcj, mask)) hi = mid; else lo = mid;
+          if (rv && prefix_match(cr[0], qcj, mask)) {
+            uint32_t lo = 0, hi = 0;
+#pragma unroll
+            for (int m = kProbe; m >= 1; --m)
+              if (!prefix_match(cr[m], qcj, mask)) hi = m;
+            if (hi == 0) {
+              lo = kProbe;
+              hi = 2 * kProbe;
+              for (;;) {
+                const int64_t pos = int64_t(r) + int64_t(B) * hi;
+                if (pos >= int64_t(n) || !prefix_match(__ldg(cj + pos), qcj, mask)) break;
+                lo = hi;
+                hi *= 2;
+              }
+              while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                const int64_t pos = int64_t(r) + int64_t(B) * mid;
+                if (pos >= int64_t(n) || !prefix_match(__ldg(cj + pos), qcj, mask)) hi = mid; else lo = mid;
+              }
             }
             const int64_t pos = int64_t(r) + int64_t(B) * hi;
             nr = pos > int64_t(n) ? n : uint32_t(pos);
