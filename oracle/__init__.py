@@ -20,6 +20,7 @@ _LIB = os.path.join(_HERE, "libpuffinn_oracle.so")
 
 SIMHASH = 0
 CROSSPOLYTOPE = 1
+CROSSPOLYTOPE_FHT = 2  # pseudo-random cross-polytope (oracle/fht.py); needs an explicit L
 PREFIX_BITS = 13
 ALPHA_STEPS = 41
 
@@ -246,7 +247,14 @@ class OracleIndex:
         points = _c(points, np.float32)
         self.n, self.d = points.shape
         self.family, self.seed, self.M, self.B = family, seed, M, B
-        lay = layout(family, self.d)
+        if family == CROSSPOLYTOPE_FHT:
+            from . import fht
+
+            lay = fht.layout(self.d)
+            if L is None:
+                raise ValueError("the pseudo-random cross-polytope family needs an explicit L")
+        else:
+            lay = layout(family, self.d)
         self.ell, self.F, self.Kb = lay["ell"], lay["F"], lay["Kb"]
         if L is None:
             L = budget_L(family, self.n, self.d, M, int(budget_bytes), sketch_layout, row_storage)
@@ -256,17 +264,29 @@ class OracleIndex:
         self.x = normalize(points)
         if row_storage == 1:  # the stored point is the binary16 rounding of the normalised row
             self.x = round_rows_f16(self.x)
-        self.A = gen_hash_params(seed, family, self.L, self.d)
         self.S = gen_sketch_params(seed, M, self.d)
-        codes = hash_codes(family, self.A, self.x)
+        if family == CROSSPOLYTOPE_FHT:
+            self.A = fht.gen_params(seed, self.L, self.d)
+            codes = fht.hash_codes(self.A, self.x, self.d)
+            self.P = fht.cp_table(seed, self.d, cp_draws)
+        else:
+            self.A = gen_hash_params(seed, family, self.L, self.d)
+            codes = hash_codes(family, self.A, self.x)
+            self.P = cp_table(seed, self.d, cp_draws) if family == CROSSPOLYTOPE else None
         self.sk = sketches(self.S, self.x)
         self.codes, self.ids = sort_tables(codes)
         self.pfx = prefix_table(self.codes)
-        self.P = cp_table(seed, self.d, cp_draws) if family == CROSSPOLYTOPE else None
+
+    def _codes(self, x):
+        if self.family == CROSSPOLYTOPE_FHT:
+            from . import fht
+
+            return fht.hash_codes(self.A, x, self.d)
+        return hash_codes(self.family, self.A, x)
 
     def hash_queries(self, queries):
         qn = normalize(queries)
-        qcodes = np.ascontiguousarray(hash_codes(self.family, self.A, qn).T)
+        qcodes = np.ascontiguousarray(self._codes(qn).T)
         qsk = np.ascontiguousarray(sketches(self.S, qn).T)
         return qn, qcodes, qsk
 
@@ -281,7 +301,9 @@ class OracleIndex:
         sims = np.zeros((Q, k_max), np.float32)
         stats = np.zeros(Q, STATS_DTYPE)
         sd = None if start_depth is None else np.broadcast_to(np.asarray(start_depth, np.int32), (Q,)).copy()
-        ix = _Index(self.family, self.d, self.ell, self.Kb, self.L, self.M, self.B, self.n,
+        # the query procedure sees a cross-polytope family through its table P
+        fam = CROSSPOLYTOPE if self.family == CROSSPOLYTOPE_FHT else self.family
+        ix = _Index(fam, self.d, self.ell, self.Kb, self.L, self.M, self.B, self.n,
                     self.x.ctypes.data, self.codes.ctypes.data, self.ids.ctypes.data,
                     self.sk.ctypes.data, self.P.ctypes.data if self.P is not None else None)
         trace = np.zeros((Q, trace_cap, 2), np.uint32) if trace_cap else None
