@@ -95,3 +95,19 @@ def test_traffic_summary_only_for_the_profiled_workload():
     # (or None once the kernel differs from the profiled one)
     v = bench.search_kernel_traffic(argparse.Namespace(**base))
     assert v is None or v > 1e10
+
+
+def test_synthetic_workload_host_side():
+    sys.path.insert(0, ROOT)
+    import bench
+    import numpy as np
+
+    w, X, Qs = bench.workload(0, n_override=25_000, q_override=8, name="paper-synthetic-n1m-d300")
+    assert X.shape == (25_000, 300) and Qs.shape == (8, 300) and w["k"] == 10 and w["recall"] == 0.99
+    # the CPU sample keeps the point every query is near (the last one)
+    S = bench.cpu_sample_points(w, X)
+    assert S.shape[0] == bench.CPU_SAMPLE_N and np.array_equal(S[-1], X[-1])
+    # another rank: other queries of the same construction (same v)
+    _, _, Q1 = bench.workload(1, n_override=25_000, q_override=8, name="paper-synthetic-n1m-d300")
+    assert np.array_equal(Q1[:, :100], Qs[:, :100]) and not np.array_equal(Q1, Qs)
+    assert bench.METRICS["paper-synthetic-n1m-d300"].startswith("k-NN queries/s")
