@@ -540,6 +540,19 @@ def main():
         cpu = {"value": nq / el, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                "sample": f"oracle index over a {CPU_SAMPLE_N}-point sample of the {ix.n} points (same data and seed, "
                          f"L={ix.L}); {nq} queries; all host cores"}
+        # the paper's protocol: one thread, queries one after another (Sec. 5)
+        import oracle
+
+        n1 = max(8, nq // max(1, cpu_cores()))
+        oracle.set_threads(1)
+        try:
+            t = time.perf_counter()
+            oix.search(Qs[:n1], k, args.recall)
+            el1 = time.perf_counter() - t
+        finally:
+            oracle.set_threads(0)
+        cpu["single_thread"] = {"value": n1 / el1, "unit": UNIT, "cores": 1,
+                                "sample": f"the same index; {n1} queries one after another"}
 
     sequential = {"value": value, "ms_per_step": t_max / args.steps * 1e3,
                   "l2": "flushed between steps (512 MiB write)", "clocks": clk}

@@ -66,6 +66,7 @@ def lib():
             L = C.CDLL(_LIB)
             vp, i32, i64, u64, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
             sig = {
+                "orc_set_threads": (None, [C.c_int]),
                 "orc_philox4x32_10": (None, [vp, vp, vp]),
                 "orc_gauss": (C.c_float, [u64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]),
                 "orc_layout": (None, [C.c_int, C.c_int, vp, vp, vp, vp]),
@@ -111,6 +112,11 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     out = np.zeros(4, np.uint32)
     lib().orc_philox4x32_10(_p(c), _p(k), _p(out))
     return out
+
+
+def set_threads(n: int) -> None:
+    """Host threads of the oracle's parallel loops (n <= 0: all processors)."""
+    lib().orc_set_threads(int(n))
 
 
 def gauss(seed: int, purpose: int, a: int, b: int, c: int) -> float:

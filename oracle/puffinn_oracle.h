@@ -34,6 +34,9 @@ enum { ORC_PURPOSE_HASH = 1, ORC_PURPOSE_SKETCH = 2, ORC_PURPOSE_CPMC = 3 };
 #define ORC_ALPHA_STEPS 41 /* similarity grid -1, -0.95, ..., 1 (Sec. 4.3) */
 #define ORC_SNAPSHOT_GROUP 32 /* repetitions per sketch-threshold snapshot in a query's first round */
 
+/* Host threads of the OpenMP loops (n <= 0: all processors). */
+void orc_set_threads(int n);
+
 /* ---- random parameters (counter-based generator, Salmon et al. SC'11) ---- */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 /* One standard normal per counter (purpose, a, b, c), Box-Muller in FP64,

@@ -182,3 +182,20 @@ def test_start_at_full_depth_keeps_the_filtered_work(orc, cp_index):
     assert np.all(jump["stats"]["rounds"] <= plain["stats"]["rounds"])
     same = np.mean(jump["stats"]["stop_depth"] == plain["stats"]["stop_depth"])
     assert same >= 0.8
+
+
+def test_one_thread_gives_the_same_answers():
+    import datagen
+    import oracle as O
+
+    X = datagen.vmf_mixture(3000, 48, 20, 40.0, seed=6)
+    Q = datagen.vmf_mixture(24, 48, 20, 40.0, seed=6, purpose="queries")
+    ix = O.OracleIndex(X, O.CROSSPOLYTOPE, L=12, seed=1)
+    a = ix.search(Q, 10, 0.9)
+    O.set_threads(1)
+    try:
+        b = ix.search(Q, 10, 0.9)
+    finally:
+        O.set_threads(0)
+    assert np.array_equal(a["ids"], b["ids"]) and np.array_equal(a["sims"], b["sims"])
+    assert np.array_equal(a["stats"], b["stats"])
