@@ -281,6 +281,31 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def cpu_baseline(w, X, Qs, L, k, recall, q_target_s=15.0):
+    """The oracle timed on the host cores on a sample of the workload (about
+    q_target_s of queries), and on one thread as the paper measures (Sec. 5)."""
+    import oracle
+
+    oix, nq = oracle_sample(w, X, Qs, L, k, recall, q_target_s=q_target_s)
+    t = time.perf_counter()
+    oix.search(Qs[:nq], k, recall)
+    el = time.perf_counter() - t
+    cpu = {"value": nq / el, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+           "sample": f"oracle index over a {CPU_SAMPLE_N}-point sample of the {X.shape[0]} points (same data and "
+                     f"seed, L={L}); {nq} queries; all host cores"}
+    n1 = max(8, nq // max(1, cpu_cores()))
+    oracle.set_threads(1)
+    try:
+        t = time.perf_counter()
+        oix.search(Qs[:n1], k, recall)
+        el1 = time.perf_counter() - t
+    finally:
+        oracle.set_threads(0)
+    cpu["single_thread"] = {"value": n1 / el1, "unit": UNIT, "cores": 1,
+                            "sample": f"the same index; {n1} queries one after another"}
+    return cpu
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -533,26 +558,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        oix, nq = oracle_sample(w, X, Qs, ix.L, k, args.recall, q_target_s=15.0)
-        t = time.perf_counter()
-        oix.search(Qs[:nq], k, args.recall)
-        el = time.perf_counter() - t
-        cpu = {"value": nq / el, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"oracle index over a {CPU_SAMPLE_N}-point sample of the {ix.n} points (same data and seed, "
-                         f"L={ix.L}); {nq} queries; all host cores"}
-        # the paper's protocol: one thread, queries one after another (Sec. 5)
-        import oracle
-
-        n1 = max(8, nq // max(1, cpu_cores()))
-        oracle.set_threads(1)
-        try:
-            t = time.perf_counter()
-            oix.search(Qs[:n1], k, args.recall)
-            el1 = time.perf_counter() - t
-        finally:
-            oracle.set_threads(0)
-        cpu["single_thread"] = {"value": n1 / el1, "unit": UNIT, "cores": 1,
-                                "sample": f"the same index; {n1} queries one after another"}
+        cpu = cpu_baseline(w, X, Qs, ix.L, k, args.recall)
 
     sequential = {"value": value, "ms_per_step": t_max / args.steps * 1e3,
                   "l2": "flushed between steps (512 MiB write)", "clocks": clk}

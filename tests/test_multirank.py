@@ -111,3 +111,14 @@ def test_synthetic_workload_host_side():
     _, _, Q1 = bench.workload(1, n_override=25_000, q_override=8, name="paper-synthetic-n1m-d300")
     assert np.array_equal(Q1[:, :100], Qs[:, :100]) and not np.array_equal(Q1, Qs)
     assert bench.METRICS["paper-synthetic-n1m-d300"].startswith("k-NN queries/s")
+
+
+def test_cpu_baseline_reports_all_cores_and_one_thread():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    w, X, Qs = bench.workload(0, n_override=4000, q_override=40)
+    cpu = bench.cpu_baseline(w, X, Qs, 12, 10, 0.9, q_target_s=0.5)
+    assert cpu["kind"] == "oracle" and cpu["value"] > 0 and cpu["cores"] >= 1
+    st = cpu["single_thread"]
+    assert st["cores"] == 1 and st["value"] > 0 and "one after another" in st["sample"]
