@@ -57,7 +57,7 @@ METRICS = {
     "paper-synthetic-n1m-d300": "k-NN queries/s, recall target 0.99 (paper SYNTHETIC: n=1M, 300 dims, k=10)",
 }
 METRIC = METRICS[WORKLOAD]
-# the paper's single-thread CPU figure on SYNTHETIC: 360.3 queries/s at recall 0.971 (Sec. 5, Fig. 7)
+# the paper's single-thread CPU figure on SYNTHETIC: 360.3 queries/s at recall 0.971 (Sec. 5, comparison with other approaches)
 PAPER_SYNTHETIC_QPS, PAPER_SYNTHETIC_RECALL = 360.3, 0.971
 UNIT = "queries/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB of L2
