@@ -280,6 +280,11 @@ typedef struct {
 } pf_tune_report;
 pf_status pf_index_tune(pf_index* index, const float* queries, int64_t Q, int32_t k, double recall,
                         const pf_search_opts* opts, pf_tune_report* report, void* stream);
+/* Set the launch shape of the index's later searches and plans directly:
+ * unroll 4 or 8 positions per lane, warps 4 or 8 per query (8 only with unroll
+ * 8), ctas_per_sm a cap on resident CTAs per SM (0: as many as fit).  Errors:
+ * PF_ERR_INVALID_ARG (other values, or search plans bound to the index). */
+pf_status pf_index_set_shape(pf_index* index, int32_t unroll, int32_t warps, int32_t ctas_per_sm);
 
 /* ---- Captured search (a CUDA graph of one batch shape) ----
  * pf_index_search for a fixed Q, k_max and options, bound to caller-owned

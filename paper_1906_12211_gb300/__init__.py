@@ -118,6 +118,7 @@ def lib():
                 "pf_index_free": (None, [vp]),
                 "pf_index_tune": (i32, [vp, vp, i64, i32, C.c_double, vp, vp, vp]),
                 "pf_index_selftest_timeout": (i32, [vp, vp, i64, vp]),
+                "pf_index_set_shape": (i32, [vp, i32, i32, i32]),
                 "pf_search_plan_create": (i32, [vp, i64, i32, vp, vp, vp]),
                 "pf_search_plan_run": (i32, [vp, vp]),
                 "pf_search_plan_check": (i32, [vp, vp]),
@@ -317,6 +318,10 @@ class Index:
         _check(lib().pf_index_tune(self._h, _ptr(queries), int(queries.shape[0]), int(k), float(recall),
                                    C.byref(o), C.byref(rep), _stream_ptr(stream)))
         return {f: getattr(rep, f) for f, _ in TuneReport._fields_}
+
+    def set_shape(self, unroll: int = 8, warps: int = 4, ctas_per_sm: int = 0):
+        """pf_index_set_shape: the launch shape of later searches and plans."""
+        _check(lib().pf_index_set_shape(self._h, int(unroll), int(warps), int(ctas_per_sm)))
 
     def selftest_timeout(self, queries, stream=None):
         """pf_index_selftest_timeout: hash with the weight loads withheld; raises

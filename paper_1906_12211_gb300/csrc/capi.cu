@@ -932,6 +932,17 @@ pf_status pf_index_tune(pf_index* ix, const float* queries, int64_t Q, int32_t k
   });
 }
 
+pf_status pf_index_set_shape(pf_index* ix, int32_t unroll, int32_t warps, int32_t ctas_per_sm) {
+  return guarded([&]() -> pf_status {
+    if (!ix) return fail(PF_ERR_INVALID_ARG, "null index");
+    if ((unroll != 4 && unroll != 8) || (warps != 4 && warps != 8) || (warps == 8 && unroll != 8) || ctas_per_sm < 0)
+      return fail(PF_ERR_INVALID_ARG, "unroll must be 4 or 8, warps 4 or 8 (8 only with unroll 8), ctas_per_sm >= 0");
+    if (ix->live_plans > 0) return fail(PF_ERR_INVALID_ARG, "search plans bound to the index exist");
+    ix->search_shape = SearchShape{unroll, ctas_per_sm, warps};
+    return PF_OK;
+  });
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------- plans

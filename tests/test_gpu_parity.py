@@ -330,3 +330,22 @@ def test_errors_are_statuses():
     assert e.value.status == -1
     ids, sims, _ = g.search(X[:0], 10, 0.9)
     assert ids.shape[0] == 0
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 0), (8, 8, 0), (8, 4, 3)])
+def test_every_launch_shape_equals_the_oracle(cpmid, shape):
+    # positions per lane, warps per query and CTAs per SM change no result
+    ref = cpmid.orc.search(cpmid.Q, 10, 0.9)
+    cpmid.gpu.set_shape(*shape)
+    try:
+        _compare(cpmid.gpu.search(cpmid.qd, 10, 0.9, stats=True), ref)
+        _compare(cpmid.gpu.search(cpmid.qd, 10, 0.9, scoring="bf16", stats=True), ref)
+    finally:
+        cpmid.gpu.set_shape(8, 4, 0)
+
+
+def test_invalid_launch_shapes_are_rejected(cpmid):
+    for bad in ((4, 8, 0), (6, 4, 0), (8, 5, 0), (8, 4, -1)):
+        with pytest.raises(pf.PuffinnError) as e:
+            cpmid.gpu.set_shape(*bad)
+        assert e.value.status == -1
