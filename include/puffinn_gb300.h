@@ -148,7 +148,8 @@ typedef enum {
  * hyperplanes from `seed`, hash every point, sort each repetition's
  * (code, pos) array and tabulate its 13-bit prefixes, and estimate the CP
  * collision table (Sec. 4.3).  L is the largest count whose resident bytes fit
- * memory_budget_bytes (PF_ERR_BUDGET_TOO_SMALL if none); the bytes counted are
+ * memory_budget_bytes (PF_ERR_BUDGET_TOO_SMALL if none), at most 2048 (a query
+ * keeps its per-repetition state in shared memory); the bytes counted are
  * those of the chosen sketch layout and row storage.  On success *out
  * receives a new index that the caller releases with pf_index_free. */
 pf_status pf_index_build(const pf_build_params* params, const void* points, pf_index** out, void* stream);
