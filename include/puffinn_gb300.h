@@ -148,8 +148,9 @@ typedef enum {
  * hyperplanes from `seed`, hash every point, sort each repetition's
  * (code, pos) array and tabulate its 13-bit prefixes, and estimate the CP
  * collision table (Sec. 4.3).  L is the largest count whose resident bytes fit
- * memory_budget_bytes (PF_ERR_BUDGET_TOO_SMALL if none), at most 2048 (a query
- * keeps its per-repetition state in shared memory); the bytes counted are
+ * memory_budget_bytes (PF_ERR_BUDGET_TOO_SMALL if none), clamped to 2048 (a
+ * query keeps its per-repetition state in shared memory); an explicit
+ * num_tables above 2048 is PF_ERR_INVALID_ARG.  The bytes counted are
  * those of the chosen sketch layout and row storage.  On success *out
  * receives a new index that the caller releases with pf_index_free. */
 pf_status pf_index_build(const pf_build_params* params, const void* points, pf_index** out, void* stream);
@@ -179,7 +180,9 @@ pf_status pf_index_search(pf_index* index, const float* queries, int64_t Q, cons
  * acceptable.  The paper has no counterpart; this is a deployment variant.
  *   - Same arguments, semantics and results as pf_index_search, except that
  *     queries, k, recall, out_ids, out_sims, stats (if not NULL) and
- *     opts->start_depth (if set) must all be device memory.
+ *     opts->start_depth (if set) must all be device memory, and that
+ *     opts->learned_start is rejected (PF_ERR_INVALID_ARG: the learned start
+ *     uses the index's own workspace); give opts->start_depth instead.
  *   - Scratch (normalised queries, query codes and sketches, work counter)
  *     lives in one 32 MiB file-scope device array that every GPU loading the
  *     library holds until the process exits.  A batch must satisfy
@@ -188,8 +191,11 @@ pf_status pf_index_search(pf_index* index, const float* queries, int64_t Q, cons
  *   - No cudaMalloc, cudaFree or other allocating call is made.
  *   - All calls share the array: calls whose device work overlaps (other
  *     streams, other threads) race and must be serialised by the caller.
- *   - The first call on a device looks up the array's device address; make that
- *     first call before any stream capture. */
+ *   - The first call on a device looks up the array's device address.  The
+ *     call synchronises `stream` before it returns, so it cannot be captured
+ *     in a CUDA graph; pf_search_plan_* is the capturable search.
+ *   - A bounded device-side wait that expired is reported as
+ *     PF_ERR_DEVICE_TIMEOUT and cleared, as pf_index_search does. */
 pf_status pf_index_search_noalloc(pf_index* index, const float* queries, int64_t Q, const int32_t* k,
                                   const double* recall, int32_t k_max, uint32_t* out_ids, float* out_sims,
                                   pf_query_stats* stats, const pf_search_opts* opts, void* stream);
@@ -335,6 +341,14 @@ void pf_search_plan_free(pf_search_plan* plan);
  * PF_ERR_INVALID_ARG (null argument, Q < 1, an index hashed without the
  * tensor-core kernel (d' > 128), or search plans bound to the index), CUDA. */
 pf_status pf_index_selftest_timeout(pf_index* index, const float* queries, int64_t Q, void* stream);
+/* Withhold (hold != 0) or restore (hold == 0) the weight-tile loads of every
+ * later tensor-core hashing launch of this index, so that a whole entry point
+ * (pf_index_search, pf_index_search_noalloc, ...) can be driven through its
+ * time-out path: while held, each such call returns PF_ERR_DEVICE_TIMEOUT
+ * after about 1 s, with its outputs unspecified.  Captured plans keep the
+ * setting they were captured with.  Errors: PF_ERR_INVALID_ARG (null index,
+ * or an index hashed without the tensor-core kernel). */
+pf_status pf_index_selftest_hold(pf_index* index, int32_t hold);
 
 /* Release an index (NULL is accepted).  Does nothing while search plans bound
  * to it exist (pf_last_error_message says so). */

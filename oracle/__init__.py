@@ -97,6 +97,21 @@ def lib():
     return _lib
 
 
+def compile_variant(src_text: str, out_path: str):
+    """Compile a modified copy of the oracle's source (tests plant mistakes in
+    it to show that a pin catches them) and load it with the query signature."""
+    src = out_path + ".c"
+    with open(src, "w") as f:
+        f.write(src_text)
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+                           "-shared", "-I", _HERE, "-o", out_path, src, "-lm"])
+    L = C.CDLL(out_path)
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    L.orc_search.restype = None
+    L.orc_search.argtypes = [vp, vp, vp, vp, i64, vp, vp, i32, vp, C.c_int, vp, vp, vp, vp, i64, vp]
+    return L
+
+
 def _p(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p)
 
@@ -297,7 +312,7 @@ class OracleIndex:
         return qn, qcodes, qsk
 
     def search(self, queries, k, recall, *, k_max: int | None = None, start_depth=None,
-               filter: bool = True, trace_cap: int = 0):
+               filter: bool = True, trace_cap: int = 0, variant=None):
         qn, qcodes, qsk = self.hash_queries(queries)
         Q = qn.shape[0]
         k = np.broadcast_to(np.asarray(k, np.int32), (Q,)).copy()
@@ -314,11 +329,11 @@ class OracleIndex:
                     self.sk.ctypes.data, self.P.ctypes.data if self.P is not None else None)
         trace = np.zeros((Q, trace_cap, 2), np.uint32) if trace_cap else None
         tlen = np.zeros(Q, np.int64) if trace_cap else None
-        lib().orc_search(C.byref(ix), _p(qn), _p(qcodes), _p(qsk), Q, _p(k), _p(recall), k_max,
+        (variant or lib()).orc_search(C.byref(ix), _p(qn), _p(qcodes), _p(qsk), Q, _p(k), _p(recall), k_max,
                          _p(sd) if sd is not None else None, 1 if filter else 0, _p(ids), _p(sims),
                          _p(stats), _p(trace) if trace is not None else None, trace_cap,
                          _p(tlen) if tlen is not None else None)
-        out = {"ids": ids, "sims": sims, "stats": stats}
+        out = {"ids": ids, "sims": sims, "stats": stats, "qn": qn, "qsk": qsk}
         if trace_cap:
             out["trace"] = trace
             out["trace_len"] = tlen

@@ -480,12 +480,13 @@ static void search_one(const orc_index* ix, const float* q, const uint32_t* qcod
         for (int64_t p = a; p < b; ++p) {
           uint32_t id = idj[p];
           s.retrieved += 1;
-          if (trace && tl < trace_cap) trace[2 * tl] = ((uint32_t)depth << 24) | (uint32_t)j, trace[2 * tl + 1] = id;
-          ++tl;
+          const int64_t slot = tl++;
+          if (trace && slot < trace_cap) trace[2 * slot] = ((uint32_t)depth << 24) | (uint32_t)j, trace[2 * slot + 1] = id;
           if (filter && depth > 0) {
             int ham = popcount64(qsk[j % M] ^ ix->sk[(int64_t)(j % M) * n + id]);
             if (ham > tau) continue;
           }
+          if (trace && slot < trace_cap) trace[2 * slot] |= 0x80000000u; /* scored */
           s.passed_filter += 1;
           s.scored += 1;
           float sim = orc_sim(q, ix->x + (int64_t)id * ix->d, ix->d);

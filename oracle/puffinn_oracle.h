@@ -109,8 +109,10 @@ typedef struct {
  * start_depth: NULL (plain schedule K, K-1, ..., 0) or per-query start depth
  * i0 (schedule i0, i0-1, ..., 0; i0 outside [0, K) means K).
  * filter: 0/1.  Outputs [Q][k_max]; stats may be NULL.
- * trace (may be NULL): per query up to trace_cap entries (depth<<24 | table, id)
- * of every retrieved candidate, count in trace_len[q]. */
+ * trace (may be NULL): per query up to trace_cap entries
+ * (scored<<31 | depth<<24 | table, id) of every retrieved candidate in the order
+ * visited, scored = 1 when it passed the sketch filter and was scored; count
+ * in trace_len[q]. */
 void orc_search(const orc_index* ix, const float* q, const uint32_t* qcodes, const uint64_t* qsk,
                 int64_t Q, const int32_t* k, const double* recall, int32_t k_max,
                 const int32_t* start_depth, int filter,

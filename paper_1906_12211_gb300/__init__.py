@@ -118,6 +118,7 @@ def lib():
                 "pf_index_free": (None, [vp]),
                 "pf_index_tune": (i32, [vp, vp, i64, i32, C.c_double, vp, vp, vp]),
                 "pf_index_selftest_timeout": (i32, [vp, vp, i64, vp]),
+                "pf_index_selftest_hold": (i32, [vp, i32]),
                 "pf_index_set_shape": (i32, [vp, i32, i32, i32]),
                 "pf_search_plan_create": (i32, [vp, i64, i32, vp, vp, vp]),
                 "pf_search_plan_run": (i32, [vp, vp]),
@@ -327,6 +328,11 @@ class Index:
         """pf_index_selftest_timeout: hash with the weight loads withheld; raises
         PuffinnError(PF_ERR_DEVICE_TIMEOUT) when the bounded waits work."""
         _check(lib().pf_index_selftest_timeout(self._h, _ptr(queries), int(queries.shape[0]), _stream_ptr(stream)))
+
+    def selftest_hold(self, hold: bool):
+        """pf_index_selftest_hold: withhold (True) or restore (False) the weight
+        loads of every later tensor-core hashing launch of this index."""
+        _check(lib().pf_index_selftest_hold(self._h, 1 if hold else 0))
 
     def plan(self, queries, k, recall, out_ids, out_sims, *, k_max: int, stats=None, start_depth=None,
              scoring: str = "fp32", filter: bool = True, learned: bool = False):

@@ -261,7 +261,9 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
                                     : budget_tables(prm->family, prm->n, prm->d, M, prm->memory_budget_bytes,
                                                     prm->sketch_layout, prm->row_storage);
     if (L < 1) return fail(PF_ERR_BUDGET_TOO_SMALL, "memory budget leaves room for no repetition");
-    if (L > kMaxL) L = kMaxL;
+    if (prm->num_tables > kMaxL)
+      return fail(PF_ERR_INVALID_ARG, "num_tables above " + std::to_string(kMaxL) + " is not supported");
+    if (L > kMaxL) L = kMaxL;  // only a budget-derived L is clamped
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
     pf_index* ix = new pf_index();
@@ -817,6 +819,15 @@ pf_status pf_index_selftest_timeout(pf_index* ix, const float* queries, int64_t 
     ix->hold_weight_loads = 0;
     PF_CK(cudaGetLastError());
     if (device_timed_out(ix)) return fail(PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out");
+    return PF_OK;
+  });
+}
+
+pf_status pf_index_selftest_hold(pf_index* ix, int32_t hold) {
+  return guarded([&]() -> pf_status {
+    if (!ix) return fail(PF_ERR_INVALID_ARG, "null index");
+    if (!hash_tc_supported(ix)) return fail(PF_ERR_INVALID_ARG, "this index hashes without the tensor-core kernel");
+    ix->hold_weight_loads = hold ? 1 : 0;
     return PF_OK;
   });
 }

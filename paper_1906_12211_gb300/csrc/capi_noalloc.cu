@@ -96,9 +96,9 @@ extern "C" pf_status pf_index_search_noalloc(pf_index* ix, const float* queries,
                         std::to_string((kScratchBytes - 6 * kAlign) / per_q) + " queries per call, got " +
                         std::to_string(Q));
     }
+    if (ix->device < 0 || ix->device >= kMaxDevices) return reject(PF_ERR_INVALID_ARG, "device ordinal too large");
     cudaError_t e = cudaSetDevice(ix->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
-    if (ix->device < 0 || ix->device >= kMaxDevices) return reject(PF_ERR_INVALID_ARG, "device ordinal too large");
     const void* must_be_device[] = {queries, k, recall, out_ids, out_sims};
     for (const void* p : must_be_device)
       if (!p || !device_pointer(p)) return reject(PF_ERR_INVALID_ARG, "all buffers must be device memory");
@@ -151,7 +151,12 @@ extern "C" pf_status pf_index_search_noalloc(pf_index* ix, const float* queries,
     int32_t herr = 0;
     if ((e = cudaMemcpy(&herr, ix->dev_error, sizeof(herr), cudaMemcpyDeviceToHost)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpy");
-    if (herr) return reject(PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out");
+    if (herr) {
+      // clear the word (a memset allocates nothing), so that the next call on
+      // this index is not reported as timed out too
+      if ((e = cudaMemset(ix->dev_error, 0, sizeof(int32_t))) != cudaSuccess) return cuda_fail(e, "cudaMemset");
+      return reject(PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out");
+    }
     if (flags & 1) return reject(PF_ERR_INVALID_ARG, "some k not in [1, k_max] or recall not in (0, 1)");
     return PF_OK;
   } catch (...) {

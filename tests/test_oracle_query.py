@@ -91,7 +91,7 @@ def test_prefix_blocks_with_unit_segments(orc):
         tr = res["trace"][t, : res["trace_len"][t]]
         seen = {}
         for key, pid in tr:
-            seen.setdefault((int(key) >> 24, int(key) & 0xFFFFFF), []).append(int(pid))
+            seen.setdefault(((int(key) >> 24) & 0x3F, int(key) & 0xFFFFFF), []).append(int(pid))
         depths = sorted({k[0] for k in seen}, reverse=True)
         stop = int(res["stats"]["stop_depth"][t])
         for j in range(ix.L):
@@ -118,7 +118,7 @@ def test_segments_extend_one_side_in_whole_segments(orc):
         tr = res["trace"][t, : res["trace_len"][t]]
         by = {}
         for key, pid in tr:
-            by.setdefault((int(key) >> 24, int(key) & 0xFFFFFF), []).append(int(pid))
+            by.setdefault(((int(key) >> 24) & 0x3F, int(key) & 0xFFFFFF), []).append(int(pid))
         for (i, j), pids in by.items():
             pos = np.sort(pos_of[j, pids])
             runs = np.split(pos, np.nonzero(np.diff(pos) != 1)[0] + 1)
