@@ -13,12 +13,19 @@ launch shape is tuned on a separate query set of the same distribution
 would: two captured searches (pf_search_plan_run, one CUDA graph each, with
 their own buffers and a second 10,000-query batch of the same distribution)
 alternate on two streams, so one batch's hashing and first queries fill the
-SMs that the other batch's last queries leave idle.  The same step run one at
-a time (pf_index_search, L2 flushed between steps) is reported under
-"sequential"; the kernel times of the roofline come from it.
+SMs that the other batch's last queries leave idle.  Every mode (plain float32
+scoring, plain bfloat16 scoring, learned start + bfloat16) is measured on the
+same two protocols: two batches in flight ("in_flight") and one batch at a
+time through pf_index_search with L2 flushed between steps ("sequential", whose
+kernel times give the roofline); recall is measured on both batches.  "e2e"
+goes through the library's host-buffer paths with page-locked host memory:
+plans bound to host buffers (their graphs copy inputs in and outputs out),
+two in flight, and pf_index_search given host pointers, one at a time.
+"cpu_baseline" is the CPU oracle on its own index over all the points with
+the same L (its build is timed apart), on a bounded sample of the queries.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--mode bf16|fp32]
-  python bench.py --impl reference ...   (times the CPU oracle on a sample)
+  python bench.py --impl reference ...   (times the CPU oracle on a sample of the queries)
   python bench.py --workload paper-synthetic-n1m-d300 ...
 
 The second workload is the paper's SYNTHETIC construction (Sec. 5): 10^6
@@ -61,7 +68,6 @@ METRIC = METRICS[WORKLOAD]
 PAPER_SYNTHETIC_QPS, PAPER_SYNTHETIC_RECALL = 360.3, 0.971
 UNIT = "queries/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB of L2
-CPU_SAMPLE_N = 20_000
 
 
 def parse():
@@ -206,14 +212,6 @@ def queries(w, m: int, purpose: str, rank: int):
     return datagen.vmf_mixture(m, w["d"], w["components"], w["kappa"], seed=0, purpose=purpose, stream=rank)
 
 
-def cpu_sample_points(w, X):
-    """The points the CPU oracle indexes: the first CPU_SAMPLE_N (SYNTHETIC: the
-    first CPU_SAMPLE_N - 1 and its last point, every query's neighbour)."""
-    if w["name"] == "paper-synthetic-n1m-d300":
-        return np.concatenate([X[:CPU_SAMPLE_N - 1], X[-1:]])
-    return X[:CPU_SAMPLE_N]
-
-
 def max_over_ranks(seconds: float, dist=None, device=None) -> float:
     """The slowest rank's time (the job ends when its last rank does); the
     local value without a process group."""
@@ -261,17 +259,23 @@ def algorithmic_bytes(st, L, n, d, k, mode):
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_sample(w, X, Qs, L, k, recall, q_target_s=2.0):
-    """Oracle index over a CPU_SAMPLE_N-point sample of the same data with the
-    same number of repetitions; returns (index, queries, query count per step)."""
+def oracle_index(X, L):
+    """The oracle's index over all the workload's points with the GPU's L and
+    the same seed; returns (index, build seconds)."""
     import oracle
 
-    oix = oracle.OracleIndex(cpu_sample_points(w, X), oracle.CROSSPOLYTOPE, L=L, seed=0)
     t = time.perf_counter()
-    oix.search(Qs[:64], k, recall)
-    per_q = (time.perf_counter() - t) / 64
-    nq = int(max(64, min(Qs.shape[0], q_target_s / max(per_q, 1e-6))))
-    return oix, nq
+    oix = oracle.OracleIndex(X, oracle.CROSSPOLYTOPE, L=L, seed=0)
+    return oix, time.perf_counter() - t
+
+
+def oracle_queries_for(oix, Qs, k, recall, seconds, probe=16):
+    """How many of the queries the oracle answers in about `seconds` (timed on
+    `probe` of them first)."""
+    t = time.perf_counter()
+    oix.search(Qs[:probe], k, recall)
+    per_q = (time.perf_counter() - t) / probe
+    return int(max(probe, min(Qs.shape[0], seconds / max(per_q, 1e-9))))
 
 
 def cpu_cores():
@@ -281,28 +285,32 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(w, X, Qs, L, k, recall, q_target_s=15.0):
-    """The oracle timed on the host cores on a sample of the workload (about
-    q_target_s of queries), and on one thread as the paper measures (Sec. 5)."""
+def cpu_baseline(w, X, Qs, L, k, recall, q_target_s=15.0, single_target_s=10.0):
+    """The oracle timed on the host cores: its index over all n points with the
+    GPU's L (build timed separately), a bounded sample of the queries (about
+    q_target_s), and one thread answering queries one after another as the paper
+    measures (Sec. 5)."""
     import oracle
 
-    oix, nq = oracle_sample(w, X, Qs, L, k, recall, q_target_s=q_target_s)
+    oix, build_s = oracle_index(X, L)
+    nq = oracle_queries_for(oix, Qs, k, recall, q_target_s)
     t = time.perf_counter()
     oix.search(Qs[:nq], k, recall)
     el = time.perf_counter() - t
     cpu = {"value": nq / el, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-           "sample": f"oracle index over a {CPU_SAMPLE_N}-point sample of the {X.shape[0]} points (same data and "
-                     f"seed, L={L}); {nq} queries; all host cores"}
-    n1 = max(8, nq // max(1, cpu_cores()))
+           "sample": f"oracle index over all {X.shape[0]:,} points (same data, seed and L={L}; built in "
+                     f"{build_s:.1f} s, not timed); the first {nq} of the {Qs.shape[0]:,} queries; all host cores",
+           "build_s": build_s}
     oracle.set_threads(1)
     try:
+        n1 = oracle_queries_for(oix, Qs, k, recall, single_target_s, probe=4)
         t = time.perf_counter()
         oix.search(Qs[:n1], k, recall)
         el1 = time.perf_counter() - t
     finally:
         oracle.set_threads(0)
     cpu["single_thread"] = {"value": n1 / el1, "unit": UNIT, "cores": 1,
-                            "sample": f"the same index; {n1} queries one after another"}
+                            "sample": f"the same index; the first {n1} queries one after another on one thread"}
     return cpu
 
 
@@ -313,8 +321,12 @@ def run_reference(args):
     w, X, Qs = workload(0, args.points, args.queries, args.budget, args.workload)
     import oracle
 
-    L = oracle.budget_L(oracle.CROSSPOLYTOPE, X.shape[0], X.shape[1], 32, w["budget"])
-    oix, nq = oracle_sample(w, X, Qs, L, w["k"], args.recall)
+    # the GPU library's L for this budget (the library caps L at 2,048)
+    L = min(2048, oracle.budget_L(oracle.CROSSPOLYTOPE, X.shape[0], X.shape[1], 32, w["budget"]))
+    oix, build_s = oracle_index(X, L)
+    # each step answers a bounded sample of the queries, sized so that all
+    # warm-up and timed steps take about a minute
+    nq = oracle_queries_for(oix, Qs, w["k"], args.recall, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         oix.search(Qs[:nq], w["k"], args.recall)
     t = time.perf_counter()
@@ -322,17 +334,54 @@ def run_reference(args):
         oix.search(Qs[:nq], w["k"], args.recall)
     el = time.perf_counter() - t
     v = nq * args.steps / el
-    sample = (f"oracle index over a {CPU_SAMPLE_N}-point sample of the {X.shape[0]} points (same data, L={L}, "
-              f"same seed), {nq} queries per step")
+    sample = (f"oracle index over all {X.shape[0]:,} points (same data, seed and L={L}; built in {build_s:.1f} s, "
+              f"not timed); the first {nq} of the {Qs.shape[0]:,} queries per step; all host cores")
     print(json.dumps({
-        "impl": "reference", "metric": METRICS[args.workload], "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
-        "config": {"workload": args.workload, "n": int(X.shape[0]), "d": int(X.shape[1]), "k": w["k"],
+        "impl": "reference", "metric": METRICS[args.workload], "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n": int(X.shape[0]), "d": int(X.shape[1]), "k": w["k"], "L": L,
                    "recall_target": args.recall, "sample": sample},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample,
+                         "build_s": build_s},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def timed_sequential(torch, run, flush, stream, steps):
+    """ms of `steps` runs one at a time, L2 flushed before each (outside the
+    events), CUDA events on the launching stream."""
+    tot = 0.0
+    for _ in range(steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot
+
+
+def timed_in_flight(torch, plans, streams, steps):
+    """ms of `steps` plan runs alternating over two streams (two batches in
+    flight), from an event on the first stream to the join of both."""
+    e0, e1, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True), torch.cuda.Event()
+    e0.record(streams[0])
+    streams[1].wait_event(e0)
+    for i in range(steps):
+        plans[i % 2].run(streams[i % 2])
+    eb.record(streams[1])
+    streams[0].wait_event(eb)
+    e1.record(streams[0])
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def recall_of(sims, kth):
+    """Tie-tolerant recall: returned similarities >= the true k-th one."""
+    return float((sims >= kth[:, None] - 1e-6).float().mean().item())
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -357,23 +406,22 @@ def main():
     pf.build()
     dev = torch.device("cuda", local)
     w, X, Qs = workload(rank, args.points, args.queries, args.budget, args.workload)
+    Qs2 = queries(w, Qs.shape[0], "queries2", rank)  # the second batch in flight
     Q, k = Qs.shape[0], w["k"]
     Xd = torch.from_numpy(X).to(dev)
-    Qd = torch.from_numpy(Qs).to(dev)
+    Qd = [torch.from_numpy(Qs).to(dev), torch.from_numpy(Qs2).to(dev)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ix = pf.Index(Xd, "crosspolytope", budget_bytes=w["budget"], seed=0)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
-    kth = brute_force_kth(torch, Xd, Qd, k)
+    kth = [brute_force_kth(torch, Xd, q, k) for q in Qd]
     del Xd
-    kq = torch.full((Q,), k, dtype=torch.int32, device=dev)
-    rq = torch.full((Q,), args.recall, dtype=torch.float64, device=dev)
-    ids = torch.empty((Q, k), dtype=torch.int32, device=dev)
-    sims = torch.empty((Q, k), dtype=torch.float32, device=dev)
-    st = torch.empty((Q, pf.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    kq = [torch.full((Q,), k, dtype=torch.int32, device=dev) for _ in range(2)]
+    rq = [torch.full((Q,), args.recall, dtype=torch.float64, device=dev) for _ in range(2)]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+    streams = [stream, torch.cuda.Stream(dev)]
 
     train_report, train_s = None, None
     if args.mode == "learned" or not args.no_compare:
@@ -393,188 +441,175 @@ def main():
         tune_report = ix.tune(torch.from_numpy(Qtune).to(dev), k, args.recall,
                               scoring="fp32" if args.mode == "fp32" else "bf16", learned=args.mode == "learned")
 
-    def run_mode(mode, timing=False):
-        ix.search(Qd, kq, rq, k_max=k, scoring="fp32" if mode == "fp32" else "bf16", out_ids=ids, out_sims=sims,
-                  stats=st, timing=timing, learned=mode == "learned")
+    def opts_of(mode):
+        return ("fp32" if mode == "fp32" else "bf16"), mode == "learned"
 
-    def step(timing=False):
-        run_mode(args.mode, timing)
+    def outputs():
+        return (torch.empty((Q, k), dtype=torch.int32, device=dev), torch.empty((Q, k), dtype=torch.float32, device=dev),
+                torch.empty((Q, pf.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev))
 
-    for _ in range(args.warmup):
-        step()
-    clocks = ClockSampler(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    total_ms, kernel_ms, hash_ms = 0.0, 0.0, 0.0
-    for _ in range(args.steps):
-        flush.fill_(1)  # evict L2 between steps (outside the timed events)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step(timing=True)
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        h, kern, _ = ix.last_timing()
-        kernel_ms += kern
-        hash_ms += h
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    t_max = max_over_ranks(total_ms / 1e3, dist, dev)
-    if dist:
-        dist.barrier()
-    value = whole_job_rate(Q, world, args.steps, t_max)
-    stats = pf.stats_to_numpy(st)
-    recall = float((sims >= kth[:, None] - 1e-6).float().mean().item())
+    def measure(mode, steps, headline=False):
+        """One mode on the same protocols: one batch at a time through
+        pf_index_search (L2 flushed between steps), and two batches in flight
+        through two captured plans.  Recall and per-query counts of both
+        batches."""
+        sc, lr = opts_of(mode)
+        o1, o2 = outputs(), outputs()
 
-    # the other modes, same queries, same timing protocol (fewer steps)
+        def run(timing=False):
+            ix.search(Qd[0], kq[0], rq[0], k_max=k, scoring=sc, out_ids=o1[0], out_sims=o1[1], stats=o1[2],
+                      timing=timing, learned=lr)
+
+        kern = {"kernel_ms": 0.0, "hash_ms": 0.0}
+
+        def run_timed():
+            run(timing=True)
+            h, kn, _ = ix.last_timing()
+            kern["kernel_ms"] += kn
+            kern["hash_ms"] += h
+
+        for _ in range(max(3, args.warmup if headline else 2)):
+            run()
+        sampler = ClockSampler(local)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        ms = timed_sequential(torch, run_timed, flush, stream, steps)
+        clk_seq = sampler.stop()
+        t_seq = max_over_ranks(ms / 1e3, dist, dev)
+        res = {"sequential": {"value": whole_job_rate(Q, world, steps, t_seq), "ms_per_step": t_seq / steps * 1e3,
+                              "l2": "flushed between steps (512 MiB write)", "clocks": clk_seq,
+                              "kernel_ms": kern["kernel_ms"] / steps, "query_hash_ms": kern["hash_ms"] / steps}}
+        stats = [pf.stats_to_numpy(o1[2])]
+        sims = [o1[1]]
+        if not args.no_graph:
+            pa = ix.plan(Qd[0], kq[0], rq[0], *outputs()[:2], k_max=k, scoring=sc, learned=lr)
+            pb = ix.plan(Qd[1], kq[1], rq[1], o2[0], o2[1], k_max=k, stats=o2[2], scoring=sc, learned=lr)
+            plans = [pa, pb]
+            try:
+                for _ in range(max(3, args.warmup)):
+                    for p_, s_ in zip(plans, streams):
+                        p_.run(s_)
+                torch.cuda.synchronize()
+                sampler = ClockSampler(local)
+                if dist:
+                    dist.barrier()
+                torch.cuda.synchronize()
+                sampler.start()
+                ms = timed_in_flight(torch, plans, streams, steps)
+                clk_fl = sampler.stop()
+                for p_, s_ in zip(plans, streams):
+                    p_.check(s_)
+                # the captured search of batch 1 returns what pf_index_search returned
+                assert torch.equal(pa._keep[3], o1[0]) and torch.equal(pa._keep[4], o1[1])
+            finally:
+                for p_ in plans:
+                    p_.close()
+            t_fl = max_over_ranks(ms / 1e3, dist, dev)
+            res["in_flight"] = {"value": whole_job_rate(Q, world, steps, t_fl), "ms_per_step": t_fl / steps * 1e3,
+                                "l2": (f"inputs larger than L2 ({w['budget'] / 2**30:.0f} GiB index streamed every "
+                                       f"step; two different {Q:,}-query batches alternate)"),
+                                "clocks": clk_fl}
+            stats.append(pf.stats_to_numpy(o2[2]))
+            sims.append(o2[1])
+        res["recall"] = [recall_of(s_, kth[b]) for b, s_ in enumerate(sims)]
+        allst = np.concatenate(stats)
+        res["per_query"] = {f: float(allst[f].mean()) for f in ("start_depth", "stop_depth", "rounds", "retrieved",
+                                                                "passed_filter", "scored", "reranked")}
+        res["_batch1"] = (o1, stats[0])
+        return res
+
+    head = measure(args.mode, args.steps, headline=True)
     compare = {}
     if not args.no_compare:
         for mode in ("fp32", "bf16", "learned"):
-            if mode == args.mode:
-                continue
-            for _ in range(2):
-                run_mode(mode)
-            tot = 0.0
-            nsteps = max(3, args.steps // 2)
-            for _ in range(nsteps):
-                flush.fill_(1)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                run_mode(mode)
-                e1.record(stream)
-                e1.synchronize()
-                tot += e0.elapsed_time(e1)
-            ms = pf.stats_to_numpy(st)
-            compare[mode] = {"value": Q * nsteps / (tot / 1e3), "ms_per_step": tot / nsteps,
-                             "recall": float((sims >= kth[:, None] - 1e-6).float().mean().item()),
-                             "rounds": float(ms["rounds"].mean()), "retrieved": float(ms["retrieved"].mean()),
-                             "scored": float(ms["scored"].mean())}
-        run_mode(args.mode)  # leave the headline mode's outputs in place
+            if mode != args.mode:
+                r = measure(mode, max(3, args.steps // 2))
+                r.pop("_batch1")
+                compare[mode] = r
+    (ids1, sims1, _), stats1 = head.pop("_batch1")
 
-    # the headline: two batches in flight (two captured plans on two streams)
-    pipe, clk_pipe, plans = None, None, None
-    sc, lr = ("fp32" if args.mode == "fp32" else "bf16"), args.mode == "learned"
-    if not args.no_graph:
-        Qs2 = queries(w, Q, "queries2", rank)
-        qdev = [Qd, torch.from_numpy(Qs2).to(dev)]
-        kdev = [kq, kq.clone()]
-        rdev = [rq, rq.clone()]
-        outs = [(torch.empty_like(ids), torch.empty_like(sims)) for _ in range(2)]
-        plans = [ix.plan(qdev[j], kdev[j], rdev[j], outs[j][0], outs[j][1], k_max=k, scoring=sc, learned=lr)
-                 for j in range(2)]
-        streams = [stream, torch.cuda.Stream(dev)]
-    try:
-        if plans:
-            for _ in range(max(3, args.warmup)):
-                for p, st_ in zip(plans, streams):
-                    p.run(st_)
-            torch.cuda.synchronize()
-            sampler = ClockSampler(local)
-            if dist:
-                dist.barrier()
-            torch.cuda.synchronize()
-            sampler.start()
-            e0, e1, eb = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-                          torch.cuda.Event())
-            e0.record(streams[0])
-            streams[1].wait_event(e0)
-            for i in range(args.steps):
-                plans[i % 2].run(streams[i % 2])
-            eb.record(streams[1])
-            streams[0].wait_event(eb)
-            e1.record(streams[0])
-            e1.synchronize()
-            clk_pipe = sampler.stop()
-            ms = e0.elapsed_time(e1)
-            for p, st_ in zip(plans, streams):
-                p.check(st_)
-            # the first batch's outputs are those of the plain search
-            assert torch.equal(outs[0][0], ids) and torch.equal(outs[0][1], sims)
-            t_pipe = max_over_ranks(ms / 1e3, dist, dev)
-            pipe = {"value": whole_job_rate(Q, world, args.steps, t_pipe), "ms_per_step": t_pipe / args.steps * 1e3}
 
-        # end to end with pinned host buffers: every step copies its queries, k
-        # and recall in and its ids and similarities out (with two batches in
-        # flight when the plans exist, else through pf_index_search)
-        e2e = None
-        if not args.no_e2e:
-            hq = [torch.from_numpy(Qs).pin_memory()]
-            if plans:
-                hq.append(torch.from_numpy(Qs2).pin_memory())
-            nb = len(hq)
-            hk = [torch.full((Q,), k, dtype=torch.int32).pin_memory() for _ in range(nb)]
-            hr = [torch.full((Q,), args.recall, dtype=torch.float64).pin_memory() for _ in range(nb)]
-            hi = [torch.empty((Q, k), dtype=torch.int32).pin_memory() for _ in range(nb)]
-            hs = [torch.empty((Q, k), dtype=torch.float32).pin_memory() for _ in range(nb)]
+    # end to end through the library's own host-buffer paths, page-locked host
+    # memory: every step copies its queries, k and recall in and its ids and
+    # similarities out inside the timed region
+    sc, lr = opts_of(args.mode)
+    e2e = None
+    if not args.no_e2e:
+        hq = [torch.from_numpy(Qs).pin_memory(), torch.from_numpy(Qs2).pin_memory()]
+        hk = [torch.full((Q,), k, dtype=torch.int32).pin_memory() for _ in range(2)]
+        hr = [torch.full((Q,), args.recall, dtype=torch.float64).pin_memory() for _ in range(2)]
+        hi = [torch.empty((Q, k), dtype=torch.int32).pin_memory() for _ in range(2)]
+        hs = [torch.empty((Q, k), dtype=torch.float32).pin_memory() for _ in range(2)]
+        h2d = int(Q * X.shape[1] * 4 + Q * 4 + Q * 8)
+        d2h = int(Q * k * 8)
 
-            def e2e_step(i):
-                j = i % nb
-                if not plans:
-                    ix.search(hq[0], hk[0], hr[0], k_max=k, scoring=sc, out_ids=hi[0], out_sims=hs[0], learned=lr)
-                    return
-                with torch.cuda.stream(streams[j]):
-                    qdev[j].copy_(hq[j], non_blocking=True)
-                    kdev[j].copy_(hk[j], non_blocking=True)
-                    rdev[j].copy_(hr[j], non_blocking=True)
-                    plans[j].run(streams[j])
-                    hi[j].copy_(outs[j][0], non_blocking=True)
-                    hs[j].copy_(outs[j][1], non_blocking=True)
-
-            for i in range(2 * nb):
-                e2e_step(i)
+        def wall(step, steps):
+            for i in range(4):
+                step(i)
             torch.cuda.synchronize()
             if dist:
                 dist.barrier()
             t = time.perf_counter()
-            for i in range(args.steps):
-                e2e_step(i)
+            for i in range(steps):
+                step(i)
             torch.cuda.synchronize()
-            el = max_over_ranks(time.perf_counter() - t, dist, dev)
-            if plans:
-                for p, st_ in zip(plans, streams):
-                    p.check(st_)
-            assert torch.equal(hi[0], ids.cpu()) and torch.equal(hs[0], sims.cpu())
-            e2e = {"value": whole_job_rate(Q, world, args.steps, el), "unit": UNIT,
-                   "h2d_bytes_per_step": int(Q * X.shape[1] * 4 + Q * 4 + Q * 8),
-                   "d2h_bytes_per_step": int(Q * k * 8),
-                   "how": ("two batches in flight (captured plans, copies on their streams)" if plans
-                           else "pf_index_search with host buffers, one batch at a time")}
-    finally:
-        if plans:
-            for p in plans:
-                p.close()
+            return max_over_ranks(time.perf_counter() - t, dist, dev)
+
+        # one batch at a time: pf_index_search given the host pointers
+        el = wall(lambda i: ix.search(hq[0], hk[0], hr[0], k_max=k, scoring=sc, out_ids=hi[0], out_sims=hs[0],
+                                      learned=lr), args.steps)
+        assert torch.equal(hi[0], ids1.cpu()) and torch.equal(hs[0], sims1.cpu())
+        seq_e2e = {"value": whole_job_rate(Q, world, args.steps, el), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h, "how": "pf_index_search with page-locked host pointers, one batch "
+                                                     "at a time (the call copies in, searches, copies out)"}
+        e2e = seq_e2e
+        if not args.no_graph:
+            # two batches in flight: plans bound to the host buffers (each graph
+            # copies its inputs in and its outputs out on its own stream)
+            plans = [ix.plan(hq[b], hk[b], hr[b], hi[b], hs[b], k_max=k, scoring=sc, learned=lr) for b in range(2)]
+            try:
+                el = wall(lambda i: plans[i % 2].run(streams[i % 2]), args.steps)
+                for p_, s_ in zip(plans, streams):
+                    p_.check(s_)
+            finally:
+                for p_ in plans:
+                    p_.close()
+            assert torch.equal(hi[0], ids1.cpu()) and torch.equal(hs[0], sims1.cpu())
+            e2e = {"value": whole_job_rate(Q, world, args.steps, el), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h,
+                   "how": "pf_search_plan_run on plans bound to page-locked host buffers (each graph copies "
+                          "queries, k and recall in and ids and similarities out), two batches in flight on two "
+                          "streams", "one_at_a_time": seq_e2e}
 
     peak, peak_kind = measured_peaks()
-    per_q = algorithmic_bytes(stats, ix.L, ix.n, ix.d, k, "fp32" if args.mode == "fp32" else "bf16")
-    kern_s = kernel_ms / args.steps / 1e3
+    seq = head["sequential"]
+    per_q = algorithmic_bytes(stats1, ix.L, ix.n, ix.d, k, sc)
+    kern_s = seq["kernel_ms"] / 1e3
     achieved = per_q * Q / kern_s / 1e9
     traffic = search_kernel_traffic(args)
     roofline = {"bound": "hbm", "kernel": "search_kernel", "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "algorithmic_bytes_per_launch": per_q * Q, "kernel_ms": kern_s * 1e3,
-                "query_hash_ms": hash_ms / args.steps}
+                "algorithmic_bytes_per_launch": per_q * Q, "kernel_ms": seq["kernel_ms"],
+                "query_hash_ms": seq["query_hash_ms"]}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, X, Qs, ix.L, k, args.recall)
 
-    sequential = {"value": value, "ms_per_step": t_max / args.steps * 1e3,
-                  "l2": "flushed between steps (512 MiB write)", "clocks": clk}
-    if pipe:
-        value, ms_step, clk = pipe["value"], pipe["ms_per_step"], clk_pipe
-        l2 = (f"inputs larger than L2 ({w['budget'] / 2**30:.0f} GiB index streamed every step; two different "
-              f"{Q:,}-query batches alternate)")
+    fl = head.get("in_flight")
+    if fl:
+        value, ms_step, clk, l2 = fl["value"], fl["ms_per_step"], fl["clocks"], fl["l2"]
         pipelining = "two batches in flight: two captured plans (CUDA graphs) alternating on two streams"
     else:
-        ms_step = t_max / args.steps * 1e3
-        l2 = "flushed between steps (512 MiB write)"
+        value, ms_step, clk, l2 = seq["value"], seq["ms_per_step"], seq["clocks"], seq["l2"]
         pipelining = "none: one batch at a time"
+    recall = head["recall"][0]
     # the paper's figure exists for SYNTHETIC only (a single-thread CPU at recall
     # 0.971): the ratio is given when the measured recall reaches it
     vs_baseline = None
-    if args.workload == "paper-synthetic-n1m-d300" and recall >= PAPER_SYNTHETIC_RECALL:
+    if args.workload == "paper-synthetic-n1m-d300" and min(head["recall"]) >= PAPER_SYNTHETIC_RECALL:
         vs_baseline = value / PAPER_SYNTHETIC_QPS
     if rank == 0:
         line = {
@@ -585,16 +620,13 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "n": ix.n, "d": ix.d, "queries_per_gpu": Q, "k": k,
                        "recall_target": args.recall, "family": "crosspolytope", "budget_bytes": w["budget"],
-                       "L": ix.L, "scoring": "fp32" if args.mode == "fp32" else "bf16",
-                       "start_depth": "learned" if args.mode == "learned" else "plain",
-                       "l2": l2, "pipelining": pipelining,
-                       "parallelism": f"replica x{world}"},
-            "recall": recall, "build_s": build_s,
-            "per_query": {f: float(stats[f].mean()) for f in ("stop_depth", "rounds", "retrieved",
-                                                             "passed_filter", "scored", "reranked")},
+                       "L": ix.L, "scoring": sc, "start_depth": "learned" if args.mode == "learned" else "plain",
+                       "l2": l2, "pipelining": pipelining, "parallelism": f"replica x{world}"},
+            "recall": recall, "recall_per_batch": head["recall"], "build_s": build_s,
+            "per_query": head["per_query"],
             "gpu_launches": (5 if args.mode == "learned" else 4) * args.steps,
-            "compare": compare, "learned_train": train_report, "learned_train_s": train_s,
-            "search_shape": tune_report, "sequential": sequential,
+            "sequential": seq, "in_flight": fl, "compare": compare,
+            "learned_train": train_report, "learned_train_s": train_s, "search_shape": tune_report,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
         }
         print(json.dumps(line), flush=True)

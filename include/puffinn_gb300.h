@@ -139,8 +139,14 @@ typedef enum {
   PF_ARRAY_CP_TABLE = 7,   /* double [41][ell+1]: CP collision table (Sec. 4.3); absent for HP */
   PF_ARRAY_TABLE_SKETCHES = 8, /* uint64 [L][n]: sketch (j mod M) of the point at each position of repetition j;
                                   PF_SKETCH_PER_TABLE only */
-  PF_ARRAY_ROWS_F16 = 9        /* binary16 [n][d_pad]: normalised points; PF_ROWS_F16 only (PF_ARRAY_ROWS_F32 is
+  PF_ARRAY_ROWS_F16 = 9,       /* binary16 [n][d_pad]: normalised points; PF_ROWS_F16 only (PF_ARRAY_ROWS_F32 is
                                   then absent) */
+  /* the start-depth perceptron (after pf_learned_train; PF_ERR_NOT_TRAINED
+     before), F = d_pad + 64 features, H = 256 hidden units, C = K + 1 classes */
+  PF_ARRAY_MLP_F32 = 10,       /* float: W1 [H][F], b1 [H], W2 [C][H], b2 [C], one after another (the biases are
+                                  also what inference uses) */
+  PF_ARRAY_MLP_W1_BF16 = 11,   /* bfloat16 [F][H]: W1 rounded to nearest even, transposed, as inference reads it */
+  PF_ARRAY_MLP_W2_BF16 = 12    /* bfloat16 [C][H]: W2 rounded to nearest even, as inference reads it */
 } pf_array;
 
 /* Build the index over `points` ([n][d] row-major, host or device).
@@ -299,6 +305,11 @@ pf_status pf_index_set_shape(pf_index* index, int32_t unroll, int32_t warps, int
  * learned start (if opts->learned_start) and the search kernel are captured
  * once into a CUDA graph; pf_search_plan_run launches it (one graph launch,
  * asynchronous on `stream`), reading whatever the buffers hold at that time.
+ * Each buffer may be device memory or page-locked host memory
+ * (cudaHostAlloc / cudaHostRegister): for a host buffer the plan keeps a
+ * device copy, and its graph copies host inputs in before the search and host
+ * outputs out after it, on the run's stream (pageable host memory is
+ * rejected: it cannot be copied asynchronously inside a graph).
  * The plan owns its own workspace, so plans and plain searches of one index
  * do not share scratch; runs of one plan must not overlap.  A plan is bound to
  * the index's state at creation: while plans exist, pf_learned_train and
@@ -316,7 +327,7 @@ typedef struct {
 } pf_plan_io;
 /* opts: scoring, filter, learned_start (timing and opts->start_depth are
  * ignored: the start depths, if any, are io->start_depth).  Errors:
- * PF_ERR_INVALID_ARG (Q < 1, k_max outside [1, 128], a null or host pointer),
+ * PF_ERR_INVALID_ARG (Q < 1, k_max outside [1, 128], a null or pageable host pointer),
  * PF_ERR_NOT_TRAINED, PF_ERR_OOM, CUDA. */
 pf_status pf_search_plan_create(pf_index* index, int64_t Q, int32_t k_max, const pf_plan_io* io,
                                 const pf_search_opts* opts, pf_search_plan** out);
@@ -349,6 +360,20 @@ pf_status pf_index_selftest_timeout(pf_index* index, const float* queries, int64
  * setting they were captured with.  Errors: PF_ERR_INVALID_ARG (null index,
  * or an index hashed without the tensor-core kernel). */
 pf_status pf_index_selftest_hold(pf_index* index, int32_t hold);
+
+/* ---- Diagnostics of the search kernel's range pass (Sec. 4.2 "Retrieving
+ *      candidate points": the range of a repetition grows to the block of
+ *      codes sharing the first i bits with the query) ----
+ * With enable != 0, later searches of this index count how each range step
+ * was settled: counts[0] steps at prefix length <= 13 read from the 13-bit
+ * prefix table, counts[1] sides settled within the first four segment
+ * boundaries probed together, counts[2] sides that galloped past them.  Each
+ * call waits for the device, writes the counts since the previous call into
+ * counts (NULL: not read) and resets them; enable == 0 stops counting (not
+ * while search plans exist: they were captured with the counters).  The
+ * counters cost device atomics: leave them off outside tests.  Errors:
+ * PF_ERR_INVALID_ARG (null index, plans exist), PF_ERR_OOM, CUDA. */
+pf_status pf_index_count_range_paths(pf_index* index, int32_t enable, uint64_t* counts);
 
 /* Release an index (NULL is accepted).  Does nothing while search plans bound
  * to it exist (pf_last_error_message says so). */

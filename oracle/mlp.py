@@ -38,3 +38,20 @@ def loss_and_grads(X, y, W1, b1, W2, b2):
     dW1 = dpre.T @ X
     db1 = dpre.sum(axis=0)
     return loss, dW1, db1, dW2, db2
+
+
+def start_depths(X, W1, b1, W2, b2, tail, margin):
+    """The start depth the perceptron predicts for each row of features X:
+    with p = softmax(z) over the stop depths 0..C-1 and A[d] = sum_{c > d} p_c
+    (the predicted chance that the query stops deeper than d), q is the smallest
+    d with A[d] <= tail, and the start is min(C - 1, q + margin).  Returns the
+    starts and A (float64 throughout)."""
+    _, _, _, z = forward(X, np.zeros(np.asarray(X).shape[0], np.int64), W1, b1, W2, b2)
+    p = np.exp(z - z.max(axis=1, keepdims=True))
+    p /= p.sum(axis=1, keepdims=True)
+    C = p.shape[1]
+    A = np.zeros_like(p)
+    for d in range(C - 2, -1, -1):
+        A[:, d] = A[:, d + 1] + p[:, d + 1]
+    q = np.array([int(np.nonzero(A[i] <= tail)[0].min()) for i in range(p.shape[0])])
+    return np.minimum(C - 1, q + margin), A

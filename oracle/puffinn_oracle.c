@@ -135,6 +135,29 @@ static double dot64(const float* a, const float* x, int d) {
   return s;
 }
 
+/* out[r] = <A_r, x> in FP64 for the rows r = 0..nrows-1 of A ([nrows][d]), each
+ * sum formed in index order exactly as dot64 forms it; the rows' sums are
+ * independent and are simply advanced side by side. */
+static void dot64_rows(const float* A, int nrows, const float* x, int d, double* out) {
+  int r = 0;
+  for (; r + 4 <= nrows; r += 4) {
+    const float* a0 = A + (int64_t)r * d;
+    const float* a1 = a0 + d;
+    const float* a2 = a1 + d;
+    const float* a3 = a2 + d;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int i = 0; i < d; ++i) {
+      const double xi = (double)x[i];
+      s0 = s0 + (double)a0[i] * xi;
+      s1 = s1 + (double)a1[i] * xi;
+      s2 = s2 + (double)a2[i] * xi;
+      s3 = s3 + (double)a3[i] * xi;
+    }
+    out[r] = s0; out[r + 1] = s1; out[r + 2] = s2; out[r + 3] = s3;
+  }
+  for (; r < nrows; ++r) out[r] = dot64(A + (int64_t)r * d, x, d);
+}
+
 /* Sec. 2.2: HP bit = 1 iff <a, x> >= 0.  CP: the index c of the hyperplane
  * with the largest |<a_c, x>| and whether that projection is negative.
  * Reading: the l-bit CP value is (sign << (l-1)) | c with sign = [v_c < 0];
@@ -144,51 +167,124 @@ static double dot64(const float* a, const float* x, int d) {
 void orc_hash_one(int family, int L, int d, const float* A, const float* x, uint32_t* codes_out) {
   int ell, F, Kb, rows;
   orc_layout(family, d, &ell, &F, &Kb, &rows);
+  double* v = (double*)malloc(sizeof(double) * (size_t)(rows > d ? rows : d));
   for (int j = 0; j < L; ++j) {
     const float* Aj = A + (int64_t)j * rows * d;
     uint32_t code = 0;
     for (int f = 0; f < F; ++f) {
       uint32_t value;
       if (family == ORC_SIMHASH) {
-        value = dot64(Aj + (int64_t)f * d, x, d) >= 0.0 ? 1u : 0u;
+        dot64_rows(Aj + (int64_t)f * d, 1, x, d, v);
+        value = v[0] >= 0.0 ? 1u : 0u;
       } else {
+        dot64_rows(Aj + (int64_t)f * d * d, d, x, d, v); /* the d projections of function f */
         int best = 0;
         double best_abs = -1.0, best_v = 0.0;
-        for (int c = 0; c < d; ++c) {
-          double v = dot64(Aj + ((int64_t)f * d + c) * d, x, d);
-          if (fabs(v) > best_abs) { best_abs = fabs(v); best = c; best_v = v; }
-        }
+        for (int c = 0; c < d; ++c)
+          if (fabs(v[c]) > best_abs) { best_abs = fabs(v[c]); best = c; best_v = v[c]; }
         value = ((best_v < 0.0 ? 1u : 0u) << (ell - 1)) | (uint32_t)best;
       }
       code |= value << (32 - ell * (f + 1));
     }
     codes_out[j] = code;
   }
+  free(v);
 }
 
+/* v[r] = <row r, x> in FP64 for the rows of one table, the table given
+ * transposed (At[i][r] = (double)A[r][i]).  Each v[r] is summed in index order
+ * exactly as dot64 sums it; eight rows are advanced side by side. */
+#define ORC_ROW_BLOCK 8
+static void project_rows_t(const double* At, int rows, const float* x, int d, double* v) {
+  int r0 = 0;
+  for (; r0 + ORC_ROW_BLOCK <= rows; r0 += ORC_ROW_BLOCK) {
+    double acc[ORC_ROW_BLOCK] = {0.0};
+    for (int i = 0; i < d; ++i) {
+      const double xi = (double)x[i];
+      const double* a = At + (int64_t)i * rows + r0;
+      for (int u = 0; u < ORC_ROW_BLOCK; ++u) acc[u] = acc[u] + a[u] * xi;
+    }
+    for (int u = 0; u < ORC_ROW_BLOCK; ++u) v[r0 + u] = acc[u];
+  }
+  for (int r = r0; r < rows; ++r) {
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) s = s + At[(int64_t)i * rows + r] * (double)x[i];
+    v[r] = s;
+  }
+}
+
+/* The code of one table from its rows' projections v (the decisions of
+ * orc_hash_one). */
+static uint32_t code_from_projections(int family, int ell, int F, int d, const double* v) {
+  uint32_t code = 0;
+  for (int f = 0; f < F; ++f) {
+    uint32_t value;
+    if (family == ORC_SIMHASH) {
+      value = v[f] >= 0.0 ? 1u : 0u;
+    } else {
+      const double* vf = v + (int64_t)f * d;
+      int best = 0;
+      double best_abs = -1.0, best_v = 0.0;
+      for (int c = 0; c < d; ++c)
+        if (fabs(vf[c]) > best_abs) { best_abs = fabs(vf[c]); best = c; best_v = vf[c]; }
+      value = ((best_v < 0.0 ? 1u : 0u) << (ell - 1)) | (uint32_t)best;
+    }
+    code |= value << (32 - ell * (f + 1));
+  }
+  return code;
+}
+
+/* The same codes as orc_hash_one, for n points: points are taken in blocks,
+ * and each table's rows are transposed to float64 once per block. */
 void orc_hash_codes(int family, int L, int d, const float* A, const float* x, int64_t n, uint32_t* codes) {
+  int ell, F, Kb, rows;
+  orc_layout(family, d, &ell, &F, &Kb, &rows);
+  const int64_t P = 256;
+  const int64_t nblocks = (n + P - 1) / P;
 #pragma omp parallel
   {
-    uint32_t* tmp = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)L);
-#pragma omp for schedule(dynamic, 16)
-    for (int64_t p = 0; p < n; ++p) {
-      orc_hash_one(family, L, d, A, x + p * d, tmp);
-      for (int j = 0; j < L; ++j) codes[(int64_t)j * n + p] = tmp[j];
+    double* At = (double*)malloc(sizeof(double) * (size_t)rows * (size_t)d);
+    double* v = (double*)malloc(sizeof(double) * (size_t)rows);
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t b = 0; b < nblocks; ++b) {
+      const int64_t p0 = b * P, p1 = (p0 + P < n) ? p0 + P : n;
+      for (int j = 0; j < L; ++j) {
+        const float* Aj = A + (int64_t)j * rows * d;
+        for (int r = 0; r < rows; ++r)
+          for (int i = 0; i < d; ++i) At[(int64_t)i * rows + r] = (double)Aj[(int64_t)r * d + i];
+        for (int64_t p = p0; p < p1; ++p) {
+          project_rows_t(At, rows, x + p * d, d, v);
+          codes[(int64_t)j * n + p] = code_from_projections(family, ell, F, d, v);
+        }
+      }
     }
-    free(tmp);
+    free(At);
+    free(v);
   }
 }
 
 /* Sec. 3.3 / 4.2: M sketches of 64 HP bits each. */
 void orc_sketches(int M, int d, const float* S, const float* x, int64_t n, uint64_t* sk) {
-#pragma omp parallel for schedule(dynamic, 64)
-  for (int64_t p = 0; p < n; ++p)
-    for (int m = 0; m < M; ++m) {
-      uint64_t w = 0;
-      for (int b = 0; b < 64; ++b)
-        if (dot64(S + (int64_t)(m * 64 + b) * d, x + p * d, d) >= 0.0) w |= (uint64_t)1 << b;
-      sk[(int64_t)m * n + p] = w;
+  const int rows = 64 * M;
+  double* St = (double*)malloc(sizeof(double) * (size_t)rows * (size_t)d);
+  for (int r = 0; r < rows; ++r)
+    for (int i = 0; i < d; ++i) St[(int64_t)i * rows + r] = (double)S[(int64_t)r * d + i];
+#pragma omp parallel
+  {
+    double* v = (double*)malloc(sizeof(double) * (size_t)rows);
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t p = 0; p < n; ++p) {
+      project_rows_t(St, rows, x + p * d, d, v);
+      for (int m = 0; m < M; ++m) {
+        uint64_t w = 0;
+        for (int b = 0; b < 64; ++b)
+          if (v[m * 64 + b] >= 0.0) w |= (uint64_t)1 << b;
+        sk[(int64_t)m * n + p] = w;
+      }
     }
+    free(v);
+  }
+  free(St);
 }
 
 /* Sec. 4.2: repetition j is the array of (code, pos) sorted by code; equal

@@ -26,7 +26,7 @@ STATUS = {0: "PF_OK", -1: "PF_ERR_INVALID_ARG", -2: "PF_ERR_BUDGET_TOO_SMALL", -
           -4: "PF_ERR_CUDA", -5: "PF_ERR_DEVICE_TIMEOUT", -6: "PF_ERR_NOT_TRAINED"}
 
 ARRAYS = {"rows_f32": 0, "rows_bf16": 1, "codes": 2, "ids": 3, "prefix": 4, "sketches": 5, "hash_rows": 6,
-          "cp_table": 7, "table_sketches": 8, "rows_f16": 9}
+          "cp_table": 7, "table_sketches": 8, "rows_f16": 9, "mlp_f32": 10, "mlp_w1_bf16": 11, "mlp_w2_bf16": 12}
 ROW_STORAGE = {"f32": 0, "f16": 1}
 SKETCH_LAYOUTS = {"table": 0, "point": 1}
 
@@ -119,6 +119,7 @@ def lib():
                 "pf_index_tune": (i32, [vp, vp, i64, i32, C.c_double, vp, vp, vp]),
                 "pf_index_selftest_timeout": (i32, [vp, vp, i64, vp]),
                 "pf_index_selftest_hold": (i32, [vp, i32]),
+                "pf_index_count_range_paths": (i32, [vp, i32, vp]),
                 "pf_index_set_shape": (i32, [vp, i32, i32, i32]),
                 "pf_search_plan_create": (i32, [vp, i64, i32, vp, vp, vp]),
                 "pf_search_plan_run": (i32, [vp, vp]),
@@ -329,6 +330,13 @@ class Index:
         PuffinnError(PF_ERR_DEVICE_TIMEOUT) when the bounded waits work."""
         _check(lib().pf_index_selftest_timeout(self._h, _ptr(queries), int(queries.shape[0]), _stream_ptr(stream)))
 
+    def count_range_paths(self, enable: bool = True):
+        """pf_index_count_range_paths: the counts since the last call as
+        {"prefix_table", "probed", "galloped"}; enable=False stops counting."""
+        c = (C.c_uint64 * 3)()
+        _check(lib().pf_index_count_range_paths(self._h, 1 if enable else 0, c))
+        return {"prefix_table": int(c[0]), "probed": int(c[1]), "galloped": int(c[2])}
+
     def selftest_hold(self, hold: bool):
         """pf_index_selftest_hold: withhold (True) or restore (False) the weight
         loads of every later tensor-core hashing launch of this index."""
@@ -348,7 +356,8 @@ class Index:
 
 
 class SearchPlan:
-    """A captured search (CUDA graph) bound to device tensors; run() launches it."""
+    """A captured search (CUDA graph) bound to device tensors or page-locked
+    host tensors (copied in and out inside the graph); run() launches it."""
 
     def __init__(self, index, queries, k, recall, out_ids, out_sims, *, k_max, stats, start_depth, opts):
         self._index = index

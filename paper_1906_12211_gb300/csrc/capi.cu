@@ -159,6 +159,7 @@ void destroy(pf_index* ix) {
   dfree(ix->cpP);
   dfree(ix->cos_tab);
   dfree(ix->dev_error);
+  dfree(ix->path_count);
   dfree(ix->mlp_w);
   dfree(ix->mlp_w1h);
   dfree(ix->mlp_w2h);
@@ -558,6 +559,23 @@ pf_status pf_index_array(const pf_index* ix, int32_t which, const void** ptr, ui
       *ptr = ix->cpP;
       *bytes = uint64_t(kAlphaSteps) * (ix->lay.ell + 1) * 8;
       break;
+    case PF_ARRAY_MLP_F32:
+    case PF_ARRAY_MLP_W1_BF16:
+    case PF_ARRAY_MLP_W2_BF16: {
+      if (!ix->mlp_trained) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
+      const uint64_t F = uint64_t(ix->mlp_F), H = uint64_t(kMlpHidden), C = uint64_t(ix->mlp_C);
+      if (which == PF_ARRAY_MLP_F32) {
+        *ptr = ix->mlp_w;
+        *bytes = (H * F + H + C * H + C) * 4;
+      } else if (which == PF_ARRAY_MLP_W1_BF16) {
+        *ptr = ix->mlp_w1h;
+        *bytes = F * H * 2;
+      } else {
+        *ptr = ix->mlp_w2h;
+        *bytes = C * H * 2;
+      }
+      break;
+    }
     default: return fail(PF_ERR_INVALID_ARG, "unknown array");
   }
   return PF_OK;
@@ -823,6 +841,29 @@ pf_status pf_index_selftest_timeout(pf_index* ix, const float* queries, int64_t 
   });
 }
 
+pf_status pf_index_count_range_paths(pf_index* ix, int32_t enable, uint64_t* counts) {
+  return guarded([&]() -> pf_status {
+    if (!ix) return fail(PF_ERR_INVALID_ARG, "null index");
+    PF_CK(cudaSetDevice(ix->device));
+    PF_CK(cudaDeviceSynchronize());
+    uint64_t c[3] = {0, 0, 0};
+    if (ix->path_count) {
+      PF_CK(cudaMemcpy(c, ix->path_count, sizeof(c), cudaMemcpyDeviceToHost));
+      PF_CK(cudaMemset(ix->path_count, 0, sizeof(c)));
+    }
+    if (counts)
+      for (int i = 0; i < 3; ++i) counts[i] = c[i];
+    if (enable && !ix->path_count) {
+      dalloc(&ix->path_count, 3);
+      PF_CK(cudaMemset(ix->path_count, 0, 3 * sizeof(unsigned long long)));
+    } else if (!enable && ix->path_count) {
+      if (ix->live_plans > 0) return fail(PF_ERR_INVALID_ARG, "search plans bound to the index exist");
+      dfree(ix->path_count);
+    }
+    return PF_OK;
+  });
+}
+
 pf_status pf_index_selftest_hold(pf_index* ix, int32_t hold) {
   return guarded([&]() -> pf_status {
     if (!ix) return fail(PF_ERR_INVALID_ARG, "null index");
@@ -962,7 +1003,9 @@ struct pf_search_plan {
   int64_t Q = 0;
   int k_max = 0;
   pf_search_opts opts{};
-  pf_plan_io io{};
+  pf_plan_io io{};   // the caller's buffers (device or page-locked host)
+  pf_plan_io dio{};  // the device buffers the kernels use: the caller's, or the plan's staging copies
+  unsigned char* stage[7] = {};  // staging of the host buffers, in pf_plan_io's field order
   pf_workspace ws;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -971,11 +1014,61 @@ struct pf_search_plan {
 namespace {
 
 // The captured sequence: the same steps as pf_index_search on device buffers.
+// Host buffer -> staging copy size in bytes, per pf_plan_io field.
+size_t io_bytes(const pf_search_plan* pl, int field) {
+  const size_t Q = size_t(pl->Q), km = size_t(pl->k_max);
+  switch (field) {
+    case 0: return Q * size_t(pl->ix->d) * sizeof(float);
+    case 1: return Q * sizeof(int32_t);
+    case 2: return Q * sizeof(double);
+    case 3: return Q * sizeof(int32_t);
+    case 4: return Q * km * sizeof(uint32_t);
+    case 5: return Q * km * sizeof(float);
+    default: return Q * sizeof(pf_query_stats);
+  }
+}
+
+void* io_field(pf_plan_io& io, int field) {
+  switch (field) {
+    case 0: return const_cast<float*>(io.queries);
+    case 1: return const_cast<int32_t*>(io.k);
+    case 2: return const_cast<double*>(io.recall);
+    case 3: return const_cast<int32_t*>(io.start_depth);
+    case 4: return io.out_ids;
+    case 5: return io.out_sims;
+    default: return io.stats;
+  }
+}
+
+void set_io_field(pf_plan_io& io, int field, void* p) {
+  switch (field) {
+    case 0: io.queries = static_cast<const float*>(p); break;
+    case 1: io.k = static_cast<const int32_t*>(p); break;
+    case 2: io.recall = static_cast<const double*>(p); break;
+    case 3: io.start_depth = static_cast<const int32_t*>(p); break;
+    case 4: io.out_ids = static_cast<uint32_t*>(p); break;
+    case 5: io.out_sims = static_cast<float*>(p); break;
+    default: io.stats = static_cast<pf_query_stats*>(p); break;
+  }
+}
+
+bool page_locked_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
 void plan_sequence(pf_search_plan* pl, cudaStream_t s) {
   pf_index* ix = pl->ix;
   pf_workspace& ws = pl->ws;
-  hash_queries_ws(ix, ws, pl->io.queries, pl->Q, s);
-  const int32_t* sd = pl->io.start_depth;
+  for (int f = 0; f <= 3; ++f)  // inputs held in host memory: copied in first
+    if (pl->stage[f]) PF_CK(cudaMemcpyAsync(pl->stage[f], io_field(pl->io, f), io_bytes(pl, f), cudaMemcpyHostToDevice, s));
+  const pf_plan_io& io = pl->dio;
+  hash_queries_ws(ix, ws, io.queries, pl->Q, s);
+  const int32_t* sd = io.start_depth;
   if (pl->opts.learned_start) {
     predict_ws(ix, ws, pl->Q, s);
     sd = ws.start;
@@ -985,24 +1078,27 @@ void plan_sequence(pf_search_plan* pl, cudaStream_t s) {
   a.qx = ws.qx;
   a.qcodes = ws.qcodes;
   a.qsk = ws.qsk;
-  a.k = pl->io.k;
-  a.recall = pl->io.recall;
+  a.k = io.k;
+  a.recall = io.recall;
   a.start = sd;
   a.k_max = pl->k_max;
   a.filter = pl->opts.filter ? 1 : 0;
   a.scoring = pl->opts.scoring;
-  a.out_ids = pl->io.out_ids;
-  a.out_sims = pl->io.out_sims;
-  a.stats = pl->io.stats;
+  a.out_ids = io.out_ids;
+  a.out_sims = io.out_sims;
+  a.stats = io.stats;
   a.counter = ws.counter;
   PF_CK(cudaMemsetAsync(ws.counter, 0, sizeof(int32_t) * 64, s));
   PF_CK(launch_search(ix, a, s));
+  for (int f = 4; f <= 6; ++f)  // outputs held in host memory: copied out last
+    if (pl->stage[f]) PF_CK(cudaMemcpyAsync(io_field(pl->io, f), pl->stage[f], io_bytes(pl, f), cudaMemcpyDeviceToHost, s));
 }
 
 void plan_release(pf_search_plan* pl) {
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
   if (pl->graph) cudaGraphDestroy(pl->graph);
   free_ws(pl->ws);
+  for (unsigned char*& p : pl->stage) dfree(p);
   delete pl;
 }
 
@@ -1020,9 +1116,15 @@ pf_status pf_search_plan_create(pf_index* ix, int64_t Q, int32_t k_max, const pf
     PF_CK(cudaSetDevice(ix->device));
     const void* need[] = {io->queries, io->k, io->recall, io->out_ids, io->out_sims};
     for (const void* p : need)
-      if (!p || !on_device(p)) return fail(PF_ERR_INVALID_ARG, "plan buffers must be device pointers");
-    if ((io->start_depth && !on_device(io->start_depth)) || (io->stats && !on_device(io->stats)))
-      return fail(PF_ERR_INVALID_ARG, "plan buffers must be device pointers");
+      if (!p) return fail(PF_ERR_INVALID_ARG, "null plan buffer");
+    const void* all[] = {io->queries, io->k, io->recall, io->start_depth, io->out_ids, io->out_sims, io->stats};
+    bool host[7] = {};
+    for (int f = 0; f < 7; ++f) {
+      if (!all[f] || on_device(all[f])) continue;
+      if (!page_locked_host(all[f]))
+        return fail(PF_ERR_INVALID_ARG, "plan buffers must be device memory or page-locked host memory");
+      host[f] = true;
+    }
     pf_search_opts o;
     pf_search_opts_default(&o);
     if (opts) o = *opts;
@@ -1036,8 +1138,14 @@ pf_status pf_search_plan_create(pf_index* ix, int64_t Q, int32_t k_max, const pf
     pl->k_max = k_max;
     pl->opts = o;
     pl->io = *io;
+    pl->dio = *io;
     cudaStream_t cs = nullptr;
     try {
+      for (int f = 0; f < 7; ++f)
+        if (host[f]) {
+          dalloc(&pl->stage[f], io_bytes(pl, f));
+          set_io_field(pl->dio, f, pl->stage[f]);
+        }
       alloc_ws(ix, pl->ws, size_t(Q), size_t(k_max));
       PF_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
       PF_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));

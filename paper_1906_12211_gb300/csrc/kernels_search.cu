@@ -61,6 +61,7 @@ cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t 
   P.out_sims = a.out_sims;
   P.stats = a.stats;
   P.counter = a.counter;
+  P.path_count = ix->path_count;
   const SearchShape sh = a.shape.unroll ? a.shape : ix->search_shape;
   const int U = sh.unroll == 4 ? 4 : 8, QW = sh.warps == 8 ? 8 : 4;
   const size_t smem = search_smem(P.d_pad, P.L, P.M, P.k_max, U, QW);

@@ -121,6 +121,7 @@ struct pf_index {
   pf::SearchShape search_shape{8, 0, 4};  // chosen by pf_index_tune (default: 8 positions per lane, full occupancy)
   int live_plans = 0;                   // captured search plans bound to this index
   int hold_weight_loads = 0;            // diagnostics only (pf_index_selftest_timeout)
+  unsigned long long* path_count = nullptr;  // diagnostics only (pf_index_count_range_paths)
   pf_workspace ws;
   // start-depth model: params = [W1 (H x F) | b1 (H) | W2 (C x H) | b2 (C)], float32
   int mlp_trained = 0, mlp_F = 0, mlp_C = 0;

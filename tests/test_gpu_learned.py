@@ -94,3 +94,35 @@ def test_not_trained_is_an_error():
     with pytest.raises(pf.PuffinnError) as e:
         g.search(torch.randn(3, 16, device=DEV), 5, 0.9, learned=True)
     assert e.value.status == -6
+
+
+def test_predict_forward_equals_float64_oracle(trained, orc):
+    """The bfloat16 inference kernel against the float64 forward of oracle/mlp.py
+    run with the same rounded weights: features = the normalised query (zero
+    padded to d_pad) and the 64 bits of its sketch 0 as +-1.  Start depths agree
+    except where the predicted tail mass sits within float32 rounding of the
+    0.05 threshold."""
+    ix, o, _, _, Q = trained
+    qd = torch.from_numpy(Q).to(DEV)
+    got = ix.learned_predict(qd).cpu().numpy()
+    F, H, C = ix.d_pad + 64, 256, ix.Kb + 1
+    w32 = ix.array("mlp_f32", device="cpu").numpy().view(np.float32)
+    assert w32.size == H * F + H + C * H + C
+    b1 = w32[H * F:H * F + H].astype(np.float64)
+    b2 = w32[H * F + H + C * H:].astype(np.float64)
+    bf = lambda name, shape: (ix.array(name, device="cpu").view(torch.bfloat16).float().numpy()
+                              .astype(np.float64).reshape(shape))
+    W1 = bf("mlp_w1_bf16", (F, H)).T  # stored transposed
+    W2 = bf("mlp_w2_bf16", (C, H))
+    # the rounded weights are the float32 master weights rounded to nearest even
+    W1_32 = w32[:H * F].reshape(H, F)
+    assert np.array_equal(W1, torch.from_numpy(W1_32).to(torch.bfloat16).float().numpy().astype(np.float64))
+    qn, _, qsk = o.hash_queries(Q)
+    X = np.zeros((Q.shape[0], F))
+    X[:, :ix.d] = qn
+    bits = (qsk[:, 0][:, None] >> np.arange(64, dtype=np.uint64)) & np.uint64(1)
+    X[:, ix.d_pad:] = np.where(bits == 1, 1.0, -1.0)
+    want, A = mlp_oracle.start_depths(X, W1, b1, W2, b2, 0.05, 6)
+    near = np.any(np.abs(A - 0.05) < 1e-4, axis=1)
+    assert np.all((got == want) | near), np.nonzero((got != want) & ~near)
+    assert np.mean(got == want) >= 0.98

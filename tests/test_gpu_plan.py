@@ -126,3 +126,44 @@ def test_tuning_changes_no_result(idx, scoring, learned):
     for f in sb.dtype.names:
         if f != "reranked":
             assert np.array_equal(sb[f], sa[f]), f
+
+
+@pytest.mark.parametrize("learned", [False, True])
+def test_plan_on_page_locked_host_buffers(idx, learned):
+    """A plan bound to page-locked host buffers copies its inputs in and its
+    outputs out inside its graph: after check() the host buffers hold what
+    pf_index_search returns; a second plan on another stream runs beside it."""
+    ix, k, r = idx["ix"], idx["k"], idx["r"]
+    hq = [idx["Q"][:300].cpu().pin_memory(), idx["Q"][300:].cpu().pin_memory()]
+    hk = [k.cpu().pin_memory() for _ in range(2)]
+    hr = [r.cpu().pin_memory() for _ in range(2)]
+    hi = [torch.empty((300, KMAX), dtype=torch.int32).pin_memory() for _ in range(2)]
+    hs = [torch.empty((300, KMAX), dtype=torch.float32).pin_memory() for _ in range(2)]
+    hst = [torch.zeros((300, pf.STATS_DTYPE.itemsize), dtype=torch.uint8).pin_memory() for _ in range(2)]
+    plans = [ix.plan(hq[b], hk[b], hr[b], hi[b], hs[b], k_max=KMAX, stats=hst[b], scoring="bf16", learned=learned)
+             for b in range(2)]
+    streams = [torch.cuda.current_stream(), torch.cuda.Stream(DEV)]
+    try:
+        for rep in range(2):
+            for b in range(2):
+                hi[b].fill_(7)
+            for b in range(2):
+                plans[b].run(streams[b])
+            for b in range(2):
+                plans[b].check(streams[b])
+            for b in range(2):
+                ref = ix.search(hq[b].to(DEV), k, r, k_max=KMAX, scoring="bf16", learned=learned, stats=True)
+                assert torch.equal(hi[b], ref[0].cpu()) and torch.equal(hs[b], ref[1].cpu())
+                assert torch.equal(hst[b], ref[2].cpu())
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_plan_rejects_pageable_host_buffers(idx):
+    ix, k, r = idx["ix"], idx["k"], idx["r"]
+    q = idx["Q"][:10].cpu()  # pageable
+    ids, sims, _ = _bufs(10)
+    with pytest.raises(pf.PuffinnError) as e:
+        ix.plan(q, k[:10], r[:10], ids, sims, k_max=KMAX)
+    assert e.value.status == -1

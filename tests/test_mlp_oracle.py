@@ -42,3 +42,26 @@ def test_gradients_match_finite_differences():
             flat[idx] = old
             fd = (lp - lm) / (2 * eps)
             assert abs(fd - G.reshape(-1)[idx]) <= 1e-7 + 1e-6 * abs(fd), (pi, idx, fd, G.reshape(-1)[idx])
+
+
+def test_start_depth_rule_hand_values():
+    """A model whose logits put (almost) all mass on stop depth c predicts
+    q = c, so the start is min(C - 1, c + margin); mass split 0.9 / 0.1 between
+    depths 3 and 7 puts q at 7 for a tail of 0.05 and at 3 for a tail of 0.2."""
+    from oracle import mlp
+
+    C, H, F = 12, 4, 3
+    X = np.ones((1, F))
+    W1 = np.zeros((H, F))
+    b1 = np.ones(H)  # h = 1 for every unit
+    W2 = np.zeros((C, H))
+    for c in (0, 4, 11):
+        b2 = np.full(C, -50.0)
+        b2[c] = 50.0
+        s, A = mlp.start_depths(X, W1, b1, W2, b2, 0.05, 6)
+        assert s[0] == min(C - 1, c + 6)
+        assert np.all(A[0, c:] < 1e-12) and np.all(A[0, :c] > 1 - 1e-12)
+    b2 = np.full(C, -np.inf)
+    b2[3], b2[7] = np.log(0.9), np.log(0.1)
+    assert mlp.start_depths(X, W1, b1, W2, b2, 0.05, 0)[0][0] == 7
+    assert mlp.start_depths(X, W1, b1, W2, b2, 0.2, 0)[0][0] == 3

@@ -304,3 +304,22 @@ def test_canonical_sim(orc):
     q = np.zeros(100, np.float32)
     q[[5, 37, 69]] = [1, 2, 3]
     assert orc.sim(q, q) == 14.0
+
+
+@pytest.mark.parametrize("family,d", [(0, 37), (1, 37), (1, 100)])
+def test_blocked_hashing_equals_one_point_at_a_time(orc, family, d):
+    """orc_hash_codes (blocks of points, rows transposed) returns exactly the
+    codes of orc_hash_one (one point, one row at a time): same sums in the same
+    order.  300 points span two blocks; 37 dimensions leave ragged row blocks."""
+    import ctypes as C
+
+    L, n = 7, 300
+    x = orc.normalize(datagen.gaussian(n, d, seed=8))
+    A = orc.gen_hash_params(12, family, L, d)
+    codes = orc.hash_codes(family, A, x)
+    one = np.zeros(L, np.uint32)
+    for p in range(n):
+        xp = np.ascontiguousarray(x[p])
+        orc.lib().orc_hash_one(family, L, d, A.ctypes.data_as(C.c_void_p), xp.ctypes.data_as(C.c_void_p),
+                               one.ctypes.data_as(C.c_void_p))
+        assert np.array_equal(codes[:, p], one), p
