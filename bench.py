@@ -84,6 +84,9 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other two modes")
     ap.add_argument("--recall", type=float, default=None,
                     help="recall target 1 - delta passed to the index (default: the workload's)")
+    ap.add_argument("--family", default="crosspolytope", choices=["crosspolytope", "fht"],
+                    help="crosspolytope: Gaussian hyperplanes (tensor cores); fht: the pseudo-random family of "
+                         "Sec. 4.3 (three Hadamard transforms)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(METRICS),
                     help="vmf1k-n1m-d100 (default) or the paper's SYNTHETIC construction (Sec. 5)")
     ap.add_argument("--points", type=int, default=None, help="override the workload's number of points")
@@ -168,7 +171,8 @@ def search_kernel_traffic(args=None):
     workload it was taken on (the default one: learned start, bf16 scoring)."""
     if args is not None and (args.points is not None or args.queries is not None or args.budget is not None
                              or args.mode != "learned" or args.train_queries != 100_000 or args.epochs != 20
-                             or args.recall != 0.9 or getattr(args, "workload", WORKLOAD) != WORKLOAD):
+                             or args.recall != 0.9 or getattr(args, "workload", WORKLOAD) != WORKLOAD
+                             or getattr(args, "family", "crosspolytope") != "crosspolytope"):
         return None
     path = os.path.join(ROOT, "profiles", "search_kernel_traffic.txt")
     src = os.path.join(ROOT, "paper_1906_12211_gb300", "csrc", "search_kernel.cuh")
@@ -412,7 +416,7 @@ def main():
     Qd = [torch.from_numpy(Qs).to(dev), torch.from_numpy(Qs2).to(dev)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ix = pf.Index(Xd, "crosspolytope", budget_bytes=w["budget"], seed=0)
+    ix = pf.Index(Xd, args.family, budget_bytes=w["budget"], seed=0)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     kth = [brute_force_kth(torch, Xd, q, k) for q in Qd]
@@ -595,7 +599,9 @@ def main():
                 "query_hash_ms": seq["query_hash_ms"]}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if args.family == "fht":  # the oracle states this family in numpy: far too slow for a full-size index
+        cpu = {"skipped": "the oracle's pseudo-random family (numpy) cannot index the full workload in minutes"}
+    elif rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, X, Qs, ix.L, k, args.recall)
 
     fl = head.get("in_flight")
@@ -619,7 +625,7 @@ def main():
             "mode": args.mode,
             "data": "synthetic",
             "config": {"workload": args.workload, "n": ix.n, "d": ix.d, "queries_per_gpu": Q, "k": k,
-                       "recall_target": args.recall, "family": "crosspolytope", "budget_bytes": w["budget"],
+                       "recall_target": args.recall, "family": args.family, "budget_bytes": w["budget"],
                        "L": ix.L, "scoring": sc, "start_depth": "learned" if args.mode == "learned" else "plain",
                        "l2": l2, "pipelining": pipelining, "parallelism": f"replica x{world}"},
             "recall": recall, "recall_per_batch": head["recall"], "build_s": build_s,

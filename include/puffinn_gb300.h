@@ -47,7 +47,10 @@ typedef enum {
 
 typedef enum {
   PF_SIMHASH = 0,       /* random hyperplane LSH, 1 bit per function (Sec. 2.2) */
-  PF_CROSSPOLYTOPE = 1  /* cross-polytope LSH, ceil(log2 2d) bits per function (Sec. 2.2, 4.3) */
+  PF_CROSSPOLYTOPE = 1,     /* cross-polytope LSH, ceil(log2 2d) bits per function (Sec. 2.2, 4.3) */
+  PF_CROSSPOLYTOPE_FHT = 2  /* pseudo-random cross-polytope (Sec. 4.3, after Andoni et al. 2015): the d Gaussian
+                               hyperplanes replaced by H D3 H D2 H D1, three Walsh-Hadamard transforms of length
+                               d'' = 2^ceil(log2 d) with random sign diagonals; same bits per function */
 } pf_family;
 
 typedef enum { PF_F32 = 0 } pf_dtype;
@@ -146,7 +149,9 @@ typedef enum {
   PF_ARRAY_MLP_F32 = 10,       /* float: W1 [H][F], b1 [H], W2 [C][H], b2 [C], one after another (the biases are
                                   also what inference uses) */
   PF_ARRAY_MLP_W1_BF16 = 11,   /* bfloat16 [F][H]: W1 rounded to nearest even, transposed, as inference reads it */
-  PF_ARRAY_MLP_W2_BF16 = 12    /* bfloat16 [C][H]: W2 rounded to nearest even, as inference reads it */
+  PF_ARRAY_MLP_W2_BF16 = 12,   /* bfloat16 [C][H]: W2 rounded to nearest even, as inference reads it */
+  PF_ARRAY_FHT_SIGNS = 13      /* uint32 [L][fns][3][W]: sign bits of D1, D2, D3 of every pseudo-random CP function,
+                                  W = max(1, d''/32) words, bit i of a vector set = -1 (PF_CROSSPOLYTOPE_FHT only) */
 } pf_array;
 
 /* Build the index over `points` ([n][d] row-major, host or device).

@@ -20,7 +20,7 @@ _LIB = os.path.join(_HERE, "libpuffinn_oracle.so")
 
 SIMHASH = 0
 CROSSPOLYTOPE = 1
-CROSSPOLYTOPE_FHT = 2  # pseudo-random cross-polytope (oracle/fht.py); needs an explicit L
+CROSSPOLYTOPE_FHT = 2  # pseudo-random cross-polytope (oracle/fht.py)
 PREFIX_BITS = 13
 ALPHA_STEPS = 41
 
@@ -272,8 +272,6 @@ class OracleIndex:
             from . import fht
 
             lay = fht.layout(self.d)
-            if L is None:
-                raise ValueError("the pseudo-random cross-polytope family needs an explicit L")
         else:
             lay = layout(family, self.d)
         self.ell, self.F, self.Kb = lay["ell"], lay["F"], lay["Kb"]

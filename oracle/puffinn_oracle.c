@@ -444,12 +444,21 @@ int64_t orc_budget_L(int family, int64_t n, int d, int M, uint64_t budget_bytes,
                      int row_storage) {
   int64_t dp = ((int64_t)d + 15) / 16 * 16;
   int F;
-  orc_layout(family, d, NULL, &F, NULL, NULL);
-  int64_t R = (family == ORC_CROSSPOLYTOPE) ? (int64_t)F * dp : 32;
+  orc_layout(family == ORC_CROSSPOLYTOPE_FHT ? ORC_CROSSPOLYTOPE : family, d, NULL, &F, NULL, NULL);
+  int64_t R = (family == ORC_CROSSPOLYTOPE) ? (int64_t)F * dp : (family == ORC_SIMHASH ? 32 : 0);
+  /* pseudo-random CP (Sec. 4.3): a function keeps three random sign vectors
+   * of d'' = 2^ceil(log2 d) bits, in 32-bit words (at least one) */
+  int64_t fht_bytes = 0;
+  if (family == ORC_CROSSPOLYTOPE_FHT) {
+    int64_t dpp = 1;
+    while (dpp < d) dpp *= 2;
+    fht_bytes = (int64_t)F * 3 * (dpp < 32 ? 1 : dpp / 32) * 4;
+  }
   /* rows: float32 (4 B) or binary16 (2 B) per element, plus the bfloat16 copy (2 B) */
   int64_t row_bytes = row_storage == 1 ? 4 : 6;
   int64_t fixed = n * dp * row_bytes + 64 * (int64_t)M * dp * 8 + (sketch_layout == 1 ? n * (int64_t)M * 8 : 0);
-  int64_t per_table = n * (sketch_layout == 1 ? 8 : 16) + (int64_t)((1 << ORC_PREFIX_BITS) + 1) * 4 + R * dp * 8;
+  int64_t per_table = n * (sketch_layout == 1 ? 8 : 16) + (int64_t)((1 << ORC_PREFIX_BITS) + 1) * 4 + R * dp * 8 +
+                      fht_bytes;
   if ((int64_t)budget_bytes <= fixed) return 0;
   return ((int64_t)budget_bytes - fixed) / per_table;
 }

@@ -28,7 +28,7 @@
 extern "C" {
 #endif
 
-enum { ORC_SIMHASH = 0, ORC_CROSSPOLYTOPE = 1 };
+enum { ORC_SIMHASH = 0, ORC_CROSSPOLYTOPE = 1, ORC_CROSSPOLYTOPE_FHT = 2 /* budget rule only (oracle/fht.py) */ };
 enum { ORC_PURPOSE_HASH = 1, ORC_PURPOSE_SKETCH = 2, ORC_PURPOSE_CPMC = 3 };
 #define ORC_PREFIX_BITS 13
 #define ORC_ALPHA_STEPS 41 /* similarity grid -1, -0.95, ..., 1 (Sec. 4.3) */

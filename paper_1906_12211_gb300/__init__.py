@@ -18,15 +18,17 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpuffinn_gb300.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "puffinn_gb300.h")
 
-SIMHASH, CROSSPOLYTOPE = 0, 1
-FAMILIES = {"simhash": SIMHASH, "hp": SIMHASH, "crosspolytope": CROSSPOLYTOPE, "cp": CROSSPOLYTOPE}
+SIMHASH, CROSSPOLYTOPE, CROSSPOLYTOPE_FHT = 0, 1, 2
+FAMILIES = {"simhash": SIMHASH, "hp": SIMHASH, "crosspolytope": CROSSPOLYTOPE, "cp": CROSSPOLYTOPE,
+            "crosspolytope-fht": CROSSPOLYTOPE_FHT, "fht": CROSSPOLYTOPE_FHT}
 
 PF_OK = 0
 STATUS = {0: "PF_OK", -1: "PF_ERR_INVALID_ARG", -2: "PF_ERR_BUDGET_TOO_SMALL", -3: "PF_ERR_OOM",
           -4: "PF_ERR_CUDA", -5: "PF_ERR_DEVICE_TIMEOUT", -6: "PF_ERR_NOT_TRAINED"}
 
 ARRAYS = {"rows_f32": 0, "rows_bf16": 1, "codes": 2, "ids": 3, "prefix": 4, "sketches": 5, "hash_rows": 6,
-          "cp_table": 7, "table_sketches": 8, "rows_f16": 9, "mlp_f32": 10, "mlp_w1_bf16": 11, "mlp_w2_bf16": 12}
+          "cp_table": 7, "table_sketches": 8, "rows_f16": 9, "mlp_f32": 10, "mlp_w1_bf16": 11, "mlp_w2_bf16": 12,
+          "fht_signs": 13}
 ROW_STORAGE = {"f32": 0, "f16": 1}
 SKETCH_LAYOUTS = {"table": 0, "point": 1}
 

@@ -160,6 +160,7 @@ void destroy(pf_index* ix) {
   dfree(ix->cos_tab);
   dfree(ix->dev_error);
   dfree(ix->path_count);
+  dfree(ix->fht_signs);
   dfree(ix->mlp_w);
   dfree(ix->mlp_w1h);
   dfree(ix->mlp_w2h);
@@ -246,7 +247,7 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
     if (prm->n < 1 || prm->n > 0x7fffffffLL) return fail(PF_ERR_INVALID_ARG, "n must be in [1, 2^31-1]");
     if (prm->d < 1 || prm->d > kMaxD) return fail(PF_ERR_INVALID_ARG, "d must be in [1, 320]");
     if (prm->dtype != PF_F32) return fail(PF_ERR_INVALID_ARG, "points must be float32");
-    if (prm->family != PF_SIMHASH && prm->family != PF_CROSSPOLYTOPE)
+    if (prm->family != PF_SIMHASH && prm->family != PF_CROSSPOLYTOPE && prm->family != PF_CROSSPOLYTOPE_FHT)
       return fail(PF_ERR_INVALID_ARG, "unknown hash family");
     const int M = prm->num_sketches ? prm->num_sketches : 32;
     const int B = prm->segment_B ? prm->segment_B : 12;
@@ -309,7 +310,16 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       dalloc(&ix->cos_tab, 65);
       dalloc(&ix->dev_error, 16);
       PF_CK(cudaMemsetAsync(ix->dev_error, 0, 16 * sizeof(int32_t), s));
-      if (ix->family == PF_CROSSPOLYTOPE) dalloc(&ix->cpP, size_t(kAlphaSteps) * (ix->lay.ell + 1));
+      const bool cp_table = ix->family == PF_CROSSPOLYTOPE || ix->family == PF_CROSSPOLYTOPE_FHT;
+      if (cp_table) dalloc(&ix->cpP, size_t(kAlphaSteps) * (ix->lay.ell + 1));
+      if (ix->family == PF_CROSSPOLYTOPE_FHT) {
+        const size_t words = size_t(ix->L) * ix->lay.fns * 3 * ix->lay.fht_words;
+        dalloc(&ix->fht_signs, words);
+        std::vector<uint32_t> sg(words);
+        gen_fht_signs(prm->seed, ix->L, ix->lay, sg.data());
+        PF_CK(cudaMemcpy(ix->fht_signs, sg.data(), sizeof(uint32_t) * words, cudaMemcpyHostToDevice));
+        fht_bands(prm->d, ix->lay, &ix->fht_gap, &ix->fht_sign);
+      }
 
       // random parameters on the host (bit-reproducible from the seed)
       std::vector<float> W(size_t(ix->hash_rows) * dp), thr(size_t(ix->hash_rows));
@@ -322,9 +332,12 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       filter_cos_table(cosv.data());
       PF_CK(cudaMemcpyAsync(ix->cos_tab, cosv.data(), sizeof(double) * 65, cudaMemcpyHostToDevice, s));
       std::vector<double> P;
-      if (ix->family == PF_CROSSPOLYTOPE) {
+      if (cp_table) {
         P.resize(size_t(kAlphaSteps) * (ix->lay.ell + 1));
-        cp_collision_table(prm->seed, prm->d, ix->lay.ell, draws, P.data());
+        if (ix->family == PF_CROSSPOLYTOPE_FHT)
+          fht_collision_table(prm->seed, ix->lay, draws, P.data());
+        else
+          cp_collision_table(prm->seed, prm->d, ix->lay.ell, draws, P.data());
         PF_CK(cudaMemcpyAsync(ix->cpP, P.data(), sizeof(double) * P.size(), cudaMemcpyHostToDevice, s));
       }
 
@@ -558,6 +571,11 @@ pf_status pf_index_array(const pf_index* ix, int32_t which, const void** ptr, ui
       if (!ix->cpP) return fail(PF_ERR_INVALID_ARG, "index has no CP table");
       *ptr = ix->cpP;
       *bytes = uint64_t(kAlphaSteps) * (ix->lay.ell + 1) * 8;
+      break;
+    case PF_ARRAY_FHT_SIGNS:
+      if (!ix->fht_signs) return fail(PF_ERR_INVALID_ARG, "index is not of the pseudo-random cross-polytope family");
+      *ptr = ix->fht_signs;
+      *bytes = uint64_t(ix->L) * ix->lay.fns * 3 * ix->lay.fht_words * 4;
       break;
     case PF_ARRAY_MLP_F32:
     case PF_ARRAY_MLP_W1_BF16:

@@ -272,14 +272,23 @@ cudaError_t launch_hash(const pf_index* ix, const float* x32, const __nv_bfloat1
                         int64_t npts, uint32_t* codes, int64_t cj, int64_t cp, uint64_t* sk, int64_t sm,
                         int64_t sp, RecheckReq* rq, uint32_t* rq_count, uint32_t rq_cap, cudaStream_t s) {
   if (npts <= 0) return cudaSuccess;
+  // repetitions hashed from rows; the pseudo-random family has its own kernel
+  // and leaves only the sketches to the row kernels
+  int tables = ix->L;
+  if (ix->family == PF_CROSSPOLYTOPE_FHT) {
+    const cudaError_t e = launch_hash_fht(ix, x32, npts, codes, cj, cp, s);
+    if (e != cudaSuccess) return e;
+    tables = 0;
+  }
   if (hash_tc_supported(ix) && xh && xl)
-    return launch_hash_tc(ix, xh, xl, x32, npts, codes, cj, cp, sk, sm, sp, ix->dev_error, rq, rq_count, rq_cap, s);
+    return launch_hash_tc(ix, xh, xl, x32, npts, codes, cj, cp, sk, sm, sp, ix->dev_error, rq, rq_count, rq_cap, s,
+                          tables);
   const Layout& lay = ix->lay;
   const size_t smem = sizeof(float) * (size_t(lay.d_pad + 4) * kHashPts + size_t(kHashGroups * kHashChunk) * lay.d_pad);
   cudaError_t e = cudaFuncSetAttribute(hash_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  dim3 grid(unsigned((npts + kHashPts - 1) / kHashPts), unsigned((ix->L + ix->M + kHashGroups - 1) / kHashGroups));
-  hash_simt_kernel<<<grid, kHashPts * kHashGroups, smem, s>>>(x32, npts, ix->d, lay.d_pad, ix->family, ix->L, ix->M,
+  dim3 grid(unsigned((npts + kHashPts - 1) / kHashPts), unsigned((tables + ix->M + kHashGroups - 1) / kHashGroups));
+  hash_simt_kernel<<<grid, kHashPts * kHashGroups, smem, s>>>(x32, npts, ix->d, lay.d_pad, ix->family, tables, ix->M,
                                                               lay.fns, lay.ell,
                                                 lay.rows_table, ix->W32, ix->Wthr, codes, cj, cp, sk, sm, sp);
   return cudaGetLastError();

@@ -1065,7 +1065,7 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int d_pad, int box
 cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __nv_bfloat16* xl, const float* x32,
                            int64_t npts, uint32_t* codes, int64_t cj, int64_t cp, uint64_t* sk, int64_t sm,
                            int64_t sp, int32_t* error, RecheckReq* rq, uint32_t* rq_count, uint32_t rq_cap,
-                           cudaStream_t s) {
+                           cudaStream_t s, int tables) {
   if (npts <= 0) return cudaSuccess;
   HashArgs A;
   A.xh = xh;
@@ -1081,12 +1081,12 @@ cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __
   A.d_pad = ix->lay.d_pad;
   A.KB = (A.d_pad + 63) / 64;
   A.family = ix->family;
-  A.L = ix->L;
+  A.L = tables;
   A.M = ix->M;
   A.fns = ix->lay.fns;
   A.ell = ix->lay.ell;
   A.rows_table = ix->lay.rows_table;
-  A.seg_tables = ix->family == PF_CROSSPOLYTOPE ? ix->L : (ix->L + 3) / 4;
+  A.seg_tables = ix->family == PF_CROSSPOLYTOPE ? tables : (tables + 3) / 4;
   A.segs = A.seg_tables + (ix->M + 1) / 2;
   const int64_t mtiles = (npts + kBM - 1) / kBM;
   A.units = (mtiles + kPair - 1) / kPair * A.segs;

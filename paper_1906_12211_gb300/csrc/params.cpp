@@ -3,6 +3,7 @@
 // Compiled with -ffp-contract=off: every expression below is evaluated as
 // written (no fused multiply-add), so the same seed gives the same bits on any
 // host, whichever compiler built this file.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <thread>
@@ -74,7 +75,22 @@ float gaussian(uint64_t seed, uint32_t purpose, uint32_t a, uint32_t b, uint32_t
 Layout make_layout(int family, int d) {
   Layout L;
   L.d_pad = (d + 15) / 16 * 16;
-  if (family == PF_CROSSPOLYTOPE) {
+  if (family == PF_CROSSPOLYTOPE_FHT) {
+    // Sec. 4.3, pseudo-random CP: the transform runs over d'' = 2^ceil(log2 d)
+    // coordinates, so a value is an index below d'' and a sign:
+    // l = log2(2 d'') = ceil(log2 2d) bits, as for the exact family
+    int n2 = 1;
+    while (n2 < d) n2 *= 2;
+    int ell = 0;
+    while ((1 << ell) < 2 * n2) ++ell;
+    L.ell = ell;
+    L.fns = 32 / ell;
+    L.Kb = L.fns * ell;
+    L.rows_fn = 0;
+    L.rows_table = 0;
+    L.fht_n = n2;
+    L.fht_words = n2 < 32 ? 1 : n2 / 32;
+  } else if (family == PF_CROSSPOLYTOPE) {
     int ell = 0;
     while ((int64_t(1) << ell) < 2 * int64_t(d)) ++ell;  // ceil(log2 2d)
     L.ell = ell;
@@ -187,6 +203,114 @@ void cp_collision_table(uint64_t seed, int d, int ell, int draws, double* P) {
     for (int r = 0; r <= ell; ++r) P[a * W + r] = std::fmin(P[a * W + r], P[(a + 1) * W + r]);
 }
 
+// ---------------------------------------------------------------------------
+// Pseudo-random cross-polytope family (Sec. 4.3: "three applications of the
+// fast Hadamard transform", after Andoni et al. 2015).  A function maps x,
+// zero-padded to d'' = 2^ceil(log2 d) coordinates, to y = H D3 H D2 H D1 x, with
+// H the unnormalised Walsh-Hadamard matrix and D_r diagonal with random +-1
+// entries; its value is the index c of the largest |y_c| (first c on ties) and
+// the sign of y_c, as for the exact family.  H v is the in-place butterfly: for
+// h = 1, 2, 4, ..., d''/2 and every pair (i, i + h) with bit h of i clear,
+// (v_i, v_{i+h}) <- (v_i + v_{i+h}, v_i - v_{i+h}).  Every float64 value
+// is defined by this order of operations.
+// Signs: the generator's counter (block, b, a, purpose) with the seed as key
+// yields 128 bits per block; bit i of a vector is bit i % 32 of word
+// (i % 128) / 32 of block i / 128, and a set bit means -1.  The index's
+// function f of table j uses (a, b) = (j, 3 f + r) for D_{r+1}, purpose
+// kPurposeFht; draw t of the collision table uses (t, r), kPurposeFhtMc.
+// ---------------------------------------------------------------------------
+namespace {
+void fht_sign_words(uint64_t seed, uint32_t purpose, uint32_t a, uint32_t b, int words, uint32_t* out) {
+  for (int blk = 0; blk * 4 < words; ++blk) {
+    uint32_t w[4] = {uint32_t(blk), b, a, purpose};
+    Philox4x32::block(w, uint32_t(seed), uint32_t(seed >> 32));
+    for (int q = 0; q < 4 && blk * 4 + q < words; ++q) out[blk * 4 + q] = w[q];
+  }
+}
+
+// y = H D3 H D2 H D1 v in float64 (v: n2 values, overwritten), signs[r][words]
+void fht_rotate64(double* v, int n2, const uint32_t* signs, int words) {
+  for (int r = 0; r < 3; ++r) {
+    const uint32_t* sg = signs + size_t(r) * words;
+    for (int i = 0; i < n2; ++i)
+      if ((sg[i / 32] >> (i % 32)) & 1u) v[i] = -v[i];
+    for (int h = 1; h < n2; h *= 2)
+      for (int i = 0; i < n2; ++i)
+        if (!(i & h)) {
+          const double a = v[i], b = v[i + h];
+          v[i] = a + b;
+          v[i + h] = a - b;
+        }
+  }
+}
+}  // namespace
+
+void gen_fht_signs(uint64_t seed, int L, const Layout& lay, uint32_t* out) {
+  const int W = lay.fht_words;
+  parallel_for(L, [&](int64_t j) {
+    for (int f = 0; f < lay.fns; ++f)
+      for (int r = 0; r < 3; ++r)
+        fht_sign_words(seed, kPurposeFht, uint32_t(j), uint32_t(3 * f + r), W,
+                       out + ((size_t(j) * lay.fns + f) * 3 + r) * W);
+  });
+}
+
+// Sec. 4.3 Monte-Carlo table for this family: x = e_1 and y = (alpha,
+// sqrt(1 - alpha^2), 0, ...) on the 0.05 grid, one random function per draw
+// (the same draws for every alpha), then made non-decreasing in alpha.
+void fht_collision_table(uint64_t seed, const Layout& lay, int draws, double* P) {
+  const int n2 = lay.fht_n, ell = lay.ell, W = lay.fht_words, WP = ell + 1;
+  std::vector<int64_t> hits(size_t(kAlphaSteps) * WP, 0);
+  std::vector<uint32_t> sg(size_t(3) * W);
+  std::vector<double> vx(n2), vy(n2);
+  for (int t = 0; t < draws; ++t) {
+    for (int r = 0; r < 3; ++r) fht_sign_words(seed, kPurposeFhtMc, uint32_t(t), uint32_t(r), W, &sg[size_t(r) * W]);
+    std::fill(vx.begin(), vx.end(), 0.0);
+    vx[0] = 1.0;
+    fht_rotate64(vx.data(), n2, sg.data(), W);
+    const uint32_t hx = cp_code_of(vx.data(), n2, ell);
+    for (int a = 0; a < kAlphaSteps; ++a) {
+      const double alpha = double(5 * a - 100) / 100.0;
+      std::fill(vy.begin(), vy.end(), 0.0);
+      vy[0] = alpha;
+      if (n2 > 1) vy[1] = std::sqrt(1.0 - alpha * alpha);
+      fht_rotate64(vy.data(), n2, sg.data(), W);
+      const uint32_t hy = cp_code_of(vy.data(), n2, ell);
+      for (int r = 0; r <= ell; ++r) hits[a * WP + r] += (hx >> (ell - r)) == (hy >> (ell - r)) ? 1 : 0;
+    }
+  }
+  for (int a = 0; a < kAlphaSteps; ++a)
+    for (int r = 0; r <= ell; ++r) P[a * WP + r] = double(hits[a * WP + r]) / double(draws);
+  for (int a = kAlphaSteps - 2; a >= 0; --a)
+    for (int r = 0; r <= ell; ++r) P[a * WP + r] = std::fmin(P[a * WP + r], P[(a + 1) * WP + r]);
+}
+
+// Error of the float32 transform for |x|_2 <= 1 + 2^-20 (a normalised row):
+// with u the unit roundoff and m = log2 d'', one butterfly pass of an input v
+// errs by at most g |v|_1 per output, g = m u / (1 - m u) (every output is a
+// depth-m tree of additions of +-v_i).  An error e of the input reaches an
+// output as at most |e|_1 <= d'' |e|_inf.  With |x|_1 <= sqrt(d) |x|_2 and
+// |v_r|_1 <= sqrt(d'') |v_r|_2 = d''^((r+1)/2) |x|_2 after pass r:
+//   e1 <= g sqrt(d) |x|,  e_{r+1} <= d'' e_r (1 + g) + g d''^((r+1)/2) |x|.
+// A decision is redone in float64 when the top two |y| (float32) are within
+// 2 (e3 + e3') of each other or the top |y| is within e3 + e3' of zero, e3'
+// the same bound for float64.
+void fht_bands(int d, const Layout& lay, float* gap, float* sign) {
+  const double N = lay.fht_n;
+  int m = 0;
+  while ((1 << m) < lay.fht_n) ++m;
+  auto e3 = [&](double u) {
+    const double g = m * u / (1.0 - m * u), x = 1.0 + std::ldexp(1.0, -20);
+    double e = g * std::sqrt(double(d)) * x;
+    e = N * e * (1.0 + g) + g * N * x;
+    e = N * e * (1.0 + g) + g * N * std::sqrt(N) * x;
+    return e;
+  };
+  const double t = (e3(std::ldexp(1.0, -24)) + e3(std::ldexp(1.0, -53))) * 1.01;
+  *gap = float(2.0 * t);
+  *sign = float(t);
+}
+
 // cos(t*pi/64), t = 0..64: the sketch threshold is the largest t whose entry
 // is >= s_k (= floor(64 arccos(s_k)/pi), Sec. 4.2).
 void filter_cos_table(double* c) {
@@ -206,7 +330,10 @@ uint64_t resident_bytes(int family, int64_t n, int d, int M, int L, int sketch_l
   const bool per_point = sketch_layout == PF_SKETCH_PER_POINT;
   const int64_t row_bytes = row_storage == PF_ROWS_F16 ? 4 : 6;  // rows (4 or 2 B) + the bfloat16 copy (2 B)
   const int64_t fixed = n * dp * row_bytes + 64LL * M * dp * 8 + (per_point ? n * int64_t(M) * 8 : 0);
-  const int64_t per_table = n * (per_point ? 8 : 16) + int64_t(kPrefixSize) * 4 + int64_t(lay.rows_table) * dp * 8;
+  // pseudo-random CP: three sign vectors per function instead of rows
+  const int64_t fht = family == PF_CROSSPOLYTOPE_FHT ? int64_t(lay.fns) * 3 * lay.fht_words * 4 : 0;
+  const int64_t per_table =
+      n * (per_point ? 8 : 16) + int64_t(kPrefixSize) * 4 + int64_t(lay.rows_table) * dp * 8 + fht;
   return uint64_t(fixed + per_table * L);
 }
 

@@ -23,7 +23,13 @@ constexpr int kMlpHidden = 256;                     // start-depth model hidden 
 constexpr float kMlpTail = 0.05f;                   // quantile: P(stop depth > q) <= this
 constexpr int kMlpMargin = 6;                       // start depth = quantile + this many bits (capped at K)
 
-enum Purpose : uint32_t { kPurposeHash = 1, kPurposeSketch = 2, kPurposeCpMc = 3 };
+enum Purpose : uint32_t {
+  kPurposeHash = 1,
+  kPurposeSketch = 2,
+  kPurposeCpMc = 3,
+  kPurposeFht = 4,    // sign vectors of the pseudo-random cross-polytope functions
+  kPurposeFhtMc = 5,  // sign vectors of its Monte-Carlo collision draws
+};
 
 // Shape of one repetition's code (Sec. 4.3): l bits per function, floor(32/l)
 // functions, K = fns * l bits.  Hash rows are padded so that every CP function
@@ -31,7 +37,9 @@ enum Purpose : uint32_t { kPurposeHash = 1, kPurposeSketch = 2, kPurposeCpMc = 3
 struct Layout {
   int ell = 1, fns = 32, Kb = 32, d_pad = 16;
   int rows_fn = 1;      // rows per hash function in the padded row matrix
-  int rows_table = 32;  // rows per repetition
+  int rows_table = 32;  // rows per repetition (0 for the pseudo-random family: no rows)
+  int fht_n = 0;        // pseudo-random family: transform length 2^ceil(log2 d)
+  int fht_words = 0;    // 32-bit words of one sign vector (at least one)
 };
 Layout make_layout(int family, int d);
 
@@ -50,6 +58,12 @@ float gaussian(uint64_t seed, uint32_t purpose, uint32_t a, uint32_t b, uint32_t
 void gen_hash_rows(uint64_t seed, int family, int L, int M, int d, const Layout& lay, float* W, float* thr);
 void cp_collision_table(uint64_t seed, int d, int ell, int draws, double* P /*[41][ell+1]*/);
 void filter_cos_table(double* c /*[65]*/);
+// pseudo-random cross-polytope family (Sec. 4.3): sign bits [L][fns][3][fht_words]
+void gen_fht_signs(uint64_t seed, int L, const Layout& lay, uint32_t* out);
+void fht_collision_table(uint64_t seed, const Layout& lay, int draws, double* P /*[41][ell+1]*/);
+// bounds on the float32 transform's error for unit inputs: decisions whose top
+// two |y| are closer than *gap, or whose top |y| is below *sign, are redone in float64
+void fht_bands(int d, const Layout& lay, float* gap, float* sign);
 int64_t budget_tables(int family, int64_t n, int d, int M, uint64_t budget, int sketch_layout, int row_storage);
 uint64_t resident_bytes(int family, int64_t n, int d, int M, int L, int sketch_layout, int row_storage);
 
@@ -114,6 +128,8 @@ struct pf_index {
   uint32_t* ids = nullptr;         // [L][n]
   uint32_t* pfx = nullptr;         // [L][8193]
   double* cpP = nullptr;           // [41][ell+1]
+  uint32_t* fht_signs = nullptr;   // [L][fns][3][fht_words] (pseudo-random family only)
+  float fht_gap = 0.f, fht_sign = 0.f;  // its float64 recheck bands
   double* cos_tab = nullptr;       // [65]
   float bf16_err = 0.f;            // bound on |bf16 estimate - float32 canonical similarity|
   int32_t* dev_error = nullptr;    // device error word (bit 1: a bounded wait timed out)
@@ -159,10 +175,14 @@ cudaError_t launch_hash(const pf_index* ix, const float* x32, const __nv_bfloat1
 // recheck-queue entries to provision for npts points
 inline uint32_t recheck_capacity(int64_t npts) { return uint32_t(npts * 48 + 65536); }
 bool hash_tc_supported(const pf_index* ix);
+// tables: repetitions hashed with row-based functions (ix->L; 0 hashes sketches only)
 cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __nv_bfloat16* xl, const float* x32,
                            int64_t npts, uint32_t* codes, int64_t cj, int64_t cp, uint64_t* sk, int64_t sm,
                            int64_t sp, int32_t* error, RecheckReq* rq, uint32_t* rq_count, uint32_t rq_cap,
-                           cudaStream_t s);
+                           cudaStream_t s, int tables);
+// pseudo-random cross-polytope codes (kernels_fht.cu): codes[j*cj + p*cp]
+cudaError_t launch_hash_fht(const pf_index* ix, const float* x32, int64_t npts, uint32_t* codes, int64_t cj,
+                            int64_t cp, cudaStream_t s);
 
 // Sort every repetition's (code, position) pairs and build the prefix tables.
 cudaError_t sort_tables(pf_index* ix, uint32_t* codes_unsorted, cudaStream_t s);

@@ -489,7 +489,6 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
       const uint32_t mask = 0xffffffffu << (32 - depth);
       const bool single = prev == depth + 1;
       uint32_t my_chunks = 0;
-      uint32_t n_table = 0, n_probe = 0, n_gallop = 0;  // diagnostics only
       const int jlo = min(L, tid * per), jhi = min(L, jlo + per);
       for (int j = jlo; j < jhi; ++j) {
         const uint32_t qcj = qc[j];
@@ -513,7 +512,7 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
           const uint32_t span = 1u << (kPrefixBits - depth);
           const uint32_t t0 = (qcj >> (32 - kPrefixBits)) & ~(span - 1u);
           const uint32_t blo = __ldg(pj + t0), bhi = __ldg(pj + t0 + span);
-          ++n_table;
+          if (P.path_count) atomicAdd(P.path_count + 0, 1ull);  // diagnostics only
           if (try_left && l > blo) {
             const uint32_t m = (l - blo + B - 1) / B;
             nl = l >= B * m ? l - B * m : 0u;
@@ -544,7 +543,7 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
             for (int m = kProbe; m >= 1; --m)
               if (!prefix_match(cl[m], qcj, mask)) hi = m;
             if (hi == 0) {  // the first kProbe boundaries are all inside the block
-              ++n_gallop;
+              if (P.path_count) atomicAdd(P.path_count + 2, 1ull);
               lo = kProbe;
               hi = 2 * kProbe;
               for (;;) {
@@ -561,7 +560,7 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
             }
             const int64_t pos = int64_t(l) - int64_t(B) * hi;
             nl = pos < 0 ? 0u : uint32_t(pos);
-            ++n_probe;
+            if (P.path_count && hi <= kProbe) atomicAdd(P.path_count + 1, 1ull);
           }
           if (rv && prefix_match(cr[0], qcj, mask)) {
             uint32_t lo = 0, hi = 0;
@@ -569,7 +568,7 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
             for (int m = kProbe; m >= 1; --m)
               if (!prefix_match(cr[m], qcj, mask)) hi = m;
             if (hi == 0) {
-              ++n_gallop;
+              if (P.path_count) atomicAdd(P.path_count + 2, 1ull);
               lo = kProbe;
               hi = 2 * kProbe;
               for (;;) {
@@ -586,17 +585,12 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
             }
             const int64_t pos = int64_t(r) + int64_t(B) * hi;
             nr = pos > int64_t(n) ? n : uint32_t(pos);
-            ++n_probe;
+            if (P.path_count && hi <= kProbe) atomicAdd(P.path_count + 1, 1ull);
           }
         }
         range[j] = make_uint2(nl, nr);
         runs[j] = make_uint4(nl, l - nl, r, nr - r);
         my_chunks += (l - nl + kSpan - 1) / kSpan + (nr - r + kSpan - 1) / kSpan;
-      }
-      if (P.path_count) {
-        if (n_table) atomicAdd(P.path_count + 0, (unsigned long long)n_table);
-        if (n_probe) atomicAdd(P.path_count + 1, (unsigned long long)(n_probe - n_gallop));
-        if (n_gallop) atomicAdd(P.path_count + 2, (unsigned long long)n_gallop);
       }
       // exclusive scan of the chunk counts over the repetitions -> cpre
       uint32_t inc = my_chunks;

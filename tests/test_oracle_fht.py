@@ -109,5 +109,6 @@ def test_small_index_meets_the_recall_target_with_the_filter_off():
     for t in range(0, 60, 7):
         for u in range(10):
             assert out["sims"][t, u] == oracle.sim(qn[t], ix.x[out["ids"][t, u]])
-    with pytest.raises(ValueError):
-        oracle.OracleIndex(X, oracle.CROSSPOLYTOPE_FHT, budget_bytes=1 << 30)
+    # a budget gives the L of the budget rule (three sign vectors per function)
+    small = oracle.OracleIndex(X, oracle.CROSSPOLYTOPE_FHT, budget_bytes=4 << 20)
+    assert small.L == oracle.budget_L(oracle.CROSSPOLYTOPE_FHT, 3000, 100, 32, 4 << 20) >= 1

@@ -261,6 +261,10 @@ def test_budget_formula_values(orc):
     assert orc.budget_L(orc.CROSSPOLYTOPE, n, d, M, 4 << 30, 0) == ((4 << 30) - fixed_table) // per_table == 220
     assert orc.budget_L(orc.SIMHASH, 10_000, 64, 32, 32 << 20, 1) == 202
     assert orc.budget_L(orc.SIMHASH, 10_000, 64, 32, 1 << 20, 0) == 0
+    # pseudo-random CP: the hash functions are three sign vectors of d'' = 128
+    # bits per function (4 words each) instead of d' x d' rows
+    per_fht = n * 16 + 8193 * 4 + 4 * 3 * 4 * 4
+    assert orc.budget_L(orc.CROSSPOLYTOPE_FHT, n, d, M, 4 << 30, 0) == ((4 << 30) - fixed_table) // per_fht == 225
 
 
 def test_budget_with_binary16_rows(orc):
