@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other two modes")
     ap.add_argument("--recall", type=float, default=None,
                     help="recall target 1 - delta passed to the index (default: the workload's)")
+    ap.add_argument("--stop-every", type=int, default=0,
+                    help="0: the stop test after each round (Sec. 4.1); G: also after every G repetitions (Alg. 1)")
     ap.add_argument("--family", default="crosspolytope", choices=["crosspolytope", "fht"],
                     help="crosspolytope: Gaussian hyperplanes (tensor cores); fht: the pseudo-random family of "
                          "Sec. 4.3 (three Hadamard transforms)")
@@ -443,7 +445,8 @@ def main():
     if not args.no_tune:
         Qtune = queries(w, Q, "tune", rank)
         tune_report = ix.tune(torch.from_numpy(Qtune).to(dev), k, args.recall,
-                              scoring="fp32" if args.mode == "fp32" else "bf16", learned=args.mode == "learned")
+                              scoring="fp32" if args.mode == "fp32" else "bf16", learned=args.mode == "learned",
+                              stop_every=args.stop_every)
 
     def opts_of(mode):
         return ("fp32" if mode == "fp32" else "bf16"), mode == "learned"
@@ -462,7 +465,7 @@ def main():
 
         def run(timing=False):
             ix.search(Qd[0], kq[0], rq[0], k_max=k, scoring=sc, out_ids=o1[0], out_sims=o1[1], stats=o1[2],
-                      timing=timing, learned=lr)
+                      timing=timing, learned=lr, stop_every=args.stop_every)
 
         kern = {"kernel_ms": 0.0, "hash_ms": 0.0}
 
@@ -488,8 +491,10 @@ def main():
         stats = [pf.stats_to_numpy(o1[2])]
         sims = [o1[1]]
         if not args.no_graph:
-            pa = ix.plan(Qd[0], kq[0], rq[0], *outputs()[:2], k_max=k, scoring=sc, learned=lr)
-            pb = ix.plan(Qd[1], kq[1], rq[1], o2[0], o2[1], k_max=k, stats=o2[2], scoring=sc, learned=lr)
+            pa = ix.plan(Qd[0], kq[0], rq[0], *outputs()[:2], k_max=k, scoring=sc, learned=lr,
+                         stop_every=args.stop_every)
+            pb = ix.plan(Qd[1], kq[1], rq[1], o2[0], o2[1], k_max=k, stats=o2[2], scoring=sc, learned=lr,
+                         stop_every=args.stop_every)
             plans = [pa, pb]
             try:
                 for _ in range(max(3, args.warmup)):
@@ -520,7 +525,8 @@ def main():
         res["recall"] = [recall_of(s_, kth[b]) for b, s_ in enumerate(sims)]
         allst = np.concatenate(stats)
         res["per_query"] = {f: float(allst[f].mean()) for f in ("start_depth", "stop_depth", "rounds", "retrieved",
-                                                                "passed_filter", "scored", "reranked")}
+                                                                "passed_filter", "scored", "reranked",
+                                                                "last_reps")}
         res["_batch1"] = (o1, stats[0])
         return res
 
@@ -563,7 +569,7 @@ def main():
 
         # one batch at a time: pf_index_search given the host pointers
         el = wall(lambda i: ix.search(hq[0], hk[0], hr[0], k_max=k, scoring=sc, out_ids=hi[0], out_sims=hs[0],
-                                      learned=lr), args.steps)
+                                      learned=lr, stop_every=args.stop_every), args.steps)
         assert torch.equal(hi[0], ids1.cpu()) and torch.equal(hs[0], sims1.cpu())
         seq_e2e = {"value": whole_job_rate(Q, world, args.steps, el), "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "how": "pf_index_search with page-locked host pointers, one batch "
@@ -572,7 +578,8 @@ def main():
         if not args.no_graph:
             # two batches in flight: plans bound to the host buffers (each graph
             # copies its inputs in and its outputs out on its own stream)
-            plans = [ix.plan(hq[b], hk[b], hr[b], hi[b], hs[b], k_max=k, scoring=sc, learned=lr) for b in range(2)]
+            plans = [ix.plan(hq[b], hk[b], hr[b], hi[b], hs[b], k_max=k, scoring=sc, learned=lr,
+                             stop_every=args.stop_every) for b in range(2)]
             try:
                 el = wall(lambda i: plans[i % 2].run(streams[i % 2]), args.steps)
                 for p_, s_ in zip(plans, streams):
@@ -627,6 +634,8 @@ def main():
             "config": {"workload": args.workload, "n": ix.n, "d": ix.d, "queries_per_gpu": Q, "k": k,
                        "recall_target": args.recall, "family": args.family, "budget_bytes": w["budget"],
                        "L": ix.L, "scoring": sc, "start_depth": "learned" if args.mode == "learned" else "plain",
+                       "stop_test": (f"after every {args.stop_every} repetitions" if args.stop_every
+                                     else "after every round"),
                        "l2": l2, "pipelining": pipelining, "parallelism": f"replica x{world}"},
             "recall": recall, "recall_per_batch": head["recall"], "build_s": build_s,
             "per_query": head["per_query"],

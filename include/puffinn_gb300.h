@@ -98,6 +98,11 @@ typedef struct {
   int32_t timing;              /* 1: record CUDA events around each phase (see pf_index_last_timing) */
   const int32_t* start_depth;  /* optional [Q] per-query start depth i0 (host or device): rounds i0, i0-1, ..., 0,
                                   the first taking the whole block at i0; values outside [0, K) mean K */
+  int32_t stop_every;          /* 0: the stop test after each round (Sec. 4.1).  G >= 1: also after every G
+                                  repetitions (Alg. 1 tests after each one: G = 1): after j repetitions of the round
+                                  at prefix length i the test is (1 - p_i)^j (1 - p_{i+1})^(L - j) <= delta (no second
+                                  factor in the first round); the filter threshold is then refreshed at every group
+                                  of G repetitions, in every round */
 } pf_search_opts;
 
 /* Per-query statistics (Sec. 5 reports recall and throughput; these counts
@@ -111,6 +116,8 @@ typedef struct {
   int64_t passed_filter; /* of those, how many passed the sketch filter */
   int64_t scored;        /* similarities computed (float32, or bfloat16 estimates) */
   int64_t reranked;      /* exact float32 similarities recomputed after a bfloat16 estimate */
+  int32_t last_reps;     /* repetitions searched in the last round: L, or fewer when the stop test ran after
+                            groups of repetitions (pf_search_opts.stop_every) and held mid-round */
 } pf_query_stats;
 
 typedef struct {

@@ -43,7 +43,7 @@ def build(force: bool = False) -> str:
 class _Stats(C.Structure):
     _fields_ = [("start_depth", C.c_int32), ("stop_depth", C.c_int32), ("rounds", C.c_int32),
                 ("full_depth", C.c_int32), ("retrieved", C.c_int64), ("passed_filter", C.c_int64),
-                ("scored", C.c_int64)]
+                ("scored", C.c_int64), ("last_reps", C.c_int32)]
 
 
 class _Index(C.Structure):
@@ -55,7 +55,7 @@ class _Index(C.Structure):
 
 STATS_DTYPE = np.dtype([("start_depth", np.int32), ("stop_depth", np.int32), ("rounds", np.int32),
                         ("full_depth", np.int32), ("retrieved", np.int64), ("passed_filter", np.int64),
-                        ("scored", np.int64)], align=True)
+                        ("scored", np.int64), ("last_reps", np.int32)], align=True)
 
 
 def lib():
@@ -86,7 +86,7 @@ def lib():
                 "orc_filter_tau": (C.c_int, [f64]),
                 "orc_budget_L": (i64, [C.c_int, i64, C.c_int, C.c_int, u64, C.c_int, C.c_int]),
                 "orc_sim": (C.c_float, [vp, vp, C.c_int]),
-                "orc_search": (None, [vp, vp, vp, vp, i64, vp, vp, i32, vp, C.c_int, vp, vp, vp, vp, i64, vp]),
+                "orc_search": (None, [vp, vp, vp, vp, i64, vp, vp, i32, vp, C.c_int, C.c_int, vp, vp, vp, vp, i64, vp]),
                 "orc_brute_force": (None, [vp, i64, C.c_int, vp, i64, C.c_int, vp, vp]),
             }
             for name, (res, args) in sig.items():
@@ -108,7 +108,7 @@ def compile_variant(src_text: str, out_path: str):
     L = C.CDLL(out_path)
     vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
     L.orc_search.restype = None
-    L.orc_search.argtypes = [vp, vp, vp, vp, i64, vp, vp, i32, vp, C.c_int, vp, vp, vp, vp, i64, vp]
+    L.orc_search.argtypes = [vp, vp, vp, vp, i64, vp, vp, i32, vp, C.c_int, C.c_int, vp, vp, vp, vp, i64, vp]
     return L
 
 
@@ -310,7 +310,7 @@ class OracleIndex:
         return qn, qcodes, qsk
 
     def search(self, queries, k, recall, *, k_max: int | None = None, start_depth=None,
-               filter: bool = True, trace_cap: int = 0, variant=None):
+               filter: bool = True, trace_cap: int = 0, variant=None, stop_every: int = 0):
         qn, qcodes, qsk = self.hash_queries(queries)
         Q = qn.shape[0]
         k = np.broadcast_to(np.asarray(k, np.int32), (Q,)).copy()
@@ -328,7 +328,7 @@ class OracleIndex:
         trace = np.zeros((Q, trace_cap, 2), np.uint32) if trace_cap else None
         tlen = np.zeros(Q, np.int64) if trace_cap else None
         (variant or lib()).orc_search(C.byref(ix), _p(qn), _p(qcodes), _p(qsk), Q, _p(k), _p(recall), k_max,
-                         _p(sd) if sd is not None else None, 1 if filter else 0, _p(ids), _p(sims),
+                         _p(sd) if sd is not None else None, 1 if filter else 0, int(stop_every), _p(ids), _p(sims),
                          _p(stats), _p(trace) if trace is not None else None, trace_cap,
                          _p(tlen) if tlen is not None else None)
         out = {"ids": ids, "sims": sims, "stats": stats, "qn": qn, "qsk": qsk}

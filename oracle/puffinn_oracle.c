@@ -542,7 +542,7 @@ static int popcount64(uint64_t w) {
  * initial range of a repetition is empty at the first position whose code is
  * >= the query code. */
 static void search_one(const orc_index* ix, const float* q, const uint32_t* qcode, const uint64_t* qsk,
-                       int k, double recall, int k_max, int32_t start_depth, int filter,
+                       int k, double recall, int k_max, int32_t start_depth, int filter, int stop_every,
                        uint32_t* out_ids, float* out_sims, orc_stats* st,
                        uint32_t* trace, int64_t trace_cap, int64_t* trace_len) {
   const int64_t n = ix->n;
@@ -554,7 +554,7 @@ static void search_one(const orc_index* ix, const float* q, const uint32_t* qcod
   uint32_t* pid = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(k > 0 ? k : 1));
   int size = 0;
   int64_t tl = 0;
-  orc_stats s = {0, 0, 0, -1, 0, 0, 0};
+  orc_stats s = {0, 0, 0, -1, 0, 0, 0, 0};
 
   for (int j = 0; j < L; ++j) {
     l[j] = r[j] = lower_bound_u32(ix->codes + (int64_t)j * n, n, qcode[j]);
@@ -564,11 +564,13 @@ static void search_one(const orc_index* ix, const float* q, const uint32_t* qcod
   s.start_depth = i0;
 
   int depth = i0;
+  int stopped = 0;
   for (;;) {
     const uint32_t mask = depth == 0 ? 0u : (0xFFFFFFFFu << (32 - depth));
     int tau = 64;
     for (int j = 0; j < L; ++j) {
-      if (j == 0 || (s.rounds == 0 && j % ORC_SNAPSHOT_GROUP == 0)) { /* threshold snapshot */
+      if (j == 0 || (stop_every > 0 ? j % stop_every == 0
+                                    : (s.rounds == 0 && j % ORC_SNAPSHOT_GROUP == 0))) { /* threshold snapshot */
         const int full = (size == k);
         tau = full ? orc_filter_tau((double)ps[k - 1]) : 64;
       }
@@ -600,10 +602,22 @@ static void search_one(const orc_index* ix, const float* q, const uint32_t* qcod
       }
       l[j] = nl;
       r[j] = nr;
+      if (stop_every > 0 && depth > 0 && size == k && ((j + 1) % stop_every == 0 || j + 1 == L)) {
+        /* Alg. 1 tests after repetitions, not rounds: repetitions 0..j have
+         * now been searched to prefix length `depth`, the others to depth + 1
+         * (to nothing yet in the first round, whose factor is 1) */
+        double fail = orc_ipow(1.0 - orc_collision_prob(ix->family, ix->ell, ix->P, (double)ps[k - 1], depth), j + 1);
+        if (s.rounds > 0)
+          fail = fail * orc_ipow(1.0 - orc_collision_prob(ix->family, ix->ell, ix->P, (double)ps[k - 1], depth + 1),
+                                 L - j - 1);
+        if (fail <= delta) { stopped = j + 1; break; }
+      }
     }
+    s.last_reps = stopped ? stopped : L;
     s.rounds += 1;
     s.stop_depth = depth;
     if (size == k && s.full_depth < 0) s.full_depth = depth;
+    if (stopped) break;
     if (depth == 0) break;
     if (size == k) {
       double p = orc_collision_prob(ix->family, ix->ell, ix->P, (double)ps[k - 1], depth);
@@ -623,13 +637,13 @@ static void search_one(const orc_index* ix, const float* q, const uint32_t* qcod
 
 void orc_search(const orc_index* ix, const float* q, const uint32_t* qcodes, const uint64_t* qsk,
                 int64_t Q, const int32_t* k, const double* recall, int32_t k_max,
-                const int32_t* start_depth, int filter,
+                const int32_t* start_depth, int filter, int stop_every,
                 uint32_t* out_ids, float* out_sims, orc_stats* stats,
                 uint32_t* trace, int64_t trace_cap, int64_t* trace_len) {
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t t = 0; t < Q; ++t) {
     search_one(ix, q + t * ix->d, qcodes + t * ix->L, qsk + t * ix->M, k[t], recall[t], k_max,
-               start_depth ? start_depth[t] : -1, filter, out_ids + t * k_max, out_sims + t * k_max,
+               start_depth ? start_depth[t] : -1, filter, stop_every, out_ids + t * k_max, out_sims + t * k_max,
                stats ? stats + t : NULL, trace ? trace + 2 * t * trace_cap : NULL, trace_cap,
                trace_len ? trace_len + t : NULL);
   }

@@ -93,6 +93,7 @@ typedef struct {
   int32_t start_depth, stop_depth, rounds;
   int32_t full_depth; /* prefix length of the first round after which k points were held, -1 if none */
   int64_t retrieved, passed_filter, scored;
+  int32_t last_reps;  /* repetitions searched in the last round (L unless the stop test ran after a group) */
 } orc_stats;
 
 typedef struct {
@@ -108,14 +109,19 @@ typedef struct {
 /* Search Q normalised queries.  qcodes[Q][L], qsk[Q][M], k[Q], recall[Q].
  * start_depth: NULL (plain schedule K, K-1, ..., 0) or per-query start depth
  * i0 (schedule i0, i0-1, ..., 0; i0 outside [0, K) means K).
- * filter: 0/1.  Outputs [Q][k_max]; stats may be NULL.
+ * filter: 0/1.  stop_every: 0 = the stop test once per round (Sec. 4.1);
+ * G >= 1 = the test after every G repetitions and after the last (Alg. 1
+ * tests after every repetition: G = 1), with fail =
+ * (1 - p_i)^j (1 - p_{i+1})^(L - j) after j repetitions at depth i; the
+ * threshold is then also refreshed at every group of G repetitions.
+ * Outputs [Q][k_max]; stats may be NULL.
  * trace (may be NULL): per query up to trace_cap entries
  * (scored<<31 | depth<<24 | table, id) of every retrieved candidate in the order
  * visited, scored = 1 when it passed the sketch filter and was scored; count
  * in trace_len[q]. */
 void orc_search(const orc_index* ix, const float* q, const uint32_t* qcodes, const uint64_t* qsk,
                 int64_t Q, const int32_t* k, const double* recall, int32_t k_max,
-                const int32_t* start_depth, int filter,
+                const int32_t* start_depth, int filter, int stop_every,
                 uint32_t* out_ids, float* out_sims, orc_stats* stats,
                 uint32_t* trace, int64_t trace_cap, int64_t* trace_len);
 

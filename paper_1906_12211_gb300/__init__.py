@@ -30,6 +30,7 @@ ARRAYS = {"rows_f32": 0, "rows_bf16": 1, "codes": 2, "ids": 3, "prefix": 4, "ske
           "cp_table": 7, "table_sketches": 8, "rows_f16": 9, "mlp_f32": 10, "mlp_w1_bf16": 11, "mlp_w2_bf16": 12,
           "fht_signs": 13}
 ROW_STORAGE = {"f32": 0, "f16": 1}
+SCORING = {"fp32": 0, "bf16": 1}
 SKETCH_LAYOUTS = {"table": 0, "point": 1}
 
 
@@ -42,18 +43,18 @@ class BuildParams(C.Structure):
 
 class SearchOpts(C.Structure):
     _fields_ = [("scoring", C.c_int32), ("filter", C.c_int32), ("learned_start", C.c_int32),
-                ("timing", C.c_int32), ("start_depth", C.c_void_p)]
+                ("timing", C.c_int32), ("start_depth", C.c_void_p), ("stop_every", C.c_int32)]
 
 
 class QueryStats(C.Structure):
     _fields_ = [("start_depth", C.c_int32), ("stop_depth", C.c_int32), ("rounds", C.c_int32),
                 ("full_depth", C.c_int32), ("retrieved", C.c_int64), ("passed_filter", C.c_int64),
-                ("scored", C.c_int64), ("reranked", C.c_int64)]
+                ("scored", C.c_int64), ("reranked", C.c_int64), ("last_reps", C.c_int32)]
 
 
 STATS_DTYPE = np.dtype([("start_depth", np.int32), ("stop_depth", np.int32), ("rounds", np.int32),
                         ("full_depth", np.int32), ("retrieved", np.int64), ("passed_filter", np.int64),
-                        ("scored", np.int64), ("reranked", np.int64)])
+                        ("scored", np.int64), ("reranked", np.int64), ("last_reps", np.int32)], align=True)
 
 
 class IndexInfo(C.Structure):
@@ -256,7 +257,7 @@ class Index:
 
     def search(self, queries, k, recall, *, k_max: int | None = None, scoring: str = "fp32", filter: bool = True,
                start_depth=None, out_ids=None, out_sims=None, stats=None, stream=None, timing: bool = False,
-               learned: bool = False):
+               learned: bool = False, stop_every: int = 0):
         """Answer a batch of queries; k and recall are per-query arrays (same
         device as the queries) or scalars.  Returns (ids, sims, stats)."""
         import torch
@@ -279,10 +280,11 @@ class Index:
             stats = None
         o = SearchOpts()
         lib().pf_search_opts_default(C.byref(o))
-        o.scoring = 1 if scoring == "bf16" else 0
+        o.scoring = SCORING[scoring]
         o.filter = 1 if filter else 0
         o.timing = 1 if timing else 0
         o.learned_start = 1 if learned else 0
+        o.stop_every = int(stop_every)
         sd = None
         if start_depth is not None:
             sd = start_depth if torch.is_tensor(start_depth) else torch.full((Q,), int(start_depth),
@@ -294,31 +296,29 @@ class Index:
 
 
     def search_noalloc(self, queries, k, recall, out_ids, out_sims, *, k_max: int, scoring: str = "fp32",
-                       filter: bool = True, stats=None, stream=None):
+                       filter: bool = True, stats=None, stream=None, stop_every: int = 0):
         """pf_index_search_noalloc: every buffer already on the device, no
         allocation inside the call (fixed 32 MiB scratch)."""
-        o = SearchOpts()
-        lib().pf_search_opts_default(C.byref(o))
-        o.scoring = 1 if scoring == "bf16" else 0
-        o.filter = 1 if filter else 0
+        o = self._opts(scoring, filter, False, stop_every)
         _check(lib().pf_index_search_noalloc(self._h, _ptr(queries), int(queries.shape[0]), _ptr(k), _ptr(recall),
                                              int(k_max), _ptr(out_ids), _ptr(out_sims), _ptr(stats), C.byref(o),
                                              _stream_ptr(stream)))
         return out_ids, out_sims, stats
 
-    def _opts(self, scoring, filter, learned):
+    def _opts(self, scoring, filter, learned, stop_every=0):
         o = SearchOpts()
         lib().pf_search_opts_default(C.byref(o))
-        o.scoring = 1 if scoring == "bf16" else 0
+        o.scoring = SCORING[scoring]
         o.filter = 1 if filter else 0
         o.learned_start = 1 if learned else 0
+        o.stop_every = int(stop_every)
         return o
 
     def tune(self, queries, k: int, recall: float, *, scoring: str = "fp32", filter: bool = True,
-             learned: bool = False, stream=None):
+             learned: bool = False, stream=None, stop_every: int = 0):
         """pf_index_tune: time the search launch shapes on this batch and keep the fastest."""
         rep = TuneReport()
-        o = self._opts(scoring, filter, learned)
+        o = self._opts(scoring, filter, learned, stop_every)
         _check(lib().pf_index_tune(self._h, _ptr(queries), int(queries.shape[0]), int(k), float(recall),
                                    C.byref(o), C.byref(rep), _stream_ptr(stream)))
         return {f: getattr(rep, f) for f, _ in TuneReport._fields_}
@@ -345,10 +345,11 @@ class Index:
         _check(lib().pf_index_selftest_hold(self._h, 1 if hold else 0))
 
     def plan(self, queries, k, recall, out_ids, out_sims, *, k_max: int, stats=None, start_depth=None,
-             scoring: str = "fp32", filter: bool = True, learned: bool = False):
-        """pf_search_plan_create: a CUDA graph of this search bound to these device tensors."""
+             scoring: str = "fp32", filter: bool = True, learned: bool = False, stop_every: int = 0):
+        """pf_search_plan_create: a CUDA graph of this search bound to these device tensors (or
+        page-locked host tensors)."""
         return SearchPlan(self, queries, k, recall, out_ids, out_sims, k_max=k_max, stats=stats,
-                          start_depth=start_depth, opts=self._opts(scoring, filter, learned))
+                          start_depth=start_depth, opts=self._opts(scoring, filter, learned, stop_every))
 
     def last_timing(self):
         """(hash_ms, search_kernel_ms, total_ms) of the last search run with timing=True."""

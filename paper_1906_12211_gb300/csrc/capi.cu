@@ -443,6 +443,7 @@ pf_status pf_index_search(pf_index* ix, const float* queries, int64_t Q, const i
     pf_search_opts_default(&o);
     if (opts) o = *opts;
     if (o.scoring != 0 && o.scoring != 1) return fail(PF_ERR_INVALID_ARG, "scoring must be 0 or 1");
+    if (o.stop_every < 0) return fail(PF_ERR_INVALID_ARG, "stop_every must be >= 0");
     if (o.learned_start && !ix->mlp_trained) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
     if (Q == 0) return PF_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -483,6 +484,7 @@ pf_status pf_index_search(pf_index* ix, const float* queries, int64_t Q, const i
     a.k_max = k_max;
     a.filter = o.filter ? 1 : 0;
     a.scoring = o.scoring;
+    a.stop_every = o.stop_every;
     a.out_ids = ids_dev ? out_ids : ws.ids;
     a.out_sims = sims_dev ? out_sims : ws.sims;
     a.stats = stats ? (st_dev ? stats : ws.stats) : nullptr;
@@ -912,6 +914,7 @@ pf_status pf_index_tune(pf_index* ix, const float* queries, int64_t Q, int32_t k
     pf_search_opts_default(&o);
     if (opts) o = *opts;
     if (o.scoring != 0 && o.scoring != 1) return fail(PF_ERR_INVALID_ARG, "scoring must be 0 or 1");
+    if (o.stop_every < 0) return fail(PF_ERR_INVALID_ARG, "stop_every must be >= 0");
     if (o.learned_start && !ix->mlp_trained) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PF_CK(cudaSetDevice(ix->device));
@@ -946,6 +949,7 @@ pf_status pf_index_tune(pf_index* ix, const float* queries, int64_t Q, int32_t k
     a.k_max = k;
     a.filter = o.filter ? 1 : 0;
     a.scoring = o.scoring;
+    a.stop_every = o.stop_every;
     a.out_ids = ws.ids;
     a.out_sims = ws.sims;
     a.stats = nullptr;
@@ -1102,6 +1106,7 @@ void plan_sequence(pf_search_plan* pl, cudaStream_t s) {
   a.k_max = pl->k_max;
   a.filter = pl->opts.filter ? 1 : 0;
   a.scoring = pl->opts.scoring;
+  a.stop_every = pl->opts.stop_every;
   a.out_ids = io.out_ids;
   a.out_sims = io.out_sims;
   a.stats = io.stats;
@@ -1147,6 +1152,7 @@ pf_status pf_search_plan_create(pf_index* ix, int64_t Q, int32_t k_max, const pf
     pf_search_opts_default(&o);
     if (opts) o = *opts;
     if (o.scoring != 0 && o.scoring != 1) return fail(PF_ERR_INVALID_ARG, "scoring must be 0 or 1");
+    if (o.stop_every < 0) return fail(PF_ERR_INVALID_ARG, "stop_every must be >= 0");
     if (o.learned_start && !ix->mlp_trained) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
     o.start_depth = nullptr;
     o.timing = 0;

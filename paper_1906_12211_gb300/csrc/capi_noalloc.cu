@@ -86,6 +86,7 @@ extern "C" pf_status pf_index_search_noalloc(pf_index* ix, const float* queries,
     pf_search_opts_default(&o);
     if (opts) o = *opts;
     if (o.scoring != 0 && o.scoring != 1) return reject(PF_ERR_INVALID_ARG, "scoring must be 0 or 1");
+    if (o.stop_every < 0) return reject(PF_ERR_INVALID_ARG, "stop_every must be >= 0");
     if (o.learned_start)
       return reject(PF_ERR_INVALID_ARG, "the learned start depth needs pf_index_search (it uses the index workspace)");
     const size_t need = scratch_bytes(ix, Q);
@@ -139,6 +140,7 @@ extern "C" pf_status pf_index_search_noalloc(pf_index* ix, const float* queries,
     a.k_max = k_max;
     a.filter = o.filter ? 1 : 0;
     a.scoring = o.scoring;
+    a.stop_every = o.stop_every;
     a.out_ids = out_ids;
     a.out_sims = out_sims;
     a.stats = stats;

@@ -124,7 +124,8 @@ void gen_hash_rows(uint64_t seed, int family, int L, int M, int d, const Layout&
     for (int i = 0; i < d; ++i) s = s + double(row[i]) * double(row[i]);
     return float(std::ldexp(std::sqrt(s), -12));
   };
-  parallel_for(L, [&](int64_t j) {
+  // the pseudo-random family keeps no rows for its repetitions (sign vectors instead)
+  parallel_for(lay.rows_table > 0 ? L : 0, [&](int64_t j) {
     for (int f = 0; f < lay.fns; ++f) {
       const int nrow = family == PF_CROSSPOLYTOPE ? d : 1;
       float band = 0.f;

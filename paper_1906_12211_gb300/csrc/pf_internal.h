@@ -205,6 +205,7 @@ struct SearchArgs {
   float* out_sims = nullptr;
   pf_query_stats* stats = nullptr;
   int32_t* counter = nullptr;
+  int stop_every = 0;  // pf_search_opts.stop_every
 };
 cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t s);
 // CTAs per SM the search kernel can keep resident for this index (0 on error)

@@ -84,6 +84,7 @@ struct Dev {
   // <= 13), [1] sides settled within the first probed boundaries, [2] sides
   // that galloped past them
   unsigned long long* path_count;
+  int stop_every;  // 0: stop test per round; G: also after every G repetitions (Alg. 1)
 };
 
 __device__ __forceinline__ bool better(float s1, uint32_t i1, float s2, uint32_t i2) {
@@ -447,6 +448,7 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
 
     int rounds = 0, depth = i0, prev = -1, stop_depth = i0;  // prev < 0: probe both sides
     int full_depth = -1;  // first depth after whose round k points were held
+    int last_reps = L;    // repetitions searched in the last round
     Counters ct;
     int wsize = 0;  // entries of this warp's list
     for (;;) {
@@ -612,10 +614,15 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
       __syncthreads();
 
       // ---- stream the chunks, group by group
-      const int ngroups = rounds == 0 ? (L + kGroup - 1) / kGroup : 1;
+      // groups of repetitions: in a first round (threshold snapshots), and in
+      // every round when the stop test also runs after groups of G repetitions
+      const bool grouped = rounds == 0 || P.stop_every > 0;
+      const int G = P.stop_every > 0 ? P.stop_every : kGroup;
+      const int ngroups = grouped ? (L + G - 1) / G : 1;
+      bool stopped_mid = false;
       for (int grp = 0; grp < ngroups; ++grp) {
-        const int j0 = rounds == 0 ? grp * kGroup : 0;
-        const int j1 = rounds == 0 ? min(L, j0 + kGroup) : L;
+        const int j0 = grouped ? grp * G : 0;
+        const int j1 = grouped ? min(L, j0 + G) : L;
         // threshold snapshot: every earlier candidate is in the merged top-k
         const int gsize = s_size;
         const float gkth = gsize == k ? gs[k - 1] : -INFINITY;
@@ -695,11 +702,34 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
         }
         wsize = 0;
         __syncthreads();
+        if (P.stop_every > 0 && j1 < L) {
+          // Alg. 1: the stop test after repetitions 0..j1-1 searched to this
+          // prefix length and the others to depth + 1 (to nothing yet in a
+          // first round); after the last group it is the round's test below
+          if (tid == 0) {
+            int stop = 0;
+            if (s_size == k) {
+              const float skf = gs[k - 1];
+              double fail = ipow(__dsub_rn(1.0, collision_prob(P, s_alpha, skf, depth)), j1);
+              if (rounds > 0)
+                fail = __dmul_rn(fail, ipow(__dsub_rn(1.0, collision_prob(P, s_alpha, skf, depth + 1)), L - j1));
+              stop = fail <= delta ? 1 : 0;
+            }
+            s_stop = stop;
+          }
+          __syncthreads();
+          if (s_stop) {
+            stopped_mid = true;
+            last_reps = j1;
+            break;
+          }
+        }
       }
       ++rounds;
       stop_depth = depth;
       const int size = s_size;
       if (size == k && full_depth < 0) full_depth = depth;
+      if (stopped_mid) break;
       if (tid == 0) {
         int stop = 0;
         if (size == k) {
@@ -740,7 +770,8 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
       st.retrieved = sum[0];
       st.passed_filter = sum[1];
       st.scored = sum[2];
-      st.reranked = P.scoring == 1 ? sum[3] : 0;
+      st.reranked = P.scoring != 0 ? sum[3] : 0;
+      st.last_reps = last_reps;
       P.stats[qi] = st;
     }
   }

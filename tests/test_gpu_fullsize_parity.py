@@ -89,3 +89,12 @@ def test_every_launch_shape_at_full_n(both, shape):
     finally:
         g.set_shape(8, 4, 0)
     _compare(out, ref)
+
+
+@pytest.mark.parametrize("G", [1, 8])
+def test_stop_every_at_full_n(both, G):
+    g, o, Q, qd = both
+    ref = o.search(Q, 10, 0.9, stop_every=G)
+    out = g.search(qd, 10, 0.9, scoring="bf16", stats=True, stop_every=G)
+    _compare(out, ref)
+    assert np.array_equal(pf.stats_to_numpy(out[2])["last_reps"], ref["stats"]["last_reps"])

@@ -240,6 +240,7 @@ def _compare(gpu_out, ref, check_stats=True):
         deep = o["stop_depth"] > 0
         assert np.array_equal(g["retrieved"][deep], o["retrieved"][deep])
         assert np.array_equal(g["passed_filter"][deep], o["passed_filter"][deep])
+        assert np.array_equal(g["last_reps"], o["last_reps"])
 
 
 @pytest.mark.parametrize("case", CASES, indirect=True)
@@ -349,3 +350,25 @@ def test_invalid_launch_shapes_are_rejected(cpmid):
         with pytest.raises(pf.PuffinnError) as e:
             cpmid.gpu.set_shape(*bad)
         assert e.value.status == -1
+
+
+# ------------------------------------------------------------------ stop test after groups of repetitions
+@pytest.mark.parametrize("case", ["cfg1", "cpmid", "cpwide", "cpmidpp"], indirect=True)
+@pytest.mark.parametrize("G", [1, 5, 32])
+@pytest.mark.parametrize("scoring", ["fp32", "bf16"])
+def test_stop_every_bit_exact(case, G, scoring):
+    """Alg. 1's stop test after every G repetitions: the same stop depth and the
+    same number of repetitions searched in the last round as the oracle."""
+    ref = case.orc.search(case.Q, 10, 0.9, stop_every=G)
+    out = case.gpu.search(case.qd, 10, 0.9, scoring=scoring, stats=True, stop_every=G)
+    _compare(out, ref)
+    assert np.any(ref["stats"]["last_reps"] < case.gpu.L) or G >= case.gpu.L
+
+
+def test_stop_every_with_start_depths_and_mixed_k(cpmid):
+    k, rec = datagen.mixed_k_recall(cpmid.Q.shape[0], seed=6)
+    sd = np.random.default_rng(2).integers(0, cpmid.gpu.Kb + 1, cpmid.Q.shape[0]).astype(np.int32)
+    ref = cpmid.orc.search(cpmid.Q, k, rec, k_max=128, start_depth=sd, stop_every=3)
+    out = cpmid.gpu.search(cpmid.qd, torch.from_numpy(k).to(DEV), torch.from_numpy(rec).to(DEV), k_max=128,
+                           start_depth=torch.from_numpy(sd).to(DEV), stats=True, scoring="bf16", stop_every=3)
+    _compare(out, ref)

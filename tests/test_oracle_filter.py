@@ -148,7 +148,7 @@ _MUTANTS = {
     "ge_instead_of_gt": ("if (ham > tau) continue;", "if (ham >= tau) continue;"),
     "query_sketch_index": ("popcount64(qsk[j % M] ^", "popcount64(qsk[(j + 1) % M] ^"),
     "no_first_round_groups": ("(s.rounds == 0 && j % ORC_SNAPSHOT_GROUP == 0)", "(0)"),
-    "no_refresh_per_round": ("if (j == 0 || (s.rounds", "if ((j == 0 && s.rounds == 0) || (s.rounds"),
+    "no_refresh_per_round": ("if (j == 0 || (stop_every", "if ((j == 0 && s.rounds == 0) || (stop_every"),
     "kth_from_wrong_slot": ("orc_filter_tau((double)ps[k - 1])", "orc_filter_tau((double)ps[0])"),
 }
 
