@@ -84,6 +84,9 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other two modes")
     ap.add_argument("--recall", type=float, default=None,
                     help="recall target 1 - delta passed to the index (default: the workload's)")
+    ap.add_argument("--estimate", default="bf16", choices=["bf16", "fp8"],
+                    help="row copy the estimate-and-rerank modes score with: bfloat16, or e4m3 with per-row scales "
+                         "(the index then keeps an e4m3 copy, which the budget counts)")
     ap.add_argument("--stop-every", type=int, default=0,
                     help="0: the stop test after each round (Sec. 4.1); G: also after every G repetitions (Alg. 1)")
     ap.add_argument("--family", default="crosspolytope", choices=["crosspolytope", "fht"],
@@ -174,7 +177,8 @@ def search_kernel_traffic(args=None):
     if args is not None and (args.points is not None or args.queries is not None or args.budget is not None
                              or args.mode != "learned" or args.train_queries != 100_000 or args.epochs != 20
                              or args.recall != 0.9 or getattr(args, "workload", WORKLOAD) != WORKLOAD
-                             or getattr(args, "family", "crosspolytope") != "crosspolytope"):
+                             or getattr(args, "family", "crosspolytope") != "crosspolytope"
+                             or getattr(args, "estimate", "bf16") != "bf16" or getattr(args, "stop_every", 0)):
         return None
     path = os.path.join(ROOT, "profiles", "search_kernel_traffic.txt")
     src = os.path.join(ROOT, "paper_1906_12211_gb300", "csrc", "search_kernel.cuh")
@@ -253,12 +257,12 @@ def algorithmic_bytes(st, L, n, d, k, mode):
     """Bytes a query must touch (per query, averaged): prefix lookups and the
     binary search for every repetition, id + sketch per retrieved candidate
     (the per-repetition sketch layout), the row of every scored candidate
-    (bf16 or fp32), the fp32 row of every reranked one, the query and the
-    output."""
+    (bf16, e4m3 + its 8-byte scale and bound, or fp32), the fp32 row of every
+    reranked one, the query and the output."""
     import math
 
     probes = max(1, math.ceil(math.log2(max(2, n / 8192))))
-    per_row = d * (2 if mode == "bf16" else 4)
+    per_row = {"bf16": d * 2, "fp8": d + 8}.get(mode, d * 4)
     b = (L * (8 + probes * 4) + st["retrieved"].astype(np.float64) * (4 + 8)
          + st["scored"].astype(np.float64) * per_row + st["reranked"].astype(np.float64) * d * 4 + d * 4 + k * 8)
     return float(b.mean())
@@ -418,7 +422,7 @@ def main():
     Qd = [torch.from_numpy(Qs).to(dev), torch.from_numpy(Qs2).to(dev)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ix = pf.Index(Xd, args.family, budget_bytes=w["budget"], seed=0)
+    ix = pf.Index(Xd, args.family, budget_bytes=w["budget"], seed=0, fp8_rows=args.estimate == "fp8")
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     kth = [brute_force_kth(torch, Xd, q, k) for q in Qd]
@@ -445,11 +449,12 @@ def main():
     if not args.no_tune:
         Qtune = queries(w, Q, "tune", rank)
         tune_report = ix.tune(torch.from_numpy(Qtune).to(dev), k, args.recall,
-                              scoring="fp32" if args.mode == "fp32" else "bf16", learned=args.mode == "learned",
+                              scoring="fp32" if args.mode == "fp32" else args.estimate,
+                              learned=args.mode == "learned",
                               stop_every=args.stop_every)
 
     def opts_of(mode):
-        return ("fp32" if mode == "fp32" else "bf16"), mode == "learned"
+        return ("fp32" if mode == "fp32" else args.estimate), mode == "learned"
 
     def outputs():
         return (torch.empty((Q, k), dtype=torch.int32, device=dev), torch.empty((Q, k), dtype=torch.float32, device=dev),
@@ -628,7 +633,8 @@ def main():
         line = {
             "metric": METRICS[args.workload], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": vs_baseline, "dtype": "f32" if args.mode == "fp32" else "bf16+f32",
+            "scaling": "weak", "vs_baseline": vs_baseline,
+            "dtype": "f32" if args.mode == "fp32" else ("e4m3+f32" if args.estimate == "fp8" else "bf16+f32"),
             "mode": args.mode,
             "data": "synthetic",
             "config": {"workload": args.workload, "n": ix.n, "d": ix.d, "queries_per_gpu": Q, "k": k,

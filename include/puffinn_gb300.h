@@ -88,11 +88,16 @@ typedef struct {
   int32_t num_tables;           /* if > 0, use exactly this L instead of the budget (tests, sweeps) */
   int32_t sketch_layout;        /* pf_sketch_layout; 0 -> PF_SKETCH_PER_TABLE */
   int32_t row_storage;          /* pf_row_storage; 0 -> PF_ROWS_F32 */
+  int32_t fp8_rows;             /* 1: also keep an 8-bit float (e4m3) copy of the rows with a scale and an error
+                                   bound per row, for scoring 2; counted in the budget (n * (d_pad + 8) bytes) */
 } pf_build_params;
 
 /* Per-call search options.  NULL = defaults (FP32 scoring, filter on). */
 typedef struct {
-  int32_t scoring;             /* 0: float32 scoring; 1: bfloat16 scoring + exact float32 rerank */
+  int32_t scoring;             /* 0: float32 scoring; 1: bfloat16 estimate + exact float32 rerank; 2: 8-bit float
+                                  (e4m3, per-row scale) estimate + exact float32 rerank (an index built with
+                                  fp8_rows).  Estimates only drop candidates that provably cannot enter the top-k,
+                                  so every mode returns the float32 mode's results */
   int32_t filter;              /* 1: sketch filter on (Sec. 4.2); 0: off.  Set by pf_search_opts_default */
   int32_t learned_start;       /* 1: start depth from the trained model (needs pf_learned_train) */
   int32_t timing;              /* 1: record CUDA events around each phase (see pf_index_last_timing) */
@@ -118,6 +123,7 @@ typedef struct {
   int64_t reranked;      /* exact float32 similarities recomputed after a bfloat16 estimate */
   int32_t last_reps;     /* repetitions searched in the last round: L, or fewer when the stop test ran after
                             groups of repetitions (pf_search_opts.stop_every) and held mid-round */
+  int32_t reserved;      /* always 0 (keeps the struct free of padding) */
 } pf_query_stats;
 
 typedef struct {
@@ -157,8 +163,11 @@ typedef enum {
                                   also what inference uses) */
   PF_ARRAY_MLP_W1_BF16 = 11,   /* bfloat16 [F][H]: W1 rounded to nearest even, transposed, as inference reads it */
   PF_ARRAY_MLP_W2_BF16 = 12,   /* bfloat16 [C][H]: W2 rounded to nearest even, as inference reads it */
-  PF_ARRAY_FHT_SIGNS = 13      /* uint32 [L][fns][3][W]: sign bits of D1, D2, D3 of every pseudo-random CP function,
+  PF_ARRAY_FHT_SIGNS = 13,     /* uint32 [L][fns][3][W]: sign bits of D1, D2, D3 of every pseudo-random CP function,
                                   W = max(1, d''/32) words, bit i of a vector set = -1 (PF_CROSSPOLYTOPE_FHT only) */
+  PF_ARRAY_ROWS_FP8 = 14,      /* e4m3 [n][d_pad]: x_i / scale rounded to nearest even, saturated (fp8_rows only) */
+  PF_ARRAY_FP8_META = 15       /* float [n][2]: scale, and the bound on |<q, x> - scale <q, x8>| + rounding for
+                                  any unit q (fp8_rows only) */
 } pf_array;
 
 /* Build the index over `points` ([n][d] row-major, host or device).

@@ -84,7 +84,7 @@ def lib():
                 "orc_collision_prob": (f64, [C.c_int, C.c_int, vp, f64, C.c_int]),
                 "orc_ipow": (f64, [f64, i64]),
                 "orc_filter_tau": (C.c_int, [f64]),
-                "orc_budget_L": (i64, [C.c_int, i64, C.c_int, C.c_int, u64, C.c_int, C.c_int]),
+                "orc_budget_L": (i64, [C.c_int, i64, C.c_int, C.c_int, u64, C.c_int, C.c_int, C.c_int]),
                 "orc_sim": (C.c_float, [vp, vp, C.c_int]),
                 "orc_search": (None, [vp, vp, vp, vp, i64, vp, vp, i32, vp, C.c_int, C.c_int, vp, vp, vp, vp, i64, vp]),
                 "orc_brute_force": (None, [vp, i64, C.c_int, vp, i64, C.c_int, vp, vp]),
@@ -230,10 +230,11 @@ def filter_tau(s_k: float) -> int:
 
 
 def budget_L(family: int, n: int, d: int, M: int, budget_bytes: int, sketch_layout: int = 0,
-             row_storage: int = 0) -> int:
+             row_storage: int = 0, fp8_rows: int = 0) -> int:
     """sketch_layout 0: a sketch per repetition entry; 1: M sketches per point.
-    row_storage 0: float32 rows; 1: binary16 rows."""
-    return int(lib().orc_budget_L(family, n, d, M, budget_bytes, sketch_layout, row_storage))
+    row_storage 0: float32 rows; 1: binary16 rows.  fp8_rows 1: an 8-bit float
+    copy of the rows is kept too."""
+    return int(lib().orc_budget_L(family, n, d, M, budget_bytes, sketch_layout, row_storage, fp8_rows))
 
 
 def round_rows_f16(x: np.ndarray) -> np.ndarray:

@@ -441,7 +441,7 @@ int orc_filter_tau(double s_k) {
  *               R = F * d' for CP (rows of a function padded to d'), 32 for HP
  *   L = floor((budget - fixed) / per_table). */
 int64_t orc_budget_L(int family, int64_t n, int d, int M, uint64_t budget_bytes, int sketch_layout,
-                     int row_storage) {
+                     int row_storage, int fp8_rows) {
   int64_t dp = ((int64_t)d + 15) / 16 * 16;
   int F;
   orc_layout(family == ORC_CROSSPOLYTOPE_FHT ? ORC_CROSSPOLYTOPE : family, d, NULL, &F, NULL, NULL);
@@ -457,6 +457,8 @@ int64_t orc_budget_L(int family, int64_t n, int d, int M, uint64_t budget_bytes,
   /* rows: float32 (4 B) or binary16 (2 B) per element, plus the bfloat16 copy (2 B) */
   int64_t row_bytes = row_storage == 1 ? 4 : 6;
   int64_t fixed = n * dp * row_bytes + 64 * (int64_t)M * dp * 8 + (sketch_layout == 1 ? n * (int64_t)M * 8 : 0);
+  /* an 8-bit float copy of the rows, with a scale and an error bound each */
+  if (fp8_rows) fixed += n * (dp + 8);
   int64_t per_table = n * (sketch_layout == 1 ? 8 : 16) + (int64_t)((1 << ORC_PREFIX_BITS) + 1) * 4 + R * dp * 8 +
                       fht_bytes;
   if ((int64_t)budget_bytes <= fixed) return 0;

@@ -81,9 +81,10 @@ int orc_filter_tau(double s_k);
 /* ---- memory budget -> number of repetitions (Sec. 5, index size) ----
  * sketch_layout 0: one sketch copy per repetition entry; 1: M per point.
  * row_storage 0: normalised rows kept in float32; 1: in binary16 (Sec. 4.2
- * keeps 16-bit vectors); a bfloat16 copy is kept either way. */
+ * keeps 16-bit vectors); a bfloat16 copy is kept either way.  fp8_rows 1: an
+ * 8-bit float copy with a scale and a bound per row is kept too. */
 int64_t orc_budget_L(int family, int64_t n, int d, int M, uint64_t budget_bytes, int sketch_layout,
-                     int row_storage);
+                     int row_storage, int fp8_rows);
 
 /* ---- canonical float32 inner product ---- */
 float orc_sim(const float* q, const float* x, int d);

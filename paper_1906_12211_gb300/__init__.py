@@ -28,9 +28,10 @@ STATUS = {0: "PF_OK", -1: "PF_ERR_INVALID_ARG", -2: "PF_ERR_BUDGET_TOO_SMALL", -
 
 ARRAYS = {"rows_f32": 0, "rows_bf16": 1, "codes": 2, "ids": 3, "prefix": 4, "sketches": 5, "hash_rows": 6,
           "cp_table": 7, "table_sketches": 8, "rows_f16": 9, "mlp_f32": 10, "mlp_w1_bf16": 11, "mlp_w2_bf16": 12,
-          "fht_signs": 13}
+          "fht_signs": 13,
+          "rows_fp8": 14, "fp8_meta": 15}
 ROW_STORAGE = {"f32": 0, "f16": 1}
-SCORING = {"fp32": 0, "bf16": 1}
+SCORING = {"fp32": 0, "bf16": 1, "fp8": 2}
 SKETCH_LAYOUTS = {"table": 0, "point": 1}
 
 
@@ -38,7 +39,7 @@ class BuildParams(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("dtype", C.c_int32), ("family", C.c_int32),
                 ("num_sketches", C.c_int32), ("memory_budget_bytes", C.c_uint64), ("seed", C.c_uint64),
                 ("segment_B", C.c_int32), ("cp_draws", C.c_int32), ("num_tables", C.c_int32),
-                ("sketch_layout", C.c_int32), ("row_storage", C.c_int32)]
+                ("sketch_layout", C.c_int32), ("row_storage", C.c_int32), ("fp8_rows", C.c_int32)]
 
 
 class SearchOpts(C.Structure):
@@ -49,12 +50,13 @@ class SearchOpts(C.Structure):
 class QueryStats(C.Structure):
     _fields_ = [("start_depth", C.c_int32), ("stop_depth", C.c_int32), ("rounds", C.c_int32),
                 ("full_depth", C.c_int32), ("retrieved", C.c_int64), ("passed_filter", C.c_int64),
-                ("scored", C.c_int64), ("reranked", C.c_int64), ("last_reps", C.c_int32)]
+                ("scored", C.c_int64), ("reranked", C.c_int64), ("last_reps", C.c_int32), ("reserved", C.c_int32)]
 
 
 STATS_DTYPE = np.dtype([("start_depth", np.int32), ("stop_depth", np.int32), ("rounds", np.int32),
                         ("full_depth", np.int32), ("retrieved", np.int64), ("passed_filter", np.int64),
-                        ("scored", np.int64), ("reranked", np.int64), ("last_reps", np.int32)], align=True)
+                        ("scored", np.int64), ("reranked", np.int64), ("last_reps", np.int32),
+                        ("reserved", np.int32)])
 
 
 class IndexInfo(C.Structure):
@@ -185,12 +187,13 @@ class Index:
 
     def __init__(self, points, family="crosspolytope", *, budget_bytes: int = 0, num_tables: int = 0,
                  seed: int = 0, num_sketches: int = 32, segment_B: int = 12, cp_draws: int = 1000,
-                 sketch_layout: str = "table", rows: str = "f32", stream=None):
+                 sketch_layout: str = "table", rows: str = "f32", fp8_rows: bool = False, stream=None):
         n, d = int(points.shape[0]), int(points.shape[1])
         p = BuildParams(n=n, d=d, dtype=0, family=_family(family), num_sketches=num_sketches,
                         memory_budget_bytes=int(budget_bytes), seed=int(seed), segment_B=segment_B,
                         cp_draws=cp_draws, num_tables=int(num_tables),
-                        sketch_layout=SKETCH_LAYOUTS[sketch_layout], row_storage=ROW_STORAGE[rows])
+                        sketch_layout=SKETCH_LAYOUTS[sketch_layout], row_storage=ROW_STORAGE[rows],
+                        fp8_rows=1 if fp8_rows else 0)
         self._points_keepalive = points
         h = C.c_void_p()
         _check(lib().pf_index_build(C.byref(p), _ptr(points), C.byref(h), _stream_ptr(stream)))

@@ -161,6 +161,8 @@ void destroy(pf_index* ix) {
   dfree(ix->dev_error);
   dfree(ix->path_count);
   dfree(ix->fht_signs);
+  dfree(ix->x8);
+  dfree(ix->x8_meta);
   dfree(ix->mlp_w);
   dfree(ix->mlp_w1h);
   dfree(ix->mlp_w2h);
@@ -261,7 +263,7 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       return fail(PF_ERR_INVALID_ARG, "unknown row storage");
     int64_t L = prm->num_tables > 0 ? prm->num_tables
                                     : budget_tables(prm->family, prm->n, prm->d, M, prm->memory_budget_bytes,
-                                                    prm->sketch_layout, prm->row_storage);
+                                                    prm->sketch_layout, prm->row_storage, prm->fp8_rows);
     if (L < 1) return fail(PF_ERR_BUDGET_TOO_SMALL, "memory budget leaves room for no repetition");
     if (prm->num_tables > kMaxL)
       return fail(PF_ERR_INVALID_ARG, "num_tables above " + std::to_string(kMaxL) + " is not supported");
@@ -282,7 +284,8 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       ix->budget = prm->memory_budget_bytes;
       ix->sketch_layout = prm->sketch_layout;
       ix->row_storage = prm->row_storage;
-      ix->bytes_used = resident_bytes(prm->family, prm->n, prm->d, M, ix->L, prm->sketch_layout, prm->row_storage);
+      ix->bytes_used =
+          resident_bytes(prm->family, prm->n, prm->d, M, ix->L, prm->sketch_layout, prm->row_storage, prm->fp8_rows);
       const int dp = ix->lay.d_pad;
       const int64_t n = ix->n;
       ix->hash_rows = int64_t(ix->L) * ix->lay.rows_table + 64LL * M;
@@ -296,6 +299,10 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       else
         dalloc(&ix->x32, size_t(n) * dp);
       dalloc(&ix->x16, size_t(n) * dp);
+      if (prm->fp8_rows) {
+        dalloc(&ix->x8, size_t(n) * dp);
+        dalloc(&ix->x8_meta, size_t(n));
+      }
       if (ix->sketch_layout == PF_SKETCH_PER_POINT)
         dalloc(&ix->sk, size_t(n) * M);
       else
@@ -371,6 +378,7 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
         PF_CK(launch_normalize(pin, n, prm->d, dp, x32, ix->x16, xlo, s));
         if (ix->row_storage == PF_ROWS_F16)  // the stored point is the binary16 row: hash that
           PF_CK(launch_round_rows_f16(x32, n, dp, ix->xf16, ix->x16, xlo, s));
+        if (ix->x8) PF_CK(launch_quantize_fp8(x32, n, prm->d, dp, ix->x8, ix->x8_meta, s));
         dalloc(&raw_codes, size_t(n) * ix->L);
         dalloc(&rq, recheck_capacity(n));
         dalloc(&rq_count, size_t(ix->num_sms));
@@ -442,7 +450,8 @@ pf_status pf_index_search(pf_index* ix, const float* queries, int64_t Q, const i
     pf_search_opts o;
     pf_search_opts_default(&o);
     if (opts) o = *opts;
-    if (o.scoring != 0 && o.scoring != 1) return fail(PF_ERR_INVALID_ARG, "scoring must be 0 or 1");
+    if (o.scoring < 0 || o.scoring > 2) return fail(PF_ERR_INVALID_ARG, "scoring must be 0, 1 or 2");
+    if (o.scoring == 2 && !ix->x8) return fail(PF_ERR_INVALID_ARG, "scoring 2 needs an index built with fp8_rows");
     if (o.stop_every < 0) return fail(PF_ERR_INVALID_ARG, "stop_every must be >= 0");
     if (o.learned_start && !ix->mlp_trained) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
     if (Q == 0) return PF_OK;
@@ -578,6 +587,12 @@ pf_status pf_index_array(const pf_index* ix, int32_t which, const void** ptr, ui
       if (!ix->fht_signs) return fail(PF_ERR_INVALID_ARG, "index is not of the pseudo-random cross-polytope family");
       *ptr = ix->fht_signs;
       *bytes = uint64_t(ix->L) * ix->lay.fns * 3 * ix->lay.fht_words * 4;
+      break;
+    case PF_ARRAY_ROWS_FP8:
+    case PF_ARRAY_FP8_META:
+      if (!ix->x8) return fail(PF_ERR_INVALID_ARG, "index was built without fp8_rows");
+      *ptr = which == PF_ARRAY_ROWS_FP8 ? static_cast<const void*>(ix->x8) : static_cast<const void*>(ix->x8_meta);
+      *bytes = which == PF_ARRAY_ROWS_FP8 ? n * dp : n * 8;
       break;
     case PF_ARRAY_MLP_F32:
     case PF_ARRAY_MLP_W1_BF16:
@@ -913,7 +928,8 @@ pf_status pf_index_tune(pf_index* ix, const float* queries, int64_t Q, int32_t k
     pf_search_opts o;
     pf_search_opts_default(&o);
     if (opts) o = *opts;
-    if (o.scoring != 0 && o.scoring != 1) return fail(PF_ERR_INVALID_ARG, "scoring must be 0 or 1");
+    if (o.scoring < 0 || o.scoring > 2) return fail(PF_ERR_INVALID_ARG, "scoring must be 0, 1 or 2");
+    if (o.scoring == 2 && !ix->x8) return fail(PF_ERR_INVALID_ARG, "scoring 2 needs an index built with fp8_rows");
     if (o.stop_every < 0) return fail(PF_ERR_INVALID_ARG, "stop_every must be >= 0");
     if (o.learned_start && !ix->mlp_trained) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1151,7 +1167,8 @@ pf_status pf_search_plan_create(pf_index* ix, int64_t Q, int32_t k_max, const pf
     pf_search_opts o;
     pf_search_opts_default(&o);
     if (opts) o = *opts;
-    if (o.scoring != 0 && o.scoring != 1) return fail(PF_ERR_INVALID_ARG, "scoring must be 0 or 1");
+    if (o.scoring < 0 || o.scoring > 2) return fail(PF_ERR_INVALID_ARG, "scoring must be 0, 1 or 2");
+    if (o.scoring == 2 && !ix->x8) return fail(PF_ERR_INVALID_ARG, "scoring 2 needs an index built with fp8_rows");
     if (o.stop_every < 0) return fail(PF_ERR_INVALID_ARG, "stop_every must be >= 0");
     if (o.learned_start && !ix->mlp_trained) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
     o.start_depth = nullptr;

@@ -85,7 +85,8 @@ extern "C" pf_status pf_index_search_noalloc(pf_index* ix, const float* queries,
     pf_search_opts o;
     pf_search_opts_default(&o);
     if (opts) o = *opts;
-    if (o.scoring != 0 && o.scoring != 1) return reject(PF_ERR_INVALID_ARG, "scoring must be 0 or 1");
+    if (o.scoring < 0 || o.scoring > 2) return reject(PF_ERR_INVALID_ARG, "scoring must be 0, 1 or 2");
+    if (o.scoring == 2 && !ix->x8) return reject(PF_ERR_INVALID_ARG, "scoring 2 needs an index built with fp8_rows");
     if (o.stop_every < 0) return reject(PF_ERR_INVALID_ARG, "stop_every must be >= 0");
     if (o.learned_start)
       return reject(PF_ERR_INVALID_ARG, "the learned start depth needs pf_index_search (it uses the index workspace)");

@@ -5,6 +5,8 @@
 
 #include <algorithm>
 
+#include <cuda_fp8.h>
+
 #include "pf_internal.h"
 
 namespace pf {
@@ -37,6 +39,34 @@ __global__ void normalize_kernel(const float* __restrict__ in, int64_t rows, int
       if (xl) xl[r * d_pad + i] = __float2bfloat16_rn(y - __bfloat162float(h));
     }
   }
+}
+
+// e4m3 copy of a normalised row: scale = max |x_i| / 448 (the largest finite
+// e4m3 value), code_i = e4m3(x_i / scale) rounded to nearest even, saturated.
+// meta = (scale, bound) with bound >= |<q, x> - scale * <q, dec(code)>| plus
+// the float32 rounding of the estimate and of the canonical similarity, for
+// any q with |q|_2 <= 1 + 2^-16: by Cauchy-Schwarz the first part is at most
+// |q| |x - scale dec(code)|_2, the residual norm taken here in float64.
+__global__ void quantize_fp8_kernel(const float* __restrict__ x32, int64_t rows, int d, int d_pad,
+                                    uint8_t* __restrict__ x8, float2* __restrict__ meta) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const float* row = x32 + r * d_pad;
+  float mx = 0.f;
+  for (int i = 0; i < d; ++i) mx = fmaxf(mx, fabsf(row[i]));
+  const float scale = mx > 0.f ? mx / 448.f : 1.f;
+  double res = 0.0;
+  for (int i = 0; i < d_pad; ++i) {
+    uint8_t c = 0;
+    if (i < d) c = __nv_cvt_float_to_fp8(row[i] / scale, __NV_SATFINITE, __NV_E4M3);
+    x8[r * d_pad + i] = c;
+    const float dec = __half2float(__half(__nv_cvt_fp8_to_halfraw(c, __NV_E4M3)));
+    const double e = double(row[i]) - double(scale) * double(dec);  // the product is exact in float64
+    res += e * e;
+  }
+  const double en = sqrt(res) * (1.0 + 1e-12);
+  const double bound = (1.0 + ldexp(1.0, -16)) * (en + (2.0 * d_pad + 2.0) * ldexp(1.0, -24) * (1.0 + en));
+  meta[r] = make_float2(scale, __double2float_ru(bound));
 }
 
 __global__ void round_rows_f16_kernel(float* __restrict__ x32, int64_t count, __half* __restrict__ xf16,
@@ -266,6 +296,13 @@ __global__ void __launch_bounds__(kHashPts * kHashGroups) hash_simt_kernel(
     else
       sk[int64_t(g - L) * sm + p * sp] = bits;
   }
+}
+
+cudaError_t launch_quantize_fp8(const float* x32, int64_t rows, int d, int d_pad, uint8_t* x8, float2* meta,
+                                cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  quantize_fp8_kernel<<<unsigned((rows + 255) / 256), 256, 0, s>>>(x32, rows, d, d_pad, x8, meta);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_hash(const pf_index* ix, const float* x32, const __nv_bfloat16* xh, const __nv_bfloat16* xl,

@@ -39,6 +39,8 @@ cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t 
   P.x32 = ix->x32;
   P.xf16 = ix->xf16;
   P.x16 = ix->x16;
+  P.x8 = ix->x8;
+  P.x8_meta = ix->x8_meta;
   P.codes = ix->codes;
   P.ids = ix->ids;
   P.pfx = ix->pfx;

@@ -325,12 +325,13 @@ void filter_cos_table(double* c) {
 // with per-repetition sketches, one uint64 per entry.  Fixed: the rows
 // (float32 + bfloat16), the sketch planes and, with per-point sketches, the M
 // sketches of every point.
-uint64_t resident_bytes(int family, int64_t n, int d, int M, int L, int sketch_layout, int row_storage) {
+uint64_t resident_bytes(int family, int64_t n, int d, int M, int L, int sketch_layout, int row_storage, int fp8_rows) {
   const Layout lay = make_layout(family, d);
   const int64_t dp = lay.d_pad;
   const bool per_point = sketch_layout == PF_SKETCH_PER_POINT;
   const int64_t row_bytes = row_storage == PF_ROWS_F16 ? 4 : 6;  // rows (4 or 2 B) + the bfloat16 copy (2 B)
-  const int64_t fixed = n * dp * row_bytes + 64LL * M * dp * 8 + (per_point ? n * int64_t(M) * 8 : 0);
+  const int64_t fixed = n * dp * row_bytes + 64LL * M * dp * 8 + (per_point ? n * int64_t(M) * 8 : 0) +
+                        (fp8_rows ? n * (dp + 8) : 0);  // e4m3 rows + (scale, bound) per row
   // pseudo-random CP: three sign vectors per function instead of rows
   const int64_t fht = family == PF_CROSSPOLYTOPE_FHT ? int64_t(lay.fns) * 3 * lay.fht_words * 4 : 0;
   const int64_t per_table =
@@ -338,10 +339,11 @@ uint64_t resident_bytes(int family, int64_t n, int d, int M, int L, int sketch_l
   return uint64_t(fixed + per_table * L);
 }
 
-int64_t budget_tables(int family, int64_t n, int d, int M, uint64_t budget, int sketch_layout, int row_storage) {
-  const uint64_t fixed = resident_bytes(family, n, d, M, 0, sketch_layout, row_storage);
+int64_t budget_tables(int family, int64_t n, int d, int M, uint64_t budget, int sketch_layout, int row_storage,
+                      int fp8_rows) {
+  const uint64_t fixed = resident_bytes(family, n, d, M, 0, sketch_layout, row_storage, fp8_rows);
   if (budget <= fixed) return 0;
-  const uint64_t per_table = resident_bytes(family, n, d, M, 1, sketch_layout, row_storage) - fixed;
+  const uint64_t per_table = resident_bytes(family, n, d, M, 1, sketch_layout, row_storage, fp8_rows) - fixed;
   return int64_t((budget - fixed) / per_table);
 }
 

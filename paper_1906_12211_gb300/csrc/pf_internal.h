@@ -64,8 +64,9 @@ void fht_collision_table(uint64_t seed, const Layout& lay, int draws, double* P 
 // bounds on the float32 transform's error for unit inputs: decisions whose top
 // two |y| are closer than *gap, or whose top |y| is below *sign, are redone in float64
 void fht_bands(int d, const Layout& lay, float* gap, float* sign);
-int64_t budget_tables(int family, int64_t n, int d, int M, uint64_t budget, int sketch_layout, int row_storage);
-uint64_t resident_bytes(int family, int64_t n, int d, int M, int L, int sketch_layout, int row_storage);
+int64_t budget_tables(int family, int64_t n, int d, int M, uint64_t budget, int sketch_layout, int row_storage,
+                      int fp8_rows);
+uint64_t resident_bytes(int family, int64_t n, int d, int M, int L, int sketch_layout, int row_storage, int fp8_rows);
 
 // A hash decision the tensor-core kernel leaves to the float64 fix-up pass.
 struct RecheckReq {
@@ -118,6 +119,8 @@ struct pf_index {
   __half* xf16 = nullptr;          // [n][d_pad] (binary16 rows; null with float32 rows)
   int row_storage = PF_ROWS_F32;
   __nv_bfloat16* x16 = nullptr;    // [n][d_pad]
+  uint8_t* x8 = nullptr;           // [n][d_pad] e4m3 copy (fp8_rows only)
+  float2* x8_meta = nullptr;       // [n] (scale, error bound) of the e4m3 copy
   uint64_t* sk = nullptr;          // [M][n] (per-point layout)
   uint64_t* skc = nullptr;         // [L][n] sketch j mod M of the point at each position (per-table layout)
   float* W32 = nullptr;            // [hash_rows][d_pad]
@@ -161,6 +164,9 @@ cudaError_t launch_round_rows_f16(float* x32, int64_t rows, int d_pad, __half* x
 // split x32 = xh + xl (xh is the round-to-nearest bfloat16 copy)
 cudaError_t launch_normalize(const float* in, int64_t rows, int d, int d_pad, float* x32, __nv_bfloat16* xh,
                              __nv_bfloat16* xl, cudaStream_t s);
+// e4m3 copy of normalised rows x32 [rows][d_pad] with per-row (scale, error bound)
+cudaError_t launch_quantize_fp8(const float* x32, int64_t rows, int d, int d_pad, uint8_t* x8, float2* meta,
+                                cudaStream_t s);
 
 // Hash rows x32 [npts][d_pad] (with its bfloat16 split xh + xl) under all L
 // repetitions and M sketches.  Codes written at codes[j*cj + p*cp], sketches

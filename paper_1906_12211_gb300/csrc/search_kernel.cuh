@@ -38,6 +38,8 @@
 
 #include <cuda_bf16.h>
 
+#include <cuda_fp8.h>
+
 #include "pf_internal.h"
 
 namespace pf {
@@ -59,6 +61,8 @@ struct Dev {
   const float* x32;     // float32 rows, or null
   const __half* xf16;   // binary16 rows (read back exactly as float32), or null
   const __nv_bfloat16* x16;
+  const uint8_t* x8;     // e4m3 rows (scoring 2), or null
+  const float2* x8_meta;  // their (scale, error bound)
   const uint32_t* codes;
   const uint32_t* ids;
   const uint32_t* pfx;
@@ -290,6 +294,47 @@ __device__ __forceinline__ float sim_bf16_pair(const float* __restrict__ q, cons
   return acc + __shfl_xor_sync(kFull, acc, 1);
 }
 
+// 8-bit float (e4m3) estimate of <q, dec(row)> by a pair of lanes (scale not
+// applied): lane h takes the 16-element chunks h, h+2, ... below d.
+template <int NT2>
+__device__ __forceinline__ float sim_fp8_pair(const float* __restrict__ q, const uint8_t* __restrict__ row, int d,
+                                              int h) {
+  constexpr int kChunks = (NT2 + 1) / 2;            // 16-byte chunks per lane
+  constexpr int kBatch = kChunks < 2 ? kChunks : 2;  // chunks loaded before their arithmetic
+  const uint4* r16 = reinterpret_cast<const uint4*>(row);
+  float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+  for (int t0 = 0; t0 < kChunks; t0 += kBatch) {
+    uint4 v[kBatch];
+#pragma unroll
+    for (int t = 0; t < kBatch; ++t) {
+      const int ch = h + 2 * (t0 + t);
+      v[t] = ch * 16 < d ? __ldg(r16 + ch) : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int t = 0; t < kBatch; ++t) {
+      const int ch = h + 2 * (t0 + t);
+      if (ch * 16 < d) {
+        const uint32_t w[4] = {v[t].x, v[t].y, v[t].z, v[t].w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4 qv = reinterpret_cast<const float4*>(q)[4 * ch + u];
+          const float2 lo = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(
+              __nv_fp8x2_storage_t(w[u] & 0xffffu), __NV_E4M3)));
+          const float2 hi = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(
+              __nv_fp8x2_storage_t(w[u] >> 16), __NV_E4M3)));
+          acc0 = fmaf(qv.x, lo.x, acc0);
+          acc1 = fmaf(qv.y, lo.y, acc1);
+          acc0 = fmaf(qv.z, hi.x, acc0);
+          acc1 = fmaf(qv.w, hi.y, acc1);
+        }
+      }
+    }
+  }
+  const float acc = acc0 + acc1;
+  return acc + __shfl_xor_sync(kFull, acc, 1);
+}
+
 struct Counters {
   uint32_t retrieved = 0, passed = 0, scored = 0, reranked = 0;
 };
@@ -330,13 +375,14 @@ __device__ __forceinline__ int flush_candidates(const Dev& P, const float* q, ui
                                                 uint32_t* pid, int size, int k, float kth_known, int lane,
                                                 Counters& ct) {
   if (lane == 0) ct.scored += cnt;
-  if (P.scoring != 1) return canonical_and_offer<NT>(P, q, cbuf, cnt, ps, pid, size, k, lane);
-  // bfloat16 estimates, 16 rows per step (a pair of lanes each).  A candidate
+  if (P.scoring == 0) return canonical_and_offer<NT>(P, q, cbuf, cnt, ps, pid, size, k, lane);
+  // bfloat16 (or e4m3) estimates, 16 rows per step (a pair of lanes each).  A candidate
   // can enter the final top-k only if its exact similarity reaches every k-th
   // similarity the query has already reached (that of the merged top-k at the
   // last snapshot, or of this warp's list: each is a k-th of a subset of the
-  // candidates); the estimate is within bf16_err of the exact value, so
-  // candidates whose estimate + bf16_err is below it are dropped and the
+  // candidates); the estimate is within its bound of the exact value (bf16_err,
+  // or the row's own bound for e4m3), so candidates whose estimate + bound is
+  // below it are dropped and the
   // others are compacted in place at the front of cbuf.  Each warp takes a
   // fixed share of the chunks, so the work done (and its count) does not
   // depend on timing.
@@ -351,8 +397,15 @@ __device__ __forceinline__ int flush_candidates(const Dev& P, const float* q, ui
       const int c = c0 + g;
       const bool valid = c < b1;
       const uint32_t id = valid ? cbuf[c] : cbuf[c0];
-      const float est = sim_bf16_pair<NT2>(q, P.x16 + size_t(id) * P.d_pad, P.d, h);
-      const bool need = valid && est + P.bf16_err >= kth;
+      bool need;
+      if (P.scoring == 2) {  // e4m3 estimate: per-row scale and error bound
+        const float2 m = __ldg(P.x8_meta + id);
+        const float est = sim_fp8_pair<NT2>(q, P.x8 + size_t(id) * P.d_pad, P.d, h) * m.x;
+        need = valid && est + m.y >= kth;
+      } else {
+        const float est = sim_bf16_pair<NT2>(q, P.x16 + size_t(id) * P.d_pad, P.d, h);
+        need = valid && est + P.bf16_err >= kth;
+      }
       const unsigned b = __ballot_sync(kFull, need && h == 0);
       __syncwarp();
       if (need && h == 0) cbuf[b0 + nr + __popc(b & ((1u << lane) - 1u))] = id;
@@ -772,6 +825,7 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
       st.scored = sum[2];
       st.reranked = P.scoring != 0 ? sum[3] : 0;
       st.last_reps = last_reps;
+      st.reserved = 0;
       P.stats[qi] = st;
     }
   }

@@ -265,6 +265,9 @@ def test_budget_formula_values(orc):
     # bits per function (4 words each) instead of d' x d' rows
     per_fht = n * 16 + 8193 * 4 + 4 * 3 * 4 * 4
     assert orc.budget_L(orc.CROSSPOLYTOPE_FHT, n, d, M, 4 << 30, 0) == ((4 << 30) - fixed_table) // per_fht == 225
+    # an 8-bit float copy of the rows: d' bytes + scale + bound per row, fixed
+    fixed_fp8 = fixed_table + n * (dp + 8)
+    assert orc.budget_L(orc.CROSSPOLYTOPE, n, d, M, 4 << 30, 0, 0, 1) == ((4 << 30) - fixed_fp8) // per_table
 
 
 def test_budget_with_binary16_rows(orc):
