@@ -50,7 +50,7 @@ class _Index(C.Structure):
     _fields_ = [("family", C.c_int), ("d", C.c_int), ("ell", C.c_int), ("Kb", C.c_int),
                 ("L", C.c_int), ("M", C.c_int), ("B", C.c_int), ("n", C.c_int64),
                 ("x", C.c_void_p), ("codes", C.c_void_p), ("ids", C.c_void_p),
-                ("sk", C.c_void_p), ("P", C.c_void_p)]
+                ("sk", C.c_void_p), ("P", C.c_void_p), ("pool_fns", C.c_int), ("pool_as_independent", C.c_int)]
 
 
 STATS_DTYPE = np.dtype([("start_depth", np.int32), ("stop_depth", np.int32), ("rounds", np.int32),
@@ -84,10 +84,14 @@ def lib():
                 "orc_collision_prob": (f64, [C.c_int, C.c_int, vp, f64, C.c_int]),
                 "orc_ipow": (f64, [f64, i64]),
                 "orc_filter_tau": (C.c_int, [f64]),
-                "orc_budget_L": (i64, [C.c_int, i64, C.c_int, C.c_int, u64, C.c_int, C.c_int, C.c_int]),
+                "orc_budget_L": (i64, [C.c_int, i64, C.c_int, C.c_int, u64, C.c_int, C.c_int, C.c_int, C.c_int]),
                 "orc_sim": (C.c_float, [vp, vp, C.c_int]),
                 "orc_search": (None, [vp, vp, vp, vp, i64, vp, vp, i32, vp, C.c_int, C.c_int, vp, vp, vp, vp, i64, vp]),
                 "orc_brute_force": (None, [vp, i64, C.c_int, vp, i64, C.c_int, vp, vp]),
+                "orc_pool_select": (None, [u64, C.c_int, C.c_int, C.c_int, vp]),
+                "orc_gen_pool_params": (None, [u64, C.c_int, C.c_int, C.c_int, vp]),
+                "orc_pool_codes": (None, [C.c_int, C.c_int, C.c_int, vp, C.c_int, vp, vp, i64, vp]),
+                "orc_pool_stop": (C.c_int, [C.c_int, C.c_int, vp, C.c_int, f64, C.c_int, i64, f64]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -230,11 +234,37 @@ def filter_tau(s_k: float) -> int:
 
 
 def budget_L(family: int, n: int, d: int, M: int, budget_bytes: int, sketch_layout: int = 0,
-             row_storage: int = 0, fp8_rows: int = 0) -> int:
+             row_storage: int = 0, fp8_rows: int = 0, pool_fns: int = 0) -> int:
     """sketch_layout 0: a sketch per repetition entry; 1: M sketches per point.
     row_storage 0: float32 rows; 1: binary16 rows.  fp8_rows 1: an 8-bit float
-    copy of the rows is kept too."""
-    return int(lib().orc_budget_L(family, n, d, M, budget_bytes, sketch_layout, row_storage, fp8_rows))
+    copy of the rows is kept too.  pool_fns > 0: functions drawn from a pool."""
+    return int(lib().orc_budget_L(family, n, d, M, budget_bytes, sketch_layout, row_storage, fp8_rows, pool_fns))
+
+
+def pool_select(seed: int, L: int, F: int, m: int) -> np.ndarray:
+    sel = np.zeros((L, F), np.int32)
+    lib().orc_pool_select(seed, L, F, m, _p(sel))
+    return sel
+
+
+def gen_pool_params(seed: int, family: int, m: int, d: int) -> np.ndarray:
+    R = d if family == CROSSPOLYTOPE else 1
+    A = np.zeros((m, R, d), np.float32)
+    lib().orc_gen_pool_params(seed, family, m, d, _p(A))
+    return A
+
+
+def pool_codes(family: int, A: np.ndarray, sel: np.ndarray, x: np.ndarray) -> np.ndarray:
+    A, sel, x = _c(A, np.float32), _c(sel, np.int32), _c(x, np.float32)
+    L = sel.shape[0]
+    codes = np.zeros((L, x.shape[0]), np.uint32)
+    lib().orc_pool_codes(family, A.shape[0], x.shape[1], _p(A), L, _p(sel), _p(x), x.shape[0], _p(codes))
+    return codes
+
+
+def pool_stop(family: int, ell: int, P, m: int, s_k: float, depth: int, j: int, delta: float) -> bool:
+    keep = _c(P, np.float64) if P is not None else None
+    return bool(lib().orc_pool_stop(family, ell, _p(keep) if keep is not None else None, m, s_k, depth, j, delta))
 
 
 def round_rows_f16(x: np.ndarray) -> np.ndarray:
@@ -265,7 +295,7 @@ class OracleIndex:
 
     def __init__(self, points, family: int, *, L: int | None = None, budget_bytes: int | None = None,
                  seed: int = 0, M: int = 32, B: int = 12, cp_draws: int = 1000, sketch_layout: int = 0,
-                 row_storage: int = 0):
+                 row_storage: int = 0, fp8_rows: int = 0, pool_bits: int = 0):
         points = _c(points, np.float32)
         self.n, self.d = points.shape
         self.family, self.seed, self.M, self.B = family, seed, M, B
@@ -276,8 +306,13 @@ class OracleIndex:
         else:
             lay = layout(family, self.d)
         self.ell, self.F, self.Kb = lay["ell"], lay["F"], lay["Kb"]
+        # pooling (Sec. 3.2): a pool of pool_bits // l functions shared by the tables
+        self.pool_fns = pool_bits // self.ell if pool_bits else 0
+        if self.pool_fns and family == CROSSPOLYTOPE_FHT:
+            raise ValueError("pooling is stated for the Gaussian families")
         if L is None:
-            L = budget_L(family, self.n, self.d, M, int(budget_bytes), sketch_layout, row_storage)
+            L = budget_L(family, self.n, self.d, M, int(budget_bytes), sketch_layout, row_storage, fp8_rows,
+                         self.pool_fns)
         self.L = int(L)
         if self.L < 1:
             raise ValueError("memory budget too small for one repetition")
@@ -289,6 +324,11 @@ class OracleIndex:
             self.A = fht.gen_params(seed, self.L, self.d)
             codes = fht.hash_codes(self.A, self.x, self.d)
             self.P = fht.cp_table(seed, self.d, cp_draws)
+        elif self.pool_fns:
+            self.A = gen_pool_params(seed, family, self.pool_fns, self.d)
+            self.sel = pool_select(seed, self.L, self.F, self.pool_fns)
+            codes = pool_codes(family, self.A, self.sel, self.x)
+            self.P = cp_table(seed, self.d, cp_draws) if family == CROSSPOLYTOPE else None
         else:
             self.A = gen_hash_params(seed, family, self.L, self.d)
             codes = hash_codes(family, self.A, self.x)
@@ -302,6 +342,8 @@ class OracleIndex:
             from . import fht
 
             return fht.hash_codes(self.A, x, self.d)
+        if self.pool_fns:
+            return pool_codes(self.family, self.A, self.sel, x)
         return hash_codes(self.family, self.A, x)
 
     def hash_queries(self, queries):
@@ -311,7 +353,8 @@ class OracleIndex:
         return qn, qcodes, qsk
 
     def search(self, queries, k, recall, *, k_max: int | None = None, start_depth=None,
-               filter: bool = True, trace_cap: int = 0, variant=None, stop_every: int = 0):
+               filter: bool = True, trace_cap: int = 0, variant=None, stop_every: int = 0,
+               pool_rule: str = "cantelli"):
         qn, qcodes, qsk = self.hash_queries(queries)
         Q = qn.shape[0]
         k = np.broadcast_to(np.asarray(k, np.int32), (Q,)).copy()
@@ -325,7 +368,8 @@ class OracleIndex:
         fam = CROSSPOLYTOPE if self.family == CROSSPOLYTOPE_FHT else self.family
         ix = _Index(fam, self.d, self.ell, self.Kb, self.L, self.M, self.B, self.n,
                     self.x.ctypes.data, self.codes.ctypes.data, self.ids.ctypes.data,
-                    self.sk.ctypes.data, self.P.ctypes.data if self.P is not None else None)
+                    self.sk.ctypes.data, self.P.ctypes.data if self.P is not None else None, self.pool_fns,
+                    1 if pool_rule == "independent" else 0)
         trace = np.zeros((Q, trace_cap, 2), np.uint32) if trace_cap else None
         tlen = np.zeros(Q, np.int64) if trace_cap else None
         (variant or lib()).orc_search(C.byref(ix), _p(qn), _p(qcodes), _p(qsk), Q, _p(k), _p(recall), k_max,

@@ -287,6 +287,74 @@ void orc_sketches(int M, int d, const float* S, const float* x, int64_t n, uint6
   free(St);
 }
 
+/* Sec. 3.2 "Pooling" / App. B.2: the tables share a pool of m functions; table
+ * j uses F of them, an independent uniformly random subset.  Reading: the
+ * subset is drawn by a partial Fisher-Yates shuffle of 0..m-1 whose swap
+ * partner at step s is s + floor(w * (m - s) / 2^32), w the first word of the
+ * generator at counter (s, j, 0, purpose 7); position s of the subset gives the
+ * value in bits 32 - l(s+1) .. 32 - l s - 1 of the code. */
+void orc_pool_select(uint64_t seed, int L, int F, int m, int32_t* sel) {
+  int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+  for (int j = 0; j < L; ++j) {
+    for (int t = 0; t < m; ++t) perm[t] = t;
+    for (int st = 0; st < F && st < m; ++st) {
+      uint32_t ctr[4] = {(uint32_t)st, (uint32_t)j, 0u, ORC_PURPOSE_POOL_SELECT};
+      uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+      uint32_t w[4];
+      orc_philox4x32_10(ctr, key, w);
+      int r = st + (int)(((uint64_t)w[0] * (uint64_t)(m - st)) >> 32);
+      int32_t tmp = perm[st]; perm[st] = perm[r]; perm[r] = tmp;
+      sel[(int64_t)j * F + st] = perm[st];
+    }
+  }
+  free(perm);
+}
+
+/* The pool's functions: CP function f has hyperplanes (f, c), c < d; HP
+ * function f one hyperplane; entries N(0,1) at counter (i, c, f, purpose 6). */
+void orc_gen_pool_params(uint64_t seed, int family, int m, int d, float* A) {
+  const int R = family == ORC_CROSSPOLYTOPE ? d : 1;
+#pragma omp parallel for schedule(static)
+  for (int f = 0; f < m; ++f)
+    for (int c = 0; c < R; ++c)
+      for (int i = 0; i < d; ++i)
+        A[((int64_t)f * R + c) * d + i] = orc_gauss(seed, ORC_PURPOSE_POOL, (uint32_t)f, (uint32_t)c, (uint32_t)i);
+}
+
+void orc_pool_codes(int family, int m, int d, const float* A, int L, const int32_t* sel, const float* x, int64_t n,
+                    uint32_t* codes) {
+  int ell, F;
+  orc_layout(family, d, &ell, &F, NULL, NULL);
+  const int R = family == ORC_CROSSPOLYTOPE ? d : 1;
+#pragma omp parallel
+  {
+    uint32_t* val = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)m);
+    double* v = (double*)malloc(sizeof(double) * (size_t)R);
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t p = 0; p < n; ++p) {
+      for (int f = 0; f < m; ++f) { /* every pool function's value (Sec. 2.2) */
+        dot64_rows(A + (int64_t)f * R * d, R, x + p * d, d, v);
+        if (family == ORC_SIMHASH) {
+          val[f] = v[0] >= 0.0 ? 1u : 0u;
+        } else {
+          int best = 0;
+          double best_abs = -1.0;
+          for (int c = 0; c < d; ++c)
+            if (fabs(v[c]) > best_abs) { best_abs = fabs(v[c]); best = c; }
+          val[f] = ((v[best] < 0.0 ? 1u : 0u) << (ell - 1)) | (uint32_t)best;
+        }
+      }
+      for (int j = 0; j < L; ++j) {
+        uint32_t code = 0;
+        for (int st = 0; st < F; ++st) code |= val[sel[(int64_t)j * F + st]] << (32 - ell * (st + 1));
+        codes[(int64_t)j * n + p] = code;
+      }
+    }
+    free(val);
+    free(v);
+  }
+}
+
 /* Sec. 4.2: repetition j is the array of (code, pos) sorted by code; equal
  * codes keep increasing pos (reading: ties ordered by position). */
 typedef struct { uint32_t code, id; } orc_pair;
@@ -416,6 +484,32 @@ double orc_collision_prob(int family, int ell, const double* P, double s, int de
   return orc_ipow(row[ell], depth / ell) * row[depth % ell];
 }
 
+/* App. B.2 adapted to general delta.  X = number of the j tables, searched to
+ * prefix length i, in which x_k collides with the query; E[X] = mu = j p_i
+ * (the functions within one table are distinct pool members, so independent).
+ * For two tables, each of the f = ceil(i/l) functions behind the first i bits
+ * of the second is one of the first's with probability <= f/(m - f), so
+ * E[X_1 X_2] <= p_i^2 (1 + f / ((m - f) P))^f <= p_i^2 e^c, c = f^2/((m - f) P),
+ * P = the collision probability of one whole function (the smallest factor).
+ * Hence Var X <= mu + mu^2 (e^c - 1), and Cantelli's inequality gives
+ * Pr[X = 0] <= Var/(mu^2 + Var).  Reading: e^c - 1 is replaced by its upper
+ * bound c/(1 - c) (c < 1), so the test needs no exponential; stop iff that
+ * bound is <= delta.  (With c -> 0 the bound is 1/(1 + mu); the paper's
+ * rule for delta = 1/2 is mu >= 2 and m >= 5 i^2 / P.) */
+int orc_pool_stop(int family, int ell, const double* P, int m, double s_k, int depth, int64_t j, double delta) {
+  const int f = (depth + ell - 1) / ell;
+  if (f <= 0 || f >= m || j <= 0) return 0;
+  const double p = orc_collision_prob(family, ell, P, s_k, depth);
+  const double p1 = orc_collision_prob(family, ell, P, s_k, ell);
+  if (!(p1 > 0.0)) return 0;
+  const double c = ((double)f * (double)f) / ((double)(m - f) * p1);
+  if (!(c < 1.0)) return 0;
+  const double mu = (double)j * p;
+  if (!(mu > 0.0)) return 0;
+  const double var = mu + (mu * mu) * (c / (1.0 - c));
+  return var / (mu * mu + var) <= delta;
+}
+
 /* Sec. 4.2 + Fig. 2 footnote: the sketch threshold is (1+eps) times the
  * expected number of differing bits, 64 * arccos(s_k)/pi, with eps = 0
  * (Sec. 5.1); a candidate passes if its Hamming distance is at most that.
@@ -441,7 +535,7 @@ int orc_filter_tau(double s_k) {
  *               R = F * d' for CP (rows of a function padded to d'), 32 for HP
  *   L = floor((budget - fixed) / per_table). */
 int64_t orc_budget_L(int family, int64_t n, int d, int M, uint64_t budget_bytes, int sketch_layout,
-                     int row_storage, int fp8_rows) {
+                     int row_storage, int fp8_rows, int pool_fns) {
   int64_t dp = ((int64_t)d + 15) / 16 * 16;
   int F;
   orc_layout(family == ORC_CROSSPOLYTOPE_FHT ? ORC_CROSSPOLYTOPE : family, d, NULL, &F, NULL, NULL);
@@ -459,8 +553,15 @@ int64_t orc_budget_L(int family, int64_t n, int d, int M, uint64_t budget_bytes,
   int64_t fixed = n * dp * row_bytes + 64 * (int64_t)M * dp * 8 + (sketch_layout == 1 ? n * (int64_t)M * 8 : 0);
   /* an 8-bit float copy of the rows, with a scale and an error bound each */
   if (fp8_rows) fixed += n * (dp + 8);
+  /* pooled functions (Sec. 3.2): the pool's rows, stored in whole groups of F
+   * functions, are fixed; a table keeps only its F indices */
+  if (pool_fns > 0) {
+    int64_t groups = (pool_fns + F - 1) / F;
+    fixed += groups * R * dp * 8;
+    R = 0;
+  }
   int64_t per_table = n * (sketch_layout == 1 ? 8 : 16) + (int64_t)((1 << ORC_PREFIX_BITS) + 1) * 4 + R * dp * 8 +
-                      fht_bytes;
+                      fht_bytes + (pool_fns > 0 ? (int64_t)F * 4 : 0);
   if ((int64_t)budget_bytes <= fixed) return 0;
   return ((int64_t)budget_bytes - fixed) / per_table;
 }
@@ -608,11 +709,18 @@ static void search_one(const orc_index* ix, const float* q, const uint32_t* qcod
         /* Alg. 1 tests after repetitions, not rounds: repetitions 0..j have
          * now been searched to prefix length `depth`, the others to depth + 1
          * (to nothing yet in the first round, whose factor is 1) */
-        double fail = orc_ipow(1.0 - orc_collision_prob(ix->family, ix->ell, ix->P, (double)ps[k - 1], depth), j + 1);
-        if (s.rounds > 0)
-          fail = fail * orc_ipow(1.0 - orc_collision_prob(ix->family, ix->ell, ix->P, (double)ps[k - 1], depth + 1),
-                                 L - j - 1);
-        if (fail <= delta) { stopped = j + 1; break; }
+        int stop_now;
+        if (ix->pool_fns > 0 && !ix->pool_as_independent) { /* pooled functions: only the j + 1 tables at this depth are counted */
+          stop_now = orc_pool_stop(ix->family, ix->ell, ix->P, ix->pool_fns, (double)ps[k - 1], depth, j + 1, delta);
+        } else {
+          double fail =
+              orc_ipow(1.0 - orc_collision_prob(ix->family, ix->ell, ix->P, (double)ps[k - 1], depth), j + 1);
+          if (s.rounds > 0)
+            fail = fail * orc_ipow(1.0 - orc_collision_prob(ix->family, ix->ell, ix->P, (double)ps[k - 1], depth + 1),
+                                   L - j - 1);
+          stop_now = fail <= delta;
+        }
+        if (stop_now) { stopped = j + 1; break; }
       }
     }
     s.last_reps = stopped ? stopped : L;
@@ -622,9 +730,13 @@ static void search_one(const orc_index* ix, const float* q, const uint32_t* qcod
     if (stopped) break;
     if (depth == 0) break;
     if (size == k) {
-      double p = orc_collision_prob(ix->family, ix->ell, ix->P, (double)ps[k - 1], depth);
-      double fail = orc_ipow(1.0 - p, L);
-      if (fail <= delta) break;
+      if (ix->pool_fns > 0 && !ix->pool_as_independent) {
+        if (orc_pool_stop(ix->family, ix->ell, ix->P, ix->pool_fns, (double)ps[k - 1], depth, L, delta)) break;
+      } else {
+        double p = orc_collision_prob(ix->family, ix->ell, ix->P, (double)ps[k - 1], depth);
+        double fail = orc_ipow(1.0 - p, L);
+        if (fail <= delta) break;
+      }
     }
     depth -= 1;
   }

@@ -29,7 +29,8 @@ extern "C" {
 #endif
 
 enum { ORC_SIMHASH = 0, ORC_CROSSPOLYTOPE = 1, ORC_CROSSPOLYTOPE_FHT = 2 /* budget rule only (oracle/fht.py) */ };
-enum { ORC_PURPOSE_HASH = 1, ORC_PURPOSE_SKETCH = 2, ORC_PURPOSE_CPMC = 3 };
+enum { ORC_PURPOSE_HASH = 1, ORC_PURPOSE_SKETCH = 2, ORC_PURPOSE_CPMC = 3,
+       ORC_PURPOSE_POOL = 6 /* rows of the pooled functions */, ORC_PURPOSE_POOL_SELECT = 7 /* their subsets */ };
 #define ORC_PREFIX_BITS 13
 #define ORC_ALPHA_STEPS 41 /* similarity grid -1, -0.95, ..., 1 (Sec. 4.3) */
 #define ORC_SNAPSHOT_GROUP 32 /* repetitions per sketch-threshold snapshot in a query's first round */
@@ -68,6 +69,22 @@ void orc_sketches(int M, int d, const float* S, const float* x, int64_t n, uint6
 void orc_sort_tables(int L, int64_t n, const uint32_t* codes, uint32_t* sorted_codes, uint32_t* ids);
 void orc_prefix_table(int L, int64_t n, const uint32_t* sorted_codes, uint32_t* pfx /*[L][8193]*/);
 
+/* ---- pooling (Sec. 3.2 "Pooling", App. B.2): a pool of m functions, each
+ *      table takes an independent random subset of F of them ---- */
+/* sel[L][F]: the subset of table j, drawn without replacement (partial
+ * Fisher-Yates driven by the counter-based generator, purpose 7) */
+void orc_pool_select(uint64_t seed, int L, int F, int m, int32_t* sel);
+/* rows of the pool's functions [m][R][d], R = d (CP) or 1 (HP), purpose 6 */
+void orc_gen_pool_params(uint64_t seed, int family, int m, int d, float* A);
+/* codes[L][n] of normalised points: table j concatenates the values of its
+ * selected functions, the first in the most significant bits */
+void orc_pool_codes(int family, int m, int d, const float* A, int L, const int32_t* sel, const float* x, int64_t n,
+                    uint32_t* codes);
+/* the stop test of a pooled index after j tables searched to prefix length
+ * `depth`: Cantelli's bound on Pr[x_k never collided] <= delta (the reading of
+ * App. B.2 for general delta) */
+int orc_pool_stop(int family, int ell, const double* P, int m, double s_k, int depth, int64_t j, double delta);
+
 /* ---- collision probabilities (Sec. 4.3 "Estimating Collision Probabilities") ---- */
 double orc_alpha(int t); /* grid value alpha_t */
 int orc_alpha_index(double s);
@@ -82,9 +99,10 @@ int orc_filter_tau(double s_k);
  * sketch_layout 0: one sketch copy per repetition entry; 1: M per point.
  * row_storage 0: normalised rows kept in float32; 1: in binary16 (Sec. 4.2
  * keeps 16-bit vectors); a bfloat16 copy is kept either way.  fp8_rows 1: an
- * 8-bit float copy with a scale and a bound per row is kept too. */
+ * 8-bit float copy with a scale and a bound per row is kept too.  pool_fns
+ * > 0: the tables draw their functions from a pool of that many. */
 int64_t orc_budget_L(int family, int64_t n, int d, int M, uint64_t budget_bytes, int sketch_layout,
-                     int row_storage, int fp8_rows);
+                     int row_storage, int fp8_rows, int pool_fns);
 
 /* ---- canonical float32 inner product ---- */
 float orc_sim(const float* q, const float* x, int d);
@@ -105,6 +123,8 @@ typedef struct {
   const uint32_t* ids;     /* ids [L][n] */
   const uint64_t* sk;      /* sketches [M][n] */
   const double* P;         /* CP table [41][ell+1] or NULL for HP */
+  int pool_fns;            /* 0: independent functions; m > 0: each table draws its functions from a pool of m */
+  int pool_as_independent; /* pooled index, 1: stop by Lemma 1's rule as if the functions were independent */
 } orc_index;
 
 /* Search Q normalised queries.  qcodes[Q][L], qsk[Q][M], k[Q], recall[Q].

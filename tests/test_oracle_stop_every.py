@@ -115,7 +115,8 @@ def test_recall_guarantee_with_per_repetition_tests(orc):
 
 _MUTANTS = {
     "exponent_L_not_j": ("(double)ps[k - 1], depth), j + 1);", "(double)ps[k - 1], depth), L);"),
-    "no_second_factor": ("        if (s.rounds > 0)\n          fail = fail *", "        if (0)\n          fail = fail *"),
+    "no_second_factor": ("          if (s.rounds > 0)\n            fail = fail *",
+                         "          if (0)\n            fail = fail *"),
     "second_factor_at_depth": ("(double)ps[k - 1], depth + 1),", "(double)ps[k - 1], depth),"),
 }
 
