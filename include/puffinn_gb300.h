@@ -90,6 +90,10 @@ typedef struct {
   int32_t row_storage;          /* pf_row_storage; 0 -> PF_ROWS_F32 */
   int32_t fp8_rows;             /* 1: also keep an 8-bit float (e4m3) copy of the rows with a scale and an error
                                    bound per row, for scoring 2; counted in the budget (n * (d_pad + 8) bytes) */
+  int32_t pool_bits;            /* 0: independent functions in every table.  m > 0: pooling (Sec. 3.2, App. B.2):
+                                   a pool of floor(m / l) functions shared by the tables, each table using a random
+                                   subset of fns of them (the paper uses m = 3072).  PF_SIMHASH and
+                                   PF_CROSSPOLYTOPE only; the pool must hold at least fns functions */
 } pf_build_params;
 
 /* Per-call search options.  NULL = defaults (FP32 scoring, filter on). */
@@ -103,6 +107,9 @@ typedef struct {
   int32_t timing;              /* 1: record CUDA events around each phase (see pf_index_last_timing) */
   const int32_t* start_depth;  /* optional [Q] per-query start depth i0 (host or device): rounds i0, i0-1, ..., 0,
                                   the first taking the whole block at i0; values outside [0, K) mean K */
+  int32_t pool_rule;           /* pooled index: 0 = stop when Cantelli's bound on missing the k-th point is <= delta
+                                  (the guarantee carried to general delta); 1 = Lemma 1's test as if the pooled
+                                  functions were independent (no guarantee).  Ignored otherwise */
   int32_t stop_every;          /* 0: the stop test after each round (Sec. 4.1).  G >= 1: also after every G
                                   repetitions (Alg. 1 tests after each one: G = 1): after j repetitions of the round
                                   at prefix length i the test is (1 - p_i)^j (1 - p_{i+1})^(L - j) <= delta (no second
@@ -166,8 +173,10 @@ typedef enum {
   PF_ARRAY_FHT_SIGNS = 13,     /* uint32 [L][fns][3][W]: sign bits of D1, D2, D3 of every pseudo-random CP function,
                                   W = max(1, d''/32) words, bit i of a vector set = -1 (PF_CROSSPOLYTOPE_FHT only) */
   PF_ARRAY_ROWS_FP8 = 14,      /* e4m3 [n][d_pad]: x_i / scale rounded to nearest even, saturated (fp8_rows only) */
-  PF_ARRAY_FP8_META = 15       /* float [n][2]: scale, and the bound on |<q, x> - scale <q, x8>| + rounding for
+  PF_ARRAY_FP8_META = 15,      /* float [n][2]: scale, and the bound on |<q, x> - scale <q, x8>| + rounding for
                                   any unit q (fp8_rows only) */
+  PF_ARRAY_POOL_SELECT = 16    /* int32 [L][fns]: the pool functions of each table, first in the most significant
+                                  bits (pool_bits only) */
 } pf_array;
 
 /* Build the index over `points` ([n][d] row-major, host or device).

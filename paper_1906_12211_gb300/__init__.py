@@ -29,9 +29,10 @@ STATUS = {0: "PF_OK", -1: "PF_ERR_INVALID_ARG", -2: "PF_ERR_BUDGET_TOO_SMALL", -
 ARRAYS = {"rows_f32": 0, "rows_bf16": 1, "codes": 2, "ids": 3, "prefix": 4, "sketches": 5, "hash_rows": 6,
           "cp_table": 7, "table_sketches": 8, "rows_f16": 9, "mlp_f32": 10, "mlp_w1_bf16": 11, "mlp_w2_bf16": 12,
           "fht_signs": 13,
-          "rows_fp8": 14, "fp8_meta": 15}
+          "rows_fp8": 14, "fp8_meta": 15, "pool_select": 16}
 ROW_STORAGE = {"f32": 0, "f16": 1}
 SCORING = {"fp32": 0, "bf16": 1, "fp8": 2}
+POOL_RULES = {"cantelli": 0, "independent": 1}
 SKETCH_LAYOUTS = {"table": 0, "point": 1}
 
 
@@ -39,12 +40,14 @@ class BuildParams(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("dtype", C.c_int32), ("family", C.c_int32),
                 ("num_sketches", C.c_int32), ("memory_budget_bytes", C.c_uint64), ("seed", C.c_uint64),
                 ("segment_B", C.c_int32), ("cp_draws", C.c_int32), ("num_tables", C.c_int32),
-                ("sketch_layout", C.c_int32), ("row_storage", C.c_int32), ("fp8_rows", C.c_int32)]
+                ("sketch_layout", C.c_int32), ("row_storage", C.c_int32), ("fp8_rows", C.c_int32),
+                ("pool_bits", C.c_int32)]
 
 
 class SearchOpts(C.Structure):
     _fields_ = [("scoring", C.c_int32), ("filter", C.c_int32), ("learned_start", C.c_int32),
-                ("timing", C.c_int32), ("start_depth", C.c_void_p), ("stop_every", C.c_int32)]
+                ("timing", C.c_int32), ("start_depth", C.c_void_p), ("pool_rule", C.c_int32),
+                ("stop_every", C.c_int32)]
 
 
 class QueryStats(C.Structure):
@@ -187,13 +190,14 @@ class Index:
 
     def __init__(self, points, family="crosspolytope", *, budget_bytes: int = 0, num_tables: int = 0,
                  seed: int = 0, num_sketches: int = 32, segment_B: int = 12, cp_draws: int = 1000,
-                 sketch_layout: str = "table", rows: str = "f32", fp8_rows: bool = False, stream=None):
+                 sketch_layout: str = "table", rows: str = "f32", fp8_rows: bool = False, pool_bits: int = 0,
+                 stream=None):
         n, d = int(points.shape[0]), int(points.shape[1])
         p = BuildParams(n=n, d=d, dtype=0, family=_family(family), num_sketches=num_sketches,
                         memory_budget_bytes=int(budget_bytes), seed=int(seed), segment_B=segment_B,
                         cp_draws=cp_draws, num_tables=int(num_tables),
                         sketch_layout=SKETCH_LAYOUTS[sketch_layout], row_storage=ROW_STORAGE[rows],
-                        fp8_rows=1 if fp8_rows else 0)
+                        fp8_rows=1 if fp8_rows else 0, pool_bits=int(pool_bits))
         self._points_keepalive = points
         h = C.c_void_p()
         _check(lib().pf_index_build(C.byref(p), _ptr(points), C.byref(h), _stream_ptr(stream)))
@@ -260,7 +264,7 @@ class Index:
 
     def search(self, queries, k, recall, *, k_max: int | None = None, scoring: str = "fp32", filter: bool = True,
                start_depth=None, out_ids=None, out_sims=None, stats=None, stream=None, timing: bool = False,
-               learned: bool = False, stop_every: int = 0):
+               learned: bool = False, stop_every: int = 0, pool_rule: str = "cantelli"):
         """Answer a batch of queries; k and recall are per-query arrays (same
         device as the queries) or scalars.  Returns (ids, sims, stats)."""
         import torch
@@ -288,6 +292,7 @@ class Index:
         o.timing = 1 if timing else 0
         o.learned_start = 1 if learned else 0
         o.stop_every = int(stop_every)
+        o.pool_rule = POOL_RULES[pool_rule]
         sd = None
         if start_depth is not None:
             sd = start_depth if torch.is_tensor(start_depth) else torch.full((Q,), int(start_depth),
@@ -308,13 +313,14 @@ class Index:
                                              _stream_ptr(stream)))
         return out_ids, out_sims, stats
 
-    def _opts(self, scoring, filter, learned, stop_every=0):
+    def _opts(self, scoring, filter, learned, stop_every=0, pool_rule="cantelli"):
         o = SearchOpts()
         lib().pf_search_opts_default(C.byref(o))
         o.scoring = SCORING[scoring]
         o.filter = 1 if filter else 0
         o.learned_start = 1 if learned else 0
         o.stop_every = int(stop_every)
+        o.pool_rule = POOL_RULES[pool_rule]
         return o
 
     def tune(self, queries, k: int, recall: float, *, scoring: str = "fp32", filter: bool = True,
@@ -348,11 +354,13 @@ class Index:
         _check(lib().pf_index_selftest_hold(self._h, 1 if hold else 0))
 
     def plan(self, queries, k, recall, out_ids, out_sims, *, k_max: int, stats=None, start_depth=None,
-             scoring: str = "fp32", filter: bool = True, learned: bool = False, stop_every: int = 0):
+             scoring: str = "fp32", filter: bool = True, learned: bool = False, stop_every: int = 0,
+             pool_rule: str = "cantelli"):
         """pf_search_plan_create: a CUDA graph of this search bound to these device tensors (or
         page-locked host tensors)."""
         return SearchPlan(self, queries, k, recall, out_ids, out_sims, k_max=k_max, stats=stats,
-                          start_depth=start_depth, opts=self._opts(scoring, filter, learned, stop_every))
+                          start_depth=start_depth, opts=self._opts(scoring, filter, learned, stop_every,
+                                                                   pool_rule))
 
     def last_timing(self):
         """(hash_ms, search_kernel_ms, total_ms) of the last search run with timing=True."""

@@ -97,6 +97,7 @@ void free_ws(pf_workspace& ws) {
   dfree(ws.qxl);
   dfree(ws.qcodes);
   dfree(ws.qsk);
+  dfree(ws.qgcodes);
   dfree(ws.k);
   dfree(ws.recall);
   dfree(ws.start);
@@ -119,6 +120,7 @@ void alloc_ws(pf_index* ix, pf_workspace& ws, size_t q, size_t km) {
   dalloc(&ws.qxh, q * dp);
   dalloc(&ws.qxl, q * dp);
   dalloc(&ws.qcodes, q * ix->L);
+  if (ix->pool_tables > 0) dalloc(&ws.qgcodes, q * ix->pool_tables);
   dalloc(&ws.qsk, q * ix->M);
   dalloc(&ws.k, q);
   dalloc(&ws.recall, q);
@@ -163,6 +165,7 @@ void destroy(pf_index* ix) {
   dfree(ix->fht_signs);
   dfree(ix->x8);
   dfree(ix->x8_meta);
+  dfree(ix->pool_sel);
   dfree(ix->mlp_w);
   dfree(ix->mlp_w1h);
   dfree(ix->mlp_w2h);
@@ -182,6 +185,12 @@ void stage_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
 // Hash and normalise Q queries (device pointer qsrc) into the workspace.
 void hash_queries_ws(pf_index* ix, pf_workspace& ws, const float* qdev, int64_t Q, cudaStream_t s) {
   PF_CK(launch_normalize(qdev, Q, ix->d, ix->lay.d_pad, ws.qx, ws.qxh, ws.qxl, s));
+  if (ix->pool_tables > 0) {  // the pool's functions once, then each table's subset
+    PF_CK(launch_hash(ix, ws.qx, ws.qxh, ws.qxl, Q, ws.qgcodes, 1, ix->pool_tables, ws.qsk, 1, ix->M, ws.rq,
+                      ws.rq_count, recheck_capacity(Q), s, ix->pool_tables));
+    PF_CK(launch_pool_gather(ix, ws.qgcodes, 1, ix->pool_tables, Q, ws.qcodes, 1, ix->L, s));
+    return;
+  }
   PF_CK(launch_hash(ix, ws.qx, ws.qxh, ws.qxl, Q, ws.qcodes, 1, ix->L, ws.qsk, 1, ix->M, ws.rq, ws.rq_count,
                     recheck_capacity(Q), s));
 }
@@ -261,9 +270,17 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       return fail(PF_ERR_INVALID_ARG, "unknown sketch layout");
     if (prm->row_storage != PF_ROWS_F32 && prm->row_storage != PF_ROWS_F16)
       return fail(PF_ERR_INVALID_ARG, "unknown row storage");
+    int pool_fns = 0;
+    if (prm->pool_bits != 0) {
+      if (prm->pool_bits < 0 || prm->family == PF_CROSSPOLYTOPE_FHT)
+        return fail(PF_ERR_INVALID_ARG, "pool_bits must be >= 0, and pooling needs PF_SIMHASH or PF_CROSSPOLYTOPE");
+      const Layout lay0 = make_layout(prm->family, prm->d);
+      pool_fns = prm->pool_bits / lay0.ell;
+      if (pool_fns < lay0.fns) return fail(PF_ERR_INVALID_ARG, "the pool must hold at least one table's functions");
+    }
     int64_t L = prm->num_tables > 0 ? prm->num_tables
                                     : budget_tables(prm->family, prm->n, prm->d, M, prm->memory_budget_bytes,
-                                                    prm->sketch_layout, prm->row_storage, prm->fp8_rows);
+                                                    prm->sketch_layout, prm->row_storage, prm->fp8_rows, pool_fns);
     if (L < 1) return fail(PF_ERR_BUDGET_TOO_SMALL, "memory budget leaves room for no repetition");
     if (prm->num_tables > kMaxL)
       return fail(PF_ERR_INVALID_ARG, "num_tables above " + std::to_string(kMaxL) + " is not supported");
@@ -285,10 +302,13 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       ix->sketch_layout = prm->sketch_layout;
       ix->row_storage = prm->row_storage;
       ix->bytes_used =
-          resident_bytes(prm->family, prm->n, prm->d, M, ix->L, prm->sketch_layout, prm->row_storage, prm->fp8_rows);
+          resident_bytes(prm->family, prm->n, prm->d, M, ix->L, prm->sketch_layout, prm->row_storage, prm->fp8_rows,
+                         pool_fns);
       const int dp = ix->lay.d_pad;
       const int64_t n = ix->n;
-      ix->hash_rows = int64_t(ix->L) * ix->lay.rows_table + 64LL * M;
+      ix->pool_fns = pool_fns;
+      ix->pool_tables = pool_fns > 0 ? (pool_fns + ix->lay.fns - 1) / ix->lay.fns : 0;
+      ix->hash_rows = int64_t(pool_fns > 0 ? ix->pool_tables : ix->L) * ix->lay.rows_table + 64LL * M;
       // bound on |bfloat16 estimate - canonical float32 similarity| for unit
       // vectors: 2^-8 from rounding the row to bfloat16, plus the float32
       // accumulation error of both sums (each <= d_pad * 2^-24 * |q||x|)
@@ -330,7 +350,15 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
 
       // random parameters on the host (bit-reproducible from the seed)
       std::vector<float> W(size_t(ix->hash_rows) * dp), thr(size_t(ix->hash_rows));
-      gen_hash_rows(prm->seed, prm->family, ix->L, M, prm->d, ix->lay, W.data(), thr.data());
+      if (pool_fns > 0) {
+        gen_pool_rows(prm->seed, prm->family, pool_fns, M, prm->d, ix->lay, W.data(), thr.data());
+        std::vector<int32_t> sel(size_t(ix->L) * ix->lay.fns);
+        pool_select(prm->seed, ix->L, ix->lay.fns, pool_fns, sel.data());
+        dalloc(&ix->pool_sel, sel.size());
+        PF_CK(cudaMemcpy(ix->pool_sel, sel.data(), sizeof(int32_t) * sel.size(), cudaMemcpyHostToDevice));
+      } else {
+        gen_hash_rows(prm->seed, prm->family, ix->L, M, prm->d, ix->lay, W.data(), thr.data());
+      }
       PF_CK(cudaMemcpyAsync(ix->W32, W.data(), sizeof(float) * W.size(), cudaMemcpyHostToDevice, s));
       PF_CK(cudaMemcpyAsync(ix->Wthr, thr.data(), sizeof(float) * thr.size(), cudaMemcpyHostToDevice, s));
       split_bf16_kernel<<<1024, 256, 0, s>>>(ix->W32, int64_t(W.size()), ix->Whi, ix->Wlo);
@@ -357,6 +385,7 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
         pin = staged;
       }
       uint32_t* raw_codes = nullptr;
+      uint32_t* gcodes = nullptr;    // codes of the pool's groups, only while hashing a pooled index
       __nv_bfloat16* xlo = nullptr;  // low bfloat16 half of the rows, only while hashing
       RecheckReq* rq = nullptr;      // deferred float64 rechecks, only while hashing
       uint32_t* rq_count = nullptr;
@@ -382,8 +411,15 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
         dalloc(&raw_codes, size_t(n) * ix->L);
         dalloc(&rq, recheck_capacity(n));
         dalloc(&rq_count, size_t(ix->num_sms));
-        PF_CK(launch_hash(ix, x32, ix->x16, xlo, n, raw_codes, n, 1, sk_out, n, 1, rq, rq_count,
-                          recheck_capacity(n), s));
+        if (ix->pool_tables > 0) {  // the pool's functions once, then each table's subset
+          dalloc(&gcodes, size_t(n) * ix->pool_tables);
+          PF_CK(launch_hash(ix, x32, ix->x16, xlo, n, gcodes, n, 1, sk_out, n, 1, rq, rq_count, recheck_capacity(n), s,
+                            ix->pool_tables));
+          PF_CK(launch_pool_gather(ix, gcodes, n, 1, n, raw_codes, n, 1, s));
+        } else {
+          PF_CK(launch_hash(ix, x32, ix->x16, xlo, n, raw_codes, n, 1, sk_out, n, 1, rq, rq_count,
+                            recheck_capacity(n), s));
+        }
         PF_CK(sort_tables(ix, raw_codes, s));
         if (ix->skc) PF_CK(gather_table_sketches(ix, sk_out, ix->skc, s));
         PF_CK(cudaMemcpyAsync(&herr, ix->dev_error, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -392,6 +428,7 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
         cudaStreamSynchronize(s);
         dfree(staged);
         dfree(raw_codes);
+        dfree(gcodes);
         dfree(xlo);
         dfree(rq);
         dfree(rq_count);
@@ -401,6 +438,7 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       }
       dfree(staged);
       dfree(raw_codes);
+      dfree(gcodes);
       dfree(xlo);
       dfree(rq);
       dfree(rq_count);
@@ -453,6 +491,7 @@ pf_status pf_index_search(pf_index* ix, const float* queries, int64_t Q, const i
     if (o.scoring < 0 || o.scoring > 2) return fail(PF_ERR_INVALID_ARG, "scoring must be 0, 1 or 2");
     if (o.scoring == 2 && !ix->x8) return fail(PF_ERR_INVALID_ARG, "scoring 2 needs an index built with fp8_rows");
     if (o.stop_every < 0) return fail(PF_ERR_INVALID_ARG, "stop_every must be >= 0");
+    if (o.pool_rule != 0 && o.pool_rule != 1) return fail(PF_ERR_INVALID_ARG, "pool_rule must be 0 or 1");
     if (o.learned_start && !ix->mlp_trained) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
     if (Q == 0) return PF_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -494,6 +533,7 @@ pf_status pf_index_search(pf_index* ix, const float* queries, int64_t Q, const i
     a.filter = o.filter ? 1 : 0;
     a.scoring = o.scoring;
     a.stop_every = o.stop_every;
+    a.pool_rule = o.pool_rule;
     a.out_ids = ids_dev ? out_ids : ws.ids;
     a.out_sims = sims_dev ? out_sims : ws.sims;
     a.stats = stats ? (st_dev ? stats : ws.stats) : nullptr;
@@ -593,6 +633,11 @@ pf_status pf_index_array(const pf_index* ix, int32_t which, const void** ptr, ui
       if (!ix->x8) return fail(PF_ERR_INVALID_ARG, "index was built without fp8_rows");
       *ptr = which == PF_ARRAY_ROWS_FP8 ? static_cast<const void*>(ix->x8) : static_cast<const void*>(ix->x8_meta);
       *bytes = which == PF_ARRAY_ROWS_FP8 ? n * dp : n * 8;
+      break;
+    case PF_ARRAY_POOL_SELECT:
+      if (!ix->pool_sel) return fail(PF_ERR_INVALID_ARG, "index does not pool its functions");
+      *ptr = ix->pool_sel;
+      *bytes = uint64_t(ix->L) * ix->lay.fns * 4;
       break;
     case PF_ARRAY_MLP_F32:
     case PF_ARRAY_MLP_W1_BF16:
@@ -931,6 +976,7 @@ pf_status pf_index_tune(pf_index* ix, const float* queries, int64_t Q, int32_t k
     if (o.scoring < 0 || o.scoring > 2) return fail(PF_ERR_INVALID_ARG, "scoring must be 0, 1 or 2");
     if (o.scoring == 2 && !ix->x8) return fail(PF_ERR_INVALID_ARG, "scoring 2 needs an index built with fp8_rows");
     if (o.stop_every < 0) return fail(PF_ERR_INVALID_ARG, "stop_every must be >= 0");
+    if (o.pool_rule != 0 && o.pool_rule != 1) return fail(PF_ERR_INVALID_ARG, "pool_rule must be 0 or 1");
     if (o.learned_start && !ix->mlp_trained) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PF_CK(cudaSetDevice(ix->device));
@@ -966,6 +1012,7 @@ pf_status pf_index_tune(pf_index* ix, const float* queries, int64_t Q, int32_t k
     a.filter = o.filter ? 1 : 0;
     a.scoring = o.scoring;
     a.stop_every = o.stop_every;
+    a.pool_rule = o.pool_rule;
     a.out_ids = ws.ids;
     a.out_sims = ws.sims;
     a.stats = nullptr;
@@ -1123,6 +1170,7 @@ void plan_sequence(pf_search_plan* pl, cudaStream_t s) {
   a.filter = pl->opts.filter ? 1 : 0;
   a.scoring = pl->opts.scoring;
   a.stop_every = pl->opts.stop_every;
+  a.pool_rule = pl->opts.pool_rule;
   a.out_ids = io.out_ids;
   a.out_sims = io.out_sims;
   a.stats = io.stats;
@@ -1170,6 +1218,7 @@ pf_status pf_search_plan_create(pf_index* ix, int64_t Q, int32_t k_max, const pf
     if (o.scoring < 0 || o.scoring > 2) return fail(PF_ERR_INVALID_ARG, "scoring must be 0, 1 or 2");
     if (o.scoring == 2 && !ix->x8) return fail(PF_ERR_INVALID_ARG, "scoring 2 needs an index built with fp8_rows");
     if (o.stop_every < 0) return fail(PF_ERR_INVALID_ARG, "stop_every must be >= 0");
+    if (o.pool_rule != 0 && o.pool_rule != 1) return fail(PF_ERR_INVALID_ARG, "pool_rule must be 0 or 1");
     if (o.learned_start && !ix->mlp_trained) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
     o.start_depth = nullptr;
     o.timing = 0;

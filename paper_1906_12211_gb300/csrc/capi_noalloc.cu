@@ -88,6 +88,9 @@ extern "C" pf_status pf_index_search_noalloc(pf_index* ix, const float* queries,
     if (o.scoring < 0 || o.scoring > 2) return reject(PF_ERR_INVALID_ARG, "scoring must be 0, 1 or 2");
     if (o.scoring == 2 && !ix->x8) return reject(PF_ERR_INVALID_ARG, "scoring 2 needs an index built with fp8_rows");
     if (o.stop_every < 0) return reject(PF_ERR_INVALID_ARG, "stop_every must be >= 0");
+    if (o.pool_rule != 0 && o.pool_rule != 1) return reject(PF_ERR_INVALID_ARG, "pool_rule must be 0 or 1");
+    if (ix->pool_tables > 0)
+      return reject(PF_ERR_INVALID_ARG, "a pooled index needs pf_index_search (its pool codes use the index workspace)");
     if (o.learned_start)
       return reject(PF_ERR_INVALID_ARG, "the learned start depth needs pf_index_search (it uses the index workspace)");
     const size_t need = scratch_bytes(ix, Q);
@@ -142,6 +145,7 @@ extern "C" pf_status pf_index_search_noalloc(pf_index* ix, const float* queries,
     a.filter = o.filter ? 1 : 0;
     a.scoring = o.scoring;
     a.stop_every = o.stop_every;
+    a.pool_rule = o.pool_rule;
     a.out_ids = out_ids;
     a.out_sims = out_sims;
     a.stats = stats;

@@ -298,6 +298,38 @@ __global__ void __launch_bounds__(kHashPts * kHashGroups) hash_simt_kernel(
   }
 }
 
+// Pooling (Sec. 3.2): table j's code concatenates the values of its pool
+// functions sel[j][0..F), the first in the most significant bits; function f is
+// slot f % F of pool group f / F, whose code holds it in bits
+// 32 - l (slot + 1) .. 32 - l slot - 1.
+__global__ void pool_gather_kernel(const uint32_t* __restrict__ gcodes, int64_t gj, int64_t gp, int64_t npts,
+                                   const int32_t* __restrict__ sel, int L, int F, int ell, uint32_t* __restrict__ codes,
+                                   int64_t cj, int64_t cp) {
+  const uint32_t mask = (1u << ell) - 1u;
+  const int64_t total = npts * L;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t j = e / npts, p = e % npts;
+    uint32_t code = 0;
+    for (int st = 0; st < F; ++st) {
+      const int f = __ldg(sel + j * F + st);
+      const int g = f / F, slot = f % F;
+      const uint32_t v = (__ldg(gcodes + g * gj + p * gp) >> (32 - ell * (slot + 1))) & mask;
+      code |= v << (32 - ell * (st + 1));
+    }
+    codes[j * cj + p * cp] = code;
+  }
+}
+
+cudaError_t launch_pool_gather(const pf_index* ix, const uint32_t* gcodes, int64_t gj, int64_t gp, int64_t npts,
+                               uint32_t* codes, int64_t cj, int64_t cp, cudaStream_t s) {
+  if (npts <= 0) return cudaSuccess;
+  const int64_t total = npts * ix->L;
+  const int blocks = int(std::min<int64_t>((total + 255) / 256, int64_t(ix->num_sms) * 32));
+  pool_gather_kernel<<<blocks, 256, 0, s>>>(gcodes, gj, gp, npts, ix->pool_sel, ix->L, ix->lay.fns, ix->lay.ell,
+                                            codes, cj, cp);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_quantize_fp8(const float* x32, int64_t rows, int d, int d_pad, uint8_t* x8, float2* meta,
                                 cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
@@ -307,11 +339,12 @@ cudaError_t launch_quantize_fp8(const float* x32, int64_t rows, int d, int d_pad
 
 cudaError_t launch_hash(const pf_index* ix, const float* x32, const __nv_bfloat16* xh, const __nv_bfloat16* xl,
                         int64_t npts, uint32_t* codes, int64_t cj, int64_t cp, uint64_t* sk, int64_t sm,
-                        int64_t sp, RecheckReq* rq, uint32_t* rq_count, uint32_t rq_cap, cudaStream_t s) {
+                        int64_t sp, RecheckReq* rq, uint32_t* rq_count, uint32_t rq_cap, cudaStream_t s,
+                        int tables) {
   if (npts <= 0) return cudaSuccess;
   // repetitions hashed from rows; the pseudo-random family has its own kernel
   // and leaves only the sketches to the row kernels
-  int tables = ix->L;
+  if (tables < 0) tables = ix->L;
   if (ix->family == PF_CROSSPOLYTOPE_FHT) {
     const cudaError_t e = launch_hash_fht(ix, x32, npts, codes, cj, cp, s);
     if (e != cudaSuccess) return e;

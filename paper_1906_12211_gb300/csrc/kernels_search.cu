@@ -65,6 +65,8 @@ cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t 
   P.counter = a.counter;
   P.path_count = ix->path_count;
   P.stop_every = a.stop_every;
+  P.pool_fns = ix->pool_fns;
+  P.pool_rule = a.pool_rule;
   const SearchShape sh = a.shape.unroll ? a.shape : ix->search_shape;
   const int U = sh.unroll == 4 ? 4 : 8, QW = sh.warps == 8 ? 8 : 4;
   const size_t smem = search_smem(P.d_pad, P.L, P.M, P.k_max, U, QW);

@@ -153,6 +153,62 @@ void gen_hash_rows(uint64_t seed, int family, int L, int M, int d, const Layout&
   });
 }
 
+// Pooling (Sec. 3.2, App. B.2).  Pool function f lives in group f / fns at
+// position f % fns, rows laid out exactly as a table's (so the hashing kernels
+// treat the groups as tables); its hyperplane c has N(0,1) entries at counter
+// (col, c, f, kPurposePool) (HP: c = 0).  Functions past m in the last group
+// are zero rows (hashed, never used).
+void gen_pool_rows(uint64_t seed, int family, int m, int M, int d, const Layout& lay, float* W, float* thr) {
+  const int dp = lay.d_pad;
+  const int groups = (m + lay.fns - 1) / lay.fns;
+  const int64_t rows = int64_t(groups) * lay.rows_table + 64LL * M;
+  std::memset(W, 0, sizeof(float) * size_t(rows) * dp);
+  std::memset(thr, 0, sizeof(float) * size_t(rows));
+  auto norm_band = [&](const float* row) {
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) s = s + double(row[i]) * double(row[i]);
+    return float(std::ldexp(std::sqrt(s), -12));
+  };
+  parallel_for(m, [&](int64_t f) {
+    const int64_t g = f / lay.fns, slot = f % lay.fns;
+    const int nrow = family == PF_CROSSPOLYTOPE ? d : 1;
+    float band = 0.f;
+    for (int c = 0; c < nrow; ++c) {
+      const int64_t row = family == PF_CROSSPOLYTOPE ? (g * lay.fns + slot) * int64_t(dp) + c : g * 32 + slot;
+      float* w = W + row * dp;
+      for (int i = 0; i < d; ++i) w[i] = gaussian(seed, kPurposePool, uint32_t(f), uint32_t(c), uint32_t(i));
+      const float b = norm_band(w);
+      if (family == PF_CROSSPOLYTOPE) band = std::max(band, b);
+      else thr[row] = b;
+    }
+    if (family == PF_CROSSPOLYTOPE)
+      for (int c = 0; c < dp; ++c) thr[(g * lay.fns + slot) * int64_t(dp) + c] = band;
+  });
+  const int64_t base = int64_t(groups) * lay.rows_table;
+  parallel_for(64LL * M, [&](int64_t r) {
+    float* w = W + (base + r) * dp;
+    for (int i = 0; i < d; ++i) w[i] = gaussian(seed, kPurposeSketch, 0u, uint32_t(r), uint32_t(i));
+    thr[base + r] = norm_band(w);
+  });
+}
+
+// Table j's subset: a partial Fisher-Yates shuffle of 0..m-1; at step s the
+// swap partner is s + floor(w (m - s) / 2^32), w word 0 of the generator at
+// counter (s, j, 0, kPurposePoolSelect); the subset in step order.
+void pool_select(uint64_t seed, int L, int F, int m, int32_t* sel) {
+  parallel_for(L, [&](int64_t j) {
+    std::vector<int32_t> perm(size_t(m > 0 ? m : 1));
+    for (int t = 0; t < m; ++t) perm[size_t(t)] = t;
+    for (int st = 0; st < F && st < m; ++st) {
+      uint32_t w[4] = {uint32_t(st), uint32_t(j), 0u, uint32_t(kPurposePoolSelect)};
+      Philox4x32::block(w, uint32_t(seed), uint32_t(seed >> 32));
+      const int r = st + int((uint64_t(w[0]) * uint64_t(m - st)) >> 32);
+      std::swap(perm[size_t(st)], perm[size_t(r)]);
+      sel[j * F + st] = perm[size_t(st)];
+    }
+  });
+}
+
 namespace {
 // index and sign bit of the largest |v_c| (first c on ties)
 uint32_t cp_code_of(const double* v, int d, int ell) {
@@ -325,25 +381,35 @@ void filter_cos_table(double* c) {
 // with per-repetition sketches, one uint64 per entry.  Fixed: the rows
 // (float32 + bfloat16), the sketch planes and, with per-point sketches, the M
 // sketches of every point.
-uint64_t resident_bytes(int family, int64_t n, int d, int M, int L, int sketch_layout, int row_storage, int fp8_rows) {
+uint64_t resident_bytes(int family, int64_t n, int d, int M, int L, int sketch_layout, int row_storage, int fp8_rows,
+                        int pool_fns) {
   const Layout lay = make_layout(family, d);
   const int64_t dp = lay.d_pad;
   const bool per_point = sketch_layout == PF_SKETCH_PER_POINT;
   const int64_t row_bytes = row_storage == PF_ROWS_F16 ? 4 : 6;  // rows (4 or 2 B) + the bfloat16 copy (2 B)
-  const int64_t fixed = n * dp * row_bytes + 64LL * M * dp * 8 + (per_point ? n * int64_t(M) * 8 : 0) +
-                        (fp8_rows ? n * (dp + 8) : 0);  // e4m3 rows + (scale, bound) per row
+  int64_t fixed = n * dp * row_bytes + 64LL * M * dp * 8 + (per_point ? n * int64_t(M) * 8 : 0) +
+                  (fp8_rows ? n * (dp + 8) : 0);  // e4m3 rows + (scale, bound) per row
+  // pooling: the pool's rows (whole groups of fns functions) are fixed; a
+  // table keeps its fns indices instead of rows
+  int64_t rows_table = lay.rows_table, sel_bytes = 0;
+  if (pool_fns > 0) {
+    fixed += int64_t((pool_fns + lay.fns - 1) / lay.fns) * lay.rows_table * dp * 8;
+    rows_table = 0;
+    sel_bytes = int64_t(lay.fns) * 4;
+  }
   // pseudo-random CP: three sign vectors per function instead of rows
   const int64_t fht = family == PF_CROSSPOLYTOPE_FHT ? int64_t(lay.fns) * 3 * lay.fht_words * 4 : 0;
   const int64_t per_table =
-      n * (per_point ? 8 : 16) + int64_t(kPrefixSize) * 4 + int64_t(lay.rows_table) * dp * 8 + fht;
+      n * (per_point ? 8 : 16) + int64_t(kPrefixSize) * 4 + rows_table * dp * 8 + fht + sel_bytes;
   return uint64_t(fixed + per_table * L);
 }
 
 int64_t budget_tables(int family, int64_t n, int d, int M, uint64_t budget, int sketch_layout, int row_storage,
-                      int fp8_rows) {
-  const uint64_t fixed = resident_bytes(family, n, d, M, 0, sketch_layout, row_storage, fp8_rows);
+                      int fp8_rows, int pool_fns) {
+  const uint64_t fixed = resident_bytes(family, n, d, M, 0, sketch_layout, row_storage, fp8_rows, pool_fns);
   if (budget <= fixed) return 0;
-  const uint64_t per_table = resident_bytes(family, n, d, M, 1, sketch_layout, row_storage, fp8_rows) - fixed;
+  const uint64_t per_table =
+      resident_bytes(family, n, d, M, 1, sketch_layout, row_storage, fp8_rows, pool_fns) - fixed;
   return int64_t((budget - fixed) / per_table);
 }
 

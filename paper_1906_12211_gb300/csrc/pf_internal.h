@@ -29,6 +29,8 @@ enum Purpose : uint32_t {
   kPurposeCpMc = 3,
   kPurposeFht = 4,    // sign vectors of the pseudo-random cross-polytope functions
   kPurposeFhtMc = 5,  // sign vectors of its Monte-Carlo collision draws
+  kPurposePool = 6,   // hyperplanes of the pooled functions
+  kPurposePoolSelect = 7,  // each table's subset of the pool
 };
 
 // Shape of one repetition's code (Sec. 4.3): l bits per function, floor(32/l)
@@ -64,9 +66,15 @@ void fht_collision_table(uint64_t seed, const Layout& lay, int draws, double* P 
 // bounds on the float32 transform's error for unit inputs: decisions whose top
 // two |y| are closer than *gap, or whose top |y| is below *sign, are redone in float64
 void fht_bands(int d, const Layout& lay, float* gap, float* sign);
+// pooling (Sec. 3.2): rows of m pooled functions laid out as ceil(m / fns)
+// groups shaped like tables (W [(groups*rows_table + 64*M)][d_pad], sketch
+// planes after them, as gen_hash_rows lays them out), and each table's subset
+void gen_pool_rows(uint64_t seed, int family, int m, int M, int d, const Layout& lay, float* W, float* thr);
+void pool_select(uint64_t seed, int L, int F, int m, int32_t* sel /*[L][F]*/);
 int64_t budget_tables(int family, int64_t n, int d, int M, uint64_t budget, int sketch_layout, int row_storage,
-                      int fp8_rows);
-uint64_t resident_bytes(int family, int64_t n, int d, int M, int L, int sketch_layout, int row_storage, int fp8_rows);
+                      int fp8_rows, int pool_fns);
+uint64_t resident_bytes(int family, int64_t n, int d, int M, int L, int sketch_layout, int row_storage, int fp8_rows,
+                        int pool_fns);
 
 // A hash decision the tensor-core kernel leaves to the float64 fix-up pass.
 struct RecheckReq {
@@ -93,6 +101,7 @@ struct pf_workspace {
   __nv_bfloat16* qxh = nullptr;  // [Q][d_pad] bfloat16 high half of qx
   __nv_bfloat16* qxl = nullptr;  // [Q][d_pad] bfloat16 low half (qx - qxh)
   uint32_t* qcodes = nullptr;  // [Q][L]
+  uint32_t* qgcodes = nullptr;  // [Q][pool groups] (pooled index only)
   uint64_t* qsk = nullptr;     // [Q][M]
   int32_t* k = nullptr;
   double* recall = nullptr;
@@ -132,6 +141,8 @@ struct pf_index {
   uint32_t* pfx = nullptr;         // [L][8193]
   double* cpP = nullptr;           // [41][ell+1]
   uint32_t* fht_signs = nullptr;   // [L][fns][3][fht_words] (pseudo-random family only)
+  int pool_fns = 0, pool_tables = 0;  // pooling: functions in the pool, groups of fns of them
+  int32_t* pool_sel = nullptr;     // [L][fns] each table's pool functions
   float fht_gap = 0.f, fht_sign = 0.f;  // its float64 recheck bands
   double* cos_tab = nullptr;       // [65]
   float bf16_err = 0.f;            // bound on |bf16 estimate - float32 canonical similarity|
@@ -175,9 +186,16 @@ cudaError_t launch_quantize_fp8(const float* x32, int64_t rows, int d, int d_pad
 // into one region per CTA of the hashing kernel; rq_count holds one counter per
 // region, at least ix->num_sms of them); without a queue, or where a region is
 // full, rechecks run inline.
+// tables: row-based repetitions to hash (-1: ix->L; a pooled index passes its
+// pool groups, whose codes pool_gather then combines)
 cudaError_t launch_hash(const pf_index* ix, const float* x32, const __nv_bfloat16* xh, const __nv_bfloat16* xl,
                         int64_t npts, uint32_t* codes, int64_t cj, int64_t cp, uint64_t* sk, int64_t sm,
-                        int64_t sp, RecheckReq* rq, uint32_t* rq_count, uint32_t rq_cap, cudaStream_t s);
+                        int64_t sp, RecheckReq* rq, uint32_t* rq_count, uint32_t rq_cap, cudaStream_t s,
+                        int tables = -1);
+// codes[j*cj + p*cp] of a pooled index from its pool groups' codes
+// gcodes[g*gj + p*gp] (group g holds pool functions g*fns .. g*fns + fns - 1)
+cudaError_t launch_pool_gather(const pf_index* ix, const uint32_t* gcodes, int64_t gj, int64_t gp, int64_t npts,
+                               uint32_t* codes, int64_t cj, int64_t cp, cudaStream_t s);
 // recheck-queue entries to provision for npts points
 inline uint32_t recheck_capacity(int64_t npts) { return uint32_t(npts * 48 + 65536); }
 bool hash_tc_supported(const pf_index* ix);
@@ -212,6 +230,7 @@ struct SearchArgs {
   pf_query_stats* stats = nullptr;
   int32_t* counter = nullptr;
   int stop_every = 0;  // pf_search_opts.stop_every
+  int pool_rule = 0;   // pf_search_opts.pool_rule
 };
 cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t s);
 // CTAs per SM the search kernel can keep resident for this index (0 on error)

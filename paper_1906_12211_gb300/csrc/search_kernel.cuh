@@ -89,6 +89,8 @@ struct Dev {
   // that galloped past them
   unsigned long long* path_count;
   int stop_every;  // 0: stop test per round; G: also after every G repetitions (Alg. 1)
+  int pool_fns;    // pooled index: functions in the pool (0: independent functions)
+  int pool_rule;   // pooled index: 0 Cantelli's bound, 1 Lemma 1 as if independent
 };
 
 __device__ __forceinline__ bool better(float s1, uint32_t i1, float s2, uint32_t i2) {
@@ -333,6 +335,28 @@ __device__ __forceinline__ float sim_fp8_pair(const float* __restrict__ q, const
   }
   const float acc = acc0 + acc1;
   return acc + __shfl_xor_sync(kFull, acc, 1);
+}
+
+// Stop test of a pooled index (Sec. 3.2, App. B.2, read for general delta):
+// j tables searched to prefix length `depth`, mu = j p_i, f = ceil(depth / l)
+// pool functions behind those bits, c = f^2 / ((m - f) P) with P one whole
+// function's collision probability; stop iff c < 1 and
+// (mu + mu^2 c/(1-c)) / (mu^2 + mu + mu^2 c/(1-c)) <= delta (Cantelli).  Every
+// operation is a correctly rounded float64 one, in the oracle's order.
+__device__ __forceinline__ bool pool_stop(const Dev& P, const float* s_alpha, float s_k, int depth, int j,
+                                          double delta) {
+  const int f = (depth + P.ell - 1) / P.ell;
+  const int m = P.pool_fns;
+  if (f <= 0 || f >= m || j <= 0) return false;
+  const double p = collision_prob(P, s_alpha, s_k, depth);
+  const double p1 = collision_prob(P, s_alpha, s_k, P.ell);
+  if (!(p1 > 0.0)) return false;
+  const double c = __ddiv_rn(double(f) * double(f), __dmul_rn(double(m - f), p1));
+  if (!(c < 1.0)) return false;
+  const double mu = __dmul_rn(double(j), p);
+  if (!(mu > 0.0)) return false;
+  const double var = __dadd_rn(mu, __dmul_rn(__dmul_rn(mu, mu), __ddiv_rn(c, __dsub_rn(1.0, c))));
+  return __ddiv_rn(var, __dadd_rn(__dmul_rn(mu, mu), var)) <= delta;
 }
 
 struct Counters {
@@ -763,10 +787,14 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
             int stop = 0;
             if (s_size == k) {
               const float skf = gs[k - 1];
-              double fail = ipow(__dsub_rn(1.0, collision_prob(P, s_alpha, skf, depth)), j1);
-              if (rounds > 0)
-                fail = __dmul_rn(fail, ipow(__dsub_rn(1.0, collision_prob(P, s_alpha, skf, depth + 1)), L - j1));
-              stop = fail <= delta ? 1 : 0;
+              if (P.pool_fns > 0 && P.pool_rule == 0) {  // only the j1 tables at this depth count
+                stop = pool_stop(P, s_alpha, skf, depth, j1, delta) ? 1 : 0;
+              } else {
+                double fail = ipow(__dsub_rn(1.0, collision_prob(P, s_alpha, skf, depth)), j1);
+                if (rounds > 0)
+                  fail = __dmul_rn(fail, ipow(__dsub_rn(1.0, collision_prob(P, s_alpha, skf, depth + 1)), L - j1));
+                stop = fail <= delta ? 1 : 0;
+              }
             }
             s_stop = stop;
           }
@@ -786,9 +814,13 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
       if (tid == 0) {
         int stop = 0;
         if (size == k) {
-          const double p = collision_prob(P, s_alpha, gs[k - 1], depth);
-          const double fail = ipow(__dsub_rn(1.0, p), L);
-          stop = fail <= delta ? 1 : 0;
+          if (P.pool_fns > 0 && P.pool_rule == 0) {
+            stop = pool_stop(P, s_alpha, gs[k - 1], depth, L, delta) ? 1 : 0;
+          } else {
+            const double p = collision_prob(P, s_alpha, gs[k - 1], depth);
+            const double fail = ipow(__dsub_rn(1.0, p), L);
+            stop = fail <= delta ? 1 : 0;
+          }
         }
         s_stop = stop;
       }
