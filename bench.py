@@ -84,6 +84,11 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other two modes")
     ap.add_argument("--recall", type=float, default=None,
                     help="recall target 1 - delta passed to the index (default: the workload's)")
+    ap.add_argument("--pool-bits", type=int, default=0,
+                    help="0: independent hash functions; m: tables draw their functions from a pool of m bits "
+                         "(Sec. 3.2; the paper uses 3072)")
+    ap.add_argument("--pool-rule", default="cantelli", choices=["cantelli", "independent"],
+                    help="stop rule of a pooled index: Cantelli's bound (guaranteed) or Lemma 1's as if independent")
     ap.add_argument("--estimate", default="bf16", choices=["bf16", "fp8"],
                     help="row copy the estimate-and-rerank modes score with: bfloat16, or e4m3 with per-row scales "
                          "(the index then keeps an e4m3 copy, which the budget counts)")
@@ -178,7 +183,8 @@ def search_kernel_traffic(args=None):
                              or args.mode != "learned" or args.train_queries != 100_000 or args.epochs != 20
                              or args.recall != 0.9 or getattr(args, "workload", WORKLOAD) != WORKLOAD
                              or getattr(args, "family", "crosspolytope") != "crosspolytope"
-                             or getattr(args, "estimate", "bf16") != "bf16" or getattr(args, "stop_every", 0)):
+                             or getattr(args, "estimate", "bf16") != "bf16" or getattr(args, "stop_every", 0)
+                             or getattr(args, "pool_bits", 0)):
         return None
     path = os.path.join(ROOT, "profiles", "search_kernel_traffic.txt")
     src = os.path.join(ROOT, "paper_1906_12211_gb300", "csrc", "search_kernel.cuh")
@@ -269,21 +275,21 @@ def algorithmic_bytes(st, L, n, d, k, mode):
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_index(X, L):
+def oracle_index(X, L, pool_bits=0):
     """The oracle's index over all the workload's points with the GPU's L and
     the same seed; returns (index, build seconds)."""
     import oracle
 
     t = time.perf_counter()
-    oix = oracle.OracleIndex(X, oracle.CROSSPOLYTOPE, L=L, seed=0)
+    oix = oracle.OracleIndex(X, oracle.CROSSPOLYTOPE, L=L, seed=0, pool_bits=pool_bits)
     return oix, time.perf_counter() - t
 
 
-def oracle_queries_for(oix, Qs, k, recall, seconds, probe=16):
+def oracle_queries_for(oix, Qs, k, recall, seconds, probe=16, pool_rule="cantelli"):
     """How many of the queries the oracle answers in about `seconds` (timed on
     `probe` of them first)."""
     t = time.perf_counter()
-    oix.search(Qs[:probe], k, recall)
+    oix.search(Qs[:probe], k, recall, pool_rule=pool_rule)
     per_q = (time.perf_counter() - t) / probe
     return int(max(probe, min(Qs.shape[0], seconds / max(per_q, 1e-9))))
 
@@ -295,17 +301,17 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(w, X, Qs, L, k, recall, q_target_s=15.0, single_target_s=10.0):
+def cpu_baseline(w, X, Qs, L, k, recall, q_target_s=15.0, single_target_s=10.0, pool_bits=0, pool_rule="cantelli"):
     """The oracle timed on the host cores: its index over all n points with the
     GPU's L (build timed separately), a bounded sample of the queries (about
     q_target_s), and one thread answering queries one after another as the paper
     measures (Sec. 5)."""
     import oracle
 
-    oix, build_s = oracle_index(X, L)
-    nq = oracle_queries_for(oix, Qs, k, recall, q_target_s)
+    oix, build_s = oracle_index(X, L, pool_bits)
+    nq = oracle_queries_for(oix, Qs, k, recall, q_target_s, pool_rule=pool_rule)
     t = time.perf_counter()
-    oix.search(Qs[:nq], k, recall)
+    oix.search(Qs[:nq], k, recall, pool_rule=pool_rule)
     el = time.perf_counter() - t
     cpu = {"value": nq / el, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
            "sample": f"oracle index over all {X.shape[0]:,} points (same data, seed and L={L}; built in "
@@ -313,9 +319,9 @@ def cpu_baseline(w, X, Qs, L, k, recall, q_target_s=15.0, single_target_s=10.0):
            "build_s": build_s}
     oracle.set_threads(1)
     try:
-        n1 = oracle_queries_for(oix, Qs, k, recall, single_target_s, probe=4)
+        n1 = oracle_queries_for(oix, Qs, k, recall, single_target_s, probe=4, pool_rule=pool_rule)
         t = time.perf_counter()
-        oix.search(Qs[:n1], k, recall)
+        oix.search(Qs[:n1], k, recall, pool_rule=pool_rule)
         el1 = time.perf_counter() - t
     finally:
         oracle.set_threads(0)
@@ -422,7 +428,8 @@ def main():
     Qd = [torch.from_numpy(Qs).to(dev), torch.from_numpy(Qs2).to(dev)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ix = pf.Index(Xd, args.family, budget_bytes=w["budget"], seed=0, fp8_rows=args.estimate == "fp8")
+    ix = pf.Index(Xd, args.family, budget_bytes=w["budget"], seed=0, fp8_rows=args.estimate == "fp8",
+                  pool_bits=args.pool_bits)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     kth = [brute_force_kth(torch, Xd, q, k) for q in Qd]
@@ -451,7 +458,7 @@ def main():
         tune_report = ix.tune(torch.from_numpy(Qtune).to(dev), k, args.recall,
                               scoring="fp32" if args.mode == "fp32" else args.estimate,
                               learned=args.mode == "learned",
-                              stop_every=args.stop_every)
+                              stop_every=args.stop_every, pool_rule=args.pool_rule)
 
     def opts_of(mode):
         return ("fp32" if mode == "fp32" else args.estimate), mode == "learned"
@@ -470,7 +477,7 @@ def main():
 
         def run(timing=False):
             ix.search(Qd[0], kq[0], rq[0], k_max=k, scoring=sc, out_ids=o1[0], out_sims=o1[1], stats=o1[2],
-                      timing=timing, learned=lr, stop_every=args.stop_every)
+                      timing=timing, learned=lr, stop_every=args.stop_every, pool_rule=args.pool_rule)
 
         kern = {"kernel_ms": 0.0, "hash_ms": 0.0}
 
@@ -497,9 +504,9 @@ def main():
         sims = [o1[1]]
         if not args.no_graph:
             pa = ix.plan(Qd[0], kq[0], rq[0], *outputs()[:2], k_max=k, scoring=sc, learned=lr,
-                         stop_every=args.stop_every)
+                         stop_every=args.stop_every, pool_rule=args.pool_rule)
             pb = ix.plan(Qd[1], kq[1], rq[1], o2[0], o2[1], k_max=k, stats=o2[2], scoring=sc, learned=lr,
-                         stop_every=args.stop_every)
+                         stop_every=args.stop_every, pool_rule=args.pool_rule)
             plans = [pa, pb]
             try:
                 for _ in range(max(3, args.warmup)):
@@ -527,6 +534,8 @@ def main():
                                 "clocks": clk_fl}
             stats.append(pf.stats_to_numpy(o2[2]))
             sims.append(o2[1])
+        res["scoring"] = sc
+        res["start_depth"] = "learned" if lr else "plain"
         res["recall"] = [recall_of(s_, kth[b]) for b, s_ in enumerate(sims)]
         allst = np.concatenate(stats)
         res["per_query"] = {f: float(allst[f].mean()) for f in ("start_depth", "stop_depth", "rounds", "retrieved",
@@ -574,7 +583,7 @@ def main():
 
         # one batch at a time: pf_index_search given the host pointers
         el = wall(lambda i: ix.search(hq[0], hk[0], hr[0], k_max=k, scoring=sc, out_ids=hi[0], out_sims=hs[0],
-                                      learned=lr, stop_every=args.stop_every), args.steps)
+                                      learned=lr, stop_every=args.stop_every, pool_rule=args.pool_rule), args.steps)
         assert torch.equal(hi[0], ids1.cpu()) and torch.equal(hs[0], sims1.cpu())
         seq_e2e = {"value": whole_job_rate(Q, world, args.steps, el), "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "how": "pf_index_search with page-locked host pointers, one batch "
@@ -584,7 +593,7 @@ def main():
             # two batches in flight: plans bound to the host buffers (each graph
             # copies its inputs in and its outputs out on its own stream)
             plans = [ix.plan(hq[b], hk[b], hr[b], hi[b], hs[b], k_max=k, scoring=sc, learned=lr,
-                             stop_every=args.stop_every) for b in range(2)]
+                             stop_every=args.stop_every, pool_rule=args.pool_rule) for b in range(2)]
             try:
                 el = wall(lambda i: plans[i % 2].run(streams[i % 2]), args.steps)
                 for p_, s_ in zip(plans, streams):
@@ -614,7 +623,7 @@ def main():
     if args.family == "fht":  # the oracle states this family in numpy: far too slow for a full-size index
         cpu = {"skipped": "the oracle's pseudo-random family (numpy) cannot index the full workload in minutes"}
     elif rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, X, Qs, ix.L, k, args.recall)
+        cpu = cpu_baseline(w, X, Qs, ix.L, k, args.recall, pool_bits=args.pool_bits, pool_rule=args.pool_rule)
 
     fl = head.get("in_flight")
     if fl:
@@ -642,6 +651,8 @@ def main():
                        "L": ix.L, "scoring": sc, "start_depth": "learned" if args.mode == "learned" else "plain",
                        "stop_test": (f"after every {args.stop_every} repetitions" if args.stop_every
                                      else "after every round"),
+                       "hash_functions": (f"pooled: {args.pool_bits} bits, stop rule {args.pool_rule}"
+                                          if args.pool_bits else "independent"),
                        "l2": l2, "pipelining": pipelining, "parallelism": f"replica x{world}"},
             "recall": recall, "recall_per_batch": head["recall"], "build_s": build_s,
             "per_query": head["per_query"],

@@ -324,10 +324,10 @@ class Index:
         return o
 
     def tune(self, queries, k: int, recall: float, *, scoring: str = "fp32", filter: bool = True,
-             learned: bool = False, stream=None, stop_every: int = 0):
+             learned: bool = False, stream=None, stop_every: int = 0, pool_rule: str = "cantelli"):
         """pf_index_tune: time the search launch shapes on this batch and keep the fastest."""
         rep = TuneReport()
-        o = self._opts(scoring, filter, learned, stop_every)
+        o = self._opts(scoring, filter, learned, stop_every, pool_rule)
         _check(lib().pf_index_tune(self._h, _ptr(queries), int(queries.shape[0]), int(k), float(recall),
                                    C.byref(o), C.byref(rep), _stream_ptr(stream)))
         return {f: getattr(rep, f) for f, _ in TuneReport._fields_}
