@@ -62,7 +62,13 @@ METRICS = {
     "vmf1k-n1m-d100": "k-NN queries/s at recall>=0.9 (n=1M, d=100, k=10)",
     # Sec. 5 SYNTHETIC (n = 10^6, 300 dimensions, 1,000 queries, k = 10)
     "paper-synthetic-n1m-d300": "k-NN queries/s, recall target 0.99 (paper SYNTHETIC: n=1M, 300 dims, k=10)",
+    # the other workloads of the scope: the planted hard instance, the uneven batch, 10^7 binary16 rows
+    "planted-n3m-d256": "1-NN queries/s at recall target 0.95 (planted: n=3,001,000, d=256, k=1)",
+    "vmf4k-n2m-d128-mixed": "k-NN queries/s, 10^5 queries with k in {1,10,100} x delta in {0.5,0.1,0.01} "
+                            "(n=2M, d=128), one captured tuned launch",
+    "vmf10k-n10m-d96-f16": "k-NN queries/s at recall target 0.9 (n=10M, d=96, binary16 rows, k=10)",
 }
+EXTRA_WORKLOADS = ("planted-n3m-d256", "vmf4k-n2m-d128-mixed", "vmf10k-n10m-d96-f16")
 METRIC = METRICS[WORKLOAD]
 # the paper's single-thread CPU figure on SYNTHETIC: 360.3 queries/s at recall 0.971 (Sec. 5, comparison with other approaches)
 PAPER_SYNTHETIC_QPS, PAPER_SYNTHETIC_RECALL = 360.3, 0.971
@@ -109,7 +115,7 @@ def parse():
                     help="skip the captured (CUDA graph) searches: the headline is then the sequential step")
     args = ap.parse_args()
     if args.recall is None:
-        args.recall = datagen.WORKLOADS[args.workload]["recall"]
+        args.recall = datagen.WORKLOADS[args.workload].get("recall")
     return args
 
 
@@ -334,6 +340,10 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.workload in EXTRA_WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable": f"the oracle cannot index {args.workload} "
+                          "(millions of points) within a bench run; the default workload has the reference arm"}))
+        return
     w, X, Qs = workload(0, args.points, args.queries, args.budget, args.workload)
     import oracle
 
@@ -361,6 +371,178 @@ def run_reference(args):
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample,
                          "build_s": build_s},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------- the other workloads
+def run_extra(args):
+    """The planted instance, the uneven batch and the 10^7-point binary16 index:
+    the batch's throughput (CUDA events on the launching stream, L2 flushed
+    between steps), its recall against brute force, the per-query counts, and
+    the same batch end to end through pf_index_search with page-locked host
+    buffers."""
+    import torch
+
+    import paper_1906_12211_gb300 as pf
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    pf.build()
+    name = args.workload
+    w = datagen.WORKLOADS[name]
+    Qn = w["Q"] if args.queries is None else args.queries
+    n = w["n"] if args.points is None else args.points
+    t0 = time.perf_counter()
+    nn_ids = None
+    if name == "planted-n3m-d256":
+        X, Qs, nn_ids = datagen.planted(n - Qn * 2001, w["d"], Qn, seed=0)
+    else:
+        X = datagen.vmf_mixture(n, w["d"], w["components"], w["kappa"], seed=0, purpose="points")
+        Qs = datagen.vmf_mixture(Qn, w["d"], w["components"], w["kappa"], seed=0, purpose="queries")
+    gen_s = time.perf_counter() - t0
+    if name == "vmf4k-n2m-d128-mixed":
+        kk, rr = datagen.mixed_k_recall(Qn, seed=0)
+        k_max = int(w["k"])
+    else:
+        kk = np.full(Qn, w["k"], np.int32)
+        rr = np.full(Qn, args.recall, np.float64)
+        k_max = int(w["k"])
+    Xd = torch.from_numpy(X).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ix = pf.Index(Xd, args.family, budget_bytes=w["budget"], seed=0, rows=w.get("rows", "f32"),
+                  fp8_rows=args.estimate == "fp8", pool_bits=args.pool_bits)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    Qd = torch.from_numpy(Qs).to(dev)
+    kd, rd = torch.from_numpy(kk).to(dev), torch.from_numpy(rr).to(dev)
+    # exact top-k_max similarities for recall (float32 matmul on the GPU)
+    Xn = torch.nn.functional.normalize(Xd, dim=1)
+    top = []
+    for s0 in range(0, Qn, 256):
+        qn = torch.nn.functional.normalize(Qd[s0:s0 + 256], dim=1)
+        best = None
+        for c0 in range(0, n, 1 << 21):
+            v = (qn @ Xn[c0:c0 + (1 << 21)].T).topk(min(k_max, Xn[c0:c0 + (1 << 21)].shape[0]), dim=1).values
+            best = v if best is None else torch.cat([best, v], dim=1).topk(k_max, dim=1).values
+        top.append(best)
+    true_top = torch.cat(top)
+    del Xn, Xd
+    torch.cuda.empty_cache()
+    sc = "fp32" if args.mode == "fp32" else args.estimate
+    # the planted queries each have a neighbour of their own: no held-out
+    # queries of that kind exist to train a start depth on, so the schedule is plain
+    learned = args.mode == "learned" and name != "planted-n3m-d256"
+    train_s = None
+    if learned:
+        Qt = datagen.vmf_mixture(200_000 if name == "vmf10k-n10m-d96-f16" else 100_000, w["d"],
+                                 w.get("components", 1000), w.get("kappa", 50.0), seed=0, purpose="train") \
+            if name != "planted-n3m-d256" else Qs[: max(1, Qn // 2)]
+        t0 = time.perf_counter()
+        ix.learned_train(torch.from_numpy(np.ascontiguousarray(Qt)).to(dev), int(np.max(kk)) if name != "vmf4k-n2m-d128-mixed" else 10,
+                         0.9 if args.recall is None else args.recall, epochs=args.epochs, seed=0)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+    ix.tune(Qd[: min(Qn, 20_000)], 10 if name == "vmf4k-n2m-d128-mixed" else int(w["k"]),
+            0.9 if args.recall is None else args.recall, scoring=sc, learned=args.mode == "learned")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def measure(filt, learned, steps):
+        ids = torch.empty((Qn, k_max), dtype=torch.int32, device=dev)
+        sims = torch.empty((Qn, k_max), dtype=torch.float32, device=dev)
+        st = torch.empty((Qn, pf.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+        if name == "vmf4k-n2m-d128-mixed":  # the whole batch as one captured, tuned launch
+            plan = ix.plan(Qd, kd, rd, ids, sims, k_max=k_max, stats=st, scoring=sc, filter=filt, learned=learned)
+            run = lambda: plan.run(stream)  # noqa: E731
+        else:
+            plan = None
+            kern = [0.0]
+
+            def run():
+                ix.search(Qd, kd, rd, k_max=k_max, scoring=sc, filter=filt, out_ids=ids, out_sims=sims, stats=st,
+                          learned=learned, timing=True)
+                kern[0] += ix.last_timing()[1]
+        try:
+            for _ in range(max(2, args.warmup)):
+                run()
+            if plan is None:
+                kern[0] = 0.0
+            sampler = ClockSampler(0)
+            torch.cuda.synchronize()
+            sampler.start()
+            ms = timed_sequential(torch, run, flush, stream, steps)
+            clk = sampler.stop()
+            if plan:
+                plan.check(stream)
+        finally:
+            if plan:
+                plan.close()
+        stats = pf.stats_to_numpy(st)
+        kth = true_top.gather(1, (kd.long() - 1).clamp(min=0)[:, None])[:, 0]
+        hit = (sims >= kth[:, None] - 1e-6) & (torch.arange(k_max, device=dev)[None, :] < kd[:, None])
+        per_q = hit.sum(1).float() / kd.float()
+        kernel_ms = kern[0] / steps if plan is None else ms / steps  # a captured plan: the whole graph
+        out = {"value": Qn * steps / (ms / 1e3), "ms_per_step": ms / steps, "clocks": clk, "kernel_ms": kernel_ms,
+               "algorithmic_bytes_per_launch": algorithmic_bytes(stats, ix.L, ix.n, ix.d, float(kk.mean()), sc) * Qn,
+               "recall": float(per_q.mean().item()),
+               "per_query": {f: float(stats[f].mean()) for f in ("start_depth", "stop_depth", "rounds", "retrieved",
+                                                                 "passed_filter", "scored", "reranked")}}
+        if nn_ids is not None:  # the planted neighbour returned first
+            out["planted_found"] = float((ids[:, 0].cpu().numpy().astype(np.int64) == nn_ids).mean())
+        if name == "vmf4k-n2m-d128-mixed":
+            cls = {}
+            pq = per_q.cpu().numpy()
+            for kv in (1, 10, 100):
+                for dv in (0.5, 0.1, 0.01):
+                    m = (kk == kv) & (np.abs((1 - rr) - dv) < 1e-12)
+                    cls[f"k={kv},delta={dv}"] = {"queries": int(m.sum()), "recall": float(pq[m].mean()),
+                                                 "target": 1 - dv}
+            out["per_class"] = cls
+        return out, ids, sims
+
+    head, ids, sims = measure(True, learned, args.steps)
+    variants = {"filter_off": measure(False, learned, max(3, args.steps // 2))[0]}
+    if learned:
+        variants["plain_schedule"] = measure(True, False, max(3, args.steps // 2))[0]
+    # end to end: host queries, k and recall in, ids and similarities out, every step
+    hq, hk, hr = (torch.from_numpy(Qs).pin_memory(), torch.from_numpy(kk).pin_memory(),
+                  torch.from_numpy(rr).pin_memory())
+    hi = torch.empty((Qn, k_max), dtype=torch.int32).pin_memory()
+    hs = torch.empty((Qn, k_max), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        ix.search(hq, hk, hr, k_max=k_max, scoring=sc, out_ids=hi, out_sims=hs, learned=learned)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        ix.search(hq, hk, hr, k_max=k_max, scoring=sc, out_ids=hi, out_sims=hs, learned=learned)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t
+    assert torch.equal(hi, ids.cpu()) and torch.equal(hs, sims.cpu())
+    e2e = {"value": Qn * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": int(Qn * w["d"] * 4 + Qn * 12),
+           "d2h_bytes_per_step": int(Qn * k_max * 8), "how": "pf_index_search with page-locked host pointers"}
+    peak, peak_kind = measured_peaks()
+    achieved = head["algorithmic_bytes_per_launch"] / (head["kernel_ms"] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "search_kernel" if name != "vmf4k-n2m-d128-mixed" else "whole graph",
+                "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "algorithmic_bytes_per_launch": head["algorithmic_bytes_per_launch"],
+                "kernel_ms": head["kernel_ms"]}
+    print(json.dumps({
+        "metric": METRICS[name], "value": head["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if sc == "fp32" else f"{sc}+f32", "mode": args.mode,
+        "data": "synthetic",
+        "config": {"workload": name, "n": int(n), "d": int(w["d"]), "queries": int(Qn), "k_max": k_max,
+                   "budget_bytes": w["budget"], "L": ix.L, "rows": w.get("rows", "f32"), "family": args.family,
+                   "scoring": sc, "start_depth": "learned" if learned else "plain",
+                   "l2": "flushed between steps (512 MiB write)", "filter": "on"},
+        "recall": head["recall"], "per_query": head["per_query"],
+        **({"planted_found": head["planted_found"]} if "planted_found" in head else {}),
+        **({"per_class": head["per_class"]} if "per_class" in head else {}),
+        "variants": variants, "build_s": build_s, "datagen_s": gen_s, "learned_train_s": train_s,
+        "gpu_launches": (5 if learned else 4) * args.steps,
+        "cpu_baseline": {"skipped": "the oracle cannot index this many points within a bench run"},
+        "roofline": roofline, "e2e": e2e, "clocks": head["clocks"],
     }), flush=True)
 
 
@@ -405,6 +587,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload in EXTRA_WORKLOADS:
+        run_extra(args)
         return
     import torch
 

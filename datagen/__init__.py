@@ -160,7 +160,9 @@ WORKLOADS = {
     "planted-n3m-d256": dict(n=3_001_000, d=256, Q=1000, family="crosspolytope", budget=8 << 30, k=1,
                              recall=0.95),
     "vmf4k-n2m-d128-mixed": dict(n=2_000_000, d=128, Q=100_000, family="crosspolytope", budget=8 << 30,
-                                 components=4000, kappa=(20.0, 200.0)),
+                                 components=4000, kappa=(20.0, 200.0), recall=None, k=100),
+    "vmf10k-n10m-d96-f16": dict(n=10_000_000, d=96, Q=100_000, family="crosspolytope", budget=40 << 30, k=10,
+                                recall=0.9, components=10_000, kappa=100.0, rows="f16"),
     # Sec. 5 SYNTHETIC: n = 10^6, 3 x 100 dimensions, 1,000 queries
     "paper-synthetic-n1m-d300": dict(n=1_000_000, d=300, Q=1000, family="crosspolytope", budget=8 << 30, k=10,
                                      recall=0.99, block=100),
