@@ -639,11 +639,18 @@ static int popcount64(uint64_t w) {
  * Readings: the paper refreshes the accumulator (and so tau) after every k
  * insertions, in the order repetitions are inspected (Sec. 4.2); here tau is
  * taken from the accumulator at the start of each round and, in a query's first
- * round (which starts with an empty accumulator), also at the start of every
- * group of 32 repetitions (j = 32, 64, ...), so within a group the visiting
- * order does not matter.  The stop test runs once per round (Sec. 4.1); the
+ * round (which starts with an empty accumulator), also before repetitions
+ * 1, 2, 4, 8, 16 and every 32 after that, so within a group the visiting order
+ * does not matter.  The stop test runs once per round (Sec. 4.1); the
  * initial range of a repetition is empty at the first position whose code is
  * >= the query code. */
+/* Reading of the accumulator's refresh in a first round (Sec. 4.2): snapshots
+ * before repetitions 1, 2, 4, 8, 16 and then every 32 (the first repetitions'
+ * blocks fill the top-k, so the threshold tightens early). */
+static int first_round_snapshot(int j) {
+  return j < ORC_SNAPSHOT_GROUP ? (j & (j - 1)) == 0 : j % ORC_SNAPSHOT_GROUP == 0;
+}
+
 static void search_one(const orc_index* ix, const float* q, const uint32_t* qcode, const uint64_t* qsk,
                        int k, double recall, int k_max, int32_t start_depth, int filter, int stop_every,
                        uint32_t* out_ids, float* out_sims, orc_stats* st,
@@ -673,7 +680,7 @@ static void search_one(const orc_index* ix, const float* q, const uint32_t* qcod
     int tau = 64;
     for (int j = 0; j < L; ++j) {
       if (j == 0 || (stop_every > 0 ? j % stop_every == 0
-                                    : (s.rounds == 0 && j % ORC_SNAPSHOT_GROUP == 0))) { /* threshold snapshot */
+                                    : (s.rounds == 0 && first_round_snapshot(j)))) { /* threshold snapshot */
         const int full = (size == k);
         tau = full ? orc_filter_tau((double)ps[k - 1]) : 64;
       }

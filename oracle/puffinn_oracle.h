@@ -33,7 +33,8 @@ enum { ORC_PURPOSE_HASH = 1, ORC_PURPOSE_SKETCH = 2, ORC_PURPOSE_CPMC = 3,
        ORC_PURPOSE_POOL = 6 /* rows of the pooled functions */, ORC_PURPOSE_POOL_SELECT = 7 /* their subsets */ };
 #define ORC_PREFIX_BITS 13
 #define ORC_ALPHA_STEPS 41 /* similarity grid -1, -0.95, ..., 1 (Sec. 4.3) */
-#define ORC_SNAPSHOT_GROUP 32 /* repetitions per sketch-threshold snapshot in a query's first round */
+#define ORC_SNAPSHOT_GROUP 32 /* repetitions per sketch-threshold snapshot in a query's first round, after the
+                                 geometric start 1, 2, 4, 8, 16 */
 
 /* Host threads of the OpenMP loops (n <= 0: all processors). */
 void orc_set_threads(int n);

@@ -52,7 +52,13 @@ constexpr unsigned kFull = 0xffffffffu;
 // chosen by the tuner); a chunk is 32*U positions of one run
 constexpr int kFlushAt = 256;   // a warp scores its buffer once it holds more than this
 __host__ __device__ constexpr int cand_buf(int U) { return kFlushAt + 32 * U; }  // compacted ids per warp
-constexpr int kGroup = 32;      // repetitions per threshold snapshot in a first round
+constexpr int kGroup = 32;      // repetitions per threshold snapshot in a first round (after 1, 2, 4, 8, 16)
+
+// first repetition of threshold-snapshot group g of a first round: 0, 1, 2,
+// 4, 8, 16, then every kGroup
+__device__ __forceinline__ int first_round_group_start(int g) {
+  return g == 0 ? 0 : (g <= 5 ? 1 << (g - 1) : kGroup * (g - 5));
+}
 constexpr int kSub = 64;        // candidates per bfloat16 sub-batch (the pruning bound is refreshed between)
 
 struct Dev {
@@ -693,13 +699,14 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
       // ---- stream the chunks, group by group
       // groups of repetitions: in a first round (threshold snapshots), and in
       // every round when the stop test also runs after groups of G repetitions
-      const bool grouped = rounds == 0 || P.stop_every > 0;
-      const int G = P.stop_every > 0 ? P.stop_every : kGroup;
-      const int ngroups = grouped ? (L + G - 1) / G : 1;
+      const bool every = P.stop_every > 0;
+      const bool grouped = rounds == 0 || every;
+      const int G = P.stop_every;
       bool stopped_mid = false;
-      for (int grp = 0; grp < ngroups; ++grp) {
-        const int j0 = grouped ? grp * G : 0;
-        const int j1 = grouped ? min(L, j0 + G) : L;
+      for (int grp = 0;; ++grp) {
+        const int j0 = !grouped ? (grp == 0 ? 0 : L) : every ? grp * G : first_round_group_start(grp);
+        if (j0 >= L) break;
+        const int j1 = !grouped ? L : min(L, every ? j0 + G : first_round_group_start(grp + 1));
         // threshold snapshot: every earlier candidate is in the merged top-k
         const int gsize = s_size;
         const float gkth = gsize == k ? gs[k - 1] : -INFINITY;

@@ -8,8 +8,8 @@ decision for every entry with nothing from the oracle's query code: the Hamming
 distance of sketch (j mod M) of the query and of the point (popcount in
 numpy), and the threshold from the top-k of the entries scored before the
 entry's snapshot (the largest t with cos(t*pi/64) >= s_k, numpy float64).
-Snapshots: at the start of every round and, in the first round, at the start
-of every group of 32 repetitions.  A plausible slip in the oracle ('>=' for
+Snapshots: at the start of every round and, in the first round, before
+repetitions 1, 2, 4, 8, 16 and every 32 after that.  A plausible slip in the oracle ('>=' for
 '>', the wrong sketch, a threshold that is not refreshed) changes some flags;
 `test_planted_mistakes_are_caught` plants each one in a copy of the oracle and
 checks that the replay sees it.
@@ -26,7 +26,13 @@ import pytest
 
 import datagen
 
-GROUP = 32  # repetitions per threshold snapshot in a query's first round
+GROUP = 32  # repetitions per threshold snapshot in a query's first round, after 1, 2, 4, 8, 16
+
+
+def _first_round_group(j: int) -> int:
+    """Snapshot group of repetition j in a first round: boundaries 1, 2, 4, 8,
+    16, then every 32."""
+    return 0 if j == 0 else (j.bit_length() if j < GROUP else 5 + j // GROUP)
 _COS = np.cos(np.arange(65) * np.pi / 64.0)
 
 
@@ -59,7 +65,7 @@ def _replay(orc, ix, res, t: int, k: int, sims_t: np.ndarray):
     prev = None
     for e in range(len(tr)):
         d_e, j_e = int(depth[e]), int(j[e])
-        snap = (d_e, j_e // GROUP if d_e == start else -1)
+        snap = (d_e, _first_round_group(j_e) if d_e == start else -1)
         if snap != prev:
             tau = 64 if len(top) < k else _tau(float(top[-1][0]))
             prev = snap
@@ -147,7 +153,9 @@ def test_ties_at_the_threshold_pass(orc, cases):
 _MUTANTS = {
     "ge_instead_of_gt": ("if (ham > tau) continue;", "if (ham >= tau) continue;"),
     "query_sketch_index": ("popcount64(qsk[j % M] ^", "popcount64(qsk[(j + 1) % M] ^"),
-    "no_first_round_groups": ("(s.rounds == 0 && j % ORC_SNAPSHOT_GROUP == 0)", "(0)"),
+    "no_first_round_groups": ("(s.rounds == 0 && first_round_snapshot(j))", "(0)"),
+    "first_round_groups_of_32": ("(s.rounds == 0 && first_round_snapshot(j))",
+                                 "(s.rounds == 0 && j % ORC_SNAPSHOT_GROUP == 0)"),
     "no_refresh_per_round": ("if (j == 0 || (stop_every", "if ((j == 0 && s.rounds == 0) || (stop_every"),
     "kth_from_wrong_slot": ("orc_filter_tau((double)ps[k - 1])", "orc_filter_tau((double)ps[0])"),
 }
