@@ -397,9 +397,11 @@ pf_status pf_index_selftest_hold(pf_index* index, int32_t hold);
  * With enable != 0, later searches of this index count how each range step
  * was settled: counts[0] steps at prefix length <= 13 read from the 13-bit
  * prefix table, counts[1] sides settled within the first four segment
- * boundaries probed together, counts[2] sides that galloped past them.  Each
- * call waits for the device, writes the counts since the previous call into
- * counts (NULL: not read) and resets them; enable == 0 stops counting (not
+ * boundaries probed together, counts[2] sides that galloped past them,
+ * counts[3] rounds whose new positions were streamed in chunks of one run,
+ * counts[4] rounds streamed as one flat sequence (short runs).  Each call waits
+ * for the device, writes the 5 counts since the previous call into counts
+ * (NULL: not read) and resets them; enable == 0 stops counting (not
  * while search plans exist: they were captured with the counters).  The
  * counters cost device atomics: leave them off outside tests.  Errors:
  * PF_ERR_INVALID_ARG (null index, plans exist), PF_ERR_OOM, CUDA. */

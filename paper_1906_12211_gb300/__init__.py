@@ -342,11 +342,12 @@ class Index:
         _check(lib().pf_index_selftest_timeout(self._h, _ptr(queries), int(queries.shape[0]), _stream_ptr(stream)))
 
     def count_range_paths(self, enable: bool = True):
-        """pf_index_count_range_paths: the counts since the last call as
-        {"prefix_table", "probed", "galloped"}; enable=False stops counting."""
-        c = (C.c_uint64 * 3)()
+        """pf_index_count_range_paths: the counts since the last call (range
+        steps by branch, rounds by streaming mode); enable=False stops counting."""
+        c = (C.c_uint64 * 5)()
         _check(lib().pf_index_count_range_paths(self._h, 1 if enable else 0, c))
-        return {"prefix_table": int(c[0]), "probed": int(c[1]), "galloped": int(c[2])}
+        return {"prefix_table": int(c[0]), "probed": int(c[1]), "galloped": int(c[2]), "chunked_rounds": int(c[3]),
+                "flat_rounds": int(c[4])}
 
     def selftest_hold(self, hold: bool):
         """pf_index_selftest_hold: withhold (True) or restore (False) the weight

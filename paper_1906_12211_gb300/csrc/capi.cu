@@ -926,16 +926,16 @@ pf_status pf_index_count_range_paths(pf_index* ix, int32_t enable, uint64_t* cou
     if (!ix) return fail(PF_ERR_INVALID_ARG, "null index");
     PF_CK(cudaSetDevice(ix->device));
     PF_CK(cudaDeviceSynchronize());
-    uint64_t c[3] = {0, 0, 0};
+    uint64_t c[5] = {0, 0, 0, 0, 0};
     if (ix->path_count) {
       PF_CK(cudaMemcpy(c, ix->path_count, sizeof(c), cudaMemcpyDeviceToHost));
       PF_CK(cudaMemset(ix->path_count, 0, sizeof(c)));
     }
     if (counts)
-      for (int i = 0; i < 3; ++i) counts[i] = c[i];
+      for (int i = 0; i < 5; ++i) counts[i] = c[i];
     if (enable && !ix->path_count) {
-      dalloc(&ix->path_count, 3);
-      PF_CK(cudaMemset(ix->path_count, 0, 3 * sizeof(unsigned long long)));
+      dalloc(&ix->path_count, 5);
+      PF_CK(cudaMemset(ix->path_count, 0, 5 * sizeof(unsigned long long)));
     } else if (!enable && ix->path_count) {
       if (ix->live_plans > 0) return fail(PF_ERR_INVALID_ARG, "search plans bound to the index exist");
       dfree(ix->path_count);

@@ -10,9 +10,9 @@ namespace {
 using skern::Dev;
 using skern::cand_buf;
 
-// q | runs | ranges | qsk | cpre | top-k | warp lists | warp candidate buffers
+// q | runs | ranges | qsk | cpre | ppre | top-k | warp lists | warp candidate buffers
 size_t search_smem(int d_pad, int L, int M, int k_max, int U, int QW) {
-  return size_t(d_pad) * 4 + size_t(L) * 24 + size_t(M) * 8 + size_t(L + 1) * 4 + size_t(k_max) * 8 * (1 + QW) +
+  return size_t(d_pad) * 4 + size_t(L) * 24 + size_t(M) * 8 + size_t(L + 1) * 8 + size_t(k_max) * 8 * (1 + QW) +
          size_t(cand_buf(U)) * 4 * QW;
 }
 

@@ -51,6 +51,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // U = positions per lane per streaming step (a template parameter: 4 or 8,
 // chosen by the tuner); a chunk is 32*U positions of one run
 constexpr int kFlushAt = 256;   // a warp scores its buffer once it holds more than this
+constexpr int kFlatFill = 3;    // a round streams flat when its chunks are less than 1/kFlatFill full
 __host__ __device__ constexpr int cand_buf(int U) { return kFlushAt + 32 * U; }  // compacted ids per warp
 constexpr int kGroup = 32;      // repetitions per threshold snapshot in a first round (after 1, 2, 4, 8, 16)
 
@@ -92,7 +93,8 @@ struct Dev {
   int32_t* counter;
   // diagnostics, or null: [0] range steps served by the prefix table (depth
   // <= 13), [1] sides settled within the first probed boundaries, [2] sides
-  // that galloped past them
+  // that galloped past them, [3] rounds streamed in chunks of one run, [4]
+  // rounds streamed flat
   unsigned long long* path_count;
   int stop_every;  // 0: stop test per round; G: also after every G repetitions (Alg. 1)
   int pool_fns;    // pooled index: functions in the pool (0: independent functions)
@@ -469,7 +471,8 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
   uint2* range = reinterpret_cast<uint2*>(runs + L);  // [L] current [l, r)
   uint64_t* qsk = reinterpret_cast<uint64_t*>(range + L);
   uint32_t* cpre = reinterpret_cast<uint32_t*>(qsk + M);  // [L + 1] chunk prefix
-  float* gs = reinterpret_cast<float*>(cpre + L + 1);
+  uint32_t* ppre = cpre + L + 1;                           // [L + 1] position prefix
+  float* gs = reinterpret_cast<float*>(ppre + L + 1);
   uint32_t* gid = reinterpret_cast<uint32_t*>(gs + kmax);
   float* ws = reinterpret_cast<float*>(gid + kmax);              // [kQW][kmax]
   uint32_t* wid = reinterpret_cast<uint32_t*>(ws + kQW * kmax);  // [kQW][kmax]
@@ -477,7 +480,7 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
   float* my_s = ws + warp * kmax;
   uint32_t* my_id = wid + warp * kmax;
   __shared__ int s_qi, s_size, s_stop, s_wsize[kQW];
-  __shared__ uint32_t s_scan[kQW];
+  __shared__ uint32_t s_scan[kQW], s_pscan[kQW];
   __shared__ float s_cosf[65];
   __shared__ float s_alpha[kAlphaSteps];
   __shared__ uint32_t s_ct[kQW][4];
@@ -573,7 +576,7 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
       // ---- range pass: thread t extends repetitions [t*per, (t+1)*per)
       const uint32_t mask = 0xffffffffu << (32 - depth);
       const bool single = prev == depth + 1;
-      uint32_t my_chunks = 0;
+      uint32_t my_chunks = 0, my_pos = 0;
       const int jlo = min(L, tid * per), jhi = min(L, jlo + per);
       for (int j = jlo; j < jhi; ++j) {
         const uint32_t qcj = qc[j];
@@ -676,25 +679,46 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
         range[j] = make_uint2(nl, nr);
         runs[j] = make_uint4(nl, l - nl, r, nr - r);
         my_chunks += (l - nl + kSpan - 1) / kSpan + (nr - r + kSpan - 1) / kSpan;
+        my_pos += (l - nl) + (nr - r);
       }
-      // exclusive scan of the chunk counts over the repetitions -> cpre
-      uint32_t inc = my_chunks;
+      // exclusive scans over the repetitions of the chunk counts -> cpre and
+      // of the new positions -> ppre
+      uint32_t inc = my_chunks, pinc = my_pos;
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
         const uint32_t v = __shfl_up_sync(kFull, inc, off);
-        if (lane >= off) inc += v;
+        const uint32_t pv = __shfl_up_sync(kFull, pinc, off);
+        if (lane >= off) {
+          inc += v;
+          pinc += pv;
+        }
       }
-      if (lane == 31) s_scan[warp] = inc;
+      if (lane == 31) {
+        s_scan[warp] = inc;
+        s_pscan[warp] = pinc;
+      }
       __syncthreads();
-      uint32_t run = inc - my_chunks;
-      for (int w = 0; w < warp; ++w) run += s_scan[w];
+      uint32_t run = inc - my_chunks, prun = pinc - my_pos;
+      for (int w = 0; w < warp; ++w) {
+        run += s_scan[w];
+        prun += s_pscan[w];
+      }
       for (int j = jlo; j < jhi; ++j) {
         cpre[j] = run;
+        ppre[j] = prun;
         const uint4 ru = runs[j];
         run += (ru.y + kSpan - 1) / kSpan + (ru.w + kSpan - 1) / kSpan;
+        prun += ru.y + ru.w;
       }
-      if (tid == kThreads - 1) cpre[L] = run;
+      if (tid == kThreads - 1) {
+        cpre[L] = run;
+        ppre[L] = prun;
+      }
       __syncthreads();
+      // short runs leave most of a chunk's lanes idle: the round then streams
+      // its positions as one flat sequence instead (the same candidates)
+      const bool flat = uint64_t(cpre[L]) * kSpan > uint64_t(kFlatFill) * ppre[L];
+      if (P.path_count && tid == 0) atomicAdd(P.path_count + (flat ? 4 : 3), 1ull);  // diagnostics only
 
       // ---- stream the chunks, group by group
       // groups of repetitions: in a first round (threshold snapshots), and in
@@ -711,10 +735,67 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
         const int gsize = s_size;
         const float gkth = gsize == k ? gs[k - 1] : -INFINITY;
         const int tau = gsize == k ? filter_tau(s_cosf, gkth) : 64;
-        const uint32_t c_end = cpre[j1];
+        const uint32_t c_end = flat ? cpre[j0] : cpre[j1];  // the chunk loop is skipped in a flat round
         int jc = j0;
         uint64_t qh = qsk[j0 % M];  // the query's sketch for repetition jc
         int nb = 0;
+        // flat round: warp w takes the spans of kSpan consecutive positions w,
+        // w + kQW, ... of the group's runs laid end to end (repetition by
+        // repetition, left run before right run); a lane finds the repetition
+        // of its first position by binary search over ppre, then walks on
+        const uint32_t p_end = ppre[j1];
+        for (uint32_t b = flat ? ppre[j0] + uint32_t(warp) * kSpan : p_end; b < p_end; b += kQW * kSpan) {
+          int jl = j0, jh = j1;  // ppre[jl] <= b + lane < ppre[jh]
+          const uint32_t p0 = min(b + uint32_t(lane), p_end - 1u);
+          while (jh - jl > 1) {
+            const int mid = (jl + jh) >> 1;
+            if (ppre[mid] <= p0) jl = mid; else jh = mid;
+          }
+          int jr = jl;
+          uint32_t id[kUnroll];
+          bool pass[kUnroll];
+          size_t at[kUnroll];
+          int jof[kUnroll];
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            const uint32_t pos = b + 32u * u + uint32_t(lane);
+            const bool valid = pos < p_end;
+            if (valid)
+              while (ppre[jr + 1] <= pos) ++jr;
+            const uint4 ru = runs[jr];
+            const uint32_t o = pos - ppre[jr];
+            const uint32_t ap = o < ru.y ? ru.x + o : ru.z + (o - ru.y);
+            at[u] = size_t(jr) * n + ap;
+            jof[u] = jr;
+            id[u] = valid ? __ldg(P.ids + at[u]) : 0u;
+            pass[u] = valid;
+          }
+          if (P.filter) {
+            uint64_t hd[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+              const uint64_t sk = !pass[u] ? 0ull
+                                  : P.skc ? __ldg(P.skc + at[u])
+                                          : __ldg(P.sk + size_t(jof[u] % M) * n + id[u]);
+              hd[u] = sk ^ qsk[jof[u] % M];
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) pass[u] = pass[u] && __popcll(hd[u]) <= tau;
+          }
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            const unsigned pm = __ballot_sync(kFull, pass[u]);
+            if (pass[u]) cbuf[nb + __popc(pm & lt_mask)] = id[u];
+            nb += __popc(pm);
+          }
+          if (lane == 0) ct.retrieved += min(kSpan, p_end - b);
+          __syncwarp();
+          if (nb > kFlushAt) {
+            if (lane == 0) ct.passed += uint32_t(nb);  // every buffered candidate passed the filter
+            wsize = flush_candidates<NT, NT2>(P, q, cbuf, nb, my_s, my_id, wsize, k, gkth, lane, ct);
+            nb = 0;
+          }
+        }
         // warp w takes chunks w, w + 4, ...: up to kSpan positions of one run,
         // lane-strided so that every load instruction is coalesced
         for (uint32_t c = cpre[j0] + uint32_t(warp); c < c_end; c += kQW) {

@@ -65,6 +65,7 @@ def test_search_equals_oracle_at_full_n(both, scoring, filt):
     # every branch of the range pass ran: prefix-table blocks, probed sides and
     # sides that galloped past the probed boundaries
     assert paths["prefix_table"] > 0 and paths["probed"] > 0 and paths["galloped"] > 0, paths
+    assert paths["chunked_rounds"] > 0 and paths["flat_rounds"] > 0, paths  # both streaming modes ran
     assert np.all(ref["stats"]["stop_depth"] > 0)
 
 
