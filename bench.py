@@ -444,7 +444,7 @@ def run_extra(args):
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
     ix.tune(Qd[: min(Qn, 20_000)], 10 if name == "vmf4k-n2m-d128-mixed" else int(w["k"]),
-            0.9 if args.recall is None else args.recall, scoring=sc, learned=args.mode == "learned")
+            0.9 if args.recall is None else args.recall, scoring=sc, learned=learned)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
