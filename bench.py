@@ -90,6 +90,8 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other two modes")
     ap.add_argument("--recall", type=float, default=None,
                     help="recall target 1 - delta passed to the index (default: the workload's)")
+    ap.add_argument("--filter-eps", type=float, default=0.0,
+                    help="slack of the sketch threshold (Fig. 2 footnote; 0 as in Sec. 5.1)")
     ap.add_argument("--pool-bits", type=int, default=0,
                     help="0: independent hash functions; m: tables draw their functions from a pool of m bits "
                          "(Sec. 3.2; the paper uses 3072)")
@@ -190,7 +192,7 @@ def search_kernel_traffic(args=None):
                              or args.recall != 0.9 or getattr(args, "workload", WORKLOAD) != WORKLOAD
                              or getattr(args, "family", "crosspolytope") != "crosspolytope"
                              or getattr(args, "estimate", "bf16") != "bf16" or getattr(args, "stop_every", 0)
-                             or getattr(args, "pool_bits", 0)):
+                             or getattr(args, "pool_bits", 0) or getattr(args, "filter_eps", 0.0)):
         return None
     path = os.path.join(ROOT, "profiles", "search_kernel_traffic.txt")
     src = os.path.join(ROOT, "paper_1906_12211_gb300", "csrc", "search_kernel.cuh")
@@ -453,7 +455,8 @@ def run_extra(args):
         sims = torch.empty((Qn, k_max), dtype=torch.float32, device=dev)
         st = torch.empty((Qn, pf.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
         if name == "vmf4k-n2m-d128-mixed":  # the whole batch as one captured, tuned launch
-            plan = ix.plan(Qd, kd, rd, ids, sims, k_max=k_max, stats=st, scoring=sc, filter=filt, learned=learned)
+            plan = ix.plan(Qd, kd, rd, ids, sims, k_max=k_max, stats=st, scoring=sc, filter=filt, learned=learned,
+                           filter_eps=args.filter_eps)
             run = lambda: plan.run(stream)  # noqa: E731
         else:
             plan = None
@@ -461,7 +464,7 @@ def run_extra(args):
 
             def run():
                 ix.search(Qd, kd, rd, k_max=k_max, scoring=sc, filter=filt, out_ids=ids, out_sims=sims, stats=st,
-                          learned=learned, timing=True)
+                          learned=learned, timing=True, filter_eps=args.filter_eps)
                 kern[0] += ix.last_timing()[1]
         try:
             for _ in range(max(2, args.warmup)):
@@ -511,11 +514,13 @@ def run_extra(args):
     hi = torch.empty((Qn, k_max), dtype=torch.int32).pin_memory()
     hs = torch.empty((Qn, k_max), dtype=torch.float32).pin_memory()
     for _ in range(2):
-        ix.search(hq, hk, hr, k_max=k_max, scoring=sc, out_ids=hi, out_sims=hs, learned=learned)
+        ix.search(hq, hk, hr, k_max=k_max, scoring=sc, out_ids=hi, out_sims=hs, learned=learned,
+                  filter_eps=args.filter_eps)
     torch.cuda.synchronize()
     t = time.perf_counter()
     for _ in range(args.steps):
-        ix.search(hq, hk, hr, k_max=k_max, scoring=sc, out_ids=hi, out_sims=hs, learned=learned)
+        ix.search(hq, hk, hr, k_max=k_max, scoring=sc, out_ids=hi, out_sims=hs, learned=learned,
+                  filter_eps=args.filter_eps)
     torch.cuda.synchronize()
     el = time.perf_counter() - t
     assert torch.equal(hi, ids.cpu()) and torch.equal(hs, sims.cpu())
@@ -535,7 +540,7 @@ def run_extra(args):
         "config": {"workload": name, "n": int(n), "d": int(w["d"]), "queries": int(Qn), "k_max": k_max,
                    "budget_bytes": w["budget"], "L": ix.L, "rows": w.get("rows", "f32"), "family": args.family,
                    "scoring": sc, "start_depth": "learned" if learned else "plain",
-                   "l2": "flushed between steps (512 MiB write)", "filter": "on"},
+                   "l2": "flushed between steps (512 MiB write)", "filter": "on", "filter_eps": args.filter_eps},
         "recall": head["recall"], "per_query": head["per_query"],
         **({"planted_found": head["planted_found"]} if "planted_found" in head else {}),
         **({"per_class": head["per_class"]} if "per_class" in head else {}),
@@ -643,7 +648,7 @@ def main():
         tune_report = ix.tune(torch.from_numpy(Qtune).to(dev), k, args.recall,
                               scoring="fp32" if args.mode == "fp32" else args.estimate,
                               learned=args.mode == "learned",
-                              stop_every=args.stop_every, pool_rule=args.pool_rule)
+                              stop_every=args.stop_every, pool_rule=args.pool_rule, filter_eps=args.filter_eps)
 
     def opts_of(mode):
         return ("fp32" if mode == "fp32" else args.estimate), mode == "learned"
@@ -662,7 +667,8 @@ def main():
 
         def run(timing=False):
             ix.search(Qd[0], kq[0], rq[0], k_max=k, scoring=sc, out_ids=o1[0], out_sims=o1[1], stats=o1[2],
-                      timing=timing, learned=lr, stop_every=args.stop_every, pool_rule=args.pool_rule)
+                      timing=timing, learned=lr, stop_every=args.stop_every, pool_rule=args.pool_rule,
+                      filter_eps=args.filter_eps)
 
         kern = {"kernel_ms": 0.0, "hash_ms": 0.0}
 
@@ -689,9 +695,9 @@ def main():
         sims = [o1[1]]
         if not args.no_graph:
             pa = ix.plan(Qd[0], kq[0], rq[0], *outputs()[:2], k_max=k, scoring=sc, learned=lr,
-                         stop_every=args.stop_every, pool_rule=args.pool_rule)
+                         stop_every=args.stop_every, pool_rule=args.pool_rule, filter_eps=args.filter_eps)
             pb = ix.plan(Qd[1], kq[1], rq[1], o2[0], o2[1], k_max=k, stats=o2[2], scoring=sc, learned=lr,
-                         stop_every=args.stop_every, pool_rule=args.pool_rule)
+                         stop_every=args.stop_every, pool_rule=args.pool_rule, filter_eps=args.filter_eps)
             plans = [pa, pb]
             try:
                 for _ in range(max(3, args.warmup)):
@@ -768,7 +774,8 @@ def main():
 
         # one batch at a time: pf_index_search given the host pointers
         el = wall(lambda i: ix.search(hq[0], hk[0], hr[0], k_max=k, scoring=sc, out_ids=hi[0], out_sims=hs[0],
-                                      learned=lr, stop_every=args.stop_every, pool_rule=args.pool_rule), args.steps)
+                                      learned=lr, stop_every=args.stop_every, pool_rule=args.pool_rule,
+                                      filter_eps=args.filter_eps), args.steps)
         assert torch.equal(hi[0], ids1.cpu()) and torch.equal(hs[0], sims1.cpu())
         seq_e2e = {"value": whole_job_rate(Q, world, args.steps, el), "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "how": "pf_index_search with page-locked host pointers, one batch "
@@ -778,7 +785,8 @@ def main():
             # two batches in flight: plans bound to the host buffers (each graph
             # copies its inputs in and its outputs out on its own stream)
             plans = [ix.plan(hq[b], hk[b], hr[b], hi[b], hs[b], k_max=k, scoring=sc, learned=lr,
-                             stop_every=args.stop_every, pool_rule=args.pool_rule) for b in range(2)]
+                             stop_every=args.stop_every, pool_rule=args.pool_rule, filter_eps=args.filter_eps)
+                     for b in range(2)]
             try:
                 el = wall(lambda i: plans[i % 2].run(streams[i % 2]), args.steps)
                 for p_, s_ in zip(plans, streams):
@@ -838,6 +846,7 @@ def main():
                                      else "after every round"),
                        "hash_functions": (f"pooled: {args.pool_bits} bits, stop rule {args.pool_rule}"
                                           if args.pool_bits else "independent"),
+                       "filter_eps": args.filter_eps,
                        "l2": l2, "pipelining": pipelining, "parallelism": f"replica x{world}"},
             "recall": recall, "recall_per_batch": head["recall"], "build_s": build_s,
             "per_query": head["per_query"],

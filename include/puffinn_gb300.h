@@ -110,6 +110,9 @@ typedef struct {
   int32_t pool_rule;           /* pooled index: 0 = stop when Cantelli's bound on missing the k-th point is <= delta
                                   (the guarantee carried to general delta); 1 = Lemma 1's test as if the pooled
                                   functions were independent (no guarantee).  Ignored otherwise */
+  double filter_eps;           /* slack of the sketch threshold (Fig. 2 footnote): a candidate passes when its
+                                  Hamming distance is <= (1 + eps) 64 arccos(s_k)/pi; 0 (Sec. 5.1's choice) by
+                                  default; larger values trade speed for recall */
   int32_t stop_every;          /* 0: the stop test after each round (Sec. 4.1).  G >= 1: also after every G
                                   repetitions (Alg. 1 tests after each one: G = 1): after j repetitions of the round
                                   at prefix length i the test is (1 - p_i)^j (1 - p_{i+1})^(L - j) <= delta (no second
@@ -222,7 +225,7 @@ pf_status pf_index_search(pf_index* index, const float* queries, int64_t Q, cons
  *   - Scratch (normalised queries, query codes and sketches, work counter)
  *     lives in one 32 MiB file-scope device array that every GPU loading the
  *     library holds until the process exits.  A batch must satisfy
- *     Q*(8*d_pad + 4*L + 8*M) + 1536 <= 32 MiB; larger batches are rejected with
+ *     Q*(8*d_pad + 4*L + 8*M) + 2048 <= 32 MiB; larger batches are rejected with
  *     PF_ERR_INVALID_ARG and a message giving the limit (split the batch).
  *   - No cudaMalloc, cudaFree or other allocating call is made.
  *   - All calls share the array: calls whose device work overlaps (other

@@ -50,7 +50,8 @@ class _Index(C.Structure):
     _fields_ = [("family", C.c_int), ("d", C.c_int), ("ell", C.c_int), ("Kb", C.c_int),
                 ("L", C.c_int), ("M", C.c_int), ("B", C.c_int), ("n", C.c_int64),
                 ("x", C.c_void_p), ("codes", C.c_void_p), ("ids", C.c_void_p),
-                ("sk", C.c_void_p), ("P", C.c_void_p), ("pool_fns", C.c_int), ("pool_as_independent", C.c_int)]
+                ("sk", C.c_void_p), ("P", C.c_void_p), ("pool_fns", C.c_int), ("pool_as_independent", C.c_int),
+                ("filter_eps", C.c_double)]
 
 
 STATS_DTYPE = np.dtype([("start_depth", np.int32), ("stop_depth", np.int32), ("rounds", np.int32),
@@ -84,6 +85,7 @@ def lib():
                 "orc_collision_prob": (f64, [C.c_int, C.c_int, vp, f64, C.c_int]),
                 "orc_ipow": (f64, [f64, i64]),
                 "orc_filter_tau": (C.c_int, [f64]),
+                "orc_filter_tau_eps": (C.c_int, [f64, f64]),
                 "orc_budget_L": (i64, [C.c_int, i64, C.c_int, C.c_int, u64, C.c_int, C.c_int, C.c_int, C.c_int]),
                 "orc_sim": (C.c_float, [vp, vp, C.c_int]),
                 "orc_search": (None, [vp, vp, vp, vp, i64, vp, vp, i32, vp, C.c_int, C.c_int, vp, vp, vp, vp, i64, vp]),
@@ -229,8 +231,8 @@ def ipow(x: float, e: int) -> float:
     return float(lib().orc_ipow(x, e))
 
 
-def filter_tau(s_k: float) -> int:
-    return int(lib().orc_filter_tau(s_k))
+def filter_tau(s_k: float, eps: float = 0.0) -> int:
+    return int(lib().orc_filter_tau_eps(s_k, eps))
 
 
 def budget_L(family: int, n: int, d: int, M: int, budget_bytes: int, sketch_layout: int = 0,
@@ -354,7 +356,7 @@ class OracleIndex:
 
     def search(self, queries, k, recall, *, k_max: int | None = None, start_depth=None,
                filter: bool = True, trace_cap: int = 0, variant=None, stop_every: int = 0,
-               pool_rule: str = "cantelli"):
+               pool_rule: str = "cantelli", filter_eps: float = 0.0):
         qn, qcodes, qsk = self.hash_queries(queries)
         Q = qn.shape[0]
         k = np.broadcast_to(np.asarray(k, np.int32), (Q,)).copy()
@@ -369,7 +371,7 @@ class OracleIndex:
         ix = _Index(fam, self.d, self.ell, self.Kb, self.L, self.M, self.B, self.n,
                     self.x.ctypes.data, self.codes.ctypes.data, self.ids.ctypes.data,
                     self.sk.ctypes.data, self.P.ctypes.data if self.P is not None else None, self.pool_fns,
-                    1 if pool_rule == "independent" else 0)
+                    1 if pool_rule == "independent" else 0, float(filter_eps))
         trace = np.zeros((Q, trace_cap, 2), np.uint32) if trace_cap else None
         tlen = np.zeros(Q, np.int64) if trace_cap else None
         (variant or lib()).orc_search(C.byref(ix), _p(qn), _p(qcodes), _p(qsk), Q, _p(k), _p(recall), k_max,

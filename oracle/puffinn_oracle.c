@@ -515,10 +515,14 @@ int orc_pool_stop(int family, int ell, const double* P, int m, double s_k, int d
  * (Sec. 5.1); a candidate passes if its Hamming distance is at most that.
  * Since the distance is an integer this is floor(64 arccos(s_k)/pi), computed
  * without arccos as the largest t with cos(t pi / 64) >= s_k. */
-int orc_filter_tau(double s_k) {
+int orc_filter_tau(double s_k) { return orc_filter_tau_eps(s_k, 0.0); }
+
+/* With the footnote's slack eps >= 0: the largest t with
+ * t <= (1 + eps) 64 arccos(s_k)/pi, i.e. cos(t pi / (64 (1 + eps))) >= s_k. */
+int orc_filter_tau_eps(double s_k, double eps) {
   int tau = 0;
   for (int t = 0; t <= 64; ++t)
-    if (cos((double)t * M_PI / 64.0) >= s_k) tau = t;
+    if (cos((double)t * M_PI / (64.0 * (1.0 + eps))) >= s_k) tau = t;
   return tau;
 }
 
@@ -682,7 +686,7 @@ static void search_one(const orc_index* ix, const float* q, const uint32_t* qcod
       if (j == 0 || (stop_every > 0 ? j % stop_every == 0
                                     : (s.rounds == 0 && first_round_snapshot(j)))) { /* threshold snapshot */
         const int full = (size == k);
-        tau = full ? orc_filter_tau((double)ps[k - 1]) : 64;
+        tau = full ? orc_filter_tau_eps((double)ps[k - 1], ix->filter_eps) : 64;
       }
       const uint32_t* cj = ix->codes + (int64_t)j * n;
       const uint32_t* idj = ix->ids + (int64_t)j * n;

@@ -95,6 +95,7 @@ double orc_ipow(double x, int64_t e);
 
 /* ---- sketch filter threshold (Sec. 4.2 "Filtering", Fig. 2 footnote) ---- */
 int orc_filter_tau(double s_k);
+int orc_filter_tau_eps(double s_k, double eps); /* threshold with slack eps (Fig. 2) */
 
 /* ---- memory budget -> number of repetitions (Sec. 5, index size) ----
  * sketch_layout 0: one sketch copy per repetition entry; 1: M per point.
@@ -126,6 +127,7 @@ typedef struct {
   const double* P;         /* CP table [41][ell+1] or NULL for HP */
   int pool_fns;            /* 0: independent functions; m > 0: each table draws its functions from a pool of m */
   int pool_as_independent; /* pooled index, 1: stop by Lemma 1's rule as if the functions were independent */
+  double filter_eps;       /* slack of the sketch threshold (Fig. 2 footnote; Sec. 5.1 uses 0) */
 } orc_index;
 
 /* Search Q normalised queries.  qcodes[Q][L], qsk[Q][M], k[Q], recall[Q].

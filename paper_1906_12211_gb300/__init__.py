@@ -47,7 +47,7 @@ class BuildParams(C.Structure):
 class SearchOpts(C.Structure):
     _fields_ = [("scoring", C.c_int32), ("filter", C.c_int32), ("learned_start", C.c_int32),
                 ("timing", C.c_int32), ("start_depth", C.c_void_p), ("pool_rule", C.c_int32),
-                ("stop_every", C.c_int32)]
+                ("filter_eps", C.c_double), ("stop_every", C.c_int32)]
 
 
 class QueryStats(C.Structure):
@@ -264,7 +264,7 @@ class Index:
 
     def search(self, queries, k, recall, *, k_max: int | None = None, scoring: str = "fp32", filter: bool = True,
                start_depth=None, out_ids=None, out_sims=None, stats=None, stream=None, timing: bool = False,
-               learned: bool = False, stop_every: int = 0, pool_rule: str = "cantelli"):
+               learned: bool = False, stop_every: int = 0, pool_rule: str = "cantelli", filter_eps: float = 0.0):
         """Answer a batch of queries; k and recall are per-query arrays (same
         device as the queries) or scalars.  Returns (ids, sims, stats)."""
         import torch
@@ -293,6 +293,7 @@ class Index:
         o.learned_start = 1 if learned else 0
         o.stop_every = int(stop_every)
         o.pool_rule = POOL_RULES[pool_rule]
+        o.filter_eps = float(filter_eps)
         sd = None
         if start_depth is not None:
             sd = start_depth if torch.is_tensor(start_depth) else torch.full((Q,), int(start_depth),
@@ -304,16 +305,16 @@ class Index:
 
 
     def search_noalloc(self, queries, k, recall, out_ids, out_sims, *, k_max: int, scoring: str = "fp32",
-                       filter: bool = True, stats=None, stream=None, stop_every: int = 0):
+                       filter: bool = True, stats=None, stream=None, stop_every: int = 0, filter_eps: float = 0.0):
         """pf_index_search_noalloc: every buffer already on the device, no
         allocation inside the call (fixed 32 MiB scratch)."""
-        o = self._opts(scoring, filter, False, stop_every)
+        o = self._opts(scoring, filter, False, stop_every, filter_eps=filter_eps)
         _check(lib().pf_index_search_noalloc(self._h, _ptr(queries), int(queries.shape[0]), _ptr(k), _ptr(recall),
                                              int(k_max), _ptr(out_ids), _ptr(out_sims), _ptr(stats), C.byref(o),
                                              _stream_ptr(stream)))
         return out_ids, out_sims, stats
 
-    def _opts(self, scoring, filter, learned, stop_every=0, pool_rule="cantelli"):
+    def _opts(self, scoring, filter, learned, stop_every=0, pool_rule="cantelli", filter_eps=0.0):
         o = SearchOpts()
         lib().pf_search_opts_default(C.byref(o))
         o.scoring = SCORING[scoring]
@@ -321,13 +322,15 @@ class Index:
         o.learned_start = 1 if learned else 0
         o.stop_every = int(stop_every)
         o.pool_rule = POOL_RULES[pool_rule]
+        o.filter_eps = float(filter_eps)
         return o
 
     def tune(self, queries, k: int, recall: float, *, scoring: str = "fp32", filter: bool = True,
-             learned: bool = False, stream=None, stop_every: int = 0, pool_rule: str = "cantelli"):
+             learned: bool = False, stream=None, stop_every: int = 0, pool_rule: str = "cantelli",
+             filter_eps: float = 0.0):
         """pf_index_tune: time the search launch shapes on this batch and keep the fastest."""
         rep = TuneReport()
-        o = self._opts(scoring, filter, learned, stop_every, pool_rule)
+        o = self._opts(scoring, filter, learned, stop_every, pool_rule, filter_eps)
         _check(lib().pf_index_tune(self._h, _ptr(queries), int(queries.shape[0]), int(k), float(recall),
                                    C.byref(o), C.byref(rep), _stream_ptr(stream)))
         return {f: getattr(rep, f) for f, _ in TuneReport._fields_}
@@ -356,12 +359,12 @@ class Index:
 
     def plan(self, queries, k, recall, out_ids, out_sims, *, k_max: int, stats=None, start_depth=None,
              scoring: str = "fp32", filter: bool = True, learned: bool = False, stop_every: int = 0,
-             pool_rule: str = "cantelli"):
+             pool_rule: str = "cantelli", filter_eps: float = 0.0):
         """pf_search_plan_create: a CUDA graph of this search bound to these device tensors (or
         page-locked host tensors)."""
         return SearchPlan(self, queries, k, recall, out_ids, out_sims, k_max=k_max, stats=stats,
                           start_depth=start_depth, opts=self._opts(scoring, filter, learned, stop_every,
-                                                                   pool_rule))
+                                                                   pool_rule, filter_eps))
 
     def last_timing(self):
         """(hash_ms, search_kernel_ms, total_ms) of the last search run with timing=True."""

@@ -105,6 +105,7 @@ void free_ws(pf_workspace& ws) {
   dfree(ws.sims);
   dfree(ws.stats);
   dfree(ws.counter);
+  dfree(ws.cos_eps);
   dfree(ws.rq);
   dfree(ws.rq_count);
   ws.cap_q = 0;
@@ -129,6 +130,7 @@ void alloc_ws(pf_index* ix, pf_workspace& ws, size_t q, size_t km) {
   dalloc(&ws.sims, q * km);
   dalloc(&ws.stats, q);
   dalloc(&ws.counter, 64);
+  dalloc(&ws.cos_eps, 65);
   dalloc(&ws.rq, recheck_capacity(int64_t(q)));
   dalloc(&ws.rq_count, size_t(ix->num_sms));
   ws.cap_q = q;
@@ -180,6 +182,20 @@ void destroy(pf_index* ix) {
 void stage_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
   if (bytes == 0) return;
   PF_CK(cudaMemcpyAsync(dst, src, bytes, on_device(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+}
+
+// The threshold table of a nonzero filter slack, copied into the workspace on
+// `s` (null for eps = 0: the index's own table).  capture: the copy must not be
+// recorded into a graph, so it is made synchronously.
+const double* slack_table(pf_workspace& ws, double eps, cudaStream_t s, bool capture = false) {
+  if (eps == 0.0) return nullptr;
+  double tab[65];
+  filter_cos_table(tab, eps);
+  if (capture)
+    PF_CK(cudaMemcpy(ws.cos_eps, tab, sizeof(tab), cudaMemcpyHostToDevice));
+  else
+    PF_CK(cudaMemcpyAsync(ws.cos_eps, tab, sizeof(tab), cudaMemcpyHostToDevice, s));  // pageable: staged on return
+  return ws.cos_eps;
 }
 
 // Hash and normalise Q queries (device pointer qsrc) into the workspace.
@@ -492,6 +508,7 @@ pf_status pf_index_search(pf_index* ix, const float* queries, int64_t Q, const i
     if (o.scoring == 2 && !ix->x8) return fail(PF_ERR_INVALID_ARG, "scoring 2 needs an index built with fp8_rows");
     if (o.stop_every < 0) return fail(PF_ERR_INVALID_ARG, "stop_every must be >= 0");
     if (o.pool_rule != 0 && o.pool_rule != 1) return fail(PF_ERR_INVALID_ARG, "pool_rule must be 0 or 1");
+    if (!(o.filter_eps >= 0.0 && o.filter_eps <= 1e6)) return fail(PF_ERR_INVALID_ARG, "filter_eps must be in [0, 1e6]");
     if (o.learned_start && !ix->mlp_trained) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
     if (Q == 0) return PF_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -534,6 +551,7 @@ pf_status pf_index_search(pf_index* ix, const float* queries, int64_t Q, const i
     a.scoring = o.scoring;
     a.stop_every = o.stop_every;
     a.pool_rule = o.pool_rule;
+    a.cos_tab = slack_table(ws, o.filter_eps, s);
     a.out_ids = ids_dev ? out_ids : ws.ids;
     a.out_sims = sims_dev ? out_sims : ws.sims;
     a.stats = stats ? (st_dev ? stats : ws.stats) : nullptr;
@@ -977,6 +995,7 @@ pf_status pf_index_tune(pf_index* ix, const float* queries, int64_t Q, int32_t k
     if (o.scoring == 2 && !ix->x8) return fail(PF_ERR_INVALID_ARG, "scoring 2 needs an index built with fp8_rows");
     if (o.stop_every < 0) return fail(PF_ERR_INVALID_ARG, "stop_every must be >= 0");
     if (o.pool_rule != 0 && o.pool_rule != 1) return fail(PF_ERR_INVALID_ARG, "pool_rule must be 0 or 1");
+    if (!(o.filter_eps >= 0.0 && o.filter_eps <= 1e6)) return fail(PF_ERR_INVALID_ARG, "filter_eps must be in [0, 1e6]");
     if (o.learned_start && !ix->mlp_trained) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PF_CK(cudaSetDevice(ix->device));
@@ -1013,6 +1032,7 @@ pf_status pf_index_tune(pf_index* ix, const float* queries, int64_t Q, int32_t k
     a.scoring = o.scoring;
     a.stop_every = o.stop_every;
     a.pool_rule = o.pool_rule;
+    a.cos_tab = slack_table(ws, o.filter_eps, s);
     a.out_ids = ws.ids;
     a.out_sims = ws.sims;
     a.stats = nullptr;
@@ -1171,6 +1191,7 @@ void plan_sequence(pf_search_plan* pl, cudaStream_t s) {
   a.scoring = pl->opts.scoring;
   a.stop_every = pl->opts.stop_every;
   a.pool_rule = pl->opts.pool_rule;
+  a.cos_tab = pl->opts.filter_eps != 0.0 ? ws.cos_eps : nullptr;  // filled before the capture
   a.out_ids = io.out_ids;
   a.out_sims = io.out_sims;
   a.stats = io.stats;
@@ -1219,6 +1240,7 @@ pf_status pf_search_plan_create(pf_index* ix, int64_t Q, int32_t k_max, const pf
     if (o.scoring == 2 && !ix->x8) return fail(PF_ERR_INVALID_ARG, "scoring 2 needs an index built with fp8_rows");
     if (o.stop_every < 0) return fail(PF_ERR_INVALID_ARG, "stop_every must be >= 0");
     if (o.pool_rule != 0 && o.pool_rule != 1) return fail(PF_ERR_INVALID_ARG, "pool_rule must be 0 or 1");
+    if (!(o.filter_eps >= 0.0 && o.filter_eps <= 1e6)) return fail(PF_ERR_INVALID_ARG, "filter_eps must be in [0, 1e6]");
     if (o.learned_start && !ix->mlp_trained) return fail(PF_ERR_NOT_TRAINED, "no start-depth model has been trained");
     o.start_depth = nullptr;
     o.timing = 0;
@@ -1237,6 +1259,7 @@ pf_status pf_search_plan_create(pf_index* ix, int64_t Q, int32_t k_max, const pf
           set_io_field(pl->dio, f, pl->stage[f]);
         }
       alloc_ws(ix, pl->ws, size_t(Q), size_t(k_max));
+      slack_table(pl->ws, o.filter_eps, nullptr, true);
       PF_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
       PF_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
       try {

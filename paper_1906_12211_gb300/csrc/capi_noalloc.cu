@@ -35,7 +35,8 @@ size_t round_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 size_t scratch_bytes(const pf_index* ix, int64_t Q) {
   return round_up(size_t(Q) * ix->lay.d_pad * sizeof(float)) + 2 * round_up(size_t(Q) * ix->lay.d_pad * 2) +
-         round_up(size_t(Q) * ix->L * sizeof(uint32_t)) + round_up(size_t(Q) * ix->M * sizeof(uint64_t)) + kAlign;
+         round_up(size_t(Q) * ix->L * sizeof(uint32_t)) + round_up(size_t(Q) * ix->M * sizeof(uint64_t)) +
+         round_up(64 + 65 * sizeof(double));  // work counter, error word, threshold table
 }
 
 bool device_pointer(const void* p) {
@@ -89,6 +90,8 @@ extern "C" pf_status pf_index_search_noalloc(pf_index* ix, const float* queries,
     if (o.scoring == 2 && !ix->x8) return reject(PF_ERR_INVALID_ARG, "scoring 2 needs an index built with fp8_rows");
     if (o.stop_every < 0) return reject(PF_ERR_INVALID_ARG, "stop_every must be >= 0");
     if (o.pool_rule != 0 && o.pool_rule != 1) return reject(PF_ERR_INVALID_ARG, "pool_rule must be 0 or 1");
+    if (!(o.filter_eps >= 0.0 && o.filter_eps <= 1e6))
+      return reject(PF_ERR_INVALID_ARG, "filter_eps must be in [0, 1e6]");
     if (ix->pool_tables > 0)
       return reject(PF_ERR_INVALID_ARG, "a pooled index needs pf_index_search (its pool codes use the index workspace)");
     if (o.learned_start)
@@ -98,7 +101,7 @@ extern "C" pf_status pf_index_search_noalloc(pf_index* ix, const float* queries,
       const size_t per_q = size_t(ix->lay.d_pad) * 8 + size_t(ix->L) * 4 + size_t(ix->M) * 8;
       return reject(PF_ERR_INVALID_ARG,
                     "batch too large for the fixed 32 MiB search scratch: this index allows about " +
-                        std::to_string((kScratchBytes - 6 * kAlign) / per_q) + " queries per call, got " +
+                        std::to_string((kScratchBytes - 8 * kAlign) / per_q) + " queries per call, got " +
                         std::to_string(Q));
     }
     if (ix->device < 0 || ix->device >= kMaxDevices) return reject(PF_ERR_INVALID_ARG, "device ordinal too large");
@@ -124,9 +127,10 @@ extern "C" pf_status pf_index_search_noalloc(pf_index* ix, const float* queries,
     uint64_t* qsk = reinterpret_cast<uint64_t*>(base);
     base += round_up(size_t(Q) * ix->M * sizeof(uint64_t));
     int32_t* counter = reinterpret_cast<int32_t*>(base);  // [0] work queue head, [1] error word
+    double* cos_eps = reinterpret_cast<double*>(base + 64);  // [65] threshold table of a nonzero filter slack
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if ((e = cudaMemsetAsync(counter, 0, kAlign, s)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    if ((e = cudaMemsetAsync(counter, 0, 64, s)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     if ((e = pf::launch_normalize(queries, Q, ix->d, ix->lay.d_pad, qx, qxh, qxl, s)) != cudaSuccess)
       return cuda_fail(e, "normalize");
     // no deferred-recheck queue here: near-boundary hash decisions are rechecked inline
@@ -146,6 +150,13 @@ extern "C" pf_status pf_index_search_noalloc(pf_index* ix, const float* queries,
     a.scoring = o.scoring;
     a.stop_every = o.stop_every;
     a.pool_rule = o.pool_rule;
+    if (o.filter_eps != 0.0) {
+      double tab[65];
+      pf::filter_cos_table(tab, o.filter_eps);
+      if ((e = cudaMemcpyAsync(cos_eps, tab, sizeof(tab), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync");
+      a.cos_tab = cos_eps;
+    }
     a.out_ids = out_ids;
     a.out_sims = out_sims;
     a.stats = stats;

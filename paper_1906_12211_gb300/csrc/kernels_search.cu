@@ -47,7 +47,7 @@ cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t 
   P.sk = ix->sk;
   P.skc = ix->skc;
   P.cpP = ix->cpP;
-  P.cos_tab = ix->cos_tab;
+  P.cos_tab = a.cos_tab ? a.cos_tab : ix->cos_tab;
   P.bf16_err = ix->bf16_err;
   P.Q = a.Q;
   P.qx = a.qx;

@@ -368,10 +368,11 @@ void fht_bands(int d, const Layout& lay, float* gap, float* sign) {
   *sign = float(t);
 }
 
-// cos(t*pi/64), t = 0..64: the sketch threshold is the largest t whose entry
-// is >= s_k (= floor(64 arccos(s_k)/pi), Sec. 4.2).
-void filter_cos_table(double* c) {
-  for (int t = 0; t <= 64; ++t) c[t] = std::cos(double(t) * M_PI / 64.0);
+// cos(t*pi/(64 (1 + eps))), t = 0..64: the sketch threshold is the largest t
+// whose entry is >= s_k (= floor((1 + eps) 64 arccos(s_k)/pi), Sec. 4.2 and the
+// footnote of Fig. 2; eps = 0 in Sec. 5.1).
+void filter_cos_table(double* c, double eps) {
+  for (int t = 0; t <= 64; ++t) c[t] = std::cos(double(t) * M_PI / (64.0 * (1.0 + eps)));
 }
 
 // Device bytes the index keeps resident for L repetitions; the budget rule

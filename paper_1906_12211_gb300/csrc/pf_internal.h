@@ -59,7 +59,7 @@ float gaussian(uint64_t seed, uint32_t purpose, uint32_t a, uint32_t b, uint32_t
 // W[(L*rows_table + 64*M)][d_pad] float32 and per-row recheck band thr[]
 void gen_hash_rows(uint64_t seed, int family, int L, int M, int d, const Layout& lay, float* W, float* thr);
 void cp_collision_table(uint64_t seed, int d, int ell, int draws, double* P /*[41][ell+1]*/);
-void filter_cos_table(double* c /*[65]*/);
+void filter_cos_table(double* c /*[65]*/, double eps = 0.0);
 // pseudo-random cross-polytope family (Sec. 4.3): sign bits [L][fns][3][fht_words]
 void gen_fht_signs(uint64_t seed, int L, const Layout& lay, uint32_t* out);
 void fht_collision_table(uint64_t seed, const Layout& lay, int draws, double* P /*[41][ell+1]*/);
@@ -110,6 +110,7 @@ struct pf_workspace {
   float* sims = nullptr;
   pf_query_stats* stats = nullptr;
   int32_t* counter = nullptr;  // work queue head + error word
+  double* cos_eps = nullptr;   // [65] threshold table of the last nonzero filter slack
   pf::RecheckReq* rq = nullptr;  // deferred hash rechecks
   uint32_t* rq_count = nullptr;
   size_t cap_kmax = 0;
@@ -231,6 +232,7 @@ struct SearchArgs {
   int32_t* counter = nullptr;
   int stop_every = 0;  // pf_search_opts.stop_every
   int pool_rule = 0;   // pf_search_opts.pool_rule
+  const double* cos_tab = nullptr;  // threshold table of a nonzero filter slack (null: the index's)
 };
 cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t s);
 // CTAs per SM the search kernel can keep resident for this index (0 on error)

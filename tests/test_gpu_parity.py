@@ -372,3 +372,28 @@ def test_stop_every_with_start_depths_and_mixed_k(cpmid):
     out = cpmid.gpu.search(cpmid.qd, torch.from_numpy(k).to(DEV), torch.from_numpy(rec).to(DEV), k_max=128,
                            start_depth=torch.from_numpy(sd).to(DEV), stats=True, scoring="bf16", stop_every=3)
     _compare(out, ref)
+
+
+# ------------------------------------------------------------------ filter slack (Fig. 2 footnote)
+@pytest.mark.parametrize("case", ["cfg1", "cpmid", "cpmidpp"], indirect=True)
+@pytest.mark.parametrize("eps", [0.1, 0.3])
+def test_filter_slack_bit_exact(case, eps):
+    ref = case.orc.search(case.Q, 10, 0.9, filter_eps=eps)
+    out = case.gpu.search(case.qd, 10, 0.9, scoring="bf16", stats=True, filter_eps=eps)
+    _compare(out, ref)
+    # a captured plan and the no-allocation entry point take the same slack
+    Q = case.qd.shape[0]
+    ids = torch.empty((Q, 10), dtype=torch.int32, device=DEV)
+    sims = torch.empty((Q, 10), dtype=torch.float32, device=DEV)
+    k = torch.full((Q,), 10, dtype=torch.int32, device=DEV)
+    r = torch.full((Q,), 0.9, dtype=torch.float64, device=DEV)
+    plan = case.gpu.plan(case.qd, k, r, ids, sims, k_max=10, scoring="bf16", filter_eps=eps)
+    try:
+        plan.run()
+        plan.check()
+    finally:
+        plan.close()
+    assert np.array_equal(u32(ids), ref["ids"]) and np.array_equal(sims.cpu().numpy(), ref["sims"])
+    ids2, sims2 = torch.empty_like(ids), torch.empty_like(sims)
+    case.gpu.search_noalloc(case.qd, k, r, ids2, sims2, k_max=10, scoring="bf16", filter_eps=eps)
+    assert torch.equal(ids2, ids) and torch.equal(sims2, sims)

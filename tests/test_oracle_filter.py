@@ -157,7 +157,7 @@ _MUTANTS = {
     "first_round_groups_of_32": ("(s.rounds == 0 && first_round_snapshot(j))",
                                  "(s.rounds == 0 && j % ORC_SNAPSHOT_GROUP == 0)"),
     "no_refresh_per_round": ("if (j == 0 || (stop_every", "if ((j == 0 && s.rounds == 0) || (stop_every"),
-    "kth_from_wrong_slot": ("orc_filter_tau((double)ps[k - 1])", "orc_filter_tau((double)ps[0])"),
+    "kth_from_wrong_slot": ("orc_filter_tau_eps((double)ps[k - 1]", "orc_filter_tau_eps((double)ps[0]"),
 }
 
 

@@ -330,3 +330,32 @@ def test_blocked_hashing_equals_one_point_at_a_time(orc, family, d):
         orc.lib().orc_hash_one(family, L, d, A.ctypes.data_as(C.c_void_p), xp.ctypes.data_as(C.c_void_p),
                                one.ctypes.data_as(C.c_void_p))
         assert np.array_equal(codes[:, p], one), p
+
+
+def test_filter_tau_with_slack(orc):
+    """Fig. 2 footnote: tau = (1 + eps) times the expected number of differing
+    bits, 64 arccos(s_k)/pi, rounded down (at most 64)."""
+    rng = np.random.default_rng(1)
+    for eps in (0.1, 0.25, 0.5):
+        for s in rng.uniform(-1, 1, 1000):
+            v = (1 + eps) * 64 * math.acos(s) / math.pi
+            if abs(v - round(v)) > 1e-9:
+                assert orc.filter_tau(s, eps) == min(64, math.floor(v)), (eps, s)
+        assert orc.filter_tau(1.0, eps) == 0 and orc.filter_tau(-1.0, eps) == 64
+
+
+def test_filter_slack_only_admits_more(orc):
+    """A slack eps > 0 lets through a superset at every snapshot with the same
+    top-k, so the plain search's recall with eps is at least eps = 0's."""
+    X = datagen.vmf_mixture(4000, 32, 25, 25.0, seed=17)
+    Q = datagen.vmf_mixture(60, 32, 25, 25.0, seed=17, purpose="queries")
+    ix = orc.OracleIndex(X, 1, L=30, seed=9)
+    _, bs = orc.brute_force(ix.x, orc.normalize(Q), 10)
+    rec = []
+    for eps in (0.0, 0.2, 1e9):
+        r = ix.search(Q, 10, 0.9, filter_eps=eps)
+        rec.append(float(np.mean(r["sims"] >= bs[:, -1:])))
+        if eps > 1e6:  # everything passes: the unfiltered search
+            off = ix.search(Q, 10, 0.9, filter=False)
+            assert np.array_equal(r["ids"], off["ids"]) and np.array_equal(r["stats"], off["stats"])
+    assert rec[0] <= rec[1] + 0.02 and rec[1] <= rec[2] + 1e-12
