@@ -90,6 +90,9 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other two modes")
     ap.add_argument("--recall", type=float, default=None,
                     help="recall target 1 - delta passed to the index (default: the workload's)")
+    ap.add_argument("--flat-fill", type=int, default=None,
+                    help="override the tuned streaming rule of the search kernel (0: chunks of one run; F: flat "
+                         "when the chunks are less than 1/F full)")
     ap.add_argument("--filter-eps", type=float, default=0.0,
                     help="slack of the sketch threshold (Fig. 2 footnote; 0 as in Sec. 5.1)")
     ap.add_argument("--pool-bits", type=int, default=0,
@@ -649,6 +652,11 @@ def main():
                               scoring="fp32" if args.mode == "fp32" else args.estimate,
                               learned=args.mode == "learned",
                               stop_every=args.stop_every, pool_rule=args.pool_rule, filter_eps=args.filter_eps)
+    if args.flat_fill is not None:  # keep the tuned shape but this streaming rule
+        t = tune_report or {"unroll": 8, "warps": 4, "ctas_per_sm": 0}
+        ix.set_shape(t["unroll"], t["warps"], t["ctas_per_sm"], args.flat_fill)
+        if tune_report:
+            tune_report = dict(tune_report, flat_fill=args.flat_fill, overridden="flat_fill")
 
     def opts_of(mode):
         return ("fp32" if mode == "fp32" else args.estimate), mode == "learned"

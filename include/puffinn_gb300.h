@@ -312,7 +312,7 @@ void pf_search_opts_default(pf_search_opts* opts);
  * in pf_index_search: scoring, filter, learned start) for each candidate shape
  * -- 4 warps per query with 4 or 8 positions per lane per streaming step, or
  * 8 warps with 8 positions, times the largest resident CTAs per SM and one or
- * two fewer -- and keeps the fastest for the index's later searches and
+ * two fewer, times streaming rule flat_fill 0 or 3 -- and keeps the fastest for the index's later searches and
  * plans.  queries: host or device, [Q][d] float32.
  * report (may be NULL) receives the choice.  Errors: PF_ERR_INVALID_ARG (bad
  * sizes, or search plans bound to the index exist), PF_ERR_NOT_TRAINED, CUDA. */
@@ -320,6 +320,7 @@ typedef struct {
   int32_t unroll;       /* chosen positions per lane per streaming step */
   int32_t warps;        /* chosen warps per query (4 or 8) */
   int32_t ctas_per_sm;  /* chosen CTAs per SM */
+  int32_t flat_fill;    /* chosen streaming rule (see pf_index_set_shape) */
   int32_t candidates;   /* shapes timed */
   float best_ms;        /* search-kernel time of the chosen shape on the batch */
   float default_ms;     /* ... of the default shape (8 positions, full occupancy) */
@@ -328,9 +329,13 @@ pf_status pf_index_tune(pf_index* index, const float* queries, int64_t Q, int32_
                         const pf_search_opts* opts, pf_tune_report* report, void* stream);
 /* Set the launch shape of the index's later searches and plans directly:
  * unroll 4 or 8 positions per lane, warps 4 or 8 per query (8 only with unroll
- * 8), ctas_per_sm a cap on resident CTAs per SM (0: as many as fit).  Errors:
- * PF_ERR_INVALID_ARG (other values, or search plans bound to the index). */
-pf_status pf_index_set_shape(pf_index* index, int32_t unroll, int32_t warps, int32_t ctas_per_sm);
+ * 8), ctas_per_sm a cap on resident CTAs per SM (0: as many as fit),
+ * flat_fill the streaming rule: 0 = every round streams its new positions in
+ * chunks of one run; F in 1..64 = a round whose chunks would be less than 1/F
+ * full streams them as one flat sequence instead (short runs; the same
+ * candidates either way).  Errors: PF_ERR_INVALID_ARG (other values, or search
+ * plans bound to the index). */
+pf_status pf_index_set_shape(pf_index* index, int32_t unroll, int32_t warps, int32_t ctas_per_sm, int32_t flat_fill);
 
 /* ---- Captured search (a CUDA graph of one batch shape) ----
  * pf_index_search for a fixed Q, k_max and options, bound to caller-owned

@@ -75,8 +75,8 @@ class LearnedReport(C.Structure):
 
 
 class TuneReport(C.Structure):
-    _fields_ = [("unroll", C.c_int32), ("warps", C.c_int32), ("ctas_per_sm", C.c_int32), ("candidates", C.c_int32),
-                ("best_ms", C.c_float), ("default_ms", C.c_float)]
+    _fields_ = [("unroll", C.c_int32), ("warps", C.c_int32), ("ctas_per_sm", C.c_int32), ("flat_fill", C.c_int32),
+                ("candidates", C.c_int32), ("best_ms", C.c_float), ("default_ms", C.c_float)]
 
 
 class PlanIO(C.Structure):
@@ -128,7 +128,7 @@ def lib():
                 "pf_index_selftest_timeout": (i32, [vp, vp, i64, vp]),
                 "pf_index_selftest_hold": (i32, [vp, i32]),
                 "pf_index_count_range_paths": (i32, [vp, i32, vp]),
-                "pf_index_set_shape": (i32, [vp, i32, i32, i32]),
+                "pf_index_set_shape": (i32, [vp, i32, i32, i32, i32]),
                 "pf_search_plan_create": (i32, [vp, i64, i32, vp, vp, vp]),
                 "pf_search_plan_run": (i32, [vp, vp]),
                 "pf_search_plan_check": (i32, [vp, vp]),
@@ -335,9 +335,9 @@ class Index:
                                    C.byref(o), C.byref(rep), _stream_ptr(stream)))
         return {f: getattr(rep, f) for f, _ in TuneReport._fields_}
 
-    def set_shape(self, unroll: int = 8, warps: int = 4, ctas_per_sm: int = 0):
+    def set_shape(self, unroll: int = 8, warps: int = 4, ctas_per_sm: int = 0, flat_fill: int = 0):
         """pf_index_set_shape: the launch shape of later searches and plans."""
-        _check(lib().pf_index_set_shape(self._h, int(unroll), int(warps), int(ctas_per_sm)))
+        _check(lib().pf_index_set_shape(self._h, int(unroll), int(warps), int(ctas_per_sm), int(flat_fill)))
 
     def selftest_timeout(self, queries, stream=None):
         """pf_index_selftest_timeout: hash with the weight loads withheld; raises

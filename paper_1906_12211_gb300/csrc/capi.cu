@@ -1040,7 +1040,8 @@ pf_status pf_index_tune(pf_index* ix, const float* queries, int64_t Q, int32_t k
     std::vector<SearchShape> cand;
     for (const auto& uw : {std::pair<int, int>{8, 4}, {4, 4}, {8, 8}}) {
       const int mx = search_max_ctas_per_sm(ix, k, uw.first, uw.second);
-      for (int c = mx; c >= 1 && c >= mx - 2; --c) cand.push_back(SearchShape{uw.first, c, uw.second});
+      for (int c = mx; c >= 1 && c >= mx - 2; --c)
+        for (int ff : {0, 3}) cand.push_back(SearchShape{uw.first, c, uw.second, ff});
     }
     if (cand.empty()) return fail(PF_ERR_CUDA, "no launchable search shape");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1081,6 +1082,7 @@ pf_status pf_index_tune(pf_index* ix, const float* queries, int64_t Q, int32_t k
       report->unroll = pick.unroll;
       report->warps = pick.warps;
       report->ctas_per_sm = pick.ctas_per_sm;
+      report->flat_fill = pick.flat_fill;
       report->candidates = int32_t(cand.size());
       report->best_ms = best;
       report->default_ms = dflt;
@@ -1089,13 +1091,15 @@ pf_status pf_index_tune(pf_index* ix, const float* queries, int64_t Q, int32_t k
   });
 }
 
-pf_status pf_index_set_shape(pf_index* ix, int32_t unroll, int32_t warps, int32_t ctas_per_sm) {
+pf_status pf_index_set_shape(pf_index* ix, int32_t unroll, int32_t warps, int32_t ctas_per_sm, int32_t flat_fill) {
   return guarded([&]() -> pf_status {
     if (!ix) return fail(PF_ERR_INVALID_ARG, "null index");
-    if ((unroll != 4 && unroll != 8) || (warps != 4 && warps != 8) || (warps == 8 && unroll != 8) || ctas_per_sm < 0)
-      return fail(PF_ERR_INVALID_ARG, "unroll must be 4 or 8, warps 4 or 8 (8 only with unroll 8), ctas_per_sm >= 0");
+    if ((unroll != 4 && unroll != 8) || (warps != 4 && warps != 8) || (warps == 8 && unroll != 8) || ctas_per_sm < 0 ||
+        flat_fill < 0 || flat_fill > 64)
+      return fail(PF_ERR_INVALID_ARG,
+                  "unroll must be 4 or 8, warps 4 or 8 (8 only with unroll 8), ctas_per_sm >= 0, flat_fill in [0, 64]");
     if (ix->live_plans > 0) return fail(PF_ERR_INVALID_ARG, "search plans bound to the index exist");
-    ix->search_shape = SearchShape{unroll, ctas_per_sm, warps};
+    ix->search_shape = SearchShape{unroll, ctas_per_sm, warps, flat_fill};
     return PF_OK;
   });
 }

@@ -68,6 +68,7 @@ cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t 
   P.pool_fns = ix->pool_fns;
   P.pool_rule = a.pool_rule;
   const SearchShape sh = a.shape.unroll ? a.shape : ix->search_shape;
+  P.flat_fill = sh.flat_fill;
   const int U = sh.unroll == 4 ? 4 : 8, QW = sh.warps == 8 ? 8 : 4;
   const size_t smem = search_smem(P.d_pad, P.L, P.M, P.k_max, U, QW);
   skern::Kernel kern = pick_search_kernel(P.d_pad, U, QW);

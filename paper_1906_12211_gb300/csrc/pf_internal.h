@@ -52,6 +52,7 @@ struct SearchShape {
   int unroll = 0;       // 0 in SearchArgs: the index's tuned shape
   int ctas_per_sm = 0;
   int warps = 4;
+  int flat_fill = 0;    // 0: rounds stream in chunks of one run; F: flat when the chunks are < 1/F full
 };
 
 // ---------------------------------------------------------------- host params

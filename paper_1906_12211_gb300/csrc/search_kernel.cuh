@@ -51,7 +51,6 @@ constexpr unsigned kFull = 0xffffffffu;
 // U = positions per lane per streaming step (a template parameter: 4 or 8,
 // chosen by the tuner); a chunk is 32*U positions of one run
 constexpr int kFlushAt = 256;   // a warp scores its buffer once it holds more than this
-constexpr int kFlatFill = 3;    // a round streams flat when its chunks are less than 1/kFlatFill full
 __host__ __device__ constexpr int cand_buf(int U) { return kFlushAt + 32 * U; }  // compacted ids per warp
 constexpr int kGroup = 32;      // repetitions per threshold snapshot in a first round (after 1, 2, 4, 8, 16)
 
@@ -99,6 +98,7 @@ struct Dev {
   int stop_every;  // 0: stop test per round; G: also after every G repetitions (Alg. 1)
   int pool_fns;    // pooled index: functions in the pool (0: independent functions)
   int pool_rule;   // pooled index: 0 Cantelli's bound, 1 Lemma 1 as if independent
+  int flat_fill;   // launch shape: stream a round flat when its chunks are < 1/flat_fill full (0: never)
 };
 
 __device__ __forceinline__ bool better(float s1, uint32_t i1, float s2, uint32_t i2) {
@@ -717,7 +717,7 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
       __syncthreads();
       // short runs leave most of a chunk's lanes idle: the round then streams
       // its positions as one flat sequence instead (the same candidates)
-      const bool flat = uint64_t(cpre[L]) * kSpan > uint64_t(kFlatFill) * ppre[L];
+      const bool flat = P.flat_fill > 0 && uint64_t(cpre[L]) * kSpan > uint64_t(P.flat_fill) * ppre[L];
       if (P.path_count && tid == 0) atomicAdd(P.path_count + (flat ? 4 : 3), 1ull);  // diagnostics only
 
       // ---- stream the chunks, group by group

@@ -47,6 +47,6 @@ def test_struct_layouts_match_header(tmp_path):
 def test_null_arguments_are_rejected_without_gpu():
     lib = pf.lib()
     assert lib.pf_index_build(None, None, None, None) == -1
-    assert lib.pf_index_set_shape(None, 8, 4, 0) == -1
+    assert lib.pf_index_set_shape(None, 8, 4, 0, 0) == -1
     assert lib.pf_index_info(None, None) == -1
     lib.pf_index_free(None)

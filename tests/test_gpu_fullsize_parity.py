@@ -56,11 +56,13 @@ def test_search_equals_oracle_at_full_n(both, scoring, filt):
     g, o, Q, qd = both
     ref = o.search(Q, 10, 0.9, filter=filt)
     g.count_range_paths(True)
+    g.set_shape(8, 4, 0, 3)  # rounds of short runs stream flat
     try:
         out = g.search(qd, 10, 0.9, scoring=scoring, filter=filt, stats=True)
         paths = g.count_range_paths(True)
     finally:
         g.count_range_paths(False)
+        g.set_shape(8, 4, 0, 0)
     _compare(out, ref)
     # every branch of the range pass ran: prefix-table blocks, probed sides and
     # sides that galloped past the probed boundaries
@@ -80,15 +82,18 @@ def test_given_start_depths_and_mixed_k_at_full_n(both):
     _compare(out, ref)
 
 
-@pytest.mark.parametrize("shape", [(8, 4, 0), (4, 4, 0), (8, 8, 0), (8, 4, 3)])
+@pytest.mark.parametrize("shape", [(8, 4, 0, 0), (4, 4, 0, 0), (8, 8, 0, 0), (8, 4, 3, 0), (8, 4, 0, 3),
+                                   (4, 4, 0, 64), (8, 8, 0, 1)])
 def test_every_launch_shape_at_full_n(both, shape):
+    """flat_fill 3 and 64 stream short-run rounds flat (64: almost every round
+    but depth 0), 1 only rounds whose chunks are nearly empty."""
     g, o, Q, qd = both
     ref = o.search(Q[:100], 10, 0.9)
     g.set_shape(*shape)
     try:
         out = g.search(qd[:100], 10, 0.9, scoring="bf16", stats=True)
     finally:
-        g.set_shape(8, 4, 0)
+        g.set_shape(8, 4, 0, 0)
     _compare(out, ref)
 
 

@@ -333,9 +333,9 @@ def test_errors_are_statuses():
     assert ids.shape[0] == 0
 
 
-@pytest.mark.parametrize("shape", [(4, 4, 0), (8, 8, 0), (8, 4, 3)])
+@pytest.mark.parametrize("shape", [(4, 4, 0), (8, 8, 0), (8, 4, 3), (8, 4, 0, 3), (4, 4, 0, 64), (8, 8, 0, 3)])
 def test_every_launch_shape_equals_the_oracle(cpmid, shape):
-    # positions per lane, warps per query and CTAs per SM change no result
+    # positions per lane, warps per query, CTAs per SM and the streaming rule change no result
     ref = cpmid.orc.search(cpmid.Q, 10, 0.9)
     cpmid.gpu.set_shape(*shape)
     try:
@@ -346,7 +346,7 @@ def test_every_launch_shape_equals_the_oracle(cpmid, shape):
 
 
 def test_invalid_launch_shapes_are_rejected(cpmid):
-    for bad in ((4, 8, 0), (6, 4, 0), (8, 5, 0), (8, 4, -1)):
+    for bad in ((4, 8, 0), (6, 4, 0), (8, 5, 0), (8, 4, -1), (8, 4, 0, -1), (8, 4, 0, 65)):
         with pytest.raises(pf.PuffinnError) as e:
             cpmid.gpu.set_shape(*bad)
         assert e.value.status == -1
