@@ -64,9 +64,21 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
+/* Round a float to the nearest bfloat16 value (ties to even), kept as a float. */
+static float round_to_bfloat16(float f) {
+  uint32_t u;
+  memcpy(&u, &f, sizeof(u));
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  u &= 0xFFFF0000u;
+  memcpy(&f, &u, sizeof(f));
+  return f;
+}
+
 /* Reading (the paper fixes no generator): counter = (c, b, a, purpose),
  * key = the 64-bit seed.  u1 in (0,1] from words 0,1 and u2 in [0,1) from
- * words 2,3 (53 bits each); z = sqrt(-2 ln u1) cos(2 pi u2), rounded to float. */
+ * words 2,3 (53 bits each); z = sqrt(-2 ln u1) cos(2 pi u2), rounded to float and
+ * then to bfloat16 (nearest, ties to even): every hyperplane entry is a
+ * bfloat16 value. */
 float orc_gauss(uint64_t seed, uint32_t purpose, uint32_t a, uint32_t b, uint32_t c) {
   uint32_t ctr[4] = {c, b, a, purpose};
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
@@ -78,7 +90,7 @@ float orc_gauss(uint64_t seed, uint32_t purpose, uint32_t a, uint32_t b, uint32_
   double u2 = (double)(w2 >> 11) * (1.0 / 9007199254740992.0);
   double rad = sqrt(-2.0 * log(u1));
   double z = rad * cos(2.0 * M_PI * u2);
-  return (float)z;
+  return round_to_bfloat16((float)z);
 }
 
 /* Sec. 4.3: l = 1 for HP, l = ceil(log2(2d)) for CP.  Reading: codes are 32
@@ -530,12 +542,12 @@ int orc_filter_tau_eps(double s_k, double eps) {
  * the hash functions and the tables.  Reading: bytes of the layout the GPU
  * library keeps resident, with d' = d rounded up to a multiple of 16:
  *   fixed     = n d' (4 + 2)   rows as float32 and bfloat16
- *             + 64 M d' 8      sketch planes (float32 + two bfloat16 halves)
+ *             + 64 M d' 6      sketch planes (float32 + their exact bfloat16 copy)
  *             + n M 8          the M sketches of every point (layout 1 only)
  *   per table = n (4 + 4)      sorted codes and positions
  *             + n 8            the sketch of each entry (layout 0 only)
  *             + 8193 * 4       prefix table
- *             + R d' 8         hash rows (float32 + two bfloat16 halves),
+ *             + R d' 6         hash rows (float32 + their exact bfloat16 copy),
  *               R = F * d' for CP (rows of a function padded to d'), 32 for HP
  *   L = floor((budget - fixed) / per_table). */
 int64_t orc_budget_L(int family, int64_t n, int d, int M, uint64_t budget_bytes, int sketch_layout,
@@ -554,17 +566,17 @@ int64_t orc_budget_L(int family, int64_t n, int d, int M, uint64_t budget_bytes,
   }
   /* rows: float32 (4 B) or binary16 (2 B) per element, plus the bfloat16 copy (2 B) */
   int64_t row_bytes = row_storage == 1 ? 4 : 6;
-  int64_t fixed = n * dp * row_bytes + 64 * (int64_t)M * dp * 8 + (sketch_layout == 1 ? n * (int64_t)M * 8 : 0);
+  int64_t fixed = n * dp * row_bytes + 64 * (int64_t)M * dp * 6 + (sketch_layout == 1 ? n * (int64_t)M * 8 : 0);
   /* an 8-bit float copy of the rows, with a scale and an error bound each */
   if (fp8_rows) fixed += n * (dp + 8);
   /* pooled functions (Sec. 3.2): the pool's rows, stored in whole groups of F
    * functions, are fixed; a table keeps only its F indices */
   if (pool_fns > 0) {
     int64_t groups = (pool_fns + F - 1) / F;
-    fixed += groups * R * dp * 8;
+    fixed += groups * R * dp * 6;
     R = 0;
   }
-  int64_t per_table = n * (sketch_layout == 1 ? 8 : 16) + (int64_t)((1 << ORC_PREFIX_BITS) + 1) * 4 + R * dp * 8 +
+  int64_t per_table = n * (sketch_layout == 1 ? 8 : 16) + (int64_t)((1 << ORC_PREFIX_BITS) + 1) * 4 + R * dp * 6 +
                       fht_bytes + (pool_fns > 0 ? (int64_t)F * 4 : 0);
   if ((int64_t)budget_bytes <= fixed) return 0;
   return ((int64_t)budget_bytes - fixed) / per_table;

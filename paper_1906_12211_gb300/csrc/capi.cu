@@ -80,14 +80,10 @@ pf_status guarded(F&& body) {
 }
 
 // bfloat16 hi/lo split of the float32 hash rows (for the tensor-core path)
-__global__ void split_bf16_kernel(const float* __restrict__ w, int64_t count, __nv_bfloat16* __restrict__ hi,
-                                  __nv_bfloat16* __restrict__ lo) {
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x) {
-    const float v = w[i];
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    hi[i] = h;
-    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
-  }
+// the hyperplanes' entries are bfloat16 values (R2): their bfloat16 copy is exact
+__global__ void to_bf16_exact_kernel(const float* __restrict__ w, int64_t count, __nv_bfloat16* __restrict__ hi) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x)
+    hi[i] = __float2bfloat16_rn(w[i]);
 }
 
 void free_ws(pf_workspace& ws) {
@@ -155,7 +151,6 @@ void destroy(pf_index* ix) {
   dfree(ix->skc);
   dfree(ix->W32);
   dfree(ix->Whi);
-  dfree(ix->Wlo);
   dfree(ix->Wthr);
   dfree(ix->codes);
   dfree(ix->ids);
@@ -345,7 +340,6 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
         dalloc(&ix->skc, size_t(n) * ix->L);
       dalloc(&ix->W32, size_t(ix->hash_rows) * dp);
       dalloc(&ix->Whi, size_t(ix->hash_rows) * dp);
-      dalloc(&ix->Wlo, size_t(ix->hash_rows) * dp);
       dalloc(&ix->Wthr, size_t(ix->hash_rows));
       dalloc(&ix->codes, size_t(n) * ix->L);
       dalloc(&ix->ids, size_t(n) * ix->L);
@@ -377,7 +371,7 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
       }
       PF_CK(cudaMemcpyAsync(ix->W32, W.data(), sizeof(float) * W.size(), cudaMemcpyHostToDevice, s));
       PF_CK(cudaMemcpyAsync(ix->Wthr, thr.data(), sizeof(float) * thr.size(), cudaMemcpyHostToDevice, s));
-      split_bf16_kernel<<<1024, 256, 0, s>>>(ix->W32, int64_t(W.size()), ix->Whi, ix->Wlo);
+      to_bf16_exact_kernel<<<1024, 256, 0, s>>>(ix->W32, int64_t(W.size()), ix->Whi);
       PF_CK(cudaGetLastError());
       std::vector<double> cosv(65);
       filter_cos_table(cosv.data());

@@ -73,7 +73,6 @@ struct HashArgs {
   const float* x32;
   int64_t npts;
   const __nv_bfloat16* wh;
-  const __nv_bfloat16* wl;
   const float* w32;
   const float* thr;
   int64_t hash_rows;
@@ -576,8 +575,8 @@ __device__ __forceinline__ void epilogue(const HashArgs& A, const Tile& t, uint3
 
 struct TensorMaps {
   CUtensorMap xh, xl;        // A: [npts][d_pad], box {64, 128}
-  CUtensorMap wh_f, wl_f;    // B, CP function tiles: box {64, d_pad}
-  CUtensorMap wh_g, wl_g;    // B, 128-row groups: box {64, 128}
+  CUtensorMap wh_f;          // B, CP function tiles: box {64, d_pad}
+  CUtensorMap wh_g;          // B, 128-row groups: box {64, 128}
 };
 
 __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const __grid_constant__ TensorMaps T) {
@@ -645,12 +644,11 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
           const Tile t = tile_of(A, seg, f);
           const bool fn_tile = t.rows == A.d_pad && seg < A.seg_tables && A.family == PF_CROSSPOLYTOPE;
           const CUtensorMap* mh = fn_tile ? &T.wh_f : &T.wh_g;
-          const CUtensorMap* ml = fn_tile ? &T.wl_f : &T.wl_g;
-          for (int u = 0; u < 2 * KB; ++u, ++stage) {
+          for (int kb = 0; kb < KB; ++kb, ++stage) {
             const uint32_t slot = stage % S, round = stage / S;
             if (!mbar_wait(smem_u32(&bempty[slot]), (round & 1) ^ 1)) { bad = true; break; }
             mbar_expect_tx(smem_u32(&bfull[slot]), uint32_t(t.rows * 128));
-            tma_load_2d(sB + slot * kTileBytes, (u & 1) ? ml : mh, (u >> 1) * 64, int(t.row0), smem_u32(&bfull[slot]));
+            tma_load_2d(sB + slot * kTileBytes, mh, kb * 64, int(t.row0), smem_u32(&bfull[slot]));
           }
         }
       if (bad) { failed = 1; break; }
@@ -675,20 +673,19 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
           if (bad) break;
           tc_fence_after();
           const uint32_t idesc = idesc_bf16(kBM, t.rows);
-          for (int u = 0; u < 2 * KB; ++u, ++stage) {
+          for (int kb = 0; kb < KB; ++kb, ++stage) {
             const uint32_t slot = stage % S, round = stage / S;
             if (!mbar_wait(smem_u32(&bfull[slot]), round & 1)) { bad = true; break; }
             tc_fence_after();
-            const int kb = u >> 1;
             const uint32_t bt = sB + slot * kTileBytes;
             for (int pt = 0; pt < kPair; ++pt) {
               const uint32_t d_tmem = tmem + (b * kPair + pt) * 128;
-              // Wh stage: Xh*Wh and Xl*Wh; Wl stage: Xh*Wl
-              for (int half = 0; half < ((u & 1) ? 1 : 2); ++half) {
+              // the hyperplane tile is exact in bfloat16: Xh*W and Xl*W
+              for (int half = 0; half < 2; ++half) {
                 const uint32_t at = sA + pt * a_bytes + uint32_t(((half ? KB : 0) + kb) * kTileBytes);
                 for (int kk = 0; kk < 4; ++kk)
                   mma_bf16(d_tmem, sw128_desc(at + kk * 32), sw128_desc(bt + kk * 32), idesc,
-                           (u | half | kk) ? 1u : 0u);
+                           (kb | half | kk) ? 1u : 0u);
               }
             }
             mma_commit(smem_u32(&bempty[slot]));
@@ -1073,7 +1070,6 @@ cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __
   A.x32 = x32;
   A.npts = npts;
   A.wh = ix->Whi;
-  A.wl = ix->Wlo;
   A.w32 = ix->W32;
   A.thr = ix->Wthr;
   A.hash_rows = ix->hash_rows;
@@ -1107,9 +1103,7 @@ cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __
   const int fn_rows = ix->family == PF_CROSSPOLYTOPE ? A.d_pad : 128;
   if (!make_map(&T.xh, xh, npts, A.d_pad, kBM) || !make_map(&T.xl, xl, npts, A.d_pad, kBM) ||
       !make_map(&T.wh_f, ix->Whi, ix->hash_rows, A.d_pad, fn_rows) ||
-      !make_map(&T.wl_f, ix->Wlo, ix->hash_rows, A.d_pad, fn_rows) ||
-      !make_map(&T.wh_g, ix->Whi, ix->hash_rows, A.d_pad, 128) ||
-      !make_map(&T.wl_g, ix->Wlo, ix->hash_rows, A.d_pad, 128))
+      !make_map(&T.wh_g, ix->Whi, ix->hash_rows, A.d_pad, 128))
     return cudaErrorInvalidValue;
   const size_t smem = hash_tc_smem(A.d_pad);
   cudaError_t e = cudaFuncSetAttribute(hash_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));

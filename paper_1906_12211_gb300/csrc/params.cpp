@@ -58,7 +58,7 @@ void parallel_for(int64_t count, F&& body) {
 
 // One N(0,1) draw per counter: counter words (c, b, a, purpose), key = seed.
 // Two 53-bit uniforms u1 in (0,1] (words 0-1) and u2 in [0,1) (words 2-3);
-// Box-Muller cosine branch in double, rounded once to float.
+// Box-Muller cosine branch in double, rounded to float, then to bfloat16.
 float gaussian(uint64_t seed, uint32_t purpose, uint32_t a, uint32_t b, uint32_t c) {
   uint32_t w[4] = {c, b, a, purpose};
   Philox4x32::block(w, uint32_t(seed), uint32_t(seed >> 32));
@@ -69,7 +69,16 @@ float gaussian(uint64_t seed, uint32_t purpose, uint32_t a, uint32_t b, uint32_t
   const double u2 = double(lo >> 11) * scale;
   const double radius = std::sqrt(-2.0 * std::log(u1));
   const double z = radius * std::cos(2.0 * M_PI * u2);
-  return float(z);
+  // then to bfloat16, nearest even (R2: every hyperplane entry is a bfloat16
+  // value, so the tensor-core products with it are exact)
+  uint32_t u;
+  const float f = float(z);
+  std::memcpy(&u, &f, sizeof(u));
+  u += 0x7fffu + ((u >> 16) & 1u);
+  u &= 0xffff0000u;
+  float r;
+  std::memcpy(&r, &u, sizeof(r));
+  return r;
 }
 
 Layout make_layout(int family, int d) {
@@ -378,7 +387,7 @@ void filter_cos_table(double* c, double eps) {
 // Device bytes the index keeps resident for L repetitions; the budget rule
 // picks the largest L whose total fits (Sec. 5: the index size covers the
 // data, the hash functions and the tables).  Per repetition: sorted codes and
-// ids, the prefix table, the hash rows (float32 + two bfloat16 halves) and,
+// ids, the prefix table, the hash rows (float32 + their exact bfloat16 copy) and,
 // with per-repetition sketches, one uint64 per entry.  Fixed: the rows
 // (float32 + bfloat16), the sketch planes and, with per-point sketches, the M
 // sketches of every point.
@@ -388,20 +397,20 @@ uint64_t resident_bytes(int family, int64_t n, int d, int M, int L, int sketch_l
   const int64_t dp = lay.d_pad;
   const bool per_point = sketch_layout == PF_SKETCH_PER_POINT;
   const int64_t row_bytes = row_storage == PF_ROWS_F16 ? 4 : 6;  // rows (4 or 2 B) + the bfloat16 copy (2 B)
-  int64_t fixed = n * dp * row_bytes + 64LL * M * dp * 8 + (per_point ? n * int64_t(M) * 8 : 0) +
+  int64_t fixed = n * dp * row_bytes + 64LL * M * dp * 6 + (per_point ? n * int64_t(M) * 8 : 0) +
                   (fp8_rows ? n * (dp + 8) : 0);  // e4m3 rows + (scale, bound) per row
   // pooling: the pool's rows (whole groups of fns functions) are fixed; a
   // table keeps its fns indices instead of rows
   int64_t rows_table = lay.rows_table, sel_bytes = 0;
   if (pool_fns > 0) {
-    fixed += int64_t((pool_fns + lay.fns - 1) / lay.fns) * lay.rows_table * dp * 8;
+    fixed += int64_t((pool_fns + lay.fns - 1) / lay.fns) * lay.rows_table * dp * 6;
     rows_table = 0;
     sel_bytes = int64_t(lay.fns) * 4;
   }
   // pseudo-random CP: three sign vectors per function instead of rows
   const int64_t fht = family == PF_CROSSPOLYTOPE_FHT ? int64_t(lay.fns) * 3 * lay.fht_words * 4 : 0;
   const int64_t per_table =
-      n * (per_point ? 8 : 16) + int64_t(kPrefixSize) * 4 + rows_table * dp * 8 + fht + sel_bytes;
+      n * (per_point ? 8 : 16) + int64_t(kPrefixSize) * 4 + rows_table * dp * 6 + fht + sel_bytes;
   return uint64_t(fixed + per_table * L);
 }
 

@@ -136,7 +136,6 @@ struct pf_index {
   uint64_t* skc = nullptr;         // [L][n] sketch j mod M of the point at each position (per-table layout)
   float* W32 = nullptr;            // [hash_rows][d_pad]
   __nv_bfloat16* Whi = nullptr;    // [hash_rows][d_pad]
-  __nv_bfloat16* Wlo = nullptr;    // [hash_rows][d_pad]
   float* Wthr = nullptr;           // [hash_rows]
   uint32_t* codes = nullptr;       // [L][n]
   uint32_t* ids = nullptr;         // [L][n]

@@ -450,6 +450,81 @@ __device__ __forceinline__ int flush_candidates(const Dev& P, const float* q, ui
   return size;
 }
 
+// A flat round's streaming (see the launch shape's flat_fill): warp `warp`
+// takes the spans of kSpan consecutive positions warp, warp + QW, ... of the
+// group's runs laid end to end (repetition by repetition, left run before right
+// run); a lane finds the repetition of its first position by binary search over
+// ppre (the position prefix), then walks on.  Kept out of line so that the
+// chunked loop, the common case, is compiled as if this did not exist.
+template <int NT, int NT2, int U, int QW>
+__device__ __noinline__ void flat_stream(const Dev& P, const float* q, const uint64_t* qsk, const uint4* runs,
+                                         const uint32_t* ppre, uint32_t* cbuf, float* my_s, uint32_t* my_id, int j0,
+                                         int j1, int tau, float gkth, int k, int lane, int warp, int& nb_io,
+                                         int& wsize_io, Counters& ct) {
+  constexpr int kUnroll = U;
+  constexpr uint32_t kSpan = 32u * U;
+  constexpr int kQW = QW;
+  const uint32_t n = uint32_t(P.n);
+  const int M = P.M;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  int nb = nb_io, wsize = wsize_io;
+  const uint32_t p_end = ppre[j1];
+  for (uint32_t b = ppre[j0] + uint32_t(warp) * kSpan; b < p_end; b += kQW * kSpan) {
+    int jl = j0, jh = j1;  // ppre[jl] <= b + lane < ppre[jh]
+    const uint32_t p0 = min(b + uint32_t(lane), p_end - 1u);
+    while (jh - jl > 1) {
+      const int mid = (jl + jh) >> 1;
+      if (ppre[mid] <= p0) jl = mid; else jh = mid;
+    }
+    int jr = jl;
+    uint32_t id[kUnroll];
+    bool pass[kUnroll];
+    size_t at[kUnroll];
+    int jof[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t pos = b + 32u * u + uint32_t(lane);
+      const bool valid = pos < p_end;
+      if (valid)
+        while (ppre[jr + 1] <= pos) ++jr;
+      const uint4 ru = runs[jr];
+      const uint32_t o = pos - ppre[jr];
+      const uint32_t ap = o < ru.y ? ru.x + o : ru.z + (o - ru.y);
+      at[u] = size_t(jr) * n + ap;
+      jof[u] = jr;
+      id[u] = valid ? __ldg(P.ids + at[u]) : 0u;
+      pass[u] = valid;
+    }
+    if (P.filter) {
+      uint64_t hd[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const uint64_t sk = !pass[u] ? 0ull
+                            : P.skc ? __ldg(P.skc + at[u])
+                                    : __ldg(P.sk + size_t(jof[u] % M) * n + id[u]);
+        hd[u] = sk ^ qsk[jof[u] % M];
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) pass[u] = pass[u] && __popcll(hd[u]) <= tau;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const unsigned pm = __ballot_sync(kFull, pass[u]);
+      if (pass[u]) cbuf[nb + __popc(pm & lt_mask)] = id[u];
+      nb += __popc(pm);
+    }
+    if (lane == 0) ct.retrieved += min(kSpan, p_end - b);
+    __syncwarp();
+    if (nb > kFlushAt) {
+      if (lane == 0) ct.passed += uint32_t(nb);  // every buffered candidate passed the filter
+      wsize = flush_candidates<NT, NT2>(P, q, cbuf, nb, my_s, my_id, wsize, k, gkth, lane, ct);
+      nb = 0;
+    }
+  }
+  nb_io = nb;
+  wsize_io = wsize;
+}
+
 // NT = d_pad / 32 rounded up: float4 chunks of a float32 row per lane of an
 // 8-lane group; NT2 = d_pad / 16 rounded up: 16-byte chunks of a bfloat16 row
 // per lane of a pair
@@ -683,7 +758,7 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
       }
       // exclusive scans over the repetitions of the chunk counts -> cpre and
       // of the new positions -> ppre
-      uint32_t inc = my_chunks, pinc = my_pos;
+      uint32_t inc = my_chunks, pinc = P.flat_fill > 0 ? my_pos : 0u;
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
         const uint32_t v = __shfl_up_sync(kFull, inc, off);
@@ -739,63 +814,9 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
         int jc = j0;
         uint64_t qh = qsk[j0 % M];  // the query's sketch for repetition jc
         int nb = 0;
-        // flat round: warp w takes the spans of kSpan consecutive positions w,
-        // w + kQW, ... of the group's runs laid end to end (repetition by
-        // repetition, left run before right run); a lane finds the repetition
-        // of its first position by binary search over ppre, then walks on
-        const uint32_t p_end = ppre[j1];
-        for (uint32_t b = flat ? ppre[j0] + uint32_t(warp) * kSpan : p_end; b < p_end; b += kQW * kSpan) {
-          int jl = j0, jh = j1;  // ppre[jl] <= b + lane < ppre[jh]
-          const uint32_t p0 = min(b + uint32_t(lane), p_end - 1u);
-          while (jh - jl > 1) {
-            const int mid = (jl + jh) >> 1;
-            if (ppre[mid] <= p0) jl = mid; else jh = mid;
-          }
-          int jr = jl;
-          uint32_t id[kUnroll];
-          bool pass[kUnroll];
-          size_t at[kUnroll];
-          int jof[kUnroll];
-#pragma unroll
-          for (int u = 0; u < kUnroll; ++u) {
-            const uint32_t pos = b + 32u * u + uint32_t(lane);
-            const bool valid = pos < p_end;
-            if (valid)
-              while (ppre[jr + 1] <= pos) ++jr;
-            const uint4 ru = runs[jr];
-            const uint32_t o = pos - ppre[jr];
-            const uint32_t ap = o < ru.y ? ru.x + o : ru.z + (o - ru.y);
-            at[u] = size_t(jr) * n + ap;
-            jof[u] = jr;
-            id[u] = valid ? __ldg(P.ids + at[u]) : 0u;
-            pass[u] = valid;
-          }
-          if (P.filter) {
-            uint64_t hd[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-              const uint64_t sk = !pass[u] ? 0ull
-                                  : P.skc ? __ldg(P.skc + at[u])
-                                          : __ldg(P.sk + size_t(jof[u] % M) * n + id[u]);
-              hd[u] = sk ^ qsk[jof[u] % M];
-            }
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) pass[u] = pass[u] && __popcll(hd[u]) <= tau;
-          }
-#pragma unroll
-          for (int u = 0; u < kUnroll; ++u) {
-            const unsigned pm = __ballot_sync(kFull, pass[u]);
-            if (pass[u]) cbuf[nb + __popc(pm & lt_mask)] = id[u];
-            nb += __popc(pm);
-          }
-          if (lane == 0) ct.retrieved += min(kSpan, p_end - b);
-          __syncwarp();
-          if (nb > kFlushAt) {
-            if (lane == 0) ct.passed += uint32_t(nb);  // every buffered candidate passed the filter
-            wsize = flush_candidates<NT, NT2>(P, q, cbuf, nb, my_s, my_id, wsize, k, gkth, lane, ct);
-            nb = 0;
-          }
-        }
+        if (flat)
+          flat_stream<NT, NT2, U, QW>(P, q, qsk, runs, ppre, cbuf, my_s, my_id, j0, j1, tau, gkth, k, lane, warp, nb,
+                                      wsize, ct);
         // warp w takes chunks w, w + 4, ...: up to kSpan positions of one run,
         // lane-strided so that every load instruction is coalesced
         for (uint32_t c = cpre[j0] + uint32_t(warp); c < c_end; c += kQW) {

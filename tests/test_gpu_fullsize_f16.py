@@ -28,7 +28,7 @@ def big(orc):
     Qs = datagen.vmf_mixture(Q, D, COMP, KAPPA, seed=0, purpose="queries")
     Xd = torch.from_numpy(X).to(DEV)
     ix = pf.Index(Xd, "crosspolytope", budget_bytes=BUDGET, seed=0, rows="f16")
-    assert ix.L == orc.budget_L(orc.CROSSPOLYTOPE, N, D, 32, BUDGET, 0, 1) == 243
+    assert ix.L == orc.budget_L(orc.CROSSPOLYTOPE, N, D, 32, BUDGET, 0, 1) == 244
     return {"X": X, "Q": Qs, "Xd": Xd, "Qd": torch.from_numpy(Qs).to(DEV), "ix": ix}
 
 

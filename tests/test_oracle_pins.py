@@ -27,6 +27,8 @@ def test_gaussian_moments(orc):
     assert abs(S.var() - 1.0) < 5 * math.sqrt(2.0 / N)
     frac = np.mean(np.abs(S) < 1.0)
     assert abs(frac - 0.682689) < 5 * math.sqrt(0.6827 * 0.3173 / N)
+    # every entry is a bfloat16 value (the low 16 bits of its float32 are zero)
+    assert np.all(S.astype(np.float32).view(np.uint32) & 0xFFFF == 0)
     # different purposes / seeds give different streams
     assert orc.gauss(1, 1, 0, 0, 0) != orc.gauss(2, 1, 0, 0, 0)
     assert orc.gauss(1, 1, 0, 0, 0) != orc.gauss(1, 2, 0, 0, 0)
@@ -253,13 +255,14 @@ def test_budget_formula_values(orc):
     # hand-evaluated with the layouts stated in orc_budget_L
     n, d, M = 1_000_000, 100, 32
     dp, R = 112, 4 * 112
-    fixed_point = n * dp * 6 + n * M * 8 + 64 * M * dp * 8
-    per_point = n * 8 + 8193 * 4 + R * dp * 8
-    assert orc.budget_L(orc.CROSSPOLYTOPE, n, d, M, 4 << 30, 1) == ((4 << 30) - fixed_point) // per_point == 398
-    fixed_table = n * dp * 6 + 64 * M * dp * 8
-    per_table = n * 16 + 8193 * 4 + R * dp * 8
-    assert orc.budget_L(orc.CROSSPOLYTOPE, n, d, M, 4 << 30, 0) == ((4 << 30) - fixed_table) // per_table == 220
-    assert orc.budget_L(orc.SIMHASH, 10_000, 64, 32, 32 << 20, 1) == 202
+    # hyperplane entries are bfloat16 values: float32 + one exact bfloat16 copy = 6 bytes each
+    fixed_point = n * dp * 6 + n * M * 8 + 64 * M * dp * 6
+    per_point = n * 8 + 8193 * 4 + R * dp * 6
+    assert orc.budget_L(orc.CROSSPOLYTOPE, n, d, M, 4 << 30, 1) == ((4 << 30) - fixed_point) // per_point == 403
+    fixed_table = n * dp * 6 + 64 * M * dp * 6
+    per_table = n * 16 + 8193 * 4 + R * dp * 6
+    assert orc.budget_L(orc.CROSSPOLYTOPE, n, d, M, 4 << 30, 0) == ((4 << 30) - fixed_table) // per_table == 221
+    assert orc.budget_L(orc.SIMHASH, 10_000, 64, 32, 32 << 20, 1) == 210
     assert orc.budget_L(orc.SIMHASH, 10_000, 64, 32, 1 << 20, 0) == 0
     # pseudo-random CP: the hash functions are three sign vectors of d'' = 128
     # bits per function (4 words each) instead of d' x d' rows
@@ -274,10 +277,10 @@ def test_budget_with_binary16_rows(orc):
     # the 10M x 96 workload with binary16 rows (2 B) + the bfloat16 copy (2 B), 40 GiB, a sketch per entry
     n, d, M = 10_000_000, 96, 32
     dp, R = 96, 4 * 96  # CP with l = ceil(log2 192) = 8: 4 functions of 96 rows
-    fixed = n * dp * 4 + 64 * M * dp * 8
-    per_table = n * 16 + 8193 * 4 + R * dp * 8
+    fixed = n * dp * 4 + 64 * M * dp * 6
+    per_table = n * 16 + 8193 * 4 + R * dp * 6
     want = ((40 << 30) - fixed) // per_table
-    assert want == 243
+    assert want == 244
     assert orc.budget_L(orc.CROSSPOLYTOPE, n, d, M, 40 << 30, 0, 1) == want
     # float32 rows leave room for fewer repetitions
     assert orc.budget_L(orc.CROSSPOLYTOPE, n, d, M, 40 << 30, 0, 0) == ((40 << 30) - fixed - n * dp * 2) // per_table

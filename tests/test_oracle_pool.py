@@ -132,6 +132,6 @@ def test_pooled_index_meets_the_recall_target_with_the_filter_off(orc):
 def test_pooled_budget(orc):
     n, d, M = 1_000_000, 100, 32
     dp, F, m = 112, 4, 384
-    fixed = n * dp * 6 + 64 * M * dp * 8 + (m // F) * F * dp * dp * 8
+    fixed = n * dp * 6 + 64 * M * dp * 6 + (m // F) * F * dp * dp * 6
     per = n * 16 + 8193 * 4 + F * 4
     assert orc.budget_L(1, n, d, M, 4 << 30, 0, 0, 0, m) == ((4 << 30) - fixed) // per
