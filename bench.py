@@ -90,6 +90,8 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other two modes")
     ap.add_argument("--recall", type=float, default=None,
                     help="recall target 1 - delta passed to the index (default: the workload's)")
+    ap.add_argument("--learned-margin", type=int, default=None,
+                    help="bits added to the model's 5 %% stop-depth quantile to make the start depth (default 6)")
     ap.add_argument("--flat-fill", type=int, default=None,
                     help="override the tuned streaming rule of the search kernel (0: chunks of one run; F: flat "
                          "when the chunks are less than 1/F full)")
@@ -642,6 +644,8 @@ def main():
                                         seed=rank)
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
+        if args.learned_margin is not None:
+            ix.learned_start_rule(0.05, args.learned_margin)
 
     # launch shape of the search kernel: timed on a separate query set of the
     # same distribution (the tuner's choice changes no result)

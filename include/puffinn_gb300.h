@@ -270,6 +270,15 @@ pf_status pf_learned_train(pf_index* index, const float* train_queries, int64_t 
  * device).  PF_ERR_NOT_TRAINED without a model. */
 pf_status pf_learned_predict(pf_index* index, const float* queries, int64_t Q, int32_t* start_depth, void* stream);
 
+/* The rule that turns the model's distribution over stop depths into a start
+ * depth: the smallest depth q with P(stop depth > q) <= tail, plus `margin`
+ * bits, capped at K (defaults 0.05 and 6).  A lower start costs only time (the
+ * first round takes the whole block at its depth), never recall.  Applies to
+ * later predictions and searches; not while plans exist (they captured the
+ * rule).  Errors: PF_ERR_INVALID_ARG (tail outside (0, 1), margin outside
+ * [0, 32], plans exist). */
+pf_status pf_learned_set_start_rule(pf_index* index, float tail, int32_t margin);
+
 /* One forward + backward pass of the start-depth perceptron on caller data
  * (all device pointers, float32, row-major): X [B][F], y [B] class labels in
  * [0, C), W1 [H][F], b1 [H], W2 [C][H], b2 [C].  Writes the mean

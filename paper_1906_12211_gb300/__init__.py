@@ -118,6 +118,7 @@ def lib():
                 "pf_index_last_timing": (i32, [vp, vp, i32]),
                 "pf_learned_train": (i32, [vp, vp, i64, i32, C.c_double, i32, C.c_uint64, vp, vp]),
                 "pf_learned_predict": (i32, [vp, vp, i64, vp, vp]),
+                "pf_learned_set_start_rule": (i32, [vp, C.c_float, i32]),
                 "pf_mlp_forward_backward": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                                   vp]),
                 "pf_index_array": (i32, [vp, i32, vp, vp]),
@@ -343,6 +344,10 @@ class Index:
         """pf_index_selftest_timeout: hash with the weight loads withheld; raises
         PuffinnError(PF_ERR_DEVICE_TIMEOUT) when the bounded waits work."""
         _check(lib().pf_index_selftest_timeout(self._h, _ptr(queries), int(queries.shape[0]), _stream_ptr(stream)))
+
+    def learned_start_rule(self, tail: float = 0.05, margin: int = 6):
+        """pf_learned_set_start_rule: start = the tail-quantile depth + margin."""
+        _check(lib().pf_learned_set_start_rule(self._h, float(tail), int(margin)))
 
     def count_range_paths(self, enable: bool = True):
         """pf_index_count_range_paths: the counts since the last call (range

@@ -211,8 +211,8 @@ void predict_ws(pf_index* ix, pf_workspace& ws, int64_t Q, cudaStream_t s) {
   const int F = ix->mlp_F, H = kMlpHidden, C = ix->mlp_C;
   const float* b1 = ix->mlp_w + size_t(H) * F;
   const float* b2 = b1 + H + size_t(C) * H;
-  PF_CK(mlp_predict(ws.qx, ws.qsk, int(Q), ix->lay.d_pad, ix->M, ix->mlp_w1h, b1, ix->mlp_w2h, b2, C, kMlpTail,
-                    kMlpMargin, ws.start, s));
+  PF_CK(mlp_predict(ws.qx, ws.qsk, int(Q), ix->lay.d_pad, ix->M, ix->mlp_w1h, b1, ix->mlp_w2h, b2, C, ix->mlp_tail,
+                    ix->mlp_margin, ws.start, s));
 }
 
 const float* stage_queries(pf_index* ix, const float* queries, int64_t Q, cudaStream_t s) {
@@ -866,7 +866,7 @@ pf_status pf_learned_train(pf_index* ix, const float* train_queries, int64_t Qt,
           PF_CK(cudaMemcpyAsync(sd.data(), ws.start, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, s));
           PF_CK(cudaStreamSynchronize(s));
           for (int64_t i = 0; i < nq; ++i) {
-            covered += sd[i] - kMlpMargin >= hy[q0 + i] || sd[i] == ix->lay.Kb ? 1 : 0;
+            covered += sd[i] - ix->mlp_margin >= hy[q0 + i] || sd[i] == ix->lay.Kb ? 1 : 0;
             sum_start += sd[i];
             sum_stop += hy[q0 + i];
           }
@@ -929,6 +929,18 @@ pf_status pf_index_selftest_timeout(pf_index* ix, const float* queries, int64_t 
     ix->hold_weight_loads = 0;
     PF_CK(cudaGetLastError());
     if (device_timed_out(ix)) return fail(PF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out");
+    return PF_OK;
+  });
+}
+
+pf_status pf_learned_set_start_rule(pf_index* ix, float tail, int32_t margin) {
+  return guarded([&]() -> pf_status {
+    if (!ix) return fail(PF_ERR_INVALID_ARG, "null index");
+    if (!(tail > 0.f && tail < 1.f) || margin < 0 || margin > 32)
+      return fail(PF_ERR_INVALID_ARG, "tail must be in (0, 1) and margin in [0, 32]");
+    if (ix->live_plans > 0) return fail(PF_ERR_INVALID_ARG, "search plans bound to the index exist");
+    ix->mlp_tail = tail;
+    ix->mlp_margin = margin;
     return PF_OK;
   });
 }

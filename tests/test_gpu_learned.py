@@ -126,3 +126,23 @@ def test_predict_forward_equals_float64_oracle(trained, orc):
     near = np.any(np.abs(A - 0.05) < 1e-4, axis=1)
     assert np.all((got == want) | near), np.nonzero((got != want) & ~near)
     assert np.mean(got == want) >= 0.98
+
+
+def test_start_rule_moves_the_start_and_keeps_the_results_equal_to_the_oracle(trained):
+    """A smaller margin starts deeper in the schedule's order (a lower prefix
+    length): the search still equals the oracle at the predicted depths."""
+    ix, o, _, _, Q = trained
+    qd = torch.from_numpy(Q).to(DEV)
+    base = ix.learned_predict(qd).cpu().numpy()
+    try:
+        ix.learned_start_rule(0.05, 2)
+        low = ix.learned_predict(qd).cpu().numpy()
+        assert np.all(low <= base) and np.any(low < base)
+        ids, sims, st = ix.search(qd, 10, 0.9, learned=True, stats=True)
+        ref = o.search(Q, 10, 0.9, start_depth=low)
+        assert np.array_equal(ids.cpu().numpy().view(np.uint32), ref["ids"])
+        assert np.array_equal(sims.cpu().numpy(), ref["sims"])
+        with pytest.raises(pf.PuffinnError):
+            ix.learned_start_rule(1.5, 2)
+    finally:
+        ix.learned_start_rule(0.05, 6)
