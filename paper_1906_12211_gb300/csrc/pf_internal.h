@@ -156,8 +156,8 @@ struct pf_index {
   pf_workspace ws;
   // start-depth model: params = [W1 (H x F) | b1 (H) | W2 (C x H) | b2 (C)], float32
   int mlp_trained = 0, mlp_F = 0, mlp_C = 0;
-  float mlp_tail = kMlpTail;  // start rule: smallest q with P(stop depth > q) <= tail ...
-  int mlp_margin = kMlpMargin;  // ... plus this many bits (capped at K)
+  float mlp_tail = pf::kMlpTail;  // start rule: smallest q with P(stop depth > q) <= tail ...
+  int mlp_margin = pf::kMlpMargin;  // ... plus this many bits (capped at K)
   float* mlp_w = nullptr;
   __nv_bfloat16* mlp_w1h = nullptr;  // bfloat16 W1 for inference, transposed: [F][H]
   __nv_bfloat16* mlp_w2h = nullptr;  // bfloat16 W2 for inference
