@@ -16,10 +16,12 @@ size_t search_smem(int d_pad, int L, int M, int k_max, int U, int QW) {
          size_t(cand_buf(U)) * 4 * QW;
 }
 
-// 8 warps per query only with 8 positions per lane
-skern::Kernel pick_search_kernel(int d_pad, int U, int QW) {
-  if (QW == 8) return skern::pick_u8w8(d_pad);
-  return U == 4 ? skern::pick_u4w4(d_pad) : skern::pick_u8w4(d_pad);
+// 8 warps per query only with 8 positions per lane; a shape with flat_fill > 0
+// takes the instantiation that can stream rounds flat
+skern::Kernel pick_search_kernel(int d_pad, int U, int QW, bool flat) {
+  if (QW == 8) return flat ? skern::pick_u8w8_flat(d_pad) : skern::pick_u8w8(d_pad);
+  if (U == 4) return flat ? skern::pick_u4w4_flat(d_pad) : skern::pick_u4w4(d_pad);
+  return flat ? skern::pick_u8w4_flat(d_pad) : skern::pick_u8w4(d_pad);
 }
 
 }  // namespace
@@ -71,7 +73,7 @@ cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t 
   P.flat_fill = sh.flat_fill;
   const int U = sh.unroll == 4 ? 4 : 8, QW = sh.warps == 8 ? 8 : 4;
   const size_t smem = search_smem(P.d_pad, P.L, P.M, P.k_max, U, QW);
-  skern::Kernel kern = pick_search_kernel(P.d_pad, U, QW);
+  skern::Kernel kern = pick_search_kernel(P.d_pad, U, QW, sh.flat_fill > 0);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -88,7 +90,7 @@ cudaError_t launch_search(const pf_index* ix, const SearchArgs& a, cudaStream_t 
 int search_max_ctas_per_sm(const pf_index* ix, int k_max, int unroll, int warps) {
   const int U = unroll == 4 ? 4 : 8, QW = warps == 8 ? 8 : 4;
   const size_t smem = search_smem(ix->lay.d_pad, ix->L, ix->M, k_max, U, QW);
-  skern::Kernel kern = pick_search_kernel(ix->lay.d_pad, U, QW);
+  skern::Kernel kern = pick_search_kernel(ix->lay.d_pad, U, QW, false);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * QW, smem) != cudaSuccess) return 0;

@@ -5,7 +5,7 @@
 namespace pf {
 namespace skern {
 
-Kernel pick_u8w4(int d_pad) { return pick_nt<8, 4>(d_pad); }
+Kernel pick_u8w4(int d_pad) { return pick_nt<8, 4, false>(d_pad); }
 
 }  // namespace skern
 }  // namespace pf

@@ -454,10 +454,11 @@ __device__ __forceinline__ int flush_candidates(const Dev& P, const float* q, ui
 // takes the spans of kSpan consecutive positions warp, warp + QW, ... of the
 // group's runs laid end to end (repetition by repetition, left run before right
 // run); a lane finds the repetition of its first position by binary search over
-// ppre (the position prefix), then walks on.  Kept out of line so that the
-// chunked loop, the common case, is compiled as if this did not exist.
+// ppre (the position prefix), then walks on.  Only the kernel instantiations
+// with FLAT = true contain it, so that the chunked loop, the common case, is
+// compiled as if this did not exist.
 template <int NT, int NT2, int U, int QW>
-__device__ __noinline__ void flat_stream(const Dev& P, const float* q, const uint64_t* qsk, const uint4* runs,
+__device__ __forceinline__ void flat_stream(const Dev& P, const float* q, const uint64_t* qsk, const uint4* runs,
                                          const uint32_t* ppre, uint32_t* cbuf, float* my_s, uint32_t* my_id, int j0,
                                          int j1, int tau, float gkth, int k, int lane, int warp, int& nb_io,
                                          int& wsize_io, Counters& ct) {
@@ -528,7 +529,9 @@ __device__ __noinline__ void flat_stream(const Dev& P, const float* q, const uin
 // NT = d_pad / 32 rounded up: float4 chunks of a float32 row per lane of an
 // 8-lane group; NT2 = d_pad / 16 rounded up: 16-byte chunks of a bfloat16 row
 // per lane of a pair
-template <int NT, int NT2, int U, int QW>
+// FLAT: the instantiation that can stream a round flat (the launch shape's
+// flat_fill > 0); the others never do and carry none of its code
+template <int NT, int NT2, int U, int QW, bool FLAT>
 __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
   constexpr int kQW = QW;
   constexpr int kThreads = 32 * QW;
@@ -758,41 +761,43 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
       }
       // exclusive scans over the repetitions of the chunk counts -> cpre and
       // of the new positions -> ppre
-      uint32_t inc = my_chunks, pinc = P.flat_fill > 0 ? my_pos : 0u;
+      uint32_t inc = my_chunks, pinc = FLAT ? my_pos : 0u;
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
         const uint32_t v = __shfl_up_sync(kFull, inc, off);
-        const uint32_t pv = __shfl_up_sync(kFull, pinc, off);
-        if (lane >= off) {
-          inc += v;
-          pinc += pv;
+        if (lane >= off) inc += v;
+        if constexpr (FLAT) {
+          const uint32_t pv = __shfl_up_sync(kFull, pinc, off);
+          if (lane >= off) pinc += pv;
         }
       }
       if (lane == 31) {
         s_scan[warp] = inc;
-        s_pscan[warp] = pinc;
+        if constexpr (FLAT) s_pscan[warp] = pinc;
       }
       __syncthreads();
       uint32_t run = inc - my_chunks, prun = pinc - my_pos;
       for (int w = 0; w < warp; ++w) {
         run += s_scan[w];
-        prun += s_pscan[w];
+        if constexpr (FLAT) prun += s_pscan[w];
       }
       for (int j = jlo; j < jhi; ++j) {
         cpre[j] = run;
-        ppre[j] = prun;
         const uint4 ru = runs[j];
         run += (ru.y + kSpan - 1) / kSpan + (ru.w + kSpan - 1) / kSpan;
-        prun += ru.y + ru.w;
+        if constexpr (FLAT) {
+          ppre[j] = prun;
+          prun += ru.y + ru.w;
+        }
       }
       if (tid == kThreads - 1) {
         cpre[L] = run;
-        ppre[L] = prun;
+        if constexpr (FLAT) ppre[L] = prun;
       }
       __syncthreads();
       // short runs leave most of a chunk's lanes idle: the round then streams
       // its positions as one flat sequence instead (the same candidates)
-      const bool flat = P.flat_fill > 0 && uint64_t(cpre[L]) * kSpan > uint64_t(P.flat_fill) * ppre[L];
+      const bool flat = FLAT && P.flat_fill > 0 && uint64_t(cpre[L]) * kSpan > uint64_t(P.flat_fill) * ppre[L];
       if (P.path_count && tid == 0) atomicAdd(P.path_count + (flat ? 4 : 3), 1ull);  // diagnostics only
 
       // ---- stream the chunks, group by group
@@ -814,9 +819,11 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
         int jc = j0;
         uint64_t qh = qsk[j0 % M];  // the query's sketch for repetition jc
         int nb = 0;
-        if (flat)
-          flat_stream<NT, NT2, U, QW>(P, q, qsk, runs, ppre, cbuf, my_s, my_id, j0, j1, tau, gkth, k, lane, warp, nb,
-                                      wsize, ct);
+        if constexpr (FLAT) {
+          if (flat)
+            flat_stream<NT, NT2, U, QW>(P, q, qsk, runs, ppre, cbuf, my_s, my_id, j0, j1, tau, gkth, k, lane, warp,
+                                        nb, wsize, ct);
+        }
         // warp w takes chunks w, w + 4, ...: up to kSpan positions of one run,
         // lane-strided so that every load instruction is coalesced
         for (uint32_t c = cpre[j0] + uint32_t(warp); c < c_end; c += kQW) {
@@ -976,20 +983,23 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
 using Kernel = void (*)(Dev);
 
 // the instantiation for d_pad (NT = d_pad / 32 rounded up to a power of two)
-template <int U, int QW>
+template <int U, int QW, bool FLAT>
 Kernel pick_nt(int d_pad) {
   const int nt = (d_pad + 31) / 32;
-  return nt <= 1   ? search_kernel<1, 2, U, QW>
-         : nt <= 2 ? search_kernel<2, 4, U, QW>
-         : nt <= 4 ? search_kernel<4, 8, U, QW>
-         : nt <= 8 ? search_kernel<8, 16, U, QW>
-                   : search_kernel<16, 32, U, QW>;
+  return nt <= 1   ? search_kernel<1, 2, U, QW, FLAT>
+         : nt <= 2 ? search_kernel<2, 4, U, QW, FLAT>
+         : nt <= 4 ? search_kernel<4, 8, U, QW, FLAT>
+         : nt <= 8 ? search_kernel<8, 16, U, QW, FLAT>
+                   : search_kernel<16, 32, U, QW, FLAT>;
 }
 
-// defined one per translation unit (kernels_search_u*w*.cu)
+// defined one per translation unit (kernels_search_u*w*[_flat].cu)
 Kernel pick_u8w4(int d_pad);
 Kernel pick_u4w4(int d_pad);
 Kernel pick_u8w8(int d_pad);
+Kernel pick_u8w4_flat(int d_pad);
+Kernel pick_u4w4_flat(int d_pad);
+Kernel pick_u8w8_flat(int d_pad);
 
 }  // namespace skern
 }  // namespace pf
