@@ -91,7 +91,7 @@ def parse():
     ap.add_argument("--recall", type=float, default=None,
                     help="recall target 1 - delta passed to the index (default: the workload's)")
     ap.add_argument("--learned-margin", type=int, default=None,
-                    help="bits added to the model's 5 %% stop-depth quantile to make the start depth (default 6)")
+                    help="bits added to the model's 5 %% stop-depth quantile to make the start depth (default 0)")
     ap.add_argument("--flat-fill", type=int, default=None,
                     help="override the tuned streaming rule of the search kernel (0: chunks of one run; F: flat "
                          "when the chunks are less than 1/F full)")
@@ -197,7 +197,9 @@ def search_kernel_traffic(args=None):
                              or args.recall != 0.9 or getattr(args, "workload", WORKLOAD) != WORKLOAD
                              or getattr(args, "family", "crosspolytope") != "crosspolytope"
                              or getattr(args, "estimate", "bf16") != "bf16" or getattr(args, "stop_every", 0)
-                             or getattr(args, "pool_bits", 0) or getattr(args, "filter_eps", 0.0)):
+                             or getattr(args, "pool_bits", 0) or getattr(args, "filter_eps", 0.0)
+                             or getattr(args, "learned_margin", None) is not None
+                             or getattr(args, "flat_fill", None) is not None):
         return None
     path = os.path.join(ROOT, "profiles", "search_kernel_traffic.txt")
     src = os.path.join(ROOT, "paper_1906_12211_gb300", "csrc", "search_kernel.cuh")
@@ -272,18 +274,22 @@ def brute_force_kth(torch, Xd, Qd, k):
     return torch.cat(out)
 
 
-def algorithmic_bytes(st, L, n, d, k, mode):
-    """Bytes a query must touch (per query, averaged): prefix lookups and the
-    binary search for every repetition, id + sketch per retrieved candidate
-    (the per-repetition sketch layout), the row of every scored candidate
-    (bf16, e4m3 + its 8-byte scale and bound, or fp32), the fp32 row of every
-    reranked one, the query and the output."""
+def algorithmic_bytes(st, L, n, d, k, mode, code_bytes=4):
+    """Bytes a query must touch (per query, averaged), the search's per-query
+    count: a prefix-table lookup and a binary search of the codes for every
+    repetition, id + code + sketch (4 + 4 + 8 bytes) per retrieved entry, the
+    row of every candidate that passed the filter (bf16 or binary16: 2d, e4m3:
+    d + its 8-byte scale and bound, fp32: 4d), the fp32 row of every reranked
+    one, the query and the output.  code_bytes=0 gives the narrower count of
+    what this kernel's layout must read (it never reads a retrieved entry's
+    code: sketches sit beside the ids)."""
     import math
 
     probes = max(1, math.ceil(math.log2(max(2, n / 8192))))
-    per_row = {"bf16": d * 2, "fp8": d + 8}.get(mode, d * 4)
-    b = (L * (8 + probes * 4) + st["retrieved"].astype(np.float64) * (4 + 8)
-         + st["scored"].astype(np.float64) * per_row + st["reranked"].astype(np.float64) * d * 4 + d * 4 + k * 8)
+    per_row = {"bf16": d * 2, "f16": d * 2, "fp8": d + 8}.get(mode, d * 4)
+    b = (L * (8 + probes * 4) + st["retrieved"].astype(np.float64) * (4 + code_bytes + 8)
+         + st["passed_filter"].astype(np.float64) * per_row + st["reranked"].astype(np.float64) * d * 4
+         + d * 4 + k * 8)
     return float(b.mean())
 
 
@@ -450,6 +456,8 @@ def run_extra(args):
                          0.9 if args.recall is None else args.recall, epochs=args.epochs, seed=0)
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
+        if args.learned_margin is not None:
+            ix.learned_start_rule(0.05, args.learned_margin)
     ix.tune(Qd[: min(Qn, 20_000)], 10 if name == "vmf4k-n2m-d128-mixed" else int(w["k"]),
             0.9 if args.recall is None else args.recall, scoring=sc, learned=learned)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -819,10 +827,15 @@ def main():
     kern_s = seq["kernel_ms"] / 1e3
     achieved = per_q * Q / kern_s / 1e9
     traffic = search_kernel_traffic(args)
+    narrow = algorithmic_bytes(stats1, ix.L, ix.n, ix.d, k, sc, code_bytes=0) * Q
     roofline = {"bound": "hbm", "kernel": "search_kernel", "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "algorithmic_bytes_per_launch": per_q * Q, "kernel_ms": seq["kernel_ms"],
-                "query_hash_ms": seq["query_hash_ms"]}
+                "query_hash_ms": seq["query_hash_ms"],
+                "without_codes": {"algorithmic_bytes_per_launch": narrow,
+                                  "frac": narrow / kern_s / 1e9 / peak,
+                                  "note": "the same count without the 4-byte code per retrieved entry, which "
+                                          "this layout never reads"}}
 
     cpu = None
     if args.family == "fht":  # the oracle states this family in numpy: far too slow for a full-size index

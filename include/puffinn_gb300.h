@@ -272,7 +272,7 @@ pf_status pf_learned_predict(pf_index* index, const float* queries, int64_t Q, i
 
 /* The rule that turns the model's distribution over stop depths into a start
  * depth: the smallest depth q with P(stop depth > q) <= tail, plus `margin`
- * bits, capped at K (defaults 0.05 and 6).  A lower start costs only time (the
+ * bits, capped at K (defaults 0.05 and 0).  A lower start costs only time (the
  * first round takes the whole block at its depth), never recall.  Applies to
  * later predictions and searches; not while plans exist (they captured the
  * rule).  Errors: PF_ERR_INVALID_ARG (tail outside (0, 1), margin outside
@@ -396,16 +396,15 @@ void pf_search_plan_free(pf_search_plan* plan);
  * kernel's weight-tile loads withheld, so that the waits on them expire (about
  * 1 s), and returns what the library reports for it: PF_ERR_DEVICE_TIMEOUT
  * when the time-out path works.  No output is written.  Errors:
- * PF_ERR_INVALID_ARG (null argument, Q < 1, an index hashed without the
- * tensor-core kernel (d' > 128), or search plans bound to the index), CUDA. */
+ * PF_ERR_INVALID_ARG (null argument, Q < 1, or search plans bound to the
+ * index), CUDA. */
 pf_status pf_index_selftest_timeout(pf_index* index, const float* queries, int64_t Q, void* stream);
 /* Withhold (hold != 0) or restore (hold == 0) the weight-tile loads of every
  * later tensor-core hashing launch of this index, so that a whole entry point
  * (pf_index_search, pf_index_search_noalloc, ...) can be driven through its
  * time-out path: while held, each such call returns PF_ERR_DEVICE_TIMEOUT
  * after about 1 s, with its outputs unspecified.  Captured plans keep the
- * setting they were captured with.  Errors: PF_ERR_INVALID_ARG (null index,
- * or an index hashed without the tensor-core kernel). */
+ * setting they were captured with.  Errors: PF_ERR_INVALID_ARG (null index). */
 pf_status pf_index_selftest_hold(pf_index* index, int32_t hold);
 
 /* ---- Diagnostics of the search kernel's range pass (Sec. 4.2 "Retrieving

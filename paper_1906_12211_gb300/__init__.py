@@ -345,7 +345,7 @@ class Index:
         PuffinnError(PF_ERR_DEVICE_TIMEOUT) when the bounded waits work."""
         _check(lib().pf_index_selftest_timeout(self._h, _ptr(queries), int(queries.shape[0]), _stream_ptr(stream)))
 
-    def learned_start_rule(self, tail: float = 0.05, margin: int = 6):
+    def learned_start_rule(self, tail: float = 0.05, margin: int = 0):
         """pf_learned_set_start_rule: start = the tail-quantile depth + margin."""
         _check(lib().pf_learned_set_start_rule(self._h, float(tail), int(margin)))
 

@@ -127,7 +127,7 @@ void alloc_ws(pf_index* ix, pf_workspace& ws, size_t q, size_t km) {
   dalloc(&ws.stats, q);
   dalloc(&ws.counter, 64);
   dalloc(&ws.cos_eps, 65);
-  dalloc(&ws.rq, recheck_capacity(int64_t(q)));
+  dalloc(&ws.rq, recheck_capacity(ix, int64_t(q), ix->pool_tables > 0 ? ix->pool_tables : ix->L));
   dalloc(&ws.rq_count, size_t(ix->num_sms));
   ws.cap_q = q;
   ws.cap_kmax = km;
@@ -198,12 +198,12 @@ void hash_queries_ws(pf_index* ix, pf_workspace& ws, const float* qdev, int64_t 
   PF_CK(launch_normalize(qdev, Q, ix->d, ix->lay.d_pad, ws.qx, ws.qxh, ws.qxl, s));
   if (ix->pool_tables > 0) {  // the pool's functions once, then each table's subset
     PF_CK(launch_hash(ix, ws.qx, ws.qxh, ws.qxl, Q, ws.qgcodes, 1, ix->pool_tables, ws.qsk, 1, ix->M, ws.rq,
-                      ws.rq_count, recheck_capacity(Q), s, ix->pool_tables));
+                      ws.rq_count, recheck_capacity(ix, Q, ix->pool_tables), s, ix->pool_tables));
     PF_CK(launch_pool_gather(ix, ws.qgcodes, 1, ix->pool_tables, Q, ws.qcodes, 1, ix->L, s));
     return;
   }
   PF_CK(launch_hash(ix, ws.qx, ws.qxh, ws.qxl, Q, ws.qcodes, 1, ix->L, ws.qsk, 1, ix->M, ws.rq, ws.rq_count,
-                    recheck_capacity(Q), s));
+                    recheck_capacity(ix, Q, ix->L), s));
 }
 
 // start depths of the model for the Q hashed queries of the workspace -> ws.start
@@ -419,16 +419,17 @@ pf_status pf_index_build(const pf_build_params* prm, const void* points, pf_inde
           PF_CK(launch_round_rows_f16(x32, n, dp, ix->xf16, ix->x16, xlo, s));
         if (ix->x8) PF_CK(launch_quantize_fp8(x32, n, prm->d, dp, ix->x8, ix->x8_meta, s));
         dalloc(&raw_codes, size_t(n) * ix->L);
-        dalloc(&rq, recheck_capacity(n));
+        const int hashed_tables = ix->pool_tables > 0 ? ix->pool_tables : ix->L;
+        dalloc(&rq, recheck_capacity(ix, n, hashed_tables));
         dalloc(&rq_count, size_t(ix->num_sms));
         if (ix->pool_tables > 0) {  // the pool's functions once, then each table's subset
           dalloc(&gcodes, size_t(n) * ix->pool_tables);
-          PF_CK(launch_hash(ix, x32, ix->x16, xlo, n, gcodes, n, 1, sk_out, n, 1, rq, rq_count, recheck_capacity(n), s,
-                            ix->pool_tables));
+          PF_CK(launch_hash(ix, x32, ix->x16, xlo, n, gcodes, n, 1, sk_out, n, 1, rq, rq_count,
+                            recheck_capacity(ix, n, hashed_tables), s, ix->pool_tables));
           PF_CK(launch_pool_gather(ix, gcodes, n, 1, n, raw_codes, n, 1, s));
         } else {
           PF_CK(launch_hash(ix, x32, ix->x16, xlo, n, raw_codes, n, 1, sk_out, n, 1, rq, rq_count,
-                            recheck_capacity(n), s));
+                            recheck_capacity(ix, n, hashed_tables), s));
         }
         PF_CK(sort_tables(ix, raw_codes, s));
         if (ix->skc) PF_CK(gather_table_sketches(ix, sk_out, ix->skc, s));
@@ -913,7 +914,6 @@ pf_status pf_index_selftest_timeout(pf_index* ix, const float* queries, int64_t 
   return guarded([&]() -> pf_status {
     if (!ix || !queries) return fail(PF_ERR_INVALID_ARG, "null argument");
     if (Q < 1 || Q > 0x7fffffffLL) return fail(PF_ERR_INVALID_ARG, "Q out of range");
-    if (!hash_tc_supported(ix)) return fail(PF_ERR_INVALID_ARG, "this index hashes without the tensor-core kernel");
     if (ix->live_plans > 0) return fail(PF_ERR_INVALID_ARG, "search plans bound to the index exist");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PF_CK(cudaSetDevice(ix->device));
@@ -971,7 +971,6 @@ pf_status pf_index_count_range_paths(pf_index* ix, int32_t enable, uint64_t* cou
 pf_status pf_index_selftest_hold(pf_index* ix, int32_t hold) {
   return guarded([&]() -> pf_status {
     if (!ix) return fail(PF_ERR_INVALID_ARG, "null index");
-    if (!hash_tc_supported(ix)) return fail(PF_ERR_INVALID_ARG, "this index hashes without the tensor-core kernel");
     ix->hold_weight_loads = hold ? 1 : 0;
     return PF_OK;
   });

@@ -97,207 +97,6 @@ cudaError_t launch_normalize(const float* in, int64_t rows, int d, int d_pad, fl
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Hashing.  Each CTA takes 128 points (one per thread) and one group of hash
-// rows: a whole repetition (CP: fns functions of d_pad rows; HP: 32 rows) or
-// one 64-row sketch.  Projections are float32 fused multiply-adds; their error
-// is below d*2^-24*|a|*|x| (<= 2^-15 |a| for d <= 320), far inside the recheck
-// band thr = 2^-12 |a|.  A decision closer to its boundary than the band is
-// recomputed in float64 in index order, which is the defining value:
-//   HP / sketch bit  = [<a, x> >= 0]
-//   CP value         = (sign << (l-1)) | argmax_c |<a_c, x>|, first c on ties
-// For CP the four largest |v| are kept; if the runner-up is within 2*band of
-// the best, the candidates within 2*band are recomputed in float64 (all d rows
-// when a fifth could be in the band).
-// ---------------------------------------------------------------------------
-constexpr int kHashPts = 128;
-constexpr int kHashGroups = 2;  // groups of hash rows per CTA, one per set of kHashPts threads
-constexpr int kHashChunk = 16;  // hash rows of a group staged in shared memory at a time
-constexpr int kRowBlock = 8;    // rows whose projections a thread accumulates together
-
-__device__ __forceinline__ double dot64(const float* __restrict__ a, const float* __restrict__ x, int d) {
-  double s = 0.0;
-  for (int i = 0; i < d; ++i) s = __dadd_rn(s, __dmul_rn(double(a[i]), double(x[i])));
-  return s;
-}
-
-// the four largest |v| (a[0] >= ... >= a[3]) and their rows, in registers
-struct Top4 {
-  float a[4];
-  int c[4];
-  __device__ __forceinline__ void reset() {
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      a[t] = -1.f;
-      c[t] = 0;
-    }
-  }
-  __device__ __forceinline__ void push(float v, int cc) {
-    if (!(v > a[3])) return;
-    if (v > a[2]) {
-      a[3] = a[2];
-      c[3] = c[2];
-      if (v > a[1]) {
-        a[2] = a[1];
-        c[2] = c[1];
-        if (v > a[0]) {
-          a[1] = a[0];
-          c[1] = c[0];
-          a[0] = v;
-          c[0] = cc;
-        } else {
-          a[1] = v;
-          c[1] = cc;
-        }
-      } else {
-        a[2] = v;
-        c[2] = cc;
-      }
-    } else {
-      a[3] = v;
-      c[3] = cc;
-    }
-  }
-};
-
-__global__ void __launch_bounds__(kHashPts * kHashGroups) hash_simt_kernel(
-    const float* __restrict__ x32, int64_t npts, int d, int d_pad, int family, int L, int M, int fns, int ell,
-    int rows_table, const float* __restrict__ W, const float* __restrict__ thr, uint32_t* __restrict__ codes,
-    int64_t cj, int64_t cp, uint64_t* __restrict__ sk, int64_t sm, int64_t sp) {
-  extern __shared__ float smem[];
-  const int xs = d_pad + 4;                 // row stride: float4 reads of 8 lanes hit 32 distinct banks
-  // the CTA's kHashPts points are shared by its kHashGroups sets of threads;
-  // set h hashes them with group blockIdx.y * kHashGroups + h
-  const int h = threadIdx.x / kHashPts, tid = threadIdx.x % kHashPts;
-  float* xS = smem;                                   // [kHashPts][d_pad + 4] this CTA's points
-  float* wS = smem + kHashPts * xs + h * kHashChunk * d_pad;  // [kHashChunk][d_pad] this set's rows
-  const int64_t p0 = int64_t(blockIdx.x) * kHashPts;
-  const int64_t p = p0 + tid;
-  const int g = blockIdx.y * kHashGroups + h;
-  const bool is_table = g < L, live_g = g < L + M;
-  const int q4 = d_pad / 4;
-
-  for (int e = threadIdx.x; e < kHashPts * q4; e += kHashPts * kHashGroups) {
-    const int pt = e / q4, i4 = e % q4;
-    const int64_t pp = p0 + pt;
-    reinterpret_cast<float4*>(xS + pt * xs)[i4] =
-        pp < npts ? __ldg(reinterpret_cast<const float4*>(x32 + pp * d_pad) + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-
-  const int64_t row0 = is_table ? int64_t(g) * rows_table : int64_t(L) * rows_table + int64_t(g - L) * 64;
-  const int nrows = !live_g ? 0 : is_table ? rows_table : 64;
-  // every set runs as many chunks as the longest group of the CTA (barriers)
-  int max_rows = 0;
-  for (int u = 0; u < kHashGroups; ++u) {
-    const int gu = blockIdx.y * kHashGroups + u;
-    max_rows = max(max_rows, gu < L ? rows_table : gu < L + M ? 64 : 0);
-  }
-  const float* xrow = x32 + (p < npts ? p : 0) * d_pad;
-  const float4* xv4 = reinterpret_cast<const float4*>(xS + tid * xs);
-
-  uint32_t code = 0;
-  uint64_t bits = 0;
-  Top4 top;
-  top.reset();
-  float best_v = 0.f;
-  int fn = 0;
-
-  // the decision for row r of the group from its float32 projection v (rows in order)
-  auto row_done = [&](int r, float v) {
-    const int64_t grow = row0 + r;
-    if (!is_table || family == PF_SIMHASH) {
-      bool bit = v >= 0.f;
-      if (fabsf(v) < thr[grow] && p < npts) bit = dot64(W + grow * d_pad, xrow, d) >= 0.0;
-      if (is_table) {
-        code |= (bit ? 1u : 0u) << (31 - r);
-      } else if (bit) {
-        bits |= uint64_t(1) << r;
-      }
-      return;
-    }
-    const int c = r - fn * d_pad;
-    if (c < d) {
-      const float av = fabsf(v);
-      if (av > top.a[0]) best_v = v;
-      top.push(av, c);
-    }
-    if (c == d_pad - 1) {  // function complete
-      const float band = thr[grow];
-      int arg = top.c[0];
-      bool neg = best_v < 0.f;
-      if ((top.a[1] >= top.a[0] - 2.f * band || top.a[0] < band) && p < npts) {
-        const float* wf = W + (row0 + int64_t(fn) * d_pad) * d_pad;
-        double bestabs = -1.0, bestval = 0.0;
-        int besti = 0;
-        if (top.a[3] >= top.a[0] - 2.f * band) {
-          for (int cc = 0; cc < d; ++cc) {
-            const double v64 = dot64(wf + int64_t(cc) * d_pad, xrow, d);
-            if (fabs(v64) > bestabs) {
-              bestabs = fabs(v64);
-              bestval = v64;
-              besti = cc;
-            }
-          }
-        } else {
-          for (int t = 0; t < 4; ++t) {
-            if (top.a[t] < top.a[0] - 2.f * band) continue;
-            const int cc = top.c[t];
-            const double v64 = dot64(wf + int64_t(cc) * d_pad, xrow, d);
-            const double av = fabs(v64);
-            if (av > bestabs || (av == bestabs && cc < besti)) {
-              bestabs = av;
-              bestval = v64;
-              besti = cc;
-            }
-          }
-        }
-        arg = besti;
-        neg = bestval < 0.0;
-      }
-      const uint32_t value = ((neg ? 1u : 0u) << (ell - 1)) | uint32_t(arg);
-      code |= value << (32 - ell * (fn + 1));
-      ++fn;
-      top.reset();
-    }
-  };
-
-  // kRowBlock rows at a time: one float4 of the point and one (broadcast) of
-  // each row per step, 4 * kRowBlock fused multiply-adds.  Every chunk holds a
-  // multiple of kRowBlock rows (rows_table = fns * d_pad or 32, sketches 64).
-  for (int r0 = 0; r0 < max_rows; r0 += kHashChunk) {
-    const int nr = max(0, min(kHashChunk, nrows - r0));
-    __syncthreads();
-    for (int e = tid; e < nr * q4; e += kHashPts)
-      reinterpret_cast<float4*>(wS)[e] = __ldg(reinterpret_cast<const float4*>(W + (row0 + r0) * d_pad) + e);
-    __syncthreads();
-    for (int rr = 0; rr < nr; rr += kRowBlock) {
-      float acc[kRowBlock];
-#pragma unroll
-      for (int q = 0; q < kRowBlock; ++q) acc[q] = 0.f;
-      const float4* w4 = reinterpret_cast<const float4*>(wS + rr * d_pad);
-      for (int i4 = 0; i4 < q4; ++i4) {
-        const float4 xv = xv4[i4];
-#pragma unroll
-        for (int q = 0; q < kRowBlock; ++q) {
-          const float4 wv = w4[q * q4 + i4];
-          acc[q] = __fmaf_rn(wv.x, xv.x, acc[q]);
-          acc[q] = __fmaf_rn(wv.y, xv.y, acc[q]);
-          acc[q] = __fmaf_rn(wv.z, xv.z, acc[q]);
-          acc[q] = __fmaf_rn(wv.w, xv.w, acc[q]);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < kRowBlock; ++q) row_done(r0 + rr + q, acc[q]);
-    }
-  }
-  if (p < npts && live_g) {
-    if (is_table)
-      codes[int64_t(g) * cj + p * cp] = code;
-    else
-      sk[int64_t(g - L) * sm + p * sp] = bits;
-  }
-}
-
 // Pooling (Sec. 3.2): table j's code concatenates the values of its pool
 // functions sel[j][0..F), the first in the most significant bits; function f is
 // slot f % F of pool group f / F, whose code holds it in bits
@@ -350,18 +149,11 @@ cudaError_t launch_hash(const pf_index* ix, const float* x32, const __nv_bfloat1
     if (e != cudaSuccess) return e;
     tables = 0;
   }
-  if (hash_tc_supported(ix) && xh && xl)
-    return launch_hash_tc(ix, xh, xl, x32, npts, codes, cj, cp, sk, sm, sp, ix->dev_error, rq, rq_count, rq_cap, s,
-                          tables);
-  const Layout& lay = ix->lay;
-  const size_t smem = sizeof(float) * (size_t(lay.d_pad + 4) * kHashPts + size_t(kHashGroups * kHashChunk) * lay.d_pad);
-  cudaError_t e = cudaFuncSetAttribute(hash_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
-  dim3 grid(unsigned((npts + kHashPts - 1) / kHashPts), unsigned((tables + ix->M + kHashGroups - 1) / kHashGroups));
-  hash_simt_kernel<<<grid, kHashPts * kHashGroups, smem, s>>>(x32, npts, ix->d, lay.d_pad, ix->family, tables, ix->M,
-                                                              lay.fns, lay.ell,
-                                                lay.rows_table, ix->W32, ix->Wthr, codes, cj, cp, sk, sm, sp);
-  return cudaGetLastError();
+  // every projection runs on the tensor cores; the caller provides the
+  // bfloat16 halves of the rows
+  if (!xh || !xl) return cudaErrorInvalidValue;
+  return launch_hash_tc(ix, xh, xl, x32, npts, codes, cj, cp, sk, sm, sp, ix->dev_error, rq, rq_count, rq_cap, s,
+                        tables);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,45 +1,48 @@
 // Hashing on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
 // The projections of a block of 128 points onto all hash rows are the dense
-// contraction V = X W^T (K = d_pad).  Each product is evaluated as three
-// bfloat16 products with float32 accumulation in tensor memory,
-//   X W^T ~= Xh Wh^T + Xh Wl^T + Xl Wh^T,   X = Xh + Xl, W = Wh + Wl,
-// whose error is below 3*2^-16*|x||w| for the split plus the accumulation
-// error of the float32 accumulation in tensor memory (<= 24 MMA steps of 16
-// exact products, each step rounding with relative error <= 2^-20 even for a
-// truncating adder: < 2.3e-5 |x||w|), i.e. < 7e-5 |w| for unit x.  The
-// epilogue decides every hash bit with the rule of the SIMT kernel and the
-// same band 2^-12 |w| = 2.44e-4 |w|: a decision closer to its boundary than
-// the band is recomputed in float64 in index order,
-// which is the defining value (Sec. 2.2: HP bit = [<a,x> >= 0]; CP value =
-// sign and index of the largest |<a_c,x>|), so codes are bit-identical to the
-// float64 definition.
+// contraction V = X W^T (K = d_pad <= 320).  The hyperplanes' entries are
+// bfloat16 values, so W is exact in bfloat16; the points are split into
+// bfloat16 halves X = Xh + Xl (|x - xh - xl| <= 2^-18 |x| per entry) and
+//   X W^T ~= Xh W^T + Xl W^T
+// (two bfloat16 products, float32 accumulation in tensor memory).  The error
+// is below 2^-18 |x||w| for the split plus the float32 accumulation (at most
+// 2 * 4 * KB <= 40 MMA steps of 16 exact products, each step rounding with
+// relative error <= 2^-20 even for a truncating adder: < 4e-5 |x||w|), i.e.
+// < 5e-5 |w| for unit x.  The epilogue decides every hash bit with the rule
+// of the float64 definition and the band 2^-12 |w| = 2.44e-4 |w|: a decision
+// closer to its boundary than the band is recomputed in float64 in index
+// order, which is the defining value (Sec. 2.2: HP bit = [<a,x> >= 0]; CP
+// value = sign and index of the largest |<a_c,x>|), so codes are
+// bit-identical to the float64 definition.
 //
-// Kernel structure (one CTA of 10 warps per SM, persistent, warp-specialised):
-//   - a unit of work is (pair of 128-point tiles, segment); a segment is one
-//     repetition (CP: fns tiles of d_pad rows; HP: a group of 4 repetitions =
-//     128 rows) or a group of 2 sketches (128 rows); CTA b takes the
-//     contiguous units [b*U/G, (b+1)*U/G) of the U = pairs*segments, so the
-//     CTAs' shares differ by at most one segment and each CTA loads the A
-//     tiles of only the one or two pairs its range touches.  Both point tiles
-//     of a pair are multiplied by every B tile the CTA loads, which halves
-//     the B stream from L2 (the operand that bounds the kernel);
-//   - warp 0 (one thread) is the TMA producer: the A tiles (Xh, Xl of the 256
-//     points, 128 KB for d_pad <= 128) once per run of segments, then for
-//     every N tile its B operand as 2*KB boxes of 64 columns (Wh and Wl per K
-//     block) into a ring of shared-memory stages (as many as fit beside the A
-//     tiles, at most 8); all tiles are K-major with the 128-byte swizzle;
+// Kernel structure (one CTA per SM, persistent, warp-specialised; P point
+// tiles per work unit: P = 2 for d_pad <= 128, 1 above, where the A tiles of
+// two point tiles would not fit in shared memory beside the B ring):
+//   - a unit of work is (P point tiles, segment); a segment is one repetition
+//     (CP: fns functions of d_pad rows, each cut into N tiles of at most 128
+//     rows; HP: a group of 4 repetitions = 128 rows) or a group of 2 sketches
+//     (128 rows); CTA b takes the contiguous units [b*U/G, (b+1)*U/G) of the
+//     U = point-tile groups * segments, so the CTAs' shares differ by at most
+//     one segment and each CTA loads the A tiles of only the one or two
+//     groups its range touches.  With P = 2 both point tiles are multiplied
+//     by every B tile the CTA loads, which halves the B stream from L2;
+//   - warp 0 (one thread) is the TMA producer: the A tiles (Xh, Xl of the P
+//     point tiles, KB blocks of 64 columns each) once per run of segments,
+//     then for every N tile its B operand as KB boxes of 64 columns into a
+//     ring of shared-memory stages (as many as fit beside the A tiles, at
+//     most 8); all tiles are K-major with the 128-byte swizzle;
 //   - warp 1 owns the tensor memory and (one thread) issues the MMAs: per K
-//     block and point tile, Xh*Wh and Xl*Wh from the Wh stage and Xh*Wl from
-//     the Wl stage, into the point tile's 128-column accumulator of one of two
-//     buffers (2 buffers x 2 point tiles = all 512 columns, so the epilogue
-//     of one N tile overlaps the MMAs of the next); tcgen05.commit frees each
-//     stage and publishes each finished accumulator;
-//   - warps 2-5 (point tile 0) and 6-9 (point tile 1) are the epilogue (one
-//     thread per point, tcgen05.ld of its lane quarter = warp % 4) and hand
-//     each accumulator back through an mbarrier; for a CP function
-//     the thread keeps the three largest |v| as integer sort keys in four
-//     independent chains (no branches); a decision closer to its boundary than
+//     block and point tile, Xh*W and Xl*W from the stage, into the point
+//     tile's 128-column accumulator of one of two buffers (2 buffers x P point
+//     tiles x 128 columns, so the epilogue of one N tile overlaps the MMAs of
+//     the next); tcgen05.commit frees each stage and publishes each finished
+//     accumulator;
+//   - four epilogue warps per point tile (one thread per point, tcgen05.ld of
+//     its lane quarter = warp % 4) hand each accumulator back through an
+//     mbarrier; for a CP function the thread keeps the three largest |v| as
+//     integer sort keys in four independent chains (no branches), merged
+//     across the function's N tiles; a decision closer to its boundary than
 //     the band is queued, with the top two rows as the candidates (or "all
 //     rows" when a third row is also close), in the CTA's own region of the
 //     request queue (a shared-memory counter, no global atomics);
@@ -57,12 +60,16 @@ namespace pf {
 namespace {
 
 constexpr int kBM = 128;          // points per tile (MMA M)
-constexpr int kPair = 2;          // point tiles per work unit: they share every B tile
-constexpr int kThreads = 32 * (2 + 4 * kPair);  // producer warp, MMA warp, 4 epilogue warps per point tile
+constexpr int kBN = 128;          // rows of an N tile (a CP function of more rows takes several)
+// producer warp, MMA warp, 4 epilogue warps per point tile (P point tiles per unit)
+constexpr int threads_for(int P) { return 32 * (2 + 4 * P); }
 constexpr int kTileBytes = kBM * 128;  // one 64-element K block of 128 rows
 constexpr int kMaxStages = 8;     // B ring (fewer when the A tiles leave less shared memory)
 constexpr int kSmemLimit = 232448;     // shared memory a CTA may use
-constexpr int kTmemCols = 512;    // [2 buffers][kPair point tiles] accumulators of 128 columns
+// [2 buffers][P point tiles] accumulators of 128 columns
+constexpr int tmem_cols_for(int P) { return 2 * P * kBN; }
+// point tiles per work unit for a padded dimension
+constexpr int pair_for(int d_pad) { return d_pad <= 128 ? 2 : 1; }
 constexpr uint32_t kSuspendNs = 5000;        // longest sleep of one try_wait
 constexpr uint64_t kWaitNs = 1000000000ull;  // a bounded wait gives up after 1 s
 constexpr uint32_t kWaitPolls = 1u << 26;    // ... or after this many polls
@@ -77,9 +84,10 @@ struct HashArgs {
   const float* thr;
   int64_t hash_rows;
   int d, d_pad, KB, family, L, M, fns, ell, rows_table;
+  int nsub;        // N tiles per CP function: ceil(d_pad / 128)
   int seg_tables;  // segments that are repetitions (CP) or groups of 4 repetitions (HP)
   int segs;        // + sketch groups of 2
-  int64_t units;   // point-tile pairs * segs; CTA b takes units [b*units/grid, (b+1)*units/grid)
+  int64_t units;   // point-tile groups * segs; CTA b takes units [b*units/grid, (b+1)*units/grid)
   int stages;      // B ring stages
   int hold_b;      // diagnostics: issue no B loads, so that the waits on them expire
   uint32_t* codes;
@@ -300,6 +308,8 @@ struct Tile {
   int first;    // first tile of its segment
   int last;     // last tile of its segment
   int fn;       // CP function index within the repetition
+  int sub;      // CP: N tile of the function (its rows start at 128 * sub)
+  int fn_last;  // CP: last N tile of the function
   int64_t row0; // first hash row
   int rows;     // N
 };
@@ -307,13 +317,18 @@ struct Tile {
 __device__ __forceinline__ Tile tile_of(const HashArgs& A, int seg, int f) {
   Tile t;
   t.seg = seg;
-  t.fn = f;
+  t.fn = 0;
+  t.sub = 0;
+  t.fn_last = 1;
   if (seg < A.seg_tables) {
     if (A.family == PF_CROSSPOLYTOPE) {
-      t.row0 = (int64_t(seg) * A.fns + f) * A.d_pad;
-      t.rows = A.d_pad;
+      t.fn = f / A.nsub;
+      t.sub = f - t.fn * A.nsub;
+      t.row0 = (int64_t(seg) * A.fns + t.fn) * A.d_pad + int64_t(kBN) * t.sub;
+      t.rows = min(kBN, A.d_pad - kBN * t.sub);
       t.first = f == 0;
-      t.last = f == A.fns - 1;
+      t.last = f == A.fns * A.nsub - 1;
+      t.fn_last = t.sub == A.nsub - 1;
     } else {
       t.row0 = int64_t(seg) * 128;
       t.rows = 128;
@@ -327,8 +342,8 @@ __device__ __forceinline__ Tile tile_of(const HashArgs& A, int seg, int f) {
   return t;
 }
 
-// A run of consecutive segments of one pair of point tiles (2*pair, 2*pair+1)
-// within the CTA's units.
+// A run of consecutive segments of one group of P point tiles (P*grp, ...,
+// P*grp + P - 1) within the CTA's units.
 struct Chunk {
   int pair, seg0, seg1;
 };
@@ -343,11 +358,12 @@ __device__ __forceinline__ bool next_chunk(const HashArgs& A, int64_t& u, int64_
 }
 
 __device__ __forceinline__ int tiles_in_seg(const HashArgs& A, int seg) {
-  return (seg < A.seg_tables && A.family == PF_CROSSPOLYTOPE) ? A.fns : 1;
+  return (seg < A.seg_tables && A.family == PF_CROSSPOLYTOPE) ? A.fns * A.nsub : 1;
 }
 
 struct EpiState {
   uint32_t code;
+  uint64_t r0, r1, r2;  // CP over several N tiles: the three largest wide keys of the function so far
 };
 
 // float64 projections of up to 4 CP hyperplanes (rows c[q] of function wf,
@@ -378,17 +394,29 @@ __device__ __forceinline__ void dot64x4(const float* __restrict__ wf, const int 
 // order of |v| up to the cut (less than 2^-16 |v|), ties to the smaller c.
 __device__ __forceinline__ uint32_t cp_key(uint32_t vbits, int c) {
   const uint32_t r = __funnelshift_l(vbits, vbits, 1);  // |v| << 1 | sign
-  return (r | 0xFEu) - 2u * uint32_t(c);
+  return (r & 0xFFFFFF01u) | (uint32_t(127 - c) << 1);  // one logic op: c is a constant of the unrolled loop
 }
 __device__ __forceinline__ float cp_key_abs(uint32_t k) { return __uint_as_float((k >> 1) & 0x7FFFFF80u); }
 __device__ __forceinline__ int cp_key_col(uint32_t k) { return 127 - int((k >> 1) & 0x7Fu); }
 
 // the three largest keys seen (m0 > m1 > m2; keys of distinct columns differ)
-__device__ __forceinline__ void top3_push(uint32_t k, uint32_t& m0, uint32_t& m1, uint32_t& m2) {
+template <typename K>
+__device__ __forceinline__ void top3_push(K k, K& m0, K& m1, K& m2) {
   m2 = max(m2, min(m1, k));
   m1 = max(m1, min(m0, k));
   m0 = max(m0, k);
 }
+
+// Wide key of a CP function with several N tiles: the 32-bit key k of column
+// c of the tile whose rows start at col0 becomes (the same cut |v|, then
+// 1023 - (col0 + c), then the sign), so that keys of different tiles order as
+// the 32-bit keys of one tile do (larger |v| first, ties to the smaller row).
+__device__ __forceinline__ uint64_t cp_wide_key(uint32_t k, int col0) {
+  const uint32_t col = uint32_t(col0 + cp_key_col(k));
+  return (uint64_t(k >> 8) << 11) | (uint64_t(1023u - col) << 1) | uint64_t(k & 1u);
+}
+__device__ __forceinline__ float cp_wide_abs(uint64_t k) { return __uint_as_float(uint32_t(k >> 11) << 7); }
+__device__ __forceinline__ int cp_wide_col(uint64_t k) { return 1023 - int((k >> 1) & 1023u); }
 
 // Reserve `cnt` consecutive entries of this CTA's region of the request queue
 // for this lane (warp-aggregated: one shared-memory atomic per warp) and
@@ -417,16 +445,20 @@ __device__ __forceinline__ RecheckReq* request_at(const HashArgs& A, uint32_t lo
 }
 
 // Epilogue of one N tile for the thread's point p (accumulator columns at taddr).
+// WIDE: the kernel for d_pad > 128, whose CP functions may span several N
+// tiles (with d_pad <= 128 every function is one tile: nsub == 1).
+template <bool WIDE>
 __device__ __forceinline__ void epilogue(const HashArgs& A, const Tile& t, uint32_t taddr, int64_t p,
                                          EpiState& st, uint32_t* s_count) {
   const bool live = p < A.npts;
   const float* xrow = A.x32 + (live ? p : 0) * A.d_pad;
   if (t.seg < A.seg_tables && A.family == PF_CROSSPOLYTOPE) {
     if (t.first) st.code = 0;
-    const float band = A.thr[t.row0];
+    const float band = A.thr[t.row0];  // one band for all rows of a function
     // the three largest |v| over the function's rows, four independent
-    // chains; rows c >= d of a function are zero and reach the top three
-    // only when fewer than three rows are nonzero (then every row is rechecked)
+    // chains (merged across the N tiles of a function of more than 128 rows);
+    // rows c >= d of a function are zero and reach the top three only when
+    // fewer than three rows are nonzero (then every row is rechecked)
     uint32_t m0[4] = {0u, 0u, 0u, 0u}, m1[4] = {0u, 0u, 0u, 0u}, m2[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -444,30 +476,52 @@ __device__ __forceinline__ void epilogue(const HashArgs& A, const Tile& t, uint3
       top3_push(m1[q], k0, k1, k2);
       top3_push(m2[q], k0, k1, k2);
     }
-    const float a0 = cp_key_abs(k0), a1 = cp_key_abs(k1), a2 = cp_key_abs(k2);
+    float a0, a1, a2;
+    int arg, cs1;
+    bool neg;
+    if (!WIDE || A.nsub == 1) {
+      a0 = cp_key_abs(k0);
+      a1 = cp_key_abs(k1);
+      a2 = cp_key_abs(k2);
+      arg = cp_key_col(k0);
+      cs1 = cp_key_col(k1);
+      neg = (k0 & 1u) != 0u;
+    } else {
+      // the function's rows span several N tiles: merge this tile's top three
+      // into the function's, decide after its last tile (uniform in the warp)
+      if (t.sub == 0) st.r0 = st.r1 = st.r2 = 0ull;
+      const int col0 = kBN * t.sub;
+      top3_push(cp_wide_key(k0, col0), st.r0, st.r1, st.r2);
+      top3_push(cp_wide_key(k1, col0), st.r0, st.r1, st.r2);
+      top3_push(cp_wide_key(k2, col0), st.r0, st.r1, st.r2);
+      if (!t.fn_last) return;
+      a0 = cp_wide_abs(st.r0);
+      a1 = cp_wide_abs(st.r1);
+      a2 = cp_wide_abs(st.r2);
+      arg = cp_wide_col(st.r0);
+      cs1 = cp_wide_col(st.r1);
+      neg = (st.r0 & 1ull) != 0ull;
+    }
     // every row whose |v| can be within 2*band of the maximum reaches lim:
     // a0 * 2^-15 covers the cut of the keys
     const float lim = a0 - 2.f * band - a0 * 3.0517578125e-05f;
-    int arg = cp_key_col(k0);
-    bool neg = (k0 & 1u) != 0u;
     const bool need = live && (a1 >= lim || a0 < band);
     if (__any_sync(0xffffffffu, need)) {
       // rare: candidates are the top two, or every row once a third reaches lim
       const bool all = a0 < band || a2 >= lim;
-      const int cs0 = arg, cs1 = cp_key_col(k1);
+      const int cs0 = arg;
       const uint32_t local = reserve_requests(A, s_count, need ? 1u : 0u);
       if (need && local < A.rq_per) {
         // keep the tensor-core decision now; the fix-up kernel rewrites the field
         RecheckReq q;
         q.p = uint32_t(p);
-        q.row0 = uint32_t(t.row0);
+        q.row0 = uint32_t(t.row0 - int64_t(kBN) * t.sub);  // the function's first row
         q.info = uint32_t(t.seg) | (uint32_t(t.fn) << 20) | (3u << 26) | ((all ? 3u : 0u) << 30);
-        q.c[0] = uint8_t(cs0);
-        q.c[1] = uint8_t(cs1);
-        q.c[2] = q.c[3] = 0;
+        q.c[0] = uint16_t(cs0);
+        q.c[1] = uint16_t(cs1);
         *request_at(A, local) = q;
       } else if (need) {
-        const float* wf = A.w32 + t.row0 * A.d_pad;
+        const float* wf = A.w32 + (t.row0 - int64_t(kBN) * t.sub) * A.d_pad;
         double bestabs = -1.0, bestval = 0.0;
         int besti = 0;
         if (all) {
@@ -543,7 +597,7 @@ __device__ __forceinline__ void epilogue(const HashArgs& A, const Tile& t, uint3
           } else {
             q.info = uint32_t(row >> 5) | (uint32_t(row & 31) << 20) | (1u << 30);
           }
-          q.c[0] = q.c[1] = q.c[2] = q.c[3] = 0;
+          q.c[0] = q.c[1] = 0;
           *request_at(A, local) = q;
           ++local;  // stays >= rq_per (including the "no queue" value) once it gets there
         } else {
@@ -575,11 +629,15 @@ __device__ __forceinline__ void epilogue(const HashArgs& A, const Tile& t, uint3
 
 struct TensorMaps {
   CUtensorMap xh, xl;        // A: [npts][d_pad], box {64, 128}
-  CUtensorMap wh_f;          // B, CP function tiles: box {64, d_pad}
-  CUtensorMap wh_g;          // B, 128-row groups: box {64, 128}
+  CUtensorMap wh_f;          // B, CP function tiles (d_pad <= 128): box {64, d_pad}
+  CUtensorMap wh_g;          // B, 128-row groups and full 128-row N tiles: box {64, 128}
+  CUtensorMap wh_t;          // B, the last N tile of a CP function of d_pad > 128 rows: box {64, d_pad % 128}
 };
 
-__global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const __grid_constant__ TensorMaps T) {
+template <int P>
+__global__ void __launch_bounds__(threads_for(P), 1) hash_tc_kernel(HashArgs A, const __grid_constant__ TensorMaps T) {
+  constexpr int kPair = P;
+  constexpr int kTmemCols = tmem_cols_for(P);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int KB = A.KB, S = A.stages;
@@ -642,8 +700,7 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
       for (int seg = seg0; seg < seg1 && !bad; ++seg)
         for (int f = 0; f < tiles_in_seg(A, seg) && !bad; ++f) {
           const Tile t = tile_of(A, seg, f);
-          const bool fn_tile = t.rows == A.d_pad && seg < A.seg_tables && A.family == PF_CROSSPOLYTOPE;
-          const CUtensorMap* mh = fn_tile ? &T.wh_f : &T.wh_g;
+          const CUtensorMap* mh = t.rows == kBN ? &T.wh_g : A.nsub == 1 ? &T.wh_f : &T.wh_t;
           for (int kb = 0; kb < KB; ++kb, ++stage) {
             const uint32_t slot = stage % S, round = stage / S;
             if (!mbar_wait(smem_u32(&bempty[slot]), (round & 1) ^ 1)) { bad = true; break; }
@@ -679,7 +736,7 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
             tc_fence_after();
             const uint32_t bt = sB + slot * kTileBytes;
             for (int pt = 0; pt < kPair; ++pt) {
-              const uint32_t d_tmem = tmem + (b * kPair + pt) * 128;
+              const uint32_t d_tmem = tmem + (b * kPair + pt) * kBN;
               // the hyperplane tile is exact in bfloat16: Xh*W and Xl*W
               for (int half = 0; half < 2; ++half) {
                 const uint32_t at = sA + pt * a_bytes + uint32_t(((half ? KB : 0) + kb) * kTileBytes);
@@ -697,7 +754,7 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
     }
   } else if (warp >= 2) {
     // ---------------- epilogue: group pt (warps 2-5: point tile 0, 6-9: point tile 1),
-    // thread = point, TMEM lane quarter = warp % 4
+    // thread = point, TMEM lane quarter = warp % 4 (the only quarter a warp may read)
     const int pt = (warp - 2) >> 2, quarter = warp & 3;
     uint32_t g = 0;
     int64_t u = u_lo;
@@ -714,7 +771,7 @@ __global__ void __launch_bounds__(kThreads, 1) hash_tc_kernel(HashArgs A, const 
           const uint32_t b = g & 1;
           if (!mbar_wait(smem_u32(&accfull[b][pt]), (g >> 1) & 1)) { bad = true; break; }
           tc_fence_after();
-          epilogue(A, t, tmem + (uint32_t(quarter * 32) << 16) + (b * kPair + pt) * 128, p, st, &s_count);
+          epilogue<P == 1>(A, t, tmem + (uint32_t(quarter * 32) << 16) + (b * kPair + pt) * kBN, p, st, &s_count);
           tc_fence_before();
           mbar_arrive(smem_u32(&accempty[b][pt]));
         }
@@ -833,9 +890,9 @@ __device__ __forceinline__ void recheck_one(const HashArgs& A, const RecheckReq&
   const float* xrow = A.x32 + p * A.d_pad;
   const uint32_t kind = q.info >> 30;
   if (kind == 0) {
-    const uint32_t use = (q.info >> 26) & 15u;
+    const uint32_t use = (q.info >> 26) & 3u;
     const float* wf = A.w32 + int64_t(q.row0) * A.d_pad;
-    const int cs[4] = {q.c[0], q.c[1], q.c[2], q.c[3]};
+    const int cs[4] = {q.c[0], q.c[1], q.c[1], q.c[1]};
     const float* w[4] = {wf + int64_t(cs[0]) * A.d_pad, wf + int64_t(cs[1]) * A.d_pad, wf + int64_t(cs[2]) * A.d_pad,
                          wf + int64_t(cs[3]) * A.d_pad};
     // float32 first: the row whose |value| exceeds every other listed row's
@@ -895,40 +952,48 @@ __device__ __forceinline__ void recheck_one(const HashArgs& A, const RecheckReq&
 }
 
 // One CP request of kind 3 (every row a candidate), by a whole warp: lane l
-// takes rows l, l+32, ... (d <= 128), each in float64 in index order, then the
-// warp keeps the largest |value|, ties to the smaller row.
+// takes rows l, l+32, ... (d <= 320, in groups of 128 rows), each in float64
+// in index order, then the warp keeps the largest |value|, ties to the
+// smaller row.
 __device__ __forceinline__ void recheck_all_rows(const HashArgs& A, uint32_t p32, uint32_t row0, uint32_t info) {
   const int lane = threadIdx.x & 31;
   const int64_t p = p32;
   const float* xrow = A.x32 + p * A.d_pad;
   const float* wf = A.w32 + int64_t(row0) * A.d_pad;
-  const float* w[4];
-  uint32_t use = 0;
+  // rows c0 + lane + 32 u (u < 4) of the group at c0
+  auto group = [&](int c0, const float* (&w)[4]) {
+    uint32_t use = 0;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int c = lane + 32 * u;
-    w[u] = wf + int64_t(min(c, A.d - 1)) * A.d_pad;
-    if (c < A.d) use |= 1u << u;
-  }
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + lane + 32 * u;
+      w[u] = wf + int64_t(min(c, A.d - 1)) * A.d_pad;
+      if (c < A.d) use |= 1u << u;
+    }
+    return use;
+  };
   // float32 first: decided if the largest |value| exceeds every other row's by
   // more than the largest bound twice over and its sign is outside the bound
   {
-    float v32[4], e32[4];
-    dot32_rows(w, use, xrow, A.d, v32, e32);
     float m1 = -1.f, m2 = -1.f, emax = 0.f, val = 0.f;
     int i1 = 0;
+    for (int c0 = 0; c0 < A.d; c0 += 128) {
+      const float* w[4];
+      const uint32_t use = group(c0, w);
+      float v32[4], e32[4];
+      dot32_rows(w, use, xrow, A.d, v32, e32);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (!(use & (1u << u))) continue;
-      const float av = fabsf(v32[u]);
-      emax = fmaxf(emax, e32[u]);
-      if (av > m1) {
-        m2 = m1;
-        m1 = av;
-        i1 = lane + 32 * u;
-        val = v32[u];
-      } else {
-        m2 = fmaxf(m2, av);
+      for (int u = 0; u < 4; ++u) {
+        if (!(use & (1u << u))) continue;
+        const float av = fabsf(v32[u]);
+        emax = fmaxf(emax, e32[u]);
+        if (av > m1) {
+          m2 = m1;
+          m1 = av;
+          i1 = c0 + lane + 32 * u;
+          val = v32[u];
+        } else {
+          m2 = fmaxf(m2, av);
+        }
       }
     }
 #pragma unroll
@@ -951,17 +1016,21 @@ __device__ __forceinline__ void recheck_all_rows(const HashArgs& A, uint32_t p32
       return;
     }
   }
-  double v64[4];
-  dot64_rows(w, use, xrow, A.d, v64);
   double bestabs = -1.0, bestval = 0.0;
   int besti = 0x7FFFFFFF;
+  for (int c0 = 0; c0 < A.d; c0 += 128) {  // rows visited in increasing order: the first of equals stays
+    const float* w[4];
+    const uint32_t use = group(c0, w);
+    double v64[4];
+    dot64_rows(w, use, xrow, A.d, v64);
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
-    if ((use & (1u << u)) && fabs(v64[u]) > bestabs) {
-      bestabs = fabs(v64[u]);
-      bestval = v64[u];
-      besti = lane + 32 * u;
-    }
+    for (int u = 0; u < 4; ++u)
+      if ((use & (1u << u)) && fabs(v64[u]) > bestabs) {
+        bestabs = fabs(v64[u]);
+        bestval = v64[u];
+        besti = c0 + lane + 32 * u;
+      }
+  }
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) {
     const double oa = __shfl_xor_sync(0xffffffffu, bestabs, off);
@@ -993,7 +1062,7 @@ __global__ void recheck_kernel(HashArgs A, int blocks_per_region) {
     const bool has = i < count;
     RecheckReq q;
     q.p = q.row0 = q.info = 0u;
-    q.c[0] = q.c[1] = q.c[2] = q.c[3] = 0;
+    q.c[0] = q.c[1] = 0;
     if (has) q = rq[i];
     const bool full = has && (q.info >> 30) == 3u;
     if (has && !full) recheck_one(A, q);
@@ -1011,18 +1080,22 @@ __global__ void recheck_kernel(HashArgs A, int blocks_per_region) {
 
 }  // namespace
 
-bool hash_tc_supported(const pf_index* ix) { return ix->lay.d_pad <= 128; }
+uint32_t recheck_capacity(const pf_index* ix, int64_t npts, int tables) {
+  const int64_t per_table = ix->family == PF_SIMHASH ? ix->lay.Kb : ix->lay.fns;
+  const int64_t per = std::max<int64_t>(48, (int64_t(tables) * per_table + 19) / 20 + (64 * int64_t(ix->M) + 255) / 256);
+  return uint32_t(std::min<int64_t>(npts * per + 65536, 0xFFFFFFFFll));
+}
 
 int hash_tc_stages(int d_pad) {
   const int KB = (d_pad + 63) / 64;
   // the static barriers (padded to 1 KB) and the 1 KB alignment slack
-  const int left = kSmemLimit - 2048 - kPair * 2 * KB * kTileBytes;
+  const int left = kSmemLimit - 2048 - pair_for(d_pad) * 2 * KB * kTileBytes;
   return std::min(kMaxStages, left / kTileBytes);
 }
 
 size_t hash_tc_smem(int d_pad) {
   const int KB = (d_pad + 63) / 64;
-  return size_t(kPair * 2 * KB + hash_tc_stages(d_pad)) * kTileBytes + 1024;
+  return size_t(pair_for(d_pad) * 2 * KB + hash_tc_stages(d_pad)) * kTileBytes + 1024;
 }
 
 namespace {
@@ -1082,10 +1155,12 @@ cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __
   A.fns = ix->lay.fns;
   A.ell = ix->lay.ell;
   A.rows_table = ix->lay.rows_table;
+  A.nsub = ix->family == PF_CROSSPOLYTOPE ? (A.d_pad + kBN - 1) / kBN : 1;
   A.seg_tables = ix->family == PF_CROSSPOLYTOPE ? tables : (tables + 3) / 4;
   A.segs = A.seg_tables + (ix->M + 1) / 2;
+  const int P = pair_for(A.d_pad);
   const int64_t mtiles = (npts + kBM - 1) / kBM;
-  A.units = (mtiles + kPair - 1) / kPair * A.segs;
+  A.units = (mtiles + P - 1) / P * A.segs;
   A.stages = hash_tc_stages(A.d_pad);
   A.hold_b = ix->hold_weight_loads;
   A.codes = codes;
@@ -1100,15 +1175,20 @@ cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __
   A.rq_count = rq_count;
   A.rq_per = A.rq ? rq_cap / uint32_t(grid) : 0u;
   TensorMaps T;
-  const int fn_rows = ix->family == PF_CROSSPOLYTOPE ? A.d_pad : 128;
+  // B boxes: a whole CP function (d_pad <= 128), a 128-row group or N tile,
+  // and the last N tile of a function of more rows (unused maps repeat wh_g)
+  const int fn_rows = ix->family == PF_CROSSPOLYTOPE && A.nsub == 1 ? A.d_pad : kBN;
+  const int tail_rows = ix->family == PF_CROSSPOLYTOPE && A.d_pad % kBN != 0 && A.nsub > 1 ? A.d_pad % kBN : kBN;
   if (!make_map(&T.xh, xh, npts, A.d_pad, kBM) || !make_map(&T.xl, xl, npts, A.d_pad, kBM) ||
       !make_map(&T.wh_f, ix->Whi, ix->hash_rows, A.d_pad, fn_rows) ||
-      !make_map(&T.wh_g, ix->Whi, ix->hash_rows, A.d_pad, 128))
+      !make_map(&T.wh_g, ix->Whi, ix->hash_rows, A.d_pad, kBN) ||
+      !make_map(&T.wh_t, ix->Whi, ix->hash_rows, A.d_pad, tail_rows))
     return cudaErrorInvalidValue;
   const size_t smem = hash_tc_smem(A.d_pad);
-  cudaError_t e = cudaFuncSetAttribute(hash_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  void (*kern)(HashArgs, TensorMaps) = P == 2 ? hash_tc_kernel<2> : hash_tc_kernel<1>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  hash_tc_kernel<<<grid, kThreads, smem, s>>>(A, T);
+  kern<<<grid, threads_for(P), smem, s>>>(A, T);
   e = cudaGetLastError();
   if (e != cudaSuccess || !A.rq) return e;
   recheck_kernel<<<4 * grid, 256, 0, s>>>(A, 4);

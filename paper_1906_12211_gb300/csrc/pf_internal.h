@@ -21,7 +21,7 @@ constexpr int kMaxD = 320;
 constexpr int kMaxL = 2048;
 constexpr int kMlpHidden = 256;                     // start-depth model hidden units
 constexpr float kMlpTail = 0.05f;                   // quantile: P(stop depth > q) <= this
-constexpr int kMlpMargin = 6;                       // start depth = quantile + this many bits (capped at K)
+constexpr int kMlpMargin = 0;                       // start depth = quantile + this many bits (capped at K)
 
 enum Purpose : uint32_t {
   kPurposeHash = 1,
@@ -81,8 +81,8 @@ uint64_t resident_bytes(int family, int64_t n, int d, int M, int L, int sketch_l
 struct RecheckReq {
   uint32_t p;     // point (row of the normalised matrix)
   uint32_t row0;  // CP: first hash row of the function; one-bit decisions: the hash row
-  uint32_t info;  // bits 0-19 repetition / sketch, 20-25 function / bit, 26-29 CP candidate mask, 30-31 kind
-  uint8_t c[4];   // CP candidate hyperplanes
+  uint32_t info;  // bits 0-19 repetition / sketch, 20-25 function / bit, 26-27 CP candidate mask, 30-31 kind
+  uint16_t c[2];  // CP candidate hyperplanes (rows of the function)
 };
 
 // ---------------------------------------------------------------- errors
@@ -200,8 +200,13 @@ cudaError_t launch_hash(const pf_index* ix, const float* x32, const __nv_bfloat1
 cudaError_t launch_pool_gather(const pf_index* ix, const uint32_t* gcodes, int64_t gj, int64_t gp, int64_t npts,
                                uint32_t* codes, int64_t cj, int64_t cp, cudaStream_t s);
 // recheck-queue entries to provision for npts points
-inline uint32_t recheck_capacity(int64_t npts) { return uint32_t(npts * 48 + 65536); }
-bool hash_tc_supported(const pf_index* ix);
+// Entries of the deferred-recheck queue for hashing npts points with `tables`
+// row-function tables: on the order of 1 % of cross-polytope decisions and
+// 0.2 % of one-bit decisions fall inside the band, so a twentieth of the
+// table decisions plus a 256th of the sketch bits per point (at least 48)
+// leaves room for a CTA's uneven share; requests beyond a CTA's region are
+// rechecked inline (slower, the same codes).
+uint32_t recheck_capacity(const pf_index* ix, int64_t npts, int tables);
 // tables: repetitions hashed with row-based functions (ix->L; 0 hashes sketches only)
 cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __nv_bfloat16* xl, const float* x32,
                            int64_t npts, uint32_t* codes, int64_t cj, int64_t cp, uint64_t* sk, int64_t sm,

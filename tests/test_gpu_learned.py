@@ -122,27 +122,28 @@ def test_predict_forward_equals_float64_oracle(trained, orc):
     X[:, :ix.d] = qn
     bits = (qsk[:, 0][:, None] >> np.arange(64, dtype=np.uint64)) & np.uint64(1)
     X[:, ix.d_pad:] = np.where(bits == 1, 1.0, -1.0)
-    want, A = mlp_oracle.start_depths(X, W1, b1, W2, b2, 0.05, 6)
+    want, A = mlp_oracle.start_depths(X, W1, b1, W2, b2, 0.05, 0)  # the default rule
     near = np.any(np.abs(A - 0.05) < 1e-4, axis=1)
     assert np.all((got == want) | near), np.nonzero((got != want) & ~near)
     assert np.mean(got == want) >= 0.98
 
 
 def test_start_rule_moves_the_start_and_keeps_the_results_equal_to_the_oracle(trained):
-    """A smaller margin starts deeper in the schedule's order (a lower prefix
-    length): the search still equals the oracle at the predicted depths."""
+    """A larger margin starts earlier in the schedule's order (a longer prefix,
+    capped at K): the search still equals the oracle at the predicted depths."""
     ix, o, _, _, Q = trained
     qd = torch.from_numpy(Q).to(DEV)
     base = ix.learned_predict(qd).cpu().numpy()
     try:
-        ix.learned_start_rule(0.05, 2)
-        low = ix.learned_predict(qd).cpu().numpy()
-        assert np.all(low <= base) and np.any(low < base)
+        ix.learned_start_rule(0.05, 3)
+        high = ix.learned_predict(qd).cpu().numpy()
+        assert np.all(high >= base) and np.any(high > base)
+        assert np.all((high == np.minimum(base + 3, ix.Kb)) | (high == ix.Kb))
         ids, sims, st = ix.search(qd, 10, 0.9, learned=True, stats=True)
-        ref = o.search(Q, 10, 0.9, start_depth=low)
+        ref = o.search(Q, 10, 0.9, start_depth=high)
         assert np.array_equal(ids.cpu().numpy().view(np.uint32), ref["ids"])
         assert np.array_equal(sims.cpu().numpy(), ref["sims"])
         with pytest.raises(pf.PuffinnError):
             ix.learned_start_rule(1.5, 2)
     finally:
-        ix.learned_start_rule(0.05, 6)
+        ix.learned_start_rule(0.05, 0)

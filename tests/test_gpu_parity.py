@@ -101,7 +101,8 @@ def cpodd(orc):
 
 @pytest.fixture(scope="module")
 def cpwide(orc):
-    # d = 150 (d_pad 160 > 128: the float32 SIMT hashing kernel), CP with l = 9
+    # d = 150 (d_pad 160 > 128: one point tile per hashing unit and CP functions
+    # of two N tiles, 128 + 32 rows), CP with l = 9
     X = datagen.vmf_mixture(3000, 150, 20, 40.0, seed=5)
     Q = datagen.vmf_mixture(40, 150, 20, 40.0, seed=5, purpose="queries")
     return Case(orc, "vmf-n3000-d150", X, Q, "crosspolytope", L=12, seed=4)
@@ -135,7 +136,7 @@ def cpmidh(orc):
 
 @pytest.fixture(scope="module")
 def cpwideh(orc):
-    # d = 150 (float32 SIMT hashing of the rounded rows) with binary16 rows
+    # d = 150 (two N tiles per CP function, hashing the rounded rows) with binary16 rows
     X = datagen.vmf_mixture(3000, 150, 20, 40.0, seed=5)
     Q = datagen.vmf_mixture(40, 150, 20, 40.0, seed=5, purpose="queries")
     return Case(orc, "vmf-n3000-d150-f16", X, Q, "crosspolytope", L=12, seed=4, rows="f16")
@@ -144,7 +145,8 @@ def cpwideh(orc):
 @pytest.fixture(scope="module")
 def cpsyn(orc):
     # the paper's SYNTHETIC construction (Sec. 5) at n = 3,000: 3 x 100 = 300
-    # dimensions (d_pad 304: SIMT hashing, CP with l = 10, three functions of 30 bits)
+    # dimensions (d_pad 304: CP functions of three N tiles, 128 + 128 + 48 rows,
+    # five K blocks; l = 10, three functions of 30 bits)
     X = datagen.paper_synthetic_points(3000, 100, seed=2)
     Q = datagen.paper_synthetic_queries(40, 100, seed=2)
     return Case(orc, "paper-synthetic-n3000-d300", X, Q, "crosspolytope", L=8, seed=6)
@@ -158,8 +160,16 @@ def cpmaxd(orc):
     return Case(orc, "gauss-n1200-d320", X, Q, "simhash", L=10, seed=3)
 
 
+@pytest.fixture(scope="module")
+def cp256(orc):
+    # d = 256 (the planted workload's dimension): CP functions of exactly two
+    # full N tiles, four K blocks, one point tile per hashing unit
+    X, Q, _ = datagen.planted(1500, 256, 30, n_decoys=15, seed=13)
+    return Case(orc, "planted-n1980-d256", X, Q, "crosspolytope", L=6, seed=8)
+
+
 CASES = ["cfg1", "cpmid", "cpodd", "cpwide", "hpodd", "cfg1pp", "cpmidpp", "cfg1h", "cpmidh", "cpwideh", "cpsyn",
-         "cpmaxd"]
+         "cpmaxd", "cp256"]
 
 
 @pytest.fixture

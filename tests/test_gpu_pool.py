@@ -3,8 +3,8 @@ the oracle: each table's subset of the pool, the codes of points and queries,
 and the search under both stop rules (Cantelli's bound, and Lemma 1's test as
 if the functions were independent), bit for bit.  The cases cover SimHash
 (3,072 one-bit functions), cross-polytope on the tensor-core path (d' <= 128,
-including a last pool group that is only partly used) and on the SIMT path
-(d' = 160)."""
+including a last pool group that is only partly used) and with d' = 160 (one
+point tile per hashing unit, two N tiles per function)."""
 import numpy as np
 import pytest
 

@@ -54,10 +54,17 @@ def test_withheld_loads_time_out_and_the_index_stays_usable(idx):
     torch.cuda.synchronize()
 
 
-def test_selftest_needs_the_tensor_core_kernel():
+def test_one_point_tile_per_unit_times_out_too():
+    """d = 150 (d' = 160 > 128): one point tile per work unit and CP functions
+    of two N tiles; the withheld loads time out there as well."""
     pf.build()
-    X = datagen.vmf_mixture(3_000, 150, 20, 50.0, seed=2)  # d' = 160 > 128: hashed by the SIMT kernel
+    X = datagen.vmf_mixture(3_000, 150, 20, 50.0, seed=2)
     ix = pf.Index(torch.from_numpy(X).to(DEV), "crosspolytope", num_tables=4, seed=1)
+    q = torch.from_numpy(X[:10]).to(DEV)
+    before = ix.hash_queries(q)
     with pytest.raises(pf.PuffinnError) as e:
-        ix.selftest_timeout(torch.from_numpy(X[:10]).to(DEV))
-    assert e.value.status == -1
+        ix.selftest_timeout(q)
+    assert e.value.status == -5
+    for a, b in zip(before, ix.hash_queries(q)):
+        assert torch.equal(a, b)
+    torch.cuda.synchronize()

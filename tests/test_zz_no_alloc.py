@@ -122,8 +122,10 @@ def test_noalloc_allocates_nothing(index):
     assert free_after == free_before
 
 
-def test_noalloc_on_the_simt_hashing_path():
-    """d = 150 (d' = 160 > 128): the queries are hashed by the SIMT kernel."""
+def test_noalloc_with_wide_rows():
+    """d = 150 (d' = 160 > 128): the hashing kernel takes one point tile per
+    unit and two N tiles per function, with near-boundary decisions rechecked
+    inline (the no-alloc call has no recheck queue)."""
     pf.build()
     X = datagen.vmf_mixture(6_000, 150, 30, 50.0, seed=21)
     ix = pf.Index(torch.from_numpy(X).to(DEV), "crosspolytope", num_tables=12, seed=5)
