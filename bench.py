@@ -95,6 +95,8 @@ def parse():
     ap.add_argument("--flat-fill", type=int, default=None,
                     help="override the tuned streaming rule of the search kernel (0: chunks of one run; F: flat "
                          "when the chunks are less than 1/F full)")
+    ap.add_argument("--no-filter", action="store_true",
+                    help="search without the sketch filter (recall >= 1 - delta guaranteed by Lemma 1)")
     ap.add_argument("--filter-eps", type=float, default=0.0,
                     help="slack of the sketch threshold (Fig. 2 footnote; 0 as in Sec. 5.1)")
     ap.add_argument("--pool-bits", type=int, default=0,
@@ -198,6 +200,7 @@ def search_kernel_traffic(args=None):
                              or getattr(args, "family", "crosspolytope") != "crosspolytope"
                              or getattr(args, "estimate", "bf16") != "bf16" or getattr(args, "stop_every", 0)
                              or getattr(args, "pool_bits", 0) or getattr(args, "filter_eps", 0.0)
+                             or getattr(args, "no_filter", False)
                              or getattr(args, "learned_margin", None) is not None
                              or getattr(args, "flat_fill", None) is not None):
         return None
@@ -662,7 +665,7 @@ def main():
         Qtune = queries(w, Q, "tune", rank)
         tune_report = ix.tune(torch.from_numpy(Qtune).to(dev), k, args.recall,
                               scoring="fp32" if args.mode == "fp32" else args.estimate,
-                              learned=args.mode == "learned",
+                              learned=args.mode == "learned", filter=not args.no_filter,
                               stop_every=args.stop_every, pool_rule=args.pool_rule, filter_eps=args.filter_eps)
     if args.flat_fill is not None:  # keep the tuned shape but this streaming rule
         t = tune_report or {"unroll": 8, "warps": 4, "ctas_per_sm": 0}
@@ -688,7 +691,7 @@ def main():
         def run(timing=False):
             ix.search(Qd[0], kq[0], rq[0], k_max=k, scoring=sc, out_ids=o1[0], out_sims=o1[1], stats=o1[2],
                       timing=timing, learned=lr, stop_every=args.stop_every, pool_rule=args.pool_rule,
-                      filter_eps=args.filter_eps)
+                      filter_eps=args.filter_eps, filter=not args.no_filter)
 
         kern = {"kernel_ms": 0.0, "hash_ms": 0.0}
 
@@ -715,9 +718,11 @@ def main():
         sims = [o1[1]]
         if not args.no_graph:
             pa = ix.plan(Qd[0], kq[0], rq[0], *outputs()[:2], k_max=k, scoring=sc, learned=lr,
-                         stop_every=args.stop_every, pool_rule=args.pool_rule, filter_eps=args.filter_eps)
+                         stop_every=args.stop_every, pool_rule=args.pool_rule, filter_eps=args.filter_eps,
+                         filter=not args.no_filter)
             pb = ix.plan(Qd[1], kq[1], rq[1], o2[0], o2[1], k_max=k, stats=o2[2], scoring=sc, learned=lr,
-                         stop_every=args.stop_every, pool_rule=args.pool_rule, filter_eps=args.filter_eps)
+                         stop_every=args.stop_every, pool_rule=args.pool_rule, filter_eps=args.filter_eps,
+                         filter=not args.no_filter)
             plans = [pa, pb]
             try:
                 for _ in range(max(3, args.warmup)):
@@ -795,7 +800,7 @@ def main():
         # one batch at a time: pf_index_search given the host pointers
         el = wall(lambda i: ix.search(hq[0], hk[0], hr[0], k_max=k, scoring=sc, out_ids=hi[0], out_sims=hs[0],
                                       learned=lr, stop_every=args.stop_every, pool_rule=args.pool_rule,
-                                      filter_eps=args.filter_eps), args.steps)
+                                      filter_eps=args.filter_eps, filter=not args.no_filter), args.steps)
         assert torch.equal(hi[0], ids1.cpu()) and torch.equal(hs[0], sims1.cpu())
         seq_e2e = {"value": whole_job_rate(Q, world, args.steps, el), "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "how": "pf_index_search with page-locked host pointers, one batch "
@@ -805,7 +810,8 @@ def main():
             # two batches in flight: plans bound to the host buffers (each graph
             # copies its inputs in and its outputs out on its own stream)
             plans = [ix.plan(hq[b], hk[b], hr[b], hi[b], hs[b], k_max=k, scoring=sc, learned=lr,
-                             stop_every=args.stop_every, pool_rule=args.pool_rule, filter_eps=args.filter_eps)
+                             stop_every=args.stop_every, pool_rule=args.pool_rule, filter_eps=args.filter_eps,
+                             filter=not args.no_filter)
                      for b in range(2)]
             try:
                 el = wall(lambda i: plans[i % 2].run(streams[i % 2]), args.steps)
@@ -871,7 +877,7 @@ def main():
                                      else "after every round"),
                        "hash_functions": (f"pooled: {args.pool_bits} bits, stop rule {args.pool_rule}"
                                           if args.pool_bits else "independent"),
-                       "filter_eps": args.filter_eps,
+                       "filter": "off" if args.no_filter else "on", "filter_eps": args.filter_eps,
                        "l2": l2, "pipelining": pipelining, "parallelism": f"replica x{world}"},
             "recall": recall, "recall_per_batch": head["recall"], "build_s": build_s,
             "per_query": head["per_query"],

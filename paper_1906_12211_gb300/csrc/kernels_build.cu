@@ -158,7 +158,9 @@ cudaError_t launch_hash(const pf_index* ix, const float* x32, const __nv_bfloat1
 
 // ---------------------------------------------------------------------------
 // Per-repetition stable LSD radix sort of (code, position), 4 passes of 8 bits
-// (positions start as 0..n-1, so equal codes stay in position order, Sec. 4.2).
+// (positions start as 0..n-1, so equal codes stay in position order, Sec. 4.2):
+// the sort of the repetitions whose codes crowd into a bucket too large for
+// the bucket sort of kernels_sort.cu (many identical points, for instance).
 // Each pass: per-tile digit histograms -> one exclusive scan per repetition in
 // (digit, tile) order -> stable scatter.  Within a tile, keys are ranked chunk
 // by chunk (256 keys, one per thread) with warp match masks, so equal digits
@@ -290,19 +292,21 @@ cudaError_t gather_table_sketches(const pf_index* ix, const uint64_t* sk, uint64
   return cudaGetLastError();
 }
 
-cudaError_t sort_tables(pf_index* ix, uint32_t* codes_unsorted, cudaStream_t s) {
+cudaError_t lsd_sort_tables(pf_index* ix, const uint32_t* codes_unsorted, int j_begin, int j_end, cudaStream_t s) {
   const int64_t n = ix->n;
+  const int nt = j_end - j_begin;
+  if (nt <= 0) return cudaSuccess;
   const int ntiles = int((n + kSortTile - 1) / kSortTile);
   // tables per group: bound the temporary buffers to ~1 GiB
-  int G = int(std::max<int64_t>(1, std::min<int64_t>(ix->L, (int64_t(1) << 30) / std::max<int64_t>(1, n * 16))));
+  int G = int(std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t(1) << 30) / std::max<int64_t>(1, n * 16))));
   uint32_t *tk = nullptr, *tv = nullptr, *cnt = nullptr;
   cudaError_t e;
   if ((e = cudaMallocAsync(&tk, sizeof(uint32_t) * size_t(n) * G, s)) != cudaSuccess) return e;
   if ((e = cudaMallocAsync(&tv, sizeof(uint32_t) * size_t(n) * G, s)) != cudaSuccess) return e;
   if ((e = cudaMallocAsync(&cnt, sizeof(uint32_t) * size_t(256) * ntiles * G, s)) != cudaSuccess) return e;
-  for (int j0 = 0; j0 < ix->L && e == cudaSuccess; j0 += G) {
-    const int g = std::min(G, ix->L - j0);
-    uint32_t* keys0 = codes_unsorted + int64_t(j0) * n;
+  for (int j0 = j_begin; j0 < j_end && e == cudaSuccess; j0 += G) {
+    const int g = std::min(G, j_end - j0);
+    const uint32_t* keys0 = codes_unsorted + int64_t(j0) * n;
     uint32_t* outk = ix->codes + int64_t(j0) * n;
     uint32_t* outv = ix->ids + int64_t(j0) * n;
     // pass buffers: in -> tmp -> out -> tmp -> out

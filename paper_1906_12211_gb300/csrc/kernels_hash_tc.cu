@@ -6,11 +6,12 @@
 // bfloat16 halves X = Xh + Xl (|x - xh - xl| <= 2^-18 |x| per entry) and
 //   X W^T ~= Xh W^T + Xl W^T
 // (two bfloat16 products, float32 accumulation in tensor memory).  The error
-// is below 2^-18 |x||w| for the split plus the float32 accumulation (at most
-// 2 * 4 * KB <= 40 MMA steps of 16 exact products, each step rounding with
-// relative error <= 2^-20 even for a truncating adder: < 4e-5 |x||w|), i.e.
-// < 5e-5 |w| for unit x.  The epilogue decides every hash bit with the rule
-// of the float64 definition and the band 2^-12 |w| = 2.44e-4 |w|: a decision
+// is below 2^-18 |x||w| for the split plus the float32 accumulation (2 * 4 *
+// KB MMAs of 16 exact products, at most 17 float32 roundings of a partial sum
+// bounded by |x||w| each, even for a truncating adder): 3.6e-5 |w| for unit x
+// and d_pad <= 128, 8.5e-5 |w| up to 320.  The epilogue decides every hash
+// bit with the rule of the float64 definition and the row's band, 2^-14 |w| =
+// 6.1e-5 |w| (d_pad <= 128) or 2^-12 |w| = 2.4e-4 |w| (params.cpp): a decision
 // closer to its boundary than the band is recomputed in float64 in index
 // order, which is the defining value (Sec. 2.2: HP bit = [<a,x> >= 0]; CP
 // value = sign and index of the largest |<a_c,x>|), so codes are
@@ -22,11 +23,14 @@
 //   - a unit of work is (P point tiles, segment); a segment is one repetition
 //     (CP: fns functions of d_pad rows, each cut into N tiles of at most 128
 //     rows; HP: a group of 4 repetitions = 128 rows) or a group of 2 sketches
-//     (128 rows); CTA b takes the contiguous units [b*U/G, (b+1)*U/G) of the
-//     U = point-tile groups * segments, so the CTAs' shares differ by at most
-//     one segment and each CTA loads the A tiles of only the one or two
-//     groups its range touches.  With P = 2 both point tiles are multiplied
-//     by every B tile the CTA loads, which halves the B stream from L2;
+//     (128 rows); while at least G groups of point tiles are left (G = the
+//     grid), CTA b takes whole groups b, b + G, ... with all their segments,
+//     so the CTAs walk the hash rows in step and each B tile comes from DRAM
+//     about once per round and from L2 for the other CTAs; the units of the
+//     last groups are split into equal contiguous ranges (the CTAs' shares
+//     differ by at most one segment, and each CTA loads the A tiles of only
+//     the one or two groups its range touches).  With P = 2 both point tiles
+//     are multiplied by every B tile the CTA loads, which halves the B stream;
 //   - warp 0 (one thread) is the TMA producer: the A tiles (Xh, Xl of the P
 //     point tiles, KB blocks of 64 columns each) once per run of segments,
 //     then for every N tile its B operand as KB boxes of 64 columns into a
@@ -87,7 +91,7 @@ struct HashArgs {
   int nsub;        // N tiles per CP function: ceil(d_pad / 128)
   int seg_tables;  // segments that are repetitions (CP) or groups of 4 repetitions (HP)
   int segs;        // + sketch groups of 2
-  int64_t units;   // point-tile groups * segs; CTA b takes units [b*units/grid, (b+1)*units/grid)
+  int64_t units;   // point-tile groups * segs (see Sched for their order)
   int stages;      // B ring stages
   int hold_b;      // diagnostics: issue no B loads, so that the waits on them expire
   uint32_t* codes;
@@ -348,12 +352,45 @@ struct Chunk {
   int pair, seg0, seg1;
 };
 
-__device__ __forceinline__ bool next_chunk(const HashArgs& A, int64_t& u, int64_t hi, Chunk& c) {
-  if (u >= hi) return false;
-  c.pair = int(u / A.segs);
-  c.seg0 = int(u - int64_t(c.pair) * A.segs);
-  c.seg1 = int(min(hi - int64_t(c.pair) * A.segs, int64_t(A.segs)));
-  u = int64_t(c.pair) * A.segs + c.seg1;
+// The CTA's work, in two phases.  While at least one group of point tiles per
+// CTA is left, CTA b takes whole groups b, b + G, b + 2G, ... (G = grid), each
+// with all its segments in order: the CTAs then walk the segments in step, so
+// each hash-row tile is read from DRAM about once per round of G groups and
+// served from L2 to the others, however large the rows are (a bigger index
+// than L2 holds would otherwise be re-read from DRAM for every group).  The
+// units (group, segment) of the last groups are then split into equal
+// contiguous ranges, one per CTA.
+struct Sched {
+  int64_t rr, rr_end;  // round-robin groups still to take: rr, rr + G, ... < rr_end
+  int64_t u, hi;       // then the units [u, hi) of the last groups
+};
+
+__device__ __forceinline__ Sched make_sched(const HashArgs& A) {
+  const int64_t G = gridDim.x, b = blockIdx.x;
+  const int64_t groups = A.units / A.segs;
+  const int64_t full = groups / G * G;  // groups taken whole, round robin
+  const int64_t tail = (groups - full) * A.segs;
+  Sched s;
+  s.rr = b;
+  s.rr_end = full;
+  s.u = full * A.segs + b * tail / G;
+  s.hi = full * A.segs + (b + 1) * tail / G;
+  return s;
+}
+
+__device__ __forceinline__ bool next_chunk(const HashArgs& A, Sched& s, Chunk& c) {
+  if (s.rr < s.rr_end) {
+    c.pair = int(s.rr);
+    c.seg0 = 0;
+    c.seg1 = A.segs;
+    s.rr += gridDim.x;
+    return true;
+  }
+  if (s.u >= s.hi) return false;
+  c.pair = int(s.u / A.segs);
+  c.seg0 = int(s.u - int64_t(c.pair) * A.segs);
+  c.seg1 = int(min(s.hi - int64_t(c.pair) * A.segs, int64_t(A.segs)));
+  s.u = int64_t(c.pair) * A.segs + c.seg1;
   return true;
 }
 
@@ -394,7 +431,7 @@ __device__ __forceinline__ void dot64x4(const float* __restrict__ wf, const int 
 // order of |v| up to the cut (less than 2^-16 |v|), ties to the smaller c.
 __device__ __forceinline__ uint32_t cp_key(uint32_t vbits, int c) {
   const uint32_t r = __funnelshift_l(vbits, vbits, 1);  // |v| << 1 | sign
-  return (r & 0xFFFFFF01u) | (uint32_t(127 - c) << 1);  // one logic op: c is a constant of the unrolled loop
+  return (r | 0xFEu) - 2u * uint32_t(c);
 }
 __device__ __forceinline__ float cp_key_abs(uint32_t k) { return __uint_as_float((k >> 1) & 0x7FFFFF80u); }
 __device__ __forceinline__ int cp_key_col(uint32_t k) { return 127 - int((k >> 1) & 0x7Fu); }
@@ -675,15 +712,13 @@ __global__ void __launch_bounds__(threads_for(P), 1) hash_tc_kernel(HashArgs A, 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_slot;
-  const int64_t u_lo = int64_t(blockIdx.x) * A.units / gridDim.x;
-  const int64_t u_hi = int64_t(blockIdx.x + 1) * A.units / gridDim.x;
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
     uint32_t stage = 0, items_done = 0;
-    int64_t u = u_lo;
+    Sched sc = make_sched(A);
     Chunk ch;
-    while (next_chunk(A, u, u_hi, ch)) {
+    while (next_chunk(A, sc, ch)) {
       const int seg0 = ch.seg0, seg1 = ch.seg1;
       if (items_done > 0 && !mbar_wait(smem_u32(&aempty), (items_done - 1) & 1)) { failed = 1; break; }
       mbar_expect_tx(smem_u32(&afull), uint32_t(kPair) * a_bytes);
@@ -713,9 +748,9 @@ __global__ void __launch_bounds__(threads_for(P), 1) hash_tc_kernel(HashArgs A, 
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer: both point tiles of the pair from every B stage
     uint32_t stage = 0, items_done = 0, g = 0;
-    int64_t u = u_lo;
+    Sched sc = make_sched(A);
     Chunk ch;
-    while (!failed && next_chunk(A, u, u_hi, ch)) {
+    while (!failed && next_chunk(A, sc, ch)) {
       const int seg0 = ch.seg0, seg1 = ch.seg1;
       if (!mbar_wait(smem_u32(&afull), items_done & 1)) { failed = 1; break; }
       ++items_done;
@@ -757,9 +792,9 @@ __global__ void __launch_bounds__(threads_for(P), 1) hash_tc_kernel(HashArgs A, 
     // thread = point, TMEM lane quarter = warp % 4 (the only quarter a warp may read)
     const int pt = (warp - 2) >> 2, quarter = warp & 3;
     uint32_t g = 0;
-    int64_t u = u_lo;
+    Sched sc = make_sched(A);
     Chunk ch;
-    while (!failed && next_chunk(A, u, u_hi, ch)) {
+    while (!failed && next_chunk(A, sc, ch)) {
       const int seg0 = ch.seg0, seg1 = ch.seg1;
       const int64_t p = int64_t(ch.pair * kPair + pt) * kBM + quarter * 32 + lane;
       EpiState st;

@@ -13,6 +13,14 @@
 
 namespace pf {
 
+// The recheck band of a hash row w is |w| * 2^-e: a tensor-core projection of a
+// unit point errs by at most 2^-18 |w| (the split of the point into bfloat16
+// halves) plus one float32 rounding of the partial sum per add inside each of
+// the 2 * 4 * ceil(d_pad / 64) MMAs of 16 products (17 adds, each within 2^-23
+// of a partial sum bounded by |w|): 3.6e-5 |w| for d_pad <= 128, under the band
+// 2^-14 |w| = 6.1e-5 |w|; 8.5e-5 |w| for d_pad <= 320, under 2^-12 |w|.
+int band_exponent(int d_pad) { return d_pad <= 128 ? 14 : 12; }
+
 namespace {
 
 // Philox4x32 with 10 rounds (Salmon et al., SC 2011).  State: four 32-bit
@@ -121,7 +129,7 @@ Layout make_layout(int family, int d) {
 // holding hyperplane c (zero for c >= d); HP table j owns rows j*32 + b; the
 // 64*M sketch rows follow.  Counter words: (col, row-in-table, table,
 // purpose), with row-in-table = f*d + c for CP.  thr[row] is the recheck band
-// 2^-12 * |a_row|_2 (for CP the largest band of the function, on every row of
+// |a_row|_2 * 2^-band_exponent (for CP the largest band of the function, on every row of
 // it): projections closer to a decision boundary than that are recomputed in
 // float64 by the kernels.
 void gen_hash_rows(uint64_t seed, int family, int L, int M, int d, const Layout& lay, float* W, float* thr) {
@@ -131,7 +139,7 @@ void gen_hash_rows(uint64_t seed, int family, int L, int M, int d, const Layout&
   auto norm_band = [&](const float* row) {
     double s = 0.0;
     for (int i = 0; i < d; ++i) s = s + double(row[i]) * double(row[i]);
-    return float(std::ldexp(std::sqrt(s), -12));
+    return float(std::ldexp(std::sqrt(s), -band_exponent(lay.d_pad)));
   };
   // the pseudo-random family keeps no rows for its repetitions (sign vectors instead)
   parallel_for(lay.rows_table > 0 ? L : 0, [&](int64_t j) {
@@ -176,7 +184,7 @@ void gen_pool_rows(uint64_t seed, int family, int m, int M, int d, const Layout&
   auto norm_band = [&](const float* row) {
     double s = 0.0;
     for (int i = 0; i < d; ++i) s = s + double(row[i]) * double(row[i]);
-    return float(std::ldexp(std::sqrt(s), -12));
+    return float(std::ldexp(std::sqrt(s), -band_exponent(lay.d_pad)));
   };
   parallel_for(m, [&](int64_t f) {
     const int64_t g = f / lay.fns, slot = f % lay.fns;

@@ -207,6 +207,8 @@ cudaError_t launch_pool_gather(const pf_index* ix, const uint32_t* gcodes, int64
 // leaves room for a CTA's uneven share; requests beyond a CTA's region are
 // rechecked inline (slower, the same codes).
 uint32_t recheck_capacity(const pf_index* ix, int64_t npts, int tables);
+// the recheck band of a hash row is its norm times 2^-band_exponent(d_pad) (params.cpp)
+int band_exponent(int d_pad);
 // tables: repetitions hashed with row-based functions (ix->L; 0 hashes sketches only)
 cudaError_t launch_hash_tc(const pf_index* ix, const __nv_bfloat16* xh, const __nv_bfloat16* xl, const float* x32,
                            int64_t npts, uint32_t* codes, int64_t cj, int64_t cp, uint64_t* sk, int64_t sm,
@@ -218,6 +220,8 @@ cudaError_t launch_hash_fht(const pf_index* ix, const float* x32, int64_t npts, 
 
 // Sort every repetition's (code, position) pairs and build the prefix tables.
 cudaError_t sort_tables(pf_index* ix, uint32_t* codes_unsorted, cudaStream_t s);
+// the stable LSD radix sort (and prefix tables) of repetitions [j_begin, j_end)
+cudaError_t lsd_sort_tables(pf_index* ix, const uint32_t* codes_unsorted, int j_begin, int j_end, cudaStream_t s);
 // skc[j][pos] = sk[j mod M][ids[j][pos]] for every repetition
 cudaError_t gather_table_sketches(const pf_index* ix, const uint64_t* sk, uint64_t* skc, cudaStream_t s);
 
