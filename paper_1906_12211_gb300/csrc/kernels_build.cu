@@ -158,9 +158,7 @@ cudaError_t launch_hash(const pf_index* ix, const float* x32, const __nv_bfloat1
 
 // ---------------------------------------------------------------------------
 // Per-repetition stable LSD radix sort of (code, position), 4 passes of 8 bits
-// (positions start as 0..n-1, so equal codes stay in position order, Sec. 4.2):
-// the sort of the repetitions whose codes crowd into a bucket too large for
-// the bucket sort of kernels_sort.cu (many identical points, for instance).
+// (positions start as 0..n-1, so equal codes stay in position order, Sec. 4.2).
 // Each pass: per-tile digit histograms -> one exclusive scan per repetition in
 // (digit, tile) order -> stable scatter.  Within a tile, keys are ranked chunk
 // by chunk (256 keys, one per thread) with warp match masks, so equal digits
@@ -292,9 +290,9 @@ cudaError_t gather_table_sketches(const pf_index* ix, const uint64_t* sk, uint64
   return cudaGetLastError();
 }
 
-cudaError_t lsd_sort_tables(pf_index* ix, const uint32_t* codes_unsorted, int j_begin, int j_end, cudaStream_t s) {
+cudaError_t sort_tables(pf_index* ix, const uint32_t* codes_unsorted, cudaStream_t s) {
   const int64_t n = ix->n;
-  const int nt = j_end - j_begin;
+  const int j_begin = 0, j_end = ix->L, nt = ix->L;
   if (nt <= 0) return cudaSuccess;
   const int ntiles = int((n + kSortTile - 1) / kSortTile);
   // tables per group: bound the temporary buffers to ~1 GiB

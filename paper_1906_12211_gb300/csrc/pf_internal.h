@@ -219,9 +219,7 @@ cudaError_t launch_hash_fht(const pf_index* ix, const float* x32, int64_t npts, 
                             int64_t cp, cudaStream_t s);
 
 // Sort every repetition's (code, position) pairs and build the prefix tables.
-cudaError_t sort_tables(pf_index* ix, uint32_t* codes_unsorted, cudaStream_t s);
-// the stable LSD radix sort (and prefix tables) of repetitions [j_begin, j_end)
-cudaError_t lsd_sort_tables(pf_index* ix, const uint32_t* codes_unsorted, int j_begin, int j_end, cudaStream_t s);
+cudaError_t sort_tables(pf_index* ix, const uint32_t* codes_unsorted, cudaStream_t s);
 // skc[j][pos] = sk[j mod M][ids[j][pos]] for every repetition
 cudaError_t gather_table_sketches(const pf_index* ix, const uint64_t* sk, uint64_t* skc, cudaStream_t s);
 
