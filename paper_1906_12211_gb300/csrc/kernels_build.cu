@@ -160,9 +160,9 @@ cudaError_t launch_hash(const pf_index* ix, const float* x32, const __nv_bfloat1
 // Per-repetition stable LSD radix sort of (code, position), 4 passes of 8 bits
 // (positions start as 0..n-1, so equal codes stay in position order, Sec. 4.2).
 // Each pass: per-tile digit histograms -> one exclusive scan per repetition in
-// (digit, tile) order -> stable scatter.  Within a tile, keys are ranked chunk
-// by chunk (256 keys, one per thread) with warp match masks, so equal digits
-// keep their input order.  No kernel waits on another CTA.
+// (digit, tile) order -> stable scatter.  Within a tile, each warp ranks its
+// own contiguous slice with warp match masks, so equal digits keep their input
+// order.  No kernel waits on another CTA.
 // ---------------------------------------------------------------------------
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
@@ -210,51 +210,60 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* __restrict__
   }
 }
 
+// Stable scatter of one tile: warp w ranks the keys of its contiguous 512-key
+// slice (item t of lane l is key w*512 + t*32 + l, so (w, t, l) is the input
+// order) with match masks against its own running digit counts, without
+// waiting for the other warps; then one CTA-wide pass turns the warps' digit
+// counts into offsets (the tile's offset of the digit, plus the counts of the
+// earlier warps), and every key goes to offset + its rank in its warp.
 __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, int ntiles, const uint32_t* __restrict__ offsets) {
-  __shared__ uint32_t base_off[256];
-  __shared__ uint32_t wcount[kSortThreads / 32][256];
+  constexpr int kWarps = kSortThreads / 32;
+  __shared__ uint32_t wcount[kWarps][256];  // per warp: digit counts, then digit offsets
   const int tile = blockIdx.x, tab = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t* ki = kin + int64_t(tab) * n;
   const uint32_t* vi = vin ? vin + int64_t(tab) * n : nullptr;
   uint32_t* ko = kout + int64_t(tab) * n;
   uint32_t* vo = vout + int64_t(tab) * n;
-  base_off[threadIdx.x] = offsets[(int64_t(tab) * 256 + threadIdx.x) * ntiles + tile];
-  for (int w = 0; w < kSortThreads / 32; ++w) wcount[w][threadIdx.x] = 0;
+  for (int w = 0; w < kWarps; ++w) wcount[w][threadIdx.x] = 0;
   __syncthreads();
-  const int64_t base = int64_t(tile) * kSortTile;
+  const int64_t base = int64_t(tile) * kSortTile + int64_t(warp) * 32 * kSortItems;
   const uint32_t lt_mask = (1u << lane) - 1u;
+  uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+#pragma unroll
   for (int t = 0; t < kSortItems; ++t) {
-    const int64_t i = base + int64_t(t) * kSortThreads + threadIdx.x;
+    const int64_t i = base + int64_t(t) * 32 + lane;
     const bool valid = i < n;
-    const uint32_t key = valid ? ki[i] : 0u;
-    const uint32_t val = valid ? (vi ? vi[i] : uint32_t(i)) : 0u;
-    const uint32_t dig = valid ? ((key >> shift) & 255u) : 256u;
+    key[t] = valid ? ki[i] : 0u;
+    val[t] = valid ? (vi ? vi[i] : uint32_t(i)) : 0u;
+    const uint32_t dig = valid ? ((key[t] >> shift) & 255u) : 256u;
     const uint32_t peers = __match_any_sync(0xffffffffu, dig);
-    const uint32_t rank = __popc(peers & lt_mask);
-    if (valid && rank == 0) wcount[warp][dig] = __popc(peers);
-    __syncthreads();
-    {  // per digit: prefix over warps, advance the running tile offset
-      const int dg = threadIdx.x;
-      uint32_t run = base_off[dg];
-      for (int w = 0; w < kSortThreads / 32; ++w) {
-        const uint32_t c = wcount[w][dg];
-        wcount[w][dg] = run;
-        run += c;
-      }
-      base_off[dg] = run;
+    rank[t] = valid ? wcount[warp][dig] + __popc(peers & lt_mask) : 0u;
+    __syncwarp();
+    if (valid && (peers & lt_mask) == 0) wcount[warp][dig] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {  // per digit: the tile's offset plus the counts of the earlier warps
+    const int dg = threadIdx.x;
+    uint32_t run = offsets[(int64_t(tab) * 256 + dg) * ntiles + tile];
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = wcount[w][dg];
+      wcount[w][dg] = run;
+      run += c;
     }
-    __syncthreads();
-    if (valid) {
-      const uint32_t pos = wcount[warp][dig] + rank;
-      ko[pos] = key;
-      vo[pos] = val;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < kSortItems; ++t) {
+    const int64_t i = base + int64_t(t) * 32 + lane;
+    if (i < n) {
+      const uint32_t pos = wcount[warp][(key[t] >> shift) & 255u] + rank[t];
+      ko[pos] = key[t];
+      vo[pos] = val[t];
     }
-    __syncthreads();
-    for (int w = 0; w < kSortThreads / 32; ++w) wcount[w][threadIdx.x] = 0;
-    __syncthreads();
   }
 }
 
