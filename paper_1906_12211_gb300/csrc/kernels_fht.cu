@@ -9,7 +9,9 @@
 //
 // One warp per point: lane t holds V = max(1, d''/32) consecutive coordinates
 // t*V .. t*V + V - 1 in registers; the butterfly passes h < V run inside a lane,
-// the passes h >= V pair lane t with lane t ^ (h / V) through shuffles.  Each
+// the passes h >= V pair lane t with lane t ^ (h / V) through shuffles.  Two
+// functions are transformed together, so that the shuffle chain of one hides
+// the latency of the other's.  Each
 // pass is the same pairwise operation (a, b) -> (a + b, a - b), lower index
 // first, as the float64 definition, so a recomputation in float64 in the same
 // order gives the definition's values bit for bit.  The transform runs in
@@ -35,6 +37,14 @@ struct FhtArgs {
   int64_t cj, cp;
 };
 
+// v <- D_r v for the lane's V coordinates (a set bit means -1)
+template <int V, class T>
+__device__ __forceinline__ void apply_signs(T (&v)[V], uint32_t bits) {
+#pragma unroll
+  for (int k = 0; k < V; ++k)
+    if ((bits >> k) & 1u) v[k] = -v[k];
+}
+
 // One pass of H over the warp's values (value i = lane * V + k).
 template <int V, class T>
 __device__ __forceinline__ void wht_pass(T (&v)[V], int lane, int n2) {
@@ -49,7 +59,9 @@ __device__ __forceinline__ void wht_pass(T (&v)[V], int lane, int n2) {
       }
   }
   const int lanes = n2 / V;  // lanes that hold coordinates (a power of two, <= 32)
-  for (int t = 1; t < lanes; t *= 2) {
+#pragma unroll
+  for (int t = 1; t < 32; t *= 2) {
+    if (t >= lanes) break;  // uniform in the warp
     const bool upper = lane & t;
 #pragma unroll
     for (int k = 0; k < V; ++k) {
@@ -59,12 +71,82 @@ __device__ __forceinline__ void wht_pass(T (&v)[V], int lane, int n2) {
   }
 }
 
-// v <- D_r v for the lane's V coordinates (a set bit means -1)
-template <int V, class T>
-__device__ __forceinline__ void apply_signs(T (&v)[V], uint32_t bits) {
+// The float32 transform of two functions at once (independent chains, so the
+// latency of one's shuffles hides behind the other's), signs given.
+template <int V>
+__device__ __forceinline__ void transform2(float (&a)[V], float (&b)[V], const uint32_t (&sa)[3],
+                                           const uint32_t (&sb)[3], int lane, int n2) {
 #pragma unroll
-  for (int k = 0; k < V; ++k)
-    if ((bits >> k) & 1u) v[k] = -v[k];
+  for (int r = 0; r < 3; ++r) {
+    apply_signs<V>(a, sa[r]);
+    apply_signs<V>(b, sb[r]);
+#pragma unroll
+    for (int h = 1; h < V; h *= 2) {
+#pragma unroll
+      for (int k = 0; k < V; ++k)
+        if (!(k & h)) {
+          const float a0 = a[k], a1 = a[k + h], b0 = b[k], b1 = b[k + h];
+          a[k] = a0 + a1;
+          a[k + h] = a0 - a1;
+          b[k] = b0 + b1;
+          b[k + h] = b0 - b1;
+        }
+    }
+    const int lanes = n2 / V;
+#pragma unroll
+    for (int t = 1; t < 32; t *= 2) {
+      if (t >= lanes) break;  // uniform in the warp
+      const bool upper = lane & t;
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        const float pa = __shfl_xor_sync(0xffffffffu, a[k], t);
+        const float pb = __shfl_xor_sync(0xffffffffu, b[k], t);
+        a[k] = upper ? pa - a[k] : a[k] + pa;
+        b[k] = upper ? pb - b[k] : b[k] + pb;
+      }
+    }
+  }
+}
+
+// The warp's largest |y| (a1, at index i1 with sign n1: first index on ties)
+// and the runner-up a2, of the lane's V values of a transform.
+struct Top2 {
+  float a1, a2;
+  uint32_t in;  // index | sign << 31
+};
+
+template <int V>
+__device__ __forceinline__ Top2 lane_top2(const float (&v)[V], int lane, bool live) {
+  Top2 t;
+  t.a1 = -1.f;
+  t.a2 = -1.f;
+  t.in = 0u;
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    const float a = fabsf(v[k]);
+    if (!live) continue;
+    if (a > t.a1) {
+      t.a2 = t.a1;
+      t.a1 = a;
+      t.in = uint32_t(lane * V + k) | (v[k] < 0.f ? 0x80000000u : 0u);
+    } else if (a > t.a2) {
+      t.a2 = a;
+    }
+  }
+  return t;
+}
+
+__device__ __forceinline__ void merge_top2(Top2& t, int off) {
+  const float o1 = __shfl_xor_sync(0xffffffffu, t.a1, off);
+  const float o2 = __shfl_xor_sync(0xffffffffu, t.a2, off);
+  const uint32_t oi = __shfl_xor_sync(0xffffffffu, t.in, off);
+  if (o1 > t.a1 || (o1 == t.a1 && (oi & 0x7FFFFFFFu) < (t.in & 0x7FFFFFFFu))) {
+    t.a2 = fmaxf(t.a1, o2);
+    t.a1 = o1;
+    t.in = oi;
+  } else {
+    t.a2 = fmaxf(t.a2, o1);
+  }
 }
 
 template <int V>
@@ -125,51 +207,37 @@ __global__ void __launch_bounds__(32 * kFhtWarps) hash_fht_kernel(FhtArgs A) {
     }
     for (int j = 0; j < A.L; ++j) {
       uint32_t code = 0;
-      for (int f = 0; f < A.fns; ++f) {
-        float v[V];
+      // two functions at a time (the second a copy of the first when fns is odd)
+      for (int f = 0; f < A.fns; f += 2) {
+        const int f2 = f + 1 < A.fns ? f + 1 : f;
+        uint32_t sa[3], sb[3];
 #pragma unroll
-        for (int k = 0; k < V; ++k) v[k] = x[k];
         for (int r = 0; r < 3; ++r) {
-          apply_signs<V>(v, lane_sign_bits<V>(A, j, f, r, lane));
-          wht_pass<V>(v, lane, A.n2);
+          sa[r] = lane_sign_bits<V>(A, j, f, r, lane);
+          sb[r] = lane_sign_bits<V>(A, j, f2, r, lane);
         }
-        // top two |y| of the warp, the top's index (first on ties) and sign
-        float a1 = -1.f, a2 = -1.f;
-        int i1 = 0;
-        bool n1 = false;
+        float va[V], vb[V];
 #pragma unroll
-        for (int k = 0; k < V; ++k) {
-          const float a = fabsf(v[k]);
-          if (!live) continue;
-          if (a > a1) {
-            a2 = a1;
-            a1 = a;
-            i1 = lane * V + k;
-            n1 = v[k] < 0.f;
-          } else if (a > a2) {
-            a2 = a;
-          }
-        }
+        for (int k = 0; k < V; ++k) va[k] = vb[k] = x[k];
+        transform2<V>(va, vb, sa, sb, lane, A.n2);
+        Top2 ta = lane_top2<V>(va, lane, live), tb = lane_top2<V>(vb, lane, live);
+#pragma unroll
         for (int t = 16; t >= 1; t >>= 1) {
-          const float o1 = __shfl_xor_sync(0xffffffffu, a1, t);
-          const float o2 = __shfl_xor_sync(0xffffffffu, a2, t);
-          const int oi = __shfl_xor_sync(0xffffffffu, i1, t);
-          const int on = __shfl_xor_sync(0xffffffffu, int(n1), t);
-          if (o1 > a1 || (o1 == a1 && oi < i1)) {
-            a2 = fmaxf(a1, o2);
-            a1 = o1;
-            i1 = oi;
-            n1 = on != 0;
-          } else {
-            a2 = fmaxf(a2, o1);
-          }
+          merge_top2(ta, t);
+          merge_top2(tb, t);
         }
-        uint32_t value;
-        if (a1 - a2 < A.gap || a1 <= A.sign)  // warp-uniform: every lane holds the reduced values
-          value = value64<V>(A, x, j, f, lane);
-        else
-          value = (uint32_t(n1) << (A.ell - 1)) | uint32_t(i1);
-        code |= value << (32 - A.ell * (f + 1));
+        const Top2 tt[2] = {ta, tb};
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int fu = u == 0 ? f : f2;
+          if (u == 1 && f2 == f) break;
+          uint32_t value;
+          if (tt[u].a1 - tt[u].a2 < A.gap || tt[u].a1 <= A.sign)  // warp-uniform: every lane holds the reduced values
+            value = value64<V>(A, x, j, fu, lane);
+          else
+            value = ((tt[u].in >> 31) << (A.ell - 1)) | (tt[u].in & 0x7FFFFFFFu);
+          code |= value << (32 - A.ell * (fu + 1));
+        }
       }
       if (lane == 0) A.codes[int64_t(j) * A.cj + p * A.cp] = code;
     }
