@@ -2,7 +2,7 @@
 transforms with random sign diagonals, after Andoni et al. 2015) in the library
 against the oracle's statement of it (oracle/fht.py): the sign vectors, the
 Monte-Carlo collision table, every point's and query's code, and the whole
-search, bit for bit.  Transform lengths 16 to 512 cover every register layout
+search, bit for bit.  Transform lengths 8 to 512 cover every register layout
 of the kernel (fewer coordinates than lanes, one per lane, 2 to 16 per lane);
 the data include rows whose top two |y| tie exactly (the zero vector, unit
 vectors, sums of two unit vectors), which exercise the float64 recomputation
@@ -21,7 +21,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 import paper_1906_12211_gb300 as pf  # noqa: E402
 
 DEV = torch.device("cuda:0")
-DIMS = [12, 20, 37, 100, 200, 300]  # transform lengths 16, 32, 64, 128, 256, 512
+DIMS = [5, 12, 20, 37, 100, 200, 300]  # transform lengths 8, 16, 32, 64, 128, 256, 512
 L = 12
 
 
