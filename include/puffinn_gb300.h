@@ -244,10 +244,11 @@ pf_status pf_index_search_noalloc(pf_index* index, const float* queries, int64_t
  * A 2-layer perceptron (hidden 256, ReLU) maps a query's features -- its
  * normalised vector and its first 64-bit sketch as +-1 -- to a distribution
  * over the prefix length at which the plain schedule K, K-1, ... stops.  With
- * opts->learned_start the search starts at min(K, q + 6), q the smallest depth
- * with P(stop depth > q) <= 0.05: the first round takes the block at that depth
- * at once (its sketch threshold refreshed every 32 repetitions), later rounds
- * drop one bit each.  The stop test of Lemma 1 still ends every query, so the
+ * opts->learned_start the search starts at min(K, q + m), q the smallest depth
+ * with P(stop depth > q) <= 0.05 and m = 0 (both settable with
+ * pf_learned_set_start_rule): the first round takes the block at that depth
+ * at once (its sketch threshold refreshed before repetitions 1, 2, 4, 8, 16
+ * and every 32 after), later rounds drop one bit each.  The stop test of Lemma 1 still ends every query, so the
  * recall guarantee is that of the plain method. */
 typedef struct {
   float final_loss;      /* mean cross-entropy of the last epoch */

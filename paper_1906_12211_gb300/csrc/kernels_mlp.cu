@@ -14,8 +14,8 @@
 // Training: float32 master weights, forward / backward with the tiled GEMM
 // and elementwise kernels below, Adam.  Inference: bfloat16 copies of W1 and
 // W2 with float32 accumulation, one warp per query; the start depth is
-// min(K, q + 6) with q the smallest d with P(stop depth > d) <= 0.05 under the
-// predicted distribution.
+// min(K, q + margin) with q the smallest d with P(stop depth > d) <= tail under
+// the predicted distribution (the index's start rule: 0.05 and 0 by default).
 #include <cuda_bf16.h>
 
 #include <algorithm>
