@@ -493,7 +493,7 @@ __device__ __forceinline__ void flat_stream(const Dev& P, const float* q, const 
       const uint32_t ap = o < ru.y ? ru.x + o : ru.z + (o - ru.y);
       at[u] = size_t(jr) * n + ap;
       jof[u] = jr;
-      id[u] = valid ? __ldg(P.ids + at[u]) : 0u;
+      id[u] = valid ? __ldcs(P.ids + at[u]) : 0u;
       pass[u] = valid;
     }
     if (P.filter) {
@@ -501,7 +501,7 @@ __device__ __forceinline__ void flat_stream(const Dev& P, const float* q, const 
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
         const uint64_t sk = !pass[u] ? 0ull
-                            : P.skc ? __ldg(P.skc + at[u])
+                            : P.skc ? __ldcs(P.skc + at[u])
                                     : __ldg(P.sk + size_t(jof[u] % M) * n + id[u]);
         hd[u] = sk ^ qsk[jof[u] % M];
       }
@@ -825,7 +825,9 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
                                         nb, wsize, ct);
         }
         // warp w takes chunks w, w + 4, ...: up to kSpan positions of one run,
-        // lane-strided so that every load instruction is coalesced
+        // lane-strided so that every load instruction is coalesced.  Ids and
+        // sketches are read once per round: their loads are marked evict-first,
+        // so that L2 keeps the rows that the scoring gathers instead
         for (uint32_t c = cpre[j0] + uint32_t(warp); c < c_end; c += kQW) {
           if (cpre[jc + 1] <= c) {  // chunk -> repetition (c only grows)
             do ++jc; while (cpre[jc + 1] <= c);
@@ -844,7 +846,7 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) {
             const uint32_t o = 32u * u + uint32_t(lane);
-            id[u] = o < cnt ? __ldg(P.ids + rowbase + o) : 0u;
+            id[u] = o < cnt ? __ldcs(P.ids + rowbase + o) : 0u;
           }
           if (P.filter) {
             uint64_t hd[kUnroll];
@@ -852,7 +854,7 @@ __global__ void __launch_bounds__(32 * QW, 32 / QW) search_kernel(Dev P) {
 #pragma unroll
               for (int u = 0; u < kUnroll; ++u) {
                 const uint32_t o = 32u * u + uint32_t(lane);
-                hd[u] = o < cnt ? __ldg(P.skc + rowbase + o) ^ qh : 0ull;
+                hd[u] = o < cnt ? __ldcs(P.skc + rowbase + o) ^ qh : 0ull;
               }
             } else {
               const uint64_t* skm = P.sk + size_t(jc % M) * n;
